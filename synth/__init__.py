@@ -1,0 +1,70 @@
+"""Seeded synthetic row streams shared by the tests, the bench and the oracle.
+
+This module only draws input data; it holds none of the sketching arithmetic.
+The recipe stands in for the paper's "Random Noisy" workload (Section 5.1.3:
+low-rank signal with a decaying spectrum plus Gaussian noise):
+
+    rows = g diag(sigma) V^T + eta,
+    g ~ N(0, 1)^{n x r},  V = Q factor of a d x r Gaussian (Householder QR,
+    diag(R) > 0),  eta ~ N(0, noise^2)^{n x d},
+
+generated in FP64 with numpy's Philox bit generator and rounded to FP32, so
+both the GPU path and the oracle consume the identical FP32 bytes.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=np.array([seed, stream], dtype=np.uint64)))
+
+
+def basis(d: int, r: int, seed: int = 0, stream: int = 0) -> np.ndarray:
+    """Random orthonormal d x r basis (Q of a Gaussian matrix, diag(R) > 0)."""
+    g = _rng(seed, 1_000_000 + stream).standard_normal((d, r))
+    q, rr = np.linalg.qr(g)
+    return q * np.sign(np.diag(rr))[None, :]
+
+
+def spectrum(kind: str, r: int) -> np.ndarray:
+    if kind == "geometric":          # sigma_i = 10 * 0.9^i, i = 0..r-1
+        return 10.0 * 0.9 ** np.arange(r)
+    if kind == "powerlaw":           # sigma_i = 1 / i, i = 1..r
+        return 1.0 / np.arange(1, r + 1)
+    raise ValueError(kind)
+
+
+def low_rank_noisy(n: int, d: int, r: int, sigma: np.ndarray, noise: float = 0.01,
+                   seed: int = 0, stream: int = 0, start: int = 0,
+                   V: np.ndarray | None = None) -> np.ndarray:
+    """Rows start..start+n-1 of the stream, FP32, C-contiguous (n x d).
+
+    Rows are drawn in chunks of 4096 keyed by chunk index, so any window of the
+    stream is reproducible without drawing the rows before it."""
+    if V is None:
+        V = basis(d, r, seed, stream)
+    out = np.empty((n, d), dtype=np.float32)
+    chunk = 4096
+    c0, c1 = start // chunk, (start + n + chunk - 1) // chunk
+    for c in range(c0, c1):
+        rng = _rng(seed, (stream << 32) + c)
+        g = rng.standard_normal((chunk, r))
+        eta = rng.standard_normal((chunk, d)) * noise
+        blk = (g * sigma[None, :]) @ V.T + eta
+        lo, hi = max(start, c * chunk), min(start + n, (c + 1) * chunk)
+        out[lo - start:hi - start] = blk[lo - c * chunk:hi - c * chunk]
+    return out
+
+
+# The workloads of the persistent setting (d, l, n, rank, spectrum).
+WORKLOADS = {
+    "small_d256_l32": dict(n=10_000, d=256, ell=32, r=20, spectrum="geometric"),
+    "tight_d4096_l1024": dict(n=1_000_000, d=4096, ell=1024, r=200, spectrum="powerlaw"),
+}
+
+
+def workload_rows(name: str, n: int | None = None, start: int = 0, seed: int = 0) -> np.ndarray:
+    w = WORKLOADS[name]
+    n = w["n"] if n is None else n
+    return low_rank_noisy(n, w["d"], w["r"], spectrum(w["spectrum"], w["r"]), seed=seed, start=start)
