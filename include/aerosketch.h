@@ -1,0 +1,166 @@
+/*
+ * aerosketch.h - C ABI of the GB300 AeroSketch update path.
+ *
+ * AeroSketch (arXiv 2601.02019) keeps a 2l x d residual buffer C, applies the
+ * exact Frequent Directions shrink when the buffer is full (Algorithm 4 lines
+ * 2-4), gates each update with a power iteration (Algorithm 1, Algorithm 4
+ * line 7-8), and moves components whose squared singular value reaches the
+ * threshold theta into snapshots (Z, Z^T C'^T C') found by a doubling
+ * simultaneous iteration (Algorithm 2, Algorithm 4 lines 9-17).  A query
+ * assembles B = C^T C + the snapshot terms and shrinks it by its l-th
+ * eigenvalue (Algorithm 5).  The persistent (ATTP) setting sets
+ * theta = eps ||A_t||_F^2 before every update (Algorithm 8).
+ *
+ * Every function returns an as_status.  Pointers named "host or device" may
+ * point to either; the library inspects them.  No function keeps a pointer the
+ * caller passed in after it returns.  All work is ordered on the CUDA stream
+ * given to sketch_create (NULL = the legacy default stream); functions that
+ * return data to the host synchronise that stream.
+ *
+ * Error behaviour: invalid arguments return AS_EINVAL without side effects;
+ * allocation failures return AS_ENOMEM and leave the sketch unchanged;
+ * conditions detected on the device (non-finite input, numerical breakdown,
+ * a bounded device wait that ran out) are recorded in a sticky status that the
+ * next synchronising call returns.
+ */
+#ifndef AEROSKETCH_H
+#define AEROSKETCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct as_sketch as_sketch; /* opaque; owns all of its device memory */
+
+typedef enum {
+  AS_OK = 0,
+  AS_EINVAL = 1,    /* bad argument or configuration, or non-finite input row */
+  AS_ENOMEM = 2,    /* device or host allocation failed */
+  AS_EDEVICE = 3,   /* a CUDA call failed */
+  AS_ENUMERIC = 4,  /* a factorisation broke down */
+  AS_ETIMEOUT = 5,  /* a bounded device-side wait ran out */
+  AS_EBUSY = 6,     /* the sketch is in use by another call */
+  AS_ENOTSUP = 7    /* valid request that this build does not implement */
+} as_status;
+
+/* The stream setting.  Only AS_PERSISTENT (Algorithm 8) and AS_FIXED_THETA
+ * (Algorithm 3 with a fixed dump threshold) are implemented; the others return
+ * AS_ENOTSUP from sketch_create. */
+typedef enum {
+  AS_PERSISTENT = 0,   /* theta = eps ||A_t||_F^2 before every update (Algorithm 8) */
+  AS_FIXED_THETA = 1,  /* theta = cfg.theta for the whole stream (Algorithm 3) */
+  AS_SLIDING = 2,      /* Algorithm 6: not implemented */
+  AS_SITE = 3,         /* Algorithm 10, site side: not implemented */
+  AS_COORDINATOR = 4   /* Algorithm 10, coordinator side: not implemented */
+} as_mode;
+
+/* Arithmetic of the d-side products (Gram cross terms, rebuild, snapshot).
+ * The G-space iterations and the small core factorisations use FP64 in both. */
+typedef enum {
+  AS_FP32_PLAIN = 0,   /* FP32 operands, FP64-combined accumulation */
+  AS_BF16 = 1          /* reserved: BF16 tensor-core operands (AS_ENOTSUP for now) */
+} as_precision;
+
+/* Flags. */
+#define AS_TRACE_DECISIONS 0x1u /* record every gate / doubling decision (sketch_trace) */
+
+typedef struct {
+  int32_t d;          /* row dimension, >= 2 */
+  int32_t ell;        /* sketch size l, 1 <= l <= d/2 (Section 2.3); 0 => ceil(2/eps) */
+  double eps;         /* error parameter; 0 => 2/l (Algorithm 3 line 1) */
+  int32_t mode;       /* as_mode */
+  int32_t prec;       /* as_precision */
+  double theta;       /* dump threshold for AS_FIXED_THETA (may be +inf) */
+  double eps_si;      /* simultaneous-iteration accuracy; 0 => 0.4 (Algorithm 4 line 11) */
+  int32_t k_pi;       /* power iterations; 0 => ceil(log2 d) + 1 (Corollary 1) */
+  int32_t q_si;       /* simultaneous-iteration products; 0 => ceil(ln d / eps_si) */
+  uint64_t seed;      /* Philox key word 0 for the method's random draws */
+  uint64_t stream_id; /* Philox key word 1 */
+  uint32_t flags;     /* AS_TRACE_DECISIONS */
+  uint32_t reserved;
+} as_config;
+
+typedef struct {
+  int64_t rows;            /* rows ingested (the current time T) */
+  int32_t ell, d;
+  int32_t rows_in_buffer;  /* r: filled rows of C */
+  int32_t reserved0;
+  double fro2;             /* ||A_T||_F^2 (FP64) */
+  double theta;            /* threshold in force after the last update */
+  int64_t shrinks;         /* FD shrinks (Algorithm 4 lines 2-4) */
+  int64_t gates;           /* rows whose power-iteration gate passed */
+  int64_t dumps;           /* snapshots taken */
+  int64_t snapshot_rank;   /* sum of xi over the snapshot queue */
+  int64_t si_runs;         /* simultaneous iterations run */
+  int64_t device_bytes;    /* device memory owned by the sketch */
+  int32_t device_status;   /* sticky as_status recorded on the device */
+  int32_t reserved1;
+} as_stats;
+
+/* One decision record (AS_TRACE_DECISIONS): a row whose gate passed. */
+typedef struct {
+  int64_t i;        /* timestamp of the row (1-based) */
+  double sig2_pi;   /* power-iteration estimate sigma_hat_1^2 (Algorithm 1) */
+  double theta;     /* threshold in force */
+  int32_t j_stop;   /* doubling step that broke the loop, 0 if none */
+  int32_t xi;       /* components dumped (Algorithm 4 line 13) */
+  double ritz_k;    /* sigma_hat_k^2 at the stopping step (or the last one) */
+  double ritz_1;    /* sigma_hat_1^2 at that step */
+} as_event;
+
+/* Create a sketch (Algorithm 3, and Algorithm 8's Initialize for
+ * AS_PERSISTENT).  `cuda_stream` is a cudaStream_t or NULL.  Allocates C
+ * (2l x d, FP32), G = C C^T (2l x 2l, FP64) and work space on the current
+ * device.  Returns AS_EINVAL for d < 2, l < 1, 2l > d, eps <= 0 or an unknown
+ * mode; AS_ENOTSUP for a mode or precision this build does not implement. */
+as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out);
+
+/* Feed n rows (Algorithm 4 for each row, preceded by Algorithm 8's threshold
+ * update in AS_PERSISTENT mode).  `rows` is host or device memory holding n
+ * rows of d FP32 values, row t at rows + t*ld (ld >= d).  n = 0 is a no-op.
+ * The call returns once the rows are consumed; `rows` may then be reused.
+ * Returns AS_EINVAL (and ingests nothing from that row on) if a row holds a
+ * non-finite value. */
+as_status sketch_update(as_sketch* h, const float* rows, int64_t n, int64_t ld);
+
+/* Algorithm 5 at the current time (t = -1; other t return AS_ENOTSUP):
+ * writes the l x d sketch B_hat, row-major with leading dimension ldo >= d,
+ * to `out` (host or device), and the number of rows written (l) to
+ * *rows_out.  Synchronises. */
+as_status sketch_query(as_sketch* h, int64_t t, float* out, int64_t ldo, int32_t* rows_out);
+
+/* The matrix B of Algorithm 5 lines 1-4 at the current time (before its
+ * eigendecomposition): d x d FP64, row-major, to host memory `out`.
+ * Synchronises. */
+as_status sketch_query_gram(as_sketch* h, double* out);
+
+/* Copy the residual buffer C (2l x d FP32, row-major, leading dimension d)
+ * and the row count r to host memory.  Synchronises. */
+as_status sketch_get_buffer(as_sketch* h, float* out, int32_t* r_out);
+
+/* Merge src into dst by decomposability (Appendix E, the sum of per-part
+ * errors bounds the error of the union): dst's query then covers both
+ * streams.  Requires equal d.  Not implemented in this build: AS_ENOTSUP. */
+as_status sketch_merge(as_sketch* dst, const as_sketch* src);
+
+/* Counters and the sticky device status.  Synchronises. */
+as_status sketch_stats(as_sketch* h, as_stats* out);
+
+/* Decision records (AS_TRACE_DECISIONS).  Copies up to `cap` records, oldest
+ * first, to host memory `out` and writes the total count to *count. */
+as_status sketch_trace(as_sketch* h, as_event* out, int64_t cap, int64_t* count);
+
+/* Free every resource of the sketch.  NULL is a no-op. */
+as_status sketch_destroy(as_sketch* h);
+
+/* Static string naming a status. */
+const char* as_status_str(as_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AEROSKETCH_H */

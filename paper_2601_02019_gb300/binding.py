@@ -1,0 +1,175 @@
+"""ctypes binding of include/aerosketch.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as ct
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libaerosketch.so")
+
+AS_OK, AS_EINVAL, AS_ENOMEM, AS_EDEVICE, AS_ENUMERIC, AS_ETIMEOUT, AS_EBUSY, AS_ENOTSUP = range(8)
+AS_PERSISTENT, AS_FIXED_THETA, AS_SLIDING, AS_SITE, AS_COORDINATOR = range(5)
+AS_FP32_PLAIN, AS_BF16 = 0, 1
+AS_TRACE_DECISIONS = 0x1
+
+EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram", "sketch_get_buffer",
+            "sketch_merge", "sketch_stats", "sketch_trace", "sketch_destroy", "as_status_str")
+
+
+class AsConfig(ct.Structure):
+    _fields_ = [("d", ct.c_int32), ("ell", ct.c_int32), ("eps", ct.c_double), ("mode", ct.c_int32),
+                ("prec", ct.c_int32), ("theta", ct.c_double), ("eps_si", ct.c_double), ("k_pi", ct.c_int32),
+                ("q_si", ct.c_int32), ("seed", ct.c_uint64), ("stream_id", ct.c_uint64), ("flags", ct.c_uint32),
+                ("reserved", ct.c_uint32)]
+
+
+class AsStats(ct.Structure):
+    _fields_ = [("rows", ct.c_int64), ("ell", ct.c_int32), ("d", ct.c_int32), ("rows_in_buffer", ct.c_int32),
+                ("reserved0", ct.c_int32), ("fro2", ct.c_double), ("theta", ct.c_double),
+                ("shrinks", ct.c_int64), ("gates", ct.c_int64), ("dumps", ct.c_int64),
+                ("snapshot_rank", ct.c_int64), ("si_runs", ct.c_int64), ("device_bytes", ct.c_int64),
+                ("device_status", ct.c_int32), ("reserved1", ct.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
+
+
+class AsEvent(ct.Structure):
+    _fields_ = [("i", ct.c_int64), ("sig2_pi", ct.c_double), ("theta", ct.c_double), ("j_stop", ct.c_int32),
+                ("xi", ct.c_int32), ("ritz_k", ct.c_double), ("ritz_1", ct.c_double)]
+
+
+class AeroSketchError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {lib().as_status_str(code).decode()}")
+
+
+_LIB = None
+
+
+def load_library(path: str = LIB_PATH) -> ct.CDLL:
+    """Load libaerosketch.so and declare every exported signature."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2601_02019_gb300/build.py")
+    L = ct.CDLL(path)
+    P, I64, I32 = ct.c_void_p, ct.c_int64, ct.c_int32
+    L.sketch_create.argtypes = [ct.POINTER(AsConfig), P, ct.POINTER(P)]
+    L.sketch_update.argtypes = [P, P, I64, I64]
+    L.sketch_query.argtypes = [P, I64, P, I64, ct.POINTER(I32)]
+    L.sketch_query_gram.argtypes = [P, P]
+    L.sketch_get_buffer.argtypes = [P, P, ct.POINTER(I32)]
+    L.sketch_merge.argtypes = [P, P]
+    L.sketch_stats.argtypes = [P, ct.POINTER(AsStats)]
+    L.sketch_trace.argtypes = [P, ct.POINTER(AsEvent), I64, ct.POINTER(I64)]
+    L.sketch_destroy.argtypes = [P]
+    L.as_status_str.argtypes = [ct.c_int]
+    L.as_status_str.restype = ct.c_char_p
+    for name in EXPORTED:
+        if name != "as_status_str":
+            getattr(L, name).restype = ct.c_int
+    _LIB = L
+    return L
+
+
+def lib() -> ct.CDLL:
+    return load_library()
+
+
+def _check(code: int, what: str) -> None:
+    if code != AS_OK:
+        raise AeroSketchError(code, what)
+
+
+def _ptr(x) -> int:
+    """Address of a numpy array (host) or a torch tensor (host or device)."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x.data_ptr())
+
+
+class Sketch:
+    """One AeroSketch stream on the current CUDA device (the C ABI's as_sketch)."""
+
+    def __init__(self, d: int, ell: int = 0, eps: float = 0.0, *, mode: int = AS_PERSISTENT,
+                 prec: int = AS_FP32_PLAIN, theta: float = 0.0, eps_si: float = 0.0, k_pi: int = 0,
+                 q_si: int = 0, seed: int = 0, stream_id: int = 0, trace: bool = False, stream=None):
+        L = lib()
+        cfg = AsConfig(d=d, ell=ell, eps=eps, mode=mode, prec=prec, theta=theta, eps_si=eps_si, k_pi=k_pi,
+                       q_si=q_si, seed=seed, stream_id=stream_id, flags=AS_TRACE_DECISIONS if trace else 0)
+        h = ct.c_void_p()
+        sp = None if stream is None else ct.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        _check(L.sketch_create(ct.byref(cfg), sp, ct.byref(h)), "sketch_create")
+        self._h = h
+        self.d = d
+        self.ell = self.stats()["ell"]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().sketch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, rows, ld: int | None = None) -> None:
+        """rows: (n, d) float32 numpy array (host) or torch tensor (host or device)."""
+        n = int(rows.shape[0])
+        if ld is None:
+            ld = int(rows.strides[0] // 4) if isinstance(rows, np.ndarray) else int(rows.stride(0))
+        if isinstance(rows, np.ndarray):
+            assert rows.dtype == np.float32 and rows.strides[1] == 4
+        _check(lib().sketch_update(self._h, ct.c_void_p(_ptr(rows)), n, ld), "sketch_update")
+
+    def query(self) -> np.ndarray:
+        out = np.zeros((self.ell, self.d), dtype=np.float32)
+        rows = ct.c_int32()
+        _check(lib().sketch_query(self._h, -1, ct.c_void_p(out.ctypes.data), self.d, ct.byref(rows)),
+               "sketch_query")
+        return out[: rows.value]
+
+    def query_gram(self) -> np.ndarray:
+        out = np.zeros((self.d, self.d), dtype=np.float64)
+        _check(lib().sketch_query_gram(self._h, ct.c_void_p(out.ctypes.data)), "sketch_query_gram")
+        return out
+
+    def buffer(self) -> tuple[np.ndarray, int]:
+        out = np.zeros((2 * self.ell, self.d), dtype=np.float32)
+        r = ct.c_int32()
+        _check(lib().sketch_get_buffer(self._h, ct.c_void_p(out.ctypes.data), ct.byref(r)), "sketch_get_buffer")
+        return out, r.value
+
+    def stats(self) -> dict:
+        s = AsStats()
+        _check(lib().sketch_stats(self._h, ct.byref(s)), "sketch_stats")
+        return s.as_dict()
+
+    def trace(self) -> list[dict]:
+        n = ct.c_int64()
+        _check(lib().sketch_trace(self._h, None, 0, ct.byref(n)), "sketch_trace")
+        arr = (AsEvent * max(1, n.value))()
+        _check(lib().sketch_trace(self._h, arr, n.value, ct.byref(n)), "sketch_trace")
+        return [{f: getattr(arr[t], f) for f, _ in AsEvent._fields_} for t in range(n.value)]
+
+    def merge(self, other: "Sketch") -> None:
+        _check(lib().sketch_merge(self._h, other._h), "sketch_merge")
+
+
+def replay_from_trace(events: list[dict]) -> dict:
+    """Decision record in the oracle's replay format (rows whose gate passed,
+    and the doubling step and xi of each)."""
+    return {"fired": {int(e["i"]) for e in events},
+            "si": {int(e["i"]): (int(e["j_stop"]), int(e["xi"])) for e in events}}
+
+
+def default_k_pi(d: int) -> int:
+    return int(math.ceil(math.log2(d))) + 1

@@ -1,0 +1,534 @@
+// The sketch state machine and the C ABI (include/aerosketch.h).
+//
+// Device state of one sketch:
+//   C      2l x ldc FP32  residual buffer (rows >= r are zero)
+//   G      2l x 2l  FP64  Gram C C^T of the stored buffer
+//   arena  FP32           snapshot store: for each snapshot Z (d x xi, row-major)
+//                         followed by Y = Z^T C'^T C' (xi x d, row-major)
+// The host walks Algorithm 4 row by row; every arithmetic step runs in the
+// kernels, and the host reads back only the scalars that decide the branches
+// (||a_i||^2, the power-iteration estimate, the Ritz values).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "eig.cuh"
+#include "kernels.cuh"
+
+using namespace as;
+
+namespace {
+
+struct Snap {
+  size_t off;  // offset in floats of Z in the arena; Y follows at off + d*xi
+  int xi;
+  int64_t s, t;
+};
+
+template <typename T>
+as_status dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) { cudaGetLastError(); *p = nullptr; return AS_ENOMEM; }
+  return AS_OK;
+}
+
+int ceil_log2(int64_t x) {  // smallest c with 2^c >= x, x >= 1
+  int c = 0;
+  while ((int64_t(1) << c) < x) ++c;
+  return c;
+}
+
+}  // namespace
+
+struct as_sketch {
+  as_config cfg{};
+  int d = 0, ell = 0, n2 = 0, ldc = 0, k_pi = 0, q = 0, jmax = 0, mode = 0;
+  double eps = 0, eps_si = 0, theta = 0;
+  cudaStream_t s = nullptr;
+  Key key{};
+  // device buffers
+  float *C = nullptr, *Cnew = nullptr, *Wfd = nullptr, *stage = nullptr;
+  double *G = nullptr, *Gtmp = nullptr, *lam = nullptr, *U = nullptr, *eigw = nullptr, *scal = nullptr;
+  int *bad = nullptr, *dstatus = nullptr;
+  SiBuffers si{};
+  double* h_buf = nullptr;  // pinned host scratch for branch scalars
+  int stage_rows = 0;
+  // host mirror of the control state
+  int r = 0;
+  int64_t T = 0;
+  double F = 0.0;
+  float* arena = nullptr;
+  size_t arena_cap = 0, arena_used = 0;
+  std::vector<Snap> snaps;
+  as_stats st{};
+  std::vector<as_event> trace;
+  size_t dev_bytes = 0;
+  std::mutex mu;
+};
+
+namespace {
+
+void free_all(as_sketch* h) {
+  float* fp[] = {h->C, h->Cnew, h->Wfd, h->stage, h->arena};
+  for (float* p : fp) if (p) cudaFree(p);
+  double* dp[] = {h->G, h->Gtmp, h->lam, h->U, h->eigw, h->scal, h->si.Y, h->si.GY, h->si.S, h->si.V,
+                  h->si.eigw, h->si.ritz, h->si.WU, h->si.GWU, h->si.tmp};
+  for (double* p : dp) if (p) cudaFree(p);
+  if (h->bad) cudaFree(h->bad);
+  if (h->dstatus) cudaFree(h->dstatus);
+  if (h->h_buf) cudaFreeHost(h->h_buf);
+}
+
+as_status sync_status(as_sketch* h) {
+  AS_CUDA_TRY(cudaStreamSynchronize(h->s));
+  int ds = 0;
+  AS_CUDA_TRY(cudaMemcpy(&ds, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+  return (as_status)ds;
+}
+
+// Read `n` doubles from device memory into the pinned host buffer (synchronising).
+as_status fetch(as_sketch* h, const double* src, int n) {
+  AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf, src, n * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  AS_CUDA_TRY(cudaStreamSynchronize(h->s));
+  return AS_OK;
+}
+
+as_status arena_reserve(as_sketch* h, size_t extra) {
+  if (h->arena_used + extra <= h->arena_cap) return AS_OK;
+  size_t cap = h->arena_cap ? h->arena_cap : (size_t)8 * h->d * h->ell;
+  while (cap < h->arena_used + extra) cap *= 2;
+  float* na = nullptr;
+  as_status st = dalloc(&na, cap);
+  if (st != AS_OK) return st;
+  if (h->arena_used)
+    AS_CUDA_TRY(cudaMemcpyAsync(na, h->arena, h->arena_used * sizeof(float), cudaMemcpyDeviceToDevice, h->s));
+  AS_CUDA_TRY(cudaStreamSynchronize(h->s));
+  if (h->arena) cudaFree(h->arena);
+  h->dev_bytes += (cap - h->arena_cap) * sizeof(float);
+  h->arena = na;
+  h->arena_cap = cap;
+  return AS_OK;
+}
+
+// Algorithm 4 lines 3-4: FD shrink of the full buffer through its Gram.
+as_status fd_shrink(as_sketch* h) {
+  const int n2 = h->n2, ell = h->ell, d = h->d;
+  AS_CUDA_TRY(cudaMemcpyAsync(h->Gtmp, h->G, (size_t)n2 * n2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+  as_status st = launch_eig(h->s, n2, h->Gtmp, n2, ell, h->lam, h->U, ell, h->eigw);
+  if (st != AS_OK) return st;
+  st = launch_shrink_weights(h->s, n2, ell, h->lam, h->U, h->Wfd);
+  if (st != AS_OK) return st;
+  AS_CUDA_TRY(cudaMemsetAsync(h->Cnew, 0, (size_t)n2 * h->ldc * sizeof(float), h->s));
+  if (ell > 1) {
+    st = gemm_strided<float, float, float>(h->s, ell - 1, d, n2, h->Wfd, n2, 1, h->C, h->ldc, 1, h->Cnew, h->ldc,
+                                           1, 1.0, 0.0);
+    if (st != AS_OK) return st;
+  }
+  std::swap(h->C, h->Cnew);
+  AS_CUDA_TRY(cudaMemsetAsync(h->G, 0, (size_t)n2 * n2 * sizeof(double), h->s));
+  if (ell > 1) {
+    st = gemm_strided<float, float, double>(h->s, ell - 1, ell - 1, d, h->C, h->ldc, 1, h->C, 1, h->ldc, h->G, n2,
+                                            1, 1.0, 0.0);
+    if (st != AS_OK) return st;
+  }
+  h->r = ell - 1;
+  h->st.shrinks++;
+  return AS_OK;
+}
+
+// Algorithm 4 lines 14-16 for the first xi columns of the last SI (k columns).
+as_status dump(as_sketch* h, int xi, int k, int64_t i) {
+  const int d = h->d, r = h->r, ldc = h->ldc, n2 = h->n2;
+  as_status st = arena_reserve(h, (size_t)2 * d * xi);
+  if (st != AS_OK) return st;
+  float* Z = h->arena + h->arena_used;
+  float* Y = Z + (size_t)d * xi;
+  // Z = C'^T (W U)_xi   (d x xi)
+  st = gemm_strided<float, double, float>(h->s, d, xi, r, h->C, 1, ldc, h->si.WU, k, 1, Z, xi, 1, 1.0, 0.0);
+  if (st != AS_OK) return st;
+  // Y = (G W U)_xi^T C' = Z^T C'^T C'   (xi x d)
+  st = gemm_strided<double, float, float>(h->s, xi, d, r, h->si.GWU, 1, k, h->C, ldc, 1, Y, d, 1, 1.0, 0.0);
+  if (st != AS_OK) return st;
+  // C = C' - C' Z Z^T = C' - (G W U)_xi Z^T
+  st = gemm_strided<double, float, float>(h->s, r, d, xi, h->si.GWU, k, 1, Z, 1, xi, h->C, ldc, 1, -1.0, 1.0);
+  if (st != AS_OK) return st;
+  // G = C C^T = G - (G W U)_xi (G W U)_xi^T   (W U is G-orthonormal)
+  st = gemm_strided<double, double, double>(h->s, r, r, xi, h->si.GWU, k, 1, h->si.GWU, 1, k, h->G, n2, 1, -1.0,
+                                            1.0);
+  if (st != AS_OK) return st;
+  const int64_t s_prev = h->snaps.empty() ? 1 : h->snaps.back().t + 1;
+  h->snaps.push_back(Snap{h->arena_used, xi, s_prev, i});
+  h->arena_used += (size_t)2 * d * xi;
+  h->st.dumps++;
+  h->st.snapshot_rank += xi;
+  return AS_OK;
+}
+
+// Algorithm 8 (threshold) + Algorithm 4 for one row already staged on the device.
+as_status update_row(as_sketch* h, const float* drow) {
+  const int d = h->d, n2 = h->n2;
+  as_status st = launch_ingest(h->s, drow, d, 1, d, h->C, h->ldc, h->r, h->scal, h->bad);
+  if (st != AS_OK) return st;
+  AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  int hbad = 0;
+  AS_CUDA_TRY(cudaMemcpyAsync(&hbad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  AS_CUDA_TRY(cudaStreamSynchronize(h->s));
+  if (hbad) {
+    AS_CUDA_TRY(cudaMemsetAsync(h->bad, 0, sizeof(int), h->s));
+    AS_CUDA_TRY(cudaMemsetAsync(h->C + (size_t)h->r * h->ldc, 0, (size_t)h->ldc * sizeof(float), h->s));
+    AS_CUDA_TRY(cudaStreamSynchronize(h->s));
+    return AS_EINVAL;
+  }
+  const double a2 = h->h_buf[0];
+  h->T += 1;
+  const int64_t i = h->T;
+  if (h->mode == AS_PERSISTENT) {  // Algorithm 8 lines 2-3
+    h->F += a2;
+    h->theta = h->eps * h->F;
+  } else {
+    h->F += a2;
+  }
+  const double theta = h->theta;
+  // line 1: insert into the first empty row, extend G
+  st = launch_gram_rows(h->s, h->C, h->ldc, d, h->r, 1, h->G, n2);
+  if (st != AS_OK) return st;
+  h->r += 1;
+  // lines 2-4
+  if (h->r == n2) {
+    st = fd_shrink(h);
+    if (st != AS_OK) return st;
+  }
+  // line 7: power iteration on C'^T
+  st = launch_power_iteration(h->s, h->G, n2, h->r, h->k_pi, h->key, (uint64_t)i, h->scal);
+  if (st != AS_OK) return st;
+  st = fetch(h, h->scal, 1);
+  if (st != AS_OK) return st;
+  const double sig2 = h->h_buf[0];
+  // line 8
+  if (!(sig2 >= theta / 2.0 && sig2 > 0.0)) return AS_OK;
+  h->st.gates++;
+  as_event ev{};
+  ev.i = i;
+  ev.sig2_pi = sig2;
+  ev.theta = theta;
+  for (int j = 1; j <= h->jmax; ++j) {              // line 9
+    const int k = std::min(std::min(1 << std::min(j, 30), h->ell), h->d);  // line 10
+    st = launch_simul_iter(h->s, h->G, n2, h->r, k, h->q, h->key, (uint64_t)i, j, h->si, h->dstatus);  // line 11
+    if (st != AS_OK) return st;
+    st = fetch(h, h->si.ritz, k);
+    if (st != AS_OK) return st;
+    h->st.si_runs++;
+    const double* ritz = h->h_buf;
+    ev.ritz_1 = ritz[0];
+    ev.ritz_k = ritz[k - 1];
+    if (ritz[k - 1] < theta) {                      // line 12
+      int xi = 0;                                   // line 13
+      for (int c = 0; c < k; ++c)
+        if (ritz[c] >= theta && ritz[c] > 0.0) ++xi;
+      ev.j_stop = j;
+      ev.xi = xi;
+      if (xi >= 1) {                                // lines 14-16
+        st = dump(h, xi, k, i);
+        if (st != AS_OK) return st;
+      }
+      break;                                        // line 17
+    }
+  }
+  if (h->cfg.flags & AS_TRACE_DECISIONS) h->trace.push_back(ev);
+  return AS_OK;
+}
+
+as_status build_query_gram(as_sketch* h, double* B) {
+  const int d = h->d;
+  as_status st = AS_OK;
+  AS_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)d * d * sizeof(double), h->s));
+  if (h->r > 0) {
+    st = gemm_strided<float, float, double>(h->s, d, d, h->r, h->C, 1, h->ldc, h->C, h->ldc, 1, B, d, 1, 1.0, 0.0);
+    if (st != AS_OK) return st;
+  }
+  int ximax = 1;
+  for (const Snap& sn : h->snaps) ximax = std::max(ximax, sn.xi);
+  double *YZ = nullptr, *T = nullptr;
+  st = dalloc(&YZ, (size_t)ximax * ximax);
+  if (st != AS_OK) return st;
+  st = dalloc(&T, (size_t)d * ximax);
+  if (st != AS_OK) { cudaFree(YZ); return st; }
+  for (const Snap& sn : h->snaps) {
+    const float* Z = h->arena + sn.off;
+    const float* Y = Z + (size_t)d * sn.xi;
+    const int xi = sn.xi;
+    // B += Z Y + (Z Y)^T - Z (Y Z) Z^T   (Algorithm 5 line 4)
+    if ((st = gemm_strided<float, float, double>(h->s, d, d, xi, Z, xi, 1, Y, d, 1, B, d, 1, 1.0, 1.0)) != AS_OK) break;
+    if ((st = gemm_strided<float, float, double>(h->s, d, d, xi, Z, xi, 1, Y, d, 1, B, 1, d, 1.0, 1.0)) != AS_OK) break;
+    if ((st = gemm_strided<float, float, double>(h->s, xi, xi, d, Y, d, 1, Z, xi, 1, YZ, xi, 1, 1.0, 0.0)) != AS_OK) break;
+    if ((st = gemm_strided<float, double, double>(h->s, d, xi, xi, Z, xi, 1, YZ, xi, 1, T, xi, 1, 1.0, 0.0)) != AS_OK) break;
+    if ((st = gemm_strided<double, float, double>(h->s, d, d, xi, T, xi, 1, Z, 1, xi, B, d, 1, -1.0, 1.0)) != AS_OK) break;
+  }
+  cudaStreamSynchronize(h->s);
+  cudaFree(YZ);
+  cudaFree(T);
+  return st;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* as_status_str(as_status s) {
+  switch (s) {
+    case AS_OK: return "AS_OK";
+    case AS_EINVAL: return "AS_EINVAL";
+    case AS_ENOMEM: return "AS_ENOMEM";
+    case AS_EDEVICE: return "AS_EDEVICE";
+    case AS_ENUMERIC: return "AS_ENUMERIC";
+    case AS_ETIMEOUT: return "AS_ETIMEOUT";
+    case AS_EBUSY: return "AS_EBUSY";
+    case AS_ENOTSUP: return "AS_ENOTSUP";
+  }
+  return "AS_UNKNOWN";
+}
+
+as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out) {
+  if (!cfg || !out) return AS_EINVAL;
+  *out = nullptr;
+  as_config c = *cfg;
+  if (c.d < 2) return AS_EINVAL;
+  if (!(c.eps >= 0.0) || std::isinf(c.eps)) return AS_EINVAL;
+  if (c.ell == 0) {
+    if (c.eps <= 0.0) return AS_EINVAL;
+    c.ell = (int32_t)std::ceil(2.0 / c.eps);  // Algorithm 3 line 1
+  }
+  if (c.ell < 1 || 2 * (int64_t)c.ell > c.d) return AS_EINVAL;
+  if (c.eps == 0.0) c.eps = 2.0 / c.ell;
+  if (c.mode != AS_PERSISTENT && c.mode != AS_FIXED_THETA) {
+    if (c.mode >= AS_SLIDING && c.mode <= AS_COORDINATOR) return AS_ENOTSUP;
+    return AS_EINVAL;
+  }
+  if (c.mode == AS_FIXED_THETA && !(c.theta >= 0.0)) return AS_EINVAL;
+  if (c.prec != AS_FP32_PLAIN) return (c.prec == AS_BF16) ? AS_ENOTSUP : AS_EINVAL;
+  if (c.eps_si == 0.0) c.eps_si = 0.4;
+  if (!(c.eps_si > 0.0 && c.eps_si < 1.0)) return AS_EINVAL;
+  if (c.k_pi < 0 || c.q_si < 0) return AS_EINVAL;
+  if (c.k_pi == 0) c.k_pi = ceil_log2(c.d) + 1;                              // Corollary 1
+  if (c.q_si == 0) c.q_si = (int32_t)std::ceil(std::log((double)c.d) / c.eps_si);  // Theta(log d / eps_SI)
+
+  as_sketch* h = new (std::nothrow) as_sketch();
+  if (!h) return AS_ENOMEM;
+  h->cfg = c;
+  h->d = c.d;
+  h->ell = c.ell;
+  h->n2 = 2 * c.ell;
+  h->ldc = (c.d + 63) / 64 * 64;
+  h->eps = c.eps;
+  h->eps_si = c.eps_si;
+  h->k_pi = c.k_pi;
+  h->q = c.q_si;
+  h->mode = c.mode;
+  h->theta = (c.mode == AS_FIXED_THETA) ? c.theta : 0.0;
+  const int mn = std::min(c.ell, c.d);
+  h->jmax = (mn > 1) ? ceil_log2(mn) : 0;
+  h->s = (cudaStream_t)cuda_stream;
+  h->key = Key{c.seed, c.stream_id};
+  h->stage_rows = 256;
+
+  const int n2 = h->n2, ell = h->ell, kmax = ell;
+  size_t bytes = 0;
+  as_status st = AS_OK;
+#define ALLOC(ptr, n)                                          \
+  do {                                                         \
+    if (st == AS_OK) {                                         \
+      st = dalloc(&(ptr), (n));                                \
+      bytes += (size_t)(n) * sizeof(*(ptr));                   \
+    }                                                          \
+  } while (0)
+  ALLOC(h->C, (size_t)n2 * h->ldc);
+  ALLOC(h->Cnew, (size_t)n2 * h->ldc);
+  ALLOC(h->Wfd, (size_t)ell * n2);
+  ALLOC(h->stage, (size_t)h->stage_rows * h->d);
+  ALLOC(h->G, (size_t)n2 * n2);
+  ALLOC(h->Gtmp, (size_t)n2 * n2);
+  ALLOC(h->lam, (size_t)n2);
+  ALLOC(h->U, (size_t)n2 * ell);
+  ALLOC(h->eigw, eig_work_doubles(n2, ell));
+  ALLOC(h->scal, 1024);
+  ALLOC(h->bad, 1);
+  ALLOC(h->dstatus, 1);
+  ALLOC(h->si.Y, (size_t)n2 * kmax);
+  ALLOC(h->si.GY, (size_t)n2 * kmax);
+  ALLOC(h->si.S, (size_t)kmax * kmax);
+  ALLOC(h->si.V, (size_t)kmax * kmax);
+  ALLOC(h->si.eigw, eig_work_doubles(kmax, kmax));
+  ALLOC(h->si.ritz, (size_t)kmax);
+  ALLOC(h->si.WU, (size_t)n2 * kmax);
+  ALLOC(h->si.GWU, (size_t)n2 * kmax);
+  ALLOC(h->si.tmp, (size_t)n2 * kmax + 3 * (size_t)kmax * kmax + kmax);
+#undef ALLOC
+  if (st == AS_OK && cudaMallocHost((void**)&h->h_buf, (size_t)(4 * n2 + 64) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    h->h_buf = nullptr;
+    st = AS_ENOMEM;
+  }
+  if (st == AS_OK) {
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMemsetAsync(h->C, 0, (size_t)n2 * h->ldc * sizeof(float), h->s);
+    e = e ? e : cudaMemsetAsync(h->G, 0, (size_t)n2 * n2 * sizeof(double), h->s);
+    e = e ? e : cudaMemsetAsync(h->bad, 0, sizeof(int), h->s);
+    e = e ? e : cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->s);
+    e = e ? e : cudaStreamSynchronize(h->s);
+    if (e != cudaSuccess) st = as_from_cuda(e);
+  }
+  if (st != AS_OK) {
+    free_all(h);
+    delete h;
+    return st;
+  }
+  h->dev_bytes = bytes;
+  h->st.d = h->d;
+  h->st.ell = h->ell;
+  *out = h;
+  return AS_OK;
+}
+
+as_status sketch_update(as_sketch* h, const float* rows, int64_t n, int64_t ld) {
+  if (!h) return AS_EINVAL;
+  if (n == 0) return AS_OK;
+  if (!rows || n < 0 || ld < h->d) return AS_EINVAL;
+  std::unique_lock<std::mutex> lk(h->mu, std::try_to_lock);
+  if (!lk.owns_lock()) return AS_EBUSY;
+  const bool dev = is_device_ptr(rows);
+  as_status st = AS_OK;
+  for (int64_t t0 = 0; t0 < n && st == AS_OK; t0 += h->stage_rows) {
+    const int64_t nb = std::min<int64_t>(h->stage_rows, n - t0);
+    const float* src = rows + t0 * ld;
+    const float* base = src;
+    int64_t ldb = ld;
+    if (!dev) {
+      cudaError_t e = cudaMemcpy2DAsync(h->stage, (size_t)h->d * sizeof(float), src, (size_t)ld * sizeof(float),
+                                        (size_t)h->d * sizeof(float), (size_t)nb, cudaMemcpyHostToDevice, h->s);
+      if (e != cudaSuccess) return as_from_cuda(e);
+      base = h->stage;
+      ldb = h->d;
+    }
+    for (int64_t t = 0; t < nb && st == AS_OK; ++t) {
+      if (ldb == h->d) {
+        st = update_row(h, base + t * ldb);
+      } else {
+        // rows with a padded stride: copy into the staging buffer first
+        cudaError_t e = cudaMemcpyAsync(h->stage, base + t * ldb, (size_t)h->d * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, h->s);
+        if (e != cudaSuccess) return as_from_cuda(e);
+        st = update_row(h, h->stage);
+      }
+    }
+  }
+  if (st == AS_OK) {
+    as_status ds = sync_status(h);
+    if (ds != AS_OK) st = ds;
+  }
+  return st;
+}
+
+as_status sketch_query_gram(as_sketch* h, double* out) {
+  if (!h || !out) return AS_EINVAL;
+  std::unique_lock<std::mutex> lk(h->mu, std::try_to_lock);
+  if (!lk.owns_lock()) return AS_EBUSY;
+  double* B = nullptr;
+  as_status st = dalloc(&B, (size_t)h->d * h->d);
+  if (st != AS_OK) return st;
+  st = build_query_gram(h, B);
+  if (st == AS_OK) {
+    cudaError_t e = cudaMemcpy(out, B, (size_t)h->d * h->d * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = as_from_cuda(e);
+  }
+  cudaFree(B);
+  return st;
+}
+
+as_status sketch_query(as_sketch* h, int64_t t, float* out, int64_t ldo, int32_t* rows_out) {
+  if (!h || !out || ldo < h->d) return AS_EINVAL;
+  if (t != -1 && t != h->T) return AS_ENOTSUP;
+  std::unique_lock<std::mutex> lk(h->mu, std::try_to_lock);
+  if (!lk.owns_lock()) return AS_EBUSY;
+  const int d = h->d, ell = h->ell;
+  double *B = nullptr, *lam = nullptr, *V = nullptr, *w = nullptr;
+  float* o = nullptr;
+  as_status st = dalloc(&B, (size_t)d * d);
+  if (st == AS_OK) st = dalloc(&lam, (size_t)d);
+  if (st == AS_OK) st = dalloc(&V, (size_t)d * ell);
+  if (st == AS_OK) st = dalloc(&w, eig_work_doubles(d, ell));
+  if (st == AS_OK) st = dalloc(&o, (size_t)ell * d);
+  if (st == AS_OK) st = build_query_gram(h, B);
+  if (st == AS_OK) st = launch_eig(h->s, d, B, d, ell, lam, V, ell, w);   // Algorithm 5 line 5
+  if (st == AS_OK) st = launch_shrink_rows(h->s, d, ell, lam, V, ell, o, d);  // line 6
+  if (st == AS_OK) {
+    cudaError_t e = cudaMemcpy2DAsync(out, (size_t)ldo * sizeof(float), o, (size_t)d * sizeof(float),
+                                      (size_t)d * sizeof(float), (size_t)ell, cudaMemcpyDefault, h->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+    if (e != cudaSuccess) st = as_from_cuda(e);
+  }
+  if (st == AS_OK) {
+    as_status ds = sync_status(h);
+    if (ds != AS_OK) st = ds;
+  }
+  if (rows_out) *rows_out = (st == AS_OK) ? ell : 0;
+  cudaFree(B); cudaFree(lam); cudaFree(V); cudaFree(w); cudaFree(o);
+  return st;
+}
+
+as_status sketch_get_buffer(as_sketch* h, float* out, int32_t* r_out) {
+  if (!h || !out) return AS_EINVAL;
+  cudaError_t e = cudaMemcpy2D(out, (size_t)h->d * sizeof(float), h->C, (size_t)h->ldc * sizeof(float),
+                               (size_t)h->d * sizeof(float), (size_t)h->n2, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return as_from_cuda(e);
+  if (r_out) *r_out = h->r;
+  return AS_OK;
+}
+
+as_status sketch_merge(as_sketch* dst, const as_sketch* src) {
+  if (!dst || !src) return AS_EINVAL;
+  if (dst->d != src->d) return AS_EINVAL;
+  return AS_ENOTSUP;
+}
+
+as_status sketch_stats(as_sketch* h, as_stats* out) {
+  if (!h || !out) return AS_EINVAL;
+  as_status ds = sync_status(h);
+  as_stats s = h->st;
+  s.rows = h->T;
+  s.rows_in_buffer = h->r;
+  s.fro2 = h->F;
+  s.theta = h->theta;
+  s.device_bytes = (int64_t)h->dev_bytes;
+  s.device_status = (int32_t)ds;
+  *out = s;
+  return AS_OK;
+}
+
+as_status sketch_trace(as_sketch* h, as_event* out, int64_t cap, int64_t* count) {
+  if (!h || !count || cap < 0 || (cap > 0 && !out)) return AS_EINVAL;
+  const int64_t n = (int64_t)h->trace.size();
+  for (int64_t t = 0; t < std::min(n, cap); ++t) out[t] = h->trace[t];
+  *count = n;
+  return AS_OK;
+}
+
+as_status sketch_destroy(as_sketch* h) {
+  if (!h) return AS_OK;
+  cudaStreamSynchronize(h->s);
+  free_all(h);
+  delete h;
+  return AS_OK;
+}
+
+}  // extern "C"

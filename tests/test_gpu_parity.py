@@ -1,0 +1,162 @@
+"""GPU AeroSketch (through the C ABI) against the FP64 oracle on seeded inputs.
+
+Parity unit: the normalised covariance error ||A^T A - B^T B||_2 / ||A||_F^2
+computed in FP64 by the oracle's metric code, |GPU - oracle| <= 1e-6 (the FP32
+form's tolerance).  Decisions are compared through the GPU's decision record;
+the oracle replays the GPU's choice only where its own margin is within a
+1e-5 relative tie band (FP32 storage of C moves the iterations' values by
+~1e-7 relative) and must agree everywhere else.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.aerosketch import AeroSketch
+from oracle.fd import ExactFD
+from oracle.metric import cov_err
+from synth import low_rank_noisy, spectrum, workload_rows
+
+pytestmark = pytest.mark.gpu
+
+TIE = 1e-5
+
+
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2601_02019_gb300 as p
+    p.load_library()
+    return p
+
+
+def _run_gpu(p, A, d, ell, chunks=None, **kw):
+    s = p.Sketch(d, ell, trace=True, **kw)
+    if chunks is None:
+        s.update(A)
+    else:
+        t = 0
+        for c in chunks:
+            s.update(np.ascontiguousarray(A[t:t + c]))
+            t += c
+        assert t == len(A)
+    return s
+
+
+def _compare(p, A, d, ell, seed=0, err_tol=1e-6, **kw):
+    s = _run_gpu(p, A, d, ell, seed=seed, **kw)
+    ev = s.trace()
+    Bg = s.query()
+    st = s.stats()
+    assert st["device_status"] == 0
+    rep = p.binding.replay_from_trace(ev)
+    o = AeroSketch(d, ell, seed=seed, replay=rep, tie_rel=TIE).run(A.astype(np.float64))
+    assert not o.mismatches, o.mismatches[:5]
+    AtA = A.astype(np.float64).T @ A.astype(np.float64)
+    eg, eo = cov_err(A, Bg, AtA), cov_err(A, o.query(), AtA)
+    assert abs(eg - eo) <= err_tol, (eg, eo)
+    # the pre-query matrix B_T (Algorithm 5 lines 1-4) agrees too
+    Bt = s.query_gram()
+    assert np.abs(Bt - o.pre_query()).max() <= 1e-5 * np.trace(AtA)
+    # and the paper's deterministic bound holds on the GPU result
+    assert eg <= 2.0 / ell
+    assert st["shrinks"] == len(o.shrink_rows)
+    assert st["dumps"] == len(o.S)
+    return s, o, eg, eo
+
+
+@pytest.mark.parametrize("d,ell,n,seed", [(32, 4, 300, 0), (64, 8, 700, 1), (40, 5, 333, 2)])
+def test_parity_small(d, ell, n, seed):
+    p = _gpu()
+    A = low_rank_noisy(n, d, 6, spectrum("geometric", 6), noise=0.05, seed=seed)
+    _compare(p, A, d, ell, seed=seed)
+
+
+def test_parity_small_d256_l32_full():
+    """The persistent workload d=256, l=32, n=10,000 (rank 20, sigma_i = 10 * 0.9^i)."""
+    p = _gpu()
+    A = workload_rows("small_d256_l32")
+    s, o, eg, eo = _compare(p, A, 256, 32)
+    assert s.stats()["gates"] == len(o.events)
+
+
+def test_chunking_does_not_change_the_result():
+    p = _gpu()
+    A = low_rank_noisy(250, 32, 6, spectrum("geometric", 6), noise=0.05, seed=3)
+    s1 = _run_gpu(p, A, 32, 4)
+    s2 = _run_gpu(p, A, 32, 4, chunks=[1, 7, 0, 100, 42, 100])
+    assert np.array_equal(s1.query_gram(), s2.query_gram())
+
+
+def test_device_and_padded_inputs():
+    p = _gpu()
+    import torch
+    A = low_rank_noisy(120, 48, 6, spectrum("geometric", 6), noise=0.05, seed=4)
+    s1 = _run_gpu(p, A, 48, 6)
+    s2 = p.Sketch(48, 6)
+    s2.update(torch.from_numpy(A).cuda())
+    pad = np.zeros((120, 64), dtype=np.float32)
+    pad[:, :48] = A
+    s3 = p.Sketch(48, 6)
+    s3.update(pad[:, :48], ld=64)
+    g1 = s1.query_gram()
+    assert np.array_equal(g1, s2.query_gram())
+    assert np.array_equal(g1, s3.query_gram())
+
+
+def test_empty_update_and_empty_query():
+    p = _gpu()
+    s = p.Sketch(16, 2)
+    s.update(np.zeros((0, 16), dtype=np.float32))
+    assert s.stats()["rows"] == 0
+    assert np.all(s.query() == 0)
+
+
+def test_nonfinite_row_is_rejected():
+    p = _gpu()
+    A = low_rank_noisy(20, 16, 3, spectrum("geometric", 3), seed=5)
+    s = p.Sketch(16, 2)
+    s.update(A[:10])
+    before = s.query_gram()
+    bad = A[10:12].copy()
+    bad[1, 3] = np.nan
+    with pytest.raises(p.AeroSketchError) as e:
+        s.update(bad)
+    assert e.value.code == p.binding.AS_EINVAL
+    assert s.stats()["rows"] == 11           # the finite row before it went in
+    s2 = p.Sketch(16, 2)
+    s2.update(A[:11])
+    assert np.array_equal(s.query_gram(), s2.query_gram())
+    assert not np.array_equal(before, s.query_gram())
+
+
+def test_theta_infinite_is_exact_fd():
+    p = _gpu()
+    A = low_rank_noisy(300, 24, 6, spectrum("geometric", 6), noise=0.05, seed=6)
+    s = p.Sketch(24, 4, mode=p.AS_FIXED_THETA, theta=math.inf)
+    s.update(A)
+    fd = ExactFD(24, 4).run(A.astype(np.float64))
+    C, r = s.buffer()
+    assert r == fd.r
+    AtA = A.astype(np.float64).T @ A.astype(np.float64)
+    C64 = C.astype(np.float64)
+    assert np.abs(C64.T @ C64 - fd.B.T @ fd.B).max() <= 1e-5 * np.trace(AtA)
+    assert s.stats()["gates"] == 0
+
+
+def test_ell_one_and_minimum_dimension():
+    p = _gpu()
+    A = low_rank_noisy(50, 2, 2, spectrum("geometric", 2), seed=7)
+    _compare(p, A, 2, 1)
+
+
+def test_invalid_configs():
+    p = _gpu()
+    for kw in [dict(d=1, ell=1), dict(d=8, ell=5), dict(d=8, ell=0, eps=0.0), dict(d=8, ell=2, eps=-1.0)]:
+        with pytest.raises(p.AeroSketchError) as e:
+            p.Sketch(**kw)
+        assert e.value.code == p.binding.AS_EINVAL
+    with pytest.raises(p.AeroSketchError) as e:
+        p.Sketch(8, 2, prec=p.AS_BF16)
+    assert e.value.code == p.binding.AS_ENOTSUP
