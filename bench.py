@@ -1,0 +1,300 @@
+"""Throughput of the AeroSketch update path (persistent setting) on GB300.
+
+One step = one call of sketch_update on a block of rows of the synthetic
+stream (d = 4096, l = 1024, rank-200 power-law signal plus noise), i.e. every
+row of the block goes through Algorithm 8 + Algorithm 4: threshold, insert,
+FD shrink when the buffer is full, power-iteration gate, simultaneous
+iteration, snapshot and residual.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank runs an independent
+sketch of its own stream (a single stream does not shard: each row's gate
+depends on the whole prefix), rank 0 prints, value = rows of all ranks / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rows/s of sketch_update at the stated cov-err (persistent AeroSketch)"
+WORKLOADS = {
+    "tight_d4096_l1024": dict(d=4096, ell=1024, r=200, spectrum="powerlaw", n=1_000_000),
+    "small_d256_l32": dict(d=256, ell=32, r=20, spectrum="geometric", n=10_000),
+}
+FP32_SIMT_LANES_PER_SM = 128   # FP32 FMA lanes per SM
+N_SM = 152
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows: list[list[str]] = []
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self) -> dict:
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 3 + k and r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reference_arm(args) -> None:
+    """The oracle (plain FP64 NumPy), timed on the host cores, on a bounded
+    sample of the same workload: the stream is first brought to a full-size
+    state by exact FD (theta = inf, no iterations), then each step times the
+    oracle's AeroSketch update on `ref_rows` rows from that state."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+
+    from oracle.aerosketch import AeroSketch
+    from synth import low_rank_noisy, spectrum
+    w = WORKLOADS[args.workload]
+    d, ell = w["d"], w["ell"]
+    pre = 2 * ell + ell // 2
+    per = args.ref_rows
+    A = low_rank_noisy(pre + (args.warmup + args.steps) * per, d, w["r"], spectrum(w["spectrum"], w["r"]))
+    A64 = A.astype(np.float64)
+    fd = AeroSketch(d, ell, theta_mode="fixed", theta_fixed=float("inf")).run(A64[:pre])
+    o = AeroSketch(d, ell)
+    o.load_state(fd.C, fd.r, float(np.sum(A64[:pre] * A64[:pre])), pre)
+    t_steps = []
+    for k in range(args.warmup + args.steps):
+        blk = A64[pre + k * per: pre + (k + 1) * per]
+        t0 = time.perf_counter()
+        o.run(blk)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            t_steps.append(t1 - t0)
+    tot = sum(t_steps)
+    value = args.steps * per / tot
+    cores = os.cpu_count()
+    sample = f"{per} rows/step of the d={d}, l={ell} stream after a {pre}-row exact-FD prefill"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "d": d, "ell": ell, "rows_per_step": per},
+        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def our_arm(args) -> None:
+    import numpy as np
+    import torch
+
+    import paper_2601_02019_gb300 as p
+    from synth import low_rank_noisy, spectrum
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[args.workload]
+    d, ell, B = w["d"], w["ell"], args.rows_per_step
+    K, W = args.steps, args.warmup
+    ntot = (W + K) * B
+    A = low_rank_noisy(ntot, d, w["r"], spectrum(w["spectrum"], w["r"]), stream=rank)
+    A_dev = torch.from_numpy(A).to(dev)
+    A_pin = torch.from_numpy(A).pin_memory()
+    stream = torch.cuda.Stream(device=dev)
+    s = p.Sketch(d, ell, profile=True, stream=stream, stream_id=rank)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    for k in range(W):
+        s.update(A_dev[k * B:(k + 1) * B])
+    torch.cuda.synchronize()
+    # state at the start of the timed region (for the CPU baseline, after timing)
+    C0, r0 = s.buffer()
+    st0 = s.stats()
+    s.profile_reset()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    with ClockSampler(local) as clk:
+        for k in range(W, W + K):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            s.update(A_dev[k * B:(k + 1) * B])
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_ms = sum(step_ms)
+    st1 = s.stats()
+    prof = s.profile()
+    if ws > 1:
+        t = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = ws * K * B / (t_ms / 1000.0)
+
+    # roofline of the dominant single-kernel class (the eigensolver and the
+    # event-row path are composites of many kernels and are listed in "profile")
+    peaks, peak_src = _peaks()
+    single = [x for x in prof if x["name"] in ("gspace_batch_gemm", "gspace_batch_orth", "gram_rows_gemm",
+                                               "ingest", "fd_rebuild_gemm")]
+    top = max(single, key=lambda x: x["total_ms"])
+    tot_prof = sum(x["total_ms"] for x in prof) or 1.0
+    if top["name"] == "ingest":
+        ach = top["bytes"] / (top["total_ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    else:
+        fp32_peak = N_SM * FP32_SIMT_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = top["flops"] / (top["total_ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s"}
+    roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": None, "kernel": top["name"],
+                 "launches": top["launches"], "avg_launch_us": 1000 * top["total_ms"] / max(1, top["launches"]),
+                 "peak_source": f"{peak_src}; FP32 SIMT = {N_SM} SMs x {FP32_SIMT_LANES_PER_SM} lanes x 2 x max SM clock"
+                 if roof["bound"] == "alu" else peak_src})
+
+    # end to end through the C ABI from pinned host memory (host->device copy
+    # inside the timed region, device->host read of the counters each step)
+    s2 = p.Sketch(d, ell, stream_id=rank)
+    for k in range(W):
+        s2.update(A_pin[k * B:(k + 1) * B].numpy())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(W, W + K):
+        s2.update(A_pin[k * B:(k + 1) * B].numpy())
+        s2.stats()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ws * K * B / e2e_s, "unit": "rows/s", "h2d_bytes_per_step": B * d * 4,
+           "d2h_bytes_per_step": 104}
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e["value"] = ws * K * B / float(t.item())
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            import numpy as _np
+
+            from oracle.aerosketch import AeroSketch
+            o = AeroSketch(d, ell, stream_id=rank)
+            o.load_state(C0.astype(_np.float64), r0, st0["fro2"], st0["rows"])
+            S = args.cpu_rows
+            blk = A[W * B: W * B + S].astype(_np.float64)
+            t0 = time.perf_counter()
+            o.run(blk)
+            dt = time.perf_counter() - t0
+            cpu = {"value": S / dt, "unit": "rows/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"first {S} rows of the timed region, from the GPU's exact state at its start"}
+        cov = None
+        if not args.no_err:
+            from oracle.metric import cov_err
+            Bq = s.query()
+            Aall = A.astype(np.float64)
+            cov = {"cov_err": cov_err(Aall, Bq), "bound_eps": 2.0 / ell, "rows": int(st1["rows"])}
+        out = {
+            "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 products, f64 core", "data": "synthetic",
+            "config": {"workload": args.workload, "d": d, "ell": ell, "rows_per_step": B,
+                       "precision": "FP32_PLAIN", "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
+            "clocks": clk.summary(),
+            "profile": [{"kernel": x["name"], "launches": x["launches"], "ms": round(x["total_ms"], 3),
+                         "share": round(x["total_ms"] / tot_prof, 4)} for x in prof],
+            "sketch": {"shrinks": st1["shrinks"] - st0["shrinks"], "dumps": st1["dumps"] - st0["dumps"],
+                       "gates": st1["gates"] - st0["gates"]},
+            "step_ms": [round(x, 3) for x in step_ms],
+            "accuracy": cov,
+        }
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tight_d4096_l1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--rows-per-step", type=int, default=1024)
+    ap.add_argument("--cpu-rows", type=int, default=48)
+    ap.add_argument("--ref-rows", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-err", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -66,6 +66,7 @@ typedef enum {
 
 /* Flags. */
 #define AS_TRACE_DECISIONS 0x1u /* record every gate / doubling decision (sketch_trace) */
+#define AS_PROFILE 0x2u         /* time each kernel class with CUDA events (sketch_profile) */
 
 typedef struct {
   int32_t d;          /* row dimension, >= 2 */
@@ -98,7 +99,18 @@ typedef struct {
   int64_t device_bytes;    /* device memory owned by the sketch */
   int32_t device_status;   /* sticky as_status recorded on the device */
   int32_t reserved1;
+  int64_t kernel_launches; /* kernels this library launched, all sketches, since load */
 } as_stats;
+
+/* Per kernel class timing (AS_PROFILE): CUDA-event time on the sketch's
+ * stream, launch count, and the algorithmic work of those launches. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+  double flops;     /* algorithmic floating-point operations, summed over launches */
+  double bytes;     /* algorithmic DRAM bytes, summed over launches */
+} as_kernel_stat;
 
 /* One decision record (AS_TRACE_DECISIONS): a row whose gate passed. */
 typedef struct {
@@ -152,6 +164,14 @@ as_status sketch_stats(as_sketch* h, as_stats* out);
 /* Decision records (AS_TRACE_DECISIONS).  Copies up to `cap` records, oldest
  * first, to host memory `out` and writes the total count to *count. */
 as_status sketch_trace(as_sketch* h, as_event* out, int64_t cap, int64_t* count);
+
+/* Kernel-class timings collected since the last reset (AS_PROFILE).
+ * Synchronises; copies up to `cap` records to host memory `out` and writes the
+ * number of classes to *count.  Without AS_PROFILE, *count = 0. */
+as_status sketch_profile(as_sketch* h, as_kernel_stat* out, int32_t cap, int32_t* count);
+
+/* Clear the kernel-class timings. */
+as_status sketch_profile_reset(as_sketch* h);
 
 /* Free every resource of the sketch.  NULL is a no-op. */
 as_status sketch_destroy(as_sketch* h);

@@ -259,6 +259,17 @@ class AeroSketch:
             return                                                # line 17
         # loop ended without break: C_i <- C'_i (R8)
 
+    def load_state(self, C: np.ndarray, r: int, F: float, T: int) -> "AeroSketch":
+        """Start from a given buffer (rows >= r zero), ||A_T||_F^2 and time T,
+        with an empty snapshot queue: lets a test continue another
+        implementation's stream for a window of rows."""
+        self.C = np.array(C, dtype=np.float64, copy=True)
+        self.C[r:] = 0.0
+        self.r, self.F, self.T = int(r), float(F), int(T)
+        if self.theta_mode == "attp":
+            self.theta = self.eps * self.F
+        return self
+
     def run(self, A: np.ndarray) -> "AeroSketch":
         for a in np.asarray(A, dtype=np.float64):
             self.update(a)

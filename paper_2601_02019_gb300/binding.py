@@ -14,9 +14,11 @@ AS_OK, AS_EINVAL, AS_ENOMEM, AS_EDEVICE, AS_ENUMERIC, AS_ETIMEOUT, AS_EBUSY, AS_
 AS_PERSISTENT, AS_FIXED_THETA, AS_SLIDING, AS_SITE, AS_COORDINATOR = range(5)
 AS_FP32_PLAIN, AS_BF16 = 0, 1
 AS_TRACE_DECISIONS = 0x1
+AS_PROFILE = 0x2
 
 EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram", "sketch_get_buffer",
-            "sketch_merge", "sketch_stats", "sketch_trace", "sketch_destroy", "as_status_str")
+            "sketch_merge", "sketch_stats", "sketch_trace", "sketch_profile", "sketch_profile_reset",
+            "sketch_destroy", "as_status_str")
 
 
 class AsConfig(ct.Structure):
@@ -31,7 +33,7 @@ class AsStats(ct.Structure):
                 ("reserved0", ct.c_int32), ("fro2", ct.c_double), ("theta", ct.c_double),
                 ("shrinks", ct.c_int64), ("gates", ct.c_int64), ("dumps", ct.c_int64),
                 ("snapshot_rank", ct.c_int64), ("si_runs", ct.c_int64), ("device_bytes", ct.c_int64),
-                ("device_status", ct.c_int32), ("reserved1", ct.c_int32)]
+                ("device_status", ct.c_int32), ("reserved1", ct.c_int32), ("kernel_launches", ct.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
@@ -40,6 +42,11 @@ class AsStats(ct.Structure):
 class AsEvent(ct.Structure):
     _fields_ = [("i", ct.c_int64), ("sig2_pi", ct.c_double), ("theta", ct.c_double), ("j_stop", ct.c_int32),
                 ("xi", ct.c_int32), ("ritz_k", ct.c_double), ("ritz_1", ct.c_double)]
+
+
+class AsKernelStat(ct.Structure):
+    _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int64), ("total_ms", ct.c_double),
+                ("flops", ct.c_double), ("bytes", ct.c_double)]
 
 
 class AeroSketchError(RuntimeError):
@@ -68,6 +75,8 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.sketch_merge.argtypes = [P, P]
     L.sketch_stats.argtypes = [P, ct.POINTER(AsStats)]
     L.sketch_trace.argtypes = [P, ct.POINTER(AsEvent), I64, ct.POINTER(I64)]
+    L.sketch_profile.argtypes = [P, ct.POINTER(AsKernelStat), I32, ct.POINTER(I32)]
+    L.sketch_profile_reset.argtypes = [P]
     L.sketch_destroy.argtypes = [P]
     L.as_status_str.argtypes = [ct.c_int]
     L.as_status_str.restype = ct.c_char_p
@@ -99,10 +108,12 @@ class Sketch:
 
     def __init__(self, d: int, ell: int = 0, eps: float = 0.0, *, mode: int = AS_PERSISTENT,
                  prec: int = AS_FP32_PLAIN, theta: float = 0.0, eps_si: float = 0.0, k_pi: int = 0,
-                 q_si: int = 0, seed: int = 0, stream_id: int = 0, trace: bool = False, stream=None):
+                 q_si: int = 0, seed: int = 0, stream_id: int = 0, trace: bool = False, profile: bool = False,
+                 stream=None):
         L = lib()
+        flags = (AS_TRACE_DECISIONS if trace else 0) | (AS_PROFILE if profile else 0)
         cfg = AsConfig(d=d, ell=ell, eps=eps, mode=mode, prec=prec, theta=theta, eps_si=eps_si, k_pi=k_pi,
-                       q_si=q_si, seed=seed, stream_id=stream_id, flags=AS_TRACE_DECISIONS if trace else 0)
+                       q_si=q_si, seed=seed, stream_id=stream_id, flags=flags)
         h = ct.c_void_p()
         sp = None if stream is None else ct.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         _check(L.sketch_create(ct.byref(cfg), sp, ct.byref(h)), "sketch_create")
@@ -124,6 +135,9 @@ class Sketch:
     def update(self, rows, ld: int | None = None) -> None:
         """rows: (n, d) float32 numpy array (host) or torch tensor (host or device)."""
         n = int(rows.shape[0])
+        if n == 0:
+            _check(lib().sketch_update(self._h, ct.c_void_p(_ptr(rows)), 0, self.d), "sketch_update")
+            return
         if ld is None:
             ld = int(rows.strides[0] // 4) if isinstance(rows, np.ndarray) else int(rows.stride(0))
         if isinstance(rows, np.ndarray):
@@ -159,6 +173,16 @@ class Sketch:
         arr = (AsEvent * max(1, n.value))()
         _check(lib().sketch_trace(self._h, arr, n.value, ct.byref(n)), "sketch_trace")
         return [{f: getattr(arr[t], f) for f, _ in AsEvent._fields_} for t in range(n.value)]
+
+    def profile(self) -> list[dict]:
+        arr = (AsKernelStat * 32)()
+        n = ct.c_int32()
+        _check(lib().sketch_profile(self._h, arr, 32, ct.byref(n)), "sketch_profile")
+        return [{"name": arr[t].name.decode(), "launches": arr[t].launches, "total_ms": arr[t].total_ms,
+                 "flops": arr[t].flops, "bytes": arr[t].bytes} for t in range(min(n.value, 32))]
+
+    def profile_reset(self) -> None:
+        _check(lib().sketch_profile_reset(self._h), "sketch_profile_reset")
 
     def merge(self, other: "Sketch") -> None:
         _check(lib().sketch_merge(self._h, other._h), "sketch_merge")

@@ -122,6 +122,10 @@ __device__ __forceinline__ T block_max(T v, T* red) {
   return t;
 }
 
+// Kernel launches issued by this library (all sketches); defined in engine.cu.
+void count_launches(int64_t n);
+int64_t launches_total();
+
 // Sticky device status: the first non-OK code wins.
 __device__ __forceinline__ void set_status(int* st, int code) {
   if (st) atomicCAS(st, 0, code);

@@ -1,0 +1,317 @@
+// FP64 symmetric eigensolver spread over the whole GPU, for the large core
+// matrices (the 2l x 2l Gram of the FD shrink when l is large, and the query).
+// Same method as eig.cuh (Householder tridiagonalisation, Sturm bisection,
+// inverse iteration, back-transformation), with each phase split across
+// thread blocks:
+//   * tridiagonalisation step k: kernel 1 forms v_k (every block recomputes it
+//     from row k) and p = A22 v_k, one warp per row, with per-block partial
+//     sums of v^T p; kernel 2 sums the partials in a fixed order and applies
+//     A22 -= v w^T + w v^T, w = 2p - 2(v^T p) v.  No atomics: results are
+//     bitwise reproducible.
+//   * bisection and inverse iteration: one thread per eigenvalue.
+//   * back-transformation: each block owns a slab of eigenvector columns in
+//     shared memory and applies every reflector to it.
+#include "eig.cuh"
+#include "kernels.cuh"
+
+namespace as {
+
+namespace {
+
+constexpr int kTriRowsPerBlock = 8;  // one warp per row of p
+
+struct TriWork {
+  double* d;      // n
+  double* e;      // n
+  double* v;      // n (current Householder vector)
+  double* p;      // n
+  double* part;   // partial sums of v^T p, one per block of kernel 1
+};
+
+__device__ __forceinline__ void house_params(const double* row, int m, double* red, double& s_out,
+                                             double& alpha, double& vn) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s += row[i] * row[i];
+  s = block_sum(s, red);
+  const double x0 = row[0];
+  s_out = s;
+  if (s == 0.0) { alpha = 0.0; vn = 1.0; return; }
+  alpha = (x0 >= 0.0) ? -sqrt(s) : sqrt(s);
+  vn = sqrt(s - x0 * x0 + (x0 - alpha) * (x0 - alpha));
+}
+
+__global__ void __launch_bounds__(256) tri_step1(double* A, int lda, int n, int k, TriWork w) {
+  extern __shared__ double vs[];  // m doubles
+  __shared__ double red[32];
+  const int m = n - k - 1;
+  const double* row = A + (size_t)k * lda + (k + 1);
+  double s, alpha, vn;
+  house_params(row, m, red, s, alpha, vn);
+  for (int i = threadIdx.x; i < m; i += blockDim.x)
+    vs[i] = (s == 0.0) ? 0.0 : ((i == 0) ? (row[0] - alpha) : row[i]) / vn;
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) w.v[i] = vs[i];
+    if (threadIdx.x == 0) { w.d[k] = A[(size_t)k * lda + k]; w.e[k] = alpha; }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int i = blockIdx.x * kTriRowsPerBlock + wid;
+  double contrib = 0.0;
+  if (i < m) {
+    const double* ar = A + (size_t)(k + 1 + i) * lda + (k + 1);
+    double acc = 0.0;
+    for (int j = lane; j < m; j += 32) acc += ar[j] * vs[j];
+    acc = warp_sum(acc);
+    if (lane == 0) { w.p[i] = acc; contrib = acc * vs[i]; }
+  }
+  // deterministic block partial of v^T p (warp order)
+  __shared__ double wpart[kTriRowsPerBlock];
+  if (lane == 0) wpart[wid] = contrib;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kTriRowsPerBlock; ++q) t += wpart[q];
+    w.part[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(256) tri_step2(double* A, int lda, int n, int k, int nparts, TriWork w) {
+  __shared__ double cs;
+  const int m = n - k - 1;
+  if (threadIdx.x == 0) {
+    double c = 0.0;
+    for (int q = 0; q < nparts; ++q) c += w.part[q];
+    cs = c;
+  }
+  __syncthreads();
+  const double c = cs;
+  // keep v in row k of A for the back-transformation (row k is not read here)
+  if (blockIdx.x == 0 && blockIdx.y == 0)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) A[(size_t)k * lda + (k + 1) + i] = w.v[i];
+  // 2D tiles of A22: blockIdx.y -> 8 rows, blockIdx.x -> 256 columns
+  const int i0 = blockIdx.y * 8;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const double vj = w.v[j];
+  const double wj = 2.0 * w.p[j] - 2.0 * c * vj;
+  for (int ii = 0; ii < 8; ++ii) {
+    const int i = i0 + ii;
+    if (i >= m) break;
+    const double vi = w.v[i];
+    const double wi = 2.0 * w.p[i] - 2.0 * c * vi;
+    A[(size_t)(k + 1 + i) * lda + (k + 1 + j)] -= vi * wj + wi * vj;
+  }
+}
+
+__global__ void tri_tail(const double* A, int lda, int n, TriWork w) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    w.d[n - 2] = A[(size_t)(n - 2) * lda + (n - 2)];
+    w.e[n - 2] = A[(size_t)(n - 2) * lda + (n - 1)];
+    w.d[n - 1] = A[(size_t)(n - 1) * lda + (n - 1)];
+    w.e[n - 1] = 0.0;
+  }
+}
+
+// tnorm, pivmin of T
+__global__ void tri_norm(int n, TriWork w, double* out2) {
+  __shared__ double red[32];
+  double tn = 0.0, em = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double el = (i > 0) ? fabs(w.e[i - 1]) : 0.0, er = (i + 1 < n) ? fabs(w.e[i]) : 0.0;
+    tn = fmax(tn, fabs(w.d[i]) + el + er);
+    em = fmax(em, er * er);
+  }
+  tn = block_max(tn, red);
+  em = block_max(em, red);
+  if (threadIdx.x == 0) { out2[0] = tn; out2[1] = 2.2250738585072014e-308 * fmax(1.0, em); }
+}
+
+__global__ void bisect_invit(int n, int nev, TriWork w, const double* norms, double* evals, double* X, int ldx,
+                             double* lu) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nev) return;
+  const double tnorm = norms[0], pivmin = norms[1];
+  const double eps = 2.220446049250313e-16;
+  const double* d = w.d;
+  const double* e = w.e;
+  const int idx = n - 1 - j;
+  double lo = -tnorm - 2 * eps * tnorm - pivmin, hi = tnorm + 2 * eps * tnorm + pivmin;
+  for (int it = 0; it < 256; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(n, d, e, mid, pivmin) > idx) hi = mid; else lo = mid;
+    if (hi - lo <= 2 * eps * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+  }
+  const double lam = 0.5 * (lo + hi);
+  evals[j] = lam;
+  // inverse iteration (same factorisation as eig.cuh)
+  const double tiny = eps * fmax(tnorm, pivmin);
+  double* u0 = lu + (size_t)(0 * n) * nev + j;
+  double* u1 = lu + (size_t)(1 * n) * nev + j;
+  double* u2 = lu + (size_t)(2 * n) * nev + j;
+  double* ll = lu + (size_t)(3 * n) * nev + j;
+  double* pv = lu + (size_t)(4 * n) * nev + j;
+  double cd = d[0] - lam, cs = e[0];
+  for (int i = 0; i + 1 < n; ++i) {
+    const double b = e[i];
+    const double nd = d[i + 1] - lam, ns = (i + 2 < n) ? e[i + 1] : 0.0;
+    if (fabs(cd) >= fabs(b)) {
+      if (cd == 0.0) cd = tiny;
+      const double li = b / cd;
+      u0[(size_t)i * nev] = cd; u1[(size_t)i * nev] = cs; u2[(size_t)i * nev] = 0.0;
+      ll[(size_t)i * nev] = li; pv[(size_t)i * nev] = 0.0;
+      cd = nd - li * cs; cs = ns;
+    } else {
+      const double li = cd / b;
+      u0[(size_t)i * nev] = b; u1[(size_t)i * nev] = nd; u2[(size_t)i * nev] = ns;
+      ll[(size_t)i * nev] = li; pv[(size_t)i * nev] = 1.0;
+      cd = cs - li * nd; cs = -li * ns;
+    }
+  }
+  if (fabs(cd) < tiny) cd = (cd < 0 ? -tiny : tiny);
+  u0[(size_t)(n - 1) * nev] = cd;
+  for (int i = 0; i < n; ++i) {
+    const double p = u0[(size_t)i * nev];
+    if (fabs(p) < tiny) u0[(size_t)i * nev] = (p < 0 ? -tiny : tiny);
+  }
+  for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] = ii_start(i, j);
+  for (int it = 0; it < 3; ++it) {
+    for (int i = 0; i + 1 < n; ++i) {
+      double yi = X[(size_t)i * ldx + j], yn = X[(size_t)(i + 1) * ldx + j];
+      if (pv[(size_t)i * nev] != 0.0) { const double t = yi; yi = yn; yn = t; }
+      yn -= ll[(size_t)i * nev] * yi;
+      X[(size_t)i * ldx + j] = yi;
+      X[(size_t)(i + 1) * ldx + j] = yn;
+    }
+    double xn1 = 0.0, xn2 = 0.0, mx = 0.0;
+    for (int i = n - 1; i >= 0; --i) {
+      const double xi = (X[(size_t)i * ldx + j] - u1[(size_t)i * nev] * xn1 - u2[(size_t)i * nev] * xn2) /
+                        u0[(size_t)i * nev];
+      X[(size_t)i * ldx + j] = xi;
+      xn2 = xn1; xn1 = xi;
+      mx = fmax(mx, fabs(xi));
+    }
+    double nrm = 0.0;
+    for (int i = 0; i < n; ++i) { const double v = X[(size_t)i * ldx + j] / mx; nrm += v * v; }
+    const double sc = 1.0 / (mx * sqrt(nrm));
+    for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] *= sc;
+  }
+}
+
+// Modified Gram-Schmidt inside clusters of close eigenvalues (one block).
+__global__ void cluster_mgs(int n, int nev, const double* norms, const double* evals, double* X, int ldx) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double ctol = 1e-9 * fmax(norms[0], norms[1]);
+  int c0 = 0;
+  for (int j = 1; j < nev; ++j) {
+    if (evals[j - 1] - evals[j] > ctol) { c0 = j; continue; }
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int q = c0; q < j; ++q) {
+        double s = 0.0;
+        for (int i = tid; i < n; i += nt) s += X[(size_t)i * ldx + q] * X[(size_t)i * ldx + j];
+        s = block_sum(s, red);
+        for (int i = tid; i < n; i += nt) X[(size_t)i * ldx + j] -= s * X[(size_t)i * ldx + q];
+        __syncthreads();
+      }
+      double s = 0.0;
+      for (int i = tid; i < n; i += nt) s += X[(size_t)i * ldx + j] * X[(size_t)i * ldx + j];
+      s = block_sum(s, red);
+      const double sc = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+      for (int i = tid; i < n; i += nt) X[(size_t)i * ldx + j] *= sc;
+      __syncthreads();
+    }
+  }
+}
+
+// Back-transformation: each block owns columns [c0, c0 + kSlab) of X.
+constexpr int kSlab = 4;
+__global__ void __launch_bounds__(256) back_transform(const double* A, int lda, int n, int nev, double* X, int ldx) {
+  extern __shared__ double xs[];  // n x kSlab
+  __shared__ double red[kSlab][8];
+  const int c0 = blockIdx.x * kSlab;
+  const int nc = min(kSlab, nev - c0);
+  for (int e = threadIdx.x; e < n * kSlab; e += blockDim.x) {
+    const int i = e / kSlab, c = e - i * kSlab;
+    xs[e] = (c < nc) ? X[(size_t)i * ldx + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = n - 3; k >= 0; --k) {
+    const int m = n - k - 1;
+    const double* v = A + (size_t)k * lda + (k + 1);
+    double s[kSlab];
+#pragma unroll
+    for (int c = 0; c < kSlab; ++c) s[c] = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const double vi = v[i];
+#pragma unroll
+      for (int c = 0; c < kSlab; ++c) s[c] += vi * xs[(k + 1 + i) * kSlab + c];
+    }
+#pragma unroll
+    for (int c = 0; c < kSlab; ++c) {
+      const double t = warp_sum(s[c]);
+      if (lane == 0) red[c][wid] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kSlab; ++c) {
+      double t = 0.0;
+      for (int q = 0; q < 8; ++q) t += red[c][q];
+      s[c] = 2.0 * t;
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const double vi = v[i];
+#pragma unroll
+      for (int c = 0; c < kSlab; ++c) xs[(k + 1 + i) * kSlab + c] -= s[c] * vi;
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * kSlab; e += blockDim.x) {
+    const int i = e / kSlab, c = e - i * kSlab;
+    if (c < nc) X[(size_t)i * ldx + c0 + c] = xs[e];
+  }
+}
+
+}  // namespace
+
+size_t eig_large_work_doubles(int n, int nev) {
+  const int nparts = (n + kTriRowsPerBlock - 1) / kTriRowsPerBlock;
+  return 4 * (size_t)n + nparts + 2 + 5 * (size_t)n * nev + 64;
+}
+
+as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, double* evals, double* X, int ldx,
+                           double* work) {
+  if (n < 3) return launch_eig(s, n, A, lda, nev, evals, X, ldx, work);
+  TriWork w;
+  w.d = work;
+  w.e = w.d + n;
+  w.v = w.e + n;
+  w.p = w.v + n;
+  w.part = w.p + n;
+  const int nparts_max = (n + kTriRowsPerBlock - 1) / kTriRowsPerBlock;
+  double* norms = w.part + nparts_max;
+  double* lu = norms + 2;
+  const size_t smem1 = (size_t)n * sizeof(double);
+  if (smem1 > 48 * 1024)
+    AS_CUDA_TRY(cudaFuncSetAttribute(tri_step1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    const int nb = (m + kTriRowsPerBlock - 1) / kTriRowsPerBlock;
+    tri_step1<<<nb, 256, (size_t)m * sizeof(double), s>>>(A, lda, n, k, w); count_launches(1);
+    dim3 g2((m + 255) / 256, (m + 7) / 8);
+    tri_step2<<<g2, 256, 0, s>>>(A, lda, n, k, nb, w); count_launches(1);
+  }
+  tri_tail<<<1, 32, 0, s>>>(A, lda, n, w); count_launches(1);
+  tri_norm<<<1, 256, 0, s>>>(n, w, norms); count_launches(1);
+  bisect_invit<<<(nev + 31) / 32, 32, 0, s>>>(n, nev, w, norms, evals, X, ldx, lu); count_launches(1);
+  cluster_mgs<<<1, 512, 0, s>>>(n, nev, norms, evals, X, ldx); count_launches(1);
+  const size_t smem3 = (size_t)n * kSlab * sizeof(double);
+  if (smem3 > 48 * 1024)
+    AS_CUDA_TRY(cudaFuncSetAttribute(back_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+  back_transform<<<(nev + kSlab - 1) / kSlab, 256, smem3, s>>>(A, lda, n, nev, X, ldx); count_launches(1);
+  AS_CUDA_TRY(cudaGetLastError());
+  return AS_OK;
+}
+
+}  // namespace as

@@ -5,12 +5,14 @@
 //   G      2l x 2l  FP64  Gram C C^T of the stored buffer
 //   arena  FP32           snapshot store: for each snapshot Z (d x xi, row-major)
 //                         followed by Y = Z^T C'^T C' (xi x d, row-major)
-// The host walks Algorithm 4 row by row; every arithmetic step runs in the
+// The host walks Algorithm 4 block by block; every arithmetic step runs in the
 // kernels, and the host reads back only the scalars that decide the branches
-// (||a_i||^2, the power-iteration estimate, the Ritz values).
+// (||a_i||^2, the power-iteration estimates, the Ritz values).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -45,6 +47,68 @@ int ceil_log2(int64_t x) {  // smallest c with 2^c >= x, x >= 1
 
 }  // namespace
 
+namespace as {
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace as
+
+namespace {
+
+const char* const kProfNames[PK_COUNT] = {"gspace_batch_gemm", "gspace_batch_orth", "eig_fp64",  "fd_rebuild_gemm",
+                                          "gram_rows_gemm",    "ingest",            "event_row_fp64"};
+
+// CUDA-event timer per kernel class; pairs are resolved lazily.
+struct EventProf final : Prof {
+  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  int64_t launches[PK_COUNT] = {};
+  double ms[PK_COUNT] = {}, flops[PK_COUNT] = {}, bytes[PK_COUNT] = {};
+  cudaEvent_t open_ev[PK_COUNT] = {};
+
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void begin(int cls, cudaStream_t s) override {
+    open_ev[cls] = get();
+    cudaEventRecord(open_ev[cls], s);
+  }
+  void end(int cls, cudaStream_t s, double f, double b) override {
+    cudaEvent_t e = get();
+    cudaEventRecord(e, s);
+    pending.push_back(Pending{cls, open_ev[cls], e, f, b});
+    if (pending.size() > 8192) resolve();
+  }
+  void resolve() {
+    for (Pending& p : pending) {
+      cudaEventSynchronize(p.b);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, p.a, p.b);
+      ms[p.cls] += t;
+      launches[p.cls] += 1;
+      flops[p.cls] += p.flops;
+      bytes[p.cls] += p.bytes;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  void reset() {
+    resolve();
+    for (int c = 0; c < PK_COUNT; ++c) { launches[c] = 0; ms[c] = flops[c] = bytes[c] = 0; }
+  }
+  ~EventProf() override {
+    for (Pending& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+}  // namespace
+
 struct as_sketch {
   as_config cfg{};
   int d = 0, ell = 0, n2 = 0, ldc = 0, k_pi = 0, q = 0, jmax = 0, mode = 0;
@@ -52,10 +116,14 @@ struct as_sketch {
   cudaStream_t s = nullptr;
   Key key{};
   // device buffers
-  float *C = nullptr, *Cnew = nullptr, *Wfd = nullptr, *stage = nullptr;
+  float *C = nullptr, *Cnew = nullptr, *Wfd = nullptr, *stage = nullptr, *Gf = nullptr;
   double *G = nullptr, *Gtmp = nullptr, *lam = nullptr, *U = nullptr, *eigw = nullptr, *scal = nullptr;
-  int *bad = nullptr, *dstatus = nullptr;
+  double *x64 = nullptr, *y64 = nullptr, *norm2 = nullptr;
+  int *bad = nullptr, *dstatus = nullptr, *zero = nullptr;
   SiBuffers si{};
+  BatchBuffers bb{};
+  int bmax = 64, bnext = 64;
+  bool big = false;  // 2l > 128: multi-block FP64 path and the spread eigensolver
   double* h_buf = nullptr;  // pinned host scratch for branch scalars
   int stage_rows = 0;
   // host mirror of the control state
@@ -69,19 +137,24 @@ struct as_sketch {
   std::vector<as_event> trace;
   size_t dev_bytes = 0;
   std::mutex mu;
+  EventProf* prof = nullptr;  // AS_PROFILE
 };
 
 namespace {
 
 void free_all(as_sketch* h) {
-  float* fp[] = {h->C, h->Cnew, h->Wfd, h->stage, h->arena};
+  float* fp[] = {h->C, h->Cnew, h->Wfd, h->stage, h->arena, h->Gf, h->bb.X, h->bb.Y};
   for (float* p : fp) if (p) cudaFree(p);
   double* dp[] = {h->G, h->Gtmp, h->lam, h->U, h->eigw, h->scal, h->si.Y, h->si.GY, h->si.S, h->si.V,
-                  h->si.eigw, h->si.ritz, h->si.WU, h->si.GWU, h->si.tmp};
+                  h->si.eigw, h->si.ritz, h->si.WU, h->si.GWU, h->si.tmp, h->x64, h->y64, h->norm2,
+                  h->bb.sig2, h->bb.ritz};
   for (double* p : dp) if (p) cudaFree(p);
   if (h->bad) cudaFree(h->bad);
   if (h->dstatus) cudaFree(h->dstatus);
+  if (h->zero) cudaFree(h->zero);
   if (h->h_buf) cudaFreeHost(h->h_buf);
+  delete h->prof;
+  h->prof = nullptr;
 }
 
 as_status sync_status(as_sketch* h) {
@@ -119,8 +192,15 @@ as_status arena_reserve(as_sketch* h, size_t extra) {
 as_status fd_shrink(as_sketch* h) {
   const int n2 = h->n2, ell = h->ell, d = h->d;
   AS_CUDA_TRY(cudaMemcpyAsync(h->Gtmp, h->G, (size_t)n2 * n2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
-  as_status st = launch_eig(h->s, n2, h->Gtmp, n2, ell, h->lam, h->U, ell, h->eigw);
+  if (h->prof) h->prof->begin(PK_EIG, h->s);
+  as_status st = h->big ? launch_eig_large(h->s, n2, h->Gtmp, n2, ell, h->lam, h->U, ell, h->eigw)
+                         : launch_eig(h->s, n2, h->Gtmp, n2, ell, h->lam, h->U, ell, h->eigw);
   if (st != AS_OK) return st;
+  // tridiagonalisation 4/3 n^3 + back-transformation 2 n^2 nev; G read once
+  if (h->prof)
+    h->prof->end(PK_EIG, h->s, 4.0 / 3.0 * (double)n2 * n2 * n2 + 2.0 * (double)n2 * n2 * ell,
+                 8.0 * (double)n2 * n2);
+  if (h->prof) h->prof->begin(PK_REBUILD, h->s);
   st = launch_shrink_weights(h->s, n2, ell, h->lam, h->U, h->Wfd);
   if (st != AS_OK) return st;
   AS_CUDA_TRY(cudaMemsetAsync(h->Cnew, 0, (size_t)n2 * h->ldc * sizeof(float), h->s));
@@ -136,6 +216,10 @@ as_status fd_shrink(as_sketch* h) {
                                             1, 1.0, 0.0);
     if (st != AS_OK) return st;
   }
+  // C' = W C~ ((l-1) x 2l x d) and G = C' C'^T ((l-1)^2 x d); C~ read, C' written and read
+  if (h->prof)
+    h->prof->end(PK_REBUILD, h->s, 2.0 * (ell - 1) * (double)n2 * d + 2.0 * (ell - 1) * (double)(ell - 1) * d,
+                 4.0 * ((double)n2 * d + 2.0 * (ell - 1) * (double)d));
   h->r = ell - 1;
   h->st.shrinks++;
   return AS_OK;
@@ -169,48 +253,30 @@ as_status dump(as_sketch* h, int xi, int k, int64_t i) {
   return AS_OK;
 }
 
-// Algorithm 8 (threshold) + Algorithm 4 for one row already staged on the device.
-as_status update_row(as_sketch* h, const float* drow) {
-  const int d = h->d, n2 = h->n2;
-  as_status st = launch_ingest(h->s, drow, d, 1, d, h->C, h->ldc, h->r, h->scal, h->bad);
-  if (st != AS_OK) return st;
-  AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->s));
-  int hbad = 0;
-  AS_CUDA_TRY(cudaMemcpyAsync(&hbad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-  AS_CUDA_TRY(cudaStreamSynchronize(h->s));
-  if (hbad) {
-    AS_CUDA_TRY(cudaMemsetAsync(h->bad, 0, sizeof(int), h->s));
-    AS_CUDA_TRY(cudaMemsetAsync(h->C + (size_t)h->r * h->ldc, 0, (size_t)h->ldc * sizeof(float), h->s));
-    AS_CUDA_TRY(cudaStreamSynchronize(h->s));
-    return AS_EINVAL;
-  }
-  const double a2 = h->h_buf[0];
-  h->T += 1;
-  const int64_t i = h->T;
-  if (h->mode == AS_PERSISTENT) {  // Algorithm 8 lines 2-3
-    h->F += a2;
-    h->theta = h->eps * h->F;
-  } else {
-    h->F += a2;
-  }
-  const double theta = h->theta;
-  // line 1: insert into the first empty row, extend G
-  st = launch_gram_rows(h->s, h->C, h->ldc, d, h->r, 1, h->G, n2);
-  if (st != AS_OK) return st;
-  h->r += 1;
-  // lines 2-4
-  if (h->r == n2) {
-    st = fd_shrink(h);
-    if (st != AS_OK) return st;
-  }
-  // line 7: power iteration on C'^T
-  st = launch_power_iteration(h->s, h->G, n2, h->r, h->k_pi, h->key, (uint64_t)i, h->scal);
+// FP64 power iteration (Algorithm 1) on the current state (first r rows).
+as_status pi_f64(as_sketch* h, int64_t i, double* sig2) {
+  as_status st = h->big ? launch_power_iteration_f64(h->s, h->G, h->n2, h->r, h->k_pi, h->key, (uint64_t)i, h->x64,
+                                                     h->y64, h->zero, h->scal)
+                        : launch_power_iteration(h->s, h->G, h->n2, h->r, h->k_pi, h->key, (uint64_t)i, h->scal);
   if (st != AS_OK) return st;
   st = fetch(h, h->scal, 1);
   if (st != AS_OK) return st;
-  const double sig2 = h->h_buf[0];
-  // line 8
-  if (!(sig2 >= theta / 2.0 && sig2 > 0.0)) return AS_OK;
+  *sig2 = h->h_buf[0];
+  return AS_OK;
+}
+
+// Algorithm 4 lines 7-17 for row i on the current state, in FP64.  When the
+// gate outcome is already known (from the batched pass, outside its tie band)
+// it is passed in and the power iteration is not repeated.
+as_status finish_row(as_sketch* h, int64_t i, double theta, int known_gate, double sig2, int batch_col = -1,
+                     int batch_ld = 0) {
+  as_status st = AS_OK;
+  if (known_gate < 0) {
+    st = pi_f64(h, i, &sig2);                        // line 7
+    if (st != AS_OK) return st;
+  }
+  const bool gate = (known_gate >= 0) ? (known_gate == 1) : (sig2 >= theta / 2.0 && sig2 > 0.0);  // line 8
+  if (!gate) return AS_OK;
   h->st.gates++;
   as_event ev{};
   ev.i = i;
@@ -218,8 +284,13 @@ as_status update_row(as_sketch* h, const float* drow) {
   ev.theta = theta;
   for (int j = 1; j <= h->jmax; ++j) {              // line 9
     const int k = std::min(std::min(1 << std::min(j, 30), h->ell), h->d);  // line 10
-    st = launch_simul_iter(h->s, h->G, n2, h->r, k, h->q, h->key, (uint64_t)i, j, h->si, h->dstatus);  // line 11
-    if (st != AS_OK) return st;
+    if (j == 1 && k == 2 && batch_col >= 0)       // iterated basis from the batched pass
+      st = launch_si_rr_from_batch(h->s, h->G, h->n2, h->r, h->bb.X, batch_ld, batch_col, h->si, h->dstatus);
+    else if (h->big)
+      st = launch_simul_iter_f64(h->s, h->G, h->n2, h->r, k, h->q, h->key, (uint64_t)i, j, h->si, h->dstatus);
+    else
+      st = launch_simul_iter(h->s, h->G, h->n2, h->r, k, h->q, h->key, (uint64_t)i, j, h->si, h->dstatus);
+    if (st != AS_OK) return st;                     // line 11
     st = fetch(h, h->si.ritz, k);
     if (st != AS_OK) return st;
     h->st.si_runs++;
@@ -241,6 +312,131 @@ as_status update_row(as_sketch* h, const float* drow) {
   }
   if (h->cfg.flags & AS_TRACE_DECISIONS) h->trace.push_back(ev);
   return AS_OK;
+}
+
+// One block of Algorithm 8 + Algorithm 4 over rows src[0..navail) (device,
+// row stride d).  Rows are appended speculatively; the batched FP32 pass finds
+// the first row whose decision changes the state (a dump, or the row that
+// fills the buffer); rows before it are committed, the state is cut back to
+// that row, and it is finished in FP64.  Returns the rows consumed in *used.
+constexpr double kTieBand = 1e-4;
+
+as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t* used, bool* bad_row) {
+  const int d = h->d, n2 = h->n2, r0 = h->r;
+  *bad_row = false;
+  const int b = (int)std::min<int64_t>({navail, (int64_t)(n2 - r0), (int64_t)h->bnext});
+  if (h->prof) h->prof->begin(PK_INGEST, h->s);
+  as_status st = launch_ingest(h->s, src, d, b, d, h->C, h->ldc, r0, h->norm2, h->bad);
+  if (st != AS_OK) return st;
+  if (h->prof) h->prof->end(PK_INGEST, h->s, 2.0 * b * (double)d, 8.0 * b * (double)d);
+  st = fetch(h, h->norm2, b);
+  if (st != AS_OK) return st;
+  std::vector<double> a2(h->h_buf, h->h_buf + b);
+  int bb = b;
+  for (int t = 0; t < b; ++t)
+    if (!std::isfinite(a2[t])) { bb = t; *bad_row = true; break; }
+  if (*bad_row) {
+    AS_CUDA_TRY(cudaMemsetAsync(h->bad, 0, sizeof(int), h->s));
+    st = launch_truncate(h->s, h->C, h->ldc, d, r0 + bb, r0 + b, h->G, n2);
+    if (st != AS_OK) return st;
+    if (bb == 0) { *used = 0; return AS_OK; }
+  }
+  // thresholds before each row (Algorithm 8 lines 2-3)
+  std::vector<double> Ft(bb), th(bb);
+  double F = h->F;
+  for (int t = 0; t < bb; ++t) {
+    F += a2[t];
+    Ft[t] = F;
+    th[t] = (h->mode == AS_PERSISTENT) ? h->eps * F : h->theta;
+  }
+  // line 1 for the whole block: G gains the new rows and columns
+  if (h->prof) h->prof->begin(PK_GRAM, h->s);
+  st = launch_gram_rows(h->s, h->C, h->ldc, d, r0, bb, h->G, n2);
+  if (st != AS_OK) return st;
+  if (h->prof)
+    h->prof->end(PK_GRAM, h->s, 2.0 * (r0 + bb) * (double)bb * d, 4.0 * (r0 + bb) * (double)d + 8.0 * (r0 + bb) * bb);
+  const bool fills = (r0 + bb == n2);
+  const int nb = fills ? bb - 1 : bb;
+  std::vector<double> sig2(nb), ritz(2 * (size_t)nb);
+  if (nb > 0) {
+    st = launch_gf_mirror(h->s, h->G, h->Gf, n2, r0 + bb);
+    if (st != AS_OK) return st;
+    st = launch_batch_gspace(h->s, h->Gf, n2, r0, nb, h->k_pi, h->q, h->key, (uint64_t)(h->T + 1), h->bb,
+                             h->prof);
+    if (st != AS_OK) return st;
+    AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf, h->bb.sig2, nb * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf + nb, h->bb.ritz, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    AS_CUDA_TRY(cudaStreamSynchronize(h->s));
+    std::copy(h->h_buf, h->h_buf + nb, sig2.begin());
+    std::copy(h->h_buf + nb, h->h_buf + 3 * nb, ritz.begin());
+  }
+  // scan for the first state-changing row
+  int tstar = -1, gate_known = -1;
+  double sig2_star = 0.0;
+  for (int t = 0; t < nb; ++t) {
+    const double theta = th[t];
+    double s2 = sig2[t];
+    const int64_t i = h->T + 1 + t;
+    if (std::fabs(s2 - theta / 2.0) <= kTieBand * theta / 2.0 || theta == 0.0) {
+      // tie band: the FP64 power iteration on the state seen by row t decides
+      const int rsave = h->r;
+      h->r = r0 + t + 1;
+      st = pi_f64(h, i, &s2);
+      h->r = rsave;
+      if (st != AS_OK) return st;
+    }
+    const bool gate = s2 >= theta / 2.0 && s2 > 0.0;
+    if (!gate) continue;
+    const double r1 = ritz[2 * (size_t)t];
+    if (r1 >= theta * (1.0 - kTieBand)) {  // a dump is possible: finish this row in FP64
+      tstar = t;
+      gate_known = 1;
+      sig2_star = s2;
+      break;
+    }
+    // gate passed, no component reaches theta: xi = 0, the state is unchanged
+    h->st.gates++;
+    h->st.si_runs++;
+    if (h->cfg.flags & AS_TRACE_DECISIONS) {
+      as_event ev{};
+      ev.i = i; ev.sig2_pi = s2; ev.theta = theta; ev.j_stop = 1; ev.xi = 0;
+      ev.ritz_1 = r1; ev.ritz_k = ritz[2 * (size_t)t + 1];
+      h->trace.push_back(ev);
+    }
+  }
+  if (tstar < 0 && fills) { tstar = bb - 1; gate_known = -1; }
+  if (tstar < 0) {
+    h->r = r0 + bb;
+    h->T += bb;
+    h->F = Ft[bb - 1];
+    h->theta = th[bb - 1];
+    *used = bb;
+    h->bnext = std::min(h->bmax, h->bnext * 2);
+    return AS_OK;
+  }
+  // commit rows 0..tstar, cut the speculative rows after it
+  const int rnew = r0 + tstar + 1;
+  if (rnew < r0 + bb) {
+    st = launch_truncate(h->s, h->C, h->ldc, d, rnew, r0 + bb, h->G, n2);
+    if (st != AS_OK) return st;
+  }
+  h->r = rnew;
+  h->T += tstar + 1;
+  h->F = Ft[tstar];
+  h->theta = th[tstar];
+  *used = tstar + 1;
+  h->bnext = std::max(8, std::min(h->bmax, 2 * (tstar + 1)));
+  if (h->r == n2) {                                  // lines 2-4
+    st = fd_shrink(h);
+    if (st != AS_OK) return st;
+    return finish_row(h, h->T, h->theta, -1, 0.0);
+  }
+  // large buffers reuse the batch's FP32-iterated basis for the k = 2 step
+  const int bcol = h->big ? nb + 2 * tstar : -1;
+  if (h->prof) h->prof->begin(PK_EVENT, h->s);
+  st = finish_row(h, h->T, h->theta, gate_known, sig2_star, bcol, 3 * nb);
+  if (h->prof) h->prof->end(PK_EVENT, h->s, 0.0, 0.0);
+  return st;
 }
 
 as_status build_query_gram(as_sketch* h, double* B) {
@@ -341,8 +537,11 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   h->s = (cudaStream_t)cuda_stream;
   h->key = Key{c.seed, c.stream_id};
   h->stage_rows = 256;
+  h->big = h->n2 > 128;
+  h->bmax = 64;
+  h->bnext = 64;
 
-  const int n2 = h->n2, ell = h->ell, kmax = ell;
+  const int n2 = h->n2, ell = h->ell, kmax = ell, bmax = h->bmax;
   size_t bytes = 0;
   as_status st = AS_OK;
 #define ALLOC(ptr, n)                                          \
@@ -360,10 +559,19 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   ALLOC(h->Gtmp, (size_t)n2 * n2);
   ALLOC(h->lam, (size_t)n2);
   ALLOC(h->U, (size_t)n2 * ell);
-  ALLOC(h->eigw, eig_work_doubles(n2, ell));
+  ALLOC(h->eigw, h->big ? eig_large_work_doubles(n2, ell) : eig_work_doubles(n2, ell));
   ALLOC(h->scal, 1024);
   ALLOC(h->bad, 1);
   ALLOC(h->dstatus, 1);
+  ALLOC(h->zero, 1);
+  ALLOC(h->x64, (size_t)n2);
+  ALLOC(h->y64, (size_t)n2);
+  ALLOC(h->norm2, (size_t)bmax);
+  ALLOC(h->Gf, (size_t)n2 * n2);
+  ALLOC(h->bb.X, (size_t)n2 * 3 * bmax);
+  ALLOC(h->bb.Y, (size_t)n2 * 3 * bmax);
+  ALLOC(h->bb.sig2, (size_t)bmax);
+  ALLOC(h->bb.ritz, (size_t)2 * bmax);
   ALLOC(h->si.Y, (size_t)n2 * kmax);
   ALLOC(h->si.GY, (size_t)n2 * kmax);
   ALLOC(h->si.S, (size_t)kmax * kmax);
@@ -374,7 +582,7 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   ALLOC(h->si.GWU, (size_t)n2 * kmax);
   ALLOC(h->si.tmp, (size_t)n2 * kmax + 3 * (size_t)kmax * kmax + kmax);
 #undef ALLOC
-  if (st == AS_OK && cudaMallocHost((void**)&h->h_buf, (size_t)(4 * n2 + 64) * sizeof(double)) != cudaSuccess) {
+  if (st == AS_OK && cudaMallocHost((void**)&h->h_buf, (size_t)(4 * std::max(n2, bmax) + 64) * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     h->h_buf = nullptr;
     st = AS_ENOMEM;
@@ -394,6 +602,7 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
     return st;
   }
   h->dev_bytes = bytes;
+  if (c.flags & AS_PROFILE) h->prof = new (std::nothrow) EventProf();
   h->st.d = h->d;
   h->st.ell = h->ell;
   *out = h;
@@ -420,16 +629,20 @@ as_status sketch_update(as_sketch* h, const float* rows, int64_t n, int64_t ld) 
       base = h->stage;
       ldb = h->d;
     }
-    for (int64_t t = 0; t < nb && st == AS_OK; ++t) {
-      if (ldb == h->d) {
-        st = update_row(h, base + t * ldb);
-      } else {
-        // rows with a padded stride: copy into the staging buffer first
-        cudaError_t e = cudaMemcpyAsync(h->stage, base + t * ldb, (size_t)h->d * sizeof(float),
-                                        cudaMemcpyDeviceToDevice, h->s);
-        if (e != cudaSuccess) return as_from_cuda(e);
-        st = update_row(h, h->stage);
-      }
+    if (ldb != h->d) {
+      // rows with a padded stride: compact them into the staging buffer
+      cudaError_t e = cudaMemcpy2DAsync(h->stage, (size_t)h->d * sizeof(float), base, (size_t)ldb * sizeof(float),
+                                        (size_t)h->d * sizeof(float), (size_t)nb, cudaMemcpyDeviceToDevice, h->s);
+      if (e != cudaSuccess) return as_from_cuda(e);
+      base = h->stage;
+    }
+    int64_t done = 0;
+    while (done < nb && st == AS_OK) {
+      int64_t used = 0;
+      bool bad = false;
+      st = process_block(h, base + done * h->d, nb - done, &used, &bad);
+      done += used;
+      if (st == AS_OK && bad) st = AS_EINVAL;
     }
   }
   if (st == AS_OK) {
@@ -466,10 +679,12 @@ as_status sketch_query(as_sketch* h, int64_t t, float* out, int64_t ldo, int32_t
   as_status st = dalloc(&B, (size_t)d * d);
   if (st == AS_OK) st = dalloc(&lam, (size_t)d);
   if (st == AS_OK) st = dalloc(&V, (size_t)d * ell);
-  if (st == AS_OK) st = dalloc(&w, eig_work_doubles(d, ell));
+  const bool big_q = d > 256;
+  if (st == AS_OK) st = dalloc(&w, big_q ? eig_large_work_doubles(d, ell) : eig_work_doubles(d, ell));
   if (st == AS_OK) st = dalloc(&o, (size_t)ell * d);
   if (st == AS_OK) st = build_query_gram(h, B);
-  if (st == AS_OK) st = launch_eig(h->s, d, B, d, ell, lam, V, ell, w);   // Algorithm 5 line 5
+  if (st == AS_OK)                                                          // Algorithm 5 line 5
+    st = big_q ? launch_eig_large(h->s, d, B, d, ell, lam, V, ell, w) : launch_eig(h->s, d, B, d, ell, lam, V, ell, w);
   if (st == AS_OK) st = launch_shrink_rows(h->s, d, ell, lam, V, ell, o, d);  // line 6
   if (st == AS_OK) {
     cudaError_t e = cudaMemcpy2DAsync(out, (size_t)ldo * sizeof(float), o, (size_t)d * sizeof(float),
@@ -511,6 +726,7 @@ as_status sketch_stats(as_sketch* h, as_stats* out) {
   s.theta = h->theta;
   s.device_bytes = (int64_t)h->dev_bytes;
   s.device_status = (int32_t)ds;
+  s.kernel_launches = as::launches_total();
   *out = s;
   return AS_OK;
 }
@@ -520,6 +736,37 @@ as_status sketch_trace(as_sketch* h, as_event* out, int64_t cap, int64_t* count)
   const int64_t n = (int64_t)h->trace.size();
   for (int64_t t = 0; t < std::min(n, cap); ++t) out[t] = h->trace[t];
   *count = n;
+  return AS_OK;
+}
+
+as_status sketch_profile(as_sketch* h, as_kernel_stat* out, int32_t cap, int32_t* count) {
+  if (!h || !count || cap < 0 || (cap > 0 && !out)) return AS_EINVAL;
+  if (!h->prof) { *count = 0; return AS_OK; }
+  AS_CUDA_TRY(cudaStreamSynchronize(h->s));
+  h->prof->resolve();
+  int n = 0;
+  for (int c = 0; c < PK_COUNT; ++c) {
+    if (n < cap) {
+      as_kernel_stat& k = out[n];
+      std::memset(&k, 0, sizeof(k));
+      std::strncpy(k.name, kProfNames[c], sizeof(k.name) - 1);
+      k.launches = h->prof->launches[c];
+      k.total_ms = h->prof->ms[c];
+      k.flops = h->prof->flops[c];
+      k.bytes = h->prof->bytes[c];
+    }
+    ++n;
+  }
+  *count = n;
+  return AS_OK;
+}
+
+as_status sketch_profile_reset(as_sketch* h) {
+  if (!h) return AS_EINVAL;
+  if (h->prof) {
+    AS_CUDA_TRY(cudaStreamSynchronize(h->s));
+    h->prof->reset();
+  }
   return AS_OK;
 }
 

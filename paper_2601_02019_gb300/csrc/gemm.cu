@@ -113,7 +113,7 @@ as_status gemm_strided(cudaStream_t s, int M, int N, int K, const TA* A, long lo
   }
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
   gemm_strided_kernel<TA, TB, TO><<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, O, som, son,
-                                                       alpha, beta);
+                                                       alpha, beta); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }

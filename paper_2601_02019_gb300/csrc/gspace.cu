@@ -308,13 +308,13 @@ __global__ void shrink_rows_kernel(int d, int ell, const double* lam, const doub
 as_status launch_ingest(cudaStream_t s, const float* rows, long long ld_in, int n, int d, float* C, int ldc,
                         int r, double* norm2, int* bad) {
   if (n <= 0) return AS_OK;
-  ingest_kernel<<<n, 256, 0, s>>>(rows, ld_in, n, d, C, ldc, r, norm2, bad);
+  ingest_kernel<<<n, 256, 0, s>>>(rows, ld_in, n, d, C, ldc, r, norm2, bad); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }
 
 as_status launch_truncate(cudaStream_t s, float* C, int ldc, int d, int r0, int r1, double* G, int n2) {
-  truncate_kernel<<<128, 256, 0, s>>>(C, ldc, d, r0, r1, G, n2);
+  truncate_kernel<<<128, 256, 0, s>>>(C, ldc, d, r0, r1, G, n2); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }
@@ -326,7 +326,7 @@ as_status launch_gram_rows(cudaStream_t s, const float* C, int ldc, int d, int r
   if (st != AS_OK) return st;
   if (r > 0) {
     dim3 grid((r + 255) / 256, b);
-    mirror_kernel<<<grid, 256, 0, s>>>(G, n2, r, b);
+    mirror_kernel<<<grid, 256, 0, s>>>(G, n2, r, b); count_launches(1);
     AS_CUDA_TRY(cudaGetLastError());
   }
   return AS_OK;
@@ -338,35 +338,35 @@ as_status launch_power_iteration(cudaStream_t s, const double* G, int n2, int m,
   if (smem > 48 * 1024)
     AS_CUDA_TRY(cudaFuncSetAttribute(power_iteration_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-  power_iteration_kernel<<<1, 512, smem, s>>>(G, n2, m, k_pi, key, i, sig2);
+  power_iteration_kernel<<<1, 512, smem, s>>>(G, n2, m, k_pi, key, i, sig2); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }
 
 as_status launch_simul_iter(cudaStream_t s, const double* G, int n2, int m, int k, int q, Key key, uint64_t i,
                             int j, const SiBuffers& b, int* status) {
-  simul_iter_kernel<<<1, 512, 0, s>>>(G, n2, m, k, q, key, i, j, b, b.tmp, status);
+  simul_iter_kernel<<<1, 512, 0, s>>>(G, n2, m, k, q, key, i, j, b, b.tmp, status); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }
 
 as_status launch_eig(cudaStream_t s, int n, double* A, int lda, int nev, double* evals, double* X, int ldx,
                      double* work) {
-  eig_kernel<<<1, 512, 0, s>>>(n, A, lda, nev, evals, X, ldx, work);
+  eig_kernel<<<1, 512, 0, s>>>(n, A, lda, nev, evals, X, ldx, work); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }
 
 as_status launch_shrink_weights(cudaStream_t s, int n2, int ell, const double* lam, double* U, float* W) {
   if (ell <= 1) return AS_OK;
-  shrink_weights_kernel<<<ell - 1, 256, 0, s>>>(n2, ell, lam, U, W);
+  shrink_weights_kernel<<<ell - 1, 256, 0, s>>>(n2, ell, lam, U, W); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }
 
 as_status launch_shrink_rows(cudaStream_t s, int d, int ell, const double* lam, const double* V, int ldv,
                              float* out, long long ldo) {
-  shrink_rows_kernel<<<ell, 256, 0, s>>>(d, ell, lam, V, ldv, out, ldo);
+  shrink_rows_kernel<<<ell, 256, 0, s>>>(d, ell, lam, V, ldv, out, ldo); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }

@@ -7,6 +7,23 @@
 
 namespace as {
 
+// Optional per-kernel-class event timer (the sketch's AS_PROFILE mode).
+enum ProfClass {
+  PK_BATCH_GEMM = 0,  // batched G-space product  Y = G X  (FP32)
+  PK_BATCH_ORTH,      // batched normalisation / SVQB / Rayleigh-Ritz
+  PK_EIG,             // FP64 eigensolver of the FD shrink
+  PK_REBUILD,         // FD rebuild C' = W C~ and G = C' C'^T
+  PK_GRAM,            // Gram rows of a block
+  PK_INGEST,          // row ingest
+  PK_EVENT,           // FP64 single-row path of an event row and the dump
+  PK_COUNT
+};
+struct Prof {
+  virtual void begin(int cls, cudaStream_t s) = 0;
+  virtual void end(int cls, cudaStream_t s, double flops, double bytes) = 0;
+  virtual ~Prof() {}
+};
+
 // Strided SIMT GEMM, see gemm.cu.
 template <typename TA, typename TB, typename TO>
 as_status gemm_strided(cudaStream_t s, int M, int N, int K, const TA* A, long long sam, long long sak,
@@ -54,6 +71,39 @@ as_status launch_eig(cudaStream_t s, int n, double* A, int lda, int nev, double*
 // FD shrink weights: sign-canonicalise columns j < l-1 of U (n2 x l) and
 // write W[j][p] = sqrt(max(lam_j - lam_l, 0) / lam_j) * u_j[p] (FP32, (l-1) x n2).
 as_status launch_shrink_weights(cudaStream_t s, int n2, int ell, const double* lam, double* U, float* W);
+
+// Large-matrix FP64 eigensolver spread over the GPU (eig_large.cu); same
+// contract as launch_eig.  Work size: eig_large_work_doubles(n, nev).
+size_t eig_large_work_doubles(int n, int nev);
+as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, double* evals, double* X, int ldx,
+                           double* work);
+
+// FP32 mirror of the leading m x m block of G (zero elsewhere).
+as_status launch_gf_mirror(cudaStream_t s, const double* G, float* Gf, int n2, int m);
+
+struct BatchBuffers {
+  float* X;       // n2 x 3*bmax
+  float* Y;       // n2 x 3*bmax
+  double* sig2;   // bmax   power-iteration estimates
+  double* ritz;   // 2*bmax the two Ritz values of the k = 2 step
+};
+
+// Block-speculative power iteration and first doubling step for rows
+// t = 0..nb-1 of a block whose row t sees the leading (r0+t+1) rows (FP32).
+as_status launch_batch_gspace(cudaStream_t s, const float* Gf, int n2, int r0, int nb, int k_pi, int q, Key key,
+                              uint64_t i0, const BatchBuffers& bb, Prof* prof);
+
+// FP64 single-row power iteration and simultaneous iteration built from
+// multi-block products (any buffer size).  x, y: n2 doubles; zero: 1 int.
+as_status launch_power_iteration_f64(cudaStream_t s, const double* G, int n2, int m, int k_pi, Key key,
+                                     uint64_t i, double* x, double* y, int* zero, double* sig2);
+as_status launch_simul_iter_f64(cudaStream_t s, const double* G, int n2, int m, int k, int q, Key key, uint64_t i,
+                                int j, const SiBuffers& b, int* status);
+
+// The Rayleigh-Ritz step of Algorithm 2 (k = 2) in FP64 on the iterated
+// basis that the batched pass left in columns col0, col0+1 of X (FP32).
+as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m, const float* X, int ldx, int col0,
+                                  const SiBuffers& b, int* status);
 
 // Query helpers.
 as_status launch_shrink_rows(cudaStream_t s, int d, int ell, const double* lam, const double* V, int ldv,

@@ -160,3 +160,46 @@ def test_invalid_configs():
     with pytest.raises(p.AeroSketchError) as e:
         p.Sketch(8, 2, prec=p.AS_BF16)
     assert e.value.code == p.binding.AS_ENOTSUP
+
+
+def test_parity_large_buffer_path():
+    """2l = 512 > 128 takes the multi-block FP64 path and the spread eigensolver
+    (d = 1024, l = 256, rank-200 power-law spectrum, several shrinks)."""
+    p = _gpu()
+    A = low_rank_noisy(1600, 1024, 200, spectrum("powerlaw", 200), seed=0)
+    s, o, eg, eo = _compare(p, A, 1024, 256)
+    assert s.stats()["shrinks"] >= 2 and s.stats()["dumps"] >= 10
+
+
+def test_full_size_window_d4096_l1024():
+    """The tight-error workload at full size (d = 4096, l = 1024): run the GPU to
+    just before the first shrink, hand its exact state to the oracle, and
+    compare a window of rows that contains the shrink and several dumps."""
+    p = _gpu()
+    d, ell = 4096, 1024
+    start, win = 2040, 24
+    A = workload_rows("tight_d4096_l1024", n=start + win)
+    s = p.Sketch(d, ell, trace=True)
+    s.update(A[:start])
+    C0, r0 = s.buffer()
+    st0 = s.stats()
+    B0 = s.query_gram()
+    n_ev0 = len(s.trace())
+    s.update(A[start:])
+    ev = s.trace()[n_ev0:]
+    o = AeroSketch(d, ell, replay=p.binding.replay_from_trace(ev), tie_rel=TIE)
+    o.load_state(C0, r0, st0["fro2"], st0["rows"])
+    o.run(A[start:].astype(np.float64))
+    assert not o.mismatches, o.mismatches[:5]
+    assert [e.i for e in o.events] == [e["i"] for e in ev]
+    assert [(e.j_stop, e.xi) for e in o.events] == [(e["j_stop"], e["xi"]) for e in ev]
+    assert len(o.shrink_rows) == 1
+    C1, _ = s.buffer()
+    C1 = C1.astype(np.float64)
+    Aw = A[start:].astype(np.float64)
+    scale = np.trace(C0.astype(np.float64).T @ C0.astype(np.float64)) + np.sum(Aw * Aw)
+    assert np.abs(C1.T @ C1 - o.C.T @ o.C).max() <= 1e-5 * scale
+    # what the window added to B (Algorithm 5 lines 1-4) agrees
+    dB_gpu = s.query_gram() - B0
+    dB_orc = o.pre_query() - C0.astype(np.float64).T @ C0.astype(np.float64)
+    assert np.abs(dB_gpu - dB_orc).max() <= 1e-5 * scale
