@@ -281,7 +281,7 @@ size_t eig_large_work_doubles(int n, int nev) {
 }
 
 as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, double* evals, double* X, int ldx,
-                           double* work) {
+                           double* work, Prof* prof) {
   if (n < 3) return launch_eig(s, n, A, lda, nev, evals, X, ldx, work);
   TriWork w;
   w.d = work;
@@ -295,6 +295,7 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
   const size_t smem1 = (size_t)n * sizeof(double);
   if (smem1 > 48 * 1024)
     AS_CUDA_TRY(cudaFuncSetAttribute(tri_step1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+  if (prof) prof->begin(PK_EIG_TRI, s);
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
     const int nb = (m + kTriRowsPerBlock - 1) / kTriRowsPerBlock;
@@ -303,13 +304,18 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
     tri_step2<<<g2, 256, 0, s>>>(A, lda, n, k, nb, w); count_launches(1);
   }
   tri_tail<<<1, 32, 0, s>>>(A, lda, n, w); count_launches(1);
+  if (prof) prof->end(PK_EIG_TRI, s, 4.0 / 3.0 * (double)n * n * n, 8.0 * (double)n * n);
+  if (prof) prof->begin(PK_EIG_SOLVE, s);
   tri_norm<<<1, 256, 0, s>>>(n, w, norms); count_launches(1);
   bisect_invit<<<(nev + 31) / 32, 32, 0, s>>>(n, nev, w, norms, evals, X, ldx, lu); count_launches(1);
   cluster_mgs<<<1, 512, 0, s>>>(n, nev, norms, evals, X, ldx); count_launches(1);
+  if (prof) prof->end(PK_EIG_SOLVE, s, 0.0, 0.0);
+  if (prof) prof->begin(PK_EIG_BACK, s);
   const size_t smem3 = (size_t)n * kSlab * sizeof(double);
   if (smem3 > 48 * 1024)
     AS_CUDA_TRY(cudaFuncSetAttribute(back_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
   back_transform<<<(nev + kSlab - 1) / kSlab, 256, smem3, s>>>(A, lda, n, nev, X, ldx); count_launches(1);
+  if (prof) prof->end(PK_EIG_BACK, s, 2.0 * (double)n * n * nev, 8.0 * (double)n * n);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }

@@ -55,8 +55,10 @@ int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
-const char* const kProfNames[PK_COUNT] = {"gspace_batch_gemm", "gspace_batch_orth", "eig_fp64",  "fd_rebuild_gemm",
-                                          "gram_rows_gemm",    "ingest",            "event_row_fp64"};
+const char* const kProfNames[PK_COUNT] = {"gspace_batch_gemm", "gspace_batch_orth", "eig_fp64",
+                                          "fd_rebuild_gemm",   "gram_rows_gemm",    "ingest",
+                                          "event_row_fp64",    "eig_tridiag",       "eig_bisect_invit",
+                                          "eig_backtransform"};
 
 // CUDA-event timer per kernel class; pairs are resolved lazily.
 struct EventProf final : Prof {
@@ -118,7 +120,9 @@ struct as_sketch {
   // device buffers
   float *C = nullptr, *Cnew = nullptr, *Wfd = nullptr, *stage = nullptr, *Gf = nullptr;
   double *G = nullptr, *Gtmp = nullptr, *lam = nullptr, *U = nullptr, *eigw = nullptr, *scal = nullptr;
-  double *x64 = nullptr, *y64 = nullptr, *norm2 = nullptr;
+  double *x64 = nullptr, *y64 = nullptr, *norm2 = nullptr, *dwork = nullptr;
+  size_t dwork_cap = 0;
+  size_t p_cap = 0;
   int *bad = nullptr, *dstatus = nullptr, *zero = nullptr;
   SiBuffers si{};
   BatchBuffers bb{};
@@ -143,10 +147,10 @@ struct as_sketch {
 namespace {
 
 void free_all(as_sketch* h) {
-  float* fp[] = {h->C, h->Cnew, h->Wfd, h->stage, h->arena, h->Gf, h->bb.X, h->bb.Y};
+  float* fp[] = {h->C, h->Cnew, h->Wfd, h->stage, h->arena, h->Gf, h->bb.X, h->bb.P};
   for (float* p : fp) if (p) cudaFree(p);
   double* dp[] = {h->G, h->Gtmp, h->lam, h->U, h->eigw, h->scal, h->si.Y, h->si.GY, h->si.S, h->si.V,
-                  h->si.eigw, h->si.ritz, h->si.WU, h->si.GWU, h->si.tmp, h->x64, h->y64, h->norm2,
+                  h->si.eigw, h->si.ritz, h->si.WU, h->si.GWU, h->si.tmp, h->x64, h->y64, h->norm2, h->dwork,
                   h->bb.sig2, h->bb.ritz};
   for (double* p : dp) if (p) cudaFree(p);
   if (h->bad) cudaFree(h->bad);
@@ -193,7 +197,7 @@ as_status fd_shrink(as_sketch* h) {
   const int n2 = h->n2, ell = h->ell, d = h->d;
   AS_CUDA_TRY(cudaMemcpyAsync(h->Gtmp, h->G, (size_t)n2 * n2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
   if (h->prof) h->prof->begin(PK_EIG, h->s);
-  as_status st = h->big ? launch_eig_large(h->s, n2, h->Gtmp, n2, ell, h->lam, h->U, ell, h->eigw)
+  as_status st = h->big ? launch_eig_large(h->s, n2, h->Gtmp, n2, ell, h->lam, h->U, ell, h->eigw, h->prof)
                          : launch_eig(h->s, n2, h->Gtmp, n2, ell, h->lam, h->U, ell, h->eigw);
   if (st != AS_OK) return st;
   // tridiagonalisation 4/3 n^3 + back-transformation 2 n^2 nev; G read once
@@ -232,18 +236,16 @@ as_status dump(as_sketch* h, int xi, int k, int64_t i) {
   if (st != AS_OK) return st;
   float* Z = h->arena + h->arena_used;
   float* Y = Z + (size_t)d * xi;
-  // Z = C'^T (W U)_xi   (d x xi)
-  st = gemm_strided<float, double, float>(h->s, d, xi, r, h->C, 1, ldc, h->si.WU, k, 1, Z, xi, 1, 1.0, 0.0);
-  if (st != AS_OK) return st;
-  // Y = (G W U)_xi^T C' = Z^T C'^T C'   (xi x d)
-  st = gemm_strided<double, float, float>(h->s, xi, d, r, h->si.GWU, 1, k, h->C, ldc, 1, Y, d, 1, 1.0, 0.0);
-  if (st != AS_OK) return st;
-  // C = C' - C' Z Z^T = C' - (G W U)_xi Z^T
-  st = gemm_strided<double, float, float>(h->s, r, d, xi, h->si.GWU, k, 1, Z, 1, xi, h->C, ldc, 1, -1.0, 1.0);
-  if (st != AS_OK) return st;
-  // G = C C^T = G - (G W U)_xi (G W U)_xi^T   (W U is G-orthonormal)
-  st = gemm_strided<double, double, double>(h->s, r, r, xi, h->si.GWU, k, 1, h->si.GWU, 1, k, h->G, n2, 1, -1.0,
-                                            1.0);
+  const size_t need = dump_work_doubles(d, xi);
+  if (need > h->dwork_cap) {
+    if (h->dwork) cudaFree(h->dwork);
+    h->dwork = nullptr;
+    h->dwork_cap = 0;
+    st = dalloc(&h->dwork, need);
+    if (st != AS_OK) return st;
+    h->dwork_cap = need;
+  }
+  st = launch_dump(h->s, h->C, ldc, d, r, h->G, n2, h->si.WU, h->si.GWU, k, xi, Z, Y, h->dwork);
   if (st != AS_OK) return st;
   const int64_t s_prev = h->snaps.empty() ? 1 : h->snaps.back().t + 1;
   h->snaps.push_back(Snap{h->arena_used, xi, s_prev, i});
@@ -285,7 +287,7 @@ as_status finish_row(as_sketch* h, int64_t i, double theta, int known_gate, doub
   for (int j = 1; j <= h->jmax; ++j) {              // line 9
     const int k = std::min(std::min(1 << std::min(j, 30), h->ell), h->d);  // line 10
     if (j == 1 && k == 2 && batch_col >= 0)       // iterated basis from the batched pass
-      st = launch_si_rr_from_batch(h->s, h->G, h->n2, h->r, h->bb.X, batch_ld, batch_col, h->si, h->dstatus);
+      st = launch_si_rr_from_batch(h->s, h->G, h->n2, h->r, h->bb.X, batch_col, h->si, h->dstatus);
     else if (h->big)
       st = launch_simul_iter_f64(h->s, h->G, h->n2, h->r, k, h->q, h->key, (uint64_t)i, j, h->si, h->dstatus);
     else
@@ -351,7 +353,7 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
   }
   // line 1 for the whole block: G gains the new rows and columns
   if (h->prof) h->prof->begin(PK_GRAM, h->s);
-  st = launch_gram_rows(h->s, h->C, h->ldc, d, r0, bb, h->G, n2);
+  st = launch_gram_rows_skinny(h->s, h->C, h->ldc, d, r0, bb, h->G, n2, h->bb.P, h->p_cap);
   if (st != AS_OK) return st;
   if (h->prof)
     h->prof->end(PK_GRAM, h->s, 2.0 * (r0 + bb) * (double)bb * d, 4.0 * (r0 + bb) * (double)d + 8.0 * (r0 + bb) * bb);
@@ -568,8 +570,10 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   ALLOC(h->y64, (size_t)n2);
   ALLOC(h->norm2, (size_t)bmax);
   ALLOC(h->Gf, (size_t)n2 * n2);
+  h->bb.max_splits = 16;
+  h->p_cap = std::max((size_t)h->bb.max_splits * n2 * 3 * bmax, (size_t)64 * bmax * n2);
   ALLOC(h->bb.X, (size_t)n2 * 3 * bmax);
-  ALLOC(h->bb.Y, (size_t)n2 * 3 * bmax);
+  ALLOC(h->bb.P, h->p_cap);
   ALLOC(h->bb.sig2, (size_t)bmax);
   ALLOC(h->bb.ritz, (size_t)2 * bmax);
   ALLOC(h->si.Y, (size_t)n2 * kmax);

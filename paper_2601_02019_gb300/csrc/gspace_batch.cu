@@ -1,4 +1,5 @@
-// Block-speculative G-space iterations and the FP64 single-row path for large buffers.
+// Block-speculative G-space iterations, the FP64 single-row path for large
+// buffers, and the dump kernels.
 //
 // Within a block of b new rows and no event (no shrink, no dump), the buffer
 // only grows by appending rows, so the state seen by row t of the block is the
@@ -7,11 +8,16 @@
 // (k = 2) of the simultaneous iteration of every row (Algorithm 2) are then
 // independent problems on masked columns of one matrix:
 //     X <- mask(G X)    (mask_t keeps rows < m_t = r + t + 1)
-// and run as one GEMM over G per iteration, followed by a per-row
+// and run as one split-K GEMM over G per iteration, followed by a per-row
 // normalisation (k = 1) or SVQB orthonormalisation (k = 2).  These batched
-// values are only used to locate the first row whose decision changes the
-// state; that row, and any row whose batched value lies within a 1e-4
-// relative band of a threshold, is recomputed by the FP64 single-row path.
+// values locate the first row whose decision changes the state; that row is
+// finished in FP64 (its Rayleigh-Ritz step reuses the batch's iterated basis)
+// and rows whose batched value lies within a 1e-4 relative band of a
+// threshold are re-decided by the FP64 power iteration.
+//
+// Batch matrix layout: column-major, column c at X + c*n2; columns [0, nb)
+// are the power-iteration vectors of rows 0..nb-1 and columns nb+2t, nb+2t+1
+// the simultaneous-iteration pair of row t.
 #include "eig.cuh"
 #include "kernels.cuh"
 
@@ -19,25 +25,23 @@ namespace as {
 
 namespace {
 
-// Column layout of the batch matrix X (n2 x ncol, row-major, ld = ncol):
-//   columns [0, nb)          : power-iteration vectors of rows 0..nb-1
-//   columns [nb + 2t, +2)    : simultaneous-iteration pair of row t
-__global__ void batch_fill_kernel(float* X, int n2, int ncol, int nb, int r0, Key key, uint64_t i0) {
-  // one block per (row t, kind); kind 0 = PI column, kind 1 = SI pair
-  const int t = blockIdx.x, kind = blockIdx.y;
+__global__ void batch_fill_kernel(float* X, int n2, int nb, int r0, Key key, uint64_t i0) {
+  const int t = blockIdx.x, kind = blockIdx.y;  // kind 0: PI column, 1: SI pair
   const int m = r0 + t + 1;
   const uint64_t i = i0 + (uint64_t)t;
   if (kind == 0) {
+    float* x = X + (size_t)t * n2;
     for (int blk = threadIdx.x; blk * 4 < n2; blk += blockDim.x) {
       double z[4];
       gauss4(key, kPurposePiStart, i, 0, blk, z);
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         const int p = blk * 4 + l;
-        if (p < n2) X[(size_t)p * ncol + t] = (p < m) ? (float)z[l] : 0.f;
+        if (p < n2) x[p] = (p < m) ? (float)z[l] : 0.f;
       }
     }
   } else {
+    float* x0 = X + (size_t)(nb + 2 * t) * n2;
     // Pi is n2 x 2 row-major: element e = 2p + c
     for (int blk = threadIdx.x; blk * 4 < 2 * n2; blk += blockDim.x) {
       double z[4];
@@ -47,73 +51,79 @@ __global__ void batch_fill_kernel(float* X, int n2, int ncol, int nb, int r0, Ke
         const int e = blk * 4 + l;
         if (e < 2 * n2) {
           const int p = e >> 1, c = e & 1;
-          X[(size_t)p * ncol + nb + 2 * t + c] = (p < m) ? (float)z[l] : 0.f;
+          x0[(size_t)c * n2 + p] = (p < m) ? (float)z[l] : 0.f;
         }
       }
     }
   }
 }
 
-// After Y = G X: mask rows >= m_t and normalise (PI) or SVQB-orthonormalise
-// (SI pair) each problem's columns; the result goes back into X.
-// On the final pass (final = 1) instead compute sigma^2 (PI: x^T G x with
-// X = x, Y = G x) and the two Ritz values (SI: S = X^T Y, M = (GW)^T(GW)).
-__global__ void batch_orth_kernel(const float* Y, float* X, int n2, int ncol, int nb, int r0, int pi_active,
-                                  int final, double* sig2, double* ritz) {
+__device__ __forceinline__ double psum(const float* P, long long plane, int S, size_t off) {
+  double v = 0.0;
+  for (int s = 0; s < S; ++s) v += (double)P[(long long)s * plane + off];
+  return v;
+}
+
+__device__ __forceinline__ void eig2(double s00, double s01, double s11, double& l0, double& l1, double& v00,
+                                     double& v01, double& v10, double& v11) {
+  const double tr = 0.5 * (s00 + s11), df = 0.5 * (s00 - s11);
+  const double rad = sqrt(df * df + s01 * s01);
+  l0 = tr + rad;
+  l1 = tr - rad;
+  if (rad == 0.0) { v00 = 1; v10 = 0; v01 = 0; v11 = 1; return; }
+  const double th = 0.5 * atan2(2.0 * s01, s00 - s11);
+  v00 = cos(th); v10 = sin(th); v01 = -v10; v11 = v00;
+}
+
+// After Y = G X (S partial planes in P): PI columns are normalised, SI pairs
+// SVQB-orthonormalised (twice); on the final pass sigma^2 = x^T (G x) and the
+// Ritz values of the pair are computed instead.  kind = kind0 + blockIdx.y.
+__global__ void batch_orth_kernel(const float* __restrict__ P, long long plane, int S, float* X, int n2, int nb,
+                                  int r0, int kind0, int final_pi, int final_si, double* sig2, double* ritz) {
   __shared__ double red[32];
-  const int t = blockIdx.x, kind = blockIdx.y;
+  const int t = blockIdx.x, kind = kind0 + blockIdx.y;
   const int m = r0 + t + 1;
   if (kind == 0) {
-    if (!pi_active) return;
-    const int c = t;
-    if (final) {
+    float* x = X + (size_t)t * n2;
+    const size_t off = (size_t)t * n2;
+    if (final_pi) {
       double s = 0.0;
-      for (int p = threadIdx.x; p < m; p += blockDim.x) s += (double)X[(size_t)p * ncol + c] * Y[(size_t)p * ncol + c];
+      for (int p = threadIdx.x; p < m; p += blockDim.x) s += (double)x[p] * psum(P, plane, S, off + p);
       s = block_sum(s, red);
       if (threadIdx.x == 0) sig2[t] = s;
       return;
     }
     double s = 0.0;
     for (int p = threadIdx.x; p < m; p += blockDim.x) {
-      const double y = Y[(size_t)p * ncol + c];
+      const double y = psum(P, plane, S, off + p);
       s += y * y;
     }
     s = block_sum(s, red);
     const double inv = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
-    for (int p = threadIdx.x; p < n2; p += blockDim.x)
-      X[(size_t)p * ncol + c] = (p < m) ? (float)(Y[(size_t)p * ncol + c] * inv) : 0.f;
+    for (int p = threadIdx.x; p < n2; p += blockDim.x) x[p] = (p < m) ? (float)(psum(P, plane, S, off + p) * inv) : 0.f;
     return;
   }
-  const int c0 = nb + 2 * t;
-  if (final) {
-    // S = X^T (G X) (X orthonormal), SVQB -> W = X V D^-1/2, GW = Y V D^-1/2,
-    // M = (GW)^T (GW); Ritz values = eig(M)
+  const size_t o0 = (size_t)(nb + 2 * t) * n2, o1 = o0 + n2;
+  float* x0 = X + o0;
+  float* x1 = X + o1;
+  if (final_si) {
+    // S = X^T (G X) (X orthonormal); SVQB -> W = X V D^-1/2, GW = Y V D^-1/2;
+    // Ritz values = eig((GW)^T (GW))
     double s00 = 0, s01 = 0, s11 = 0;
     for (int p = threadIdx.x; p < m; p += blockDim.x) {
-      const double x0 = X[(size_t)p * ncol + c0], x1 = X[(size_t)p * ncol + c0 + 1];
-      const double y0 = Y[(size_t)p * ncol + c0], y1 = Y[(size_t)p * ncol + c0 + 1];
-      s00 += x0 * y0; s01 += 0.5 * (x0 * y1 + x1 * y0); s11 += x1 * y1;
+      const double a = x0[p], b = x1[p];
+      const double y0 = psum(P, plane, S, o0 + p), y1 = psum(P, plane, S, o1 + p);
+      s00 += a * y0; s01 += 0.5 * (a * y1 + b * y0); s11 += b * y1;
     }
     s00 = block_sum(s00, red); s01 = block_sum(s01, red); s11 = block_sum(s11, red);
-    // eig of the 2x2 S
     double l0, l1, v00, v01, v10, v11;
-    {
-      const double tr = 0.5 * (s00 + s11), df = 0.5 * (s00 - s11);
-      const double rad = sqrt(df * df + s01 * s01);
-      l0 = tr + rad; l1 = tr - rad;
-      if (rad == 0.0) { v00 = 1; v10 = 0; v01 = 0; v11 = 1; }
-      else {
-        const double th = 0.5 * atan2(2.0 * s01, s00 - s11);
-        v00 = cos(th); v10 = sin(th); v01 = -v10; v11 = v00;
-      }
-    }
+    eig2(s00, s01, s11, l0, l1, v00, v01, v10, v11);
     const double tol = 1e-6 * fmax(l0, 0.0);
     const double a0 = (l0 > tol && l0 > 0) ? 1.0 / sqrt(l0) : 0.0;
     const double a1 = (l1 > tol && l1 > 0) ? 1.0 / sqrt(l1) : 0.0;
-    // GW columns: g_c = Y v_c a_c ; M = G W^T G W
     double m00 = 0, m01 = 0, m11 = 0;
     for (int p = threadIdx.x; p < m; p += blockDim.x) {
-      const double y0 = Y[(size_t)p * ncol + c0], y1 = Y[(size_t)p * ncol + c0 + 1];
+      const double y0 = psum(P, plane, S, o0 + p), y1 = psum(P, plane, S, o1 + p);
       const double g0 = (y0 * v00 + y1 * v10) * a0, g1 = (y0 * v01 + y1 * v11) * a1;
       m00 += g0 * g0; m01 += g0 * g1; m11 += g1 * g1;
     }
@@ -121,44 +131,35 @@ __global__ void batch_orth_kernel(const float* Y, float* X, int n2, int ncol, in
     if (threadIdx.x == 0) {
       const double tr = 0.5 * (m00 + m11), df = 0.5 * (m00 - m11);
       const double rad = sqrt(df * df + m01 * m01);
-      ritz[2 * t] = tr + rad;
+      ritz[2 * t] = (a0 > 0) ? tr + rad : 0.0;
       ritz[2 * t + 1] = (a0 > 0 && a1 > 0) ? tr - rad : 0.0;
-      if (!(a0 > 0)) { ritz[2 * t] = 0.0; ritz[2 * t + 1] = 0.0; }
     }
     return;
   }
-  // Euclidean SVQB of the pair, twice (second pass on the result)
-  double y0s[1];
-  (void)y0s;
+  // Euclidean SVQB of the pair: pass 0 reads Y (partials), pass 1 re-orthonormalises X
   for (int pass = 0; pass < 2; ++pass) {
-    const float* src = (pass == 0) ? Y : X;
     double s00 = 0, s01 = 0, s11 = 0;
     for (int p = threadIdx.x; p < m; p += blockDim.x) {
-      const double a = src[(size_t)p * ncol + c0], b = src[(size_t)p * ncol + c0 + 1];
+      const double a = pass ? (double)x0[p] : psum(P, plane, S, o0 + p);
+      const double b = pass ? (double)x1[p] : psum(P, plane, S, o1 + p);
       s00 += a * a; s01 += a * b; s11 += b * b;
     }
     s00 = block_sum(s00, red); s01 = block_sum(s01, red); s11 = block_sum(s11, red);
-    const double tr = 0.5 * (s00 + s11), df = 0.5 * (s00 - s11);
-    const double rad = sqrt(df * df + s01 * s01);
-    const double l0 = tr + rad, l1 = tr - rad;
-    double v00, v01, v10, v11;
-    if (rad == 0.0) { v00 = 1; v10 = 0; v01 = 0; v11 = 1; }
-    else {
-      const double th = 0.5 * atan2(2.0 * s01, s00 - s11);
-      v00 = cos(th); v10 = sin(th); v01 = -v10; v11 = v00;
-    }
+    double l0, l1, v00, v01, v10, v11;
+    eig2(s00, s01, s11, l0, l1, v00, v01, v10, v11);
     const double tol = 1e-13 * fmax(l0, 0.0);
     const double a0 = (l0 > tol && l0 > 0) ? 1.0 / sqrt(l0) : 0.0;
     const double a1 = (l1 > tol && l1 > 0) ? 1.0 / sqrt(l1) : 0.0;
     for (int p = threadIdx.x; p < n2; p += blockDim.x) {
-      float o0 = 0.f, o1 = 0.f;
+      float o0v = 0.f, o1v = 0.f;
       if (p < m) {
-        const double a = src[(size_t)p * ncol + c0], b = src[(size_t)p * ncol + c0 + 1];
-        o0 = (float)((a * v00 + b * v10) * a0);
-        o1 = (float)((a * v01 + b * v11) * a1);
+        const double a = pass ? (double)x0[p] : psum(P, plane, S, o0 + p);
+        const double b = pass ? (double)x1[p] : psum(P, plane, S, o1 + p);
+        o0v = (float)((a * v00 + b * v10) * a0);
+        o1v = (float)((a * v01 + b * v11) * a1);
       }
-      X[(size_t)p * ncol + c0] = o0;
-      X[(size_t)p * ncol + c0 + 1] = o1;
+      x0[p] = o0v;
+      x1[p] = o1v;
     }
     __syncthreads();
   }
@@ -173,7 +174,7 @@ __global__ void mirror_f32_kernel(const double* G, float* Gf, int n2, int m) {
   }
 }
 
-// ---- FP64 single-row path pieces (any buffer size) --------------------------
+// ---- FP64 single-row path (any buffer size) ---------------------------------
 __global__ void fill_pi_start(double* x, int n2, int m, Key key, uint64_t i) {
   for (int blk = blockIdx.x * blockDim.x + threadIdx.x; blk * 4 < n2; blk += gridDim.x * blockDim.x) {
     double z[4];
@@ -199,7 +200,31 @@ __global__ void fill_si_test(double* Y, int n2, int m, int k, Key key, uint64_t 
   }
 }
 
-// x <- y / ||y|| (first m entries); flag[0] = 1 if ||y|| == 0.  One block.
+// Y[p][c] = sum_{q<m} G[p][q] X[q][c] for p < m, c < k <= KT (X, Y row-major n2 x k); one warp per row.
+template <int KT>
+__global__ void __launch_bounds__(256) gmul_thin_kernel(const double* __restrict__ G, int n2, int m, int k,
+                                                       const double* __restrict__ X, double* __restrict__ Y) {
+  const int lane = threadIdx.x & 31;
+  const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (p >= m) return;
+  const double* g = G + (size_t)p * n2;
+  double acc[KT];
+#pragma unroll
+  for (int c = 0; c < KT; ++c) acc[c] = 0.0;
+  for (int q = lane; q < m; q += 32) {
+    const double gv = g[q];
+#pragma unroll
+    for (int c = 0; c < KT; ++c)
+      if (c < k) acc[c] += gv * X[(size_t)q * k + c];
+  }
+#pragma unroll
+  for (int c = 0; c < KT; ++c) {
+    const double v = warp_sum(acc[c]);
+    if (lane == 0 && c < k) Y[(size_t)p * k + c] = v;
+  }
+}
+
+// x <- y / ||y|| (first m entries); *zero = 1 if ||y|| == 0.  One block.
 __global__ void normalize_kernel(const double* y, double* x, int m, int* zero) {
   __shared__ double red[32];
   double s = 0.0;
@@ -218,16 +243,24 @@ __global__ void dot_kernel(const double* x, const double* y, int m, const int* z
   if (threadIdx.x == 0) *out = (*zero) ? 0.0 : s;
 }
 
-// One block: S = X^T X (or X^T Xg for the G inner product when gram_of != nullptr),
-// SVQB with eig(S); X, Xg <- (.) V D^-1/2 (kept columns).  Rows >= m are zero.
-__global__ void svqb_kernel(int n2, int m, int k, double* X, double* Xg, int g_inner, double* S, double* V,
-                            double* D, double* eigw, double* tmp) {
-  __shared__ double red[32];
-  const double* B = g_inner ? Xg : X;
+// S = sym(A^T B) over the first m rows (A, B row-major n2 x k).
+__device__ void block_gram(int m, int k, const double* A, const double* B, double* S, double* red) {
+  if (k <= 8) {
+    for (int a = 0; a < k; ++a)
+      for (int c = a; c < k; ++c) {
+        double acc = 0.0;
+        for (int p = threadIdx.x; p < m; p += blockDim.x)
+          acc += 0.5 * (A[(size_t)p * k + a] * B[(size_t)p * k + c] + A[(size_t)p * k + c] * B[(size_t)p * k + a]);
+        acc = block_sum(acc, red);
+        if (threadIdx.x == 0) { S[a * k + c] = acc; S[c * k + a] = acc; }
+      }
+    __syncthreads();
+    return;
+  }
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
     const int a = e / k, c = e - a * k;
     double acc = 0.0;
-    for (int p = 0; p < m; ++p) acc += X[(size_t)p * k + a] * B[(size_t)p * k + c];
+    for (int p = 0; p < m; ++p) acc += A[(size_t)p * k + a] * B[(size_t)p * k + c];
     S[e] = acc;
   }
   __syncthreads();
@@ -236,6 +269,14 @@ __global__ void svqb_kernel(int n2, int m, int k, double* X, double* Xg, int g_i
     if (a < c) { const double v = 0.5 * (S[a * k + c] + S[c * k + a]); S[a * k + c] = v; S[c * k + a] = v; }
   }
   __syncthreads();
+}
+
+// One block: SVQB of X with S = X^T X (or X^T Xg for the G inner product);
+// X, Xg <- (.) V D^-1/2 on the kept columns.  Rows >= m are zero.
+__global__ void svqb_kernel(int n2, int m, int k, double* X, double* Xg, int g_inner, double* S, double* V,
+                            double* D, double* eigw, double* tmp) {
+  __shared__ double red[32];
+  block_gram(m, k, X, g_inner ? Xg : X, S, red);
   EigWork w = eig_work_view(eigw, k, k);
   cta_eig_sym(k, S, k, k, D, V, k, w, red);
   __syncthreads();
@@ -258,18 +299,11 @@ __global__ void svqb_kernel(int n2, int m, int k, double* X, double* Xg, int g_i
   }
 }
 
-// One block: with W (n2 x k) G-orthonormal and GW: M = GW^T GW, eig -> ritz (descending),
-// WU = W U, GWU = GW U.
-__global__ void rayleigh_ritz_kernel(int n2, int m, int k, const double* W, const double* GW, double* M,
-                                     double* U, double* ritz, double* eigw, double* WU, double* GWU, int* status) {
+// One block: with W G-orthonormal and GW: M = GW^T GW, eig -> ritz (descending), WU, GWU.
+__global__ void rayleigh_ritz_kernel(int n2, int m, int k, const double* W, const double* GW, double* M, double* U,
+                                     double* ritz, double* eigw, double* WU, double* GWU, int* status) {
   __shared__ double red[32];
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int a = e / k, c = e - a * k;
-    double acc = 0.0;
-    for (int p = 0; p < m; ++p) acc += GW[(size_t)p * k + a] * GW[(size_t)p * k + c];
-    M[e] = acc;
-  }
-  __syncthreads();
+  block_gram(m, k, GW, GW, M, red);
   EigWork w = eig_work_view(eigw, k, k);
   cta_eig_sym(k, M, k, k, ritz, U, k, w, red);
   __syncthreads();
@@ -286,27 +320,75 @@ __global__ void rayleigh_ritz_kernel(int n2, int m, int k, const double* W, cons
   if (threadIdx.x == 0 && !(ritz[0] == ritz[0])) set_status(status, AS_ENUMERIC);
 }
 
-__global__ void promote_pair_kernel(const float* X, int ldx, int col0, int n2, int m, int k, double* Y) {
+__global__ void promote_pair_kernel(const float* X, int n2, int col0, int m, int k, double* Y) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n2 * k; e += gridDim.x * blockDim.x) {
     const int p = e / k, c = e - p * k;
-    Y[e] = (p < m) ? (double)X[(size_t)p * ldx + col0 + c] : 0.0;
+    Y[e] = (p < m) ? (double)X[(size_t)(col0 + c) * n2 + p] : 0.0;
   }
 }
 
-}  // namespace
-
-as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m, const float* X, int ldx, int col0,
-                                  const SiBuffers& b, int* status) {
-  const int k = 2;
-  promote_pair_kernel<<<(n2 * k + 255) / 256, 256, 0, s>>>(X, ldx, col0, n2, m, k, b.Y); count_launches(1);
-  AS_CUDA_TRY(cudaMemsetAsync(b.GY, 0, (size_t)n2 * k * sizeof(double), s));
-  as_status st = gemm_strided<double, double, double>(s, m, k, m, G, n2, 1, b.Y, k, 1, b.GY, k, 1, 1.0, 0.0);
-  if (st != AS_OK) return st;
-  svqb_kernel<<<1, 512, 0, s>>>(n2, m, k, b.Y, b.GY, 1, b.S, b.V, b.ritz, b.eigw, b.tmp); count_launches(1);
-  rayleigh_ritz_kernel<<<1, 512, 0, s>>>(n2, m, k, b.Y, b.GY, b.S, b.V, b.ritz, b.eigw, b.WU, b.GWU, status); count_launches(1);
-  AS_CUDA_TRY(cudaGetLastError());
-  return AS_OK;
+// ---- dump (Algorithm 4 lines 14-16) -----------------------------------------
+// Partial sums over row chunks s: Zp[s][c][a] = sum_p C[p][c] WU[p][a] and
+// Yp[s][a][c] = sum_p GWU[p][a] C[p][c] for a in [a0, a0+na), one thread per column c.
+constexpr int kDumpChunks = 8;
+__global__ void dump_partial_kernel(const float* __restrict__ C, int ldc, int d, int r, const double* WU,
+                                    const double* GWU, int k, int xi, int a0, int na, double* Zp, double* Yp) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (c >= d) return;
+  const int chunk = (r + kDumpChunks - 1) / kDumpChunks;
+  const int pb = s * chunk, pe = min(r, pb + chunk);
+  double z[8], y[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) { z[a] = 0.0; y[a] = 0.0; }
+  for (int p = pb; p < pe; ++p) {
+    const double cv = C[(size_t)p * ldc + c];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if (a < na) {
+        z[a] += cv * WU[(size_t)p * k + a0 + a];
+        y[a] += cv * GWU[(size_t)p * k + a0 + a];
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+    if (a < na) {
+      Zp[((size_t)s * d + c) * xi + a0 + a] = z[a];
+      Yp[((size_t)s * xi + a0 + a) * d + c] = y[a];
+    }
 }
+
+__global__ void dump_reduce_kernel(const double* Zp, const double* Yp, int d, int xi, float* Z, float* Y) {
+  const int tot = d * xi;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+    double z = 0.0, y = 0.0;
+    for (int s = 0; s < kDumpChunks; ++s) { z += Zp[(size_t)s * tot + e]; y += Yp[(size_t)s * tot + e]; }
+    Z[e] = (float)z;   // Z: d x xi row-major (e = c*xi + a)
+    Y[e] = (float)y;   // Y: xi x d row-major (e = a*d + c)
+  }
+}
+
+// C[p][c] -= sum_a GWU[p][a] Z[c][a]   (the residual C' - C' Z Z^T)
+__global__ void residual_kernel(float* C, int ldc, int d, int r, const double* GWU, int k, int xi, const float* Z) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (c >= d || p >= r) return;
+  double acc = 0.0;
+  for (int a = 0; a < xi; ++a) acc += GWU[(size_t)p * k + a] * (double)Z[(size_t)c * xi + a];
+  C[(size_t)p * ldc + c] = (float)((double)C[(size_t)p * ldc + c] - acc);
+}
+
+// G[p][q] -= sum_a GWU[p][a] GWU[q][a]
+__global__ void gram_downdate_kernel(double* G, int n2, int r, const double* GWU, int k, int xi) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (q >= r || p >= r) return;
+  double acc = 0.0;
+  for (int a = 0; a < xi; ++a) acc += GWU[(size_t)p * k + a] * GWU[(size_t)q * k + a];
+  G[(size_t)p * n2 + q] -= acc;
+}
+
+}  // namespace
 
 as_status launch_gf_mirror(cudaStream_t s, const double* G, float* Gf, int n2, int m) {
   const size_t tot = (size_t)n2 * n2;
@@ -321,7 +403,8 @@ as_status launch_batch_gspace(cudaStream_t s, const float* Gf, int n2, int r0, i
   if (nb <= 0) return AS_OK;
   const int ncol = 3 * nb;
   const int mmax = r0 + nb;
-  batch_fill_kernel<<<dim3(nb, 2), 128, 0, s>>>(bb.X, n2, ncol, nb, r0, key, i0); count_launches(1);
+  const long long plane = (long long)n2 * ncol;
+  batch_fill_kernel<<<dim3(nb, 2), 128, 0, s>>>(bb.X, n2, nb, r0, key, i0); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   const int iters = std::max(k_pi, q);
   for (int it = 0; it <= iters; ++it) {
@@ -329,44 +412,56 @@ as_status launch_batch_gspace(cudaStream_t s, const float* Gf, int n2, int r0, i
     const bool si_on = it <= q;
     const int c0 = pi_on ? 0 : nb;
     const int c1 = si_on ? ncol : nb;
+    int S = std::min(skinny_splits(mmax, c1 - c0, mmax), bb.max_splits);
     if (prof) prof->begin(PK_BATCH_GEMM, s);
-    as_status st = gemm_strided<float, float, float>(s, mmax, c1 - c0, mmax, Gf, n2, 1, bb.X + c0, ncol, 1,
-                                                     bb.Y + c0, ncol, 1, 1.0, 0.0);
+    as_status st = launch_skinny_partial(s, mmax, c1 - c0, mmax, &S, Gf, n2, bb.X + (size_t)c0 * n2, n2,
+                                         bb.P + (size_t)c0 * n2, n2, plane);
     if (st != AS_OK) return st;
-    // algorithmic work of one product: 2 m^2 N flops; G (m^2 FP32) read once, X read, Y written
+    // algorithmic work of one product: 2 m^2 N flops; G (m^2 FP32) and X read, Y written
     if (prof)
       prof->end(PK_BATCH_GEMM, s, 2.0 * mmax * (double)mmax * (c1 - c0),
                 4.0 * ((double)mmax * mmax + 2.0 * (double)mmax * (c1 - c0)));
     if (prof) prof->begin(PK_BATCH_ORTH, s);
-    // PI: iterations 0..k_pi-1 normalise, iteration k_pi evaluates sigma^2.
-    // SI: iterations 0..q-1 orthonormalise, iteration q does Rayleigh-Ritz.
-    if (pi_on) {
-      batch_orth_kernel<<<dim3(nb, 1), 256, 0, s>>>(bb.Y, bb.X, n2, ncol, nb, r0, 1, it == k_pi ? 1 : 0,
-                                                    bb.sig2, bb.ritz); count_launches(1);
-      AS_CUDA_TRY(cudaGetLastError());
-    }
-    if (si_on) {
-      // the SI pair's kernel instance is selected by blockIdx.y = 1
-      batch_orth_kernel<<<dim3(nb, 2), 256, 0, s>>>(bb.Y, bb.X, n2, ncol, nb, r0, 0, it == q ? 1 : 0, bb.sig2,
-                                                    bb.ritz); count_launches(1);
-      AS_CUDA_TRY(cudaGetLastError());
-    }
-    if (prof) prof->end(PK_BATCH_ORTH, s, 0.0, 8.0 * (double)mmax * (c1 - c0));
+    // PI: iterations 0..k_pi-1 normalise, k_pi evaluates sigma^2;
+    // SI: iterations 0..q-1 orthonormalise, q does Rayleigh-Ritz.
+    const int kind0 = pi_on ? 0 : 1;
+    const int kinds = (pi_on ? 1 : 0) + (si_on ? 1 : 0);
+    batch_orth_kernel<<<dim3(nb, kinds), 256, 0, s>>>(bb.P, plane, S, bb.X, n2, nb, r0, kind0, it == k_pi ? 1 : 0,
+                                                      it == q ? 1 : 0, bb.sig2, bb.ritz); count_launches(1);
+    AS_CUDA_TRY(cudaGetLastError());
+    if (prof) prof->end(PK_BATCH_ORTH, s, 0.0, 4.0 * (double)mmax * (c1 - c0) * (S + 2));
   }
   return AS_OK;
 }
 
-as_status launch_power_iteration_f64(cudaStream_t s, const double* G, int n2, int m, int k_pi, Key key,
-                                     uint64_t i, double* x, double* y, int* zero, double* sig2) {
+static as_status gmul_thin(cudaStream_t s, const double* G, int n2, int m, int k, const double* X, double* Y) {
+  const int grid = (m + 7) / 8;
+  if (k <= 2) {
+    gmul_thin_kernel<2><<<grid, 256, 0, s>>>(G, n2, m, k, X, Y); count_launches(1);
+  } else {
+    gmul_thin_kernel<8><<<grid, 256, 0, s>>>(G, n2, m, k, X, Y); count_launches(1);
+  }
+  AS_CUDA_TRY(cudaGetLastError());
+  return AS_OK;
+}
+
+// products by G for the FP64 single-row path: thin kernel for k <= 8, else the tiled GEMM
+static as_status gmul64(cudaStream_t s, const double* G, int n2, int m, int k, const double* X, double* Y) {
+  if (k <= 8) return gmul_thin(s, G, n2, m, k, X, Y);
+  return gemm_strided<double, double, double>(s, m, k, m, G, n2, 1, X, k, 1, Y, k, 1, 1.0, 0.0);
+}
+
+as_status launch_power_iteration_f64(cudaStream_t s, const double* G, int n2, int m, int k_pi, Key key, uint64_t i,
+                                     double* x, double* y, int* zero, double* sig2) {
   AS_CUDA_TRY(cudaMemsetAsync(zero, 0, sizeof(int), s));
   fill_pi_start<<<(n2 / 4 + 255) / 256 + 1, 256, 0, s>>>(x, n2, m, key, i); count_launches(1);
   normalize_kernel<<<1, 512, 0, s>>>(x, x, m, zero); count_launches(1);
   for (int it = 0; it < k_pi; ++it) {
-    as_status st = gemm_strided<double, double, double>(s, m, 1, m, G, n2, 1, x, 1, 1, y, 1, 1, 1.0, 0.0);
+    as_status st = gmul64(s, G, n2, m, 1, x, y);
     if (st != AS_OK) return st;
     normalize_kernel<<<1, 512, 0, s>>>(y, x, m, zero); count_launches(1);
   }
-  as_status st = gemm_strided<double, double, double>(s, m, 1, m, G, n2, 1, x, 1, 1, y, 1, 1, 1.0, 0.0);
+  as_status st = gmul64(s, G, n2, m, 1, x, y);
   if (st != AS_OK) return st;
   dot_kernel<<<1, 512, 0, s>>>(x, y, m, zero, sig2); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
@@ -378,17 +473,50 @@ as_status launch_simul_iter_f64(cudaStream_t s, const double* G, int n2, int m, 
   fill_si_test<<<((n2 * k) / 4 + 255) / 256 + 1, 256, 0, s>>>(b.Y, n2, m, k, key, i, j); count_launches(1);
   AS_CUDA_TRY(cudaMemsetAsync(b.GY, 0, (size_t)n2 * k * sizeof(double), s));
   for (int t = 0; t < q; ++t) {
-    as_status st = gemm_strided<double, double, double>(s, m, k, m, G, n2, 1, b.Y, k, 1, b.GY, k, 1, 1.0, 0.0);
+    as_status st = gmul64(s, G, n2, m, k, b.Y, b.GY);
     if (st != AS_OK) return st;
     for (int pass = 0; pass < 2; ++pass) {
       svqb_kernel<<<1, 512, 0, s>>>(n2, m, k, b.GY, nullptr, 0, b.S, b.V, b.ritz, b.eigw, b.tmp); count_launches(1);
     }
     AS_CUDA_TRY(cudaMemcpyAsync(b.Y, b.GY, (size_t)n2 * k * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
-  as_status st = gemm_strided<double, double, double>(s, m, k, m, G, n2, 1, b.Y, k, 1, b.GY, k, 1, 1.0, 0.0);
+  as_status st = gmul64(s, G, n2, m, k, b.Y, b.GY);
   if (st != AS_OK) return st;
   svqb_kernel<<<1, 512, 0, s>>>(n2, m, k, b.Y, b.GY, 1, b.S, b.V, b.ritz, b.eigw, b.tmp); count_launches(1);
   rayleigh_ritz_kernel<<<1, 512, 0, s>>>(n2, m, k, b.Y, b.GY, b.S, b.V, b.ritz, b.eigw, b.WU, b.GWU, status); count_launches(1);
+  AS_CUDA_TRY(cudaGetLastError());
+  return AS_OK;
+}
+
+as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m, const float* X, int col0,
+                                  const SiBuffers& b, int* status) {
+  const int k = 2;
+  promote_pair_kernel<<<(n2 * k + 255) / 256, 256, 0, s>>>(X, n2, col0, m, k, b.Y); count_launches(1);
+  AS_CUDA_TRY(cudaMemsetAsync(b.GY, 0, (size_t)n2 * k * sizeof(double), s));
+  as_status st = gmul64(s, G, n2, m, k, b.Y, b.GY);
+  if (st != AS_OK) return st;
+  svqb_kernel<<<1, 512, 0, s>>>(n2, m, k, b.Y, b.GY, 1, b.S, b.V, b.ritz, b.eigw, b.tmp); count_launches(1);
+  rayleigh_ritz_kernel<<<1, 512, 0, s>>>(n2, m, k, b.Y, b.GY, b.S, b.V, b.ritz, b.eigw, b.WU, b.GWU, status); count_launches(1);
+  AS_CUDA_TRY(cudaGetLastError());
+  return AS_OK;
+}
+
+size_t dump_work_doubles(int d, int xi) { return (size_t)2 * kDumpChunks * d * xi; }
+
+as_status launch_dump(cudaStream_t s, float* C, int ldc, int d, int r, double* G, int n2, const double* WU,
+                      const double* GWU, int k, int xi, float* Z, float* Y, double* work) {
+  double* Zp = work;
+  double* Yp = work + (size_t)kDumpChunks * d * xi;
+  for (int a0 = 0; a0 < xi; a0 += 8) {
+    const int na = std::min(8, xi - a0);
+    dim3 grid((d + 127) / 128, kDumpChunks);
+    dump_partial_kernel<<<grid, 128, 0, s>>>(C, ldc, d, r, WU, GWU, k, xi, a0, na, Zp, Yp); count_launches(1);
+  }
+  dump_reduce_kernel<<<(d * xi + 255) / 256, 256, 0, s>>>(Zp, Yp, d, xi, Z, Y); count_launches(1);
+  if (r > 0) {
+    residual_kernel<<<dim3((d + 255) / 256, r), 256, 0, s>>>(C, ldc, d, r, GWU, k, xi, Z); count_launches(1);
+    gram_downdate_kernel<<<dim3((r + 255) / 256, r), 256, 0, s>>>(G, n2, r, GWU, k, xi); count_launches(1);
+  }
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }

@@ -16,6 +16,9 @@ enum ProfClass {
   PK_GRAM,            // Gram rows of a block
   PK_INGEST,          // row ingest
   PK_EVENT,           // FP64 single-row path of an event row and the dump
+  PK_EIG_TRI,         // eigensolver phase: tridiagonalisation
+  PK_EIG_SOLVE,       // eigensolver phase: bisection, inverse iteration, cluster MGS
+  PK_EIG_BACK,        // eigensolver phase: back-transformation
   PK_COUNT
 };
 struct Prof {
@@ -76,14 +79,31 @@ as_status launch_shrink_weights(cudaStream_t s, int n2, int ell, const double* l
 // contract as launch_eig.  Work size: eig_large_work_doubles(n, nev).
 size_t eig_large_work_doubles(int n, int nev);
 as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, double* evals, double* X, int ldx,
-                           double* work);
+                           double* work, Prof* prof = nullptr);
+
+// Split-K tall-skinny FP32 GEMM (skinny.cu): P[s](m, n) = sum_{k in split s}
+// A[m*lda + k] X[n*ldx + k]; *S in: requested splits, out: planes written.
+int skinny_splits(int M, int N, int K);
+as_status launch_skinny_partial(cudaStream_t s, int M, int N, int K, int* S, const float* A, long long lda,
+                                const float* X, long long ldx, float* P, long long ldp, long long plane);
+// G gains the Gram rows/columns of block rows [r, r+b) (FP64 combine of the splits).
+as_status launch_gram_rows_skinny(cudaStream_t s, const float* C, int ldc, int d, int r, int b, double* G, int n2,
+                                  float* P, size_t p_cap);
+
+// Dump (Algorithm 4 lines 14-16) for the first xi columns of W U / G W U
+// (row-major n2 x k): Z = C'^T (WU)_xi, Y = (GWU)_xi^T C', C -= (GWU)_xi Z^T,
+// G -= (GWU)_xi (GWU)_xi^T.  work: dump_work_doubles(d, xi).
+size_t dump_work_doubles(int d, int xi);
+as_status launch_dump(cudaStream_t s, float* C, int ldc, int d, int r, double* G, int n2, const double* WU,
+                      const double* GWU, int k, int xi, float* Z, float* Y, double* work);
 
 // FP32 mirror of the leading m x m block of G (zero elsewhere).
 as_status launch_gf_mirror(cudaStream_t s, const double* G, float* Gf, int n2, int m);
 
 struct BatchBuffers {
-  float* X;       // n2 x 3*bmax
-  float* Y;       // n2 x 3*bmax
+  float* X;       // n2 x 3*bmax, column-major
+  float* P;       // split-K partial planes (max_splits x n2 x 3*bmax)
+  int max_splits;
   double* sig2;   // bmax   power-iteration estimates
   double* ritz;   // 2*bmax the two Ritz values of the k = 2 step
 };
@@ -102,7 +122,7 @@ as_status launch_simul_iter_f64(cudaStream_t s, const double* G, int n2, int m, 
 
 // The Rayleigh-Ritz step of Algorithm 2 (k = 2) in FP64 on the iterated
 // basis that the batched pass left in columns col0, col0+1 of X (FP32).
-as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m, const float* X, int ldx, int col0,
+as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m, const float* X, int col0,
                                   const SiBuffers& b, int* status);
 
 // Query helpers.
