@@ -173,6 +173,15 @@ as_status sketch_profile(as_sketch* h, as_kernel_stat* out, int32_t cap, int32_t
 /* Clear the kernel-class timings. */
 as_status sketch_profile_reset(as_sketch* h);
 
+/* FP64 symmetric eigendecomposition on the current device: the core
+ * factorisation that the FD shrink (Algorithm 4 line 3, through the Gram
+ * matrix of the buffer) and the query (Algorithm 5 line 5) use.  A is n x n,
+ * row-major, host memory (only its values are read; it is not modified).
+ * Writes the nev largest eigenvalues in descending order to evals (host) and
+ * the matching unit eigenvectors as the columns of vecs (host, n x nev,
+ * row-major).  1 <= nev <= n.  Synchronous. */
+as_status as_symeig(int32_t n, const double* A, int32_t nev, double* evals, double* vecs);
+
 /* Free every resource of the sketch.  NULL is a no-op. */
 as_status sketch_destroy(as_sketch* h);
 

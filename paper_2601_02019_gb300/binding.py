@@ -18,7 +18,7 @@ AS_PROFILE = 0x2
 
 EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram", "sketch_get_buffer",
             "sketch_merge", "sketch_stats", "sketch_trace", "sketch_profile", "sketch_profile_reset",
-            "sketch_destroy", "as_status_str")
+            "sketch_destroy", "as_symeig", "as_status_str")
 
 
 class AsConfig(ct.Structure):
@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.sketch_profile.argtypes = [P, ct.POINTER(AsKernelStat), I32, ct.POINTER(I32)]
     L.sketch_profile_reset.argtypes = [P]
     L.sketch_destroy.argtypes = [P]
+    L.as_symeig.argtypes = [I32, P, I32, P, P]
     L.as_status_str.argtypes = [ct.c_int]
     L.as_status_str.restype = ct.c_char_p
     for name in EXPORTED:
@@ -186,6 +187,17 @@ class Sketch:
 
     def merge(self, other: "Sketch") -> None:
         _check(lib().sketch_merge(self._h, other._h), "sketch_merge")
+
+
+def symeig(A: np.ndarray, nev: int) -> tuple[np.ndarray, np.ndarray]:
+    """The library's FP64 symmetric eigensolver (descending nev pairs)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    lam = np.zeros(nev)
+    V = np.zeros((n, nev))
+    _check(lib().as_symeig(n, ct.c_void_p(A.ctypes.data), nev, ct.c_void_p(lam.ctypes.data),
+                           ct.c_void_p(V.ctypes.data)), "as_symeig")
+    return lam, V
 
 
 def replay_from_trace(events: list[dict]) -> dict:

@@ -26,6 +26,9 @@ struct TriWork {
   double* v;      // n (current Householder vector)
   double* p;      // n
   double* part;   // partial sums of v^T p, one per block of kernel 1
+  double* v2;     // n (second buffer of the fused steps)
+  double* p2;     // n
+  double* part2;  // partials of the second buffer
 };
 
 __device__ __forceinline__ void house_params(const double* row, int m, double* red, double& s_out,
@@ -75,31 +78,101 @@ __global__ void __launch_bounds__(256) tri_step1(double* A, int lda, int n, int 
   }
 }
 
-__global__ void __launch_bounds__(256) tri_step2(double* A, int lda, int n, int k, int nparts, TriWork w) {
-  __shared__ double cs;
-  const int m = n - k - 1;
-  if (threadIdx.x == 0) {
+// Fused step k (k >= 0): apply step k's update A22 -= v w^T + w v^T
+// (w = 2p - 2(v^T p)v) to rows and columns >= k+2, and in the same pass form
+// step k+1's Householder vector (every block recomputes it from the updated
+// row k+1) and p_{k+1} = A22' v_{k+1}.  Row and column k+1 of A are not
+// updated: only their diagonal (d[k+1]) and v_{k+1} are needed afterwards.
+// Double-buffered vectors: in = (v_k, p_k, parts_k), out = (v_{k+1}, p_{k+1}, parts_{k+1}),
+// indexed by absolute row (entries [k+1, n) of in, [k+2, n) of out).
+struct TriVec { double* v; double* p; double* part; int nparts; };
+
+__global__ void __launch_bounds__(256) tri_fused(double* A, int lda, int n, int k, TriVec in, TriVec out,
+                                                 double* d, double* e) {
+  extern __shared__ double sm[];
+  double* wk = sm;          // w_k[j], j in [k+1, n)   (offset k+1)
+  double* vk = sm + n;      // v_k[j]
+  double* vn_ = sm + 2 * n; // v_{k+1}[j], j in [k+2, n)
+  __shared__ double red[32];
+  __shared__ double c_s;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
     double c = 0.0;
-    for (int q = 0; q < nparts; ++q) c += w.part[q];
-    cs = c;
+    for (int q = 0; q < in.nparts; ++q) c += in.part[q];
+    c_s = c;
   }
   __syncthreads();
-  const double c = cs;
-  // keep v in row k of A for the back-transformation (row k is not read here)
-  if (blockIdx.x == 0 && blockIdx.y == 0)
-    for (int i = threadIdx.x; i < m; i += blockDim.x) A[(size_t)k * lda + (k + 1) + i] = w.v[i];
-  // 2D tiles of A22: blockIdx.y -> 8 rows, blockIdx.x -> 256 columns
-  const int i0 = blockIdx.y * 8;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m) return;
-  const double vj = w.v[j];
-  const double wj = 2.0 * w.p[j] - 2.0 * c * vj;
-  for (int ii = 0; ii < 8; ++ii) {
-    const int i = i0 + ii;
-    if (i >= m) break;
-    const double vi = w.v[i];
-    const double wi = 2.0 * w.p[i] - 2.0 * c * vi;
-    A[(size_t)(k + 1 + i) * lda + (k + 1 + j)] -= vi * wj + wi * vj;
+  const double c = c_s;
+  for (int j = k + 1 + tid; j < n; j += blockDim.x) {
+    const double v = in.v[j];
+    vk[j] = v;
+    wk[j] = 2.0 * in.p[j] - 2.0 * c * v;
+  }
+  __syncthreads();
+  const int k1 = k + 1;
+  const double vk1 = vk[k1], wk1 = wk[k1];
+  if (blockIdx.x == 0) {
+    // keep v_k in row k of A for the back-transformation; d[k+1] = updated diagonal
+    for (int j = k + 1 + tid; j < n; j += blockDim.x) A[(size_t)k * lda + j] = vk[j];
+    if (tid == 0) d[k1] = A[(size_t)k1 * lda + k1] - 2.0 * vk1 * wk1;
+  }
+  if (k1 + 1 >= n) return;
+  // updated row k+1 over columns [k+2, n): x_j = A[k+1][j] - v_{k+1} w_j - w_{k+1} v_j
+  const int m1 = n - k1 - 1;
+  double s = 0.0;
+  for (int j = k1 + 1 + tid; j < n; j += blockDim.x) {
+    const double x = A[(size_t)k1 * lda + j] - vk1 * wk[j] - wk1 * vk[j];
+    vn_[j] = x;
+    s += x * x;
+  }
+  s = block_sum(s, red);
+  if (m1 == 1) {
+    // last 2 x 2 block: no further reflector
+    if (blockIdx.x == 0 && tid == 0) {
+      const int j = n - 1;
+      e[k1] = vn_[j];
+      d[j] = A[(size_t)j * lda + j] - 2.0 * vk[j] * wk[j];
+      e[j] = 0.0;
+    }
+    return;
+  }
+  const double x0 = vn_[k1 + 1];
+  double alpha = 0.0, vnorm = 1.0;
+  if (s > 0.0) {
+    alpha = (x0 >= 0.0) ? -sqrt(s) : sqrt(s);
+    vnorm = sqrt(s - x0 * x0 + (x0 - alpha) * (x0 - alpha));
+  }
+  __syncthreads();
+  for (int j = k1 + 1 + tid; j < n; j += blockDim.x)
+    vn_[j] = (s == 0.0) ? 0.0 : ((j == k1 + 1) ? (vn_[j] - alpha) : vn_[j]) / vnorm;
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    for (int j = k1 + 1 + tid; j < n; j += blockDim.x) out.v[j] = vn_[j];
+    if (tid == 0) e[k1] = alpha;
+  }
+  // rows i in [k+2, n): one warp per row; update and dot with v_{k+1}
+  const int lane = tid & 31, wid = tid >> 5;
+  const int i = k1 + 1 + blockIdx.x * 8 + wid;
+  double contrib = 0.0;
+  if (i < n) {
+    double* ar = A + (size_t)i * lda;
+    const double vi = vk[i], wi = wk[i];
+    double acc = 0.0;
+    for (int j = k1 + 1 + lane; j < n; j += 32) {
+      const double a = ar[j] - vi * wk[j] - wi * vk[j];
+      ar[j] = a;
+      acc += a * vn_[j];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) { out.p[i] = acc; contrib = acc * vn_[i]; }
+  }
+  __shared__ double wpart[8];
+  if (lane == 0) wpart[wid] = contrib;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += wpart[q];
+    out.part[blockIdx.x] = t;
   }
 }
 
@@ -126,9 +199,13 @@ __global__ void tri_norm(int n, TriWork w, double* out2) {
   if (threadIdx.x == 0) { out2[0] = tn; out2[1] = 2.2250738585072014e-308 * fmax(1.0, em); }
 }
 
+// One warp per eigenvalue: multisection on Sturm counts (each round the 32
+// lanes evaluate 31 interior points, narrowing the bracket 32-fold) down to an
+// absolute width of 4 eps ||T||, then inverse iteration by lane 0.
 __global__ void bisect_invit(int n, int nev, TriWork w, const double* norms, double* evals, double* X, int ldx,
                              double* lu) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= nev) return;
   const double tnorm = norms[0], pivmin = norms[1];
   const double eps = 2.220446049250313e-16;
@@ -136,12 +213,21 @@ __global__ void bisect_invit(int n, int nev, TriWork w, const double* norms, dou
   const double* e = w.e;
   const int idx = n - 1 - j;
   double lo = -tnorm - 2 * eps * tnorm - pivmin, hi = tnorm + 2 * eps * tnorm + pivmin;
-  for (int it = 0; it < 256; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_count(n, d, e, mid, pivmin) > idx) hi = mid; else lo = mid;
-    if (hi - lo <= 2 * eps * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+  const double atol = 4 * eps * fmax(tnorm, pivmin);
+  for (int it = 0; it < 40; ++it) {
+    if (hi - lo <= atol + 2 * eps * fmax(fabs(lo), fabs(hi))) break;
+    // lane l evaluates x_l = lo + (l+1) (hi-lo)/32, l = 0..30; lane 31 idle
+    const double x = lo + (double)(lane + 1) * ((hi - lo) / 32.0);
+    const bool above = (lane < 31) ? (sturm_count(n, d, e, x, pivmin) > idx) : true;
+    const unsigned mask = __ballot_sync(0xffffffffu, above);
+    const int first = __ffs(mask) - 1;   // smallest lane whose point lies above the eigenvalue
+    const double nlo = (first == 0) ? lo : lo + (double)first * ((hi - lo) / 32.0);
+    const double nhi = (first >= 31) ? hi : lo + (double)(first + 1) * ((hi - lo) / 32.0);
+    if (!(nhi > nlo)) break;
+    lo = nlo;
+    hi = nhi;
   }
+  if (lane != 0) return;
   const double lam = 0.5 * (lo + hi);
   evals[j] = lam;
   // inverse iteration (same factorisation as eig.cuh)
@@ -277,7 +363,7 @@ __global__ void __launch_bounds__(256) back_transform(const double* A, int lda, 
 
 size_t eig_large_work_doubles(int n, int nev) {
   const int nparts = (n + kTriRowsPerBlock - 1) / kTriRowsPerBlock;
-  return 4 * (size_t)n + nparts + 2 + 5 * (size_t)n * nev + 64;
+  return 6 * (size_t)n + 2 * (size_t)nparts + 2 + 5 * (size_t)n * nev + 64;
 }
 
 as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, double* evals, double* X, int ldx,
@@ -290,24 +376,42 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
   w.p = w.v + n;
   w.part = w.p + n;
   const int nparts_max = (n + kTriRowsPerBlock - 1) / kTriRowsPerBlock;
-  double* norms = w.part + nparts_max;
+  w.v2 = w.part + nparts_max;
+  w.p2 = w.v2 + n;
+  w.part2 = w.p2 + n;
+  double* norms = w.part2 + nparts_max;
   double* lu = norms + 2;
   const size_t smem1 = (size_t)n * sizeof(double);
   if (smem1 > 48 * 1024)
     AS_CUDA_TRY(cudaFuncSetAttribute(tri_step1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
   if (prof) prof->begin(PK_EIG_TRI, s);
-  for (int k = 0; k + 2 < n; ++k) {
-    const int m = n - k - 1;
+  {
+    // step 0 forms v_0 and p_0 = A22 v_0 (written to absolute rows 1..n-1)
+    const int m = n - 1;
     const int nb = (m + kTriRowsPerBlock - 1) / kTriRowsPerBlock;
-    tri_step1<<<nb, 256, (size_t)m * sizeof(double), s>>>(A, lda, n, k, w); count_launches(1);
-    dim3 g2((m + 255) / 256, (m + 7) / 8);
-    tri_step2<<<g2, 256, 0, s>>>(A, lda, n, k, nb, w); count_launches(1);
+    tri_step1<<<nb, 256, (size_t)m * sizeof(double), s>>>(A, lda, n, 0, w); count_launches(1);
+    TriVec buf[2];
+    buf[0] = TriVec{w.v - 1, w.p - 1, w.part, nb};   // v_0, p_0 indexed by absolute row
+    buf[1] = TriVec{w.v2, w.p2, w.part2, 0};
+    const size_t smem = 3 * (size_t)n * sizeof(double);
+    if (smem > 48 * 1024)
+      AS_CUDA_TRY(cudaFuncSetAttribute(tri_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int k = 0; k + 2 < n; ++k) {
+      TriVec& in = buf[k & 1];
+      TriVec& out = buf[(k + 1) & 1];
+      const int rows = n - k - 2;           // rows k+2..n-1
+      const int grid = std::max(1, (rows + 7) / 8);
+      out.nparts = grid;
+      tri_fused<<<grid, 256, smem, s>>>(A, lda, n, k, in, out, w.d, w.e); count_launches(1);
+      // the buffers alternate; the base pointers of buffer 0 are re-pointed to
+      // absolute indexing after the first step
+      if (k == 0) buf[0] = TriVec{w.v, w.p, w.part, 0};
+    }
   }
-  tri_tail<<<1, 32, 0, s>>>(A, lda, n, w); count_launches(1);
   if (prof) prof->end(PK_EIG_TRI, s, 4.0 / 3.0 * (double)n * n * n, 8.0 * (double)n * n);
   if (prof) prof->begin(PK_EIG_SOLVE, s);
   tri_norm<<<1, 256, 0, s>>>(n, w, norms); count_launches(1);
-  bisect_invit<<<(nev + 31) / 32, 32, 0, s>>>(n, nev, w, norms, evals, X, ldx, lu); count_launches(1);
+  bisect_invit<<<(nev + 3) / 4, 128, 0, s>>>(n, nev, w, norms, evals, X, ldx, lu); count_launches(1);
   cluster_mgs<<<1, 512, 0, s>>>(n, nev, norms, evals, X, ldx); count_launches(1);
   if (prof) prof->end(PK_EIG_SOLVE, s, 0.0, 0.0);
   if (prof) prof->begin(PK_EIG_BACK, s);

@@ -774,6 +774,25 @@ as_status sketch_profile_reset(as_sketch* h) {
   return AS_OK;
 }
 
+as_status as_symeig(int32_t n, const double* A, int32_t nev, double* evals, double* vecs) {
+  if (n < 1 || nev < 1 || nev > n || !A || !evals || !vecs) return AS_EINVAL;
+  const bool big = n > 256;
+  double *dA = nullptr, *dl = nullptr, *dX = nullptr, *w = nullptr;
+  as_status st = dalloc(&dA, (size_t)n * n);
+  if (st == AS_OK) st = dalloc(&dl, (size_t)n);
+  if (st == AS_OK) st = dalloc(&dX, (size_t)n * nev);
+  if (st == AS_OK) st = dalloc(&w, big ? eig_large_work_doubles(n, nev) : eig_work_doubles(n, nev));
+  cudaError_t e = cudaSuccess;
+  if (st == AS_OK) e = cudaMemcpy(dA, A, (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice);
+  if (st == AS_OK && e == cudaSuccess)
+    st = big ? launch_eig_large(nullptr, n, dA, n, nev, dl, dX, nev, w) : launch_eig(nullptr, n, dA, n, nev, dl, dX, nev, w);
+  if (st == AS_OK && e == cudaSuccess) e = cudaMemcpy(evals, dl, (size_t)nev * sizeof(double), cudaMemcpyDeviceToHost);
+  if (st == AS_OK && e == cudaSuccess) e = cudaMemcpy(vecs, dX, (size_t)n * nev * sizeof(double), cudaMemcpyDeviceToHost);
+  if (st == AS_OK && e != cudaSuccess) st = as_from_cuda(e);
+  cudaFree(dA); cudaFree(dl); cudaFree(dX); cudaFree(w);
+  return st;
+}
+
 as_status sketch_destroy(as_sketch* h) {
   if (!h) return AS_OK;
   cudaStreamSynchronize(h->s);

@@ -165,6 +165,17 @@ __global__ void batch_orth_kernel(const float* __restrict__ P, long long plane, 
   }
 }
 
+// Y(p, c) = sum_s P[s](p, c) for columns [c0, c1), rows < mmax, written into plane 0.
+__global__ void plane_reduce_kernel(float* P, long long plane, int S, int n2, int c0, int c1, int mmax) {
+  const int c = c0 + blockIdx.y;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < mmax; p += gridDim.x * blockDim.x) {
+    const size_t off = (size_t)c * n2 + p;
+    double v = 0.0;
+    for (int s = 0; s < S; ++s) v += (double)P[(long long)s * plane + off];
+    P[off] = (float)v;
+  }
+}
+
 // Gf (FP32 mirror) = G (FP64) on the leading m x m block, zero elsewhere.
 __global__ void mirror_f32_kernel(const double* G, float* Gf, int n2, int m) {
   const size_t tot = (size_t)n2 * n2;
@@ -320,6 +331,51 @@ __global__ void rayleigh_ritz_kernel(int n2, int m, int k, const double* W, cons
   if (threadIdx.x == 0 && !(ritz[0] == ritz[0])) set_status(status, AS_ENUMERIC);
 }
 
+// Rayleigh-Ritz of Algorithm 2 for k = 2 in FP64, one block, closed-form 2 x 2
+// eigenproblems: S = Y^T (G Y) = V D V^T, W = Y V D^-1/2, GW = (G Y) V D^-1/2,
+// M = GW^T GW = U diag(ritz) U^T, WU, GWU.  Y is orthonormal (Euclidean).
+__global__ void rr2_kernel(int n2, int m, const double* Y, const double* GY, double* ritz, double* WU, double* GWU,
+                           int* status) {
+  __shared__ double red[32];
+  double s00 = 0, s01 = 0, s11 = 0;
+  for (int p = threadIdx.x; p < m; p += blockDim.x) {
+    const double a = Y[2 * p], b = Y[2 * p + 1], ga = GY[2 * p], gb = GY[2 * p + 1];
+    s00 += a * ga; s01 += 0.5 * (a * gb + b * ga); s11 += b * gb;
+  }
+  s00 = block_sum(s00, red); s01 = block_sum(s01, red); s11 = block_sum(s11, red);
+  double l0, l1, v00, v01, v10, v11;
+  eig2(s00, s01, s11, l0, l1, v00, v01, v10, v11);
+  const double a0 = (l0 > 0.0) ? 1.0 / sqrt(l0) : 0.0;
+  const double a1 = (l1 > 1e-13 * l0 && l1 > 0.0) ? 1.0 / sqrt(l1) : 0.0;
+  // G W columns
+  double m00 = 0, m01 = 0, m11 = 0;
+  for (int p = threadIdx.x; p < m; p += blockDim.x) {
+    const double ga = GY[2 * p], gb = GY[2 * p + 1];
+    const double g0 = (ga * v00 + gb * v10) * a0, g1 = (ga * v01 + gb * v11) * a1;
+    m00 += g0 * g0; m01 += g0 * g1; m11 += g1 * g1;
+  }
+  m00 = block_sum(m00, red); m01 = block_sum(m01, red); m11 = block_sum(m11, red);
+  double r0, r1, u00, u01, u10, u11;
+  eig2(m00, m01, m11, r0, r1, u00, u01, u10, u11);
+  if (threadIdx.x == 0) {
+    ritz[0] = r0;
+    ritz[1] = (a1 > 0.0) ? r1 : 0.0;
+    if (!(r0 == r0)) set_status(status, AS_ENUMERIC);
+  }
+  for (int p = threadIdx.x; p < n2; p += blockDim.x) {
+    double w0 = 0, w1 = 0, g0 = 0, g1 = 0;
+    if (p < m) {
+      const double a = Y[2 * p], b = Y[2 * p + 1], ga = GY[2 * p], gb = GY[2 * p + 1];
+      const double x0 = (a * v00 + b * v10) * a0, x1 = (a * v01 + b * v11) * a1;      // W
+      const double y0 = (ga * v00 + gb * v10) * a0, y1 = (ga * v01 + gb * v11) * a1;  // G W
+      w0 = x0 * u00 + x1 * u10; w1 = x0 * u01 + x1 * u11;
+      g0 = y0 * u00 + y1 * u10; g1 = y0 * u01 + y1 * u11;
+    }
+    WU[2 * p] = w0; WU[2 * p + 1] = w1;
+    GWU[2 * p] = g0; GWU[2 * p + 1] = g1;
+  }
+}
+
 __global__ void promote_pair_kernel(const float* X, int n2, int col0, int m, int k, double* Y) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n2 * k; e += gridDim.x * blockDim.x) {
     const int p = e / k, c = e - p * k;
@@ -422,11 +478,15 @@ as_status launch_batch_gspace(cudaStream_t s, const float* Gf, int n2, int r0, i
       prof->end(PK_BATCH_GEMM, s, 2.0 * mmax * (double)mmax * (c1 - c0),
                 4.0 * ((double)mmax * mmax + 2.0 * (double)mmax * (c1 - c0)));
     if (prof) prof->begin(PK_BATCH_ORTH, s);
+    if (S > 1) {
+      plane_reduce_kernel<<<dim3((mmax + 255) / 256, c1 - c0), 256, 0, s>>>(bb.P, plane, S, n2, c0, c1, mmax); count_launches(1);
+      S = 1;
+    }
     // PI: iterations 0..k_pi-1 normalise, k_pi evaluates sigma^2;
     // SI: iterations 0..q-1 orthonormalise, q does Rayleigh-Ritz.
     const int kind0 = pi_on ? 0 : 1;
     const int kinds = (pi_on ? 1 : 0) + (si_on ? 1 : 0);
-    batch_orth_kernel<<<dim3(nb, kinds), 256, 0, s>>>(bb.P, plane, S, bb.X, n2, nb, r0, kind0, it == k_pi ? 1 : 0,
+    batch_orth_kernel<<<dim3(nb, kinds), 512, 0, s>>>(bb.P, plane, S, bb.X, n2, nb, r0, kind0, it == k_pi ? 1 : 0,
                                                       it == q ? 1 : 0, bb.sig2, bb.ritz); count_launches(1);
     AS_CUDA_TRY(cudaGetLastError());
     if (prof) prof->end(PK_BATCH_ORTH, s, 0.0, 4.0 * (double)mmax * (c1 - c0) * (S + 2));
@@ -495,8 +555,7 @@ as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m
   AS_CUDA_TRY(cudaMemsetAsync(b.GY, 0, (size_t)n2 * k * sizeof(double), s));
   as_status st = gmul64(s, G, n2, m, k, b.Y, b.GY);
   if (st != AS_OK) return st;
-  svqb_kernel<<<1, 512, 0, s>>>(n2, m, k, b.Y, b.GY, 1, b.S, b.V, b.ritz, b.eigw, b.tmp); count_launches(1);
-  rayleigh_ritz_kernel<<<1, 512, 0, s>>>(n2, m, k, b.Y, b.GY, b.S, b.V, b.ritz, b.eigw, b.WU, b.GWU, status); count_launches(1);
+  rr2_kernel<<<1, 1024, 0, s>>>(n2, m, b.Y, b.GY, b.ritz, b.WU, b.GWU, status); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }
