@@ -149,7 +149,7 @@ static __device__ void cta_eig_sym(int n, double* A, int lda, int nev, double* e
       if (sturm_count(n, d, e, mid, pivmin) > idx) hi = mid; else lo = mid;
       if (hi - lo <= 2 * eps * fmax(fabs(lo), fabs(hi)) + pivmin) break;
     }
-    evals[j] = 0.5 * (lo + hi);
+    evals[j] = (tnorm == 0.0) ? 0.0 : 0.5 * (lo + hi);   // a zero matrix has exact zero eigenvalues
   }
   __syncthreads();
 

@@ -228,7 +228,7 @@ __global__ void bisect_invit(int n, int nev, TriWork w, const double* norms, dou
     hi = nhi;
   }
   if (lane != 0) return;
-  const double lam = 0.5 * (lo + hi);
+  const double lam = (tnorm == 0.0) ? 0.0 : 0.5 * (lo + hi);   // a zero matrix has exact zero eigenvalues
   evals[j] = lam;
   // inverse iteration (same factorisation as eig.cuh)
   const double tiny = eps * fmax(tnorm, pivmin);
