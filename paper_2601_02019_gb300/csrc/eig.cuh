@@ -154,7 +154,7 @@ static __device__ void cta_eig_sym(int n, double* A, int lda, int nev, double* e
   __syncthreads();
 
   // 3. inverse iteration, one thread per eigenvalue
-  const double tiny = eps * fmax(tnorm, pivmin);
+  const double tiny = fmax(eps * tnorm, 1e-300);
   for (int j = tid; j < nev; j += nt) {
     const double lam = evals[j];
     double* u0 = w.lu + (size_t)(0 * n) * nev + j;   // entry i at [i * nev]
@@ -184,6 +184,10 @@ static __device__ void cta_eig_sym(int n, double* A, int lda, int nev, double* e
     for (int i = 0; i < n; ++i) {
       const double p = u0[(size_t)i * nev];
       if (fabs(p) < tiny) u0[(size_t)i * nev] = (p < 0 ? -tiny : tiny);
+    }
+    if (tnorm == 0.0) {   // zero matrix: any orthonormal basis is an eigenbasis
+      for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] = (i == j) ? 1.0 : 0.0;
+      continue;
     }
     for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] = ii_start(i, j);
     for (int it = 0; it < 3; ++it) {

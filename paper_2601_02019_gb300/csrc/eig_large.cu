@@ -231,7 +231,7 @@ __global__ void bisect_invit(int n, int nev, TriWork w, const double* norms, dou
   const double lam = (tnorm == 0.0) ? 0.0 : 0.5 * (lo + hi);   // a zero matrix has exact zero eigenvalues
   evals[j] = lam;
   // inverse iteration (same factorisation as eig.cuh)
-  const double tiny = eps * fmax(tnorm, pivmin);
+  const double tiny = fmax(eps * tnorm, 1e-300);
   double* u0 = lu + (size_t)(0 * n) * nev + j;
   double* u1 = lu + (size_t)(1 * n) * nev + j;
   double* u2 = lu + (size_t)(2 * n) * nev + j;
@@ -259,6 +259,10 @@ __global__ void bisect_invit(int n, int nev, TriWork w, const double* norms, dou
   for (int i = 0; i < n; ++i) {
     const double p = u0[(size_t)i * nev];
     if (fabs(p) < tiny) u0[(size_t)i * nev] = (p < 0 ? -tiny : tiny);
+  }
+  if (tnorm == 0.0) {   // zero matrix: any orthonormal basis is an eigenbasis
+    for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] = (i == j) ? 1.0 : 0.0;
+    return;
   }
   for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] = ii_start(i, j);
   for (int it = 0; it < 3; ++it) {
