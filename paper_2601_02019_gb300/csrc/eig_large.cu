@@ -386,20 +386,20 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
   double* norms = w.part2 + nparts_max;
   double* lu = norms + 2;
   const size_t smem1 = (size_t)n * sizeof(double);
-  if (smem1 > 48 * 1024)
-    AS_CUDA_TRY(cudaFuncSetAttribute(tri_step1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+  AS_CUDA_TRY(cudaFuncSetAttribute(tri_step1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
   if (prof) prof->begin(PK_EIG_TRI, s);
   {
     // step 0 forms v_0 and p_0 = A22 v_0 (written to absolute rows 1..n-1)
     const int m = n - 1;
     const int nb = (m + kTriRowsPerBlock - 1) / kTriRowsPerBlock;
     tri_step1<<<nb, 256, (size_t)m * sizeof(double), s>>>(A, lda, n, 0, w); count_launches(1);
+    AS_CUDA_TRY(cudaGetLastError());
     TriVec buf[2];
     buf[0] = TriVec{w.v - 1, w.p - 1, w.part, nb};   // v_0, p_0 indexed by absolute row
     buf[1] = TriVec{w.v2, w.p2, w.part2, 0};
     const size_t smem = 3 * (size_t)n * sizeof(double);
-    if (smem > 48 * 1024)
-      AS_CUDA_TRY(cudaFuncSetAttribute(tri_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // opt in for the dynamic size itself: the static shared memory comes on top
+    AS_CUDA_TRY(cudaFuncSetAttribute(tri_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int k = 0; k + 2 < n; ++k) {
       TriVec& in = buf[k & 1];
       TriVec& out = buf[(k + 1) & 1];
@@ -407,6 +407,7 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
       const int grid = std::max(1, (rows + 7) / 8);
       out.nparts = grid;
       tri_fused<<<grid, 256, smem, s>>>(A, lda, n, k, in, out, w.d, w.e); count_launches(1);
+      AS_CUDA_TRY(cudaGetLastError());
       // the buffers alternate; the base pointers of buffer 0 are re-pointed to
       // absolute indexing after the first step
       if (k == 0) buf[0] = TriVec{w.v, w.p, w.part, 0};
@@ -420,8 +421,7 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
   if (prof) prof->end(PK_EIG_SOLVE, s, 0.0, 0.0);
   if (prof) prof->begin(PK_EIG_BACK, s);
   const size_t smem3 = (size_t)n * kSlab * sizeof(double);
-  if (smem3 > 48 * 1024)
-    AS_CUDA_TRY(cudaFuncSetAttribute(back_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+  AS_CUDA_TRY(cudaFuncSetAttribute(back_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
   back_transform<<<(nev + kSlab - 1) / kSlab, 256, smem3, s>>>(A, lda, n, nev, X, ldx); count_launches(1);
   if (prof) prof->end(PK_EIG_BACK, s, 2.0 * (double)n * n * nev, 8.0 * (double)n * n);
   AS_CUDA_TRY(cudaGetLastError());

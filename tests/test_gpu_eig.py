@@ -56,3 +56,16 @@ def test_zero_and_diagonal():
     D = np.diag(np.arange(1.0, 301.0))
     lam, V = p.binding.symeig(D, 10)
     assert np.allclose(lam, np.arange(300.0, 290.0, -1), rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("n,nev", [(2048, 1024), (1024, 512)])
+def test_fd_buffer_spectrum(n, nev):
+    """The shape of the FD shrink's Gram: a low-rank block of large eigenvalues
+    over a wide noise floor (2l = n buffer rows of a rank-200 power-law stream)."""
+    p = _p()
+    rng = np.random.default_rng(n)
+    d, r = 2 * n, 200
+    V, _ = np.linalg.qr(rng.standard_normal((d, r)))
+    C = (rng.standard_normal((n, r)) / np.arange(1, r + 1)) @ V.T + 0.01 * rng.standard_normal((n, d))
+    G = C @ C.T
+    _check(p, G, nev)
