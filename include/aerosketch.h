@@ -182,6 +182,16 @@ as_status sketch_profile_reset(as_sketch* h);
  * row-major).  1 <= nev <= n.  Synchronous. */
 as_status as_symeig(int32_t n, const double* A, int32_t nev, double* evals, double* vecs);
 
+/* The tensor-core product that the BF16 forms use for their d-side and
+ * G-space contractions: out = A B^T with A (M x K) and B (N x K) FP32,
+ * row-major, host memory, computed by the tcgen05 kernel with BF16 operands
+ * and FP32 accumulation: npass = 1 rounds the operands to BF16 once, npass =
+ * 3 uses the split-BF16 form (hi*hi + hi*lo + lo*hi).  `splits` > 1 splits K
+ * across thread blocks (partials summed in FP64 here).  out: M x N row-major
+ * host memory.  Synchronous.  AS_ENOTSUP if the driver lacks tensor-map support. */
+as_status as_tc_gemm(int32_t M, int32_t N, int32_t K, const float* A, const float* B, int32_t npass, int32_t splits,
+                     double* out);
+
 /* Free every resource of the sketch.  NULL is a no-op. */
 as_status sketch_destroy(as_sketch* h);
 

@@ -18,7 +18,7 @@ AS_PROFILE = 0x2
 
 EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram", "sketch_get_buffer",
             "sketch_merge", "sketch_stats", "sketch_trace", "sketch_profile", "sketch_profile_reset",
-            "sketch_destroy", "as_symeig", "as_status_str")
+            "sketch_destroy", "as_symeig", "as_tc_gemm", "as_status_str")
 
 
 class AsConfig(ct.Structure):
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.sketch_profile_reset.argtypes = [P]
     L.sketch_destroy.argtypes = [P]
     L.as_symeig.argtypes = [I32, P, I32, P, P]
+    L.as_tc_gemm.argtypes = [I32, I32, I32, P, P, I32, I32, P]
     L.as_status_str.argtypes = [ct.c_int]
     L.as_status_str.restype = ct.c_char_p
     for name in EXPORTED:
@@ -198,6 +199,16 @@ def symeig(A: np.ndarray, nev: int) -> tuple[np.ndarray, np.ndarray]:
     _check(lib().as_symeig(n, ct.c_void_p(A.ctypes.data), nev, ct.c_void_p(lam.ctypes.data),
                            ct.c_void_p(V.ctypes.data)), "as_symeig")
     return lam, V
+
+
+def tc_gemm(A: np.ndarray, B: np.ndarray, npass: int = 3, splits: int = 1) -> np.ndarray:
+    """A B^T on the tensor cores (tcgen05, BF16 operands, FP32 accumulation)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    out = np.zeros((A.shape[0], B.shape[0]))
+    _check(lib().as_tc_gemm(A.shape[0], B.shape[0], A.shape[1], ct.c_void_p(A.ctypes.data), ct.c_void_p(B.ctypes.data),
+                            npass, splits, ct.c_void_p(out.ctypes.data)), "as_tc_gemm")
+    return out
 
 
 def replay_from_trace(events: list[dict]) -> dict:

@@ -793,6 +793,63 @@ as_status as_symeig(int32_t n, const double* A, int32_t nev, double* evals, doub
   return st;
 }
 
+as_status as_tc_gemm(int32_t M, int32_t N, int32_t K, const float* A, const float* B, int32_t npass, int32_t splits,
+                     double* out) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !out || (npass != 1 && npass != 3) || splits < 1) return AS_EINVAL;
+  if (!umma_available()) return AS_ENOTSUP;
+  const int Kp = (K + 63) / 64 * 64;
+  const int bn = umma_bn_for(std::min(N, 256));
+  float *dA = nullptr, *dB = nullptr, *dO = nullptr;
+  __nv_bfloat16 *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+  int* err = nullptr;
+  as_status st = dalloc(&dA, (size_t)M * Kp);
+  if (st == AS_OK) st = dalloc(&dB, (size_t)N * Kp);
+  if (st == AS_OK) st = dalloc(&ah, (size_t)M * Kp);
+  if (st == AS_OK) st = dalloc(&al, (size_t)M * Kp);
+  if (st == AS_OK) st = dalloc(&bh, (size_t)N * Kp);
+  if (st == AS_OK) st = dalloc(&bl, (size_t)N * Kp);
+  if (st == AS_OK) st = dalloc(&dO, (size_t)splits * M * N);
+  if (st == AS_OK) st = dalloc(&err, 1);
+  cudaError_t e = cudaSuccess;
+  if (st == AS_OK) {
+    e = cudaMemset(dA, 0, (size_t)M * Kp * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(dB, 0, (size_t)N * Kp * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(dO, 0, (size_t)splits * M * N * sizeof(float));
+    if (e == cudaSuccess)
+      e = cudaMemcpy2D(dA, (size_t)Kp * 4, A, (size_t)K * 4, (size_t)K * 4, M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2D(dB, (size_t)Kp * 4, B, (size_t)K * 4, (size_t)K * 4, N, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = as_from_cuda(e);
+  }
+  if (st == AS_OK) st = launch_split_bf16(nullptr, dA, Kp, M, Kp, ah, al, Kp, false);
+  if (st == AS_OK) st = launch_split_bf16(nullptr, dB, Kp, N, Kp, bh, bl, Kp, false);
+  UmmaOperand oa{}, ob{};
+  if (st == AS_OK) st = umma_make_map(&oa.hi, ah, M, Kp, Kp, 128);
+  if (st == AS_OK) st = umma_make_map(&oa.lo, al, M, Kp, Kp, 128);
+  if (st == AS_OK) st = umma_make_map(&ob.hi, bh, N, Kp, Kp, bn);
+  if (st == AS_OK) st = umma_make_map(&ob.lo, bl, N, Kp, Kp, bn);
+  if (st == AS_OK)
+    st = launch_umma_gemm(nullptr, oa, ob, M, N, Kp, bn, npass, splits, 0, dO, N, 1, (long long)M * N, err);
+  std::vector<float> h((size_t)splits * M * N);
+  int herr = 0;
+  if (st == AS_OK) {
+    e = cudaMemcpy(h.data(), dO, h.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = as_from_cuda(e);
+    if (st == AS_OK && herr) st = (as_status)herr;
+  }
+  if (st == AS_OK) {
+    for (size_t t = 0; t < (size_t)M * N; ++t) {
+      double v = 0.0;
+      for (int z = 0; z < splits; ++z) v += h[(size_t)z * M * N + t];
+      out[t] = v;
+    }
+  }
+  cudaFree(dA); cudaFree(dB); cudaFree(dO); cudaFree(ah); cudaFree(al); cudaFree(bh); cudaFree(bl); cudaFree(err);
+  return st;
+}
+
 as_status sketch_destroy(as_sketch* h) {
   if (!h) return AS_OK;
   cudaStreamSynchronize(h->s);

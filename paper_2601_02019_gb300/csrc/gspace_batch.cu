@@ -58,12 +58,6 @@ __global__ void batch_fill_kernel(float* X, int n2, int nb, int r0, Key key, uin
   }
 }
 
-__device__ __forceinline__ double psum(const float* P, long long plane, int S, size_t off) {
-  double v = 0.0;
-  for (int s = 0; s < S; ++s) v += (double)P[(long long)s * plane + off];
-  return v;
-}
-
 __device__ __forceinline__ void eig2(double s00, double s01, double s11, double& l0, double& l1, double& v00,
                                      double& v01, double& v10, double& v11) {
   const double tr = 0.5 * (s00 + s11), df = 0.5 * (s00 - s11);
@@ -75,60 +69,62 @@ __device__ __forceinline__ void eig2(double s00, double s01, double s11, double&
   v00 = cos(th); v10 = sin(th); v01 = -v10; v11 = v00;
 }
 
-// After Y = G X (S partial planes in P): PI columns are normalised, SI pairs
-// SVQB-orthonormalised (twice); on the final pass sigma^2 = x^T (G x) and the
-// Ritz values of the pair are computed instead.  kind = kind0 + blockIdx.y.
-__global__ void batch_orth_kernel(const float* __restrict__ P, long long plane, int S, float* X, int n2, int nb,
-                                  int r0, int kind0, int final_pi, int final_si, double* sig2, double* ritz) {
+// After Y = G X (plane 0 of P after the split reduction): PI columns are
+// normalised, SI pairs SVQB-orthonormalised (twice); on the final pass
+// sigma^2 = x^T (G x) and the Ritz values of the pair are computed instead.
+// Per-element arithmetic is FP32 (FP64 throughput is a small fraction of FP32
+// on this part); only the per-thread partial sums are widened to FP64 for the
+// block reductions and the 2 x 2 eigenproblems.  kind = kind0 + blockIdx.y.
+__global__ void __launch_bounds__(512) batch_orth_kernel(const float* __restrict__ Y, float* X, int n2, int nb,
+                                                         int r0, int kind0, int final_pi, int final_si,
+                                                         double* sig2, double* ritz) {
   __shared__ double red[32];
   const int t = blockIdx.x, kind = kind0 + blockIdx.y;
   const int m = r0 + t + 1;
   if (kind == 0) {
     float* x = X + (size_t)t * n2;
-    const size_t off = (size_t)t * n2;
+    const float* y = Y + (size_t)t * n2;
+    float sf = 0.f;
     if (final_pi) {
-      double s = 0.0;
-      for (int p = threadIdx.x; p < m; p += blockDim.x) s += (double)x[p] * psum(P, plane, S, off + p);
-      s = block_sum(s, red);
+      for (int p = threadIdx.x; p < m; p += blockDim.x) sf = fmaf(x[p], y[p], sf);
+      const double s = block_sum((double)sf, red);
       if (threadIdx.x == 0) sig2[t] = s;
       return;
     }
-    double s = 0.0;
-    for (int p = threadIdx.x; p < m; p += blockDim.x) {
-      const double y = psum(P, plane, S, off + p);
-      s += y * y;
-    }
-    s = block_sum(s, red);
-    const double inv = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
-    for (int p = threadIdx.x; p < n2; p += blockDim.x) x[p] = (p < m) ? (float)(psum(P, plane, S, off + p) * inv) : 0.f;
+    for (int p = threadIdx.x; p < m; p += blockDim.x) sf = fmaf(y[p], y[p], sf);
+    const double s = block_sum((double)sf, red);
+    const float inv = (s > 0.0) ? (float)(1.0 / sqrt(s)) : 0.f;
+    for (int p = threadIdx.x; p < n2; p += blockDim.x) x[p] = (p < m) ? y[p] * inv : 0.f;
     return;
   }
   const size_t o0 = (size_t)(nb + 2 * t) * n2, o1 = o0 + n2;
   float* x0 = X + o0;
   float* x1 = X + o1;
+  const float* y0 = Y + o0;
+  const float* y1 = Y + o1;
   if (final_si) {
     // S = X^T (G X) (X orthonormal); SVQB -> W = X V D^-1/2, GW = Y V D^-1/2;
-    // Ritz values = eig((GW)^T (GW))
-    double s00 = 0, s01 = 0, s11 = 0;
+    // Ritz values = eig((GW)^T (GW)) = eig(D^-1/2 V^T (Y^T Y) V D^-1/2)
+    float f00 = 0.f, f01 = 0.f, f11 = 0.f, g00 = 0.f, g01 = 0.f, g11 = 0.f;
     for (int p = threadIdx.x; p < m; p += blockDim.x) {
-      const double a = x0[p], b = x1[p];
-      const double y0 = psum(P, plane, S, o0 + p), y1 = psum(P, plane, S, o1 + p);
-      s00 += a * y0; s01 += 0.5 * (a * y1 + b * y0); s11 += b * y1;
+      const float a = x0[p], b = x1[p], ya = y0[p], yb = y1[p];
+      f00 = fmaf(a, ya, f00); f01 = fmaf(0.5f, fmaf(a, yb, b * ya), f01); f11 = fmaf(b, yb, f11);
+      g00 = fmaf(ya, ya, g00); g01 = fmaf(ya, yb, g01); g11 = fmaf(yb, yb, g11);
     }
-    s00 = block_sum(s00, red); s01 = block_sum(s01, red); s11 = block_sum(s11, red);
-    double l0, l1, v00, v01, v10, v11;
-    eig2(s00, s01, s11, l0, l1, v00, v01, v10, v11);
-    const double tol = 1e-6 * fmax(l0, 0.0);
-    const double a0 = (l0 > tol && l0 > 0) ? 1.0 / sqrt(l0) : 0.0;
-    const double a1 = (l1 > tol && l1 > 0) ? 1.0 / sqrt(l1) : 0.0;
-    double m00 = 0, m01 = 0, m11 = 0;
-    for (int p = threadIdx.x; p < m; p += blockDim.x) {
-      const double y0 = psum(P, plane, S, o0 + p), y1 = psum(P, plane, S, o1 + p);
-      const double g0 = (y0 * v00 + y1 * v10) * a0, g1 = (y0 * v01 + y1 * v11) * a1;
-      m00 += g0 * g0; m01 += g0 * g1; m11 += g1 * g1;
-    }
-    m00 = block_sum(m00, red); m01 = block_sum(m01, red); m11 = block_sum(m11, red);
+    const double s00 = block_sum((double)f00, red), s01 = block_sum((double)f01, red), s11 = block_sum((double)f11, red);
+    const double h00 = block_sum((double)g00, red), h01 = block_sum((double)g01, red), h11 = block_sum((double)g11, red);
     if (threadIdx.x == 0) {
+      double l0, l1, v00, v01, v10, v11;
+      eig2(s00, s01, s11, l0, l1, v00, v01, v10, v11);
+      const double tol = 1e-6 * fmax(l0, 0.0);
+      const double a0 = (l0 > tol && l0 > 0) ? 1.0 / sqrt(l0) : 0.0;
+      const double a1 = (l1 > tol && l1 > 0) ? 1.0 / sqrt(l1) : 0.0;
+      // M = diag(a) V^T H V diag(a), H = Y^T Y
+      const double hv00 = h00 * v00 + h01 * v10, hv10 = h01 * v00 + h11 * v10;
+      const double hv01 = h00 * v01 + h01 * v11, hv11 = h01 * v01 + h11 * v11;
+      const double m00 = a0 * a0 * (v00 * hv00 + v10 * hv10);
+      const double m01 = a0 * a1 * (v00 * hv01 + v10 * hv11);
+      const double m11 = a1 * a1 * (v01 * hv01 + v11 * hv11);
       const double tr = 0.5 * (m00 + m11), df = 0.5 * (m00 - m11);
       const double rad = sqrt(df * df + m01 * m01);
       ritz[2 * t] = (a0 > 0) ? tr + rad : 0.0;
@@ -136,27 +132,28 @@ __global__ void batch_orth_kernel(const float* __restrict__ P, long long plane, 
     }
     return;
   }
-  // Euclidean SVQB of the pair: pass 0 reads Y (partials), pass 1 re-orthonormalises X
+  // Euclidean SVQB of the pair: pass 0 reads Y, pass 1 re-orthonormalises X
   for (int pass = 0; pass < 2; ++pass) {
-    double s00 = 0, s01 = 0, s11 = 0;
+    const float* s0 = pass ? x0 : y0;
+    const float* s1 = pass ? x1 : y1;
+    float f00 = 0.f, f01 = 0.f, f11 = 0.f;
     for (int p = threadIdx.x; p < m; p += blockDim.x) {
-      const double a = pass ? (double)x0[p] : psum(P, plane, S, o0 + p);
-      const double b = pass ? (double)x1[p] : psum(P, plane, S, o1 + p);
-      s00 += a * a; s01 += a * b; s11 += b * b;
+      const float a = s0[p], b = s1[p];
+      f00 = fmaf(a, a, f00); f01 = fmaf(a, b, f01); f11 = fmaf(b, b, f11);
     }
-    s00 = block_sum(s00, red); s01 = block_sum(s01, red); s11 = block_sum(s11, red);
+    const double s00 = block_sum((double)f00, red), s01 = block_sum((double)f01, red), s11 = block_sum((double)f11, red);
     double l0, l1, v00, v01, v10, v11;
     eig2(s00, s01, s11, l0, l1, v00, v01, v10, v11);
     const double tol = 1e-13 * fmax(l0, 0.0);
-    const double a0 = (l0 > tol && l0 > 0) ? 1.0 / sqrt(l0) : 0.0;
-    const double a1 = (l1 > tol && l1 > 0) ? 1.0 / sqrt(l1) : 0.0;
+    const float a0 = (l0 > tol && l0 > 0) ? (float)(1.0 / sqrt(l0)) : 0.f;
+    const float a1 = (l1 > tol && l1 > 0) ? (float)(1.0 / sqrt(l1)) : 0.f;
+    const float c00 = (float)v00 * a0, c10 = (float)v10 * a0, c01 = (float)v01 * a1, c11 = (float)v11 * a1;
     for (int p = threadIdx.x; p < n2; p += blockDim.x) {
       float o0v = 0.f, o1v = 0.f;
       if (p < m) {
-        const double a = pass ? (double)x0[p] : psum(P, plane, S, o0 + p);
-        const double b = pass ? (double)x1[p] : psum(P, plane, S, o1 + p);
-        o0v = (float)((a * v00 + b * v10) * a0);
-        o1v = (float)((a * v01 + b * v11) * a1);
+        const float a = s0[p], b = s1[p];
+        o0v = fmaf(a, c00, b * c10);
+        o1v = fmaf(a, c01, b * c11);
       }
       x0[p] = o0v;
       x1[p] = o1v;
@@ -170,9 +167,9 @@ __global__ void plane_reduce_kernel(float* P, long long plane, int S, int n2, in
   const int c = c0 + blockIdx.y;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < mmax; p += gridDim.x * blockDim.x) {
     const size_t off = (size_t)c * n2 + p;
-    double v = 0.0;
-    for (int s = 0; s < S; ++s) v += (double)P[(long long)s * plane + off];
-    P[off] = (float)v;
+    float v = 0.f;
+    for (int s = 0; s < S; ++s) v += P[(long long)s * plane + off];
+    P[off] = v;
   }
 }
 
@@ -480,13 +477,12 @@ as_status launch_batch_gspace(cudaStream_t s, const float* Gf, int n2, int r0, i
     if (prof) prof->begin(PK_BATCH_ORTH, s);
     if (S > 1) {
       plane_reduce_kernel<<<dim3((mmax + 255) / 256, c1 - c0), 256, 0, s>>>(bb.P, plane, S, n2, c0, c1, mmax); count_launches(1);
-      S = 1;
     }
     // PI: iterations 0..k_pi-1 normalise, k_pi evaluates sigma^2;
     // SI: iterations 0..q-1 orthonormalise, q does Rayleigh-Ritz.
     const int kind0 = pi_on ? 0 : 1;
     const int kinds = (pi_on ? 1 : 0) + (si_on ? 1 : 0);
-    batch_orth_kernel<<<dim3(nb, kinds), 512, 0, s>>>(bb.P, plane, S, bb.X, n2, nb, r0, kind0, it == k_pi ? 1 : 0,
+    batch_orth_kernel<<<dim3(nb, kinds), 512, 0, s>>>(bb.P, bb.X, n2, nb, r0, kind0, it == k_pi ? 1 : 0,
                                                       it == q ? 1 : 0, bb.sig2, bb.ritz); count_launches(1);
     AS_CUDA_TRY(cudaGetLastError());
     if (prof) prof->end(PK_BATCH_ORTH, s, 0.0, 4.0 * (double)mmax * (c1 - c0) * (S + 2));

@@ -1,6 +1,9 @@
 // Launchers of the AeroSketch kernels (internal C++ interface of the library).
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include <type_traits>
 
 #include "common.cuh"
@@ -124,6 +127,23 @@ as_status launch_simul_iter_f64(cudaStream_t s, const double* G, int n2, int m, 
 // basis that the batched pass left in columns col0, col0+1 of X (FP32).
 as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m, const float* X, int col0,
                                   const SiBuffers& b, int* status);
+
+// tcgen05 GEMM (umma.cu).  An operand is one or two TMA tensor maps over BF16
+// data (hi, and lo for the split-BF16 form), K innermost, box 64 x box_rows.
+struct UmmaOperand {
+  CUtensorMap hi;
+  CUtensorMap lo;
+};
+bool umma_available();
+as_status umma_make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int kdim, long long ld, int box_rows);
+int umma_bn_for(int N);
+// out[z*plane + m*som + n*son] = sum_{k in split z} A(m,k) B(b_row0 + n, k); npass 1 (BF16) or 3 (split-BF16).
+as_status launch_umma_gemm(cudaStream_t s, const UmmaOperand& A, const UmmaOperand& B, int M, int N, int K, int bn,
+                           int npass, int splits, int b_row0, float* out, long long som, long long son, long long plane,
+                           int* err);
+// (hi, lo) BF16 split of an FP32 matrix, optionally transposed (dst(c, r) = src(r, c)).
+as_status launch_split_bf16(cudaStream_t s, const float* src, long long lds, int rows, int cols, __nv_bfloat16* hi,
+                            __nv_bfloat16* lo, long long ldd, bool transpose);
 
 // Query helpers.
 as_status launch_shrink_rows(cudaStream_t s, int d, int ell, const double* lam, const double* V, int ldv,

@@ -1,0 +1,352 @@
+// tcgen05 tensor-core GEMM for sm_103a: TMA-fed, TMEM-accumulated, BF16 in,
+// FP32 out, optional split-BF16 (three products) for near-FP32 accuracy.
+//
+//   D(m, n) = sum_{k in split z} A(m, k) B(n, k)         (both K-major, "TN")
+//   out[z*plane + m*som + n*son] = D(m, n)
+//
+// A and B are read through 2-D TMA tensor maps (BF16, K innermost, 128-byte
+// swizzle, box 64 x rows).  With npass = 3 the maps come in (hi, lo) pairs,
+// x = hi + lo with hi = bf16(x), lo = bf16(x - hi), and the block accumulates
+// A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo*lo term is below FP32 resolution).
+//
+// One CTA computes a 128 x BN tile for one K split with 4 warps:
+//   warp 0 (one lane)  TMA producer over a STAGES-deep shared-memory ring,
+//   warp 1 (one lane)  issues tcgen05.mma (cta_group::1, kind::f16, M = 128),
+//   warp 2             allocates / frees the TMEM accumulator (BN columns),
+//   warps 0-3          epilogue: tcgen05.ld 32x32b, one accumulator row per thread.
+// Every mbarrier wait is bounded: on a timeout the kernel records an error in
+// *err and falls through, so a fault in the pipeline cannot hang the GPU.
+#include <cuda.h>
+
+#include "kernels.cuh"
+
+namespace as {
+
+namespace {
+
+constexpr int UM = 128;     // tile rows (UMMA M)
+constexpr int UK = 64;      // K elements per stage (128 bytes of BF16)
+constexpr int STAGES = 4;
+constexpr uint32_t kSpinLimit = 1u << 22;   // bounded polling: a stuck pipeline reports an error
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the phase with the given parity; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major operand, 128-byte
+// swizzle, 8-row groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+  d |= (uint64_t)1 << 46;                          // version
+  d |= (uint64_t)2 << 61;                          // layout: 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = bn.
+__host__ __device__ constexpr uint32_t idesc_bf16(int bn) {
+  return (1u << 4)                     // D format F32
+         | (1u << 7)                   // A format BF16
+         | (1u << 10)                  // B format BF16
+         | ((uint32_t)(bn >> 3) << 17) // N >> 3
+         | ((uint32_t)(UM >> 4) << 24);// M >> 4
+}
+
+template <int BN, int NPASS>
+__global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
+                                                           const __grid_constant__ CUtensorMap mapA_lo,
+                                                           const __grid_constant__ CUtensorMap mapB_hi,
+                                                           const __grid_constant__ CUtensorMap mapB_lo, int M,
+                                                           int N, int K, int klen, int b_row0, float* out,
+                                                           long long som, long long son, long long plane, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-byte alignment for the swizzled tiles
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr uint32_t A_BYTES = UM * UK * 2;
+  constexpr uint32_t B_BYTES = BN * UK * 2;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int fail_s;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * UM, n0 = blockIdx.y * BN, z = blockIdx.z;
+  const int kb = z * klen, ke = min(K, kb + klen);
+  const int ktiles = (ke > kb) ? (ke - kb + UK - 1) / UK : 0;
+  const int niter = ktiles * NPASS;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    mbar_init(&done_bar, 1);
+    fail_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    // TMEM accumulator: BN columns (a power of two >= 32)
+    constexpr uint32_t ncols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0 && lane == 0 && niter > 0) {
+    // TMA producer
+    for (int it = 0; it < niter; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&empty_bar[s], ph ^ 1u)) { atomicExch(&fail_s, 1); break; }
+      const int kt = it / NPASS, pass = it % NPASS;
+      const int kx = kb + kt * UK;
+      const CUtensorMap* ma = (pass == 2) ? &mapA_lo : &mapA_hi;
+      const CUtensorMap* mb = (pass == 1) ? &mapB_lo : &mapB_hi;
+      mbar_expect_tx(&full_bar[s], A_BYTES + B_BYTES);
+      tma_load_2d(sA + s * A_BYTES, ma, &full_bar[s], kx, m0);
+      tma_load_2d(sB + s * B_BYTES, mb, &full_bar[s], kx, b_row0 + n0);
+    }
+  } else if (warp == 1 && lane == 0 && niter > 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BN);
+    bool ok = true;
+    for (int it = 0; it < niter; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&full_bar[s], ph)) { atomicExch(&fail_s, 1); ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < UK / 16; ++kk) {
+        const uint64_t da = smem_desc(a0 + kk * 32), db = smem_desc(b0 + kk * 32);
+        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+      }
+      // the stage is free once these MMAs have read it
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&empty_bar[s]))
+                   : "memory");
+    }
+    (void)ok;
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(&done_bar))
+                 : "memory");
+  }
+  __syncwarp();
+  // epilogue: thread (warp w, lane l) owns accumulator row 32w + l
+  const int row = warp * 32 + lane;
+  const int gm = m0 + row;
+  bool have = niter > 0;
+  if (have && !mbar_wait(&done_bar, 0)) { atomicExch(&fail_s, 1); have = false; }
+  have = __all_sync(0xffffffffu, have);   // tcgen05.ld below is warp-collective
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  float* o = out + (long long)z * plane;
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 16) {
+    uint32_t r[16];
+    if (have) {
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) r[j] = 0u;
+    }
+    if (gm < M) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int gn = n0 + c0 + j;
+        if (gn < N) o[(long long)gm * som + (long long)gn * son] = __uint_as_float(r[j]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 2) {
+    constexpr uint32_t ncols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+  }
+  if (threadIdx.x == 0 && fail_s && err) atomicExch(err, AS_ETIMEOUT);
+}
+
+}  // namespace
+
+namespace {
+
+// x -> (hi, lo) BF16 pair: hi = bf16(x), lo = bf16(x - hi).  Source row-major
+// (rows x cols, lds); destinations row-major with ldd.
+__global__ void split_bf16_kernel(const float* __restrict__ src, long long lds, int rows, int cols,
+                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long ldd) {
+  const long long tot = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / cols), c = (int)(e - (long long)r * cols);
+    const float x = src[(long long)r * lds + c];
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[(long long)r * ldd + c] = h;
+    if (lo) lo[(long long)r * ldd + c] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
+// Transposing split: dst(c, r) = src(r, c); 32 x 32 tiles through shared memory.
+__global__ void split_bf16_t_kernel(const float* __restrict__ src, long long lds, int rows, int cols,
+                                    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long ldd) {
+  __shared__ float tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < rows && c < cols) ? src[(long long)r * lds + c] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) {
+      const float x = tile[threadIdx.x][i];
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      hi[(long long)c * ldd + r] = h;
+      if (lo) lo[(long long)c * ldd + r] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+  }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeFn)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+template <int BN, int NPASS>
+as_status launch_umma_t(cudaStream_t s, const UmmaOperand& A, const UmmaOperand& B, int M, int N, int K, int splits,
+                        int b_row0, float* out, long long som, long long son, long long plane, int* err) {
+  const int ktiles = (K + UK - 1) / UK;
+  int S = std::max(1, std::min(splits, ktiles));
+  int klen = ((ktiles + S - 1) / S) * UK;
+  S = (K + klen - 1) / klen;
+  dim3 grid((M + UM - 1) / UM, (N + BN - 1) / BN, S);
+  const size_t smem = (size_t)STAGES * (UM * UK * 2 + BN * UK * 2) + 1024;
+  AS_CUDA_TRY(cudaFuncSetAttribute(umma_gemm_kernel<BN, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  umma_gemm_kernel<BN, NPASS><<<grid, 128, smem, s>>>(A.hi, A.lo, B.hi, B.lo, M, N, K, klen, b_row0, out, som, son,
+                                                      plane, err); count_launches(1);
+  AS_CUDA_TRY(cudaGetLastError());
+  return AS_OK;
+}
+
+}  // namespace
+
+bool umma_available() { return encode_fn() != nullptr; }
+
+as_status umma_make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int kdim, long long ld, int box_rows) {
+  EncodeFn fn = encode_fn();
+  if (!fn) return AS_ENOTSUP;
+  if (((uintptr_t)base & 15) || ((ld * 2) & 15) || (kdim % 8)) return AS_EINVAL;
+  const cuuint64_t dims[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)UK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? AS_OK : AS_EINVAL;
+}
+
+as_status launch_umma_gemm(cudaStream_t s, const UmmaOperand& A, const UmmaOperand& B, int M, int N, int K, int bn,
+                           int npass, int splits, int b_row0, float* out, long long som, long long son, long long plane,
+                           int* err) {
+  if (M <= 0 || N <= 0) return AS_OK;
+  if (npass != 1 && npass != 3) return AS_EINVAL;
+#define AS_UMMA_CASE(BNV)                                                                                          \
+  if (bn == BNV)                                                                                                   \
+    return npass == 3 ? launch_umma_t<BNV, 3>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err)         \
+                      : launch_umma_t<BNV, 1>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err);
+  AS_UMMA_CASE(32)
+  AS_UMMA_CASE(64)
+  AS_UMMA_CASE(128)
+  AS_UMMA_CASE(192)
+  AS_UMMA_CASE(256)
+#undef AS_UMMA_CASE
+  return AS_EINVAL;
+}
+
+int umma_bn_for(int N) {
+  if (N <= 32) return 32;
+  if (N <= 64) return 64;
+  if (N <= 128) return 128;
+  if (N <= 192) return 192;
+  return 256;
+}
+
+as_status launch_split_bf16(cudaStream_t s, const float* src, long long lds, int rows, int cols, __nv_bfloat16* hi,
+                            __nv_bfloat16* lo, long long ldd, bool transpose) {
+  if (rows <= 0 || cols <= 0) return AS_OK;
+  if (transpose) {
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    split_bf16_t_kernel<<<grid, dim3(32, 8), 0, s>>>(src, lds, rows, cols, hi, lo, ldd); count_launches(1);
+  } else {
+    const long long tot = (long long)rows * cols;
+    const int blocks = (int)std::min<long long>((tot + 255) / 256, 8192);
+    split_bf16_kernel<<<blocks, 256, 0, s>>>(src, lds, rows, cols, hi, lo, ldd); count_launches(1);
+  }
+  AS_CUDA_TRY(cudaGetLastError());
+  return AS_OK;
+}
+
+}  // namespace as
