@@ -57,11 +57,20 @@ typedef enum {
   AS_COORDINATOR = 4   /* Algorithm 10, coordinator side: not implemented */
 } as_mode;
 
-/* Arithmetic of the d-side products (Gram cross terms, rebuild, snapshot).
- * The G-space iterations and the small core factorisations use FP64 in both. */
+/* Arithmetic of the products.  In every form the orthonormalisations, the
+ * Rayleigh-Ritz steps and the eigendecompositions run in FP64, and every
+ * branch of Algorithm 4 is decided on FP64 values (values inside a 1e-4
+ * relative band of a threshold are recomputed in FP64).
+ *   AS_FP32_PLAIN  SIMT FP32 products, FP32 partial sums combined in FP64.
+ *   AS_BF16        d-side products (Gram rows, FD rebuild) on the tcgen05
+ *                  tensor cores with BF16 operands and FP32 accumulation;
+ *                  batched G-space products in split-BF16 on tcgen05.
+ *   AS_BF16X3      as AS_BF16 with the d-side products also in split-BF16
+ *                  (hi*hi + hi*lo + lo*hi, near-FP32 accuracy). */
 typedef enum {
-  AS_FP32_PLAIN = 0,   /* FP32 operands, FP64-combined accumulation */
-  AS_BF16 = 1          /* reserved: BF16 tensor-core operands (AS_ENOTSUP for now) */
+  AS_FP32_PLAIN = 0,
+  AS_BF16 = 1,
+  AS_BF16X3 = 2
 } as_precision;
 
 /* Flags. */

@@ -142,6 +142,15 @@ struct as_sketch {
   size_t dev_bytes = 0;
   std::mutex mu;
   EventProf* prof = nullptr;  // AS_PROFILE
+  // tensor-core forms (AS_BF16, AS_BF16X3)
+  bool tc = false;
+  int dpass = 1;            // passes of the d-side products (1 BF16, 3 split-BF16)
+  int n2p = 0;              // n2 rounded up to 64
+  int rows_pad = 0;         // row counts of the BF16 buffers, >= 256
+  __nv_bfloat16 *Chi = nullptr, *Clo = nullptr, *Cthi = nullptr, *Ctlo = nullptr, *Gfh = nullptr, *Gfl = nullptr,
+                *Xh = nullptr, *Xl = nullptr, *Wh = nullptr, *Wl = nullptr;
+  UmmaOperand mCA{}, mCB64{}, mCB256{}, mGA{}, mXB{}, mWA{}, mCtB{};
+  TcBatch tcb{};
 };
 
 namespace {
@@ -156,6 +165,8 @@ void free_all(as_sketch* h) {
   if (h->bad) cudaFree(h->bad);
   if (h->dstatus) cudaFree(h->dstatus);
   if (h->zero) cudaFree(h->zero);
+  __nv_bfloat16* bp[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Gfh, h->Gfl, h->Xh, h->Xl, h->Wh, h->Wl};
+  for (__nv_bfloat16* p : bp) if (p) cudaFree(p);
   if (h->h_buf) cudaFreeHost(h->h_buf);
   delete h->prof;
   h->prof = nullptr;
@@ -192,6 +203,28 @@ as_status arena_reserve(as_sketch* h, size_t extra) {
   return AS_OK;
 }
 
+// BF16 (hi, lo) shadows of C rows [r0, r1) for the tensor-core forms.
+as_status tc_split_rows(as_sketch* h, int r0, int r1) {
+  if (!h->tc || r1 <= r0) return AS_OK;
+  return launch_split_bf16(h->s, h->C + (size_t)r0 * h->ldc, h->ldc, r1 - r0, h->ldc, h->Chi + (size_t)r0 * h->ldc,
+                           h->Clo + (size_t)r0 * h->ldc, h->ldc, false);
+}
+
+// G gains the Gram rows/columns of rows [r, r+b) through the tcgen05 GEMM
+// (A = C rows [0, r+b), B = C rows [r, r+b), K = d) and the split reduction.
+as_status tc_gram_rows(as_sketch* h, int r, int b, const UmmaOperand& Bmap, int bn) {
+  const int M = r + b;
+  const int mt = (M + 127) / 128, nt = (b + bn - 1) / bn, ktiles = h->ldc / 64;
+  int S = std::max(1, std::min((2 * 152 + mt * nt - 1) / (mt * nt), ktiles));
+  while (S > 1 && (size_t)S * b * M > h->p_cap) --S;
+  const int klen = ((ktiles + S - 1) / S) * 64;
+  S = (h->ldc + klen - 1) / klen;
+  as_status st = launch_umma_gemm(h->s, h->mCA, Bmap, M, b, h->ldc, bn, h->dpass, S, r, h->bb.P, 1, M,
+                                  (long long)b * M, h->dstatus);
+  if (st != AS_OK) return st;
+  return launch_gram_reduce(h->s, h->bb.P, M, (long long)b * M, S, M, r, b, h->G, h->n2);
+}
+
 // Algorithm 4 lines 3-4: FD shrink of the full buffer through its Gram.
 as_status fd_shrink(as_sketch* h) {
   const int n2 = h->n2, ell = h->ell, d = h->d;
@@ -208,16 +241,31 @@ as_status fd_shrink(as_sketch* h) {
   st = launch_shrink_weights(h->s, n2, ell, h->lam, h->U, h->Wfd);
   if (st != AS_OK) return st;
   AS_CUDA_TRY(cudaMemsetAsync(h->Cnew, 0, (size_t)n2 * h->ldc * sizeof(float), h->s));
-  if (ell > 1) {
+  if (ell > 1 && h->tc) {
+    // C' = W C~ on tcgen05: A = W (rows j, K = p), B = C~^T (rows c, K = p)
+    st = launch_split_bf16(h->s, h->Wfd, n2, ell - 1, n2, h->Wh, h->Wl, h->n2p, false);
+    if (st == AS_OK) st = launch_split_bf16(h->s, h->C, h->ldc, n2, d, h->Cthi, h->Ctlo, h->n2p, true);
+    if (st == AS_OK)
+      st = launch_umma_gemm(h->s, h->mWA, h->mCtB, ell - 1, d, h->n2p, 256, h->dpass, 1, 0, h->Cnew, h->ldc, 1, 0,
+                            h->dstatus);
+    if (st != AS_OK) return st;
+  } else if (ell > 1) {
     st = gemm_strided<float, float, float>(h->s, ell - 1, d, n2, h->Wfd, n2, 1, h->C, h->ldc, 1, h->Cnew, h->ldc,
                                            1, 1.0, 0.0);
     if (st != AS_OK) return st;
   }
   std::swap(h->C, h->Cnew);
   AS_CUDA_TRY(cudaMemsetAsync(h->G, 0, (size_t)n2 * n2 * sizeof(double), h->s));
-  if (ell > 1) {
+  if (ell > 1 && h->tc) {
+    st = tc_split_rows(h, 0, n2);
+    if (st == AS_OK) st = tc_gram_rows(h, 0, ell - 1, h->mCB256, 256);
+    if (st != AS_OK) return st;
+  } else if (ell > 1) {
     st = gemm_strided<float, float, double>(h->s, ell - 1, ell - 1, d, h->C, h->ldc, 1, h->C, 1, h->ldc, h->G, n2,
                                             1, 1.0, 0.0);
+    if (st != AS_OK) return st;
+  } else if (h->tc) {
+    st = tc_split_rows(h, 0, n2);
     if (st != AS_OK) return st;
   }
   // C' = W C~ ((l-1) x 2l x d) and G = C' C'^T ((l-1)^2 x d); C~ read, C' written and read
@@ -246,6 +294,8 @@ as_status dump(as_sketch* h, int xi, int k, int64_t i) {
     h->dwork_cap = need;
   }
   st = launch_dump(h->s, h->C, ldc, d, r, h->G, n2, h->si.WU, h->si.GWU, k, xi, Z, Y, h->dwork);
+  if (st != AS_OK) return st;
+  st = tc_split_rows(h, 0, r);
   if (st != AS_OK) return st;
   const int64_t s_prev = h->snaps.empty() ? 1 : h->snaps.back().t + 1;
   h->snaps.push_back(Snap{h->arena_used, xi, s_prev, i});
@@ -343,6 +393,8 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
     if (st != AS_OK) return st;
     if (bb == 0) { *used = 0; return AS_OK; }
   }
+  st = tc_split_rows(h, r0, r0 + b);
+  if (st != AS_OK) return st;
   // thresholds before each row (Algorithm 8 lines 2-3)
   std::vector<double> Ft(bb), th(bb);
   double F = h->F;
@@ -353,7 +405,8 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
   }
   // line 1 for the whole block: G gains the new rows and columns
   if (h->prof) h->prof->begin(PK_GRAM, h->s);
-  st = launch_gram_rows_skinny(h->s, h->C, h->ldc, d, r0, bb, h->G, n2, h->bb.P, h->p_cap);
+  st = h->tc ? tc_gram_rows(h, r0, bb, h->mCB64, 64)
+             : launch_gram_rows_skinny(h->s, h->C, h->ldc, d, r0, bb, h->G, n2, h->bb.P, h->p_cap);
   if (st != AS_OK) return st;
   if (h->prof)
     h->prof->end(PK_GRAM, h->s, 2.0 * (r0 + bb) * (double)bb * d, 4.0 * (r0 + bb) * (double)d + 8.0 * (r0 + bb) * bb);
@@ -361,10 +414,11 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
   const int nb = fills ? bb - 1 : bb;
   std::vector<double> sig2(nb), ritz(2 * (size_t)nb);
   if (nb > 0) {
-    st = launch_gf_mirror(h->s, h->G, h->Gf, n2, r0 + bb);
+    st = h->tc ? launch_gbf16_mirror(h->s, h->G, n2, r0 + bb, h->Gfh, h->Gfl, h->n2p)
+               : launch_gf_mirror(h->s, h->G, h->Gf, n2, r0 + bb);
     if (st != AS_OK) return st;
     st = launch_batch_gspace(h->s, h->Gf, n2, r0, nb, h->k_pi, h->q, h->key, (uint64_t)(h->T + 1), h->bb,
-                             h->prof);
+                             h->prof, h->tc ? &h->tcb : nullptr);
     if (st != AS_OK) return st;
     AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf, h->bb.sig2, nb * sizeof(double), cudaMemcpyDeviceToHost, h->s));
     AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf + nb, h->bb.ritz, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, h->s));
@@ -420,6 +474,7 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
   const int rnew = r0 + tstar + 1;
   if (rnew < r0 + bb) {
     st = launch_truncate(h->s, h->C, h->ldc, d, rnew, r0 + bb, h->G, n2);
+    if (st == AS_OK) st = tc_split_rows(h, rnew, r0 + bb);
     if (st != AS_OK) return st;
   }
   h->r = rnew;
@@ -514,7 +569,8 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
     return AS_EINVAL;
   }
   if (c.mode == AS_FIXED_THETA && !(c.theta >= 0.0)) return AS_EINVAL;
-  if (c.prec != AS_FP32_PLAIN) return (c.prec == AS_BF16) ? AS_ENOTSUP : AS_EINVAL;
+  if (c.prec != AS_FP32_PLAIN && c.prec != AS_BF16 && c.prec != AS_BF16X3) return AS_EINVAL;
+  if (c.prec != AS_FP32_PLAIN && !umma_available()) return AS_ENOTSUP;
   if (c.eps_si == 0.0) c.eps_si = 0.4;
   if (!(c.eps_si > 0.0 && c.eps_si < 1.0)) return AS_EINVAL;
   if (c.k_pi < 0 || c.q_si < 0) return AS_EINVAL;
@@ -585,6 +641,36 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   ALLOC(h->si.WU, (size_t)n2 * kmax);
   ALLOC(h->si.GWU, (size_t)n2 * kmax);
   ALLOC(h->si.tmp, (size_t)n2 * kmax + 3 * (size_t)kmax * kmax + kmax);
+  if (st == AS_OK && c.prec != AS_FP32_PLAIN) {
+    h->tc = true;
+    h->dpass = (c.prec == AS_BF16X3) ? 3 : 1;
+    h->n2p = (n2 + 63) / 64 * 64;
+    const int rp = std::max(256, std::max(n2, std::max(3 * bmax, ell)));
+    h->rows_pad = rp;
+    const size_t cN = (size_t)std::max(rp, n2) * h->ldc, ctN = (size_t)std::max(h->d, 256) * h->n2p;
+    const size_t gN = (size_t)std::max(h->n2p, 256) * h->n2p, xN = (size_t)std::max(3 * bmax, 256) * h->n2p;
+    const size_t wN = (size_t)std::max(ell, 256) * h->n2p;
+    ALLOC(h->Chi, cN); ALLOC(h->Clo, cN); ALLOC(h->Cthi, ctN); ALLOC(h->Ctlo, ctN);
+    ALLOC(h->Gfh, gN); ALLOC(h->Gfl, gN); ALLOC(h->Xh, xN); ALLOC(h->Xl, xN); ALLOC(h->Wh, wN); ALLOC(h->Wl, wN);
+    __nv_bfloat16* bz[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Gfh, h->Gfl, h->Xh, h->Xl, h->Wh, h->Wl};
+    const size_t bn[] = {cN, cN, ctN, ctN, gN, gN, xN, xN, wN, wN};
+    for (int t = 0; t < 10 && st == AS_OK; ++t)
+      if (cudaMemsetAsync(bz[t], 0, bn[t] * sizeof(__nv_bfloat16), h->s) != cudaSuccess) st = AS_EDEVICE;
+    const int cr = (int)(cN / h->ldc);
+    auto mk = [&](UmmaOperand& o, __nv_bfloat16* hi, __nv_bfloat16* lo, int rows, int kdim, long long ld, int box) {
+      if (st != AS_OK) return;
+      st = umma_make_map(&o.hi, hi, rows, kdim, ld, box);
+      if (st == AS_OK) st = umma_make_map(&o.lo, lo, rows, kdim, ld, box);
+    };
+    mk(h->mCA, h->Chi, h->Clo, cr, h->ldc, h->ldc, 128);
+    mk(h->mCB64, h->Chi, h->Clo, cr, h->ldc, h->ldc, 64);
+    mk(h->mCB256, h->Chi, h->Clo, cr, h->ldc, h->ldc, 256);
+    mk(h->mGA, h->Gfh, h->Gfl, (int)(gN / h->n2p), h->n2p, h->n2p, 128);
+    mk(h->mXB, h->Xh, h->Xl, (int)(xN / h->n2p), h->n2p, h->n2p, 192);
+    mk(h->mWA, h->Wh, h->Wl, (int)(wN / h->n2p), h->n2p, h->n2p, 128);
+    mk(h->mCtB, h->Cthi, h->Ctlo, (int)(ctN / h->n2p), h->n2p, h->n2p, 256);
+    h->tcb = TcBatch{&h->mGA, &h->mXB, h->Xh, h->Xl, h->n2p, h->dstatus};
+  }
 #undef ALLOC
   if (st == AS_OK && cudaMallocHost((void**)&h->h_buf, (size_t)(4 * std::max(n2, bmax) + 64) * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();

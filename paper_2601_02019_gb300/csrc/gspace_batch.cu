@@ -18,6 +18,8 @@
 // Batch matrix layout: column-major, column c at X + c*n2; columns [0, nb)
 // are the power-iteration vectors of rows 0..nb-1 and columns nb+2t, nb+2t+1
 // the simultaneous-iteration pair of row t.
+#include <algorithm>
+
 #include "eig.cuh"
 #include "kernels.cuh"
 
@@ -179,6 +181,17 @@ __global__ void mirror_f32_kernel(const double* G, float* Gf, int n2, int m) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     const int p = (int)(e / n2), q = (int)(e % n2);
     Gf[e] = (p < m && q < m) ? (float)G[e] : 0.f;
+  }
+}
+
+__global__ void mirror_bf16_kernel(const double* G, int n2, int m, __nv_bfloat16* hi, __nv_bfloat16* lo, int n2p) {
+  const size_t tot = (size_t)n2p * n2p;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / n2p), q = (int)(e % n2p);
+    const float x = (p < m && q < m) ? (float)G[(size_t)p * n2 + q] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
   }
 }
 
@@ -451,14 +464,27 @@ as_status launch_gf_mirror(cudaStream_t s, const double* G, float* Gf, int n2, i
   return AS_OK;
 }
 
+as_status launch_gbf16_mirror(cudaStream_t s, const double* G, int n2, int m, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                              int n2p) {
+  const size_t tot = (size_t)n2p * n2p;
+  const int blocks = (int)std::min<size_t>((tot + 255) / 256, 4096);
+  mirror_bf16_kernel<<<blocks, 256, 0, s>>>(G, n2, m, hi, lo, n2p); count_launches(1);
+  AS_CUDA_TRY(cudaGetLastError());
+  return AS_OK;
+}
+
 as_status launch_batch_gspace(cudaStream_t s, const float* Gf, int n2, int r0, int nb, int k_pi, int q, Key key,
-                              uint64_t i0, const BatchBuffers& bb, Prof* prof) {
+                              uint64_t i0, const BatchBuffers& bb, Prof* prof, const TcBatch* tc) {
   if (nb <= 0) return AS_OK;
   const int ncol = 3 * nb;
   const int mmax = r0 + nb;
   const long long plane = (long long)n2 * ncol;
   batch_fill_kernel<<<dim3(nb, 2), 128, 0, s>>>(bb.X, n2, nb, r0, key, i0); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
+  if (tc) {
+    as_status st = launch_split_bf16(s, bb.X, n2, ncol, n2, tc->Xh, tc->Xl, tc->n2p, false);
+    if (st != AS_OK) return st;
+  }
   const int iters = std::max(k_pi, q);
   for (int it = 0; it <= iters; ++it) {
     const bool pi_on = it <= k_pi;
@@ -467,8 +493,21 @@ as_status launch_batch_gspace(cudaStream_t s, const float* Gf, int n2, int r0, i
     const int c1 = si_on ? ncol : nb;
     int S = std::min(skinny_splits(mmax, c1 - c0, mmax), bb.max_splits);
     if (prof) prof->begin(PK_BATCH_GEMM, s);
-    as_status st = launch_skinny_partial(s, mmax, c1 - c0, mmax, &S, Gf, n2, bb.X + (size_t)c0 * n2, n2,
-                                         bb.P + (size_t)c0 * n2, n2, plane);
+    as_status st;
+    if (tc) {
+      // split-BF16 tcgen05 product Y = G X: A = G (rows p, K = q), B = X^T (rows c, K = q)
+      const int Kp = (mmax + 63) / 64 * 64;
+      const int ktiles = Kp / 64;
+      const int mt = (mmax + 127) / 128;
+      S = std::max(1, std::min({(2 * 152 + mt - 1) / mt, ktiles, bb.max_splits}));
+      const int klen = ((ktiles + S - 1) / S) * 64;
+      S = (Kp + klen - 1) / klen;
+      st = launch_umma_gemm(s, *tc->mapG, *tc->mapX, mmax, c1 - c0, Kp, 192,
+                            3, S, c0, bb.P + (size_t)c0 * n2, 1, n2, plane, tc->err);
+    } else {
+      st = launch_skinny_partial(s, mmax, c1 - c0, mmax, &S, Gf, n2, bb.X + (size_t)c0 * n2, n2,
+                                 bb.P + (size_t)c0 * n2, n2, plane);
+    }
     if (st != AS_OK) return st;
     // algorithmic work of one product: 2 m^2 N flops; G (m^2 FP32) and X read, Y written
     if (prof)
@@ -485,6 +524,12 @@ as_status launch_batch_gspace(cudaStream_t s, const float* Gf, int n2, int r0, i
     batch_orth_kernel<<<dim3(nb, kinds), 512, 0, s>>>(bb.P, bb.X, n2, nb, r0, kind0, it == k_pi ? 1 : 0,
                                                       it == q ? 1 : 0, bb.sig2, bb.ritz); count_launches(1);
     AS_CUDA_TRY(cudaGetLastError());
+    if (tc && it < iters) {
+      const int nc0 = (it + 1 <= k_pi) ? 0 : nb;   // columns the next product reads
+      st = launch_split_bf16(s, bb.X + (size_t)nc0 * n2, n2, ncol - nc0, n2, tc->Xh + (size_t)nc0 * tc->n2p,
+                             tc->Xl + (size_t)nc0 * tc->n2p, tc->n2p, false);
+      if (st != AS_OK) return st;
+    }
     if (prof) prof->end(PK_BATCH_ORTH, s, 0.0, 4.0 * (double)mmax * (c1 - c0) * (S + 2));
   }
   return AS_OK;

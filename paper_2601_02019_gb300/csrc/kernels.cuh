@@ -89,6 +89,9 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
 int skinny_splits(int M, int N, int K);
 as_status launch_skinny_partial(cudaStream_t s, int M, int N, int K, int* S, const float* A, long long lda,
                                 const float* X, long long ldx, float* P, long long ldp, long long plane);
+// G[p][r+t] = sum_s P[s][t*ldp + p] (FP64), mirrored to G[r+t][p] for p < r.
+as_status launch_gram_reduce(cudaStream_t s, const float* P, long long ldp, long long plane, int S, int mrows, int r,
+                             int b, double* G, int n2);
 // G gains the Gram rows/columns of block rows [r, r+b) (FP64 combine of the splits).
 as_status launch_gram_rows_skinny(cudaStream_t s, const float* C, int ldc, int d, int r, int b, double* G, int n2,
                                   float* P, size_t p_cap);
@@ -103,6 +106,24 @@ as_status launch_dump(cudaStream_t s, float* C, int ldc, int d, int r, double* G
 // FP32 mirror of the leading m x m block of G (zero elsewhere).
 as_status launch_gf_mirror(cudaStream_t s, const double* G, float* Gf, int n2, int m);
 
+// tcgen05 GEMM operand (umma.cu): one or two TMA tensor maps over BF16 data
+// (hi, and lo for the split-BF16 form), K innermost, box 64 x box_rows.
+struct UmmaOperand {
+  CUtensorMap hi;
+  CUtensorMap lo;
+};
+
+// Tensor-core variant of the batched products (BF16 forms): G and X in
+// split-BF16 with leading dimension n2p (n2 rounded up to 64, zero padded).
+struct TcBatch {
+  const UmmaOperand* mapG;   // over Gf hi/lo, box 128
+  const UmmaOperand* mapX;   // over X hi/lo, box 192
+  __nv_bfloat16* Xh;         // 3*bmax x n2p
+  __nv_bfloat16* Xl;
+  int n2p;
+  int* err;
+};
+
 struct BatchBuffers {
   float* X;       // n2 x 3*bmax, column-major
   float* P;       // split-K partial planes (max_splits x n2 x 3*bmax)
@@ -114,7 +135,10 @@ struct BatchBuffers {
 // Block-speculative power iteration and first doubling step for rows
 // t = 0..nb-1 of a block whose row t sees the leading (r0+t+1) rows (FP32).
 as_status launch_batch_gspace(cudaStream_t s, const float* Gf, int n2, int r0, int nb, int k_pi, int q, Key key,
-                              uint64_t i0, const BatchBuffers& bb, Prof* prof);
+                              uint64_t i0, const BatchBuffers& bb, Prof* prof, const TcBatch* tc = nullptr);
+// Split-BF16 mirror of the leading m x m block of G (ld n2p, zero elsewhere).
+as_status launch_gbf16_mirror(cudaStream_t s, const double* G, int n2, int m, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                              int n2p);
 
 // FP64 single-row power iteration and simultaneous iteration built from
 // multi-block products (any buffer size).  x, y: n2 doubles; zero: 1 int.
@@ -128,12 +152,6 @@ as_status launch_simul_iter_f64(cudaStream_t s, const double* G, int n2, int m, 
 as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m, const float* X, int col0,
                                   const SiBuffers& b, int* status);
 
-// tcgen05 GEMM (umma.cu).  An operand is one or two TMA tensor maps over BF16
-// data (hi, and lo for the split-BF16 form), K innermost, box 64 x box_rows.
-struct UmmaOperand {
-  CUtensorMap hi;
-  CUtensorMap lo;
-};
 bool umma_available();
 as_status umma_make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int kdim, long long ld, int box_rows);
 int umma_bn_for(int N);

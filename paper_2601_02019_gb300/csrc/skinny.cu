@@ -103,6 +103,14 @@ as_status launch_skinny_partial(cudaStream_t s, int M, int N, int K, int* S, con
   return AS_OK;
 }
 
+as_status launch_gram_reduce(cudaStream_t s, const float* P, long long ldp, long long plane, int S, int mrows, int r,
+                             int b, double* G, int n2) {
+  dim3 grid((mrows + 255) / 256, b);
+  gram_reduce_kernel<<<grid, 256, 0, s>>>(P, ldp, plane, S, mrows, r, b, G, n2); count_launches(1);
+  AS_CUDA_TRY(cudaGetLastError());
+  return AS_OK;
+}
+
 as_status launch_gram_rows_skinny(cudaStream_t s, const float* C, int ldc, int d, int r, int b, double* G, int n2,
                                   float* P, size_t p_cap) {
   const int M = r + b;
