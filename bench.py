@@ -138,34 +138,23 @@ def reference_arm(args) -> None:
     }))
 
 
-def our_arm(args) -> None:
-    import numpy as np
-    import torch
+PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
 
-    import paper_2601_02019_gb300 as p
-    from synth import low_rank_noisy, spectrum
 
-    ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    w = WORKLOADS[args.workload]
-    d, ell, B = w["d"], w["ell"], args.rows_per_step
-    K, W = args.steps, args.warmup
-    ntot = (W + K) * B
-    A = low_rank_noisy(ntot, d, w["r"], spectrum(w["spectrum"], w["r"]), stream=rank)
-    A_dev = torch.from_numpy(A).to(dev)
-    A_pin = torch.from_numpy(A).pin_memory()
+def _run_form(p, torch, args, A_dev, d, ell, B, K, W, rank, local, ws, prec, want_state=False):
+    """Warm up W steps, time K steps (L2 flushed between steps); returns timings,
+    counters, the kernel-class profile and (optionally) the state at the start."""
+    dev = A_dev.device
     stream = torch.cuda.Stream(device=dev)
-    s = p.Sketch(d, ell, profile=True, stream=stream, stream_id=rank)
+    s = p.Sketch(d, ell, prec=prec, profile=True, stream=stream, stream_id=rank)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     for k in range(W):
         s.update(A_dev[k * B:(k + 1) * B])
     torch.cuda.synchronize()
-    # state at the start of the timed region (for the CPU baseline, after timing)
-    C0, r0 = s.buffer()
+    state = None
+    if want_state:
+        C0, r0 = s.buffer()
+        state = (C0, r0, s.stats())
     st0 = s.stats()
     s.profile_reset()
     if ws > 1:
@@ -188,37 +177,78 @@ def our_arm(args) -> None:
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     t_ms = sum(step_ms)
-    st1 = s.stats()
-    prof = s.profile()
     if ws > 1:
         t = torch.tensor([t_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_ms = float(t.item())
-    value = ws * K * B / (t_ms / 1000.0)
+    st1 = s.stats()
+    return dict(sketch=s, t_ms=t_ms, step_ms=step_ms, st0=st0, st1=st1, prof=s.profile(), clocks=clk.summary(),
+                state=state)
 
-    # roofline of the dominant single-kernel class (the eigensolver and the
-    # event-row path are composites of many kernels and are listed in "profile")
+
+def our_arm(args) -> None:
+    import numpy as np
+    import torch
+
+    import paper_2601_02019_gb300 as p
+    from synth import low_rank_noisy, spectrum
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[args.workload]
+    d, ell, B = w["d"], w["ell"], args.rows_per_step
+    K, W = args.steps, args.warmup
+    ntot = (W + K) * B
+    A = low_rank_noisy(ntot, d, w["r"], spectrum(w["spectrum"], w["r"]), stream=rank)
+    A_dev = torch.from_numpy(A).to(dev)
+    forms = [f for f in args.forms.split(",") if f]
+    head = args.prec
+    if head not in forms:
+        forms.append(head)
+    runs = {}
+    for f in forms:
+        runs[f] = _run_form(p, torch, args, A_dev, d, ell, B, K, W, rank, local, ws, PRECISIONS[f],
+                            want_state=(f == head))
+    hr = runs[head]
+    value = ws * K * B / (hr["t_ms"] / 1000.0)
+
+    # roofline of the dominant single-kernel class of the headline form (the
+    # eigensolver and the event-row path are composites and are listed in "profile")
     peaks, peak_src = _peaks()
+    prof = hr["prof"]
     single = [x for x in prof if x["name"] in ("gspace_batch_gemm", "gspace_batch_orth", "ingest")]
     top = max(single, key=lambda x: x["total_ms"])
     tot_prof = sum(x["total_ms"] for x in prof) or 1.0
+    tensor = PRECISIONS[head] != 0
     if top["name"] == "ingest":
         ach = top["bytes"] / (top["total_ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+        src = peak_src
+    elif top["name"] == "gspace_batch_gemm" and tensor:
+        ach = top["flops"] / (top["total_ms"] / 1e3) / 1e12
+        pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s"}
+        src = (f"{peak_src} sustained BF16; achieved counts the algorithmic 2 m^2 N flops of Y = G X, the tensor "
+               "pipe executes 3x that (split-BF16)")
     else:
         fp32_peak = N_SM * FP32_SIMT_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         ach = top["flops"] / (top["total_ms"] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s"}
+        src = f"{peak_src}; FP32 SIMT = {N_SM} SMs x {FP32_SIMT_LANES_PER_SM} lanes x 2 x max SM clock"
     roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": None, "kernel": top["name"],
                  "launches": top["launches"], "avg_launch_us": 1000 * top["total_ms"] / max(1, top["launches"]),
-                 "peak_source": f"{peak_src}; FP32 SIMT = {N_SM} SMs x {FP32_SIMT_LANES_PER_SM} lanes x 2 x max SM clock"
-                 if roof["bound"] == "alu" else peak_src})
+                 "peak_source": src})
 
     # end to end through the C ABI from pinned host memory (host->device copy
     # inside the timed region, device->host read of the counters each step)
     e2e = None
     if not args.no_e2e:
-        s2 = p.Sketch(d, ell, stream_id=rank)
+        A_pin = torch.from_numpy(A).pin_memory()
+        s2 = p.Sketch(d, ell, prec=PRECISIONS[head], stream_id=rank)
         for k in range(W):
             s2.update(A_pin[k * B:(k + 1) * B].numpy())
         torch.cuda.synchronize()
@@ -227,51 +257,59 @@ def our_arm(args) -> None:
             s2.update(A_pin[k * B:(k + 1) * B].numpy())
             s2.stats()
         e2e_s = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
         e2e = {"value": ws * K * B / e2e_s, "unit": "rows/s", "h2d_bytes_per_step": B * d * 4,
                "d2h_bytes_per_step": 112}
-    if ws > 1 and e2e is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e["value"] = ws * K * B / float(t.item())
 
-    out = None
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            import numpy as _np
-
             from oracle.aerosketch import AeroSketch
+            C0, r0, st0 = hr["state"]
             o = AeroSketch(d, ell, stream_id=rank)
-            o.load_state(C0.astype(_np.float64), r0, st0["fro2"], st0["rows"])
+            o.load_state(C0.astype(np.float64), r0, st0["fro2"], st0["rows"])
             S = args.cpu_rows
-            blk = A[W * B: W * B + S].astype(_np.float64)
+            blk = A[W * B: W * B + S].astype(np.float64)
             t0 = time.perf_counter()
             o.run(blk)
             dt = time.perf_counter() - t0
             cpu = {"value": S / dt, "unit": "rows/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"first {S} rows of the timed region, from the GPU's exact state at its start"}
-        cov = None
+        forms_out = {}
+        errs = {}
         if not args.no_err:
-            from oracle.metric import cov_err
-            Bq = s.query()
-            Aall = A.astype(np.float64)
-            cov = {"cov_err": cov_err(Aall, Bq), "bound_eps": 2.0 / ell, "rows": int(st1["rows"])}
+            from oracle.metric import cov_err, gram
+            AtA = gram(A)
+        for f, r in runs.items():
+            fo = {"rows_per_s": ws * K * B / (r["t_ms"] / 1000.0), "ms_per_step": r["t_ms"] / K,
+                  "shrinks": r["st1"]["shrinks"] - r["st0"]["shrinks"], "dumps": r["st1"]["dumps"] - r["st0"]["dumps"],
+                  "gpu_launches": int(r["st1"]["kernel_launches"] - r["st0"]["kernel_launches"])}
+            if not args.no_err:
+                errs[f] = cov_err(A, r["sketch"].query(), AtA)
+                fo["cov_err"] = errs[f]
+            forms_out[f] = fo
+        if errs and "fp32" in errs:
+            for f in forms_out:
+                forms_out[f]["cov_err_rel_to_fp32"] = abs(errs[f] - errs["fp32"]) / errs["fp32"]
         out = {
             "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": ws, "steps": K, "warmup": W,
-            "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 products, f64 core", "data": "synthetic",
-            "config": {"workload": args.workload, "d": d, "ell": ell, "rows_per_step": B,
-                       "precision": "FP32_PLAIN", "l2": "flushed between steps (256 MB write)",
-                       "parallelism": f"replicas x{ws}"},
+            "ms_per_step": hr["t_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32 products, f64 core", "bf16": "bf16 tensor products (f32 acc), f64 core",
+                      "bf16x3": "split-bf16 tensor products (f32 acc), f64 core"}[head],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "d": d, "ell": ell, "rows_per_step": B, "precision": head,
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
-            "clocks": clk.summary(),
+            "gpu_launches": forms_out[head]["gpu_launches"],
+            "clocks": hr["clocks"],
             "profile": [{"kernel": x["name"], "launches": x["launches"], "ms": round(x["total_ms"], 3),
                          "share": round(x["total_ms"] / tot_prof, 4)} for x in prof],
-            "sketch": {"shrinks": st1["shrinks"] - st0["shrinks"], "dumps": st1["dumps"] - st0["dumps"],
-                       "gates": st1["gates"] - st0["gates"]},
-            "step_ms": [round(x, 3) for x in step_ms],
-            "accuracy": cov,
+            "forms": forms_out,
+            "accuracy": ({"cov_err": errs.get(head), "bound_eps": 2.0 / ell, "rows": int(hr["st1"]["rows"])}
+                         if errs else None),
         }
         print(json.dumps(out))
     if ws > 1:
@@ -291,6 +329,9 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-err", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--prec", default="bf16x3", choices=sorted(PRECISIONS))
+    ap.add_argument("--forms", default="fp32,bf16,bf16x3",
+                    help="precision forms measured side by side (comma-separated)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
