@@ -138,7 +138,7 @@ def reference_arm(args) -> None:
     }))
 
 
-PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3}
 
 
 def _run_form(p, torch, args, A_dev, d, ell, B, K, W, rank, local, ws, prec, want_state=False):
@@ -298,7 +298,8 @@ def our_arm(args) -> None:
             "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": ws, "steps": K, "warmup": W,
             "ms_per_step": hr["t_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32 products, f64 core", "bf16": "bf16 tensor products (f32 acc), f64 core",
-                      "bf16x3": "split-bf16 tensor products (f32 acc), f64 core"}[head],
+                      "bf16x3": "2-level split-bf16 tensor products (f32 acc), f64 core",
+                      "bf16x6": "3-level split-bf16 tensor products (f32 acc), f64 core"}[head],
             "data": "synthetic",
             "config": {"workload": args.workload, "d": d, "ell": ell, "rows_per_step": B, "precision": head,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
@@ -329,8 +330,8 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-err", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--prec", default="bf16x3", choices=sorted(PRECISIONS))
-    ap.add_argument("--forms", default="fp32,bf16,bf16x3",
+    ap.add_argument("--prec", default="bf16x6", choices=sorted(PRECISIONS))
+    ap.add_argument("--forms", default="fp32,bf16,bf16x3,bf16x6",
                     help="precision forms measured side by side (comma-separated)")
     args = ap.parse_args()
     if args.impl == "reference":

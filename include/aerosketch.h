@@ -65,12 +65,16 @@ typedef enum {
  *   AS_BF16        d-side products (Gram rows, FD rebuild) on the tcgen05
  *                  tensor cores with BF16 operands and FP32 accumulation;
  *                  batched G-space products in split-BF16 on tcgen05.
- *   AS_BF16X3      as AS_BF16 with the d-side products also in split-BF16
- *                  (hi*hi + hi*lo + lo*hi, near-FP32 accuracy). */
+ *   AS_BF16X3      as AS_BF16 with the d-side products in two-level split-BF16
+ *                  (x = hi + lo; hi*hi + hi*lo + lo*hi: ~16-bit operands).
+ *   AS_BF16X6      as AS_BF16 with the d-side products in three-level
+ *                  split-BF16 (x = hi + mid + lo, the six products above
+ *                  2^-24: operands as exact as FP32). */
 typedef enum {
   AS_FP32_PLAIN = 0,
   AS_BF16 = 1,
-  AS_BF16X3 = 2
+  AS_BF16X3 = 2,
+  AS_BF16X6 = 3
 } as_precision;
 
 /* Flags. */
@@ -195,7 +199,8 @@ as_status as_symeig(int32_t n, const double* A, int32_t nev, double* evals, doub
  * G-space contractions: out = A B^T with A (M x K) and B (N x K) FP32,
  * row-major, host memory, computed by the tcgen05 kernel with BF16 operands
  * and FP32 accumulation: npass = 1 rounds the operands to BF16 once, npass =
- * 3 uses the split-BF16 form (hi*hi + hi*lo + lo*hi).  `splits` > 1 splits K
+ * 3 uses the two-level split-BF16 form (hi*hi + hi*lo + lo*hi), npass = 6 the
+ * three-level one (all products of levels i + j <= 2).  `splits` > 1 splits K
  * across thread blocks (partials summed in FP64 here).  out: M x N row-major
  * host memory.  Synchronous.  AS_ENOTSUP if the driver lacks tensor-map support. */
 as_status as_tc_gemm(int32_t M, int32_t N, int32_t K, const float* A, const float* B, int32_t npass, int32_t splits,

@@ -12,7 +12,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libaerosketch.so")
 
 AS_OK, AS_EINVAL, AS_ENOMEM, AS_EDEVICE, AS_ENUMERIC, AS_ETIMEOUT, AS_EBUSY, AS_ENOTSUP = range(8)
 AS_PERSISTENT, AS_FIXED_THETA, AS_SLIDING, AS_SITE, AS_COORDINATOR = range(5)
-AS_FP32_PLAIN, AS_BF16, AS_BF16X3 = 0, 1, 2
+AS_FP32_PLAIN, AS_BF16, AS_BF16X3, AS_BF16X6 = 0, 1, 2, 3
 AS_TRACE_DECISIONS = 0x1
 AS_PROFILE = 0x2
 

@@ -149,6 +149,7 @@ struct as_sketch {
   int rows_pad = 0;         // row counts of the BF16 buffers, >= 256
   __nv_bfloat16 *Chi = nullptr, *Clo = nullptr, *Cthi = nullptr, *Ctlo = nullptr, *Gfh = nullptr, *Gfl = nullptr,
                 *Xh = nullptr, *Xl = nullptr, *Wh = nullptr, *Wl = nullptr;
+  __nv_bfloat16 *Cl2 = nullptr, *Ctl2 = nullptr, *Wl2 = nullptr;   // third BF16 level (AS_BF16X6)
   UmmaOperand mCA{}, mCB64{}, mCB256{}, mGA{}, mXB{}, mWA{}, mCtB{};
   TcBatch tcb{};
 };
@@ -165,7 +166,8 @@ void free_all(as_sketch* h) {
   if (h->bad) cudaFree(h->bad);
   if (h->dstatus) cudaFree(h->dstatus);
   if (h->zero) cudaFree(h->zero);
-  __nv_bfloat16* bp[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Gfh, h->Gfl, h->Xh, h->Xl, h->Wh, h->Wl};
+  __nv_bfloat16* bp[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Gfh, h->Gfl, h->Xh, h->Xl, h->Wh, h->Wl,
+                         h->Cl2, h->Ctl2, h->Wl2};
   for (__nv_bfloat16* p : bp) if (p) cudaFree(p);
   if (h->h_buf) cudaFreeHost(h->h_buf);
   delete h->prof;
@@ -207,7 +209,8 @@ as_status arena_reserve(as_sketch* h, size_t extra) {
 as_status tc_split_rows(as_sketch* h, int r0, int r1) {
   if (!h->tc || r1 <= r0) return AS_OK;
   return launch_split_bf16(h->s, h->C + (size_t)r0 * h->ldc, h->ldc, r1 - r0, h->ldc, h->Chi + (size_t)r0 * h->ldc,
-                           h->Clo + (size_t)r0 * h->ldc, h->ldc, false);
+                           h->Clo + (size_t)r0 * h->ldc, h->ldc, false,
+                           h->Cl2 ? h->Cl2 + (size_t)r0 * h->ldc : nullptr);
 }
 
 // G gains the Gram rows/columns of rows [r, r+b) through the tcgen05 GEMM
@@ -243,8 +246,8 @@ as_status fd_shrink(as_sketch* h) {
   AS_CUDA_TRY(cudaMemsetAsync(h->Cnew, 0, (size_t)n2 * h->ldc * sizeof(float), h->s));
   if (ell > 1 && h->tc) {
     // C' = W C~ on tcgen05: A = W (rows j, K = p), B = C~^T (rows c, K = p)
-    st = launch_split_bf16(h->s, h->Wfd, n2, ell - 1, n2, h->Wh, h->Wl, h->n2p, false);
-    if (st == AS_OK) st = launch_split_bf16(h->s, h->C, h->ldc, n2, d, h->Cthi, h->Ctlo, h->n2p, true);
+    st = launch_split_bf16(h->s, h->Wfd, n2, ell - 1, n2, h->Wh, h->Wl, h->n2p, false, h->Wl2);
+    if (st == AS_OK) st = launch_split_bf16(h->s, h->C, h->ldc, n2, d, h->Cthi, h->Ctlo, h->n2p, true, h->Ctl2);
     if (st == AS_OK)
       st = launch_umma_gemm(h->s, h->mWA, h->mCtB, ell - 1, d, h->n2p, 256, h->dpass, 1, 0, h->Cnew, h->ldc, 1, 0,
                             h->dstatus);
@@ -569,7 +572,7 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
     return AS_EINVAL;
   }
   if (c.mode == AS_FIXED_THETA && !(c.theta >= 0.0)) return AS_EINVAL;
-  if (c.prec != AS_FP32_PLAIN && c.prec != AS_BF16 && c.prec != AS_BF16X3) return AS_EINVAL;
+  if (c.prec != AS_FP32_PLAIN && c.prec != AS_BF16 && c.prec != AS_BF16X3 && c.prec != AS_BF16X6) return AS_EINVAL;
   if (c.prec != AS_FP32_PLAIN && !umma_available()) return AS_ENOTSUP;
   if (c.eps_si == 0.0) c.eps_si = 0.4;
   if (!(c.eps_si > 0.0 && c.eps_si < 1.0)) return AS_EINVAL;
@@ -643,7 +646,7 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   ALLOC(h->si.tmp, (size_t)n2 * kmax + 3 * (size_t)kmax * kmax + kmax);
   if (st == AS_OK && c.prec != AS_FP32_PLAIN) {
     h->tc = true;
-    h->dpass = (c.prec == AS_BF16X3) ? 3 : 1;
+    h->dpass = (c.prec == AS_BF16X6) ? 6 : (c.prec == AS_BF16X3) ? 3 : 1;
     h->n2p = (n2 + 63) / 64 * 64;
     const int rp = std::max(256, std::max(n2, std::max(3 * bmax, ell)));
     h->rows_pad = rp;
@@ -652,23 +655,28 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
     const size_t wN = (size_t)std::max(ell, 256) * h->n2p;
     ALLOC(h->Chi, cN); ALLOC(h->Clo, cN); ALLOC(h->Cthi, ctN); ALLOC(h->Ctlo, ctN);
     ALLOC(h->Gfh, gN); ALLOC(h->Gfl, gN); ALLOC(h->Xh, xN); ALLOC(h->Xl, xN); ALLOC(h->Wh, wN); ALLOC(h->Wl, wN);
-    __nv_bfloat16* bz[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Gfh, h->Gfl, h->Xh, h->Xl, h->Wh, h->Wl};
-    const size_t bn[] = {cN, cN, ctN, ctN, gN, gN, xN, xN, wN, wN};
-    for (int t = 0; t < 10 && st == AS_OK; ++t)
-      if (cudaMemsetAsync(bz[t], 0, bn[t] * sizeof(__nv_bfloat16), h->s) != cudaSuccess) st = AS_EDEVICE;
+    if (h->dpass == 6) { ALLOC(h->Cl2, cN); ALLOC(h->Ctl2, ctN); ALLOC(h->Wl2, wN); }
+    __nv_bfloat16* bz[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Gfh, h->Gfl, h->Xh, h->Xl, h->Wh, h->Wl,
+                           h->Cl2, h->Ctl2, h->Wl2};
+    const size_t bn[] = {cN, cN, ctN, ctN, gN, gN, xN, xN, wN, wN, cN, ctN, wN};
+    for (int t = 0; t < 13 && st == AS_OK; ++t)
+      if (bz[t] && cudaMemsetAsync(bz[t], 0, bn[t] * sizeof(__nv_bfloat16), h->s) != cudaSuccess) st = AS_EDEVICE;
     const int cr = (int)(cN / h->ldc);
-    auto mk = [&](UmmaOperand& o, __nv_bfloat16* hi, __nv_bfloat16* lo, int rows, int kdim, long long ld, int box) {
+    // level maps; a missing third level repeats the second (never read then)
+    auto mk = [&](UmmaOperand& o, __nv_bfloat16* l0, __nv_bfloat16* l1, __nv_bfloat16* l2, int rows, int kdim,
+                  long long ld, int box) {
       if (st != AS_OK) return;
-      st = umma_make_map(&o.hi, hi, rows, kdim, ld, box);
-      if (st == AS_OK) st = umma_make_map(&o.lo, lo, rows, kdim, ld, box);
+      st = umma_make_map(&o.m[0], l0, rows, kdim, ld, box);
+      if (st == AS_OK) st = umma_make_map(&o.m[1], l1, rows, kdim, ld, box);
+      if (st == AS_OK) st = umma_make_map(&o.m[2], l2 ? l2 : l1, rows, kdim, ld, box);
     };
-    mk(h->mCA, h->Chi, h->Clo, cr, h->ldc, h->ldc, 128);
-    mk(h->mCB64, h->Chi, h->Clo, cr, h->ldc, h->ldc, 64);
-    mk(h->mCB256, h->Chi, h->Clo, cr, h->ldc, h->ldc, 256);
-    mk(h->mGA, h->Gfh, h->Gfl, (int)(gN / h->n2p), h->n2p, h->n2p, 128);
-    mk(h->mXB, h->Xh, h->Xl, (int)(xN / h->n2p), h->n2p, h->n2p, 192);
-    mk(h->mWA, h->Wh, h->Wl, (int)(wN / h->n2p), h->n2p, h->n2p, 128);
-    mk(h->mCtB, h->Cthi, h->Ctlo, (int)(ctN / h->n2p), h->n2p, h->n2p, 256);
+    mk(h->mCA, h->Chi, h->Clo, h->Cl2, cr, h->ldc, h->ldc, 128);
+    mk(h->mCB64, h->Chi, h->Clo, h->Cl2, cr, h->ldc, h->ldc, 64);
+    mk(h->mCB256, h->Chi, h->Clo, h->Cl2, cr, h->ldc, h->ldc, 256);
+    mk(h->mGA, h->Gfh, h->Gfl, nullptr, (int)(gN / h->n2p), h->n2p, h->n2p, 128);
+    mk(h->mXB, h->Xh, h->Xl, nullptr, (int)(xN / h->n2p), h->n2p, h->n2p, 192);
+    mk(h->mWA, h->Wh, h->Wl, h->Wl2, (int)(wN / h->n2p), h->n2p, h->n2p, 128);
+    mk(h->mCtB, h->Cthi, h->Ctlo, h->Ctl2, (int)(ctN / h->n2p), h->n2p, h->n2p, 256);
     h->tcb = TcBatch{&h->mGA, &h->mXB, h->Xh, h->Xl, h->n2p, h->dstatus};
   }
 #undef ALLOC
@@ -881,12 +889,13 @@ as_status as_symeig(int32_t n, const double* A, int32_t nev, double* evals, doub
 
 as_status as_tc_gemm(int32_t M, int32_t N, int32_t K, const float* A, const float* B, int32_t npass, int32_t splits,
                      double* out) {
-  if (M < 1 || N < 1 || K < 1 || !A || !B || !out || (npass != 1 && npass != 3) || splits < 1) return AS_EINVAL;
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !out || (npass != 1 && npass != 3 && npass != 6) || splits < 1)
+    return AS_EINVAL;
   if (!umma_available()) return AS_ENOTSUP;
   const int Kp = (K + 63) / 64 * 64;
   const int bn = umma_bn_for(std::min(N, 256));
   float *dA = nullptr, *dB = nullptr, *dO = nullptr;
-  __nv_bfloat16 *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+  __nv_bfloat16 *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr, *a2 = nullptr, *b2 = nullptr;
   int* err = nullptr;
   as_status st = dalloc(&dA, (size_t)M * Kp);
   if (st == AS_OK) st = dalloc(&dB, (size_t)N * Kp);
@@ -894,6 +903,8 @@ as_status as_tc_gemm(int32_t M, int32_t N, int32_t K, const float* A, const floa
   if (st == AS_OK) st = dalloc(&al, (size_t)M * Kp);
   if (st == AS_OK) st = dalloc(&bh, (size_t)N * Kp);
   if (st == AS_OK) st = dalloc(&bl, (size_t)N * Kp);
+  if (st == AS_OK) st = dalloc(&a2, (size_t)M * Kp);
+  if (st == AS_OK) st = dalloc(&b2, (size_t)N * Kp);
   if (st == AS_OK) st = dalloc(&dO, (size_t)splits * M * N);
   if (st == AS_OK) st = dalloc(&err, 1);
   cudaError_t e = cudaSuccess;
@@ -908,13 +919,15 @@ as_status as_tc_gemm(int32_t M, int32_t N, int32_t K, const float* A, const floa
       e = cudaMemcpy2D(dB, (size_t)Kp * 4, B, (size_t)K * 4, (size_t)K * 4, N, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) st = as_from_cuda(e);
   }
-  if (st == AS_OK) st = launch_split_bf16(nullptr, dA, Kp, M, Kp, ah, al, Kp, false);
-  if (st == AS_OK) st = launch_split_bf16(nullptr, dB, Kp, N, Kp, bh, bl, Kp, false);
+  if (st == AS_OK) st = launch_split_bf16(nullptr, dA, Kp, M, Kp, ah, al, Kp, false, a2);
+  if (st == AS_OK) st = launch_split_bf16(nullptr, dB, Kp, N, Kp, bh, bl, Kp, false, b2);
   UmmaOperand oa{}, ob{};
-  if (st == AS_OK) st = umma_make_map(&oa.hi, ah, M, Kp, Kp, 128);
-  if (st == AS_OK) st = umma_make_map(&oa.lo, al, M, Kp, Kp, 128);
-  if (st == AS_OK) st = umma_make_map(&ob.hi, bh, N, Kp, Kp, bn);
-  if (st == AS_OK) st = umma_make_map(&ob.lo, bl, N, Kp, Kp, bn);
+  __nv_bfloat16* la[3] = {ah, al, a2};
+  __nv_bfloat16* lb[3] = {bh, bl, b2};
+  for (int t = 0; t < 3 && st == AS_OK; ++t) {
+    st = umma_make_map(&oa.m[t], la[t], M, Kp, Kp, 128);
+    if (st == AS_OK) st = umma_make_map(&ob.m[t], lb[t], N, Kp, Kp, bn);
+  }
   if (st == AS_OK)
     st = launch_umma_gemm(nullptr, oa, ob, M, N, Kp, bn, npass, splits, 0, dO, N, 1, (long long)M * N, err);
   std::vector<float> h((size_t)splits * M * N);
@@ -933,6 +946,7 @@ as_status as_tc_gemm(int32_t M, int32_t N, int32_t K, const float* A, const floa
     }
   }
   cudaFree(dA); cudaFree(dB); cudaFree(dO); cudaFree(ah); cudaFree(al); cudaFree(bh); cudaFree(bl); cudaFree(err);
+  cudaFree(a2); cudaFree(b2);
   return st;
 }
 

@@ -106,11 +106,11 @@ as_status launch_dump(cudaStream_t s, float* C, int ldc, int d, int r, double* G
 // FP32 mirror of the leading m x m block of G (zero elsewhere).
 as_status launch_gf_mirror(cudaStream_t s, const double* G, float* Gf, int n2, int m);
 
-// tcgen05 GEMM operand (umma.cu): one or two TMA tensor maps over BF16 data
-// (hi, and lo for the split-BF16 form), K innermost, box 64 x box_rows.
+// tcgen05 GEMM operand (umma.cu): TMA tensor maps over the BF16 levels of a
+// split FP32 matrix (m[0] = hi; m[1], m[2] the lower levels), K innermost,
+// box 64 x box_rows.
 struct UmmaOperand {
-  CUtensorMap hi;
-  CUtensorMap lo;
+  CUtensorMap m[3];
 };
 
 // Tensor-core variant of the batched products (BF16 forms): G and X in
@@ -155,13 +155,15 @@ as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m
 bool umma_available();
 as_status umma_make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int kdim, long long ld, int box_rows);
 int umma_bn_for(int N);
-// out[z*plane + m*som + n*son] = sum_{k in split z} A(m,k) B(b_row0 + n, k); npass 1 (BF16) or 3 (split-BF16).
+// out[z*plane + m*som + n*son] = sum_{k in split z} A(m,k) B(b_row0 + n, k); npass 1 (BF16),
+// 3 (two-level split-BF16) or 6 (three-level split-BF16, FP32-equivalent operands).
 as_status launch_umma_gemm(cudaStream_t s, const UmmaOperand& A, const UmmaOperand& B, int M, int N, int K, int bn,
                            int npass, int splits, int b_row0, float* out, long long som, long long son, long long plane,
                            int* err);
-// (hi, lo) BF16 split of an FP32 matrix, optionally transposed (dst(c, r) = src(r, c)).
+// BF16 levels of an FP32 matrix (hi, lo, and optionally a third level lo2),
+// optionally transposed (dst(c, r) = src(r, c)).
 as_status launch_split_bf16(cudaStream_t s, const float* src, long long lds, int rows, int cols, __nv_bfloat16* hi,
-                            __nv_bfloat16* lo, long long ldd, bool transpose);
+                            __nv_bfloat16* lo, long long ldd, bool transpose, __nv_bfloat16* lo2 = nullptr);
 
 // Query helpers.
 as_status launch_shrink_rows(cudaStream_t s, int d, int ell, const double* lam, const double* V, int ldv,

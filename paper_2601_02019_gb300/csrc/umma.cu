@@ -86,13 +86,17 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int bn) {
          | ((uint32_t)(UM >> 4) << 24);// M >> 4
 }
 
+// Operand levels multiplied in each pass: split-BF16 with two levels (npass 3:
+// hi*hi, hi*lo, lo*hi) or three levels (npass 6: every product of levels
+// i + j <= 2, i.e. all terms above 2^-24 relative).
+__device__ __constant__ int kPassA[6] = {0, 0, 1, 0, 1, 2};
+__device__ __constant__ int kPassB[6] = {0, 1, 0, 2, 1, 0};
+
 template <int BN, int NPASS>
-__global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi,
-                                                           const __grid_constant__ CUtensorMap mapA_lo,
-                                                           const __grid_constant__ CUtensorMap mapB_hi,
-                                                           const __grid_constant__ CUtensorMap mapB_lo, int M,
-                                                           int N, int K, int klen, int b_row0, float* out,
-                                                           long long som, long long son, long long plane, int* err) {
+__global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant__ UmmaOperand opA,
+                                                           const __grid_constant__ UmmaOperand opB, int M, int N,
+                                                           int K, int klen, int b_row0, float* out, long long som,
+                                                           long long son, long long plane, int* err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment for the swizzled tiles
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -138,8 +142,9 @@ __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant
       if (!mbar_wait(&empty_bar[s], ph ^ 1u)) { atomicExch(&fail_s, 1); break; }
       const int kt = it / NPASS, pass = it % NPASS;
       const int kx = kb + kt * UK;
-      const CUtensorMap* ma = (pass == 2) ? &mapA_lo : &mapA_hi;
-      const CUtensorMap* mb = (pass == 1) ? &mapB_lo : &mapB_hi;
+      const int la = (NPASS == 1) ? 0 : kPassA[pass], lb = (NPASS == 1) ? 0 : kPassB[pass];
+      const CUtensorMap* ma = &opA.m[la];
+      const CUtensorMap* mb = &opB.m[lb];
       mbar_expect_tx(&full_bar[s], A_BYTES + B_BYTES);
       tma_load_2d(sA + s * A_BYTES, ma, &full_bar[s], kx, m0);
       tma_load_2d(sB + s * B_BYTES, mb, &full_bar[s], kx, b_row0 + n0);
@@ -218,23 +223,35 @@ __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant
 
 namespace {
 
-// x -> (hi, lo) BF16 pair: hi = bf16(x), lo = bf16(x - hi).  Source row-major
-// (rows x cols, lds); destinations row-major with ldd.
+// x -> BF16 levels: l0 = bf16(x), l1 = bf16(x - l0), l2 = bf16(x - l0 - l1)
+// (each residual is exact in FP32).  Source row-major (rows x cols, lds);
+// destinations row-major with ldd; l1 / l2 may be null.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  a = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r1);
+  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+
 __global__ void split_bf16_kernel(const float* __restrict__ src, long long lds, int rows, int cols,
-                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long ldd) {
+                                  __nv_bfloat16* __restrict__ l0, __nv_bfloat16* __restrict__ l1,
+                                  __nv_bfloat16* __restrict__ l2, long long ldd) {
   const long long tot = (long long)rows * cols;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e / cols), c = (int)(e - (long long)r * cols);
-    const float x = src[(long long)r * lds + c];
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    hi[(long long)r * ldd + c] = h;
-    if (lo) lo[(long long)r * ldd + c] = __float2bfloat16_rn(x - __bfloat162float(h));
+    __nv_bfloat16 a, b, d;
+    split3(src[(long long)r * lds + c], a, b, d);
+    const long long o = (long long)r * ldd + c;
+    l0[o] = a;
+    if (l1) l1[o] = b;
+    if (l2) l2[o] = d;
   }
 }
 
 // Transposing split: dst(c, r) = src(r, c); 32 x 32 tiles through shared memory.
 __global__ void split_bf16_t_kernel(const float* __restrict__ src, long long lds, int rows, int cols,
-                                    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long ldd) {
+                                    __nv_bfloat16* __restrict__ l0, __nv_bfloat16* __restrict__ l1,
+                                    __nv_bfloat16* __restrict__ l2, long long ldd) {
   __shared__ float tile[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -245,10 +262,12 @@ __global__ void split_bf16_t_kernel(const float* __restrict__ src, long long lds
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int c = c0 + i, r = r0 + threadIdx.x;
     if (c < cols && r < rows) {
-      const float x = tile[threadIdx.x][i];
-      const __nv_bfloat16 h = __float2bfloat16_rn(x);
-      hi[(long long)c * ldd + r] = h;
-      if (lo) lo[(long long)c * ldd + r] = __float2bfloat16_rn(x - __bfloat162float(h));
+      __nv_bfloat16 a, b, d;
+      split3(tile[threadIdx.x][i], a, b, d);
+      const long long o = (long long)c * ldd + r;
+      l0[o] = a;
+      if (l1) l1[o] = b;
+      if (l2) l2[o] = d;
     }
   }
 }
@@ -284,8 +303,7 @@ as_status launch_umma_t(cudaStream_t s, const UmmaOperand& A, const UmmaOperand&
   const size_t smem = (size_t)STAGES * (UM * UK * 2 + BN * UK * 2) + 1024;
   AS_CUDA_TRY(cudaFuncSetAttribute(umma_gemm_kernel<BN, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
-  umma_gemm_kernel<BN, NPASS><<<grid, 128, smem, s>>>(A.hi, A.lo, B.hi, B.lo, M, N, K, klen, b_row0, out, som, son,
-                                                      plane, err); count_launches(1);
+  umma_gemm_kernel<BN, NPASS><<<grid, 128, smem, s>>>(A, B, M, N, K, klen, b_row0, out, som, son, plane, err); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }
@@ -312,11 +330,12 @@ as_status launch_umma_gemm(cudaStream_t s, const UmmaOperand& A, const UmmaOpera
                            int npass, int splits, int b_row0, float* out, long long som, long long son, long long plane,
                            int* err) {
   if (M <= 0 || N <= 0) return AS_OK;
-  if (npass != 1 && npass != 3) return AS_EINVAL;
+  if (npass != 1 && npass != 3 && npass != 6) return AS_EINVAL;
 #define AS_UMMA_CASE(BNV)                                                                                          \
   if (bn == BNV)                                                                                                   \
-    return npass == 3 ? launch_umma_t<BNV, 3>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err)         \
-                      : launch_umma_t<BNV, 1>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err);
+    return npass == 6   ? launch_umma_t<BNV, 6>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err)       \
+           : npass == 3 ? launch_umma_t<BNV, 3>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err)       \
+                        : launch_umma_t<BNV, 1>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err);
   AS_UMMA_CASE(32)
   AS_UMMA_CASE(64)
   AS_UMMA_CASE(128)
@@ -335,15 +354,15 @@ int umma_bn_for(int N) {
 }
 
 as_status launch_split_bf16(cudaStream_t s, const float* src, long long lds, int rows, int cols, __nv_bfloat16* hi,
-                            __nv_bfloat16* lo, long long ldd, bool transpose) {
+                            __nv_bfloat16* lo, long long ldd, bool transpose, __nv_bfloat16* lo2) {
   if (rows <= 0 || cols <= 0) return AS_OK;
   if (transpose) {
     dim3 grid((cols + 31) / 32, (rows + 31) / 32);
-    split_bf16_t_kernel<<<grid, dim3(32, 8), 0, s>>>(src, lds, rows, cols, hi, lo, ldd); count_launches(1);
+    split_bf16_t_kernel<<<grid, dim3(32, 8), 0, s>>>(src, lds, rows, cols, hi, lo, lo2, ldd); count_launches(1);
   } else {
     const long long tot = (long long)rows * cols;
     const int blocks = (int)std::min<long long>((tot + 255) / 256, 8192);
-    split_bf16_kernel<<<blocks, 256, 0, s>>>(src, lds, rows, cols, hi, lo, ldd); count_launches(1);
+    split_bf16_kernel<<<blocks, 256, 0, s>>>(src, lds, rows, cols, hi, lo, lo2, ldd); count_launches(1);
   }
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;

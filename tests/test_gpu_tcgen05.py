@@ -48,3 +48,16 @@ def test_split_bf16_is_near_fp32(M, N, K, splits):
     err3 = np.abs(got - ref).max()
     assert err3 <= 1e-4 * np.sqrt(K)
     assert err3 < err1 / 50
+
+
+def test_three_level_split_is_fp32_accurate():
+    """npass = 6: the three-level split reaches FP32-product accuracy."""
+    p = _p()
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((512, 1024)).astype(np.float32)
+    B = rng.standard_normal((96, 1024)).astype(np.float32)
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    err6 = np.abs(p.binding.tc_gemm(A, B, npass=6, splits=4) - ref).max()
+    err3 = np.abs(p.binding.tc_gemm(A, B, npass=3, splits=4) - ref).max()
+    assert err6 <= 1e-4 * np.sqrt(1024)
+    assert err6 < err3
