@@ -150,6 +150,8 @@ struct as_sketch {
   __nv_bfloat16 *Chi = nullptr, *Clo = nullptr, *Cthi = nullptr, *Ctlo = nullptr, *Gfh = nullptr, *Gfl = nullptr,
                 *Xh = nullptr, *Xl = nullptr, *Wh = nullptr, *Wl = nullptr;
   __nv_bfloat16 *Cl2 = nullptr, *Ctl2 = nullptr, *Wl2 = nullptr;   // third BF16 level (AS_BF16X6)
+  float* Prb = nullptr;     // split-K planes of the FD rebuild (tensor forms)
+  size_t prb_cap = 0;
   UmmaOperand mCA{}, mCB64{}, mCB256{}, mGA{}, mXB{}, mWA{}, mCtB{};
   TcBatch tcb{};
 };
@@ -157,7 +159,7 @@ struct as_sketch {
 namespace {
 
 void free_all(as_sketch* h) {
-  float* fp[] = {h->C, h->Cnew, h->Wfd, h->stage, h->arena, h->Gf, h->bb.X, h->bb.P};
+  float* fp[] = {h->C, h->Cnew, h->Wfd, h->stage, h->arena, h->Gf, h->bb.X, h->bb.P, h->Prb};
   for (float* p : fp) if (p) cudaFree(p);
   double* dp[] = {h->G, h->Gtmp, h->lam, h->U, h->eigw, h->scal, h->si.Y, h->si.GY, h->si.S, h->si.V,
                   h->si.eigw, h->si.ritz, h->si.WU, h->si.GWU, h->si.tmp, h->x64, h->y64, h->norm2, h->dwork,
@@ -213,12 +215,19 @@ as_status tc_split_rows(as_sketch* h, int r0, int r1) {
                            h->Cl2 ? h->Cl2 + (size_t)r0 * h->ldc : nullptr);
 }
 
+// Longest K range that one TMEM accumulator sums for the products that write
+// state (Gram rows, FD rebuild): longer ranges are split and the partial
+// planes summed in FP64, which keeps the accumulation error of the tensor
+// forms near that of the FP32 form (FP32 partial sums of 64, combined in FP64).
+constexpr int kTcStateChunk = 256;
+
 // G gains the Gram rows/columns of rows [r, r+b) through the tcgen05 GEMM
 // (A = C rows [0, r+b), B = C rows [r, r+b), K = d) and the split reduction.
 as_status tc_gram_rows(as_sketch* h, int r, int b, const UmmaOperand& Bmap, int bn) {
   const int M = r + b;
   const int mt = (M + 127) / 128, nt = (b + bn - 1) / bn, ktiles = h->ldc / 64;
   int S = std::max(1, std::min((2 * 152 + mt * nt - 1) / (mt * nt), ktiles));
+  S = std::max(S, (h->ldc + kTcStateChunk - 1) / kTcStateChunk);
   while (S > 1 && (size_t)S * b * M > h->p_cap) --S;
   const int klen = ((ktiles + S - 1) / S) * 64;
   S = (h->ldc + klen - 1) / klen;
@@ -248,9 +257,22 @@ as_status fd_shrink(as_sketch* h) {
     // C' = W C~ on tcgen05: A = W (rows j, K = p), B = C~^T (rows c, K = p)
     st = launch_split_bf16(h->s, h->Wfd, n2, ell - 1, n2, h->Wh, h->Wl, h->n2p, false, h->Wl2);
     if (st == AS_OK) st = launch_split_bf16(h->s, h->C, h->ldc, n2, d, h->Cthi, h->Ctlo, h->n2p, true, h->Ctl2);
+    // split K (the 2l buffer rows) into chunks of kTcStateChunk; planes summed in FP64
+    int S = (h->n2p + kTcStateChunk - 1) / kTcStateChunk;
+    const int klen = ((h->n2p / 64 + S - 1) / S) * 64;
+    S = (h->n2p + klen - 1) / klen;
+    const size_t need = (size_t)S * (ell - 1) * d;
+    if (st == AS_OK && need > h->prb_cap) {
+      if (h->Prb) cudaFree(h->Prb);
+      h->Prb = nullptr;
+      h->prb_cap = 0;
+      st = dalloc(&h->Prb, need);
+      if (st == AS_OK) h->prb_cap = need;
+    }
     if (st == AS_OK)
-      st = launch_umma_gemm(h->s, h->mWA, h->mCtB, ell - 1, d, h->n2p, 256, h->dpass, 1, 0, h->Cnew, h->ldc, 1, 0,
-                            h->dstatus);
+      st = launch_umma_gemm(h->s, h->mWA, h->mCtB, ell - 1, d, h->n2p, 256, h->dpass, S, 0, h->Prb, d, 1,
+                            (long long)(ell - 1) * d, h->dstatus);
+    if (st == AS_OK) st = launch_plane_sum(h->s, h->Prb, S, (long long)(ell - 1) * d, ell - 1, d, d, h->Cnew, h->ldc);
     if (st != AS_OK) return st;
   } else if (ell > 1) {
     st = gemm_strided<float, float, float>(h->s, ell - 1, d, n2, h->Wfd, n2, 1, h->C, h->ldc, 1, h->Cnew, h->ldc,
@@ -630,7 +652,8 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   ALLOC(h->norm2, (size_t)bmax);
   ALLOC(h->Gf, (size_t)n2 * n2);
   h->bb.max_splits = 16;
-  h->p_cap = std::max((size_t)h->bb.max_splits * n2 * 3 * bmax, (size_t)64 * bmax * n2);
+  h->p_cap = std::max({(size_t)h->bb.max_splits * n2 * 3 * bmax, (size_t)64 * bmax * n2,
+                       (size_t)16 * ell * ell});
   ALLOC(h->bb.X, (size_t)n2 * 3 * bmax);
   ALLOC(h->bb.P, h->p_cap);
   ALLOC(h->bb.sig2, (size_t)bmax);

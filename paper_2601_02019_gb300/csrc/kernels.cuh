@@ -89,6 +89,9 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
 int skinny_splits(int M, int N, int K);
 as_status launch_skinny_partial(cudaStream_t s, int M, int N, int K, int* S, const float* A, long long lda,
                                 const float* X, long long ldx, float* P, long long ldp, long long plane);
+// out[r*ldo + c] = sum_s P[s*plane + r*ldp + c], summed in FP64.
+as_status launch_plane_sum(cudaStream_t s, const float* P, int S, long long plane, int rows, int cols, long long ldp,
+                           float* out, long long ldo);
 // G[p][r+t] = sum_s P[s][t*ldp + p] (FP64), mirrored to G[r+t][p] for p < r.
 as_status launch_gram_reduce(cudaStream_t s, const float* P, long long ldp, long long plane, int S, int mrows, int r,
                              int b, double* G, int n2);

@@ -81,7 +81,29 @@ __global__ void gram_reduce_kernel(const float* __restrict__ P, long long ldp, l
   }
 }
 
+// out[r*ldo + c] = sum_s P[s*plane + r*ldp + c] (FP64 sum, FP32 result).
+__global__ void plane_sum_kernel(const float* __restrict__ P, int S, long long plane, int rows, int cols, long long ldp,
+                                 float* __restrict__ out, long long ldo) {
+  const long long tot = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / cols), c = (int)(e - (long long)r * cols);
+    double v = 0.0;
+    for (int s = 0; s < S; ++s) v += (double)P[(long long)s * plane + (long long)r * ldp + c];
+    out[(long long)r * ldo + c] = (float)v;
+  }
+}
+
 }  // namespace
+
+as_status launch_plane_sum(cudaStream_t s, const float* P, int S, long long plane, int rows, int cols, long long ldp,
+                           float* out, long long ldo) {
+  if (rows <= 0 || cols <= 0) return AS_OK;
+  const long long tot = (long long)rows * cols;
+  const int blocks = (int)std::min<long long>((tot + 255) / 256, 8192);
+  plane_sum_kernel<<<blocks, 256, 0, s>>>(P, S, plane, rows, cols, ldp, out, ldo); count_launches(1);
+  AS_CUDA_TRY(cudaGetLastError());
+  return AS_OK;
+}
 
 int skinny_splits(int M, int N, int K) {
   const int tiles = ((M + SBM - 1) / SBM) * ((N + SBN - 1) / SBN);
