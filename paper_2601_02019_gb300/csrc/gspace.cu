@@ -45,12 +45,18 @@ __global__ void truncate_kernel(float* C, int ldc, int d, int r0, int r1, double
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot_c;
        e += (long long)gridDim.x * blockDim.x)
     C[(long long)r0 * ldc + e] = 0.f;
-  // rows and columns >= r0 of G
-  const long long tot_g = (long long)n2 * n2;
+  // G: rows [r0, n2) in full, then columns [r0, n2) of rows [0, r0)
+  const long long w = n2 - r0;
+  const long long tot_g = w * n2 + (long long)r0 * w;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot_g;
        e += (long long)gridDim.x * blockDim.x) {
-    const int p = (int)(e / n2), q = (int)(e % n2);
-    if (p >= r0 || q >= r0) G[e] = 0.0;
+    if (e < w * n2) {
+      G[(long long)r0 * n2 + e] = 0.0;
+    } else {
+      const long long f = e - w * n2;
+      const long long p = f / w, q = r0 + f % w;
+      G[p * n2 + q] = 0.0;
+    }
   }
 }
 

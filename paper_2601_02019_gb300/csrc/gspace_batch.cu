@@ -134,7 +134,9 @@ __global__ void __launch_bounds__(512) batch_orth_kernel(const float* __restrict
     }
     return;
   }
-  // Euclidean SVQB of the pair: pass 0 reads Y, pass 1 re-orthonormalises X
+  // Euclidean SVQB of the pair: pass 0 reads Y, pass 1 re-orthonormalises X.
+  // The 2 x 2 eigenproblem is solved once (thread 0, FP64) and broadcast.
+  __shared__ float coef[4];
   for (int pass = 0; pass < 2; ++pass) {
     const float* s0 = pass ? x0 : y0;
     const float* s1 = pass ? x1 : y1;
@@ -144,12 +146,17 @@ __global__ void __launch_bounds__(512) batch_orth_kernel(const float* __restrict
       f00 = fmaf(a, a, f00); f01 = fmaf(a, b, f01); f11 = fmaf(b, b, f11);
     }
     const double s00 = block_sum((double)f00, red), s01 = block_sum((double)f01, red), s11 = block_sum((double)f11, red);
-    double l0, l1, v00, v01, v10, v11;
-    eig2(s00, s01, s11, l0, l1, v00, v01, v10, v11);
-    const double tol = 1e-13 * fmax(l0, 0.0);
-    const float a0 = (l0 > tol && l0 > 0) ? (float)(1.0 / sqrt(l0)) : 0.f;
-    const float a1 = (l1 > tol && l1 > 0) ? (float)(1.0 / sqrt(l1)) : 0.f;
-    const float c00 = (float)v00 * a0, c10 = (float)v10 * a0, c01 = (float)v01 * a1, c11 = (float)v11 * a1;
+    if (threadIdx.x == 0) {
+      double l0, l1, v00, v01, v10, v11;
+      eig2(s00, s01, s11, l0, l1, v00, v01, v10, v11);
+      const double tol = 1e-13 * fmax(l0, 0.0);
+      const double a0 = (l0 > tol && l0 > 0) ? 1.0 / sqrt(l0) : 0.0;
+      const double a1 = (l1 > tol && l1 > 0) ? 1.0 / sqrt(l1) : 0.0;
+      coef[0] = (float)(v00 * a0); coef[1] = (float)(v10 * a0);
+      coef[2] = (float)(v01 * a1); coef[3] = (float)(v11 * a1);
+    }
+    __syncthreads();
+    const float c00 = coef[0], c10 = coef[1], c01 = coef[2], c11 = coef[3];
     for (int p = threadIdx.x; p < n2; p += blockDim.x) {
       float o0v = 0.f, o1v = 0.f;
       if (p < m) {
@@ -347,37 +354,46 @@ __global__ void rayleigh_ritz_kernel(int n2, int m, int k, const double* W, cons
 __global__ void rr2_kernel(int n2, int m, const double* Y, const double* GY, double* ritz, double* WU, double* GWU,
                            int* status) {
   __shared__ double red[32];
+  __shared__ double cf[8];   // (v00, v10, v01, v11) * (a0, a0, a1, a1), then U
   double s00 = 0, s01 = 0, s11 = 0;
   for (int p = threadIdx.x; p < m; p += blockDim.x) {
     const double a = Y[2 * p], b = Y[2 * p + 1], ga = GY[2 * p], gb = GY[2 * p + 1];
     s00 += a * ga; s01 += 0.5 * (a * gb + b * ga); s11 += b * gb;
   }
   s00 = block_sum(s00, red); s01 = block_sum(s01, red); s11 = block_sum(s11, red);
-  double l0, l1, v00, v01, v10, v11;
-  eig2(s00, s01, s11, l0, l1, v00, v01, v10, v11);
-  const double a0 = (l0 > 0.0) ? 1.0 / sqrt(l0) : 0.0;
-  const double a1 = (l1 > 1e-13 * l0 && l1 > 0.0) ? 1.0 / sqrt(l1) : 0.0;
+  if (threadIdx.x == 0) {
+    double l0, l1, v00, v01, v10, v11;
+    eig2(s00, s01, s11, l0, l1, v00, v01, v10, v11);
+    const double a0 = (l0 > 0.0) ? 1.0 / sqrt(l0) : 0.0;
+    const double a1 = (l1 > 1e-13 * l0 && l1 > 0.0) ? 1.0 / sqrt(l1) : 0.0;
+    cf[0] = v00 * a0; cf[1] = v10 * a0; cf[2] = v01 * a1; cf[3] = v11 * a1;
+  }
+  __syncthreads();
+  const double w00 = cf[0], w10 = cf[1], w01 = cf[2], w11 = cf[3];
   // G W columns
   double m00 = 0, m01 = 0, m11 = 0;
   for (int p = threadIdx.x; p < m; p += blockDim.x) {
     const double ga = GY[2 * p], gb = GY[2 * p + 1];
-    const double g0 = (ga * v00 + gb * v10) * a0, g1 = (ga * v01 + gb * v11) * a1;
+    const double g0 = ga * w00 + gb * w10, g1 = ga * w01 + gb * w11;
     m00 += g0 * g0; m01 += g0 * g1; m11 += g1 * g1;
   }
   m00 = block_sum(m00, red); m01 = block_sum(m01, red); m11 = block_sum(m11, red);
-  double r0, r1, u00, u01, u10, u11;
-  eig2(m00, m01, m11, r0, r1, u00, u01, u10, u11);
   if (threadIdx.x == 0) {
+    double r0, r1, u00, u01, u10, u11;
+    eig2(m00, m01, m11, r0, r1, u00, u01, u10, u11);
     ritz[0] = r0;
-    ritz[1] = (a1 > 0.0) ? r1 : 0.0;
+    ritz[1] = (w01 != 0.0 || w11 != 0.0) ? r1 : 0.0;
     if (!(r0 == r0)) set_status(status, AS_ENUMERIC);
+    cf[4] = u00; cf[5] = u10; cf[6] = u01; cf[7] = u11;
   }
+  __syncthreads();
+  const double u00 = cf[4], u10 = cf[5], u01 = cf[6], u11 = cf[7];
   for (int p = threadIdx.x; p < n2; p += blockDim.x) {
     double w0 = 0, w1 = 0, g0 = 0, g1 = 0;
     if (p < m) {
       const double a = Y[2 * p], b = Y[2 * p + 1], ga = GY[2 * p], gb = GY[2 * p + 1];
-      const double x0 = (a * v00 + b * v10) * a0, x1 = (a * v01 + b * v11) * a1;      // W
-      const double y0 = (ga * v00 + gb * v10) * a0, y1 = (ga * v01 + gb * v11) * a1;  // G W
+      const double x0 = a * w00 + b * w10, x1 = a * w01 + b * w11;      // W
+      const double y0 = ga * w00 + gb * w10, y1 = ga * w01 + gb * w11;  // G W
       w0 = x0 * u00 + x1 * u10; w1 = x0 * u01 + x1 * u11;
       g0 = y0 * u00 + y1 * u10; g1 = y0 * u01 + y1 * u11;
     }
@@ -405,22 +421,29 @@ __global__ void dump_partial_kernel(const float* __restrict__ C, int ldc, int d,
   const int chunk = (r + kDumpChunks - 1) / kDumpChunks;
   const int pb = s * chunk, pe = min(r, pb + chunk);
   double z[8], y[8];
+  float zf[8], yf[8];
 #pragma unroll
-  for (int a = 0; a < 8; ++a) { z[a] = 0.0; y[a] = 0.0; }
+  for (int a = 0; a < 8; ++a) { z[a] = 0.0; y[a] = 0.0; zf[a] = 0.f; yf[a] = 0.f; }
+  int cnt = 0;
   for (int p = pb; p < pe; ++p) {
-    const double cv = C[(size_t)p * ldc + c];
+    const float cv = C[(size_t)p * ldc + c];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
       if (a < na) {
-        z[a] += cv * WU[(size_t)p * k + a0 + a];
-        y[a] += cv * GWU[(size_t)p * k + a0 + a];
+        zf[a] = fmaf(cv, (float)WU[(size_t)p * k + a0 + a], zf[a]);
+        yf[a] = fmaf(cv, (float)GWU[(size_t)p * k + a0 + a], yf[a]);
       }
+    if (++cnt == 64) {   // FP32 partial sums of 64 rows, combined in FP64
+      cnt = 0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) { z[a] += zf[a]; y[a] += yf[a]; zf[a] = 0.f; yf[a] = 0.f; }
+    }
   }
 #pragma unroll
   for (int a = 0; a < 8; ++a)
     if (a < na) {
-      Zp[((size_t)s * d + c) * xi + a0 + a] = z[a];
-      Yp[((size_t)s * xi + a0 + a) * d + c] = y[a];
+      Zp[((size_t)s * d + c) * xi + a0 + a] = z[a] + zf[a];
+      Yp[((size_t)s * xi + a0 + a) * d + c] = y[a] + yf[a];
     }
 }
 
