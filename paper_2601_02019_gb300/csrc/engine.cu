@@ -219,7 +219,17 @@ as_status tc_split_rows(as_sketch* h, int r0, int r1) {
 // state (Gram rows, FD rebuild): longer ranges are split and the partial
 // planes summed in FP64, which keeps the accumulation error of the tensor
 // forms near that of the FP32 form (FP32 partial sums of 64, combined in FP64).
-constexpr int kTcStateChunk = 256;
+constexpr int kTcStateChunk = 64;
+
+as_status ensure_prb(as_sketch* h, size_t need) {
+  if (need <= h->prb_cap) return AS_OK;
+  if (h->Prb) cudaFree(h->Prb);
+  h->Prb = nullptr;
+  h->prb_cap = 0;
+  as_status st = dalloc(&h->Prb, need);
+  if (st == AS_OK) h->prb_cap = need;
+  return st;
+}
 
 // G gains the Gram rows/columns of rows [r, r+b) through the tcgen05 GEMM
 // (A = C rows [0, r+b), B = C rows [r, r+b), K = d) and the split reduction.
@@ -228,13 +238,19 @@ as_status tc_gram_rows(as_sketch* h, int r, int b, const UmmaOperand& Bmap, int 
   const int mt = (M + 127) / 128, nt = (b + bn - 1) / bn, ktiles = h->ldc / 64;
   int S = std::max(1, std::min((2 * 152 + mt * nt - 1) / (mt * nt), ktiles));
   S = std::max(S, (h->ldc + kTcStateChunk - 1) / kTcStateChunk);
-  while (S > 1 && (size_t)S * b * M > h->p_cap) --S;
   const int klen = ((ktiles + S - 1) / S) * 64;
   S = (h->ldc + klen - 1) / klen;
-  as_status st = launch_umma_gemm(h->s, h->mCA, Bmap, M, b, h->ldc, bn, h->dpass, S, r, h->bb.P, 1, M,
-                                  (long long)b * M, h->dstatus);
+  as_status st = AS_OK;
+  float* P = h->bb.P;
+  const size_t need = (size_t)S * b * M;
+  if (need > h->p_cap) {
+    st = ensure_prb(h, need);
+    if (st != AS_OK) return st;
+    P = h->Prb;
+  }
+  st = launch_umma_gemm(h->s, h->mCA, Bmap, M, b, h->ldc, bn, h->dpass, S, r, P, 1, M, (long long)b * M, h->dstatus);
   if (st != AS_OK) return st;
-  return launch_gram_reduce(h->s, h->bb.P, M, (long long)b * M, S, M, r, b, h->G, h->n2);
+  return launch_gram_reduce(h->s, P, M, (long long)b * M, S, M, r, b, h->G, h->n2);
 }
 
 // Algorithm 4 lines 3-4: FD shrink of the full buffer through its Gram.
@@ -262,13 +278,7 @@ as_status fd_shrink(as_sketch* h) {
     const int klen = ((h->n2p / 64 + S - 1) / S) * 64;
     S = (h->n2p + klen - 1) / klen;
     const size_t need = (size_t)S * (ell - 1) * d;
-    if (st == AS_OK && need > h->prb_cap) {
-      if (h->Prb) cudaFree(h->Prb);
-      h->Prb = nullptr;
-      h->prb_cap = 0;
-      st = dalloc(&h->Prb, need);
-      if (st == AS_OK) h->prb_cap = need;
-    }
+    if (st == AS_OK) st = ensure_prb(h, need);
     if (st == AS_OK)
       st = launch_umma_gemm(h->s, h->mWA, h->mCtB, ell - 1, d, h->n2p, 256, h->dpass, S, 0, h->Prb, d, 1,
                             (long long)(ell - 1) * d, h->dstatus);
@@ -406,20 +416,45 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
   as_status st = launch_ingest(h->s, src, d, b, d, h->C, h->ldc, r0, h->norm2, h->bad);
   if (st != AS_OK) return st;
   if (h->prof) h->prof->end(PK_INGEST, h->s, 2.0 * b * (double)d, 8.0 * b * (double)d);
-  st = fetch(h, h->norm2, b);
+  st = tc_split_rows(h, r0, r0 + b);
   if (st != AS_OK) return st;
+  // line 1 for the whole block: G gains the new rows and columns (a rejected
+  // row was ingested as zeros, so nothing non-finite reaches the products)
+  if (h->prof) h->prof->begin(PK_GRAM, h->s);
+  st = h->tc ? tc_gram_rows(h, r0, b, h->mCB64, 64)
+             : launch_gram_rows_skinny(h->s, h->C, h->ldc, d, r0, b, h->G, n2, h->bb.P, h->p_cap);
+  if (st != AS_OK) return st;
+  if (h->prof)
+    h->prof->end(PK_GRAM, h->s, 2.0 * (r0 + b) * (double)b * d, 4.0 * (r0 + b) * (double)d + 8.0 * (r0 + b) * b);
+  const bool fills_all = (r0 + b == n2);
+  const int nbb = fills_all ? b - 1 : b;   // batched rows (the filling row needs the shrink first)
+  if (nbb > 0) {
+    st = h->tc ? launch_gbf16_mirror(h->s, h->G, n2, r0 + b, h->Gfh, h->Gfl, h->n2p)
+               : launch_gf_mirror(h->s, h->G, h->Gf, n2, r0 + b);
+    if (st != AS_OK) return st;
+    st = launch_batch_gspace(h->s, h->Gf, n2, r0, nbb, h->k_pi, h->q, h->key, (uint64_t)(h->T + 1), h->bb,
+                             h->prof, h->tc ? &h->tcb : nullptr);
+    if (st != AS_OK) return st;
+  }
+  // one synchronisation per block: row norms, power-iteration values, Ritz values
+  AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf, h->norm2, b * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  if (nbb > 0) {
+    AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf + b, h->bb.sig2, nbb * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf + b + nbb, h->bb.ritz, 2 * nbb * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  }
+  AS_CUDA_TRY(cudaStreamSynchronize(h->s));
   std::vector<double> a2(h->h_buf, h->h_buf + b);
+  std::vector<double> sig2(h->h_buf + b, h->h_buf + b + nbb), ritz(h->h_buf + b + nbb, h->h_buf + b + 3 * nbb);
   int bb = b;
   for (int t = 0; t < b; ++t)
     if (!std::isfinite(a2[t])) { bb = t; *bad_row = true; break; }
   if (*bad_row) {
     AS_CUDA_TRY(cudaMemsetAsync(h->bad, 0, sizeof(int), h->s));
     st = launch_truncate(h->s, h->C, h->ldc, d, r0 + bb, r0 + b, h->G, n2);
+    if (st == AS_OK) st = tc_split_rows(h, r0 + bb, r0 + b);
     if (st != AS_OK) return st;
     if (bb == 0) { *used = 0; return AS_OK; }
   }
-  st = tc_split_rows(h, r0, r0 + b);
-  if (st != AS_OK) return st;
   // thresholds before each row (Algorithm 8 lines 2-3)
   std::vector<double> Ft(bb), th(bb);
   double F = h->F;
@@ -428,29 +463,8 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
     Ft[t] = F;
     th[t] = (h->mode == AS_PERSISTENT) ? h->eps * F : h->theta;
   }
-  // line 1 for the whole block: G gains the new rows and columns
-  if (h->prof) h->prof->begin(PK_GRAM, h->s);
-  st = h->tc ? tc_gram_rows(h, r0, bb, h->mCB64, 64)
-             : launch_gram_rows_skinny(h->s, h->C, h->ldc, d, r0, bb, h->G, n2, h->bb.P, h->p_cap);
-  if (st != AS_OK) return st;
-  if (h->prof)
-    h->prof->end(PK_GRAM, h->s, 2.0 * (r0 + bb) * (double)bb * d, 4.0 * (r0 + bb) * (double)d + 8.0 * (r0 + bb) * bb);
   const bool fills = (r0 + bb == n2);
-  const int nb = fills ? bb - 1 : bb;
-  std::vector<double> sig2(nb), ritz(2 * (size_t)nb);
-  if (nb > 0) {
-    st = h->tc ? launch_gbf16_mirror(h->s, h->G, n2, r0 + bb, h->Gfh, h->Gfl, h->n2p)
-               : launch_gf_mirror(h->s, h->G, h->Gf, n2, r0 + bb);
-    if (st != AS_OK) return st;
-    st = launch_batch_gspace(h->s, h->Gf, n2, r0, nb, h->k_pi, h->q, h->key, (uint64_t)(h->T + 1), h->bb,
-                             h->prof, h->tc ? &h->tcb : nullptr);
-    if (st != AS_OK) return st;
-    AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf, h->bb.sig2, nb * sizeof(double), cudaMemcpyDeviceToHost, h->s));
-    AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf + nb, h->bb.ritz, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, h->s));
-    AS_CUDA_TRY(cudaStreamSynchronize(h->s));
-    std::copy(h->h_buf, h->h_buf + nb, sig2.begin());
-    std::copy(h->h_buf + nb, h->h_buf + 3 * nb, ritz.begin());
-  }
+  const int nb = std::min(nbb, fills ? bb - 1 : bb);
   // scan for the first state-changing row
   int tstar = -1, gate_known = -1;
   double sig2_star = 0.0;
@@ -514,9 +528,9 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
     return finish_row(h, h->T, h->theta, -1, 0.0);
   }
   // large buffers reuse the batch's FP32-iterated basis for the k = 2 step
-  const int bcol = h->big ? nb + 2 * tstar : -1;
+  const int bcol = h->big ? nbb + 2 * tstar : -1;
   if (h->prof) h->prof->begin(PK_EVENT, h->s);
-  st = finish_row(h, h->T, h->theta, gate_known, sig2_star, bcol, 3 * nb);
+  st = finish_row(h, h->T, h->theta, gate_known, sig2_star, bcol, 3 * nbb);
   if (h->prof) h->prof->end(PK_EVENT, h->s, 0.0, 0.0);
   return st;
 }

@@ -27,15 +27,16 @@ __global__ void ingest_kernel(const float* __restrict__ rows, long long ld_in, i
   int nonfinite = 0;
   for (int c = threadIdx.x; c < d; c += blockDim.x) {
     const float v = src[c];
-    nonfinite |= !isfinite(v);
-    dst[c] = v;
-    s += (double)v * (double)v;
+    const bool ok = isfinite(v);
+    nonfinite |= !ok;
+    dst[c] = ok ? v : 0.f;   // a rejected row never reaches the products as NaN / Inf
+    s += ok ? (double)v * (double)v : 0.0;
   }
   __shared__ double red[32];
   s = block_sum(s, red);
   nonfinite = __syncthreads_or(nonfinite);
   if (threadIdx.x == 0) {
-    norm2[t] = s;
+    norm2[t] = nonfinite ? __longlong_as_double(0x7ff8000000000000ll) : s;   // NaN marks the row
     if (nonfinite) atomicExch(bad, 1);
   }
 }

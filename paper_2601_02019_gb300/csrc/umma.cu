@@ -301,8 +301,14 @@ as_status launch_umma_t(cudaStream_t s, const UmmaOperand& A, const UmmaOperand&
   S = (K + klen - 1) / klen;
   dim3 grid((M + UM - 1) / UM, (N + BN - 1) / BN, S);
   const size_t smem = (size_t)STAGES * (UM * UK * 2 + BN * UK * 2) + 1024;
-  AS_CUDA_TRY(cudaFuncSetAttribute(umma_gemm_kernel<BN, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
+  static int configured_device = -1;   // the attribute is per device; set it once
+  int dev = 0;
+  AS_CUDA_TRY(cudaGetDevice(&dev));
+  if (configured_device != dev) {
+    AS_CUDA_TRY(cudaFuncSetAttribute(umma_gemm_kernel<BN, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    configured_device = dev;
+  }
   umma_gemm_kernel<BN, NPASS><<<grid, 128, smem, s>>>(A, B, M, N, K, klen, b_row0, out, som, son, plane, err); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
