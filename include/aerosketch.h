@@ -166,6 +166,12 @@ as_status sketch_query_gram(as_sketch* h, double* out);
  * and the row count r to host memory.  Synchronises. */
 as_status sketch_get_buffer(as_sketch* h, float* out, int32_t* r_out);
 
+/* Copy the maintained Gram matrix G = C C^T of the buffer (2l x 2l FP64,
+ * row-major) to host memory.  G feeds the power iteration, the simultaneous
+ * iteration and the FD shrink's eigendecomposition; it should equal the Gram
+ * of the rows sketch_get_buffer returns.  Synchronises. */
+as_status sketch_get_gram(as_sketch* h, double* out);
+
 /* Merge src into dst by decomposability (Appendix E, the sum of per-part
  * errors bounds the error of the union): dst's query then covers both
  * streams.  Requires equal d.  Not implemented in this build: AS_ENOTSUP. */

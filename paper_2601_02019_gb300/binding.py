@@ -16,7 +16,7 @@ AS_FP32_PLAIN, AS_BF16, AS_BF16X3, AS_BF16X6 = 0, 1, 2, 3
 AS_TRACE_DECISIONS = 0x1
 AS_PROFILE = 0x2
 
-EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram", "sketch_get_buffer",
+EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram", "sketch_get_buffer", "sketch_get_gram",
             "sketch_merge", "sketch_stats", "sketch_trace", "sketch_profile", "sketch_profile_reset",
             "sketch_destroy", "as_symeig", "as_tc_gemm", "as_status_str")
 
@@ -72,6 +72,7 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.sketch_query.argtypes = [P, I64, P, I64, ct.POINTER(I32)]
     L.sketch_query_gram.argtypes = [P, P]
     L.sketch_get_buffer.argtypes = [P, P, ct.POINTER(I32)]
+    L.sketch_get_gram.argtypes = [P, P]
     L.sketch_merge.argtypes = [P, P]
     L.sketch_stats.argtypes = [P, ct.POINTER(AsStats)]
     L.sketch_trace.argtypes = [P, ct.POINTER(AsEvent), I64, ct.POINTER(I64)]
@@ -163,6 +164,11 @@ class Sketch:
         r = ct.c_int32()
         _check(lib().sketch_get_buffer(self._h, ct.c_void_p(out.ctypes.data), ct.byref(r)), "sketch_get_buffer")
         return out, r.value
+
+    def gram(self) -> np.ndarray:
+        out = np.zeros((2 * self.ell, 2 * self.ell), dtype=np.float64)
+        _check(lib().sketch_get_gram(self._h, ct.c_void_p(out.ctypes.data)), "sketch_get_gram")
+        return out
 
     def stats(self) -> dict:
         s = AsStats()

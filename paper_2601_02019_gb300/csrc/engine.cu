@@ -845,6 +845,13 @@ as_status sketch_get_buffer(as_sketch* h, float* out, int32_t* r_out) {
   return AS_OK;
 }
 
+as_status sketch_get_gram(as_sketch* h, double* out) {
+  if (!h || !out) return AS_EINVAL;
+  AS_CUDA_TRY(cudaStreamSynchronize(h->s));
+  cudaError_t e = cudaMemcpy(out, h->G, (size_t)h->n2 * h->n2 * sizeof(double), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? AS_OK : as_from_cuda(e);
+}
+
 as_status sketch_merge(as_sketch* dst, const as_sketch* src) {
   if (!dst || !src) return AS_EINVAL;
   if (dst->d != src->d) return AS_EINVAL;
