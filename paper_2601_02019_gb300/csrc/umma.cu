@@ -9,6 +9,13 @@
 // x = hi + lo with hi = bf16(x), lo = bf16(x - hi), and the block accumulates
 // A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo*lo term is below FP32 resolution).
 //
+// Split-BF16 passes accumulate in two TMEM accumulators: the hi*hi products in
+// one, every lower-order product in the other, added in the epilogue.  The
+// tensor core's FP32 accumulation does not round to nearest, so each
+// accumulate step can lose up to an ulp of the running sum; keeping the small
+// correction terms out of the large accumulator makes their steps cost an ulp
+// of a value ~2^8 smaller.
+//
 // One CTA computes a 128 x BN tile for one K split with 4 warps:
 //   warp 0 (one lane)  TMA producer over a STAGES-deep shared-memory ring,
 //   warp 1 (one lane)  issues tcgen05.mma (cta_group::1, kind::f16, M = 128),
@@ -122,9 +129,11 @@ __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant
     fail_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  constexpr int NACC = (NPASS > 1) ? 2 : 1;
   if (warp == 2) {
-    // TMEM accumulator: BN columns (a power of two >= 32)
-    constexpr uint32_t ncols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+    // TMEM accumulators: NACC x BN columns, allocated as a power of two >= 32
+    constexpr uint32_t need = (uint32_t)(NACC * BN);
+    constexpr uint32_t ncols = need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : (need <= 256 ? 256 : 512)));
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
                  "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -159,13 +168,16 @@ __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant
       if (!mbar_wait(&full_bar[s], ph)) { atomicExch(&fail_s, 1); ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+      const int pass = it % NPASS;
+      const uint32_t dst = tmem + ((NACC == 2 && pass > 0) ? (uint32_t)BN : 0u);
+      const bool first = (NACC == 2 && pass > 0) ? (it == 1) : (it == 0);   // first MMA into this accumulator
 #pragma unroll
       for (int kk = 0; kk < UK / 16; ++kk) {
         const uint64_t da = smem_desc(a0 + kk * 32), db = smem_desc(b0 + kk * 32);
-        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+        const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
             "l"(da), "l"(db), "r"(idesc), "r"(acc));
       }
       // the stage is free once these MMAs have read it
@@ -189,31 +201,37 @@ __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant
   float* o = out + (long long)z * plane;
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 16) {
-    uint32_t r[16];
-    if (have) {
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    } else {
+    float v[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) r[j] = 0u;
+    for (int j = 0; j < 16; ++j) v[j] = 0.f;
+    if (have) {
+#pragma unroll
+      for (int a = 0; a < NACC; ++a) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + a * BN);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(r[j]);
+      }
     }
     if (gm < M) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int gn = n0 + c0 + j;
-        if (gn < N) o[(long long)gm * som + (long long)gn * son] = __uint_as_float(r[j]);
+        if (gn < N) o[(long long)gm * som + (long long)gn * son] = v[j];
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 2) {
-    constexpr uint32_t ncols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+    constexpr uint32_t need = (uint32_t)(NACC * BN);
+    constexpr uint32_t ncols = need <= 32 ? 32 : (need <= 64 ? 64 : (need <= 128 ? 128 : (need <= 256 ? 256 : 512)));
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
   }
   if (threadIdx.x == 0 && fail_s && err) atomicExch(err, AS_ETIMEOUT);

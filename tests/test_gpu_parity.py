@@ -240,3 +240,20 @@ def test_bf16_form_error_is_stated_and_bounded(d, ell, n, r):
     eo = cov_err(A, AeroSketch(d, ell, seed=2).run(A.astype(np.float64)).query(), AtA)
     print(f"BF16 form: cov-err {eg:.6e}, oracle {eo:.6e}, relative deviation {abs(eg - eo) / eo:.3e}")
     assert eg <= 2.0 / ell
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 5e-7), (3, 2e-6), (2, 1e-5)])
+@pytest.mark.parametrize("n", [40, 200, 1000])
+def test_gram_matches_buffer(prec, tol, n):
+    """Invariant of the engine: the maintained G equals C C^T of the stored
+    buffer (through ingest, dumps, shrinks), in every precision form."""
+    p = _gpu()
+    A = low_rank_noisy(n, 256, 20, spectrum("geometric", 20), noise=0.01, seed=1)
+    s = p.Sketch(256, 32, seed=1, prec=prec)
+    s.update(A)
+    C, r = s.buffer()
+    C = C.astype(np.float64)
+    E = C @ C.T
+    G = s.gram()
+    assert np.abs(G - E).max() <= tol * np.abs(E).max()
+    assert np.abs(G[r:]).max() == 0.0 and np.abs(G[:, r:]).max() == 0.0
