@@ -248,7 +248,8 @@ as_status tc_gram_rows(as_sketch* h, int r, int b, const UmmaOperand& Bmap, int 
     if (st != AS_OK) return st;
     P = h->Prb;
   }
-  st = launch_umma_gemm(h->s, h->mCA, Bmap, M, b, h->ldc, bn, h->dpass, S, r, P, 1, M, (long long)b * M, h->dstatus);
+  st = launch_umma_gemm(h->s, h->mCA, Bmap, M, b, h->ldc, bn, h->dpass, S, r, P, 1, M, (long long)b * M, h->dstatus,
+                        bn == 64);
   if (st != AS_OK) return st;
   return launch_gram_reduce(h->s, P, M, (long long)b * M, S, M, r, b, h->G, h->n2);
 }
@@ -280,8 +281,8 @@ as_status fd_shrink(as_sketch* h) {
     const size_t need = (size_t)S * (ell - 1) * d;
     if (st == AS_OK) st = ensure_prb(h, need);
     if (st == AS_OK)
-      st = launch_umma_gemm(h->s, h->mWA, h->mCtB, ell - 1, d, h->n2p, 256, h->dpass, S, 0, h->Prb, d, 1,
-                            (long long)(ell - 1) * d, h->dstatus);
+      st = launch_umma_gemm(h->s, h->mWA, h->mCtB, ell - 1, d, h->n2p, 64, h->dpass, S, 0, h->Prb, d, 1,
+                            (long long)(ell - 1) * d, h->dstatus, true);
     if (st == AS_OK) st = launch_plane_sum(h->s, h->Prb, S, (long long)(ell - 1) * d, ell - 1, d, d, h->Cnew, h->ldc);
     if (st != AS_OK) return st;
   } else if (ell > 1) {
@@ -293,7 +294,7 @@ as_status fd_shrink(as_sketch* h) {
   AS_CUDA_TRY(cudaMemsetAsync(h->G, 0, (size_t)n2 * n2 * sizeof(double), h->s));
   if (ell > 1 && h->tc) {
     st = tc_split_rows(h, 0, n2);
-    if (st == AS_OK) st = tc_gram_rows(h, 0, ell - 1, h->mCB256, 256);
+    if (st == AS_OK) st = tc_gram_rows(h, 0, ell - 1, h->mCB64, 64);
     if (st != AS_OK) return st;
   } else if (ell > 1) {
     st = gemm_strided<float, float, double>(h->s, ell - 1, ell - 1, d, h->C, h->ldc, 1, h->C, 1, h->ldc, h->G, n2,
@@ -713,7 +714,7 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
     mk(h->mGA, h->Gfh, h->Gfl, nullptr, (int)(gN / h->n2p), h->n2p, h->n2p, 128);
     mk(h->mXB, h->Xh, h->Xl, nullptr, (int)(xN / h->n2p), h->n2p, h->n2p, 192);
     mk(h->mWA, h->Wh, h->Wl, h->Wl2, (int)(wN / h->n2p), h->n2p, h->n2p, 128);
-    mk(h->mCtB, h->Cthi, h->Ctlo, h->Ctl2, (int)(ctN / h->n2p), h->n2p, h->n2p, 256);
+    mk(h->mCtB, h->Cthi, h->Ctlo, h->Ctl2, (int)(ctN / h->n2p), h->n2p, h->n2p, 64);
     h->tcb = TcBatch{&h->mGA, &h->mXB, h->Xh, h->Xl, h->n2p, h->dstatus};
   }
 #undef ALLOC

@@ -160,9 +160,11 @@ as_status umma_make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, i
 int umma_bn_for(int N);
 // out[z*plane + m*som + n*son] = sum_{k in split z} A(m,k) B(b_row0 + n, k); npass 1 (BF16),
 // 3 (two-level split-BF16) or 6 (three-level split-BF16, FP32-equivalent operands).
+// precise = true (bn must be 64): one accumulator per K = 16 step of a stage
+// (for products that write sketch state; use 64-element K splits).
 as_status launch_umma_gemm(cudaStream_t s, const UmmaOperand& A, const UmmaOperand& B, int M, int N, int K, int bn,
                            int npass, int splits, int b_row0, float* out, long long som, long long son, long long plane,
-                           int* err);
+                           int* err, bool precise = false);
 // BF16 levels of an FP32 matrix (hi, lo, and optionally a third level lo2),
 // optionally transposed (dst(c, r) = src(r, c)).
 as_status launch_split_bf16(cudaStream_t s, const float* src, long long lds, int rows, int cols, __nv_bfloat16* hi,

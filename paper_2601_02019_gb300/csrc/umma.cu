@@ -99,7 +99,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int bn) {
 __device__ __constant__ int kPassA[6] = {0, 0, 1, 0, 1, 2};
 __device__ __constant__ int kPassB[6] = {0, 1, 0, 2, 1, 0};
 
-template <int BN, int NPASS>
+// PRECISE (state-writing products, BN <= 64): each of the four K = 16 MMAs of
+// a stage has its own hi*hi accumulator, so with 64-element K splits every
+// accumulator takes a single step and the rest of the sum happens in FP32
+// registers (round to nearest) and in the FP64 plane reduction.
+template <int BN, int NPASS, bool PRECISE>
 __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant__ UmmaOperand opA,
                                                            const __grid_constant__ UmmaOperand opB, int M, int N,
                                                            int K, int klen, int b_row0, float* out, long long som,
@@ -129,7 +133,8 @@ __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant
     fail_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  constexpr int NACC = (NPASS > 1) ? 2 : 1;
+  constexpr int NACC = PRECISE ? ((NPASS > 1) ? 5 : 4) : ((NPASS > 1) ? 2 : 1);
+  static_assert(NACC * BN <= 512, "TMEM holds 512 columns");
   if (warp == 2) {
     // TMEM accumulators: NACC x BN columns, allocated as a power of two >= 32
     constexpr uint32_t need = (uint32_t)(NACC * BN);
@@ -169,12 +174,21 @@ __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
       const int pass = it % NPASS;
-      const uint32_t dst = tmem + ((NACC == 2 && pass > 0) ? (uint32_t)BN : 0u);
-      const bool first = (NACC == 2 && pass > 0) ? (it == 1) : (it == 0);   // first MMA into this accumulator
 #pragma unroll
       for (int kk = 0; kk < UK / 16; ++kk) {
+        // accumulator of this MMA and whether this is its first write
+        int aidx;
+        bool first;
+        if (pass == 0) {
+          aidx = PRECISE ? kk : 0;
+          first = (it == 0) && (PRECISE || kk == 0);
+        } else {
+          aidx = PRECISE ? 4 : 1;
+          first = (it == 1) && (kk == 0);
+        }
+        const uint32_t dst = tmem + (uint32_t)(aidx * BN);
         const uint64_t da = smem_desc(a0 + kk * 32), db = smem_desc(b0 + kk * 32);
-        const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+        const uint32_t acc = first ? 0u : 1u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
@@ -310,7 +324,7 @@ EncodeFn encode_fn() {
   return fn;
 }
 
-template <int BN, int NPASS>
+template <int BN, int NPASS, bool PRECISE>
 as_status launch_umma_t(cudaStream_t s, const UmmaOperand& A, const UmmaOperand& B, int M, int N, int K, int splits,
                         int b_row0, float* out, long long som, long long son, long long plane, int* err) {
   const int ktiles = (K + UK - 1) / UK;
@@ -323,11 +337,11 @@ as_status launch_umma_t(cudaStream_t s, const UmmaOperand& A, const UmmaOperand&
   int dev = 0;
   AS_CUDA_TRY(cudaGetDevice(&dev));
   if (configured_device != dev) {
-    AS_CUDA_TRY(cudaFuncSetAttribute(umma_gemm_kernel<BN, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    AS_CUDA_TRY(cudaFuncSetAttribute(umma_gemm_kernel<BN, NPASS, PRECISE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     configured_device = dev;
   }
-  umma_gemm_kernel<BN, NPASS><<<grid, 128, smem, s>>>(A, B, M, N, K, klen, b_row0, out, som, son, plane, err); count_launches(1);
+  umma_gemm_kernel<BN, NPASS, PRECISE><<<grid, 128, smem, s>>>(A, B, M, N, K, klen, b_row0, out, som, son, plane, err); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }
@@ -352,14 +366,20 @@ as_status umma_make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, i
 
 as_status launch_umma_gemm(cudaStream_t s, const UmmaOperand& A, const UmmaOperand& B, int M, int N, int K, int bn,
                            int npass, int splits, int b_row0, float* out, long long som, long long son, long long plane,
-                           int* err) {
+                           int* err, bool precise) {
   if (M <= 0 || N <= 0) return AS_OK;
   if (npass != 1 && npass != 3 && npass != 6) return AS_EINVAL;
+  if (precise) {
+    if (bn != 64) return AS_EINVAL;
+    return npass == 6   ? launch_umma_t<64, 6, true>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err)
+           : npass == 3 ? launch_umma_t<64, 3, true>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err)
+                        : launch_umma_t<64, 1, true>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err);
+  }
 #define AS_UMMA_CASE(BNV)                                                                                          \
   if (bn == BNV)                                                                                                   \
-    return npass == 6   ? launch_umma_t<BNV, 6>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err)       \
-           : npass == 3 ? launch_umma_t<BNV, 3>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err)       \
-                        : launch_umma_t<BNV, 1>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err);
+    return npass == 6   ? launch_umma_t<BNV, 6, false>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err) \
+           : npass == 3 ? launch_umma_t<BNV, 3, false>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err) \
+                        : launch_umma_t<BNV, 1, false>(s, A, B, M, N, K, splits, b_row0, out, som, son, plane, err);
   AS_UMMA_CASE(32)
   AS_UMMA_CASE(64)
   AS_UMMA_CASE(128)
