@@ -95,6 +95,22 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest of the ranks' values (all ranks get it); x itself when ws == 1."""
+    if ws <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rows_per_s(ws: int, steps: int, rows_per_step: int, slowest_s: float) -> float:
+    """Whole-job throughput: every rank sketches its own stream of steps x
+    rows_per_step rows (weak scaling), timed by the slowest rank."""
+    return ws * steps * rows_per_step / slowest_s
+
+
 def reference_arm(args) -> None:
     """The oracle (plain FP64 NumPy), timed on the host cores, on a bounded
     sample of the same workload: the stream is first brought to a full-size
@@ -176,11 +192,7 @@ def _run_form(p, torch, args, A_dev, d, ell, B, K, W, rank, local, ws, prec, wan
         torch.distributed.barrier()
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = _max_over_ranks(sum(step_ms), ws, dev)
     st1 = s.stats()
     return dict(sketch=s, t_ms=t_ms, step_ms=step_ms, st0=st0, st1=st1, prof=s.profile(), clocks=clk.summary(),
                 state=state)
@@ -214,7 +226,7 @@ def our_arm(args) -> None:
         runs[f] = _run_form(p, torch, args, A_dev, d, ell, B, K, W, rank, local, ws, PRECISIONS[f],
                             want_state=(f == head))
     hr = runs[head]
-    value = ws * K * B / (hr["t_ms"] / 1000.0)
+    value = _job_rows_per_s(ws, K, B, hr["t_ms"] / 1000.0)
 
     # roofline of the dominant single-kernel class of the headline form (the
     # eigensolver and the event-row path are composites and are listed in "profile")
@@ -256,12 +268,8 @@ def our_arm(args) -> None:
         for k in range(W, W + K):
             s2.update(A_pin[k * B:(k + 1) * B].numpy())
             s2.stats()
-        e2e_s = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": ws * K * B / e2e_s, "unit": "rows/s", "h2d_bytes_per_step": B * d * 4,
+        e2e_s = _max_over_ranks(time.perf_counter() - t0, ws, dev)
+        e2e = {"value": _job_rows_per_s(ws, K, B, e2e_s), "unit": "rows/s", "h2d_bytes_per_step": B * d * 4,
                "d2h_bytes_per_step": 112}
 
     if rank == 0:
