@@ -212,6 +212,20 @@ as_status as_symeig(int32_t n, const double* A, int32_t nev, double* evals, doub
 as_status as_tc_gemm(int32_t M, int32_t N, int32_t K, const float* A, const float* B, int32_t npass, int32_t splits,
                      double* out);
 
+/* as_symeig without any allocation, for callers that cannot allocate device
+ * memory (inside a CUDA stream capture, in allocator callbacks, on serving
+ * paths that forbid allocation after start-up).  The paper has no
+ * counterpart: this is a library service.  A (n x n, row-major, device
+ * memory, not modified), evals (nev, device) and vecs (n x nev row-major,
+ * device) are the caller's; the scratch space is a fixed device array of
+ * 788,992 bytes inside the library, reserved on every GPU that loads it.
+ * n must be <= 128 (AS_EINVAL otherwise).  Work is ordered on cuda_stream
+ * (NULL = legacy default stream) and the call returns without synchronising.
+ * All calls share the scratch array: calls that overlap on the GPU race.  The
+ * first call on a device looks up the array's address; make it before any
+ * stream capture. */
+as_status as_symeig_noalloc(int32_t n, const double* A, int32_t nev, double* evals, double* vecs, void* cuda_stream);
+
 /* Free every resource of the sketch.  NULL is a no-op. */
 as_status sketch_destroy(as_sketch* h);
 

@@ -18,7 +18,7 @@ AS_PROFILE = 0x2
 
 EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram", "sketch_get_buffer", "sketch_get_gram",
             "sketch_merge", "sketch_stats", "sketch_trace", "sketch_profile", "sketch_profile_reset",
-            "sketch_destroy", "as_symeig", "as_tc_gemm", "as_status_str")
+            "sketch_destroy", "as_symeig", "as_symeig_noalloc", "as_tc_gemm", "as_status_str")
 
 
 class AsConfig(ct.Structure):
@@ -80,6 +80,7 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.sketch_profile_reset.argtypes = [P]
     L.sketch_destroy.argtypes = [P]
     L.as_symeig.argtypes = [I32, P, I32, P, P]
+    L.as_symeig_noalloc.argtypes = [I32, P, I32, P, P, P]
     L.as_tc_gemm.argtypes = [I32, I32, I32, P, P, I32, I32, P]
     L.as_status_str.argtypes = [ct.c_int]
     L.as_status_str.restype = ct.c_char_p

@@ -1,0 +1,52 @@
+// as_symeig_noalloc: the FP64 symmetric eigensolver with no allocation.
+//
+// Some callers cannot allocate device memory: code running inside a CUDA
+// stream capture (cudaMalloc is not capturable), allocators' own callbacks,
+// and real-time serving paths that forbid allocation after start-up.  This
+// entry point takes device pointers for its input and outputs and keeps its
+// scratch space (a copy of A, since the solver overwrites its input, and the
+// solver's work vectors) in one file-scope device array.
+//
+// The array is reserved on every GPU that loads this library until the
+// process exits.  All calls share it and it keeps the last call's contents
+// (nothing in it has to start at zero: every value the solver reads is
+// written earlier in the same call).  Calls whose work overlaps on the GPU
+// race with each other.  The first call on a device looks up the array's
+// device address; make that first call before any stream capture.
+#include "eig.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+// Largest supported order and the resulting scratch size (doubles):
+// n*n for the copy of A plus the solver's work vectors for nev <= n.
+constexpr int kNoAllocMaxN = 128;
+constexpr size_t kNoAllocDoubles = (size_t)kNoAllocMaxN * kNoAllocMaxN + 2 * (size_t)kNoAllocMaxN +
+                                   5 * (size_t)kNoAllocMaxN * kNoAllocMaxN + 64;   // 98,624 doubles = 788,992 bytes
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+constexpr int kMaxDevices = 64;
+double* g_scratch_ptr[kMaxDevices] = {};   // device address of the array, per device
+
+}  // namespace
+
+extern "C" as_status as_symeig_noalloc(int32_t n, const double* A, int32_t nev, double* evals, double* vecs,
+                                       void* cuda_stream) {
+  if (n < 1 || n > kNoAllocMaxN || nev < 1 || nev > n || !A || !evals || !vecs) return AS_EINVAL;
+  int dev = 0;
+  AS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return AS_EINVAL;
+  if (!g_scratch_ptr[dev]) {
+    // once per device, with that device current: the host-side name of the
+    // array is only a stand-in, the kernels need its device address
+    void* p = nullptr;
+    AS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_scratch_ptr[dev] = (double*)p;
+  }
+  double* Acopy = g_scratch_ptr[dev];
+  double* work = Acopy + (size_t)kNoAllocMaxN * kNoAllocMaxN;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  AS_CUDA_TRY(cudaMemcpyAsync(Acopy, A, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return as::launch_eig(s, n, Acopy, n, nev, evals, vecs, nev, work);
+}
