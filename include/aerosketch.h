@@ -232,6 +232,12 @@ as_status sketch_destroy(as_sketch* h);
 /* Static string naming a status. */
 const char* as_status_str(as_status s);
 
+/* The last CUDA call of this library that failed on the calling thread, as
+ * "<cudaError name> (<source file>:<line>)"; "" if none.  Library service
+ * (the paper has no counterpart).  The string is owned by the library and
+ * valid until the thread's next failing call. */
+const char* as_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

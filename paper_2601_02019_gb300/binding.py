@@ -18,7 +18,7 @@ AS_PROFILE = 0x2
 
 EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram", "sketch_get_buffer", "sketch_get_gram",
             "sketch_merge", "sketch_stats", "sketch_trace", "sketch_profile", "sketch_profile_reset",
-            "sketch_destroy", "as_symeig", "as_symeig_noalloc", "as_tc_gemm", "as_status_str")
+            "sketch_destroy", "as_symeig", "as_symeig_noalloc", "as_tc_gemm", "as_status_str", "as_last_error")
 
 
 class AsConfig(ct.Structure):
@@ -52,7 +52,11 @@ class AsKernelStat(ct.Structure):
 class AeroSketchError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
-        super().__init__(f"{what}: {lib().as_status_str(code).decode()}")
+        msg = f"{what}: {lib().as_status_str(code).decode()}"
+        cuda = lib().as_last_error().decode()
+        if cuda and code == AS_EDEVICE:   # name the CUDA call that failed
+            msg += f" [{cuda}]"
+        super().__init__(msg)
 
 
 _LIB = None
@@ -84,8 +88,10 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.as_tc_gemm.argtypes = [I32, I32, I32, P, P, I32, I32, P]
     L.as_status_str.argtypes = [ct.c_int]
     L.as_status_str.restype = ct.c_char_p
+    L.as_last_error.argtypes = []
+    L.as_last_error.restype = ct.c_char_p
     for name in EXPORTED:
-        if name != "as_status_str":
+        if name not in ("as_status_str", "as_last_error"):
             getattr(L, name).restype = ct.c_int
     _LIB = L
     return L

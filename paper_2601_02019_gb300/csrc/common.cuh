@@ -7,10 +7,16 @@
 
 #include "../../include/aerosketch.h"
 
+// Records a failed CUDA call (error name, file, line) for as_last_error().
+void as_note_cuda_error(cudaError_t e, const char* file, int line);
+
 #define AS_CUDA_TRY(expr)                                   \
   do {                                                      \
     cudaError_t _e = (expr);                                \
-    if (_e != cudaSuccess) return as_from_cuda(_e);         \
+    if (_e != cudaSuccess) {                                \
+      as_note_cuda_error(_e, __FILE__, __LINE__);           \
+      return as_from_cuda(_e);                              \
+    }                                                       \
   } while (0)
 
 static inline as_status as_from_cuda(cudaError_t e) {

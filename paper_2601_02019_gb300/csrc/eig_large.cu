@@ -8,7 +8,8 @@
 //     sums of v^T p; kernel 2 sums the partials in a fixed order and applies
 //     A22 -= v w^T + w v^T, w = 2p - 2(v^T p) v.  No atomics: results are
 //     bitwise reproducible.
-//   * bisection and inverse iteration: one thread per eigenvalue.
+//   * bisection: one warp per eigenvalue (multisection); inverse iteration:
+//     one thread per eigenvalue.
 //   * back-transformation: each block owns a slab of eigenvector columns in
 //     shared memory and applies every reflector to it.
 #include "eig.cuh"
@@ -96,10 +97,11 @@ __global__ void __launch_bounds__(256) tri_fused(double* A, int lda, int n, int 
   __shared__ double red[32];
   __shared__ double c_s;
   const int tid = threadIdx.x;
-  if (tid == 0) {
+  if (tid < 32) {   // v^T p from the previous step's block partials (fixed order)
     double c = 0.0;
-    for (int q = 0; q < in.nparts; ++q) c += in.part[q];
-    c_s = c;
+    for (int q = tid; q < in.nparts; q += 32) c += in.part[q];
+    c = warp_sum(c);
+    if (tid == 0) c_s = c;
   }
   __syncthreads();
   const double c = c_s;

@@ -55,7 +55,7 @@ int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
-const char* const kProfNames[PK_COUNT] = {"gspace_batch_gemm", "gspace_batch_orth", "eig_fp64",
+const char* const kProfNames[PK_COUNT] = {"batch_persist",     "batch_prep",        "eig_fp64",
                                           "fd_rebuild_gemm",   "gram_rows_gemm",    "ingest",
                                           "event_row_fp64",    "eig_tridiag",       "eig_bisect_invit",
                                           "eig_backtransform"};
@@ -147,29 +147,30 @@ struct as_sketch {
   int dpass = 1;            // passes of the d-side products (1 BF16, 3 split-BF16)
   int n2p = 0;              // n2 rounded up to 64
   int rows_pad = 0;         // row counts of the BF16 buffers, >= 256
-  __nv_bfloat16 *Chi = nullptr, *Clo = nullptr, *Cthi = nullptr, *Ctlo = nullptr, *Gfh = nullptr, *Gfl = nullptr,
-                *Xh = nullptr, *Xl = nullptr, *Wh = nullptr, *Wl = nullptr;
+  __nv_bfloat16 *Chi = nullptr, *Clo = nullptr, *Cthi = nullptr, *Ctlo = nullptr, *Wh = nullptr, *Wl = nullptr;
   __nv_bfloat16 *Cl2 = nullptr, *Ctl2 = nullptr, *Wl2 = nullptr;   // third BF16 level (AS_BF16X6)
   float* Prb = nullptr;     // split-K planes of the FD rebuild (tensor forms)
   size_t prb_cap = 0;
-  UmmaOperand mCA{}, mCB64{}, mCB256{}, mGA{}, mXB{}, mWA{}, mCtB{};
-  TcBatch tcb{};
+  UmmaOperand mCA{}, mCB64{}, mCB256{}, mWA{}, mCtB{};
+  // persistent batched iterations
+  PersistBuffers pb{};
+  int gf_valid = 0;         // leading rows/columns of Gf that equal G (FP32-rounded)
 };
 
 namespace {
 
 void free_all(as_sketch* h) {
-  float* fp[] = {h->C, h->Cnew, h->Wfd, h->stage, h->arena, h->Gf, h->bb.X, h->bb.P, h->Prb};
+  float* fp[] = {h->C, h->Cnew, h->Wfd, h->stage, h->arena, h->Gf, h->bb.P, h->Prb, h->pb.Y, h->pb.X, h->pb.part};
   for (float* p : fp) if (p) cudaFree(p);
   double* dp[] = {h->G, h->Gtmp, h->lam, h->U, h->eigw, h->scal, h->si.Y, h->si.GY, h->si.S, h->si.V,
                   h->si.eigw, h->si.ritz, h->si.WU, h->si.GWU, h->si.tmp, h->x64, h->y64, h->norm2, h->dwork,
-                  h->bb.sig2, h->bb.ritz};
+                  h->pb.sig2, h->pb.ritz};
   for (double* p : dp) if (p) cudaFree(p);
   if (h->bad) cudaFree(h->bad);
   if (h->dstatus) cudaFree(h->dstatus);
   if (h->zero) cudaFree(h->zero);
-  __nv_bfloat16* bp[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Gfh, h->Gfl, h->Xh, h->Xl, h->Wh, h->Wl,
-                         h->Cl2, h->Ctl2, h->Wl2};
+  if (h->pb.cnt) cudaFree(h->pb.cnt);
+  __nv_bfloat16* bp[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Wh, h->Wl, h->Cl2, h->Ctl2, h->Wl2};
   for (__nv_bfloat16* p : bp) if (p) cudaFree(p);
   if (h->h_buf) cudaFreeHost(h->h_buf);
   delete h->prof;
@@ -309,6 +310,7 @@ as_status fd_shrink(as_sketch* h) {
     h->prof->end(PK_REBUILD, h->s, 2.0 * (ell - 1) * (double)n2 * d + 2.0 * (ell - 1) * (double)(ell - 1) * d,
                  4.0 * ((double)n2 * d + 2.0 * (ell - 1) * (double)d));
   h->r = ell - 1;
+  h->gf_valid = 0;
   h->st.shrinks++;
   return AS_OK;
 }
@@ -331,6 +333,7 @@ as_status dump(as_sketch* h, int xi, int k, int64_t i) {
   }
   st = launch_dump(h->s, h->C, ldc, d, r, h->G, n2, h->si.WU, h->si.GWU, k, xi, Z, Y, h->dwork);
   if (st != AS_OK) return st;
+  h->gf_valid = 0;
   st = tc_split_rows(h, 0, r);
   if (st != AS_OK) return st;
   const int64_t s_prev = h->snaps.empty() ? 1 : h->snaps.back().t + 1;
@@ -373,7 +376,7 @@ as_status finish_row(as_sketch* h, int64_t i, double theta, int known_gate, doub
   for (int j = 1; j <= h->jmax; ++j) {              // line 9
     const int k = std::min(std::min(1 << std::min(j, 30), h->ell), h->d);  // line 10
     if (j == 1 && k == 2 && batch_col >= 0)       // iterated basis from the batched pass
-      st = launch_si_rr_from_batch(h->s, h->G, h->n2, h->r, h->bb.X, batch_col, h->si, h->dstatus);
+      st = launch_si_rr_from_batch(h->s, h->G, h->n2, h->r, h->pb.X, batch_col, h->si, h->dstatus);
     else if (h->big)
       st = launch_simul_iter_f64(h->s, h->G, h->n2, h->r, k, h->q, h->key, (uint64_t)i, j, h->si, h->dstatus);
     else
@@ -425,25 +428,38 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
   st = h->tc ? tc_gram_rows(h, r0, b, h->mCB64, 64)
              : launch_gram_rows_skinny(h->s, h->C, h->ldc, d, r0, b, h->G, n2, h->bb.P, h->p_cap);
   if (st != AS_OK) return st;
+  h->gf_valid = std::min(h->gf_valid, r0);
   if (h->prof)
     h->prof->end(PK_GRAM, h->s, 2.0 * (r0 + b) * (double)b * d, 4.0 * (r0 + b) * (double)d + 8.0 * (r0 + b) * b);
   const bool fills_all = (r0 + b == n2);
   const int nbb = fills_all ? b - 1 : b;   // batched rows (the filling row needs the shrink first)
   if (nbb > 0) {
-    st = h->tc ? launch_gbf16_mirror(h->s, h->G, n2, r0 + b, h->Gfh, h->Gfl, h->n2p)
-               : launch_gf_mirror(h->s, h->G, h->Gf, n2, r0 + b);
+    if (h->prof) h->prof->begin(PK_BATCH_ORTH, h->s);
+    st = launch_gf_mirror(h->s, h->G, h->Gf, n2, h->gf_valid, r0 + nbb);
     if (st != AS_OK) return st;
-    st = launch_batch_gspace(h->s, h->Gf, n2, r0, nbb, h->k_pi, h->q, h->key, (uint64_t)(h->T + 1), h->bb,
-                             h->prof, h->tc ? &h->tcb : nullptr);
+    if (h->prof) {
+      const double nm = (double)(r0 + nbb) * (r0 + nbb) - (double)h->gf_valid * h->gf_valid;
+      h->prof->end(PK_BATCH_ORTH, h->s, 0.0, 12.0 * nm);
+    }
+    h->gf_valid = r0 + nbb;
+    st = launch_batch_persist(h->s, h->Gf, n2, r0, nbb, h->k_pi, h->q, h->key, (uint64_t)(h->T + 1), h->pb,
+                              h->dstatus, h->prof);
     if (st != AS_OK) return st;
   }
-  // one synchronisation per block: row norms, power-iteration values, Ritz values
+  // one synchronisation per block: row norms, power-iteration values, Ritz
+  // values and the sticky device status
   AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf, h->norm2, b * sizeof(double), cudaMemcpyDeviceToHost, h->s));
   if (nbb > 0) {
-    AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf + b, h->bb.sig2, nbb * sizeof(double), cudaMemcpyDeviceToHost, h->s));
-    AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf + b + nbb, h->bb.ritz, 2 * nbb * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf + b, h->pb.sig2, nbb * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf + b + nbb, h->pb.ritz, 2 * nbb * sizeof(double), cudaMemcpyDeviceToHost, h->s));
   }
+  AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf + b + 3 * nbb, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, h->s));
   AS_CUDA_TRY(cudaStreamSynchronize(h->s));
+  {
+    int ds = 0;
+    std::memcpy(&ds, h->h_buf + b + 3 * nbb, sizeof(int));
+    if (ds != 0) return (as_status)ds;
+  }
   std::vector<double> a2(h->h_buf, h->h_buf + b);
   std::vector<double> sig2(h->h_buf + b, h->h_buf + b + nbb), ritz(h->h_buf + b + nbb, h->h_buf + b + 3 * nbb);
   int bb = b;
@@ -452,6 +468,7 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
   if (*bad_row) {
     AS_CUDA_TRY(cudaMemsetAsync(h->bad, 0, sizeof(int), h->s));
     st = launch_truncate(h->s, h->C, h->ldc, d, r0 + bb, r0 + b, h->G, n2);
+    h->gf_valid = std::min(h->gf_valid, r0 + bb);
     if (st == AS_OK) st = tc_split_rows(h, r0 + bb, r0 + b);
     if (st != AS_OK) return st;
     if (bb == 0) { *used = 0; return AS_OK; }
@@ -514,6 +531,7 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
   const int rnew = r0 + tstar + 1;
   if (rnew < r0 + bb) {
     st = launch_truncate(h->s, h->C, h->ldc, d, rnew, r0 + bb, h->G, n2);
+    h->gf_valid = std::min(h->gf_valid, rnew);
     if (st == AS_OK) st = tc_split_rows(h, rnew, r0 + bb);
     if (st != AS_OK) return st;
   }
@@ -529,7 +547,7 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
     return finish_row(h, h->T, h->theta, -1, 0.0);
   }
   // large buffers reuse the batch's FP32-iterated basis for the k = 2 step
-  const int bcol = h->big ? nbb + 2 * tstar : -1;
+  const int bcol = h->big ? batch_si_col(nbb, tstar) : -1;
   if (h->prof) h->prof->begin(PK_EVENT, h->s);
   st = finish_row(h, h->T, h->theta, gate_known, sig2_star, bcol, 3 * nbb);
   if (h->prof) h->prof->end(PK_EVENT, h->s, 0.0, 0.0);
@@ -576,7 +594,19 @@ bool is_device_ptr(const void* p) {
 
 }  // namespace
 
+namespace {
+thread_local char g_last_error[192] = "";
+}
+
+void as_note_cuda_error(cudaError_t e, const char* file, int line) {
+  const char* base = std::strrchr(file, '/');
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s (%s:%d)", cudaGetErrorName(e), base ? base + 1 : file, line);
+}
+
+
 extern "C" {
+
+const char* as_last_error(void) { return g_last_error; }
 
 const char* as_status_str(as_status s) {
   switch (s) {
@@ -669,10 +699,17 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   h->bb.max_splits = 16;
   h->p_cap = std::max({(size_t)h->bb.max_splits * n2 * 3 * bmax, (size_t)64 * bmax * n2,
                        (size_t)16 * ell * ell});
-  ALLOC(h->bb.X, (size_t)n2 * 3 * bmax);
   ALLOC(h->bb.P, h->p_cap);
-  ALLOC(h->bb.sig2, (size_t)bmax);
-  ALLOC(h->bb.ritz, (size_t)2 * bmax);
+  h->pb.ycols = batch_persist_ycols(bmax);
+  h->pb.ldy = (n2 + 31) / 32 * 32;
+  h->pb.ybuf = (long long)h->pb.ldy * (long long)h->pb.ycols;
+  h->pb.bmax = bmax;
+  ALLOC(h->pb.Y, 2 * (size_t)h->pb.ybuf);
+  ALLOC(h->pb.X, (size_t)n2 * h->pb.ycols);
+  ALLOC(h->pb.part, batch_persist_part_floats(bmax));
+  ALLOC(h->pb.cnt, 1);
+  ALLOC(h->pb.sig2, (size_t)bmax);
+  ALLOC(h->pb.ritz, (size_t)2 * bmax);
   ALLOC(h->si.Y, (size_t)n2 * kmax);
   ALLOC(h->si.GY, (size_t)n2 * kmax);
   ALLOC(h->si.S, (size_t)kmax * kmax);
@@ -689,15 +726,13 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
     const int rp = std::max(256, std::max(n2, std::max(3 * bmax, ell)));
     h->rows_pad = rp;
     const size_t cN = (size_t)std::max(rp, n2) * h->ldc, ctN = (size_t)std::max(h->d, 256) * h->n2p;
-    const size_t gN = (size_t)std::max(h->n2p, 256) * h->n2p, xN = (size_t)std::max(3 * bmax, 256) * h->n2p;
     const size_t wN = (size_t)std::max(ell, 256) * h->n2p;
     ALLOC(h->Chi, cN); ALLOC(h->Clo, cN); ALLOC(h->Cthi, ctN); ALLOC(h->Ctlo, ctN);
-    ALLOC(h->Gfh, gN); ALLOC(h->Gfl, gN); ALLOC(h->Xh, xN); ALLOC(h->Xl, xN); ALLOC(h->Wh, wN); ALLOC(h->Wl, wN);
+    ALLOC(h->Wh, wN); ALLOC(h->Wl, wN);
     if (h->dpass == 6) { ALLOC(h->Cl2, cN); ALLOC(h->Ctl2, ctN); ALLOC(h->Wl2, wN); }
-    __nv_bfloat16* bz[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Gfh, h->Gfl, h->Xh, h->Xl, h->Wh, h->Wl,
-                           h->Cl2, h->Ctl2, h->Wl2};
-    const size_t bn[] = {cN, cN, ctN, ctN, gN, gN, xN, xN, wN, wN, cN, ctN, wN};
-    for (int t = 0; t < 13 && st == AS_OK; ++t)
+    __nv_bfloat16* bz[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Wh, h->Wl, h->Cl2, h->Ctl2, h->Wl2};
+    const size_t bn[] = {cN, cN, ctN, ctN, wN, wN, cN, ctN, wN};
+    for (int t = 0; t < 9 && st == AS_OK; ++t)
       if (bz[t] && cudaMemsetAsync(bz[t], 0, bn[t] * sizeof(__nv_bfloat16), h->s) != cudaSuccess) st = AS_EDEVICE;
     const int cr = (int)(cN / h->ldc);
     // level maps; a missing third level repeats the second (never read then)
@@ -711,11 +746,8 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
     mk(h->mCA, h->Chi, h->Clo, h->Cl2, cr, h->ldc, h->ldc, 128);
     mk(h->mCB64, h->Chi, h->Clo, h->Cl2, cr, h->ldc, h->ldc, 64);
     mk(h->mCB256, h->Chi, h->Clo, h->Cl2, cr, h->ldc, h->ldc, 256);
-    mk(h->mGA, h->Gfh, h->Gfl, nullptr, (int)(gN / h->n2p), h->n2p, h->n2p, 128);
-    mk(h->mXB, h->Xh, h->Xl, nullptr, (int)(xN / h->n2p), h->n2p, h->n2p, 192);
     mk(h->mWA, h->Wh, h->Wl, h->Wl2, (int)(wN / h->n2p), h->n2p, h->n2p, 128);
     mk(h->mCtB, h->Cthi, h->Ctlo, h->Ctl2, (int)(ctN / h->n2p), h->n2p, h->n2p, 64);
-    h->tcb = TcBatch{&h->mGA, &h->mXB, h->Xh, h->Xl, h->n2p, h->dstatus};
   }
 #undef ALLOC
   if (st == AS_OK && cudaMallocHost((void**)&h->h_buf, (size_t)(4 * std::max(n2, bmax) + 64) * sizeof(double)) != cudaSuccess) {

@@ -1,23 +1,7 @@
-// Block-speculative G-space iterations, the FP64 single-row path for large
-// buffers, and the dump kernels.
-//
-// Within a block of b new rows and no event (no shrink, no dump), the buffer
-// only grows by appending rows, so the state seen by row t of the block is the
-// leading (r+t+1) x (r+t+1) principal submatrix of the block's Gram G.  The
-// power iteration of every row (Algorithm 1) and the first doubling step
-// (k = 2) of the simultaneous iteration of every row (Algorithm 2) are then
-// independent problems on masked columns of one matrix:
-//     X <- mask(G X)    (mask_t keeps rows < m_t = r + t + 1)
-// and run as one split-K GEMM over G per iteration, followed by a per-row
-// normalisation (k = 1) or SVQB orthonormalisation (k = 2).  These batched
-// values locate the first row whose decision changes the state; that row is
-// finished in FP64 (its Rayleigh-Ritz step reuses the batch's iterated basis)
-// and rows whose batched value lies within a 1e-4 relative band of a
-// threshold are re-decided by the FP64 power iteration.
-//
-// Batch matrix layout: column-major, column c at X + c*n2; columns [0, nb)
-// are the power-iteration vectors of rows 0..nb-1 and columns nb+2t, nb+2t+1
-// the simultaneous-iteration pair of row t.
+// The FP64 single-row path of the G-space iterations for large buffers
+// (power iteration, simultaneous iteration, Rayleigh-Ritz from the batched
+// basis), the incremental FP32 mirror of G read by the batched iterations
+// (batch_persist.cu), and the dump kernels (Algorithm 4 lines 14-16).
 #include <algorithm>
 
 #include "eig.cuh"
@@ -26,39 +10,6 @@
 namespace as {
 
 namespace {
-
-__global__ void batch_fill_kernel(float* X, int n2, int nb, int r0, Key key, uint64_t i0) {
-  const int t = blockIdx.x, kind = blockIdx.y;  // kind 0: PI column, 1: SI pair
-  const int m = r0 + t + 1;
-  const uint64_t i = i0 + (uint64_t)t;
-  if (kind == 0) {
-    float* x = X + (size_t)t * n2;
-    for (int blk = threadIdx.x; blk * 4 < n2; blk += blockDim.x) {
-      double z[4];
-      gauss4(key, kPurposePiStart, i, 0, blk, z);
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        const int p = blk * 4 + l;
-        if (p < n2) x[p] = (p < m) ? (float)z[l] : 0.f;
-      }
-    }
-  } else {
-    float* x0 = X + (size_t)(nb + 2 * t) * n2;
-    // Pi is n2 x 2 row-major: element e = 2p + c
-    for (int blk = threadIdx.x; blk * 4 < 2 * n2; blk += blockDim.x) {
-      double z[4];
-      gauss4(key, kPurposeSiTest, i, 1, blk, z);
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        const int e = blk * 4 + l;
-        if (e < 2 * n2) {
-          const int p = e >> 1, c = e & 1;
-          x0[(size_t)c * n2 + p] = (p < m) ? (float)z[l] : 0.f;
-        }
-      }
-    }
-  }
-}
 
 __device__ __forceinline__ void eig2(double s00, double s01, double s11, double& l0, double& l1, double& v00,
                                      double& v01, double& v10, double& v11) {
@@ -71,135 +22,16 @@ __device__ __forceinline__ void eig2(double s00, double s01, double s11, double&
   v00 = cos(th); v10 = sin(th); v01 = -v10; v11 = v00;
 }
 
-// After Y = G X (plane 0 of P after the split reduction): PI columns are
-// normalised, SI pairs SVQB-orthonormalised (twice); on the final pass
-// sigma^2 = x^T (G x) and the Ritz values of the pair are computed instead.
-// Per-element arithmetic is FP32 (FP64 throughput is a small fraction of FP32
-// on this part); only the per-thread partial sums are widened to FP64 for the
-// block reductions and the 2 x 2 eigenproblems.  kind = kind0 + blockIdx.y.
-__global__ void __launch_bounds__(512) batch_orth_kernel(const float* __restrict__ Y, float* X, int n2, int nb,
-                                                         int r0, int kind0, int final_pi, int final_si,
-                                                         double* sig2, double* ritz) {
-  __shared__ double red[32];
-  const int t = blockIdx.x, kind = kind0 + blockIdx.y;
-  const int m = r0 + t + 1;
-  if (kind == 0) {
-    float* x = X + (size_t)t * n2;
-    const float* y = Y + (size_t)t * n2;
-    float sf = 0.f;
-    if (final_pi) {
-      for (int p = threadIdx.x; p < m; p += blockDim.x) sf = fmaf(x[p], y[p], sf);
-      const double s = block_sum((double)sf, red);
-      if (threadIdx.x == 0) sig2[t] = s;
-      return;
-    }
-    for (int p = threadIdx.x; p < m; p += blockDim.x) sf = fmaf(y[p], y[p], sf);
-    const double s = block_sum((double)sf, red);
-    const float inv = (s > 0.0) ? (float)(1.0 / sqrt(s)) : 0.f;
-    for (int p = threadIdx.x; p < n2; p += blockDim.x) x[p] = (p < m) ? y[p] * inv : 0.f;
-    return;
-  }
-  const size_t o0 = (size_t)(nb + 2 * t) * n2, o1 = o0 + n2;
-  float* x0 = X + o0;
-  float* x1 = X + o1;
-  const float* y0 = Y + o0;
-  const float* y1 = Y + o1;
-  if (final_si) {
-    // S = X^T (G X) (X orthonormal); SVQB -> W = X V D^-1/2, GW = Y V D^-1/2;
-    // Ritz values = eig((GW)^T (GW)) = eig(D^-1/2 V^T (Y^T Y) V D^-1/2)
-    float f00 = 0.f, f01 = 0.f, f11 = 0.f, g00 = 0.f, g01 = 0.f, g11 = 0.f;
-    for (int p = threadIdx.x; p < m; p += blockDim.x) {
-      const float a = x0[p], b = x1[p], ya = y0[p], yb = y1[p];
-      f00 = fmaf(a, ya, f00); f01 = fmaf(0.5f, fmaf(a, yb, b * ya), f01); f11 = fmaf(b, yb, f11);
-      g00 = fmaf(ya, ya, g00); g01 = fmaf(ya, yb, g01); g11 = fmaf(yb, yb, g11);
-    }
-    const double s00 = block_sum((double)f00, red), s01 = block_sum((double)f01, red), s11 = block_sum((double)f11, red);
-    const double h00 = block_sum((double)g00, red), h01 = block_sum((double)g01, red), h11 = block_sum((double)g11, red);
-    if (threadIdx.x == 0) {
-      double l0, l1, v00, v01, v10, v11;
-      eig2(s00, s01, s11, l0, l1, v00, v01, v10, v11);
-      const double tol = 1e-6 * fmax(l0, 0.0);
-      const double a0 = (l0 > tol && l0 > 0) ? 1.0 / sqrt(l0) : 0.0;
-      const double a1 = (l1 > tol && l1 > 0) ? 1.0 / sqrt(l1) : 0.0;
-      // M = diag(a) V^T H V diag(a), H = Y^T Y
-      const double hv00 = h00 * v00 + h01 * v10, hv10 = h01 * v00 + h11 * v10;
-      const double hv01 = h00 * v01 + h01 * v11, hv11 = h01 * v01 + h11 * v11;
-      const double m00 = a0 * a0 * (v00 * hv00 + v10 * hv10);
-      const double m01 = a0 * a1 * (v00 * hv01 + v10 * hv11);
-      const double m11 = a1 * a1 * (v01 * hv01 + v11 * hv11);
-      const double tr = 0.5 * (m00 + m11), df = 0.5 * (m00 - m11);
-      const double rad = sqrt(df * df + m01 * m01);
-      ritz[2 * t] = (a0 > 0) ? tr + rad : 0.0;
-      ritz[2 * t + 1] = (a0 > 0 && a1 > 0) ? tr - rad : 0.0;
-    }
-    return;
-  }
-  // Euclidean SVQB of the pair: pass 0 reads Y, pass 1 re-orthonormalises X.
-  // The 2 x 2 eigenproblem is solved once (thread 0, FP64) and broadcast.
-  __shared__ float coef[4];
-  for (int pass = 0; pass < 2; ++pass) {
-    const float* s0 = pass ? x0 : y0;
-    const float* s1 = pass ? x1 : y1;
-    float f00 = 0.f, f01 = 0.f, f11 = 0.f;
-    for (int p = threadIdx.x; p < m; p += blockDim.x) {
-      const float a = s0[p], b = s1[p];
-      f00 = fmaf(a, a, f00); f01 = fmaf(a, b, f01); f11 = fmaf(b, b, f11);
-    }
-    const double s00 = block_sum((double)f00, red), s01 = block_sum((double)f01, red), s11 = block_sum((double)f11, red);
-    if (threadIdx.x == 0) {
-      double l0, l1, v00, v01, v10, v11;
-      eig2(s00, s01, s11, l0, l1, v00, v01, v10, v11);
-      const double tol = 1e-13 * fmax(l0, 0.0);
-      const double a0 = (l0 > tol && l0 > 0) ? 1.0 / sqrt(l0) : 0.0;
-      const double a1 = (l1 > tol && l1 > 0) ? 1.0 / sqrt(l1) : 0.0;
-      coef[0] = (float)(v00 * a0); coef[1] = (float)(v10 * a0);
-      coef[2] = (float)(v01 * a1); coef[3] = (float)(v11 * a1);
-    }
-    __syncthreads();
-    const float c00 = coef[0], c10 = coef[1], c01 = coef[2], c11 = coef[3];
-    for (int p = threadIdx.x; p < n2; p += blockDim.x) {
-      float o0v = 0.f, o1v = 0.f;
-      if (p < m) {
-        const float a = s0[p], b = s1[p];
-        o0v = fmaf(a, c00, b * c10);
-        o1v = fmaf(a, c01, b * c11);
-      }
-      x0[p] = o0v;
-      x1[p] = o1v;
-    }
-    __syncthreads();
-  }
-}
-
-// Y(p, c) = sum_s P[s](p, c) for columns [c0, c1), rows < mmax, written into plane 0.
-__global__ void plane_reduce_kernel(float* P, long long plane, int S, int n2, int c0, int c1, int mmax) {
-  const int c = c0 + blockIdx.y;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < mmax; p += gridDim.x * blockDim.x) {
-    const size_t off = (size_t)c * n2 + p;
-    float v = 0.f;
-    for (int s = 0; s < S; ++s) v += P[(long long)s * plane + off];
-    P[off] = v;
-  }
-}
-
-// Gf (FP32 mirror) = G (FP64) on the leading m x m block, zero elsewhere.
-__global__ void mirror_f32_kernel(const double* G, float* Gf, int n2, int m) {
-  const size_t tot = (size_t)n2 * n2;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-    const int p = (int)(e / n2), q = (int)(e % n2);
-    Gf[e] = (p < m && q < m) ? (float)G[e] : 0.f;
-  }
-}
-
-__global__ void mirror_bf16_kernel(const double* G, int n2, int m, __nv_bfloat16* hi, __nv_bfloat16* lo, int n2p) {
-  const size_t tot = (size_t)n2p * n2p;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-    const int p = (int)(e / n2p), q = (int)(e % n2p);
-    const float x = (p < m && q < m) ? (float)G[(size_t)p * n2 + q] : 0.f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    hi[e] = h;
-    lo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
-  }
+// Gf (FP32) = G (FP64) on the rows/columns of the leading m x m block that
+// are not yet mirrored: row p (one CTA per row) gets columns [valid, m) when
+// p < valid and [0, m) otherwise.
+__global__ void mirror_strip_kernel(const double* G, float* Gf, int n2, int valid, int m) {
+  const int p = blockIdx.x;
+  if (p >= m) return;
+  const int q0 = (p < valid) ? valid : 0;
+  const double* g = G + (size_t)p * n2;
+  float* f = Gf + (size_t)p * n2;
+  for (int q = q0 + threadIdx.x; q < m; q += blockDim.x) f[q] = (float)g[q];
 }
 
 // ---- FP64 single-row path (any buffer size) ---------------------------------
@@ -479,82 +311,10 @@ __global__ void gram_downdate_kernel(double* G, int n2, int r, const double* GWU
 
 }  // namespace
 
-as_status launch_gf_mirror(cudaStream_t s, const double* G, float* Gf, int n2, int m) {
-  const size_t tot = (size_t)n2 * n2;
-  const int blocks = (int)std::min<size_t>((tot + 255) / 256, 4096);
-  mirror_f32_kernel<<<blocks, 256, 0, s>>>(G, Gf, n2, m); count_launches(1);
+as_status launch_gf_mirror(cudaStream_t s, const double* G, float* Gf, int n2, int valid, int m) {
+  if (m <= 0 || valid >= m) return AS_OK;
+  mirror_strip_kernel<<<m, 256, 0, s>>>(G, Gf, n2, std::max(valid, 0), m); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
-  return AS_OK;
-}
-
-as_status launch_gbf16_mirror(cudaStream_t s, const double* G, int n2, int m, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                              int n2p) {
-  const size_t tot = (size_t)n2p * n2p;
-  const int blocks = (int)std::min<size_t>((tot + 255) / 256, 4096);
-  mirror_bf16_kernel<<<blocks, 256, 0, s>>>(G, n2, m, hi, lo, n2p); count_launches(1);
-  AS_CUDA_TRY(cudaGetLastError());
-  return AS_OK;
-}
-
-as_status launch_batch_gspace(cudaStream_t s, const float* Gf, int n2, int r0, int nb, int k_pi, int q, Key key,
-                              uint64_t i0, const BatchBuffers& bb, Prof* prof, const TcBatch* tc) {
-  if (nb <= 0) return AS_OK;
-  const int ncol = 3 * nb;
-  const int mmax = r0 + nb;
-  const long long plane = (long long)n2 * ncol;
-  batch_fill_kernel<<<dim3(nb, 2), 128, 0, s>>>(bb.X, n2, nb, r0, key, i0); count_launches(1);
-  AS_CUDA_TRY(cudaGetLastError());
-  if (tc) {
-    as_status st = launch_split_bf16(s, bb.X, n2, ncol, n2, tc->Xh, tc->Xl, tc->n2p, false);
-    if (st != AS_OK) return st;
-  }
-  const int iters = std::max(k_pi, q);
-  for (int it = 0; it <= iters; ++it) {
-    const bool pi_on = it <= k_pi;
-    const bool si_on = it <= q;
-    const int c0 = pi_on ? 0 : nb;
-    const int c1 = si_on ? ncol : nb;
-    int S = std::min(skinny_splits(mmax, c1 - c0, mmax), bb.max_splits);
-    if (prof) prof->begin(PK_BATCH_GEMM, s);
-    as_status st;
-    if (tc) {
-      // split-BF16 tcgen05 product Y = G X: A = G (rows p, K = q), B = X^T (rows c, K = q)
-      const int Kp = (mmax + 63) / 64 * 64;
-      const int ktiles = Kp / 64;
-      const int mt = (mmax + 127) / 128;
-      S = std::max(1, std::min({(2 * 152 + mt - 1) / mt, ktiles, bb.max_splits}));
-      const int klen = ((ktiles + S - 1) / S) * 64;
-      S = (Kp + klen - 1) / klen;
-      st = launch_umma_gemm(s, *tc->mapG, *tc->mapX, mmax, c1 - c0, Kp, 192,
-                            3, S, c0, bb.P + (size_t)c0 * n2, 1, n2, plane, tc->err);
-    } else {
-      st = launch_skinny_partial(s, mmax, c1 - c0, mmax, &S, Gf, n2, bb.X + (size_t)c0 * n2, n2,
-                                 bb.P + (size_t)c0 * n2, n2, plane);
-    }
-    if (st != AS_OK) return st;
-    // algorithmic work of one product: 2 m^2 N flops; G (m^2 FP32) and X read, Y written
-    if (prof)
-      prof->end(PK_BATCH_GEMM, s, 2.0 * mmax * (double)mmax * (c1 - c0),
-                4.0 * ((double)mmax * mmax + 2.0 * (double)mmax * (c1 - c0)));
-    if (prof) prof->begin(PK_BATCH_ORTH, s);
-    if (S > 1) {
-      plane_reduce_kernel<<<dim3((mmax + 255) / 256, c1 - c0), 256, 0, s>>>(bb.P, plane, S, n2, c0, c1, mmax); count_launches(1);
-    }
-    // PI: iterations 0..k_pi-1 normalise, k_pi evaluates sigma^2;
-    // SI: iterations 0..q-1 orthonormalise, q does Rayleigh-Ritz.
-    const int kind0 = pi_on ? 0 : 1;
-    const int kinds = (pi_on ? 1 : 0) + (si_on ? 1 : 0);
-    batch_orth_kernel<<<dim3(nb, kinds), 512, 0, s>>>(bb.P, bb.X, n2, nb, r0, kind0, it == k_pi ? 1 : 0,
-                                                      it == q ? 1 : 0, bb.sig2, bb.ritz); count_launches(1);
-    AS_CUDA_TRY(cudaGetLastError());
-    if (tc && it < iters) {
-      const int nc0 = (it + 1 <= k_pi) ? 0 : nb;   // columns the next product reads
-      st = launch_split_bf16(s, bb.X + (size_t)nc0 * n2, n2, ncol - nc0, n2, tc->Xh + (size_t)nc0 * tc->n2p,
-                             tc->Xl + (size_t)nc0 * tc->n2p, tc->n2p, false);
-      if (st != AS_OK) return st;
-    }
-    if (prof) prof->end(PK_BATCH_ORTH, s, 0.0, 4.0 * (double)mmax * (c1 - c0) * (S + 2));
-  }
   return AS_OK;
 }
 

@@ -12,8 +12,8 @@ namespace as {
 
 // Optional per-kernel-class event timer (the sketch's AS_PROFILE mode).
 enum ProfClass {
-  PK_BATCH_GEMM = 0,  // batched G-space product  Y = G X  (FP32)
-  PK_BATCH_ORTH,      // batched normalisation / SVQB / Rayleigh-Ritz
+  PK_BATCH_GEMM = 0,  // batched G-space iterations (persistent kernel, FP32)
+  PK_BATCH_ORTH,      // starting vectors and FP32 mirror of G for the batch
   PK_EIG,             // FP64 eigensolver of the FD shrink
   PK_REBUILD,         // FD rebuild C' = W C~ and G = C' C'^T
   PK_GRAM,            // Gram rows of a block
@@ -106,8 +106,9 @@ size_t dump_work_doubles(int d, int xi);
 as_status launch_dump(cudaStream_t s, float* C, int ldc, int d, int r, double* G, int n2, const double* WU,
                       const double* GWU, int k, int xi, float* Z, float* Y, double* work);
 
-// FP32 mirror of the leading m x m block of G (zero elsewhere).
-as_status launch_gf_mirror(cudaStream_t s, const double* G, float* Gf, int n2, int m);
+// FP32 mirror of the leading m x m block of G for the rows/columns at or past
+// `valid` (the leading valid x valid block is already mirrored).
+as_status launch_gf_mirror(cudaStream_t s, const double* G, float* Gf, int n2, int valid, int m);
 
 // tcgen05 GEMM operand (umma.cu): TMA tensor maps over the BF16 levels of a
 // split FP32 matrix (m[0] = hi; m[1], m[2] the lower levels), K innermost,
@@ -116,32 +117,37 @@ struct UmmaOperand {
   CUtensorMap m[3];
 };
 
-// Tensor-core variant of the batched products (BF16 forms): G and X in
-// split-BF16 with leading dimension n2p (n2 rounded up to 64, zero padded).
-struct TcBatch {
-  const UmmaOperand* mapG;   // over Gf hi/lo, box 128
-  const UmmaOperand* mapX;   // over X hi/lo, box 192
-  __nv_bfloat16* Xh;         // 3*bmax x n2p
-  __nv_bfloat16* Xl;
-  int n2p;
-  int* err;
+// Scratch of the GEMM paths (split-K planes, also used by the FP32 Gram rows).
+struct BatchBuffers {
+  float* P;       // p_cap floats
+  int max_splits;
 };
 
-struct BatchBuffers {
-  float* X;       // n2 x 3*bmax, column-major
-  float* P;       // split-K partial planes (max_splits x n2 x 3*bmax)
-  int max_splits;
+// Buffers of the persistent batched iterations (batch_persist.cu).
+struct PersistBuffers {
+  float* Y;       // 2 buffers of ybuf floats, columns of ldy floats
+  long long ybuf;
+  int ldy;
+  size_t ycols;   // columns per buffer (batch_persist_ycols(bmax))
+  int bmax;
+  float* X;       // n2 x ycols, column-major (ld n2): final basis of every pair
+  float* part;    // batch_persist_part_floats(bmax)
+  unsigned* cnt;  // grid-barrier counter
   double* sig2;   // bmax   power-iteration estimates
   double* ritz;   // 2*bmax the two Ritz values of the k = 2 step
 };
+size_t batch_persist_ycols(int bmax);
+size_t batch_persist_part_floats(int bmax);
+// Column of the first vector of row t's simultaneous-iteration pair.
+int batch_si_col(int nb, int t);
 
-// Block-speculative power iteration and first doubling step for rows
-// t = 0..nb-1 of a block whose row t sees the leading (r0+t+1) rows (FP32).
-as_status launch_batch_gspace(cudaStream_t s, const float* Gf, int n2, int r0, int nb, int k_pi, int q, Key key,
-                              uint64_t i0, const BatchBuffers& bb, Prof* prof, const TcBatch* tc = nullptr);
-// Split-BF16 mirror of the leading m x m block of G (ld n2p, zero elsewhere).
-as_status launch_gbf16_mirror(cudaStream_t s, const double* G, int n2, int m, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                              int n2p);
+// Block-speculative power iteration (Algorithm 1) and first doubling step
+// (k = 2) of the simultaneous iteration (Algorithm 2) for rows t = 0..nb-1 of
+// a block whose row t sees the leading r0+t+1 rows of G; Gf is the FP32
+// mirror of G's leading (r0+nb) x (r0+nb) block.  One cooperative launch;
+// a grid-barrier wait that gives up sets AS_ETIMEOUT in *status.
+as_status launch_batch_persist(cudaStream_t s, const float* Gf, int n2, int r0, int nb, int k_pi, int q, Key key,
+                               uint64_t i0, const PersistBuffers& pb, int* status, Prof* prof = nullptr);
 
 // FP64 single-row power iteration and simultaneous iteration built from
 // multi-block products (any buffer size).  x, y: n2 doubles; zero: 1 int.
