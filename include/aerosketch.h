@@ -151,16 +151,19 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
  * non-finite value. */
 as_status sketch_update(as_sketch* h, const float* rows, int64_t n, int64_t ld);
 
-/* Algorithm 5 at the current time (t = -1; other t return AS_ENOTSUP):
- * writes the l x d sketch B_hat, row-major with leading dimension ldo >= d,
- * to `out` (host or device), and the number of rows written (l) to
- * *rows_out.  Synchronises. */
+/* Algorithm 8's Query(t) = Algorithm 5 with lb = 0, ub = t: writes the
+ * l x d sketch B_hat, row-major with leading dimension ldo >= d, to `out`
+ * (host or device), and the number of rows written (l) to *rows_out.
+ * t = -1 or t = T (rows fed so far) is the current time: B = C_T^T C_T plus
+ * every snapshot term.  0 <= t < T is a historical time: the residual C_t is
+ * not stored, and B is the sum of the snapshot terms taken at rows <= t (the
+ * B_t of the ATTP error analysis).  Other t: AS_EINVAL.  Synchronises. */
 as_status sketch_query(as_sketch* h, int64_t t, float* out, int64_t ldo, int32_t* rows_out);
 
-/* The matrix B of Algorithm 5 lines 1-4 at the current time (before its
- * eigendecomposition): d x d FP64, row-major, to host memory `out`.
- * Synchronises. */
-as_status sketch_query_gram(as_sketch* h, double* out);
+/* The matrix B of Algorithm 5 lines 1-4 for the time t of sketch_query
+ * (before its eigendecomposition): d x d FP64, row-major, to host memory
+ * `out`.  Synchronises. */
+as_status sketch_query_gram(as_sketch* h, int64_t t, double* out);
 
 /* Copy the residual buffer C (2l x d FP32, row-major, leading dimension d)
  * and the row count r to host memory.  Synchronises. */

@@ -43,6 +43,9 @@ the design notes of the repository):
      largest magnitude of u_j (the left singular vector, a 2l-vector) is
      positive, the lowest index winning exact ties.
  R11 The current-time query (lb = 0, ub = T) includes C_T (Algorithm 5 line 1).
+ R12 A historical query ub = t < T (Algorithm 8's Query(t) = Query(0, t)) has
+     no residual C_t to add (it is not stored); B is the sum of the snapshot
+     terms with t_j <= t, as in B_i of the ATTP error analysis.
 """
 from __future__ import annotations
 
@@ -278,11 +281,16 @@ class AeroSketch:
     # -- Algorithm 5 ------------------------------------------------------------
     def pre_query(self, lb: int = 0, ub: int | None = None) -> np.ndarray:
         """B of Algorithm 5 lines 1-4 (before the eigendecomposition).
-        Only the current time (ub = T) is supported here."""
+
+        At the current time (ub = T) B = C_T^T C_T plus the snapshot terms
+        with lb < t <= T.  For a historical time ub < T (the ATTP Query(t) of
+        Algorithm 8 asks for Query(0, t)) the residual C_ub is no longer
+        stored, and B is the sum of the snapshot terms with lb < t <= ub, the
+        B_i of the ATTP error analysis (reading R12)."""
         ub = self.T if ub is None else ub
-        if ub != self.T:
-            raise NotImplementedError("historical queries are not part of this oracle")
-        B = self.C.T @ self.C
+        if not (0 <= ub <= self.T):
+            raise ValueError("ub must lie in [0, T]")
+        B = self.C.T @ self.C if ub == self.T else np.zeros((self.d, self.d))
         for sn in self.S:
             if lb < sn.t <= ub:
                 B += snapshot_term(sn.Z, sn.Y)

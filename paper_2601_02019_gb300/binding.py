@@ -74,7 +74,7 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.sketch_create.argtypes = [ct.POINTER(AsConfig), P, ct.POINTER(P)]
     L.sketch_update.argtypes = [P, P, I64, I64]
     L.sketch_query.argtypes = [P, I64, P, I64, ct.POINTER(I32)]
-    L.sketch_query_gram.argtypes = [P, P]
+    L.sketch_query_gram.argtypes = [P, I64, P]
     L.sketch_get_buffer.argtypes = [P, P, ct.POINTER(I32)]
     L.sketch_get_gram.argtypes = [P, P]
     L.sketch_merge.argtypes = [P, P]
@@ -154,16 +154,17 @@ class Sketch:
             assert rows.dtype == np.float32 and rows.strides[1] == 4
         _check(lib().sketch_update(self._h, ct.c_void_p(_ptr(rows)), n, ld), "sketch_update")
 
-    def query(self) -> np.ndarray:
+    def query(self, t: int = -1) -> np.ndarray:
+        """Query(t) of Algorithm 8 (t = -1: the current time)."""
         out = np.zeros((self.ell, self.d), dtype=np.float32)
         rows = ct.c_int32()
-        _check(lib().sketch_query(self._h, -1, ct.c_void_p(out.ctypes.data), self.d, ct.byref(rows)),
+        _check(lib().sketch_query(self._h, t, ct.c_void_p(out.ctypes.data), self.d, ct.byref(rows)),
                "sketch_query")
         return out[: rows.value]
 
-    def query_gram(self) -> np.ndarray:
+    def query_gram(self, t: int = -1) -> np.ndarray:
         out = np.zeros((self.d, self.d), dtype=np.float64)
-        _check(lib().sketch_query_gram(self._h, ct.c_void_p(out.ctypes.data)), "sketch_query_gram")
+        _check(lib().sketch_query_gram(self._h, t, ct.c_void_p(out.ctypes.data)), "sketch_query_gram")
         return out
 
     def buffer(self) -> tuple[np.ndarray, int]:

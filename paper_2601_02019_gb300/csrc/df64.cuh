@@ -1,0 +1,125 @@
+// Double-float ("df64") arithmetic: a value is the unevaluated sum hi + lo of
+// two FP32 numbers with |lo| <= ulp(hi)/2, about 48 significant bits.  On this
+// part FP64 throughput is a small fraction of FP32 throughput, so the
+// eigensolver's O(n^3) loops run in df64 on the FP32 pipes.
+//
+// The building blocks are the error-free transformations: Knuth's TwoSum
+// (s + e = a + b exactly), Dekker's FastTwoSum (the same when |a| >= |b|) and
+// the FMA form of Dekker's TwoProduct (p + e = a * b exactly).  Sums and
+// products are then formed as in the double-double literature (Dekker 1971;
+// Hida, Li and Bailey 2001): the high parts through an error-free step, the
+// low-order terms gathered in plain FP32, one renormalisation at the end.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace as {
+
+struct df64 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df64 df_make(float hi, float lo) { return df64{hi, lo}; }
+
+// s + e = a + b exactly (any a, b).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// s + e = a + b exactly when |a| >= |b| (or a = 0).
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// p + e = a * b exactly (FMA computes the rounding error of the product).
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+__device__ __forceinline__ df64 df_renorm(float s, float e) {
+  df64 r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+
+// Conversions.  from_double: hi = fl32(x), lo = fl32(x - hi).
+__device__ __forceinline__ df64 df_from_double(double x) {
+  const float hi = (float)x;
+  const float lo = (float)(x - (double)hi);
+  return df64{hi, lo};
+}
+__device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df64 df_neg(df64 a) { return df64{-a.hi, -a.lo}; }
+
+// a + b
+__device__ __forceinline__ df64 df_add(df64 a, df64 b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_renorm(s, e);
+}
+
+// a - b
+__device__ __forceinline__ df64 df_sub(df64 a, df64 b) { return df_add(a, df_neg(b)); }
+
+// a * b
+__device__ __forceinline__ df64 df_mul(df64 a, df64 b) {
+  float p, e;
+  two_prod(a.hi, b.hi, p, e);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_renorm(p, e);
+}
+
+// c + a * b with one renormalisation.
+__device__ __forceinline__ df64 df_fma(df64 a, df64 b, df64 c) {
+  float p, e;
+  two_prod(a.hi, b.hi, p, e);
+  float s, f;
+  two_sum(c.hi, p, s, f);
+  f = __fadd_rn(f, e);
+  f = __fmaf_rn(a.hi, b.lo, f);
+  f = __fmaf_rn(a.lo, b.hi, f);
+  f = __fadd_rn(f, c.lo);
+  return df_renorm(s, f);
+}
+
+// a - (u * v + w * z): the two-sided rank-2 update of one matrix entry.
+__device__ __forceinline__ df64 df_rank2(df64 a, df64 u, df64 v, df64 w, df64 z) {
+  float p1, e1, p2, e2;
+  two_prod(u.hi, v.hi, p1, e1);
+  two_prod(w.hi, z.hi, p2, e2);
+  float s, f1, s2, f2;
+  two_sum(a.hi, -p1, s, f1);
+  two_sum(s, -p2, s2, f2);
+  float lo = __fsub_rn(a.lo, __fadd_rn(e1, e2));
+  lo = __fadd_rn(lo, __fadd_rn(f1, f2));
+  lo = __fmaf_rn(-u.hi, v.lo, lo);
+  lo = __fmaf_rn(-u.lo, v.hi, lo);
+  lo = __fmaf_rn(-w.hi, z.lo, lo);
+  lo = __fmaf_rn(-w.lo, z.hi, lo);
+  return df_renorm(s2, lo);
+}
+
+// a / b (one correction step of the FP32 quotient).
+__device__ __forceinline__ df64 df_div(df64 a, df64 b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  // r = a - q1 * b, exactly enough for the correction
+  float p, e;
+  two_prod(q1, b.hi, p, e);
+  float s, f;
+  two_sum(a.hi, -p, s, f);
+  f = __fsub_rn(f, e);
+  f = __fadd_rn(f, a.lo);
+  f = __fmaf_rn(-q1, b.lo, f);
+  const float r = __fadd_rn(s, f);
+  const float q2 = __fdiv_rn(r, b.hi);
+  return df_renorm(q1, q2);
+}
+
+}  // namespace as

@@ -1,17 +1,22 @@
-// FP64 symmetric eigensolver spread over the whole GPU, for the large core
+// Symmetric eigensolver spread over the whole GPU, for the large core
 // matrices (the 2l x 2l Gram of the FD shrink when l is large, and the query).
-// Same method as eig.cuh (Householder tridiagonalisation, Sturm bisection,
-// inverse iteration, back-transformation), with each phase split across
-// thread blocks:
-//   * tridiagonalisation step k: kernel 1 forms v_k (every block recomputes it
-//     from row k) and p = A22 v_k, one warp per row, with per-block partial
-//     sums of v^T p; kernel 2 sums the partials in a fixed order and applies
-//     A22 -= v w^T + w v^T, w = 2p - 2(v^T p) v.  No atomics: results are
-//     bitwise reproducible.
-//   * bisection: one warp per eigenvalue (multisection); inverse iteration:
-//     one thread per eigenvalue.
-//   * back-transformation: each block owns a slab of eigenvector columns in
-//     shared memory and applies every reflector to it.
+// FP64 in and out.  Method: Householder tridiagonalisation, Sturm bisection,
+// inverse iteration, back-transformation (as eig.cuh).  The O(n^3) loops run
+// in double-float arithmetic (df64.cuh, about 48 significant bits) on the
+// FP32 pipes, because FP64 throughput is a small fraction of FP32 on this
+// part; A is scaled by a power of two so that its entries fit FP32's
+// exponent range, and converted in place.
+//   * tridiagonalisation step k (df64): one kernel applies step k's update
+//     A22 -= v w^T + w v^T (w = 2p - 2(v^T p) v) and, in the same pass, forms
+//     v_{k+1} (every block recomputes it from row k+1) and p = A22 v_{k+1},
+//     one warp per row, with per-block partial sums of v^T p summed in a fixed
+//     order by the next step.  No atomics: results are bitwise reproducible.
+//   * bisection: eight lanes per eigenvalue (multisection) on df64 Sturm
+//     counts of T / ||T||; inverse iteration in FP64, one thread per
+//     eigenvalue.
+//   * back-transformation (df64): each block owns a slab of eigenvector
+//     columns in shared memory and applies every reflector to it.
+#include "df64.cuh"
 #include "eig.cuh"
 #include "kernels.cuh"
 
@@ -32,161 +37,6 @@ struct TriWork {
   double* part2;  // partials of the second buffer
 };
 
-__device__ __forceinline__ void house_params(const double* row, int m, double* red, double& s_out,
-                                             double& alpha, double& vn) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) s += row[i] * row[i];
-  s = block_sum(s, red);
-  const double x0 = row[0];
-  s_out = s;
-  if (s == 0.0) { alpha = 0.0; vn = 1.0; return; }
-  alpha = (x0 >= 0.0) ? -sqrt(s) : sqrt(s);
-  vn = sqrt(s - x0 * x0 + (x0 - alpha) * (x0 - alpha));
-}
-
-__global__ void __launch_bounds__(256) tri_step1(double* A, int lda, int n, int k, TriWork w) {
-  extern __shared__ double vs[];  // m doubles
-  __shared__ double red[32];
-  const int m = n - k - 1;
-  const double* row = A + (size_t)k * lda + (k + 1);
-  double s, alpha, vn;
-  house_params(row, m, red, s, alpha, vn);
-  for (int i = threadIdx.x; i < m; i += blockDim.x)
-    vs[i] = (s == 0.0) ? 0.0 : ((i == 0) ? (row[0] - alpha) : row[i]) / vn;
-  __syncthreads();
-  if (blockIdx.x == 0) {
-    for (int i = threadIdx.x; i < m; i += blockDim.x) w.v[i] = vs[i];
-    if (threadIdx.x == 0) { w.d[k] = A[(size_t)k * lda + k]; w.e[k] = alpha; }
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int i = blockIdx.x * kTriRowsPerBlock + wid;
-  double contrib = 0.0;
-  if (i < m) {
-    const double* ar = A + (size_t)(k + 1 + i) * lda + (k + 1);
-    double acc = 0.0;
-    for (int j = lane; j < m; j += 32) acc += ar[j] * vs[j];
-    acc = warp_sum(acc);
-    if (lane == 0) { w.p[i] = acc; contrib = acc * vs[i]; }
-  }
-  // deterministic block partial of v^T p (warp order)
-  __shared__ double wpart[kTriRowsPerBlock];
-  if (lane == 0) wpart[wid] = contrib;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < kTriRowsPerBlock; ++q) t += wpart[q];
-    w.part[blockIdx.x] = t;
-  }
-}
-
-// Fused step k (k >= 0): apply step k's update A22 -= v w^T + w v^T
-// (w = 2p - 2(v^T p)v) to rows and columns >= k+2, and in the same pass form
-// step k+1's Householder vector (every block recomputes it from the updated
-// row k+1) and p_{k+1} = A22' v_{k+1}.  Row and column k+1 of A are not
-// updated: only their diagonal (d[k+1]) and v_{k+1} are needed afterwards.
-// Double-buffered vectors: in = (v_k, p_k, parts_k), out = (v_{k+1}, p_{k+1}, parts_{k+1}),
-// indexed by absolute row (entries [k+1, n) of in, [k+2, n) of out).
-struct TriVec { double* v; double* p; double* part; int nparts; };
-
-__global__ void __launch_bounds__(256) tri_fused(double* A, int lda, int n, int k, TriVec in, TriVec out,
-                                                 double* d, double* e) {
-  extern __shared__ double sm[];
-  double* wk = sm;          // w_k[j], j in [k+1, n)   (offset k+1)
-  double* vk = sm + n;      // v_k[j]
-  double* vn_ = sm + 2 * n; // v_{k+1}[j], j in [k+2, n)
-  __shared__ double red[32];
-  __shared__ double c_s;
-  const int tid = threadIdx.x;
-  if (tid < 32) {   // v^T p from the previous step's block partials (fixed order)
-    double c = 0.0;
-    for (int q = tid; q < in.nparts; q += 32) c += in.part[q];
-    c = warp_sum(c);
-    if (tid == 0) c_s = c;
-  }
-  __syncthreads();
-  const double c = c_s;
-  for (int j = k + 1 + tid; j < n; j += blockDim.x) {
-    const double v = in.v[j];
-    vk[j] = v;
-    wk[j] = 2.0 * in.p[j] - 2.0 * c * v;
-  }
-  __syncthreads();
-  const int k1 = k + 1;
-  const double vk1 = vk[k1], wk1 = wk[k1];
-  if (blockIdx.x == 0) {
-    // keep v_k in row k of A for the back-transformation; d[k+1] = updated diagonal
-    for (int j = k + 1 + tid; j < n; j += blockDim.x) A[(size_t)k * lda + j] = vk[j];
-    if (tid == 0) d[k1] = A[(size_t)k1 * lda + k1] - 2.0 * vk1 * wk1;
-  }
-  if (k1 + 1 >= n) return;
-  // updated row k+1 over columns [k+2, n): x_j = A[k+1][j] - v_{k+1} w_j - w_{k+1} v_j
-  const int m1 = n - k1 - 1;
-  double s = 0.0;
-  for (int j = k1 + 1 + tid; j < n; j += blockDim.x) {
-    const double x = A[(size_t)k1 * lda + j] - vk1 * wk[j] - wk1 * vk[j];
-    vn_[j] = x;
-    s += x * x;
-  }
-  s = block_sum(s, red);
-  if (m1 == 1) {
-    // last 2 x 2 block: no further reflector
-    if (blockIdx.x == 0 && tid == 0) {
-      const int j = n - 1;
-      e[k1] = vn_[j];
-      d[j] = A[(size_t)j * lda + j] - 2.0 * vk[j] * wk[j];
-      e[j] = 0.0;
-    }
-    return;
-  }
-  const double x0 = vn_[k1 + 1];
-  double alpha = 0.0, vnorm = 1.0;
-  if (s > 0.0) {
-    alpha = (x0 >= 0.0) ? -sqrt(s) : sqrt(s);
-    vnorm = sqrt(s - x0 * x0 + (x0 - alpha) * (x0 - alpha));
-  }
-  __syncthreads();
-  for (int j = k1 + 1 + tid; j < n; j += blockDim.x)
-    vn_[j] = (s == 0.0) ? 0.0 : ((j == k1 + 1) ? (vn_[j] - alpha) : vn_[j]) / vnorm;
-  __syncthreads();
-  if (blockIdx.x == 0) {
-    for (int j = k1 + 1 + tid; j < n; j += blockDim.x) out.v[j] = vn_[j];
-    if (tid == 0) e[k1] = alpha;
-  }
-  // rows i in [k+2, n): one warp per row; update and dot with v_{k+1}
-  const int lane = tid & 31, wid = tid >> 5;
-  const int i = k1 + 1 + blockIdx.x * 8 + wid;
-  double contrib = 0.0;
-  if (i < n) {
-    double* ar = A + (size_t)i * lda;
-    const double vi = vk[i], wi = wk[i];
-    double acc = 0.0;
-    for (int j = k1 + 1 + lane; j < n; j += 32) {
-      const double a = ar[j] - vi * wk[j] - wi * vk[j];
-      ar[j] = a;
-      acc += a * vn_[j];
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) { out.p[i] = acc; contrib = acc * vn_[i]; }
-  }
-  __shared__ double wpart[8];
-  if (lane == 0) wpart[wid] = contrib;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int q = 0; q < 8; ++q) t += wpart[q];
-    out.part[blockIdx.x] = t;
-  }
-}
-
-__global__ void tri_tail(const double* A, int lda, int n, TriWork w) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    w.d[n - 2] = A[(size_t)(n - 2) * lda + (n - 2)];
-    w.e[n - 2] = A[(size_t)(n - 2) * lda + (n - 1)];
-    w.d[n - 1] = A[(size_t)(n - 1) * lda + (n - 1)];
-    w.e[n - 1] = 0.0;
-  }
-}
-
 // tnorm, pivmin of T
 __global__ void tri_norm(int n, TriWork w, double* out2) {
   __shared__ double red[32];
@@ -201,37 +51,130 @@ __global__ void tri_norm(int n, TriWork w, double* out2) {
   if (threadIdx.x == 0) { out2[0] = tn; out2[1] = 2.2250738585072014e-308 * fmax(1.0, em); }
 }
 
-// One warp per eigenvalue: multisection on Sturm counts (each round the 32
-// lanes evaluate 31 interior points, narrowing the bracket 32-fold) down to an
-// absolute width of 4 eps ||T||, then inverse iteration by lane 0.
-__global__ void bisect_invit(int n, int nev, TriWork w, const double* norms, double* evals, double* X, int ldx,
-                             double* lu) {
+// Eight lanes per eigenvalue (four eigenvalues per warp): multisection on
+// Sturm counts, each round evaluating 7 interior points and narrowing the
+// bracket 8-fold, down to an absolute width of 4 eps ||T||; then inverse
+// iteration by the group's first lane.  Eight lanes spend 7/3 Sturm counts per
+// bit (a 32-lane multisection spends 31/5): the Sturm recurrences are bound by
+// FP64 throughput on this part, and the shorter chain of rounds keeps the
+// latency down.  The round loop is warp-uniform (the ballot spans the warp).
+constexpr int kBisLanes = 8;
+
+// Modified Gram-Schmidt inside clusters of close eigenvalues (one block).
+__global__ void cluster_mgs(int n, int nev, const double* norms, const double* evals, double* X, int ldx) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double ctol = 1e-9 * fmax(norms[0], norms[1]) * norms[3];   // evals are unscaled
+  int c0 = 0;
+  for (int j = 1; j < nev; ++j) {
+    if (evals[j - 1] - evals[j] > ctol) { c0 = j; continue; }
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int q = c0; q < j; ++q) {
+        double s = 0.0;
+        for (int i = tid; i < n; i += nt) s += X[(size_t)i * ldx + q] * X[(size_t)i * ldx + j];
+        s = block_sum(s, red);
+        for (int i = tid; i < n; i += nt) X[(size_t)i * ldx + j] -= s * X[(size_t)i * ldx + q];
+        __syncthreads();
+      }
+      double s = 0.0;
+      for (int i = tid; i < n; i += nt) s += X[(size_t)i * ldx + j] * X[(size_t)i * ldx + j];
+      s = block_sum(s, red);
+      const double sc = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+      for (int i = tid; i < n; i += nt) X[(size_t)i * ldx + j] *= sc;
+      __syncthreads();
+    }
+  }
+}
+
+// Back-transformation: each block owns columns [c0, c0 + kSlab) of X.
+constexpr int kSlab = 4;
+
+
+// ---- double-float (df64) kernels -------------------------------------------
+// T scaled by 1/||T|| in df64: dd[i] = d_i / tn, e2[i] = (e_i / tn)^2.  With
+// |entries| <= 1 the Sturm recurrence stays far from FP32 overflow.
+__global__ void tri_scale_df(int n, TriWork w, const double* norms, df64* dd, df64* e2) {
+  const double tn = norms[0];
+  const double inv = (tn > 0.0) ? 1.0 / tn : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    dd[i] = df_from_double(w.d[i] * inv);
+    const double es = (i + 1 < n) ? w.e[i] * inv : 0.0;
+    e2[i] = df_from_double(es * es);
+  }
+}
+
+// q <- a - b / q with the quotient from a fast FP32 estimate and one df64
+// correction (q1 + (num - q1 b) / b), accurate to about 2^-44 relative.
+__device__ __forceinline__ df64 df_div_fast(df64 a, df64 b) {
+  const float q1 = __fdividef(a.hi, b.hi);
+  float p, e;
+  two_prod(q1, b.hi, p, e);
+  float s, f;
+  two_sum(a.hi, -p, s, f);
+  f = __fsub_rn(f, e);
+  f = __fadd_rn(f, a.lo);
+  f = __fmaf_rn(-q1, b.lo, f);
+  const float q2 = __fdividef(__fadd_rn(s, f), b.hi);
+  return df_renorm(q1, q2);
+}
+
+// Number of eigenvalues of the scaled T below x (LDL^T pivots in df64; a
+// pivot smaller than pivmin is replaced by -pivmin as in the FP64 count).
+__device__ int sturm_count_df(int n, const df64* dd, const df64* e2, df64 x, float pivmin) {
+  int c = 0;
+  df64 q = df_sub(dd[0], x);
+  if (fabsf(q.hi) < pivmin) q = df64{-pivmin, 0.f};
+  if (q.hi < 0.f) ++c;
+  for (int i = 1; i < n; ++i) {
+    q = df_sub(df_sub(dd[i], x), df_div_fast(e2[i - 1], q));
+    if (fabsf(q.hi) < pivmin) q = df64{-pivmin, 0.f};
+    if (q.hi < 0.f) ++c;
+  }
+  return c;
+}
+
+// Multisection on the scaled T with df64 Sturm counts (eight lanes per
+// eigenvalue, as bisect_invit), then inverse iteration in FP64 by the group's
+// first lane.  The bracket is kept in FP64; evaluation points are rounded to
+// df64.  Stops at a width of 2^-44 of ||T|| (df64 resolution).
+__global__ void bisect_invit_df(int n, int nev, TriWork w, const double* norms, const df64* dd, const df64* e2,
+                                double* evals, double* X, int ldx, double* lu) {
   const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= nev) return;
-  const double tnorm = norms[0], pivmin = norms[1];
+  const int g = lane & (kBisLanes - 1), grp = lane / kBisLanes;
+  const int j = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / kBisLanes) + grp;
+  const bool active = j < nev;
+  const double tnorm = norms[0];
   const double eps = 2.220446049250313e-16;
+  const int idx = n - 1 - j;
+  const float pivmin = 0x1p-100f;
+  const double tol = 0x1p-44;
+  double lo = -1.0 - tol, hi = 1.0 + tol;
+  bool stop = !active || tnorm == 0.0;
+  for (int it = 0; it < 64; ++it) {
+    if (!stop && hi - lo <= tol * fmax(1.0, fmax(fabs(lo), fabs(hi)))) stop = true;
+    if (__all_sync(0xffffffffu, stop)) break;
+    const double step = (hi - lo) / (double)kBisLanes;
+    bool above = true;
+    if (!stop && g < kBisLanes - 1)
+      above = sturm_count_df(n, dd, e2, df_from_double(lo + (double)(g + 1) * step), pivmin) > idx;
+    const unsigned mask = (__ballot_sync(0xffffffffu, above) >> (grp * kBisLanes)) & ((1u << kBisLanes) - 1);
+    if (!stop) {
+      const int first = __ffs(mask) - 1;
+      const double nlo = (first == 0) ? lo : lo + (double)first * step;
+      const double nhi = (first >= kBisLanes - 1) ? hi : lo + (double)(first + 1) * step;
+      if (!(nhi > nlo)) {
+        stop = true;
+      } else {
+        lo = nlo;
+        hi = nhi;
+      }
+    }
+  }
+  if (g != 0 || !active) return;
   const double* d = w.d;
   const double* e = w.e;
-  const int idx = n - 1 - j;
-  double lo = -tnorm - 2 * eps * tnorm - pivmin, hi = tnorm + 2 * eps * tnorm + pivmin;
-  const double atol = 4 * eps * fmax(tnorm, pivmin);
-  for (int it = 0; it < 40; ++it) {
-    if (hi - lo <= atol + 2 * eps * fmax(fabs(lo), fabs(hi))) break;
-    // lane l evaluates x_l = lo + (l+1) (hi-lo)/32, l = 0..30; lane 31 idle
-    const double x = lo + (double)(lane + 1) * ((hi - lo) / 32.0);
-    const bool above = (lane < 31) ? (sturm_count(n, d, e, x, pivmin) > idx) : true;
-    const unsigned mask = __ballot_sync(0xffffffffu, above);
-    const int first = __ffs(mask) - 1;   // smallest lane whose point lies above the eigenvalue
-    const double nlo = (first == 0) ? lo : lo + (double)first * ((hi - lo) / 32.0);
-    const double nhi = (first >= 31) ? hi : lo + (double)(first + 1) * ((hi - lo) / 32.0);
-    if (!(nhi > nlo)) break;
-    lo = nlo;
-    hi = nhi;
-  }
-  if (lane != 0) return;
-  const double lam = (tnorm == 0.0) ? 0.0 : 0.5 * (lo + hi);   // a zero matrix has exact zero eigenvalues
-  evals[j] = lam;
+  const double lam = (tnorm == 0.0) ? 0.0 : 0.5 * (lo + hi) * tnorm;   // of the scaled matrix
+  evals[j] = lam * norms[3];                                            // exact power-of-two unscaling
   // inverse iteration (same factorisation as eig.cuh)
   const double tiny = fmax(eps * tnorm, 1e-300);
   double* u0 = lu + (size_t)(0 * n) * nev + j;
@@ -290,78 +233,276 @@ __global__ void bisect_invit(int n, int nev, TriWork w, const double* norms, dou
   }
 }
 
-// Modified Gram-Schmidt inside clusters of close eigenvalues (one block).
-__global__ void cluster_mgs(int n, int nev, const double* norms, const double* evals, double* X, int ldx) {
+__device__ __forceinline__ df64 df_warp_sum(df64 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const df64 t{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = df_add(v, t);
+  }
+  return v;
+}
+
+// max |A_ij| as the bit pattern of a non-negative double (ordered like an
+// unsigned integer), by atomicMax: the result does not depend on the order.
+__global__ void amax_bits(const double* A, int lda, int n, unsigned long long* out) {
   __shared__ double red[32];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const double ctol = 1e-9 * fmax(norms[0], norms[1]);
-  int c0 = 0;
-  for (int j = 1; j < nev; ++j) {
-    if (evals[j - 1] - evals[j] > ctol) { c0 = j; continue; }
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int q = c0; q < j; ++q) {
-        double s = 0.0;
-        for (int i = tid; i < n; i += nt) s += X[(size_t)i * ldx + q] * X[(size_t)i * ldx + j];
-        s = block_sum(s, red);
-        for (int i = tid; i < n; i += nt) X[(size_t)i * ldx + j] -= s * X[(size_t)i * ldx + q];
-        __syncthreads();
-      }
-      double s = 0.0;
-      for (int i = tid; i < n; i += nt) s += X[(size_t)i * ldx + j] * X[(size_t)i * ldx + j];
-      s = block_sum(s, red);
-      const double sc = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
-      for (int i = tid; i < n; i += nt) X[(size_t)i * ldx + j] *= sc;
-      __syncthreads();
-    }
+  double m = 0.0;
+  const size_t tot = (size_t)n * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / n, j = e - i * n;
+    m = fmax(m, fabs(A[i * lda + j]));
+  }
+  m = block_max(m, red);
+  if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// scale[0] = 2^-e with max |A| * 2^-e in [1, 2) (1 for a zero matrix),
+// scale[1] = 2^e: exact powers of two.
+__global__ void pow2_scale(const unsigned long long* bits, double* scale) {
+  const double m = __longlong_as_double((long long)*bits);
+  const int ex = (m > 0.0 && m < INFINITY) ? ilogb(m) : 0;
+  scale[0] = ldexp(1.0, -ex);
+  scale[1] = ldexp(1.0, ex);
+}
+
+// In-place conversion of A * scale (FP64, n x n, ld lda) to df64: the same
+// 8 bytes per entry now hold (hi, lo).  The power-of-two scale keeps the
+// entries inside the FP32 exponent range.
+__global__ void to_df_inplace(double* A, int lda, int n, const double* scale) {
+  const double sc = scale[0];
+  const size_t tot = (size_t)n * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / n, j = e - i * n;
+    double* p = A + i * lda + j;
+    const df64 v = df_from_double(*p * sc);
+    *reinterpret_cast<df64*>(p) = v;
   }
 }
 
-// Back-transformation: each block owns columns [c0, c0 + kSlab) of X.
-constexpr int kSlab = 4;
-__global__ void __launch_bounds__(256) back_transform(const double* A, int lda, int n, int nev, double* X, int ldx) {
-  extern __shared__ double xs[];  // n x kSlab
-  __shared__ double red[kSlab][8];
+// Sum over the block of a df64 value; every thread gets the result.
+__device__ __forceinline__ df64 df_block_sum(df64 v, df64* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = df_warp_sum(v);
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    df64 t = red[0];
+    for (int q = 1; q < nw; ++q) t = df_add(t, red[q]);
+    red[0] = t;
+  }
+  __syncthreads();
+  const df64 t = red[0];
+  __syncthreads();
+  return t;
+}
+
+// Householder data of a df64 row x[0..m): s = ||x||^2, alpha, ||x - alpha e_1||.
+__device__ __forceinline__ void house_params_df(const df64* x, int m, df64* red, double& s, double& alpha,
+                                                double& vn) {
+  df64 acc{0.f, 0.f};
+  for (int i = threadIdx.x; i < m; i += blockDim.x) acc = df_fma(x[i], x[i], acc);
+  s = df_to_double(df_block_sum(acc, red));
+  const double x0 = df_to_double(x[0]);
+  if (s == 0.0) { alpha = 0.0; vn = 1.0; return; }
+  alpha = (x0 >= 0.0) ? -sqrt(s) : sqrt(s);
+  vn = sqrt(s - x0 * x0 + (x0 - alpha) * (x0 - alpha));
+}
+
+// v_j = (x_j - alpha [j == 0]) / vn in df64 (zero vector when s = 0).
+__device__ __forceinline__ df64 house_v_df(df64 xj, bool first, double s, double alpha, df64 rvn) {
+  if (s == 0.0) return df64{0.f, 0.f};
+  const df64 t = first ? df_sub(xj, df_from_double(alpha)) : xj;
+  return df_mul(t, rvn);
+}
+
+// Step 0 in df64 (see tri_step1): v_0 from row 0, p_0 = A22 v_0 and the block
+// partials of v_0^T p_0.  Vectors use TriWork's arrays as df64.
+__global__ void __launch_bounds__(256) tri_step1_df(df64* A, int lda, int n, TriWork w) {
+  extern __shared__ df64 vsd[];  // m values
+  __shared__ df64 red[32];
+  const int m = n - 1;
+  const df64* row = A + 1;
+  double s, alpha, vn;
+  house_params_df(row, m, red, s, alpha, vn);
+  const df64 rvn = df_from_double(1.0 / vn);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) vsd[i] = house_v_df(row[i], i == 0, s, alpha, rvn);
+  __syncthreads();
+  df64* wv = reinterpret_cast<df64*>(w.v);
+  df64* wp = reinterpret_cast<df64*>(w.p);
+  df64* wpart = reinterpret_cast<df64*>(w.part);
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) wv[i] = vsd[i];
+    if (threadIdx.x == 0) { w.d[0] = df_to_double(A[0]); w.e[0] = alpha; }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int i = blockIdx.x * kTriRowsPerBlock + wid;
+  df64 contrib{0.f, 0.f};
+  if (i < m) {
+    const df64* ar = A + (size_t)(1 + i) * lda + 1;
+    df64 acc{0.f, 0.f};
+    for (int j = lane; j < m; j += 32) acc = df_fma(ar[j], vsd[j], acc);
+    acc = df_warp_sum(acc);
+    if (lane == 0) { wp[i] = acc; contrib = df_mul(acc, vsd[i]); }
+  }
+  __shared__ df64 bpart[kTriRowsPerBlock];
+  if (lane == 0) bpart[wid] = contrib;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    df64 t = bpart[0];
+    for (int q = 1; q < kTriRowsPerBlock; ++q) t = df_add(t, bpart[q]);
+    wpart[blockIdx.x] = t;
+  }
+}
+
+struct TriVecDf { df64* v; df64* p; df64* part; int nparts; };
+
+// Fused step k in df64 (see tri_fused): apply step k's update
+// A22 -= v w^T + w v^T (w = 2p - 2(v^T p) v) to rows/columns >= k+2, form
+// v_{k+1} from the updated row k+1 and p_{k+1} = A22' v_{k+1}.  v_k is kept in
+// row k of A (df64) for the back-transformation; d and e are written in FP64.
+__global__ void __launch_bounds__(256) tri_fused_df(df64* A, int lda, int n, int k, TriVecDf in, TriVecDf out,
+                                                    double* d, double* e) {
+  extern __shared__ df64 smd[];
+  df64* wk = smd;           // w_k[j], j in [k+1, n)
+  df64* vk = smd + n;       // v_k[j]
+  df64* vn_ = smd + 2 * n;  // v_{k+1}[j], j in [k+2, n)
+  __shared__ df64 red[32];
+  __shared__ df64 c_s;
+  const int tid = threadIdx.x;
+  if (tid < 32) {   // v^T p from the previous step's block partials (fixed order)
+    df64 c{0.f, 0.f};
+    for (int q = tid; q < in.nparts; q += 32) c = df_add(c, in.part[q]);
+    c = df_warp_sum(c);
+    if (tid == 0) c_s = c;
+  }
+  __syncthreads();
+  const df64 c2 = df64{2.f * c_s.hi, 2.f * c_s.lo};
+  for (int j = k + 1 + tid; j < n; j += blockDim.x) {
+    const df64 v = in.v[j];
+    const df64 p = in.p[j];
+    vk[j] = v;
+    // w = 2p - 2c v
+    wk[j] = df_sub(df64{2.f * p.hi, 2.f * p.lo}, df_mul(c2, v));
+  }
+  __syncthreads();
+  const int k1 = k + 1;
+  const df64 vk1 = vk[k1], wk1 = wk[k1];
+  if (blockIdx.x == 0) {
+    for (int j = k + 1 + tid; j < n; j += blockDim.x) A[(size_t)k * lda + j] = vk[j];
+    if (tid == 0) {
+      const df64 dd = df_rank2(A[(size_t)k1 * lda + k1], vk1, wk1, wk1, vk1);
+      d[k1] = df_to_double(dd);
+    }
+  }
+  if (k1 + 1 >= n) return;
+  const int m1 = n - k1 - 1;
+  // updated row k+1 over columns [k+2, n)
+  df64 acc{0.f, 0.f};
+  for (int j = k1 + 1 + tid; j < n; j += blockDim.x) {
+    const df64 x = df_rank2(A[(size_t)k1 * lda + j], vk1, wk[j], wk1, vk[j]);
+    vn_[j] = x;
+    acc = df_fma(x, x, acc);
+  }
+  const double s = df_to_double(df_block_sum(acc, red));
+  if (m1 == 1) {
+    if (blockIdx.x == 0 && tid == 0) {
+      const int j = n - 1;
+      e[k1] = df_to_double(vn_[j]);
+      d[j] = df_to_double(df_rank2(A[(size_t)j * lda + j], vk[j], wk[j], wk[j], vk[j]));
+      e[j] = 0.0;
+    }
+    return;
+  }
+  const double x0 = df_to_double(vn_[k1 + 1]);
+  double alpha = 0.0, vnorm = 1.0;
+  if (s > 0.0) {
+    alpha = (x0 >= 0.0) ? -sqrt(s) : sqrt(s);
+    vnorm = sqrt(s - x0 * x0 + (x0 - alpha) * (x0 - alpha));
+  }
+  const df64 rvn = df_from_double(1.0 / vnorm);
+  __syncthreads();
+  for (int j = k1 + 1 + tid; j < n; j += blockDim.x) vn_[j] = house_v_df(vn_[j], j == k1 + 1, s, alpha, rvn);
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    for (int j = k1 + 1 + tid; j < n; j += blockDim.x) out.v[j] = vn_[j];
+    if (tid == 0) e[k1] = alpha;
+  }
+  // rows i in [k+2, n): one warp per row; update and dot with v_{k+1}
+  const int lane = tid & 31, wid = tid >> 5;
+  const int i = k1 + 1 + blockIdx.x * 8 + wid;
+  df64 contrib{0.f, 0.f};
+  if (i < n) {
+    df64* ar = A + (size_t)i * lda;
+    const df64 vi = vk[i], wi = wk[i];
+    df64 dot{0.f, 0.f};
+    for (int j = k1 + 1 + lane; j < n; j += 32) {
+      const df64 a = df_rank2(ar[j], vi, wk[j], wi, vk[j]);
+      ar[j] = a;
+      dot = df_fma(a, vn_[j], dot);
+    }
+    dot = df_warp_sum(dot);
+    if (lane == 0) { out.p[i] = dot; contrib = df_mul(dot, vn_[i]); }
+  }
+  __shared__ df64 bpart[8];
+  if (lane == 0) bpart[wid] = contrib;
+  __syncthreads();
+  if (tid == 0) {
+    df64 t = bpart[0];
+    for (int q = 1; q < 8; ++q) t = df_add(t, bpart[q]);
+    out.part[blockIdx.x] = t;
+  }
+}
+
+// Back-transformation in df64: each block owns columns [c0, c0 + kSlab) of X
+// (df64 in shared memory) and applies every reflector H_k = I - 2 v_k v_k^T,
+// k = n-3 .. 0, read from row k of the df64 matrix Vd (ld ldv).  X is read and
+// written in FP64.
+__global__ void __launch_bounds__(256) back_transform_df(const df64* Vd, int ldv, int n, int nev, double* X,
+                                                          int ldx) {
+  extern __shared__ df64 xd[];  // n x kSlab
+  __shared__ df64 red[kSlab][8];
   const int c0 = blockIdx.x * kSlab;
   const int nc = min(kSlab, nev - c0);
   for (int e = threadIdx.x; e < n * kSlab; e += blockDim.x) {
     const int i = e / kSlab, c = e - i * kSlab;
-    xs[e] = (c < nc) ? X[(size_t)i * ldx + c0 + c] : 0.0;
+    xd[e] = (c < nc) ? df_from_double(X[(size_t)i * ldx + c0 + c]) : df64{0.f, 0.f};
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int k = n - 3; k >= 0; --k) {
     const int m = n - k - 1;
-    const double* v = A + (size_t)k * lda + (k + 1);
-    double s[kSlab];
+    const df64* v = Vd + (size_t)k * ldv + (k + 1);
+    df64 s[kSlab];
 #pragma unroll
-    for (int c = 0; c < kSlab; ++c) s[c] = 0.0;
+    for (int c = 0; c < kSlab; ++c) s[c] = df64{0.f, 0.f};
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const double vi = v[i];
+      const df64 vi = v[i];
 #pragma unroll
-      for (int c = 0; c < kSlab; ++c) s[c] += vi * xs[(k + 1 + i) * kSlab + c];
+      for (int c = 0; c < kSlab; ++c) s[c] = df_fma(vi, xd[(k + 1 + i) * kSlab + c], s[c]);
     }
 #pragma unroll
     for (int c = 0; c < kSlab; ++c) {
-      const double t = warp_sum(s[c]);
+      const df64 t = df_warp_sum(s[c]);
       if (lane == 0) red[c][wid] = t;
     }
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < kSlab; ++c) {
-      double t = 0.0;
-      for (int q = 0; q < 8; ++q) t += red[c][q];
-      s[c] = 2.0 * t;
+      df64 t = red[c][0];
+      for (int q = 1; q < 8; ++q) t = df_add(t, red[c][q]);
+      s[c] = df64{-2.f * t.hi, -2.f * t.lo};   // exact scaling by -2
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const double vi = v[i];
+      const df64 vi = v[i];
 #pragma unroll
-      for (int c = 0; c < kSlab; ++c) xs[(k + 1 + i) * kSlab + c] -= s[c] * vi;
+      for (int c = 0; c < kSlab; ++c) xd[(k + 1 + i) * kSlab + c] = df_fma(s[c], vi, xd[(k + 1 + i) * kSlab + c]);
     }
     __syncthreads();
   }
   for (int e = threadIdx.x; e < n * kSlab; e += blockDim.x) {
     const int i = e / kSlab, c = e - i * kSlab;
-    if (c < nc) X[(size_t)i * ldx + c0 + c] = xs[e];
+    if (c < nc) X[(size_t)i * ldx + c0 + c] = df_to_double(xd[e]);
   }
 }
 
@@ -369,7 +510,8 @@ __global__ void __launch_bounds__(256) back_transform(const double* A, int lda, 
 
 size_t eig_large_work_doubles(int n, int nev) {
   const int nparts = (n + kTriRowsPerBlock - 1) / kTriRowsPerBlock;
-  return 6 * (size_t)n + 2 * (size_t)nparts + 2 + 5 * (size_t)n * nev + 64;
+  // ... + the df64 copy of T (2n values, one double each)
+  return 6 * (size_t)n + 2 * (size_t)nparts + 4 + 5 * (size_t)n * nev + 2 * (size_t)n + 64;
 }
 
 as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, double* evals, double* X, int ldx,
@@ -386,45 +528,57 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
   w.p2 = w.v2 + n;
   w.part2 = w.p2 + n;
   double* norms = w.part2 + nparts_max;
-  double* lu = norms + 2;
-  const size_t smem1 = (size_t)n * sizeof(double);
-  AS_CUDA_TRY(cudaFuncSetAttribute(tri_step1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+  double* lu = norms + 4;   // norms: ||T||, pivmin, and the scale of A and its inverse
+  df64* dd = reinterpret_cast<df64*>(lu + 5 * (size_t)n * nev);
+  df64* e2 = dd + n;
+  df64* Ad = reinterpret_cast<df64*>(A);
   if (prof) prof->begin(PK_EIG_TRI, s);
   {
+    unsigned long long* bits = reinterpret_cast<unsigned long long*>(norms + 2);
+    AS_CUDA_TRY(cudaMemsetAsync(bits, 0, sizeof(unsigned long long), s));
+    amax_bits<<<304, 256, 0, s>>>(A, lda, n, bits); count_launches(1);
+    pow2_scale<<<1, 1, 0, s>>>(bits, norms + 2); count_launches(1);
+    to_df_inplace<<<1024, 256, 0, s>>>(A, lda, n, norms + 2); count_launches(1);
     // step 0 forms v_0 and p_0 = A22 v_0 (written to absolute rows 1..n-1)
     const int m = n - 1;
     const int nb = (m + kTriRowsPerBlock - 1) / kTriRowsPerBlock;
-    tri_step1<<<nb, 256, (size_t)m * sizeof(double), s>>>(A, lda, n, 0, w); count_launches(1);
+    const size_t smem1 = (size_t)m * sizeof(df64);
+    AS_CUDA_TRY(cudaFuncSetAttribute(tri_step1_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+    tri_step1_df<<<nb, 256, smem1, s>>>(Ad, lda, n, w); count_launches(1);
     AS_CUDA_TRY(cudaGetLastError());
-    TriVec buf[2];
-    buf[0] = TriVec{w.v - 1, w.p - 1, w.part, nb};   // v_0, p_0 indexed by absolute row
-    buf[1] = TriVec{w.v2, w.p2, w.part2, 0};
-    const size_t smem = 3 * (size_t)n * sizeof(double);
+    df64* v0 = reinterpret_cast<df64*>(w.v);
+    df64* p0 = reinterpret_cast<df64*>(w.p);
+    df64* q0 = reinterpret_cast<df64*>(w.part);
+    TriVecDf buf[2];
+    buf[0] = TriVecDf{v0 - 1, p0 - 1, q0, nb};   // v_0, p_0 indexed by absolute row
+    buf[1] = TriVecDf{reinterpret_cast<df64*>(w.v2), reinterpret_cast<df64*>(w.p2), reinterpret_cast<df64*>(w.part2), 0};
+    const size_t smem = 3 * (size_t)n * sizeof(df64);
     // opt in for the dynamic size itself: the static shared memory comes on top
-    AS_CUDA_TRY(cudaFuncSetAttribute(tri_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AS_CUDA_TRY(cudaFuncSetAttribute(tri_fused_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int k = 0; k + 2 < n; ++k) {
-      TriVec& in = buf[k & 1];
-      TriVec& out = buf[(k + 1) & 1];
+      TriVecDf& in = buf[k & 1];
+      TriVecDf& out = buf[(k + 1) & 1];
       const int rows = n - k - 2;           // rows k+2..n-1
       const int grid = std::max(1, (rows + 7) / 8);
       out.nparts = grid;
-      tri_fused<<<grid, 256, smem, s>>>(A, lda, n, k, in, out, w.d, w.e); count_launches(1);
+      tri_fused_df<<<grid, 256, smem, s>>>(Ad, lda, n, k, in, out, w.d, w.e); count_launches(1);
       AS_CUDA_TRY(cudaGetLastError());
       // the buffers alternate; the base pointers of buffer 0 are re-pointed to
       // absolute indexing after the first step
-      if (k == 0) buf[0] = TriVec{w.v, w.p, w.part, 0};
+      if (k == 0) buf[0] = TriVecDf{v0, p0, q0, 0};
     }
   }
   if (prof) prof->end(PK_EIG_TRI, s, 4.0 / 3.0 * (double)n * n * n, 8.0 * (double)n * n);
   if (prof) prof->begin(PK_EIG_SOLVE, s);
   tri_norm<<<1, 256, 0, s>>>(n, w, norms); count_launches(1);
-  bisect_invit<<<(nev + 3) / 4, 128, 0, s>>>(n, nev, w, norms, evals, X, ldx, lu); count_launches(1);
+  tri_scale_df<<<(n + 255) / 256, 256, 0, s>>>(n, w, norms, dd, e2); count_launches(1);
+  bisect_invit_df<<<(nev + 15) / 16, 128, 0, s>>>(n, nev, w, norms, dd, e2, evals, X, ldx, lu); count_launches(1);
   cluster_mgs<<<1, 512, 0, s>>>(n, nev, norms, evals, X, ldx); count_launches(1);
   if (prof) prof->end(PK_EIG_SOLVE, s, 0.0, 0.0);
   if (prof) prof->begin(PK_EIG_BACK, s);
-  const size_t smem3 = (size_t)n * kSlab * sizeof(double);
-  AS_CUDA_TRY(cudaFuncSetAttribute(back_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
-  back_transform<<<(nev + kSlab - 1) / kSlab, 256, smem3, s>>>(A, lda, n, nev, X, ldx); count_launches(1);
+  const size_t smem3 = (size_t)n * kSlab * sizeof(df64);
+  AS_CUDA_TRY(cudaFuncSetAttribute(back_transform_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+  back_transform_df<<<(nev + kSlab - 1) / kSlab, 256, smem3, s>>>(Ad, lda, n, nev, X, ldx); count_launches(1);
   if (prof) prof->end(PK_EIG_BACK, s, 2.0 * (double)n * n * nev, 8.0 * (double)n * n);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;

@@ -554,11 +554,14 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
   return st;
 }
 
-as_status build_query_gram(as_sketch* h, double* B) {
+// Algorithm 5 lines 1-4 with lb = 0, ub = t: the residual C_t only at the
+// current time (t = T; older residuals are not stored) plus the snapshot
+// terms with t_j <= t.
+as_status build_query_gram(as_sketch* h, int64_t t, double* B) {
   const int d = h->d;
   as_status st = AS_OK;
   AS_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)d * d * sizeof(double), h->s));
-  if (h->r > 0) {
+  if (t == h->T && h->r > 0) {
     st = gemm_strided<float, float, double>(h->s, d, d, h->r, h->C, 1, h->ldc, h->C, h->ldc, 1, B, d, 1, 1.0, 0.0);
     if (st != AS_OK) return st;
   }
@@ -570,6 +573,7 @@ as_status build_query_gram(as_sketch* h, double* B) {
   st = dalloc(&T, (size_t)d * ximax);
   if (st != AS_OK) { cudaFree(YZ); return st; }
   for (const Snap& sn : h->snaps) {
+    if (sn.t > t) break;   // the queue is in time order
     const float* Z = h->arena + sn.off;
     const float* Y = Z + (size_t)d * sn.xi;
     const int xi = sn.xi;
@@ -820,14 +824,16 @@ as_status sketch_update(as_sketch* h, const float* rows, int64_t n, int64_t ld) 
   return st;
 }
 
-as_status sketch_query_gram(as_sketch* h, double* out) {
+as_status sketch_query_gram(as_sketch* h, int64_t t, double* out) {
   if (!h || !out) return AS_EINVAL;
+  if (t == -1) t = h->T;
+  if (t < 0 || t > h->T) return AS_EINVAL;
   std::unique_lock<std::mutex> lk(h->mu, std::try_to_lock);
   if (!lk.owns_lock()) return AS_EBUSY;
   double* B = nullptr;
   as_status st = dalloc(&B, (size_t)h->d * h->d);
   if (st != AS_OK) return st;
-  st = build_query_gram(h, B);
+  st = build_query_gram(h, t, B);
   if (st == AS_OK) {
     cudaError_t e = cudaMemcpy(out, B, (size_t)h->d * h->d * sizeof(double), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) st = as_from_cuda(e);
@@ -838,7 +844,8 @@ as_status sketch_query_gram(as_sketch* h, double* out) {
 
 as_status sketch_query(as_sketch* h, int64_t t, float* out, int64_t ldo, int32_t* rows_out) {
   if (!h || !out || ldo < h->d) return AS_EINVAL;
-  if (t != -1 && t != h->T) return AS_ENOTSUP;
+  if (t == -1) t = h->T;
+  if (t < 0 || t > h->T) return AS_EINVAL;
   std::unique_lock<std::mutex> lk(h->mu, std::try_to_lock);
   if (!lk.owns_lock()) return AS_EBUSY;
   const int d = h->d, ell = h->ell;
@@ -850,7 +857,7 @@ as_status sketch_query(as_sketch* h, int64_t t, float* out, int64_t ldo, int32_t
   const bool big_q = d > 256;
   if (st == AS_OK) st = dalloc(&w, big_q ? eig_large_work_doubles(d, ell) : eig_work_doubles(d, ell));
   if (st == AS_OK) st = dalloc(&o, (size_t)ell * d);
-  if (st == AS_OK) st = build_query_gram(h, B);
+  if (st == AS_OK) st = build_query_gram(h, t, B);
   if (st == AS_OK)                                                          // Algorithm 5 line 5
     st = big_q ? launch_eig_large(h->s, d, B, d, ell, lam, V, ell, w) : launch_eig(h->s, d, B, d, ell, lam, V, ell, w);
   if (st == AS_OK) st = launch_shrink_rows(h->s, d, ell, lam, V, ell, o, d);  // line 6
