@@ -35,6 +35,7 @@
 // odd), then the pair of row t at columns 2*npi + 2t and 2*npi + 2t + 1.
 #include <algorithm>
 
+#include "grid.cuh"
 #include "kernels.cuh"
 
 namespace as {
@@ -47,7 +48,6 @@ constexpr int kPWarps = kPThreads / 32;
 constexpr int kPairsPerUnit = 4;     // a warp unit: 4 column pairs (8 columns) x one K range
 constexpr int kMaxUnits = 64;
 constexpr int kSlots = 6;            // partial sums per pair
-constexpr long long kBarrierSpins = 1LL << 24;
 constexpr int kMaxGrid = 1024;
 
 struct PersistArgs {
@@ -86,38 +86,6 @@ __device__ __forceinline__ int pick_ksplit(int ngrp) {
     if (c < bc * (1.f - 1e-6f)) { bc = c; best = ks; }
   }
   return best;
-}
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Grid-wide barrier with a bounded wait.  Returns false when this CTA gave up
-// (status set to AS_ETIMEOUT) or found the sticky status already set.
-__device__ bool grid_barrier(unsigned* cnt, unsigned target, int* status) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    // release: this CTA's writes (ordered before by __syncthreads) become
-    // visible with the arrival; acquire on the loads that observe the target
-    red_release_add_u32(cnt, 1u);
-    int ok = 1;
-    long long n = 0;
-    while (ld_acquire_u32(cnt) < target) {
-      if (*(volatile int*)status != 0) { ok = 0; break; }
-      if (++n > kBarrierSpins) { set_status(status, AS_ETIMEOUT); ok = 0; break; }
-      __nanosleep(32);
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
 }
 
 // Sums v[0..128) over the 32 lanes by recursive halving: 124 shuffles, after

@@ -6,11 +6,12 @@
 // FP32 pipes, because FP64 throughput is a small fraction of FP32 on this
 // part; A is scaled by a power of two so that its entries fit FP32's
 // exponent range, and converted in place.
-//   * tridiagonalisation step k (df64): one kernel applies step k's update
-//     A22 -= v w^T + w v^T (w = 2p - 2(v^T p) v) and, in the same pass, forms
-//     v_{k+1} (every block recomputes it from row k+1) and p = A22 v_{k+1},
-//     one warp per row, with per-block partial sums of v^T p summed in a fixed
-//     order by the next step.  No atomics: results are bitwise reproducible.
+//   * tridiagonalisation (df64): one cooperative launch, one grid barrier per
+//     column; pass r applies update r-1 (A22 -= v w^T + w v^T,
+//     w = 2p - 2(v^T p) v) and, in the same sweep over the rows, forms v_r
+//     (every block recomputes it from row r) and p = A22 v_r, one warp per
+//     row, with per-block partial sums of v^T p summed in a fixed order by the
+//     next pass.  No atomics: results are bitwise reproducible.
 //   * bisection: eight lanes per eigenvalue (multisection) on df64 Sturm
 //     counts of T / ||T||; inverse iteration in FP64, one thread per
 //     eigenvalue.
@@ -18,6 +19,7 @@
 //     columns in shared memory and applies every reflector to it.
 #include "df64.cuh"
 #include "eig.cuh"
+#include "grid.cuh"
 #include "kernels.cuh"
 
 namespace as {
@@ -297,18 +299,6 @@ __device__ __forceinline__ df64 df_block_sum(df64 v, df64* red) {
   return t;
 }
 
-// Householder data of a df64 row x[0..m): s = ||x||^2, alpha, ||x - alpha e_1||.
-__device__ __forceinline__ void house_params_df(const df64* x, int m, df64* red, double& s, double& alpha,
-                                                double& vn) {
-  df64 acc{0.f, 0.f};
-  for (int i = threadIdx.x; i < m; i += blockDim.x) acc = df_fma(x[i], x[i], acc);
-  s = df_to_double(df_block_sum(acc, red));
-  const double x0 = df_to_double(x[0]);
-  if (s == 0.0) { alpha = 0.0; vn = 1.0; return; }
-  alpha = (x0 >= 0.0) ? -sqrt(s) : sqrt(s);
-  vn = sqrt(s - x0 * x0 + (x0 - alpha) * (x0 - alpha));
-}
-
 // v_j = (x_j - alpha [j == 0]) / vn in df64 (zero vector when s = 0).
 __device__ __forceinline__ df64 house_v_df(df64 xj, bool first, double s, double alpha, df64 rvn) {
   if (s == 0.0) return df64{0.f, 0.f};
@@ -316,141 +306,153 @@ __device__ __forceinline__ df64 house_v_df(df64 xj, bool first, double s, double
   return df_mul(t, rvn);
 }
 
-// Step 0 in df64 (see tri_step1): v_0 from row 0, p_0 = A22 v_0 and the block
-// partials of v_0^T p_0.  Vectors use TriWork's arrays as df64.
-__global__ void __launch_bounds__(256) tri_step1_df(df64* A, int lda, int n, TriWork w) {
-  extern __shared__ df64 vsd[];  // m values
-  __shared__ df64 red[32];
-  const int m = n - 1;
-  const df64* row = A + 1;
-  double s, alpha, vn;
-  house_params_df(row, m, red, s, alpha, vn);
-  const df64 rvn = df_from_double(1.0 / vn);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) vsd[i] = house_v_df(row[i], i == 0, s, alpha, rvn);
-  __syncthreads();
-  df64* wv = reinterpret_cast<df64*>(w.v);
-  df64* wp = reinterpret_cast<df64*>(w.p);
-  df64* wpart = reinterpret_cast<df64*>(w.part);
-  if (blockIdx.x == 0) {
-    for (int i = threadIdx.x; i < m; i += blockDim.x) wv[i] = vsd[i];
-    if (threadIdx.x == 0) { w.d[0] = df_to_double(A[0]); w.e[0] = alpha; }
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int i = blockIdx.x * kTriRowsPerBlock + wid;
-  df64 contrib{0.f, 0.f};
-  if (i < m) {
-    const df64* ar = A + (size_t)(1 + i) * lda + 1;
-    df64 acc{0.f, 0.f};
-    for (int j = lane; j < m; j += 32) acc = df_fma(ar[j], vsd[j], acc);
-    acc = df_warp_sum(acc);
-    if (lane == 0) { wp[i] = acc; contrib = df_mul(acc, vsd[i]); }
-  }
-  __shared__ df64 bpart[kTriRowsPerBlock];
-  if (lane == 0) bpart[wid] = contrib;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    df64 t = bpart[0];
-    for (int q = 1; q < kTriRowsPerBlock; ++q) t = df_add(t, bpart[q]);
-    wpart[blockIdx.x] = t;
-  }
-}
+// The whole tridiagonalisation in one cooperative launch (df64), one grid
+// barrier per column.  Pass r (r = 0 .. n-2):
+//   1. r >= 1: c = v_{r-1}^T p_{r-1} from the previous pass's per-CTA partials
+//      (fixed order), w = 2 p_{r-1} - 2 c v_{r-1};
+//   2. d_r = the diagonal entry of row r after update r-1; CTA 0 keeps v_{r-1}
+//      in row r-1 of A for the back-transformation;
+//   3. row r past the diagonal after update r-1 (every CTA, from A and the
+//      vectors) -> the Householder vector v_r and e_r = alpha; the last pass
+//      (r = n-2) only closes the 2 x 2 tail;
+//   4. each warp updates its rows i >= r+1 (columns >= r+1) with
+//      A -= v w^T + w v^T and forms p_r[i] = A[i] . v_r; per-CTA partials of
+//      v_r^T p_r;
+//   5. grid barrier.
+// v stays in shared memory across passes (every CTA computes it); p and the
+// partials are double buffered by pass parity.  Rows are dealt to the grid's
+// warps round-robin (row i to warp i mod warps).
+struct TriPersist {
+  df64* A;
+  int lda, n;
+  df64* p[2];      // p_r, absolute row index
+  df64* q[2];      // per-CTA partials of v_r^T p_r
+  double* d;
+  double* e;
+  unsigned* cnt;   // barrier arrivals (zero at launch)
+  int* status;
+};
 
-struct TriVecDf { df64* v; df64* p; df64* part; int nparts; };
+constexpr int kTriThreads = 512;
+constexpr int kTriWarps = kTriThreads / 32;
+constexpr int kTriUnroll = 8;   // row entries in flight per lane
 
-// Fused step k in df64 (see tri_fused): apply step k's update
-// A22 -= v w^T + w v^T (w = 2p - 2(v^T p) v) to rows/columns >= k+2, form
-// v_{k+1} from the updated row k+1 and p_{k+1} = A22' v_{k+1}.  v_k is kept in
-// row k of A (df64) for the back-transformation; d and e are written in FP64.
-__global__ void __launch_bounds__(256) tri_fused_df(df64* A, int lda, int n, int k, TriVecDf in, TriVecDf out,
-                                                    double* d, double* e) {
-  extern __shared__ df64 smd[];
-  df64* wk = smd;           // w_k[j], j in [k+1, n)
-  df64* vk = smd + n;       // v_k[j]
-  df64* vn_ = smd + 2 * n;  // v_{k+1}[j], j in [k+2, n)
+__global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersist t) {
+  extern __shared__ df64 smp[];
+  const int n = t.n, G = gridDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  df64* vcur = smp;           // v_{r-1}[j], j in [r, n)
+  df64* vnew = smp + n;       // row r, then v_r[j], j in [r+1, n)
+  df64* wk = smp + 2 * n;     // w_{r-1}[j], j in [r, n)
   __shared__ df64 red[32];
   __shared__ df64 c_s;
-  const int tid = threadIdx.x;
-  if (tid < 32) {   // v^T p from the previous step's block partials (fixed order)
-    df64 c{0.f, 0.f};
-    for (int q = tid; q < in.nparts; q += 32) c = df_add(c, in.part[q]);
-    c = df_warp_sum(c);
-    if (tid == 0) c_s = c;
-  }
-  __syncthreads();
-  const df64 c2 = df64{2.f * c_s.hi, 2.f * c_s.lo};
-  for (int j = k + 1 + tid; j < n; j += blockDim.x) {
-    const df64 v = in.v[j];
-    const df64 p = in.p[j];
-    vk[j] = v;
-    // w = 2p - 2c v
-    wk[j] = df_sub(df64{2.f * p.hi, 2.f * p.lo}, df_mul(c2, v));
-  }
-  __syncthreads();
-  const int k1 = k + 1;
-  const df64 vk1 = vk[k1], wk1 = wk[k1];
-  if (blockIdx.x == 0) {
-    for (int j = k + 1 + tid; j < n; j += blockDim.x) A[(size_t)k * lda + j] = vk[j];
+  __shared__ df64 wpart[kTriWarps];
+  const int W = G * kTriWarps, gw = blockIdx.x * kTriWarps + warp;
+  for (int r = 0; r <= n - 2; ++r) {
+    const bool upd = r >= 1;
+    if (upd) {
+      const df64* qin = ((r - 1) & 1) ? t.q[1] : t.q[0];
+      if (tid < 32) {
+        df64 c{0.f, 0.f};
+        for (int g = tid; g < G; g += 32) c = df_add(c, qin[g]);
+        c = df_warp_sum(c);
+        if (tid == 0) c_s = c;
+      }
+      __syncthreads();
+      const df64 c2{2.f * c_s.hi, 2.f * c_s.lo};
+      const df64* pin = ((r - 1) & 1) ? t.p[1] : t.p[0];
+      for (int j = r + tid; j < n; j += blockDim.x) {
+        const df64 pj = pin[j];
+        wk[j] = df_sub(df64{2.f * pj.hi, 2.f * pj.lo}, df_mul(c2, vcur[j]));
+      }
+      __syncthreads();
+    }
+    const df64* arow = t.A + (size_t)r * t.lda;
+    const df64 vr = upd ? vcur[r] : df64{0.f, 0.f};
+    const df64 wr = upd ? wk[r] : df64{0.f, 0.f};
+    if (blockIdx.x == 0) {
+      if (upd)
+        for (int j = r + tid; j < n; j += blockDim.x) t.A[(size_t)(r - 1) * t.lda + j] = vcur[j];
+      if (tid == 0) t.d[r] = df_to_double(upd ? df_rank2(arow[r], vr, wr, wr, vr) : arow[r]);
+    }
+    df64 acc{0.f, 0.f};
+#pragma unroll 4
+    for (int j = r + 1 + tid; j < n; j += blockDim.x) {
+      const df64 x = upd ? df_rank2(arow[j], vr, wk[j], wr, vcur[j]) : arow[j];
+      vnew[j] = x;
+      acc = df_fma(x, x, acc);
+    }
+    const double s = df_to_double(df_block_sum(acc, red));
+    if (r == n - 2) {   // 2 x 2 tail: no further reflector
+      if (blockIdx.x == 0 && tid == 0) {
+        const int j = n - 1;
+        t.e[r] = df_to_double(vnew[j]);
+        const df64 ajj = t.A[(size_t)j * t.lda + j];
+        t.d[j] = df_to_double(upd ? df_rank2(ajj, vcur[j], wk[j], wk[j], vcur[j]) : ajj);
+        t.e[j] = 0.0;
+      }
+      return;
+    }
+    const double x0 = df_to_double(vnew[r + 1]);
+    double alpha = 0.0, vnorm = 1.0;
+    if (s > 0.0) {
+      alpha = (x0 >= 0.0) ? -sqrt(s) : sqrt(s);
+      vnorm = sqrt(s - x0 * x0 + (x0 - alpha) * (x0 - alpha));
+    }
+    const df64 rvn = df_from_double(1.0 / vnorm);
+    __syncthreads();
+    for (int j = r + 1 + tid; j < n; j += blockDim.x) vnew[j] = house_v_df(vnew[j], j == r + 1, s, alpha, rvn);
+    if (blockIdx.x == 0 && tid == 0) t.e[r] = alpha;
+    __syncthreads();
+    // rows i >= r+1 of this warp: update with (v_{r-1}, w_{r-1}), dot with v_r
+    df64* pout = (r & 1) ? t.p[1] : t.p[0];
+    df64 contrib{0.f, 0.f};
+    for (int i = gw; i < n; i += W) {
+      if (i < r + 1) continue;
+      df64* ar = t.A + (size_t)i * t.lda;
+      const df64 vi = upd ? vcur[i] : df64{0.f, 0.f};
+      const df64 wi = upd ? wk[i] : df64{0.f, 0.f};
+      // kTriUnroll loads issued before the arithmetic that uses them; two
+      // accumulators shorten the dependent chain of the dot product
+      df64 dot0{0.f, 0.f}, dot1{0.f, 0.f};
+      for (int jb = r + 1 + lane; jb < n; jb += 32 * kTriUnroll) {
+        df64 av[kTriUnroll];
+#pragma unroll
+        for (int u = 0; u < kTriUnroll; ++u) {
+          const int j = jb + 32 * u;
+          av[u] = (j < n) ? ar[j] : df64{0.f, 0.f};
+        }
+#pragma unroll
+        for (int u = 0; u < kTriUnroll; ++u) {
+          const int j = jb + 32 * u;
+          if (j < n) {
+            df64 a = av[u];
+            if (upd) {
+              a = df_rank2(a, vi, wk[j], wi, vcur[j]);
+              ar[j] = a;
+            }
+            if (u & 1) dot1 = df_fma(a, vnew[j], dot1);
+            else dot0 = df_fma(a, vnew[j], dot0);
+          }
+        }
+      }
+      df64 dot = df_add(dot0, dot1);
+      dot = df_warp_sum(dot);
+      if (lane == 0) {
+        pout[i] = dot;
+        contrib = df_add(contrib, df_mul(dot, vnew[i]));
+      }
+    }
+    if (lane == 0) wpart[warp] = contrib;
+    __syncthreads();
     if (tid == 0) {
-      const df64 dd = df_rank2(A[(size_t)k1 * lda + k1], vk1, wk1, wk1, vk1);
-      d[k1] = df_to_double(dd);
+      df64 q = wpart[0];
+      for (int u = 1; u < kTriWarps; ++u) q = df_add(q, wpart[u]);
+      ((r & 1) ? t.q[1] : t.q[0])[blockIdx.x] = q;
     }
-  }
-  if (k1 + 1 >= n) return;
-  const int m1 = n - k1 - 1;
-  // updated row k+1 over columns [k+2, n)
-  df64 acc{0.f, 0.f};
-  for (int j = k1 + 1 + tid; j < n; j += blockDim.x) {
-    const df64 x = df_rank2(A[(size_t)k1 * lda + j], vk1, wk[j], wk1, vk[j]);
-    vn_[j] = x;
-    acc = df_fma(x, x, acc);
-  }
-  const double s = df_to_double(df_block_sum(acc, red));
-  if (m1 == 1) {
-    if (blockIdx.x == 0 && tid == 0) {
-      const int j = n - 1;
-      e[k1] = df_to_double(vn_[j]);
-      d[j] = df_to_double(df_rank2(A[(size_t)j * lda + j], vk[j], wk[j], wk[j], vk[j]));
-      e[j] = 0.0;
-    }
-    return;
-  }
-  const double x0 = df_to_double(vn_[k1 + 1]);
-  double alpha = 0.0, vnorm = 1.0;
-  if (s > 0.0) {
-    alpha = (x0 >= 0.0) ? -sqrt(s) : sqrt(s);
-    vnorm = sqrt(s - x0 * x0 + (x0 - alpha) * (x0 - alpha));
-  }
-  const df64 rvn = df_from_double(1.0 / vnorm);
-  __syncthreads();
-  for (int j = k1 + 1 + tid; j < n; j += blockDim.x) vn_[j] = house_v_df(vn_[j], j == k1 + 1, s, alpha, rvn);
-  __syncthreads();
-  if (blockIdx.x == 0) {
-    for (int j = k1 + 1 + tid; j < n; j += blockDim.x) out.v[j] = vn_[j];
-    if (tid == 0) e[k1] = alpha;
-  }
-  // rows i in [k+2, n): one warp per row; update and dot with v_{k+1}
-  const int lane = tid & 31, wid = tid >> 5;
-  const int i = k1 + 1 + blockIdx.x * 8 + wid;
-  df64 contrib{0.f, 0.f};
-  if (i < n) {
-    df64* ar = A + (size_t)i * lda;
-    const df64 vi = vk[i], wi = wk[i];
-    df64 dot{0.f, 0.f};
-    for (int j = k1 + 1 + lane; j < n; j += 32) {
-      const df64 a = df_rank2(ar[j], vi, wk[j], wi, vk[j]);
-      ar[j] = a;
-      dot = df_fma(a, vn_[j], dot);
-    }
-    dot = df_warp_sum(dot);
-    if (lane == 0) { out.p[i] = dot; contrib = df_mul(dot, vn_[i]); }
-  }
-  __shared__ df64 bpart[8];
-  if (lane == 0) bpart[wid] = contrib;
-  __syncthreads();
-  if (tid == 0) {
-    df64 t = bpart[0];
-    for (int q = 1; q < 8; ++q) t = df_add(t, bpart[q]);
-    out.part[blockIdx.x] = t;
+    if (!grid_barrier(t.cnt, (unsigned)(r + 1) * (unsigned)G, t.status)) return;
+    df64* tmp = vcur;   // v_r becomes the vector of the next pass's update
+    vcur = vnew;
+    vnew = tmp;
   }
 }
 
@@ -511,11 +513,12 @@ __global__ void __launch_bounds__(256) back_transform_df(const df64* Vd, int ldv
 size_t eig_large_work_doubles(int n, int nev) {
   const int nparts = (n + kTriRowsPerBlock - 1) / kTriRowsPerBlock;
   // ... + the df64 copy of T (2n values, one double each)
-  return 6 * (size_t)n + 2 * (size_t)nparts + 4 + 5 * (size_t)n * nev + 2 * (size_t)n + 64;
+  // ... + the barrier counter and a status word (one double)
+  return 6 * (size_t)n + 2 * (size_t)nparts + 4 + 5 * (size_t)n * nev + 2 * (size_t)n + 1 + 64;
 }
 
 as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, double* evals, double* X, int ldx,
-                           double* work, Prof* prof) {
+                           double* work, Prof* prof, int* status) {
   if (n < 3) return launch_eig(s, n, A, lda, nev, evals, X, ldx, work);
   TriWork w;
   w.d = work;
@@ -531,6 +534,11 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
   double* lu = norms + 4;   // norms: ||T||, pivmin, and the scale of A and its inverse
   df64* dd = reinterpret_cast<df64*>(lu + 5 * (size_t)n * nev);
   df64* e2 = dd + n;
+  unsigned* cnt = reinterpret_cast<unsigned*>(e2 + n);
+  if (!status) {   // scratch word when the caller passes none, cleared per call
+    status = reinterpret_cast<int*>(e2 + n) + 1;
+    AS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+  }
   df64* Ad = reinterpret_cast<df64*>(A);
   if (prof) prof->begin(PK_EIG_TRI, s);
   {
@@ -539,34 +547,25 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
     amax_bits<<<304, 256, 0, s>>>(A, lda, n, bits); count_launches(1);
     pow2_scale<<<1, 1, 0, s>>>(bits, norms + 2); count_launches(1);
     to_df_inplace<<<1024, 256, 0, s>>>(A, lda, n, norms + 2); count_launches(1);
-    // step 0 forms v_0 and p_0 = A22 v_0 (written to absolute rows 1..n-1)
-    const int m = n - 1;
-    const int nb = (m + kTriRowsPerBlock - 1) / kTriRowsPerBlock;
-    const size_t smem1 = (size_t)m * sizeof(df64);
-    AS_CUDA_TRY(cudaFuncSetAttribute(tri_step1_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
-    tri_step1_df<<<nb, 256, smem1, s>>>(Ad, lda, n, w); count_launches(1);
-    AS_CUDA_TRY(cudaGetLastError());
-    df64* v0 = reinterpret_cast<df64*>(w.v);
-    df64* p0 = reinterpret_cast<df64*>(w.p);
-    df64* q0 = reinterpret_cast<df64*>(w.part);
-    TriVecDf buf[2];
-    buf[0] = TriVecDf{v0 - 1, p0 - 1, q0, nb};   // v_0, p_0 indexed by absolute row
-    buf[1] = TriVecDf{reinterpret_cast<df64*>(w.v2), reinterpret_cast<df64*>(w.p2), reinterpret_cast<df64*>(w.part2), 0};
+    // all passes in one cooperative launch (one grid barrier per column)
+    int dev = 0, sms = 0;
+    AS_CUDA_TRY(cudaGetDevice(&dev));
+    AS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = std::max(1, std::min(sms, nparts_max));
     const size_t smem = 3 * (size_t)n * sizeof(df64);
-    // opt in for the dynamic size itself: the static shared memory comes on top
-    AS_CUDA_TRY(cudaFuncSetAttribute(tri_fused_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    for (int k = 0; k + 2 < n; ++k) {
-      TriVecDf& in = buf[k & 1];
-      TriVecDf& out = buf[(k + 1) & 1];
-      const int rows = n - k - 2;           // rows k+2..n-1
-      const int grid = std::max(1, (rows + 7) / 8);
-      out.nparts = grid;
-      tri_fused_df<<<grid, 256, smem, s>>>(Ad, lda, n, k, in, out, w.d, w.e); count_launches(1);
-      AS_CUDA_TRY(cudaGetLastError());
-      // the buffers alternate; the base pointers of buffer 0 are re-pointed to
-      // absolute indexing after the first step
-      if (k == 0) buf[0] = TriVecDf{v0, p0, q0, 0};
-    }
+    AS_CUDA_TRY(cudaFuncSetAttribute(tri_persist_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per = 0;
+    AS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tri_persist_df, kTriThreads, smem));
+    if ((long long)per * sms < grid) return AS_ENOTSUP;
+    AS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned), s));
+    TriPersist tp{};
+    tp.A = Ad; tp.lda = lda; tp.n = n;
+    tp.p[0] = reinterpret_cast<df64*>(w.p); tp.p[1] = reinterpret_cast<df64*>(w.p2);
+    tp.q[0] = reinterpret_cast<df64*>(w.part); tp.q[1] = reinterpret_cast<df64*>(w.part2);
+    tp.d = w.d; tp.e = w.e; tp.cnt = cnt; tp.status = status;
+    void* args[] = {&tp};
+    AS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tri_persist_df, dim3(grid), dim3(kTriThreads), args, smem, s));
+    count_launches(1);
   }
   if (prof) prof->end(PK_EIG_TRI, s, 4.0 / 3.0 * (double)n * n * n, 8.0 * (double)n * n);
   if (prof) prof->begin(PK_EIG_SOLVE, s);

@@ -260,7 +260,7 @@ as_status fd_shrink(as_sketch* h) {
   const int n2 = h->n2, ell = h->ell, d = h->d;
   AS_CUDA_TRY(cudaMemcpyAsync(h->Gtmp, h->G, (size_t)n2 * n2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
   if (h->prof) h->prof->begin(PK_EIG, h->s);
-  as_status st = h->big ? launch_eig_large(h->s, n2, h->Gtmp, n2, ell, h->lam, h->U, ell, h->eigw, h->prof)
+  as_status st = h->big ? launch_eig_large(h->s, n2, h->Gtmp, n2, ell, h->lam, h->U, ell, h->eigw, h->prof, h->dstatus)
                          : launch_eig(h->s, n2, h->Gtmp, n2, ell, h->lam, h->U, ell, h->eigw);
   if (st != AS_OK) return st;
   // tridiagonalisation 4/3 n^3 + back-transformation 2 n^2 nev; G read once
@@ -859,7 +859,8 @@ as_status sketch_query(as_sketch* h, int64_t t, float* out, int64_t ldo, int32_t
   if (st == AS_OK) st = dalloc(&o, (size_t)ell * d);
   if (st == AS_OK) st = build_query_gram(h, t, B);
   if (st == AS_OK)                                                          // Algorithm 5 line 5
-    st = big_q ? launch_eig_large(h->s, d, B, d, ell, lam, V, ell, w) : launch_eig(h->s, d, B, d, ell, lam, V, ell, w);
+    st = big_q ? launch_eig_large(h->s, d, B, d, ell, lam, V, ell, w, nullptr, h->dstatus)
+               : launch_eig(h->s, d, B, d, ell, lam, V, ell, w);
   if (st == AS_OK) st = launch_shrink_rows(h->s, d, ell, lam, V, ell, o, d);  // line 6
   if (st == AS_OK) {
     cudaError_t e = cudaMemcpy2DAsync(out, (size_t)ldo * sizeof(float), o, (size_t)d * sizeof(float),
@@ -956,18 +957,25 @@ as_status as_symeig(int32_t n, const double* A, int32_t nev, double* evals, doub
   if (n < 1 || nev < 1 || nev > n || !A || !evals || !vecs) return AS_EINVAL;
   const bool big = n > 256;
   double *dA = nullptr, *dl = nullptr, *dX = nullptr, *w = nullptr;
+  int* dst = nullptr;
   as_status st = dalloc(&dA, (size_t)n * n);
   if (st == AS_OK) st = dalloc(&dl, (size_t)n);
   if (st == AS_OK) st = dalloc(&dX, (size_t)n * nev);
   if (st == AS_OK) st = dalloc(&w, big ? eig_large_work_doubles(n, nev) : eig_work_doubles(n, nev));
+  if (st == AS_OK) st = dalloc(&dst, 1);
   cudaError_t e = cudaSuccess;
-  if (st == AS_OK) e = cudaMemcpy(dA, A, (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice);
+  if (st == AS_OK) e = cudaMemset(dst, 0, sizeof(int));
+  if (st == AS_OK && e == cudaSuccess) e = cudaMemcpy(dA, A, (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice);
   if (st == AS_OK && e == cudaSuccess)
-    st = big ? launch_eig_large(nullptr, n, dA, n, nev, dl, dX, nev, w) : launch_eig(nullptr, n, dA, n, nev, dl, dX, nev, w);
+    st = big ? launch_eig_large(nullptr, n, dA, n, nev, dl, dX, nev, w, nullptr, dst)
+             : launch_eig(nullptr, n, dA, n, nev, dl, dX, nev, w);
   if (st == AS_OK && e == cudaSuccess) e = cudaMemcpy(evals, dl, (size_t)nev * sizeof(double), cudaMemcpyDeviceToHost);
   if (st == AS_OK && e == cudaSuccess) e = cudaMemcpy(vecs, dX, (size_t)n * nev * sizeof(double), cudaMemcpyDeviceToHost);
+  int ds = 0;
+  if (st == AS_OK && e == cudaSuccess) e = cudaMemcpy(&ds, dst, sizeof(int), cudaMemcpyDeviceToHost);
   if (st == AS_OK && e != cudaSuccess) st = as_from_cuda(e);
-  cudaFree(dA); cudaFree(dl); cudaFree(dX); cudaFree(w);
+  if (st == AS_OK && ds != 0) st = (as_status)ds;
+  cudaFree(dA); cudaFree(dl); cudaFree(dX); cudaFree(w); cudaFree(dst);
   return st;
 }
 

@@ -1,0 +1,45 @@
+// Grid-wide barrier for cooperative (co-resident) launches, with a bounded
+// wait.  Arrivals are counted on a zeroed counter that only grows: the n-th
+// barrier of a launch completes when the counter reaches n * gridDim.x.
+#pragma once
+
+#include "common.cuh"
+
+namespace as {
+
+constexpr long long kGridBarrierSpins = 1LL << 24;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Returns false when this CTA gave up waiting (status set to AS_ETIMEOUT) or
+// found the sticky status already set; the caller then returns, and every
+// other CTA gives up at its next barrier.
+__device__ __forceinline__ bool grid_barrier(unsigned* cnt, unsigned target, int* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // release: this CTA's writes (ordered before by __syncthreads) become
+    // visible with the arrival; acquire on the loads that observe the target
+    red_release_add_u32(cnt, 1u);
+    int ok = 1;
+    long long n = 0;
+    while (ld_acquire_u32(cnt) < target) {
+      if (*(volatile int*)status != 0) { ok = 0; break; }
+      if (++n > kGridBarrierSpins) { set_status(status, AS_ETIMEOUT); ok = 0; break; }
+      __nanosleep(32);
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+}  // namespace as

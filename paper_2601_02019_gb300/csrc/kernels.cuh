@@ -81,8 +81,10 @@ as_status launch_shrink_weights(cudaStream_t s, int n2, int ell, const double* l
 // Large-matrix FP64 eigensolver spread over the GPU (eig_large.cu); same
 // contract as launch_eig.  Work size: eig_large_work_doubles(n, nev).
 size_t eig_large_work_doubles(int n, int nev);
+// status: sticky status word for a grid-barrier timeout (AS_ETIMEOUT); NULL
+// uses a scratch word in `work`, cleared by each call.
 as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, double* evals, double* X, int ldx,
-                           double* work, Prof* prof = nullptr);
+                           double* work, Prof* prof = nullptr, int* status = nullptr);
 
 // Split-K tall-skinny FP32 GEMM (skinny.cu): P[s](m, n) = sum_{k in split s}
 // A[m*lda + k] X[n*ldx + k]; *S in: requested splits, out: planes written.
