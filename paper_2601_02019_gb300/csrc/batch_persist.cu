@@ -153,6 +153,49 @@ __global__ void __launch_bounds__(kPThreads, 1) batch_persist_kernel(const Persi
     const float* pold = a.part + (size_t)((it + 1) & 1) * a.pbuf;
     float* pnew = a.part + (size_t)(it & 1) * a.pbuf;
 
+    // product geometry: units of 4 pairs x one of KS ranges of kc rows of X
+    const int ngrp = (nact + kPairsPerUnit - 1) / kPairsPerUnit;
+    const int KS = pick_ksplit(ngrp);
+    const int nunits = ngrp * KS;
+    const int kc = ((a.mmax + KS - 1) / KS + 127) / 128 * 128;
+    // unit u covers pairs [pb, pb + nv) and rows [k0, k1) of X_old
+    auto unit_of = [&](int uu, int& pb, int& nv, int& k0, int& k1) {
+      const int gi = uu / KS, ks = uu - gi * KS;
+      pb = pa0 + gi * kPairsPerUnit;
+      nv = min(kPairsPerUnit, pa1 - pb);
+      k0 = ks * kc;
+      k1 = min(a.mmax, k0 + kc);
+    };
+    // raw Y_old rows k .. k+3 (k = kk + 4 lane) of the unit's 8 columns
+    // (k0 and interior k1 are multiples of 128; only k1 = mmax can cut a quad)
+    auto load = [&](float4 (&v)[2 * kPairsPerUnit], int pb, int nv, int kk, int k1) {
+      const float* ybase = Yold + (size_t)(2 * pb) * a.ldy;
+      const int k = kk + 4 * lane;
+#pragma unroll
+      for (int j = 0; j < 2 * kPairsPerUnit; ++j) {
+        v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((j >> 1) < nv && k < k1) {
+          const float* q = ybase + (size_t)j * a.ldy + k;
+          if (k + 3 < k1) {
+            v[j] = __ldcg(reinterpret_cast<const float4*>(q));
+          } else {
+            v[j].x = __ldcg(q);
+            if (k + 1 < k1) v[j].y = __ldcg(q + 1);
+            if (k + 2 < k1) v[j].z = __ldcg(q + 2);
+          }
+        }
+      }
+    };
+    // the warp's first item is the same for every tile: its loads go out now,
+    // while the coefficient phase waits on the partial sums
+    float4 yn[2 * kPairsPerUnit];
+    bool have = false;
+    if (warp < nunits) {
+      int pb, nv, k0, k1;
+      unit_of(warp, pb, nv, k0, k1);
+      if (k0 < k1) { load(yn, pb, nv, k0, k1); have = true; }
+    }
+
     // (1) coefficients: x0 = c00 y0 + c10 y1, x1 = c01 y0 + c11 y1
     if (it == 0) {
       for (int p = tid; p < P; p += kPThreads) {
@@ -164,18 +207,31 @@ __global__ void __launch_bounds__(kPThreads, 1) batch_persist_kernel(const Persi
         float sv[4][3];
 #pragma unroll
         for (int j = 0; j < 4; ++j) sv[j][0] = sv[j][1] = sv[j][2] = 0.f;
-#pragma unroll 4
-        for (int g = lane; g < G; g += 32) {
+        // all loads of a chunk of 4 x 32 CTAs are issued before any add uses
+        // them (in-order issue would otherwise pay one L2 round trip per 32)
+        for (int g0 = 0; g0 < G; g0 += 128) {
+          float buf[4][4][3];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int p = pbase + j;
-            if (p < pa1) {
+          for (int gg = 0; gg < 4; ++gg) {
+            const int g = g0 + 32 * gg + lane;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int p = pbase + j;
+              const bool on = p < pa1 && g < G;
               const float* q0 = pold + (size_t)(p * kSlots) * G + g;
-              sv[j][0] += __ldcg(q0);
-              sv[j][1] += __ldcg(q0 + G);
-              if (p >= a.npi) sv[j][2] += __ldcg(q0 + 2 * G);
+              buf[gg][j][0] = on ? __ldcg(q0) : 0.f;
+              buf[gg][j][1] = on ? __ldcg(q0 + G) : 0.f;
+              buf[gg][j][2] = (on && p >= a.npi) ? __ldcg(q0 + 2 * G) : 0.f;
             }
           }
+#pragma unroll
+          for (int gg = 0; gg < 4; ++gg)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              sv[j][0] += buf[gg][j][0];
+              sv[j][1] += buf[gg][j][1];
+              sv[j][2] += buf[gg][j][2];
+            }
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -210,45 +266,22 @@ __global__ void __launch_bounds__(kPThreads, 1) batch_persist_kernel(const Persi
     __syncthreads();
 
     // (2)-(3) rows of Y_new = G X_old for this CTA's tiles
-    const int ngrp = (nact + kPairsPerUnit - 1) / kPairsPerUnit;
-    const int KS = pick_ksplit(ngrp);
-    const int nunits = ngrp * KS;
-    const int kc = ((a.mmax + KS - 1) / KS + 127) / 128 * 128;
     float ps[kSlots] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int tile = blk; tile < a.ntiles; tile += G) {
       const int row0 = tile * kTile;
       const int R = min(kTile, a.mmax - row0);
+      // items (unit, 128-row step) in order; the next item's loads are issued
+      // before the current item's arithmetic, across unit boundaries
       for (int u = warp; u < nunits; u += kPWarps) {
-        const int gi = u / KS, ks = u - gi * KS;
-        const int pb = pa0 + gi * kPairsPerUnit;
-        const int nv = min(kPairsPerUnit, pa1 - pb);   // valid pairs of this unit
-        const int k0 = ks * kc, k1 = min(a.mmax, k0 + kc);
+        int pb, nv, k0, k1;
+        unit_of(u, pb, nv, k0, k1);
         const float4* cf4 = reinterpret_cast<const float4*>(coef) + pb;   // (c00, c10, c01, c11) per pair
-        const float* ybase = Yold + (size_t)(2 * pb) * a.ldy;
-        // steps of 128 rows of X: lane l takes rows k .. k+3, k = kk + 4l
-        // (k0 and interior k1 are multiples of 128; only k1 = mmax can cut a quad)
-        auto load = [&](float4 (&v)[2 * kPairsPerUnit], int kk) {
-          const int k = kk + 4 * lane;
-#pragma unroll
-          for (int j = 0; j < 2 * kPairsPerUnit; ++j) {
-            v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if ((j >> 1) < nv && k < k1) {
-              const float* p = ybase + (size_t)j * a.ldy + k;
-              if (k + 3 < k1) {
-                v[j] = __ldcg(reinterpret_cast<const float4*>(p));
-              } else {
-                v[j].x = __ldcg(p);
-                if (k + 1 < k1) v[j].y = __ldcg(p + 1);
-                if (k + 2 < k1) v[j].z = __ldcg(p + 2);
-              }
-            }
-          }
-        };
+        if (!have && k0 < k1) load(yn, pb, nv, k0, k1);
+        have = false;
         float acc[128];
 #pragma unroll
         for (int e = 0; e < 128; ++e) acc[e] = 0.f;
-        float4 yv[2 * kPairsPerUnit], yn[2 * kPairsPerUnit];
-        if (k0 < k1) load(yn, k0);
+        float4 yv[2 * kPairsPerUnit];
         for (int kk = k0; kk < k1; kk += 128) {
           // X_old = Y_old * coefficients (pairs past nv are zero)
 #pragma unroll
@@ -260,7 +293,13 @@ __global__ void __launch_bounds__(kPThreads, 1) batch_persist_kernel(const Persi
             yv[2 * j + 1] = make_float4(fmaf(c.z, ya.x, c.w * yb.x), fmaf(c.z, ya.y, c.w * yb.y),
                                         fmaf(c.z, ya.z, c.w * yb.z), fmaf(c.z, ya.w, c.w * yb.w));
           }
-          if (kk + 128 < k1) load(yn, kk + 128);   // next step's rows in flight during this step
+          if (kk + 128 < k1) {
+            load(yn, pb, nv, kk + 128, k1);
+          } else if (u + kPWarps < nunits) {   // first step of the warp's next unit
+            int pb2, nv2, k02, k12;
+            unit_of(u + kPWarps, pb2, nv2, k02, k12);
+            if (k02 < k12) { load(yn, pb2, nv2, k02, k12); have = true; }
+          }
           const int k = kk + 4 * lane;
 #pragma unroll
           for (int r = 0; r < kTile; ++r) {

@@ -322,7 +322,7 @@ as_status dump(as_sketch* h, int xi, int k, int64_t i) {
   if (st != AS_OK) return st;
   float* Z = h->arena + h->arena_used;
   float* Y = Z + (size_t)d * xi;
-  const size_t need = dump_work_doubles(d, xi);
+  const size_t need = dump_work_doubles(d, n2, xi);
   if (need > h->dwork_cap) {
     if (h->dwork) cudaFree(h->dwork);
     h->dwork = nullptr;

@@ -245,8 +245,25 @@ __global__ void promote_pair_kernel(const float* X, int n2, int col0, int m, int
 // Partial sums over row chunks s: Zp[s][c][a] = sum_p C[p][c] WU[p][a] and
 // Yp[s][a][c] = sum_p GWU[p][a] C[p][c] for a in [a0, a0+na), one thread per column c.
 constexpr int kDumpChunks = 8;
-__global__ void dump_partial_kernel(const float* __restrict__ C, int ldc, int d, int r, const double* WU,
-                                    const double* GWU, int k, int xi, int a0, int na, double* Zp, double* Yp) {
+
+// FP32 copies of the first xi columns of WU and GWU (rows < r, row-major
+// r x xi), and the low part GWUlo = fl32(GWU - GWUf) for the residual.
+// Converting once keeps FP64 work out of the per-entry loops below.
+__global__ void dump_coef_f32(const double* WU, const double* GWU, int r, int k, int xi, float* WUf, float* GWUf,
+                              float* GWUlo) {
+  const int tot = r * xi;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+    const int p = e / xi, a = e - p * xi;
+    const double g = GWU[(size_t)p * k + a];
+    const float gf = (float)g;
+    WUf[e] = (float)WU[(size_t)p * k + a];
+    GWUf[e] = gf;
+    GWUlo[e] = (float)(g - (double)gf);
+  }
+}
+
+__global__ void dump_partial_kernel(const float* __restrict__ C, int ldc, int d, int r, const float* __restrict__ WUf,
+                                    const float* __restrict__ GWUf, int xi, int a0, int na, double* Zp, double* Yp) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blockIdx.y;
   if (c >= d) return;
@@ -262,8 +279,8 @@ __global__ void dump_partial_kernel(const float* __restrict__ C, int ldc, int d,
 #pragma unroll
     for (int a = 0; a < 8; ++a)
       if (a < na) {
-        zf[a] = fmaf(cv, (float)WU[(size_t)p * k + a0 + a], zf[a]);
-        yf[a] = fmaf(cv, (float)GWU[(size_t)p * k + a0 + a], yf[a]);
+        zf[a] = fmaf(cv, WUf[(size_t)p * xi + a0 + a], zf[a]);
+        yf[a] = fmaf(cv, GWUf[(size_t)p * xi + a0 + a], yf[a]);
       }
     if (++cnt == 64) {   // FP32 partial sums of 64 rows, combined in FP64
       cnt = 0;
@@ -289,14 +306,21 @@ __global__ void dump_reduce_kernel(const double* Zp, const double* Yp, int d, in
   }
 }
 
-// C[p][c] -= sum_a GWU[p][a] Z[c][a]   (the residual C' - C' Z Z^T)
-__global__ void residual_kernel(float* C, int ldc, int d, int r, const double* GWU, int k, int xi, const float* Z) {
+// C[p][c] -= sum_a GWU[p][a] Z[c][a]   (the residual C' - C' Z Z^T), as an
+// FMA chain in FP32 with GWU split into hi + lo: each term enters with one
+// rounding, so a strongly cancelling entry keeps its relative accuracy.
+__global__ void residual_kernel(float* C, int ldc, int d, int r, const float* __restrict__ GWUf,
+                                const float* __restrict__ GWUlo, int xi, const float* Z) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   if (c >= d || p >= r) return;
-  double acc = 0.0;
-  for (int a = 0; a < xi; ++a) acc += GWU[(size_t)p * k + a] * (double)Z[(size_t)c * xi + a];
-  C[(size_t)p * ldc + c] = (float)((double)C[(size_t)p * ldc + c] - acc);
+  float v = C[(size_t)p * ldc + c];
+  for (int a = 0; a < xi; ++a) {
+    const float z = Z[(size_t)c * xi + a];
+    v = fmaf(-GWUf[(size_t)p * xi + a], z, v);
+    v = fmaf(-GWUlo[(size_t)p * xi + a], z, v);
+  }
+  C[(size_t)p * ldc + c] = v;
 }
 
 // G[p][q] -= sum_a GWU[p][a] GWU[q][a]
@@ -384,20 +408,28 @@ as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m
   return AS_OK;
 }
 
-size_t dump_work_doubles(int d, int xi) { return (size_t)2 * kDumpChunks * d * xi; }
+size_t dump_work_doubles(int d, int n2, int xi) {
+  return (size_t)2 * kDumpChunks * d * xi + ((size_t)3 * n2 * xi + 1) / 2;   // + the FP32 coefficients
+}
 
 as_status launch_dump(cudaStream_t s, float* C, int ldc, int d, int r, double* G, int n2, const double* WU,
                       const double* GWU, int k, int xi, float* Z, float* Y, double* work) {
   double* Zp = work;
   double* Yp = work + (size_t)kDumpChunks * d * xi;
+  float* WUf = reinterpret_cast<float*>(Yp + (size_t)kDumpChunks * d * xi);
+  float* GWUf = WUf + (size_t)n2 * xi;
+  float* GWUlo = GWUf + (size_t)n2 * xi;
+  if (r > 0) {
+    dump_coef_f32<<<(r * xi + 255) / 256, 256, 0, s>>>(WU, GWU, r, k, xi, WUf, GWUf, GWUlo); count_launches(1);
+  }
   for (int a0 = 0; a0 < xi; a0 += 8) {
     const int na = std::min(8, xi - a0);
     dim3 grid((d + 127) / 128, kDumpChunks);
-    dump_partial_kernel<<<grid, 128, 0, s>>>(C, ldc, d, r, WU, GWU, k, xi, a0, na, Zp, Yp); count_launches(1);
+    dump_partial_kernel<<<grid, 128, 0, s>>>(C, ldc, d, r, WUf, GWUf, xi, a0, na, Zp, Yp); count_launches(1);
   }
   dump_reduce_kernel<<<(d * xi + 255) / 256, 256, 0, s>>>(Zp, Yp, d, xi, Z, Y); count_launches(1);
   if (r > 0) {
-    residual_kernel<<<dim3((d + 255) / 256, r), 256, 0, s>>>(C, ldc, d, r, GWU, k, xi, Z); count_launches(1);
+    residual_kernel<<<dim3((d + 255) / 256, r), 256, 0, s>>>(C, ldc, d, r, GWUf, GWUlo, xi, Z); count_launches(1);
     gram_downdate_kernel<<<dim3((r + 255) / 256, r), 256, 0, s>>>(G, n2, r, GWU, k, xi); count_launches(1);
   }
   AS_CUDA_TRY(cudaGetLastError());

@@ -103,8 +103,8 @@ as_status launch_gram_rows_skinny(cudaStream_t s, const float* C, int ldc, int d
 
 // Dump (Algorithm 4 lines 14-16) for the first xi columns of W U / G W U
 // (row-major n2 x k): Z = C'^T (WU)_xi, Y = (GWU)_xi^T C', C -= (GWU)_xi Z^T,
-// G -= (GWU)_xi (GWU)_xi^T.  work: dump_work_doubles(d, xi).
-size_t dump_work_doubles(int d, int xi);
+// G -= (GWU)_xi (GWU)_xi^T.  work: dump_work_doubles(d, n2, xi).
+size_t dump_work_doubles(int d, int n2, int xi);
 as_status launch_dump(cudaStream_t s, float* C, int ldc, int d, int r, double* G, int n2, const double* WU,
                       const double* GWU, int k, int xi, float* Z, float* Y, double* work);
 
