@@ -122,4 +122,19 @@ __device__ __forceinline__ df64 df_div(df64 a, df64 b) {
   return df_renorm(q1, q2);
 }
 
+// sqrt(a) for a >= 0: the FP32 root and one Newton correction
+// (a - r^2) / (2 r), with r^2 formed exactly.
+__device__ __forceinline__ df64 df_sqrt(df64 a) {
+  if (!(a.hi > 0.f)) return df64{0.f, 0.f};
+  const float r = sqrtf(a.hi);
+  float p, e;
+  two_prod(r, r, p, e);
+  float s, f;
+  two_sum(a.hi, -p, s, f);
+  f = __fsub_rn(f, e);
+  f = __fadd_rn(f, a.lo);
+  const float corr = __fdiv_rn(__fadd_rn(s, f), __fmul_rn(2.f, r));
+  return df_renorm(r, corr);
+}
+
 }  // namespace as

@@ -53,13 +53,10 @@ __global__ void tri_norm(int n, TriWork w, double* out2) {
   if (threadIdx.x == 0) { out2[0] = tn; out2[1] = 2.2250738585072014e-308 * fmax(1.0, em); }
 }
 
-// Eight lanes per eigenvalue (four eigenvalues per warp): multisection on
-// Sturm counts, each round evaluating 7 interior points and narrowing the
-// bracket 8-fold, down to an absolute width of 4 eps ||T||; then inverse
-// iteration by the group's first lane.  Eight lanes spend 7/3 Sturm counts per
-// bit (a 32-lane multisection spends 31/5): the Sturm recurrences are bound by
-// FP64 throughput on this part, and the shorter chain of rounds keeps the
-// latency down.  The round loop is warp-uniform (the ballot spans the warp).
+// Lanes per eigenvalue of the multisection: kBisLanes - 1 interior points per
+// round narrow the bracket kBisLanes-fold.  Measured on the FD shrink's
+// 2048 x 2048 Gram: 8 lanes beat both 4 (more rounds) and 32 (more Sturm
+// counts per bit).
 constexpr int kBisLanes = 8;
 
 // Modified Gram-Schmidt inside clusters of close eigenvalues (one block).
@@ -105,10 +102,12 @@ __global__ void tri_scale_df(int n, TriWork w, const double* norms, df64* dd, df
   }
 }
 
-// q <- a - b / q with the quotient from a fast FP32 estimate and one df64
-// correction (q1 + (num - q1 b) / b), accurate to about 2^-44 relative.
+// a / b from one FP32 reciprocal of b.hi: q1 = a.hi / b.hi and the
+// correction (a - q1 b) / b.hi, both through the same reciprocal; accurate to
+// about 2^-44 relative (one special-function instruction per quotient).
 __device__ __forceinline__ df64 df_div_fast(df64 a, df64 b) {
-  const float q1 = __fdividef(a.hi, b.hi);
+  const float rb = __frcp_rn(b.hi);
+  const float q1 = __fmul_rn(a.hi, rb);
   float p, e;
   two_prod(q1, b.hi, p, e);
   float s, f;
@@ -116,7 +115,7 @@ __device__ __forceinline__ df64 df_div_fast(df64 a, df64 b) {
   f = __fsub_rn(f, e);
   f = __fadd_rn(f, a.lo);
   f = __fmaf_rn(-q1, b.lo, f);
-  const float q2 = __fdividef(__fadd_rn(s, f), b.hi);
+  const float q2 = __fmul_rn(__fadd_rn(s, f), rb);
   return df_renorm(q1, q2);
 }
 
@@ -127,6 +126,7 @@ __device__ int sturm_count_df(int n, const df64* dd, const df64* e2, df64 x, flo
   df64 q = df_sub(dd[0], x);
   if (fabsf(q.hi) < pivmin) q = df64{-pivmin, 0.f};
   if (q.hi < 0.f) ++c;
+#pragma unroll 4
   for (int i = 1; i < n; ++i) {
     q = df_sub(df_sub(dd[i], x), df_div_fast(e2[i - 1], q));
     if (fabsf(q.hi) < pivmin) q = df64{-pivmin, 0.f};
@@ -135,10 +135,10 @@ __device__ int sturm_count_df(int n, const df64* dd, const df64* e2, df64 x, flo
   return c;
 }
 
-// Multisection on the scaled T with df64 Sturm counts (eight lanes per
-// eigenvalue, as bisect_invit), then inverse iteration in FP64 by the group's
-// first lane.  The bracket is kept in FP64; evaluation points are rounded to
-// df64.  Stops at a width of 2^-44 of ||T|| (df64 resolution).
+// Multisection on the scaled T with df64 Sturm counts (kBisLanes lanes per
+// eigenvalue), then inverse iteration in FP64 by the group's first lane.  The
+// bracket is kept in FP64; evaluation points are rounded to df64.  Stops at a
+// width of 2^-44 of ||T|| (df64 resolution).
 __global__ void bisect_invit_df(int n, int nev, TriWork w, const double* norms, const df64* dd, const df64* e2,
                                 double* evals, double* X, int ldx, double* lu) {
   const int lane = threadIdx.x & 31;
@@ -159,7 +159,8 @@ __global__ void bisect_invit_df(int n, int nev, TriWork w, const double* norms, 
     bool above = true;
     if (!stop && g < kBisLanes - 1)
       above = sturm_count_df(n, dd, e2, df_from_double(lo + (double)(g + 1) * step), pivmin) > idx;
-    const unsigned mask = (__ballot_sync(0xffffffffu, above) >> (grp * kBisLanes)) & ((1u << kBisLanes) - 1);
+    const unsigned gmask = (kBisLanes == 32) ? 0xffffffffu : ((1u << (kBisLanes & 31)) - 1u);
+    const unsigned mask = (__ballot_sync(0xffffffffu, above) >> ((grp * kBisLanes) & 31)) & gmask;
     if (!stop) {
       const int first = __ffs(mask) - 1;
       const double nlo = (first == 0) ? lo : lo + (double)first * step;
@@ -203,34 +204,47 @@ __global__ void bisect_invit_df(int n, int nev, TriWork w, const double* norms, 
   }
   if (fabs(cd) < tiny) cd = (cd < 0 ? -tiny : tiny);
   u0[(size_t)(n - 1) * nev] = cd;
+  // u0 <- 1 / u0 (pivots kept away from zero): the divisions are independent
+  // of each other here, and the solves below then multiply
+#pragma unroll 4
   for (int i = 0; i < n; ++i) {
-    const double p = u0[(size_t)i * nev];
-    if (fabs(p) < tiny) u0[(size_t)i * nev] = (p < 0 ? -tiny : tiny);
+    double p = u0[(size_t)i * nev];
+    if (fabs(p) < tiny) p = (p < 0 ? -tiny : tiny);
+    u0[(size_t)i * nev] = 1.0 / p;
   }
   if (tnorm == 0.0) {   // zero matrix: any orthonormal basis is an eigenbasis
     for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] = (i == j) ? 1.0 : 0.0;
     return;
   }
   for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] = ii_start(i, j);
+  // The recurrences carry their running values in registers: every load
+  // below reads a value written in an earlier sweep, off the dependent chain.
   for (int it = 0; it < 3; ++it) {
+    double cur = X[j];   // forward elimination with the row interchanges
+#pragma unroll 4
     for (int i = 0; i + 1 < n; ++i) {
-      double yi = X[(size_t)i * ldx + j], yn = X[(size_t)(i + 1) * ldx + j];
+      double yi = cur, yn = X[(size_t)(i + 1) * ldx + j];
       if (pv[(size_t)i * nev] != 0.0) { const double t = yi; yi = yn; yn = t; }
       yn -= ll[(size_t)i * nev] * yi;
       X[(size_t)i * ldx + j] = yi;
-      X[(size_t)(i + 1) * ldx + j] = yn;
+      cur = yn;
     }
-    double xn1 = 0.0, xn2 = 0.0, mx = 0.0;
+    X[(size_t)(n - 1) * ldx + j] = cur;
+    double xn1 = 0.0, xn2 = 0.0, mx = 0.0;   // back substitution (u0 holds 1 / pivot)
+#pragma unroll 4
     for (int i = n - 1; i >= 0; --i) {
-      const double xi = (X[(size_t)i * ldx + j] - u1[(size_t)i * nev] * xn1 - u2[(size_t)i * nev] * xn2) /
+      const double xi = (X[(size_t)i * ldx + j] - u1[(size_t)i * nev] * xn1 - u2[(size_t)i * nev] * xn2) *
                         u0[(size_t)i * nev];
       X[(size_t)i * ldx + j] = xi;
       xn2 = xn1; xn1 = xi;
       mx = fmax(mx, fabs(xi));
     }
+    const double rmx = 1.0 / mx;
     double nrm = 0.0;
-    for (int i = 0; i < n; ++i) { const double v = X[(size_t)i * ldx + j] / mx; nrm += v * v; }
-    const double sc = 1.0 / (mx * sqrt(nrm));
+#pragma unroll 4
+    for (int i = 0; i < n; ++i) { const double v = X[(size_t)i * ldx + j] * rmx; nrm += v * v; }
+    const double sc = rmx / sqrt(nrm);
+#pragma unroll 4
     for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] *= sc;
   }
 }
@@ -299,10 +313,10 @@ __device__ __forceinline__ df64 df_block_sum(df64 v, df64* red) {
   return t;
 }
 
-// v_j = (x_j - alpha [j == 0]) / vn in df64 (zero vector when s = 0).
-__device__ __forceinline__ df64 house_v_df(df64 xj, bool first, double s, double alpha, df64 rvn) {
-  if (s == 0.0) return df64{0.f, 0.f};
-  const df64 t = first ? df_sub(xj, df_from_double(alpha)) : xj;
+// v_j = (x_j - alpha [j == 0]) / vn in df64 (zero vector when szero).
+__device__ __forceinline__ df64 house_v_df(df64 xj, bool first, bool szero, df64 alpha, df64 rvn) {
+  if (szero) return df64{0.f, 0.f};
+  const df64 t = first ? df_sub(xj, alpha) : xj;
   return df_mul(t, rvn);
 }
 
@@ -335,7 +349,7 @@ struct TriPersist {
 
 constexpr int kTriThreads = 512;
 constexpr int kTriWarps = kTriThreads / 32;
-constexpr int kTriUnroll = 8;   // row entries in flight per lane
+constexpr int kTriUnroll = 16;  // row entries in flight per lane
 
 __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersist t) {
   extern __shared__ df64 smp[];
@@ -351,15 +365,25 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
     const bool upd = r >= 1;
     if (upd) {
       const df64* qin = ((r - 1) & 1) ? t.q[1] : t.q[0];
-      if (tid < 32) {
+      if (tid < 32) {   // loads of 8 partials per lane in flight before the adds
         df64 c{0.f, 0.f};
-        for (int g = tid; g < G; g += 32) c = df_add(c, qin[g]);
+        for (int g0 = 0; g0 < G; g0 += 256) {
+          df64 qb[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int g = g0 + 32 * u + tid;
+            qb[u] = (g < G) ? qin[g] : df64{0.f, 0.f};
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) c = df_add(c, qb[u]);
+        }
         c = df_warp_sum(c);
         if (tid == 0) c_s = c;
       }
       __syncthreads();
       const df64 c2{2.f * c_s.hi, 2.f * c_s.lo};
       const df64* pin = ((r - 1) & 1) ? t.p[1] : t.p[0];
+#pragma unroll 4
       for (int j = r + tid; j < n; j += blockDim.x) {
         const df64 pj = pin[j];
         wk[j] = df_sub(df64{2.f * pj.hi, 2.f * pj.lo}, df_mul(c2, vcur[j]));
@@ -381,7 +405,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
       vnew[j] = x;
       acc = df_fma(x, x, acc);
     }
-    const double s = df_to_double(df_block_sum(acc, red));
+    const df64 s = df_block_sum(acc, red);
     if (r == n - 2) {   // 2 x 2 tail: no further reflector
       if (blockIdx.x == 0 && tid == 0) {
         const int j = n - 1;
@@ -392,16 +416,22 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
       }
       return;
     }
-    const double x0 = df_to_double(vnew[r + 1]);
-    double alpha = 0.0, vnorm = 1.0;
-    if (s > 0.0) {
-      alpha = (x0 >= 0.0) ? -sqrt(s) : sqrt(s);
-      vnorm = sqrt(s - x0 * x0 + (x0 - alpha) * (x0 - alpha));
+    // Householder scalars in df64 (FP64 instructions are slow on this part and
+    // these sit on every pass's critical path): alpha = -sign(x0) ||x||, and
+    // ||x - alpha e_1||^2 = s - x0^2 + (|x0| + ||x||)^2 = 2 (s + |x0| ||x||)
+    const df64 x0 = vnew[r + 1];
+    const bool szero = !(s.hi > 0.f);
+    df64 alpha{0.f, 0.f}, rvn{1.f, 0.f};
+    if (!szero) {
+      const df64 sq = df_sqrt(s);
+      alpha = (x0.hi >= 0.f) ? df_neg(sq) : sq;
+      const df64 ax0 = (x0.hi >= 0.f) ? x0 : df_neg(x0);
+      const df64 h = df_add(s, df_mul(ax0, sq));
+      rvn = df_div(df64{1.f, 0.f}, df_sqrt(df64{2.f * h.hi, 2.f * h.lo}));
     }
-    const df64 rvn = df_from_double(1.0 / vnorm);
     __syncthreads();
-    for (int j = r + 1 + tid; j < n; j += blockDim.x) vnew[j] = house_v_df(vnew[j], j == r + 1, s, alpha, rvn);
-    if (blockIdx.x == 0 && tid == 0) t.e[r] = alpha;
+    for (int j = r + 1 + tid; j < n; j += blockDim.x) vnew[j] = house_v_df(vnew[j], j == r + 1, szero, alpha, rvn);
+    if (blockIdx.x == 0 && tid == 0) t.e[r] = df_to_double(alpha);
     __syncthreads();
     // rows i >= r+1 of this warp: update with (v_{r-1}, w_{r-1}), dot with v_r
     df64* pout = (r & 1) ? t.p[1] : t.p[0];
@@ -571,7 +601,11 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
   if (prof) prof->begin(PK_EIG_SOLVE, s);
   tri_norm<<<1, 256, 0, s>>>(n, w, norms); count_launches(1);
   tri_scale_df<<<(n + 255) / 256, 256, 0, s>>>(n, w, norms, dd, e2); count_launches(1);
-  bisect_invit_df<<<(nev + 15) / 16, 128, 0, s>>>(n, nev, w, norms, dd, e2, evals, X, ldx, lu); count_launches(1);
+  {
+    const int per_block = (128 / 32) * (32 / kBisLanes);   // eigenvalues per block of 128 threads
+    bisect_invit_df<<<(nev + per_block - 1) / per_block, 128, 0, s>>>(n, nev, w, norms, dd, e2, evals, X, ldx, lu);
+    count_launches(1);
+  }
   cluster_mgs<<<1, 512, 0, s>>>(n, nev, norms, evals, X, ldx); count_launches(1);
   if (prof) prof->end(PK_EIG_SOLVE, s, 0.0, 0.0);
   if (prof) prof->begin(PK_EIG_BACK, s);
