@@ -46,15 +46,17 @@ typedef enum {
   AS_ENOTSUP = 7    /* valid request that this build does not implement */
 } as_status;
 
-/* The stream setting.  Only AS_PERSISTENT (Algorithm 8) and AS_FIXED_THETA
- * (Algorithm 3 with a fixed dump threshold) are implemented; the others return
- * AS_ENOTSUP from sketch_create. */
+/* The stream setting.  AS_SLIDING (Algorithm 6) is not implemented:
+ * sketch_create returns AS_ENOTSUP for it. */
 typedef enum {
   AS_PERSISTENT = 0,   /* theta = eps ||A_t||_F^2 before every update (Algorithm 8) */
-  AS_FIXED_THETA = 1,  /* theta = cfg.theta for the whole stream (Algorithm 3) */
+  AS_FIXED_THETA = 1,  /* theta = cfg.theta, changed only by sketch_set_theta (Algorithm 3) */
   AS_SLIDING = 2,      /* Algorithm 6: not implemented */
-  AS_SITE = 3,         /* Algorithm 10, site side: not implemented */
-  AS_COORDINATOR = 4   /* Algorithm 10, coordinator side: not implemented */
+  AS_SITE = 3,         /* Algorithm 10, a site: as AS_FIXED_THETA (cfg.theta may be +inf); its
+                          snapshots are moved to a coordinator by sketch_send_snapshots */
+  AS_COORDINATOR = 4   /* Algorithm 10, the coordinator: no rows (sketch_update returns
+                          AS_EINVAL); accumulates received snapshot terms; its query is
+                          Algorithm 5 lines 5-7 on that sum */
 } as_mode;
 
 /* Arithmetic of the products.  In every form the orthonormalisations, the
@@ -113,6 +115,8 @@ typedef struct {
   int32_t device_status;   /* sticky as_status recorded on the device */
   int32_t reserved1;
   int64_t kernel_launches; /* kernels this library launched, all sketches, since load */
+  int64_t snapshots_sent;      /* snapshots moved out by sketch_send_snapshots */
+  int64_t snapshots_received;  /* snapshots accumulated from other sketches */
 } as_stats;
 
 /* Per kernel class timing (AS_PROFILE): CUDA-event time on the sketch's
@@ -175,10 +179,62 @@ as_status sketch_get_buffer(as_sketch* h, float* out, int32_t* r_out);
  * of the rows sketch_get_buffer returns.  Synchronises. */
 as_status sketch_get_gram(as_sketch* h, double* out);
 
-/* Merge src into dst by decomposability (Appendix E, the sum of per-part
- * errors bounds the error of the union): dst's query then covers both
- * streams.  Requires equal d.  Not implemented in this build: AS_ENOTSUP. */
+/* Merge src into dst by decomposability (Appendix E: the covariance of a
+ * union of streams is the sum of the parts', and the errors add): dst
+ * accumulates src's whole query Gram, C^T C plus every snapshot term plus
+ * what src itself absorbed, in a d x d FP64 accumulator that dst's
+ * current-time query adds to its own B.  src is not modified.  Requires equal
+ * d (AS_EINVAL otherwise; also for dst == src).  Synchronises both streams. */
 as_status sketch_merge(as_sketch* dst, const as_sketch* src);
+
+/* Set the dump threshold theta (>= 0, +inf allowed) of an AS_FIXED_THETA or
+ * AS_SITE sketch; it applies from the next row on.  Algorithm 10: a site sets
+ * theta when it receives the coordinator's broadcast.  Other modes or a
+ * negative or NaN theta: AS_EINVAL. */
+as_status sketch_set_theta(as_sketch* h, double theta);
+
+/* Algorithm 10, site side: send every snapshot in src's queue to dst (the
+ * coordinator, or any sketch of the same d) and delete them from src's queue.
+ * dst adds each term Z Y + Y^T Z^T - Z (Y Z) Z^T to its d x d FP64
+ * accumulator, in time order, on dst's stream.  *sent (may be NULL) receives
+ * the number of snapshots moved.  Requires equal d. */
+as_status sketch_send_snapshots(as_sketch* src, as_sketch* dst, int32_t* sent);
+
+/* ---- P5: distributed sites and coordinator (Algorithm 10) --------------
+ * m AS_SITE sketches and one AS_COORDINATOR sketch on one stream, driven in
+ * synchronous rounds.  Per row of site j: F_j += ||a||^2; when F_j >=
+ * (eps/m) F_hat (the last broadcast value) the site messages F_j and resets
+ * it; the row updates site j; site j's snapshots are then sent to the
+ * coordinator.  At the end of a round the coordinator adds the messages in
+ * site order and, at every m-th message, broadcasts F_hat: each site's
+ * threshold becomes (eps/m) F_hat (the per-site error of the analysis; the
+ * algorithm text prints eps F_hat).  Sites start with theta = +inf
+ * (Algorithm 10 leaves it open): nothing is sent before the first broadcast.
+ * Site j uses Philox stream_id = site_cfg->stream_id + j. */
+typedef struct as_p5 as_p5;
+
+typedef struct {
+  int64_t rounds, messages, broadcasts, snapshots_sent;
+  double f_hat;    /* the coordinator's F_hat */
+  double f_site;   /* F_hat as the sites know it (last broadcast) */
+} as_p5_counters;
+
+/* site_cfg: the sites' configuration (mode and theta are overridden).  m >= 1.
+ * AS_EINVAL on bad arguments; errors of sketch_create are passed through. */
+as_status as_p5_create(const as_config* site_cfg, int32_t m, void* cuda_stream, as_p5** out);
+/* One synchronous round: rows[j] (host or device, n[j] rows of d FP32 values,
+ * row stride ld[j] >= d) are site j's rows; n[j] = 0 is allowed. */
+as_status as_p5_round(as_p5* p, const float* const* rows, const int64_t* n, const int64_t* ld);
+/* The coordinator's Query (Algorithm 5 lines 5-7 on B): l x d, as sketch_query. */
+as_status as_p5_query(as_p5* p, float* out, int64_t ldo, int32_t* rows_out);
+/* The coordinator's B (d x d FP64, host memory). */
+as_status as_p5_query_gram(as_p5* p, double* out);
+as_status as_p5_stats(as_p5* p, as_p5_counters* out);
+/* Borrowed handles (owned by p): site j, the coordinator. */
+as_status as_p5_site(as_p5* p, int32_t j, as_sketch** out);
+as_status as_p5_coordinator(as_p5* p, as_sketch** out);
+/* Destroy p, its sites and its coordinator.  NULL is a no-op. */
+as_status as_p5_destroy(as_p5* p);
 
 /* Counters and the sticky device status.  Synchronises. */
 as_status sketch_stats(as_sketch* h, as_stats* out);

@@ -47,6 +47,7 @@ class P5:
         self.F_site = 0.0             # F_hat as the sites know it (last broadcast)
         self.F_hat = 0.0              # the coordinator's running F_hat
         self.msgs = 0
+        self.messages = 0
         self.broadcasts = 0
         self.B = np.zeros((d, d))
         self.sent_snapshots = 0
@@ -69,6 +70,7 @@ class P5:
                     self.sent_snapshots += 1
         for f in pending:                                    # coordinator, Receive_Update
             self.F_hat += f
+            self.messages += 1
             self.msgs += 1
             if self.msgs >= self.m:
                 self.msgs = 0

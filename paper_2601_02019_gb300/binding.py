@@ -18,7 +18,9 @@ AS_PROFILE = 0x2
 
 EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram", "sketch_get_buffer", "sketch_get_gram",
             "sketch_merge", "sketch_stats", "sketch_trace", "sketch_profile", "sketch_profile_reset",
-            "sketch_destroy", "as_symeig", "as_symeig_noalloc", "as_tc_gemm", "as_status_str", "as_last_error")
+            "sketch_destroy", "as_symeig", "as_symeig_noalloc", "as_tc_gemm", "as_status_str", "as_last_error",
+            "sketch_set_theta", "sketch_send_snapshots", "as_p5_create", "as_p5_round", "as_p5_query",
+            "as_p5_query_gram", "as_p5_stats", "as_p5_site", "as_p5_coordinator", "as_p5_destroy")
 
 
 class AsConfig(ct.Structure):
@@ -33,10 +35,16 @@ class AsStats(ct.Structure):
                 ("reserved0", ct.c_int32), ("fro2", ct.c_double), ("theta", ct.c_double),
                 ("shrinks", ct.c_int64), ("gates", ct.c_int64), ("dumps", ct.c_int64),
                 ("snapshot_rank", ct.c_int64), ("si_runs", ct.c_int64), ("device_bytes", ct.c_int64),
-                ("device_status", ct.c_int32), ("reserved1", ct.c_int32), ("kernel_launches", ct.c_int64)]
+                ("device_status", ct.c_int32), ("reserved1", ct.c_int32), ("kernel_launches", ct.c_int64),
+                ("snapshots_sent", ct.c_int64), ("snapshots_received", ct.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
+
+
+class AsP5Counters(ct.Structure):
+    _fields_ = [("rounds", ct.c_int64), ("messages", ct.c_int64), ("broadcasts", ct.c_int64),
+                ("snapshots_sent", ct.c_int64), ("f_hat", ct.c_double), ("f_site", ct.c_double)]
 
 
 class AsEvent(ct.Structure):
@@ -86,6 +94,16 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.as_symeig.argtypes = [I32, P, I32, P, P]
     L.as_symeig_noalloc.argtypes = [I32, P, I32, P, P, P]
     L.as_tc_gemm.argtypes = [I32, I32, I32, P, P, I32, I32, P]
+    L.sketch_set_theta.argtypes = [P, ct.c_double]
+    L.sketch_send_snapshots.argtypes = [P, P, ct.POINTER(I32)]
+    L.as_p5_create.argtypes = [ct.POINTER(AsConfig), I32, P, ct.POINTER(P)]
+    L.as_p5_round.argtypes = [P, ct.POINTER(P), ct.POINTER(I64), ct.POINTER(I64)]
+    L.as_p5_query.argtypes = [P, P, I64, ct.POINTER(I32)]
+    L.as_p5_query_gram.argtypes = [P, P]
+    L.as_p5_stats.argtypes = [P, ct.POINTER(AsP5Counters)]
+    L.as_p5_site.argtypes = [P, I32, ct.POINTER(P)]
+    L.as_p5_coordinator.argtypes = [P, ct.POINTER(P)]
+    L.as_p5_destroy.argtypes = [P]
     L.as_status_str.argtypes = [ct.c_int]
     L.as_status_str.restype = ct.c_char_p
     L.as_last_error.argtypes = []
@@ -201,7 +219,89 @@ class Sketch:
         _check(lib().sketch_profile_reset(self._h), "sketch_profile_reset")
 
     def merge(self, other: "Sketch") -> None:
+        """Absorb other's whole query Gram (decomposability); other is unchanged."""
         _check(lib().sketch_merge(self._h, other._h), "sketch_merge")
+
+    def set_theta(self, theta: float) -> None:
+        _check(lib().sketch_set_theta(self._h, float(theta)), "sketch_set_theta")
+
+    def send_snapshots(self, dst: "Sketch") -> int:
+        """Move every queued snapshot term into dst's accumulator; returns how many."""
+        n = ct.c_int32()
+        _check(lib().sketch_send_snapshots(self._h, dst._h, ct.byref(n)), "sketch_send_snapshots")
+        return n.value
+
+
+class _Borrowed(Sketch):
+    """A sketch handle owned by someone else (a P5 site or coordinator)."""
+
+    def __init__(self, h, d: int, owner):
+        self._h = h
+        self.d = d
+        self._owner = owner
+        self.ell = self.stats()["ell"]
+
+    def close(self) -> None:
+        self._h = None
+
+
+class P5:
+    """Algorithm 10: m sites and a coordinator in synchronous rounds (C ABI as_p5)."""
+
+    def __init__(self, d: int, ell: int, m: int, *, eps: float = 0.0, prec: int = AS_FP32_PLAIN,
+                 seed: int = 0, stream_id: int = 0, trace: bool = False, stream=None):
+        cfg = AsConfig(d=d, ell=ell, eps=eps, mode=AS_SITE, prec=prec, seed=seed, stream_id=stream_id,
+                       flags=AS_TRACE_DECISIONS if trace else 0)
+        h = ct.c_void_p()
+        sp = None if stream is None else ct.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        _check(lib().as_p5_create(ct.byref(cfg), m, sp, ct.byref(h)), "as_p5_create")
+        self._h, self.d, self.m = h, d, m
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().as_p5_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def round(self, blocks) -> None:
+        """blocks[j]: site j's rows of this round (numpy FP32 or torch tensors, contiguous)."""
+        assert len(blocks) == self.m
+        keep = [np.ascontiguousarray(b, dtype=np.float32) if isinstance(b, np.ndarray) else b for b in blocks]
+        ptrs = (ct.c_void_p * self.m)(*[_ptr(b) for b in keep])
+        ns = (ct.c_int64 * self.m)(*[int(b.shape[0]) for b in keep])
+        lds = (ct.c_int64 * self.m)(*[self.d] * self.m)
+        _check(lib().as_p5_round(self._h, ptrs, ns, lds), "as_p5_round")
+
+    def query(self) -> np.ndarray:
+        out = np.zeros((self.site(0).ell, self.d), dtype=np.float32)
+        rows = ct.c_int32()
+        _check(lib().as_p5_query(self._h, ct.c_void_p(out.ctypes.data), self.d, ct.byref(rows)), "as_p5_query")
+        return out[: rows.value]
+
+    def query_gram(self) -> np.ndarray:
+        out = np.zeros((self.d, self.d), dtype=np.float64)
+        _check(lib().as_p5_query_gram(self._h, ct.c_void_p(out.ctypes.data)), "as_p5_query_gram")
+        return out
+
+    def stats(self) -> dict:
+        c = AsP5Counters()
+        _check(lib().as_p5_stats(self._h, ct.byref(c)), "as_p5_stats")
+        return {f: getattr(c, f) for f, _ in AsP5Counters._fields_}
+
+    def site(self, j: int) -> Sketch:
+        h = ct.c_void_p()
+        _check(lib().as_p5_site(self._h, j, ct.byref(h)), "as_p5_site")
+        return _Borrowed(h, self.d, self)
+
+    def coordinator(self) -> Sketch:
+        h = ct.c_void_p()
+        _check(lib().as_p5_coordinator(self._h, ct.byref(h)), "as_p5_coordinator")
+        return _Borrowed(h, self.d, self)
 
 
 def symeig(A: np.ndarray, nev: int) -> tuple[np.ndarray, np.ndarray]:

@@ -137,6 +137,11 @@ struct as_sketch {
   float* arena = nullptr;
   size_t arena_cap = 0, arena_used = 0;
   std::vector<Snap> snaps;
+  // absorbed terms (d x d FP64): snapshots sent here by sketch_send_snapshots
+  // and sketches merged in by sketch_merge; allocated on first use
+  double* Bx = nullptr;
+  double *sx_yz = nullptr, *sx_t = nullptr;   // scratch of the snapshot-term products
+  int sx_cap = 0;                              // xi capacity of the scratch
   as_stats st{};
   std::vector<as_event> trace;
   size_t dev_bytes = 0;
@@ -170,6 +175,8 @@ void free_all(as_sketch* h) {
   if (h->dstatus) cudaFree(h->dstatus);
   if (h->zero) cudaFree(h->zero);
   if (h->pb.cnt) cudaFree(h->pb.cnt);
+  double* xp[] = {h->Bx, h->sx_yz, h->sx_t};
+  for (double* p : xp) if (p) cudaFree(p);
   __nv_bfloat16* bp[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Wh, h->Wl, h->Cl2, h->Ctl2, h->Wl2};
   for (__nv_bfloat16* p : bp) if (p) cudaFree(p);
   if (h->h_buf) cudaFreeHost(h->h_buf);
@@ -554,9 +561,57 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
   return st;
 }
 
+__global__ void add_f64_kernel(double* dst, const double* src, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] += src[e];
+}
+
+// The absorbed accumulator Bx (d x d FP64, zeroed) on first use.
+as_status ensure_bx(as_sketch* h) {
+  if (h->Bx) return AS_OK;
+  as_status st = dalloc(&h->Bx, (size_t)h->d * h->d);
+  if (st != AS_OK) return st;
+  AS_CUDA_TRY(cudaMemsetAsync(h->Bx, 0, (size_t)h->d * h->d * sizeof(double), h->s));
+  return AS_OK;
+}
+
+// B += Z Y + (Z Y)^T - Z (Y Z) Z^T for every snapshot of `src` taken at a
+// row <= tmax (Algorithm 5 line 4), in time order, on stream st; the scratch
+// of `scr` (xi x xi and d x xi) is grown as needed.
+as_status add_snapshot_terms(const as_sketch* src, int64_t tmax, double* B, as_sketch* scr, cudaStream_t st) {
+  const int d = src->d;
+  int ximax = 1;
+  for (const Snap& sn : src->snaps) ximax = std::max(ximax, sn.xi);
+  if (ximax > scr->sx_cap) {
+    if (scr->sx_yz) cudaFree(scr->sx_yz);
+    if (scr->sx_t) cudaFree(scr->sx_t);
+    scr->sx_yz = scr->sx_t = nullptr;
+    scr->sx_cap = 0;
+    as_status st2 = dalloc(&scr->sx_yz, (size_t)ximax * ximax);
+    if (st2 == AS_OK) st2 = dalloc(&scr->sx_t, (size_t)scr->d * ximax);
+    if (st2 != AS_OK) return st2;
+    scr->sx_cap = ximax;
+  }
+  double* YZ = scr->sx_yz;
+  double* T = scr->sx_t;
+  as_status st2 = AS_OK;
+  for (const Snap& sn : src->snaps) {
+    if (sn.t > tmax) break;   // the queue is in time order
+    const float* Z = src->arena + sn.off;
+    const float* Y = Z + (size_t)d * sn.xi;
+    const int xi = sn.xi;
+    if ((st2 = gemm_strided<float, float, double>(st, d, d, xi, Z, xi, 1, Y, d, 1, B, d, 1, 1.0, 1.0)) != AS_OK) break;
+    if ((st2 = gemm_strided<float, float, double>(st, d, d, xi, Z, xi, 1, Y, d, 1, B, 1, d, 1.0, 1.0)) != AS_OK) break;
+    if ((st2 = gemm_strided<float, float, double>(st, xi, xi, d, Y, d, 1, Z, xi, 1, YZ, xi, 1, 1.0, 0.0)) != AS_OK) break;
+    if ((st2 = gemm_strided<float, double, double>(st, d, xi, xi, Z, xi, 1, YZ, xi, 1, T, xi, 1, 1.0, 0.0)) != AS_OK) break;
+    if ((st2 = gemm_strided<double, float, double>(st, d, d, xi, T, xi, 1, Z, 1, xi, B, d, 1, -1.0, 1.0)) != AS_OK) break;
+  }
+  return st2;
+}
+
 // Algorithm 5 lines 1-4 with lb = 0, ub = t: the residual C_t only at the
 // current time (t = T; older residuals are not stored) plus the snapshot
-// terms with t_j <= t.
+// terms with t_j <= t, plus (current time only) the absorbed terms Bx.
 as_status build_query_gram(as_sketch* h, int64_t t, double* B) {
   const int d = h->d;
   as_status st = AS_OK;
@@ -565,28 +620,12 @@ as_status build_query_gram(as_sketch* h, int64_t t, double* B) {
     st = gemm_strided<float, float, double>(h->s, d, d, h->r, h->C, 1, h->ldc, h->C, h->ldc, 1, B, d, 1, 1.0, 0.0);
     if (st != AS_OK) return st;
   }
-  int ximax = 1;
-  for (const Snap& sn : h->snaps) ximax = std::max(ximax, sn.xi);
-  double *YZ = nullptr, *T = nullptr;
-  st = dalloc(&YZ, (size_t)ximax * ximax);
-  if (st != AS_OK) return st;
-  st = dalloc(&T, (size_t)d * ximax);
-  if (st != AS_OK) { cudaFree(YZ); return st; }
-  for (const Snap& sn : h->snaps) {
-    if (sn.t > t) break;   // the queue is in time order
-    const float* Z = h->arena + sn.off;
-    const float* Y = Z + (size_t)d * sn.xi;
-    const int xi = sn.xi;
-    // B += Z Y + (Z Y)^T - Z (Y Z) Z^T   (Algorithm 5 line 4)
-    if ((st = gemm_strided<float, float, double>(h->s, d, d, xi, Z, xi, 1, Y, d, 1, B, d, 1, 1.0, 1.0)) != AS_OK) break;
-    if ((st = gemm_strided<float, float, double>(h->s, d, d, xi, Z, xi, 1, Y, d, 1, B, 1, d, 1.0, 1.0)) != AS_OK) break;
-    if ((st = gemm_strided<float, float, double>(h->s, xi, xi, d, Y, d, 1, Z, xi, 1, YZ, xi, 1, 1.0, 0.0)) != AS_OK) break;
-    if ((st = gemm_strided<float, double, double>(h->s, d, xi, xi, Z, xi, 1, YZ, xi, 1, T, xi, 1, 1.0, 0.0)) != AS_OK) break;
-    if ((st = gemm_strided<double, float, double>(h->s, d, d, xi, T, xi, 1, Z, 1, xi, B, d, 1, -1.0, 1.0)) != AS_OK) break;
+  st = add_snapshot_terms(h, t, B, h, h->s);
+  if (st == AS_OK && t == h->T && h->Bx) {
+    add_f64_kernel<<<256, 256, 0, h->s>>>(B, h->Bx, (size_t)d * d); count_launches(1);
+    AS_CUDA_TRY(cudaGetLastError());
   }
   cudaStreamSynchronize(h->s);
-  cudaFree(YZ);
-  cudaFree(T);
   return st;
 }
 
@@ -638,11 +677,10 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   }
   if (c.ell < 1 || 2 * (int64_t)c.ell > c.d) return AS_EINVAL;
   if (c.eps == 0.0) c.eps = 2.0 / c.ell;
-  if (c.mode != AS_PERSISTENT && c.mode != AS_FIXED_THETA) {
-    if (c.mode >= AS_SLIDING && c.mode <= AS_COORDINATOR) return AS_ENOTSUP;
+  if (c.mode == AS_SLIDING) return AS_ENOTSUP;
+  if (c.mode != AS_PERSISTENT && c.mode != AS_FIXED_THETA && c.mode != AS_SITE && c.mode != AS_COORDINATOR)
     return AS_EINVAL;
-  }
-  if (c.mode == AS_FIXED_THETA && !(c.theta >= 0.0)) return AS_EINVAL;
+  if ((c.mode == AS_FIXED_THETA || c.mode == AS_SITE) && !(c.theta >= 0.0)) return AS_EINVAL;
   if (c.prec != AS_FP32_PLAIN && c.prec != AS_BF16 && c.prec != AS_BF16X3 && c.prec != AS_BF16X6) return AS_EINVAL;
   if (c.prec != AS_FP32_PLAIN && !umma_available()) return AS_ENOTSUP;
   if (c.eps_si == 0.0) c.eps_si = 0.4;
@@ -663,7 +701,7 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   h->k_pi = c.k_pi;
   h->q = c.q_si;
   h->mode = c.mode;
-  h->theta = (c.mode == AS_FIXED_THETA) ? c.theta : 0.0;
+  h->theta = (c.mode == AS_FIXED_THETA || c.mode == AS_SITE) ? c.theta : 0.0;
   const int mn = std::min(c.ell, c.d);
   h->jmax = (mn > 1) ? ceil_log2(mn) : 0;
   h->s = (cudaStream_t)cuda_stream;
@@ -783,6 +821,7 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
 
 as_status sketch_update(as_sketch* h, const float* rows, int64_t n, int64_t ld) {
   if (!h) return AS_EINVAL;
+  if (h->mode == AS_COORDINATOR) return AS_EINVAL;   // a coordinator only receives
   if (n == 0) return AS_OK;
   if (!rows || n < 0 || ld < h->d) return AS_EINVAL;
   std::unique_lock<std::mutex> lk(h->mu, std::try_to_lock);
@@ -893,10 +932,61 @@ as_status sketch_get_gram(as_sketch* h, double* out) {
   return e == cudaSuccess ? AS_OK : as_from_cuda(e);
 }
 
-as_status sketch_merge(as_sketch* dst, const as_sketch* src) {
-  if (!dst || !src) return AS_EINVAL;
+as_status sketch_merge(as_sketch* dst, const as_sketch* src_c) {
+  if (!dst || !src_c || dst == src_c) return AS_EINVAL;
+  as_sketch* src = const_cast<as_sketch*>(src_c);   // locked and synchronised, not modified
   if (dst->d != src->d) return AS_EINVAL;
-  return AS_ENOTSUP;
+  std::unique_lock<std::mutex> l1(dst->mu, std::try_to_lock);
+  if (!l1.owns_lock()) return AS_EBUSY;
+  std::unique_lock<std::mutex> l2(src->mu, std::try_to_lock);
+  if (!l2.owns_lock()) return AS_EBUSY;
+  AS_CUDA_TRY(cudaStreamSynchronize(src->s));
+  as_status st = ensure_bx(dst);
+  if (st != AS_OK) return st;
+  const int d = dst->d;
+  // dst.Bx += src.C^T C + src's snapshot terms + src.Bx: src's whole query Gram
+  if (src->r > 0)
+    st = gemm_strided<float, float, double>(dst->s, d, d, src->r, src->C, 1, src->ldc, src->C, src->ldc, 1, dst->Bx, d,
+                                            1, 1.0, 1.0);
+  if (st == AS_OK) st = add_snapshot_terms(src, INT64_MAX, dst->Bx, dst, dst->s);
+  if (st == AS_OK && src->Bx) {
+    add_f64_kernel<<<256, 256, 0, dst->s>>>(dst->Bx, src->Bx, (size_t)d * d); count_launches(1);
+    AS_CUDA_TRY(cudaGetLastError());
+  }
+  if (st == AS_OK) AS_CUDA_TRY(cudaStreamSynchronize(dst->s));
+  return st;
+}
+
+as_status sketch_set_theta(as_sketch* h, double theta) {
+  if (!h || !(theta >= 0.0)) return AS_EINVAL;
+  if (h->mode != AS_FIXED_THETA && h->mode != AS_SITE) return AS_EINVAL;
+  std::unique_lock<std::mutex> lk(h->mu, std::try_to_lock);
+  if (!lk.owns_lock()) return AS_EBUSY;
+  h->theta = theta;
+  return AS_OK;
+}
+
+as_status sketch_send_snapshots(as_sketch* src, as_sketch* dst, int32_t* sent) {
+  if (sent) *sent = 0;
+  if (!src || !dst || src == dst || src->d != dst->d) return AS_EINVAL;
+  std::unique_lock<std::mutex> l1(dst->mu, std::try_to_lock);
+  if (!l1.owns_lock()) return AS_EBUSY;
+  std::unique_lock<std::mutex> l2(src->mu, std::try_to_lock);
+  if (!l2.owns_lock()) return AS_EBUSY;
+  const int32_t n = (int32_t)src->snaps.size();
+  if (n == 0) return AS_OK;
+  if (src->s != dst->s) AS_CUDA_TRY(cudaStreamSynchronize(src->s));
+  as_status st = ensure_bx(dst);
+  if (st == AS_OK) st = add_snapshot_terms(src, INT64_MAX, dst->Bx, dst, dst->s);
+  if (st != AS_OK) return st;
+  // the terms are queued on dst's stream before src's arena can be refilled
+  if (src->s != dst->s) AS_CUDA_TRY(cudaStreamSynchronize(dst->s));
+  src->snaps.clear();
+  src->arena_used = 0;
+  src->st.snapshots_sent += n;
+  dst->st.snapshots_received += n;
+  if (sent) *sent = n;
+  return AS_OK;
 }
 
 as_status sketch_stats(as_sketch* h, as_stats* out) {

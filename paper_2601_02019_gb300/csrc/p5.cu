@@ -1,0 +1,219 @@
+// P5 (Algorithm 10): the tracking distributed matrix sketch with m sites and
+// one coordinator, driven in synchronous rounds on one stream.
+//
+// Site j, for each of its rows a (in order):
+//   F_j += ||a||^2; if F_j >= (eps/m) F_hat_known: message F_j, F_j = 0;
+//   AeroSketch update of a (AS_SITE sketch, threshold theta);
+//   every snapshot taken is sent to the coordinator and deleted.
+// Coordinator:
+//   each message: F_hat += F_j, msgs += 1; at msgs >= m: msgs = 0 and
+//   broadcast F_hat (every site then uses theta = (eps/m) F_hat);
+//   each snapshot (Z, Y = Z^T C'^T C'): B += Z Y + Y^T Z^T - Z (Y Z) Z^T;
+//   Query: Algorithm 5 lines 5-7 on B.
+// Readings: a site starts with theta = +inf (Algorithm 10 leaves the initial
+// threshold open; with 0 the stop test of Algorithm 2 would depend on the
+// rounding sign of numerically zero Ritz values), its threshold after a
+// broadcast is (eps/m) F_hat (the per-site error of the analysis), and the
+// messages of a round reach the coordinator at the round's end in site order.
+//
+// The scalar protocol runs on the host; the rows, the snapshot terms and the
+// coordinator's query run in the library's kernels (sketch calls only).
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+struct as_p5 {
+  int m = 0, d = 0, ell = 0;
+  double eps = 0.0;
+  cudaStream_t s = nullptr;
+  std::vector<as_sketch*> sites;
+  as_sketch* coord = nullptr;
+  std::vector<double> F;     // unsent row mass of each site
+  double F_site = 0.0;       // F_hat as the sites know it (last broadcast)
+  double F_hat = 0.0;        // the coordinator's running sum
+  int msgs = 0;
+  as_p5_counters st{};
+  double* dn = nullptr;      // device row norms
+  double* hn = nullptr;      // pinned host copy
+  size_t n_cap = 0;
+};
+
+namespace {
+
+// ||row||^2 in FP64, one warp per row.
+__global__ void row_norm2_kernel(const float* rows, long long ld, long long n, int d, double* out) {
+  const long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const float* r = rows + i * ld;
+  double s = 0.0;
+  for (int c = lane; c < d; c += 32) {
+    const double v = (double)r[c];
+    s += v * v;
+  }
+  s = as::warp_sum(s);
+  if (lane == 0) out[i] = s;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+as_status norms_of(as_p5* p, const float* rows, long long n, long long ld, std::vector<double>& out) {
+  out.assign((size_t)n, 0.0);
+  if (n == 0) return AS_OK;
+  if (!on_device(rows)) {
+    for (long long i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int c = 0; c < p->d; ++c) {
+        const double v = (double)rows[i * ld + c];
+        s += v * v;
+      }
+      out[(size_t)i] = s;
+    }
+    return AS_OK;
+  }
+  if ((size_t)n > p->n_cap) {
+    if (p->dn) cudaFree(p->dn);
+    if (p->hn) cudaFreeHost(p->hn);
+    p->dn = nullptr;
+    p->hn = nullptr;
+    p->n_cap = 0;
+    AS_CUDA_TRY(cudaMalloc((void**)&p->dn, (size_t)n * sizeof(double)));
+    AS_CUDA_TRY(cudaMallocHost((void**)&p->hn, (size_t)n * sizeof(double)));
+    p->n_cap = (size_t)n;
+  }
+  row_norm2_kernel<<<(unsigned)((n + 7) / 8), 256, 0, p->s>>>(rows, ld, n, p->d, p->dn);
+  as::count_launches(1);
+  AS_CUDA_TRY(cudaGetLastError());
+  AS_CUDA_TRY(cudaMemcpyAsync(p->hn, p->dn, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, p->s));
+  AS_CUDA_TRY(cudaStreamSynchronize(p->s));
+  for (long long i = 0; i < n; ++i) out[(size_t)i] = p->hn[i];
+  return AS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+as_status as_p5_destroy(as_p5* p) {
+  if (!p) return AS_OK;
+  for (as_sketch* h : p->sites) sketch_destroy(h);
+  sketch_destroy(p->coord);
+  if (p->dn) cudaFree(p->dn);
+  if (p->hn) cudaFreeHost(p->hn);
+  delete p;
+  return AS_OK;
+}
+
+as_status as_p5_create(const as_config* site_cfg, int32_t m, void* cuda_stream, as_p5** out) {
+  if (!site_cfg || !out || m < 1) return AS_EINVAL;
+  *out = nullptr;
+  as_p5* p = new (std::nothrow) as_p5();
+  if (!p) return AS_ENOMEM;
+  p->m = m;
+  p->s = (cudaStream_t)cuda_stream;
+  as_config c = *site_cfg;
+  c.mode = AS_COORDINATOR;
+  as_status st = sketch_create(&c, cuda_stream, &p->coord);
+  for (int j = 0; j < m && st == AS_OK; ++j) {
+    as_config cj = *site_cfg;
+    cj.mode = AS_SITE;
+    cj.theta = INFINITY;
+    cj.stream_id = site_cfg->stream_id + (uint64_t)j;
+    as_sketch* h = nullptr;
+    st = sketch_create(&cj, cuda_stream, &h);
+    if (st == AS_OK) p->sites.push_back(h);
+  }
+  if (st == AS_OK) {
+    as_stats cs{};
+    st = sketch_stats(p->coord, &cs);
+    p->d = cs.d;
+    p->ell = cs.ell;
+    p->eps = (site_cfg->eps > 0.0) ? site_cfg->eps : 2.0 / cs.ell;
+  }
+  if (st != AS_OK) {
+    as_p5_destroy(p);
+    return st;
+  }
+  p->F.assign((size_t)m, 0.0);
+  *out = p;
+  return AS_OK;
+}
+
+as_status as_p5_round(as_p5* p, const float* const* rows, const int64_t* n, const int64_t* ld) {
+  if (!p || !rows || !n || !ld) return AS_EINVAL;
+  for (int j = 0; j < p->m; ++j)
+    if (n[j] < 0 || (n[j] > 0 && (!rows[j] || ld[j] < p->d))) return AS_EINVAL;
+  std::vector<double> pending, nrm;
+  for (int j = 0; j < p->m; ++j) {
+    as_status st = norms_of(p, rows[j], n[j], ld[j], nrm);
+    if (st != AS_OK) return st;
+    for (double v : nrm) {
+      p->F[(size_t)j] += v;
+      if (p->F[(size_t)j] >= (p->eps / p->m) * p->F_site) {   // message F_j
+        pending.push_back(p->F[(size_t)j]);
+        p->F[(size_t)j] = 0.0;
+      }
+    }
+    if (n[j] > 0) {
+      st = sketch_update(p->sites[(size_t)j], rows[j], n[j], ld[j]);
+      if (st != AS_OK) return st;
+    }
+    int32_t sent = 0;
+    st = sketch_send_snapshots(p->sites[(size_t)j], p->coord, &sent);
+    if (st != AS_OK) return st;
+    p->st.snapshots_sent += sent;
+  }
+  for (double f : pending) {   // the coordinator's Receive_Update, at the round's end
+    p->F_hat += f;
+    p->st.messages += 1;
+    if (++p->msgs >= p->m) {
+      p->msgs = 0;
+      p->st.broadcasts += 1;
+      p->F_site = p->F_hat;
+      for (as_sketch* h : p->sites) {
+        as_status st = sketch_set_theta(h, (p->eps / p->m) * p->F_hat);
+        if (st != AS_OK) return st;
+      }
+    }
+  }
+  p->st.rounds += 1;
+  p->st.f_hat = p->F_hat;
+  p->st.f_site = p->F_site;
+  return AS_OK;
+}
+
+as_status as_p5_query(as_p5* p, float* out, int64_t ldo, int32_t* rows_out) {
+  if (!p) return AS_EINVAL;
+  return sketch_query(p->coord, -1, out, ldo, rows_out);
+}
+
+as_status as_p5_query_gram(as_p5* p, double* out) {
+  if (!p) return AS_EINVAL;
+  return sketch_query_gram(p->coord, -1, out);
+}
+
+as_status as_p5_stats(as_p5* p, as_p5_counters* out) {
+  if (!p || !out) return AS_EINVAL;
+  *out = p->st;
+  return AS_OK;
+}
+
+as_status as_p5_site(as_p5* p, int32_t j, as_sketch** out) {
+  if (!p || !out || j < 0 || j >= p->m) return AS_EINVAL;
+  *out = p->sites[(size_t)j];
+  return AS_OK;
+}
+
+as_status as_p5_coordinator(as_p5* p, as_sketch** out) {
+  if (!p || !out) return AS_EINVAL;
+  *out = p->coord;
+  return AS_OK;
+}
+
+}  // extern "C"
