@@ -46,12 +46,13 @@ typedef enum {
   AS_ENOTSUP = 7    /* valid request that this build does not implement */
 } as_status;
 
-/* The stream setting.  AS_SLIDING (Algorithm 6) is not implemented:
- * sketch_create returns AS_ENOTSUP for it. */
+/* The stream setting.  The sliding window (Algorithm 6) is a set of
+ * AS_FIXED_THETA levels built by as_sw_create; sketch_create returns
+ * AS_ENOTSUP for AS_SLIDING. */
 typedef enum {
   AS_PERSISTENT = 0,   /* theta = eps ||A_t||_F^2 before every update (Algorithm 8) */
   AS_FIXED_THETA = 1,  /* theta = cfg.theta, changed only by sketch_set_theta (Algorithm 3) */
-  AS_SLIDING = 2,      /* Algorithm 6: not implemented */
+  AS_SLIDING = 2,      /* Algorithm 6: use as_sw_create (sketch_create: AS_ENOTSUP) */
   AS_SITE = 3,         /* Algorithm 10, a site: as AS_FIXED_THETA (cfg.theta may be +inf); its
                           snapshots are moved to a coordinator by sketch_send_snapshots */
   AS_COORDINATOR = 4   /* Algorithm 10, the coordinator: no rows (sketch_update returns
@@ -235,6 +236,44 @@ as_status as_p5_site(as_p5* p, int32_t j, as_sketch** out);
 as_status as_p5_coordinator(as_p5* p, as_sketch** out);
 /* Destroy p, its sites and its coordinator.  NULL is a no-op. */
 as_status as_p5_destroy(as_p5* p);
+
+/* ---- Sliding window: ML-AeroSketch (Algorithm 6) ------------------------
+ * The sketch of the last N rows.  L = ceil(log2 R) + 1 levels (R: an upper
+ * bound of the rows' squared norms, >= 1), level j an AS_FIXED_THETA sketch
+ * with theta_j = 2^j eps N (Philox stream_id = cfg->stream_id + j) and a
+ * queue of its snapshots and of the raw rows with ||a||^2 >= theta_j, at
+ * most 8/eps items, items older than the window dropped.  Each queued item
+ * carries s = (t of the previous item) + 1, or 1 on an empty queue (the
+ * snapshot rule of Algorithm 4, read for raw rows too).  The query answers
+ * from the lowest level whose queue is empty or starts at s <= max(1,
+ * T - N + 1) (the top level if none), with B = its residual C^T C + its
+ * queued snapshot terms and raw rows a^T a in (T-N, T], then Algorithm 5
+ * lines 5-7.  A level's sketch numbers its own rows for its random draws. */
+typedef struct as_sw as_sw;
+
+typedef struct {
+  int64_t rows;               /* T: rows fed */
+  int32_t levels, last_level; /* L; the level of the last query (-1 before any) */
+  int64_t raw_queued, snapshots_queued;   /* items in all queues now */
+  int64_t popped_expired, popped_cap;     /* items dropped by age, by the 8/eps cap */
+} as_sw_counters;
+
+/* cfg: d, ell or eps, prec, seed, stream_id of the levels (mode and theta
+ * are overridden).  N >= 1; R >= 1 and finite.  AS_EINVAL on bad arguments. */
+as_status as_sw_create(const as_config* cfg, int64_t N, double R, void* cuda_stream, as_sw** out);
+/* Feed n rows (host or device, row stride ld >= d); a non-finite row: AS_EINVAL,
+ * nothing of the call ingested. */
+as_status as_sw_update(as_sw* w, const float* rows, int64_t n, int64_t ld);
+/* The l x d sketch of the window (T-N, T] (as sketch_query); *level_out (may be
+ * NULL) receives the level that answered.  Synchronises. */
+as_status as_sw_query(as_sw* w, float* out, int64_t ldo, int32_t* rows_out, int32_t* level_out);
+/* The window's B (d x d FP64, host memory) before its eigendecomposition. */
+as_status as_sw_query_gram(as_sw* w, double* out, int32_t* level_out);
+as_status as_sw_stats(as_sw* w, as_sw_counters* out);
+/* Borrowed handle of level j's sketch (owned by w). */
+as_status as_sw_level(as_sw* w, int32_t j, as_sketch** out);
+/* Destroy w and its levels.  NULL is a no-op. */
+as_status as_sw_destroy(as_sw* w);
 
 /* Counters and the sticky device status.  Synchronises. */
 as_status sketch_stats(as_sketch* h, as_stats* out);

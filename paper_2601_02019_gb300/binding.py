@@ -20,7 +20,9 @@ EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram
             "sketch_merge", "sketch_stats", "sketch_trace", "sketch_profile", "sketch_profile_reset",
             "sketch_destroy", "as_symeig", "as_symeig_noalloc", "as_tc_gemm", "as_status_str", "as_last_error",
             "sketch_set_theta", "sketch_send_snapshots", "as_p5_create", "as_p5_round", "as_p5_query",
-            "as_p5_query_gram", "as_p5_stats", "as_p5_site", "as_p5_coordinator", "as_p5_destroy")
+            "as_p5_query_gram", "as_p5_stats", "as_p5_site", "as_p5_coordinator", "as_p5_destroy",
+            "as_sw_create", "as_sw_update", "as_sw_query", "as_sw_query_gram", "as_sw_stats", "as_sw_level",
+            "as_sw_destroy")
 
 
 class AsConfig(ct.Structure):
@@ -45,6 +47,12 @@ class AsStats(ct.Structure):
 class AsP5Counters(ct.Structure):
     _fields_ = [("rounds", ct.c_int64), ("messages", ct.c_int64), ("broadcasts", ct.c_int64),
                 ("snapshots_sent", ct.c_int64), ("f_hat", ct.c_double), ("f_site", ct.c_double)]
+
+
+class AsSwCounters(ct.Structure):
+    _fields_ = [("rows", ct.c_int64), ("levels", ct.c_int32), ("last_level", ct.c_int32),
+                ("raw_queued", ct.c_int64), ("snapshots_queued", ct.c_int64),
+                ("popped_expired", ct.c_int64), ("popped_cap", ct.c_int64)]
 
 
 class AsEvent(ct.Structure):
@@ -104,6 +112,13 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.as_p5_site.argtypes = [P, I32, ct.POINTER(P)]
     L.as_p5_coordinator.argtypes = [P, ct.POINTER(P)]
     L.as_p5_destroy.argtypes = [P]
+    L.as_sw_create.argtypes = [ct.POINTER(AsConfig), I64, ct.c_double, P, ct.POINTER(P)]
+    L.as_sw_update.argtypes = [P, P, I64, I64]
+    L.as_sw_query.argtypes = [P, P, I64, ct.POINTER(I32), ct.POINTER(I32)]
+    L.as_sw_query_gram.argtypes = [P, P, ct.POINTER(I32)]
+    L.as_sw_stats.argtypes = [P, ct.POINTER(AsSwCounters)]
+    L.as_sw_level.argtypes = [P, I32, ct.POINTER(P)]
+    L.as_sw_destroy.argtypes = [P]
     L.as_status_str.argtypes = [ct.c_int]
     L.as_status_str.restype = ct.c_char_p
     L.as_last_error.argtypes = []
@@ -334,3 +349,56 @@ def replay_from_trace(events: list[dict]) -> dict:
 
 def default_k_pi(d: int) -> int:
     return int(math.ceil(math.log2(d))) + 1
+
+
+class SlidingWindow:
+    """Algorithm 6: the sketch of the last N rows (C ABI as_sw)."""
+
+    def __init__(self, d: int, ell: int, N: int, R: float, *, eps: float = 0.0, prec: int = AS_FP32_PLAIN,
+                 seed: int = 0, stream_id: int = 0, trace: bool = False, stream=None):
+        cfg = AsConfig(d=d, ell=ell, eps=eps, mode=AS_FIXED_THETA, prec=prec, seed=seed, stream_id=stream_id,
+                       flags=AS_TRACE_DECISIONS if trace else 0)
+        h = ct.c_void_p()
+        sp = None if stream is None else ct.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        _check(lib().as_sw_create(ct.byref(cfg), int(N), float(R), sp, ct.byref(h)), "as_sw_create")
+        self._h, self.d, self.N = h, d, N
+        self.ell = self.level(0).ell
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().as_sw_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, rows) -> None:
+        if isinstance(rows, np.ndarray):
+            rows = np.ascontiguousarray(rows, dtype=np.float32)
+        _check(lib().as_sw_update(self._h, ct.c_void_p(_ptr(rows)), int(rows.shape[0]), self.d), "as_sw_update")
+
+    def query(self) -> tuple[np.ndarray, int]:
+        out = np.zeros((self.ell, self.d), dtype=np.float32)
+        rows, lvl = ct.c_int32(), ct.c_int32()
+        _check(lib().as_sw_query(self._h, ct.c_void_p(out.ctypes.data), self.d, ct.byref(rows), ct.byref(lvl)),
+               "as_sw_query")
+        return out[: rows.value], lvl.value
+
+    def query_gram(self) -> tuple[np.ndarray, int]:
+        out = np.zeros((self.d, self.d), dtype=np.float64)
+        lvl = ct.c_int32()
+        _check(lib().as_sw_query_gram(self._h, ct.c_void_p(out.ctypes.data), ct.byref(lvl)), "as_sw_query_gram")
+        return out, lvl.value
+
+    def stats(self) -> dict:
+        c = AsSwCounters()
+        _check(lib().as_sw_stats(self._h, ct.byref(c)), "as_sw_stats")
+        return {f: getattr(c, f) for f, _ in AsSwCounters._fields_}
+
+    def level(self, j: int) -> Sketch:
+        h = ct.c_void_p()
+        _check(lib().as_sw_level(self._h, j, ct.byref(h)), "as_sw_level")
+        return _Borrowed(h, self.d, self)

@@ -578,7 +578,8 @@ as_status ensure_bx(as_sketch* h) {
 // B += Z Y + (Z Y)^T - Z (Y Z) Z^T for every snapshot of `src` taken at a
 // row <= tmax (Algorithm 5 line 4), in time order, on stream st; the scratch
 // of `scr` (xi x xi and d x xi) is grown as needed.
-as_status add_snapshot_terms(const as_sketch* src, int64_t tmax, double* B, as_sketch* scr, cudaStream_t st) {
+as_status add_snapshot_terms(const as_sketch* src, int64_t tmax, double* B, as_sketch* scr, cudaStream_t st,
+                             int64_t tmin_excl = INT64_MIN) {
   const int d = src->d;
   int ximax = 1;
   for (const Snap& sn : src->snaps) ximax = std::max(ximax, sn.xi);
@@ -597,6 +598,7 @@ as_status add_snapshot_terms(const as_sketch* src, int64_t tmax, double* B, as_s
   as_status st2 = AS_OK;
   for (const Snap& sn : src->snaps) {
     if (sn.t > tmax) break;   // the queue is in time order
+    if (sn.t <= tmin_excl) continue;
     const float* Z = src->arena + sn.off;
     const float* Y = Z + (size_t)d * sn.xi;
     const int xi = sn.xi;
@@ -629,6 +631,36 @@ as_status build_query_gram(as_sketch* h, int64_t t, double* B) {
   return st;
 }
 
+// Eigendecomposition of the device matrix B (d x d FP64, destroyed) and the
+// shrink of Algorithm 5 lines 5-7: the l x d sketch to out (host or device,
+// row stride ldo).  Synchronises.
+as_status eig_shrink_to(as_sketch* h, double* B, float* out, int64_t ldo) {
+  const int d = h->d, ell = h->ell;
+  double *lam = nullptr, *V = nullptr, *w = nullptr;
+  float* o = nullptr;
+  const bool big_q = d > 256;
+  as_status st = dalloc(&lam, (size_t)d);
+  if (st == AS_OK) st = dalloc(&V, (size_t)d * ell);
+  if (st == AS_OK) st = dalloc(&w, big_q ? eig_large_work_doubles(d, ell) : eig_work_doubles(d, ell));
+  if (st == AS_OK) st = dalloc(&o, (size_t)ell * d);
+  if (st == AS_OK)
+    st = big_q ? launch_eig_large(h->s, d, B, d, ell, lam, V, ell, w, nullptr, h->dstatus)
+               : launch_eig(h->s, d, B, d, ell, lam, V, ell, w);
+  if (st == AS_OK) st = launch_shrink_rows(h->s, d, ell, lam, V, ell, o, d);
+  if (st == AS_OK) {
+    cudaError_t e = cudaMemcpy2DAsync(out, (size_t)ldo * sizeof(float), o, (size_t)d * sizeof(float),
+                                      (size_t)d * sizeof(float), (size_t)ell, cudaMemcpyDefault, h->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+    if (e != cudaSuccess) st = as_from_cuda(e);
+  }
+  if (st == AS_OK) {
+    as_status ds = sync_status(h);
+    if (ds != AS_OK) st = ds;
+  }
+  cudaFree(lam); cudaFree(V); cudaFree(w); cudaFree(o);
+  return st;
+}
+
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a{};
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
@@ -636,6 +668,59 @@ bool is_device_ptr(const void* p) {
 }
 
 }  // namespace
+
+// ---- library-internal access for the runtimes built on sketches (sliding.cu)
+namespace as {
+
+cudaStream_t sk_stream(const as_sketch* h) { return h->s; }
+int64_t sk_rows(const as_sketch* h) { return h->T; }
+int sk_snap_count(const as_sketch* h) { return (int)h->snaps.size(); }
+int64_t sk_snap_t(const as_sketch* h, int k) { return h->snaps[(size_t)k].t; }
+
+// B = C^T C (the current residual) + the snapshot terms with t > lb (the
+// sketch's own row times), on the sketch's stream; B is d x d FP64 device.
+as_status sk_window_gram(as_sketch* h, int64_t lb, double* B) {
+  const int d = h->d;
+  AS_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)d * d * sizeof(double), h->s));
+  as_status st = AS_OK;
+  if (h->r > 0)
+    st = gemm_strided<float, float, double>(h->s, d, d, h->r, h->C, 1, h->ldc, h->C, h->ldc, 1, B, d, 1, 1.0, 0.0);
+  if (st == AS_OK) st = add_snapshot_terms(h, INT64_MAX, B, h, h->s, lb);
+  return st;
+}
+
+// B += R^T R for the k rows of R (device FP32, row stride ld).
+as_status sk_add_rows_gram(as_sketch* h, const float* R, int k, int64_t ld, double* B) {
+  if (k <= 0) return AS_OK;
+  const int d = h->d;
+  return gemm_strided<float, float, double>(h->s, d, d, k, R, 1, ld, R, ld, 1, B, d, 1, 1.0, 1.0);
+}
+
+// Remove the `count` oldest snapshots; the arena is compacted once the dropped
+// prefix is at least as long as the live part (the copy then cannot overlap).
+as_status sk_drop_front(as_sketch* h, int count) {
+  count = std::min(count, (int)h->snaps.size());
+  if (count <= 0) return AS_OK;
+  for (int k = 0; k < count; ++k) h->st.snapshot_rank -= h->snaps[(size_t)k].xi;
+  h->snaps.erase(h->snaps.begin(), h->snaps.begin() + count);
+  if (h->snaps.empty()) {
+    h->arena_used = 0;
+    return AS_OK;
+  }
+  const size_t head = h->snaps.front().off;
+  const size_t live = h->arena_used - head;
+  if (head >= live) {
+    AS_CUDA_TRY(cudaMemcpyAsync(h->arena, h->arena + head, live * sizeof(float), cudaMemcpyDeviceToDevice, h->s));
+    for (Snap& sn : h->snaps) sn.off -= head;
+    h->arena_used = live;
+  }
+  return AS_OK;
+}
+
+as_status sk_eig_shrink(as_sketch* h, double* B, float* out, int64_t ldo) { return eig_shrink_to(h, B, out, ldo); }
+
+}  // namespace as
+
 
 namespace {
 thread_local char g_last_error[192] = "";

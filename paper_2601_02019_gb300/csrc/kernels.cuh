@@ -178,6 +178,21 @@ as_status launch_umma_gemm(cudaStream_t s, const UmmaOperand& A, const UmmaOpera
 as_status launch_split_bf16(cudaStream_t s, const float* src, long long lds, int rows, int cols, __nv_bfloat16* hi,
                             __nv_bfloat16* lo, long long ldd, bool transpose, __nv_bfloat16* lo2 = nullptr);
 
+// Library-internal access to a sketch for the runtimes built on sketches
+// (engine.cu): stream, rows fed, the snapshot queue's times (the sketch's own
+// row indices), the windowed query Gram, raw-row Grams, dropping the oldest
+// snapshots, and the eigen-shrink of a device B (Algorithm 5 lines 5-7).
+cudaStream_t sk_stream(const as_sketch* h);
+int64_t sk_rows(const as_sketch* h);
+int sk_snap_count(const as_sketch* h);
+int64_t sk_snap_t(const as_sketch* h, int k);
+as_status sk_window_gram(as_sketch* h, int64_t lb, double* B);
+as_status sk_add_rows_gram(as_sketch* h, const float* R, int k, int64_t ld, double* B);
+as_status sk_drop_front(as_sketch* h, int count);
+as_status sk_eig_shrink(as_sketch* h, double* B, float* out, int64_t ldo);
+// FP64 squared norms of n rows (host or device, row stride ld) into out.
+as_status row_norms_f64(const float* rows, long long n, long long ld, int d, cudaStream_t s, double* out);
+
 // Query helpers.
 as_status launch_shrink_rows(cudaStream_t s, int d, int ell, const double* lam, const double* V, int ldv,
                              float* out, long long ldo);

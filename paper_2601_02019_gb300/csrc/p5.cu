@@ -22,7 +22,7 @@
 #include <new>
 #include <vector>
 
-#include "common.cuh"
+#include "kernels.cuh"
 
 struct as_p5 {
   int m = 0, d = 0, ell = 0;
@@ -35,68 +35,7 @@ struct as_p5 {
   double F_hat = 0.0;        // the coordinator's running sum
   int msgs = 0;
   as_p5_counters st{};
-  double* dn = nullptr;      // device row norms
-  double* hn = nullptr;      // pinned host copy
-  size_t n_cap = 0;
 };
-
-namespace {
-
-// ||row||^2 in FP64, one warp per row.
-__global__ void row_norm2_kernel(const float* rows, long long ld, long long n, int d, double* out) {
-  const long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (i >= n) return;
-  const float* r = rows + i * ld;
-  double s = 0.0;
-  for (int c = lane; c < d; c += 32) {
-    const double v = (double)r[c];
-    s += v * v;
-  }
-  s = as::warp_sum(s);
-  if (lane == 0) out[i] = s;
-}
-
-bool on_device(const void* p) {
-  cudaPointerAttributes a{};
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-as_status norms_of(as_p5* p, const float* rows, long long n, long long ld, std::vector<double>& out) {
-  out.assign((size_t)n, 0.0);
-  if (n == 0) return AS_OK;
-  if (!on_device(rows)) {
-    for (long long i = 0; i < n; ++i) {
-      double s = 0.0;
-      for (int c = 0; c < p->d; ++c) {
-        const double v = (double)rows[i * ld + c];
-        s += v * v;
-      }
-      out[(size_t)i] = s;
-    }
-    return AS_OK;
-  }
-  if ((size_t)n > p->n_cap) {
-    if (p->dn) cudaFree(p->dn);
-    if (p->hn) cudaFreeHost(p->hn);
-    p->dn = nullptr;
-    p->hn = nullptr;
-    p->n_cap = 0;
-    AS_CUDA_TRY(cudaMalloc((void**)&p->dn, (size_t)n * sizeof(double)));
-    AS_CUDA_TRY(cudaMallocHost((void**)&p->hn, (size_t)n * sizeof(double)));
-    p->n_cap = (size_t)n;
-  }
-  row_norm2_kernel<<<(unsigned)((n + 7) / 8), 256, 0, p->s>>>(rows, ld, n, p->d, p->dn);
-  as::count_launches(1);
-  AS_CUDA_TRY(cudaGetLastError());
-  AS_CUDA_TRY(cudaMemcpyAsync(p->hn, p->dn, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, p->s));
-  AS_CUDA_TRY(cudaStreamSynchronize(p->s));
-  for (long long i = 0; i < n; ++i) out[(size_t)i] = p->hn[i];
-  return AS_OK;
-}
-
-}  // namespace
 
 extern "C" {
 
@@ -104,8 +43,6 @@ as_status as_p5_destroy(as_p5* p) {
   if (!p) return AS_OK;
   for (as_sketch* h : p->sites) sketch_destroy(h);
   sketch_destroy(p->coord);
-  if (p->dn) cudaFree(p->dn);
-  if (p->hn) cudaFreeHost(p->hn);
   delete p;
   return AS_OK;
 }
@@ -151,7 +88,8 @@ as_status as_p5_round(as_p5* p, const float* const* rows, const int64_t* n, cons
     if (n[j] < 0 || (n[j] > 0 && (!rows[j] || ld[j] < p->d))) return AS_EINVAL;
   std::vector<double> pending, nrm;
   for (int j = 0; j < p->m; ++j) {
-    as_status st = norms_of(p, rows[j], n[j], ld[j], nrm);
+    nrm.assign((size_t)n[j], 0.0);
+    as_status st = as::row_norms_f64(rows[j], n[j], ld[j], p->d, p->s, nrm.data());
     if (st != AS_OK) return st;
     for (double v : nrm) {
       p->F[(size_t)j] += v;
