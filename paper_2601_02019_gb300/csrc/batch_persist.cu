@@ -34,6 +34,7 @@
 // columns 0 .. 2*npi-1 (npi = ceil(nb/2), one zero padding column when nb is
 // odd), then the pair of row t at columns 2*npi + 2t and 2*npi + 2t + 1.
 #include <algorithm>
+#include <mutex>
 
 #include "grid.cuh"
 #include "kernels.cuh"
@@ -484,6 +485,7 @@ struct PersistDevice {
   size_t attr[2] = {0, 0};         // dynamic shared memory limit set so far
 };
 PersistDevice g_pdev[64];
+std::mutex g_pdev_mu;   // guards g_pdev (sketches may run from several host threads)
 
 size_t persist_smem_bytes(bool gsmem, int mmax, int P) {
   const size_t mpad = (size_t)((mmax + 3) & ~3);
@@ -510,6 +512,7 @@ as_status launch_batch_persist(cudaStream_t s, const float* Gf, int n2, int r0, 
   int dev = 0;
   AS_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return AS_EINVAL;
+  std::unique_lock<std::mutex> plk(g_pdev_mu);
   PersistDevice& pd = g_pdev[dev];
   if (pd.sms == 0) {
     AS_CUDA_TRY(cudaDeviceGetAttribute(&pd.sms, cudaDevAttrMultiProcessorCount, dev));
@@ -553,6 +556,7 @@ as_status launch_batch_persist(cudaStream_t s, const float* Gf, int n2, int r0, 
     grid = std::min(ntiles, per * pd.sms);
   }
   grid = std::min(grid, kMaxGrid);
+  plk.unlock();
 
   if (prof) prof->begin(PK_BATCH_ORTH, s);
   persist_fill_kernel<<<dim3(nb, 2), 128, 0, s>>>(pb.Y + pb.ybuf, pb.ldy, mmax, nb, npi, r0, key, i0);

@@ -13,6 +13,8 @@
 // written earlier in the same call).  Calls whose work overlaps on the GPU
 // race with each other.  The first call on a device looks up the array's
 // device address; make that first call before any stream capture.
+#include <atomic>
+
 #include "eig.cuh"
 #include "kernels.cuh"
 
@@ -27,7 +29,7 @@ constexpr size_t kNoAllocDoubles = (size_t)kNoAllocMaxN * kNoAllocMaxN + 2 * (si
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 constexpr int kMaxDevices = 64;
-double* g_scratch_ptr[kMaxDevices] = {};   // device address of the array, per device
+std::atomic<double*> g_scratch_ptr[kMaxDevices] = {};   // device address of the array, per device
 
 }  // namespace
 
@@ -37,14 +39,14 @@ extern "C" as_status as_symeig_noalloc(int32_t n, const double* A, int32_t nev, 
   int dev = 0;
   AS_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return AS_EINVAL;
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev].load()) {
     // once per device, with that device current: the host-side name of the
     // array is only a stand-in, the kernels need its device address
     void* p = nullptr;
     AS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_scratch_ptr[dev] = (double*)p;
+    g_scratch_ptr[dev].store((double*)p);
   }
-  double* Acopy = g_scratch_ptr[dev];
+  double* Acopy = g_scratch_ptr[dev].load();
   double* work = Acopy + (size_t)kNoAllocMaxN * kNoAllocMaxN;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   AS_CUDA_TRY(cudaMemcpyAsync(Acopy, A, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s));

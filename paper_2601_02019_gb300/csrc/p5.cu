@@ -17,9 +17,13 @@
 // messages of a round reach the coordinator at the round's end in site order.
 //
 // The scalar protocol runs on the host; the rows, the snapshot terms and the
-// coordinator's query run in the library's kernels (sketch calls only).
+// coordinator's query run in the library's kernels (sketch calls only).  Each
+// site has its own stream, and a round updates the sites from several host
+// threads so that their kernels overlap on the GPU.
+#include <algorithm>
 #include <cmath>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "kernels.cuh"
@@ -29,6 +33,7 @@ struct as_p5 {
   double eps = 0.0;
   cudaStream_t s = nullptr;
   std::vector<as_sketch*> sites;
+  std::vector<cudaStream_t> ss;   // one stream per site: sites update concurrently
   as_sketch* coord = nullptr;
   std::vector<double> F;     // unsent row mass of each site
   double F_site = 0.0;       // F_hat as the sites know it (last broadcast)
@@ -43,6 +48,7 @@ as_status as_p5_destroy(as_p5* p) {
   if (!p) return AS_OK;
   for (as_sketch* h : p->sites) sketch_destroy(h);
   sketch_destroy(p->coord);
+  for (cudaStream_t s : p->ss) cudaStreamDestroy(s);
   delete p;
   return AS_OK;
 }
@@ -63,7 +69,14 @@ as_status as_p5_create(const as_config* site_cfg, int32_t m, void* cuda_stream, 
     cj.theta = INFINITY;
     cj.stream_id = site_cfg->stream_id + (uint64_t)j;
     as_sketch* h = nullptr;
-    st = sketch_create(&cj, cuda_stream, &h);
+    cudaStream_t sj = nullptr;
+    if (cudaStreamCreateWithFlags(&sj, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      st = AS_EDEVICE;
+      break;
+    }
+    p->ss.push_back(sj);
+    st = sketch_create(&cj, sj, &h);
     if (st == AS_OK) p->sites.push_back(h);
   }
   if (st == AS_OK) {
@@ -86,24 +99,37 @@ as_status as_p5_round(as_p5* p, const float* const* rows, const int64_t* n, cons
   if (!p || !rows || !n || !ld) return AS_EINVAL;
   for (int j = 0; j < p->m; ++j)
     if (n[j] < 0 || (n[j] > 0 && (!rows[j] || ld[j] < p->d))) return AS_EINVAL;
-  std::vector<double> pending, nrm;
-  for (int j = 0; j < p->m; ++j) {
-    nrm.assign((size_t)n[j], 0.0);
-    as_status st = as::row_norms_f64(rows[j], n[j], ld[j], p->d, p->s, nrm.data());
+  // the sites' rows, concurrently (one host thread and one stream per site,
+  // at most 16 threads): row norms for the protocol and the site updates
+  const int m = p->m;
+  std::vector<std::vector<double>> nrm((size_t)m);
+  std::vector<as_status> sts((size_t)m, AS_OK);
+  auto work = [&](int j) {
+    nrm[(size_t)j].assign((size_t)n[j], 0.0);
+    sts[(size_t)j] = as::row_norms_f64(rows[j], n[j], ld[j], p->d, p->ss[(size_t)j], nrm[(size_t)j].data());
+    if (sts[(size_t)j] == AS_OK && n[j] > 0) sts[(size_t)j] = sketch_update(p->sites[(size_t)j], rows[j], n[j], ld[j]);
+  };
+  const int nt = std::min(m, 16);
+  std::vector<std::thread> pool;
+  for (int w = 0; w < nt; ++w)
+    pool.emplace_back([&, w]() {
+      for (int j = w; j < m; j += nt) work(j);
+    });
+  for (std::thread& t : pool) t.join();
+  for (as_status st : sts)
     if (st != AS_OK) return st;
-    for (double v : nrm) {
+  // messages and snapshots in site order (the coordinator's sums keep a fixed order)
+  std::vector<double> pending;
+  for (int j = 0; j < m; ++j) {
+    for (double v : nrm[(size_t)j]) {
       p->F[(size_t)j] += v;
       if (p->F[(size_t)j] >= (p->eps / p->m) * p->F_site) {   // message F_j
         pending.push_back(p->F[(size_t)j]);
         p->F[(size_t)j] = 0.0;
       }
     }
-    if (n[j] > 0) {
-      st = sketch_update(p->sites[(size_t)j], rows[j], n[j], ld[j]);
-      if (st != AS_OK) return st;
-    }
     int32_t sent = 0;
-    st = sketch_send_snapshots(p->sites[(size_t)j], p->coord, &sent);
+    as_status st = sketch_send_snapshots(p->sites[(size_t)j], p->coord, &sent);
     if (st != AS_OK) return st;
     p->st.snapshots_sent += sent;
   }

@@ -17,12 +17,14 @@
 // A level's sketch computation does not depend on its queue, so a block of
 // rows runs each level's sketch over its runs of light rows first, then
 // replays the queue row by row on the host and drops the popped snapshots
-// from the front of the sketch's own queue.  A level's sketch numbers its own
+// from the front of the sketch's own queue.  Each level has its own stream
+// and is updated from its own host thread, so the levels' kernels overlap.  A level's sketch numbers its own
 // rows (the light rows it received) for its random draws.
 #include <algorithm>
 #include <cmath>
 #include <deque>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "kernels.cuh"
@@ -38,7 +40,9 @@ struct SwItem {
 
 struct SwLevel {
   as_sketch* h = nullptr;
+  cudaStream_t s = nullptr;       // the level's own stream: levels update concurrently
   double theta = 0.0;
+  int64_t popped_expired = 0, popped_cap = 0;
   std::deque<SwItem> Q;
   float* ring = nullptr;          // (cap + 2) x d raw rows
   std::vector<int> free_slots;
@@ -65,6 +69,7 @@ as_status as_sw_destroy(as_sw* w) {
   for (SwLevel& l : w->lv) {
     sketch_destroy(l.h);
     if (l.ring) cudaFree(l.ring);
+    if (l.s) cudaStreamDestroy(l.s);
   }
   if (w->B) cudaFree(w->B);
   if (w->rawtmp) cudaFree(w->rawtmp);
@@ -87,8 +92,16 @@ as_status as_sw_create(const as_config* cfg, int64_t N, double R, void* cuda_str
     c.stream_id = cfg->stream_id + (uint64_t)j;
     c.theta = 0.0;   // set below once eps is known
     SwLevel l;
-    st = sketch_create(&c, cuda_stream, &l.h);
-    if (st != AS_OK) break;
+    if (cudaStreamCreateWithFlags(&l.s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      st = AS_EDEVICE;
+      break;
+    }
+    st = sketch_create(&c, l.s, &l.h);
+    if (st != AS_OK) {
+      cudaStreamDestroy(l.s);
+      break;
+    }
     if (j == 0) {
       as_stats s0{};
       st = sketch_stats(l.h, &s0);
@@ -132,7 +145,10 @@ as_status as_sw_update(as_sw* w, const float* rows, int64_t n, int64_t ld) {
   if (st != AS_OK) return st;
   for (double v : nrm)
     if (!std::isfinite(v)) return AS_EINVAL;
-  for (SwLevel& l : w->lv) {
+  // the levels are independent: one host thread per level, each on its own stream
+  std::vector<as_status> sts(w->lv.size(), AS_OK);
+  auto level_update = [&](SwLevel& l) -> as_status {
+    as_status st2 = AS_OK;
     // the level's sketch over its runs of light rows
     const int64_t nl0 = as::sk_rows(l.h);
     const int ns0 = as::sk_snap_count(l.h);
@@ -141,8 +157,8 @@ as_status as_sw_update(as_sw* w, const float* rows, int64_t n, int64_t ld) {
       if (nrm[(size_t)t0] >= l.theta) { ++t0; continue; }
       int64_t t1 = t0;
       while (t1 < n && nrm[(size_t)t1] < l.theta) light.push_back(t1++);
-      st = sketch_update(l.h, rows + t0 * ld, t1 - t0, ld);
-      if (st != AS_OK) return st;
+      st2 = sketch_update(l.h, rows + t0 * ld, t1 - t0, ld);
+      if (st2 != AS_OK) return st2;
       t0 = t1;
     }
     std::vector<int64_t> snap_at((size_t)n, 0);   // the sketch's row index of a snapshot taken at block row t
@@ -157,7 +173,7 @@ as_status as_sw_update(as_sw* w, const float* rows, int64_t n, int64_t ld) {
       const int64_t i = w->T + 1 + t;
       while (!l.Q.empty() && ((int)l.Q.size() > w->cap || l.Q.front().t <= i - w->N)) {
         const SwItem& it = l.Q.front();
-        if (it.t <= i - w->N) w->st.popped_expired += 1; else w->st.popped_cap += 1;
+        if (it.t <= i - w->N) l.popped_expired += 1; else l.popped_cap += 1;
         if (it.kind == 0) ++drop; else l.free_slots.push_back(it.slot);
         l.Q.pop_front();
       }
@@ -166,14 +182,23 @@ as_status as_sw_update(as_sw* w, const float* rows, int64_t n, int64_t ld) {
         const int slot = l.free_slots.back();
         l.free_slots.pop_back();
         AS_CUDA_TRY(cudaMemcpyAsync(l.ring + (size_t)slot * w->d, rows + t * ld, (size_t)w->d * sizeof(float),
-                                    cudaMemcpyDefault, w->s));
+                                    cudaMemcpyDefault, l.s));
         l.Q.push_back(SwItem{s, i, 1, 0, slot});
       } else if (snap_at[(size_t)t] != 0) {
         l.Q.push_back(SwItem{s, i, 0, snap_at[(size_t)t], -1});
       }
     }
-    st = as::sk_drop_front(l.h, drop);
-    if (st != AS_OK) return st;
+    return as::sk_drop_front(l.h, drop);
+  };
+  std::vector<std::thread> pool;
+  for (size_t j = 0; j < w->lv.size(); ++j) pool.emplace_back([&, j]() { sts[j] = level_update(w->lv[j]); });
+  for (std::thread& t : pool) t.join();
+  for (as_status s2 : sts)
+    if (s2 != AS_OK) return s2;
+  w->st.popped_expired = w->st.popped_cap = 0;
+  for (const SwLevel& l : w->lv) {
+    w->st.popped_expired += l.popped_expired;
+    w->st.popped_cap += l.popped_cap;
   }
   w->T += n;
   w->st.rows = w->T;
@@ -220,7 +245,6 @@ extern "C" {
 as_status as_sw_query(as_sw* w, float* out, int64_t ldo, int32_t* rows_out, int32_t* level_out) {
   if (!w || !out || ldo < w->d) return AS_EINVAL;
   const int j = query_level(w);
-  if (w->s != as::sk_stream(w->lv[(size_t)j].h)) AS_CUDA_TRY(cudaStreamSynchronize(w->s));
   as_status st = window_gram(w, j);
   if (st == AS_OK) st = as::sk_eig_shrink(w->lv[(size_t)j].h, w->B, out, ldo);
   if (rows_out) *rows_out = (st == AS_OK) ? w->ell : 0;

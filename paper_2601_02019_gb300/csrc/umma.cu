@@ -25,6 +25,8 @@
 // *err and falls through, so a fault in the pipeline cannot hang the GPU.
 #include <cuda.h>
 
+#include <atomic>
+
 #include "kernels.cuh"
 
 namespace as {
@@ -309,18 +311,16 @@ using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, voi
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeFn encode_fn() {
-  static EncodeFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once; a function-local static is initialised thread-safely
+  static const EncodeFn fn = []() -> EncodeFn {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeFn)p;
-    else
-      cudaGetLastError();
-  }
+      return (EncodeFn)p;
+    cudaGetLastError();
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -333,13 +333,13 @@ as_status launch_umma_t(cudaStream_t s, const UmmaOperand& A, const UmmaOperand&
   S = (K + klen - 1) / klen;
   dim3 grid((M + UM - 1) / UM, (N + BN - 1) / BN, S);
   const size_t smem = (size_t)STAGES * (UM * UK * 2 + BN * UK * 2) + 1024;
-  static int configured_device = -1;   // the attribute is per device; set it once
+  static std::atomic<int> configured_device{-1};   // the attribute is per device; set it once
   int dev = 0;
   AS_CUDA_TRY(cudaGetDevice(&dev));
-  if (configured_device != dev) {
+  if (configured_device.load() != dev) {   // setting it twice from two threads is harmless
     AS_CUDA_TRY(cudaFuncSetAttribute(umma_gemm_kernel<BN, NPASS, PRECISE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-    configured_device = dev;
+    configured_device.store(dev);
   }
   umma_gemm_kernel<BN, NPASS, PRECISE><<<grid, 128, smem, s>>>(A, B, M, N, K, klen, b_row0, out, som, son, plane, err); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
