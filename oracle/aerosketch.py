@@ -43,6 +43,10 @@ the design notes of the repository):
      largest magnitude of u_j (the left singular vector, a 2l-vector) is
      positive, the lowest index winning exact ties.
  R11 The current-time query (lb = 0, ub = T) includes C_T (Algorithm 5 line 1).
+ R17 Probability amplification (Algorithm 7, optional: delta): r and s are
+     rounded up; SI h of the r draws its test matrix at sub-index
+     j + 64 (h - 1) (h = 1 is the plain draw), estimate g of SI h its start
+     vector at sub-index 64 h + g; the first minimum of the estimates wins.
  R12 A historical query ub = t < T (Algorithm 8's Query(t) = Query(0, t)) has
      no residual C_t to add (it is not stored); B is the sum of the snapshot
      terms with t_j <= t, as in B_i of the ATTP error analysis.
@@ -126,7 +130,7 @@ class AeroSketch:
                  q: int | None = None, theta_mode: str = "attp",
                  theta_fixed: float | None = None, replay: dict | None = None,
                  tie_rel: float = 1e-4, track_delta: bool = False,
-                 check_restore: bool = False):
+                 check_restore: bool = False, delta: float | None = None):
         if not (1 <= ell and 2 * ell <= d):
             raise ValueError("needs 1 <= l <= d/2")
         self.d, self.ell = d, ell
@@ -152,6 +156,15 @@ class AeroSketch:
         self.delta_sum = np.zeros((d, d)) if track_delta else None
         self.check_restore = check_restore
         self.restore_err = 0.0
+        # Algorithm 7 (probability amplification), R17: r = ceil(log_100(2/delta))
+        # simultaneous iterations with eps_SI = 0.2, s = ceil(2 log_3(2/delta))
+        # power-iteration estimates of each residual's top eigenvalue
+        self.delta = delta
+        if delta is not None:
+            self.amp_r = max(1, int(math.ceil(math.log(2.0 / delta) / math.log(100.0))))
+            self.amp_s = max(1, int(math.ceil(2.0 * math.log(2.0 / delta) / math.log(3.0))))
+            self.q_amp = default_q(d, 0.2)
+        self.amp_choices: list[tuple[int, int, list[float], int]] = []   # (i, j, c_h, chosen h)
 
     # -- decisions, with optional replay of another run's choices at ties -----
     def _decide(self, own: bool, value: float, thr: float, kind: str, i: int, other):
@@ -226,9 +239,12 @@ class AeroSketch:
         jmax = int(math.ceil(math.log2(min(ell, self.d)))) if min(ell, self.d) > 1 else 0
         for j in range(1, jmax + 1):                              # line 9
             k = min(2 ** j, ell, self.d)                          # line 10
-            Pi = philox.gaussians(self.seed, self.stream_id, philox.PURPOSE_SI_TEST,
-                                  i, j, 2 * ell * k).reshape(2 * ell, k)
-            Zp, s2 = simul_iter(Cp.T, self.q, Pi)                 # line 11
+            if self.delta is None:
+                Pi = philox.gaussians(self.seed, self.stream_id, philox.PURPOSE_SI_TEST,
+                                      i, j, 2 * ell * k).reshape(2 * ell, k)
+                Zp, s2 = simul_iter(Cp.T, self.q, Pi)             # line 11
+            else:
+                Zp, s2 = self._amplified_si(Cp, k, i, j, theta)   # Algorithm 7 in place of line 11
             ev.ritz.append(s2.copy())
             own_stop = s2[k - 1] < theta                          # line 12
             stop = self._decide(own_stop, s2[k - 1], theta, "stop", i,
@@ -261,6 +277,44 @@ class AeroSketch:
                 self.C = Cnew
             return                                                # line 17
         # loop ended without break: C_i <- C'_i (R8)
+
+    def _amplified_si(self, Cp: np.ndarray, k: int, i: int, j: int, theta: float):
+        """Algorithm 7: r simultaneous iterations; keep the one whose residual
+        C' - C' Z_h Z_h^T has the smallest estimated top eigenvalue (the
+        maximum of s power iterations).  R17: SI h draws Pi at sub-index
+        j + 64 (h-1); estimate g of SI h draws x^(0) at sub-index 64 h + g."""
+        ell = self.ell
+        best = None
+        cs = []
+        for h in range(1, self.amp_r + 1):
+            Pi = philox.gaussians(self.seed, self.stream_id, philox.PURPOSE_SI_TEST,
+                                  i, j + 64 * (h - 1), 2 * ell * k).reshape(2 * ell, k)
+            Zh, s2h = simul_iter(Cp.T, self.q_amp, Pi)
+            xi_h = int(np.sum((s2h >= theta) & (s2h > 0.0)))
+            Zx = Zh[:, :xi_h]
+            R = Cp - (Cp @ Zx) @ Zx.T
+            ch = 0.0
+            for g in range(1, self.amp_s + 1):
+                x0 = philox.gaussians(self.seed, self.stream_id, philox.PURPOSE_PI_START, i, 64 * h + g, 2 * ell)
+                c2, _ = power_iteration(R.T, self.k_pi, x0)
+                ch = max(ch, c2)
+            cs.append(ch)
+            if best is None or ch < best[0]:
+                best = (ch, h, Zh, s2h)
+        h_star = best[1]
+        other = None if self.replay is None else self.replay.get(("amp", i, j))
+        if other is not None and other != h_star:
+            # adopt the other run's choice only when the two estimates tie
+            c_o, c_b = cs[other - 1], cs[h_star - 1]
+            if abs(c_o - c_b) <= self.tie_rel * max(c_o, c_b):
+                self.replayed += 1
+                h_star = other
+            else:
+                self.mismatches.append(("amp", i, j, h_star, other))
+        self.amp_choices.append((i, j, cs, h_star))
+        Pi = philox.gaussians(self.seed, self.stream_id, philox.PURPOSE_SI_TEST,
+                              i, j + 64 * (h_star - 1), 2 * ell * k).reshape(2 * ell, k)
+        return simul_iter(Cp.T, self.q_amp, Pi)
 
     def load_state(self, C: np.ndarray, r: int, F: float, T: int) -> "AeroSketch":
         """Start from a given buffer (rows >= r zero), ||A_T||_F^2 and time T,
