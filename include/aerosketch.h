@@ -98,6 +98,14 @@ typedef struct {
   uint64_t stream_id; /* Philox key word 1 */
   uint32_t flags;     /* AS_TRACE_DECISIONS */
   uint32_t reserved;
+  double delta;       /* probability amplification (Algorithm 7): 0 = off, else the
+                         failure probability delta in (0, 1): at every doubling step
+                         r = ceil(log_100(2/delta)) simultaneous iterations with
+                         eps_SI = 0.2 are run and the one whose residual has the smallest
+                         maximum of s = ceil(2 log_3(2/delta)) power-iteration estimates
+                         is kept; SI h draws its test matrix at Philox sub-index
+                         j + 64 (h-1), estimate g of SI h its start vector at 64 h + g.
+                         Every row whose gate passes takes the FP64 single-row path. */
 } as_config;
 
 typedef struct {
@@ -139,6 +147,9 @@ typedef struct {
   int32_t xi;       /* components dumped (Algorithm 4 line 13) */
   double ritz_k;    /* sigma_hat_k^2 at the stopping step (or the last one) */
   double ritz_1;    /* sigma_hat_1^2 at that step */
+  uint64_t amp_choice; /* with probability amplification: the simultaneous
+                          iteration kept at doubling step j (1-based, 0 = none)
+                          in bits 4(j-1) .. 4(j-1)+3 */
 } as_event;
 
 /* Create a sketch (Algorithm 3, and Algorithm 8's Initialize for

@@ -47,6 +47,8 @@ the design notes of the repository):
      rounded up; SI h of the r draws its test matrix at sub-index
      j + 64 (h - 1) (h = 1 is the plain draw), estimate g of SI h its start
      vector at sub-index 64 h + g; the first minimum of the estimates wins.
+     Estimates below tie_rel * theta are rounding noise of a zero residual:
+     when replaying another run, any SI among them is a valid minimiser.
  R12 A historical query ub = t < T (Algorithm 8's Query(t) = Query(0, t)) has
      no residual C_t to add (it is not stored); B is the sum of the snapshot
      terms with t_j <= t, as in B_i of the ATTP error analysis.
@@ -304,9 +306,12 @@ class AeroSketch:
         h_star = best[1]
         other = None if self.replay is None else self.replay.get(("amp", i, j))
         if other is not None and other != h_star:
-            # adopt the other run's choice only when the two estimates tie
+            # adopt the other run's choice only when the two estimates tie:
+            # within tie_rel of the larger, or both at the rounding level of
+            # a residual that is zero (below tie_rel * theta, every such SI
+            # is a minimiser)
             c_o, c_b = cs[other - 1], cs[h_star - 1]
-            if abs(c_o - c_b) <= self.tie_rel * max(c_o, c_b):
+            if abs(c_o - c_b) <= self.tie_rel * max(c_o, c_b, theta):
                 self.replayed += 1
                 h_star = other
             else:

@@ -29,7 +29,7 @@ class AsConfig(ct.Structure):
     _fields_ = [("d", ct.c_int32), ("ell", ct.c_int32), ("eps", ct.c_double), ("mode", ct.c_int32),
                 ("prec", ct.c_int32), ("theta", ct.c_double), ("eps_si", ct.c_double), ("k_pi", ct.c_int32),
                 ("q_si", ct.c_int32), ("seed", ct.c_uint64), ("stream_id", ct.c_uint64), ("flags", ct.c_uint32),
-                ("reserved", ct.c_uint32)]
+                ("reserved", ct.c_uint32), ("delta", ct.c_double)]
 
 
 class AsStats(ct.Structure):
@@ -57,7 +57,8 @@ class AsSwCounters(ct.Structure):
 
 class AsEvent(ct.Structure):
     _fields_ = [("i", ct.c_int64), ("sig2_pi", ct.c_double), ("theta", ct.c_double), ("j_stop", ct.c_int32),
-                ("xi", ct.c_int32), ("ritz_k", ct.c_double), ("ritz_1", ct.c_double)]
+                ("xi", ct.c_int32), ("ritz_k", ct.c_double), ("ritz_1", ct.c_double),
+                ("amp_choice", ct.c_uint64)]
 
 
 class AsKernelStat(ct.Structure):
@@ -152,11 +153,11 @@ class Sketch:
     def __init__(self, d: int, ell: int = 0, eps: float = 0.0, *, mode: int = AS_PERSISTENT,
                  prec: int = AS_FP32_PLAIN, theta: float = 0.0, eps_si: float = 0.0, k_pi: int = 0,
                  q_si: int = 0, seed: int = 0, stream_id: int = 0, trace: bool = False, profile: bool = False,
-                 stream=None):
+                 delta: float = 0.0, stream=None):
         L = lib()
         flags = (AS_TRACE_DECISIONS if trace else 0) | (AS_PROFILE if profile else 0)
         cfg = AsConfig(d=d, ell=ell, eps=eps, mode=mode, prec=prec, theta=theta, eps_si=eps_si, k_pi=k_pi,
-                       q_si=q_si, seed=seed, stream_id=stream_id, flags=flags)
+                       q_si=q_si, seed=seed, stream_id=stream_id, flags=flags, delta=delta)
         h = ct.c_void_p()
         sp = None if stream is None else ct.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         _check(L.sketch_create(ct.byref(cfg), sp, ct.byref(h)), "sketch_create")
@@ -342,9 +343,19 @@ def tc_gemm(A: np.ndarray, B: np.ndarray, npass: int = 3, splits: int = 1) -> np
 
 def replay_from_trace(events: list[dict]) -> dict:
     """Decision record in the oracle's replay format (rows whose gate passed,
-    and the doubling step and xi of each)."""
-    return {"fired": {int(e["i"]) for e in events},
-            "si": {int(e["i"]): (int(e["j_stop"]), int(e["xi"])) for e in events}}
+    the doubling step and xi of each, and with probability amplification the
+    simultaneous iteration kept at each doubling step, keyed ("amp", i, j))."""
+    rec = {"fired": {int(e["i"]) for e in events},
+           "si": {int(e["i"]): (int(e["j_stop"]), int(e["xi"])) for e in events}}
+    for e in events:
+        c = int(e.get("amp_choice", 0))
+        j = 1
+        while c:
+            if c & 15:
+                rec[("amp", int(e["i"]), j)] = c & 15
+            c >>= 4
+            j += 1
+    return rec
 
 
 def default_k_pi(d: int) -> int:

@@ -114,6 +114,7 @@ struct EventProf final : Prof {
 struct as_sketch {
   as_config cfg{};
   int d = 0, ell = 0, n2 = 0, ldc = 0, k_pi = 0, q = 0, jmax = 0, mode = 0;
+  int amp_r = 0, amp_s = 0, q_amp = 0;   // probability amplification (Algorithm 7); amp_r = 0: off
   double eps = 0, eps_si = 0, theta = 0;
   cudaStream_t s = nullptr;
   Key key{};
@@ -363,6 +364,56 @@ as_status pi_f64(as_sketch* h, int64_t i, double* sig2) {
   return AS_OK;
 }
 
+// Algorithm 2 (FP64) for row i with k columns, q products and the test matrix
+// at Philox sub-index jsub; the Ritz values land in h->h_buf[0..k).
+as_status si_f64(as_sketch* h, int64_t i, int jsub, int k, int q) {
+  as_status st = h->big ? launch_simul_iter_f64(h->s, h->G, h->n2, h->r, k, q, h->key, (uint64_t)i, jsub, h->si, h->dstatus)
+                        : launch_simul_iter(h->s, h->G, h->n2, h->r, k, q, h->key, (uint64_t)i, jsub, h->si, h->dstatus);
+  if (st != AS_OK) return st;
+  h->st.si_runs++;
+  return fetch(h, h->si.ritz, k);
+}
+
+// Algorithm 7 in place of Algorithm 4 line 11 (doubling step j, k columns):
+// amp_r simultaneous iterations with eps_SI = 0.2, SI h drawing its test matrix
+// at sub-index j + 64 (h-1); each is scored by the largest of amp_s power-
+// iteration estimates (start vectors at sub-index 64 h + g) of the top
+// eigenvalue of its residual C' - C' Z_h Z_h^T, whose Gram G - (G WU)(G WU)^T
+// is formed in Gtmp (Z_h restricted to its xi_h columns at or above theta).
+// The first minimum is kept; its WU, GWU and Ritz values are left in h->si and
+// h->h_buf.  *chosen = the kept h.
+as_status amplified_si(as_sketch* h, int64_t i, int j, int k, double theta, int* chosen) {
+  double best = 0.0;
+  int hbest = 0;
+  for (int hh = 1; hh <= h->amp_r; ++hh) {
+    as_status st = si_f64(h, i, j + 64 * (hh - 1), k, h->q_amp);
+    if (st != AS_OK) return st;
+    int xi = 0;
+    for (int c = 0; c < k; ++c)
+      if (h->h_buf[c] >= theta && h->h_buf[c] > 0.0) ++xi;
+    st = launch_residual_gram(h->s, h->G, h->n2, h->r, h->si.GWU, k, xi, h->Gtmp);
+    for (int g = 1; g <= h->amp_s && st == AS_OK; ++g) {
+      const uint64_t jsub = 64 * (uint64_t)hh + (uint64_t)g;
+      st = h->big ? launch_power_iteration_f64(h->s, h->Gtmp, h->n2, h->r, h->k_pi, h->key, (uint64_t)i, h->x64,
+                                               h->y64, h->zero, h->scal + (g - 1), jsub)
+                  : launch_power_iteration(h->s, h->Gtmp, h->n2, h->r, h->k_pi, h->key, (uint64_t)i,
+                                           h->scal + (g - 1), jsub);
+    }
+    if (st == AS_OK) st = fetch(h, h->scal, h->amp_s);
+    if (st != AS_OK) return st;
+    double ch = 0.0;
+    for (int g = 0; g < h->amp_s; ++g) ch = std::max(ch, h->h_buf[g]);
+    if (hbest == 0 || ch < best) {
+      best = ch;
+      hbest = hh;
+    }
+  }
+  *chosen = hbest;
+  // the last SI's buffers are the kept ones unless an earlier h won
+  if (hbest == h->amp_r) return fetch(h, h->si.ritz, k);
+  return si_f64(h, i, j + 64 * (hbest - 1), k, h->q_amp);
+}
+
 // Algorithm 4 lines 7-17 for row i on the current state, in FP64.  When the
 // gate outcome is already known (from the batched pass, outside its tie band)
 // it is passed in and the power iteration is not repeated.
@@ -382,16 +433,18 @@ as_status finish_row(as_sketch* h, int64_t i, double theta, int known_gate, doub
   ev.theta = theta;
   for (int j = 1; j <= h->jmax; ++j) {              // line 9
     const int k = std::min(std::min(1 << std::min(j, 30), h->ell), h->d);  // line 10
-    if (j == 1 && k == 2 && batch_col >= 0)       // iterated basis from the batched pass
+    if (h->amp_r > 0) {                             // Algorithm 7 in place of line 11
+      int hk = 0;
+      st = amplified_si(h, i, j, k, theta, &hk);
+      if (st == AS_OK && j <= 16) ev.amp_choice |= (uint64_t)hk << (4 * (j - 1));
+    } else if (j == 1 && k == 2 && batch_col >= 0) {  // iterated basis from the batched pass
       st = launch_si_rr_from_batch(h->s, h->G, h->n2, h->r, h->pb.X, batch_col, h->si, h->dstatus);
-    else if (h->big)
-      st = launch_simul_iter_f64(h->s, h->G, h->n2, h->r, k, h->q, h->key, (uint64_t)i, j, h->si, h->dstatus);
-    else
-      st = launch_simul_iter(h->s, h->G, h->n2, h->r, k, h->q, h->key, (uint64_t)i, j, h->si, h->dstatus);
-    if (st != AS_OK) return st;                     // line 11
-    st = fetch(h, h->si.ritz, k);
+      if (st == AS_OK) st = fetch(h, h->si.ritz, k);
+      h->st.si_runs++;
+    } else {
+      st = si_f64(h, i, j, k, h->q);                // line 11
+    }
     if (st != AS_OK) return st;
-    h->st.si_runs++;
     const double* ritz = h->h_buf;
     ev.ritz_1 = ritz[0];
     ev.ritz_k = ritz[k - 1];
@@ -508,7 +561,7 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
     const bool gate = s2 >= theta / 2.0 && s2 > 0.0;
     if (!gate) continue;
     const double r1 = ritz[2 * (size_t)t];
-    if (r1 >= theta * (1.0 - kTieBand)) {  // a dump is possible: finish this row in FP64
+    if (r1 >= theta * (1.0 - kTieBand) || h->amp_r > 0) {  // a dump is possible (amplified: always)
       tstar = t;
       gate_known = 1;
       sig2_star = s2;
@@ -554,7 +607,7 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
     return finish_row(h, h->T, h->theta, -1, 0.0);
   }
   // large buffers reuse the batch's FP32-iterated basis for the k = 2 step
-  const int bcol = h->big ? batch_si_col(nbb, tstar) : -1;
+  const int bcol = (h->big && h->amp_r == 0) ? batch_si_col(nbb, tstar) : -1;
   if (h->prof) h->prof->begin(PK_EVENT, h->s);
   st = finish_row(h, h->T, h->theta, gate_known, sig2_star, bcol, 3 * nbb);
   if (h->prof) h->prof->end(PK_EVENT, h->s, 0.0, 0.0);
@@ -773,6 +826,17 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   if (c.k_pi < 0 || c.q_si < 0) return AS_EINVAL;
   if (c.k_pi == 0) c.k_pi = ceil_log2(c.d) + 1;                              // Corollary 1
   if (c.q_si == 0) c.q_si = (int32_t)std::ceil(std::log((double)c.d) / c.eps_si);  // Theta(log d / eps_SI)
+  // Algorithm 7: r = ceil(log_100(2/delta)) SIs, s = ceil(2 log_3(2/delta))
+  // estimates each; r <= 15 and s <= 63 keep the trace's 4-bit choices and the
+  // Philox sub-indices 64 h + g of the estimates distinct
+  int amp_r = 0, amp_s = 0;
+  if (c.delta != 0.0) {
+    if (!(c.delta > 0.0 && c.delta < 1.0)) return AS_EINVAL;
+    const double lg = std::log(2.0 / c.delta);
+    amp_r = std::max(1, (int)std::ceil(lg / std::log(100.0)));
+    amp_s = std::max(1, (int)std::ceil(2.0 * lg / std::log(3.0)));
+    if (amp_r > 15 || amp_s > 63) return AS_EINVAL;
+  }
 
   as_sketch* h = new (std::nothrow) as_sketch();
   if (!h) return AS_ENOMEM;
@@ -785,6 +849,9 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   h->eps_si = c.eps_si;
   h->k_pi = c.k_pi;
   h->q = c.q_si;
+  h->amp_r = amp_r;
+  h->amp_s = amp_s;
+  h->q_amp = (int)std::ceil(std::log((double)c.d) / 0.2);
   h->mode = c.mode;
   h->theta = (c.mode == AS_FIXED_THETA || c.mode == AS_SITE) ? c.theta : 0.0;
   const int mn = std::min(c.ell, c.d);

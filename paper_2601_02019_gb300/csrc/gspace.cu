@@ -70,19 +70,19 @@ __global__ void mirror_kernel(double* G, int n2, int r, int b) {
 
 // ---------------------------------------------------------- power iteration --
 // One block; x and y live in shared memory (2 * n2 doubles).
-__global__ void power_iteration_kernel(const double* __restrict__ G, int n2, int m, int k_pi, Key key,
+__global__ void power_iteration_kernel(const double* __restrict__ G, int n2, int m, int k_pi, Key key, uint64_t jsub,
                                        uint64_t i, double* sig2) {
   extern __shared__ double sm[];
   double* x = sm;
   double* y = sm + n2;
   __shared__ double red[32];
   const int tid = threadIdx.x, nt = blockDim.x;
-  // x^(0) ~ N(0, I_{2l}) (Philox purpose 3, (i, 0)); entries of empty rows do
+  // x^(0) ~ N(0, I_{2l}) (Philox purpose 3, (i, jsub)); entries of empty rows do
   // not reach G x, so only the first m are kept (the normalisation of x^(0)
   // does not change the direction of G x^(0)).
   for (int blk = tid; blk * 4 < n2; blk += nt) {
     double z[4];
-    gauss4(key, kPurposePiStart, i, 0, blk, z);
+    gauss4(key, kPurposePiStart, i, jsub, blk, z);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const int e = blk * 4 + l;
@@ -340,10 +340,10 @@ as_status launch_gram_rows(cudaStream_t s, const float* C, int ldc, int d, int r
 }
 
 as_status launch_power_iteration(cudaStream_t s, const double* G, int n2, int m, int k_pi, Key key, uint64_t i,
-                                 double* sig2) {
+                                 double* sig2, uint64_t jsub) {
   const size_t smem = 2 * (size_t)n2 * sizeof(double);
   AS_CUDA_TRY(cudaFuncSetAttribute(power_iteration_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  power_iteration_kernel<<<1, 512, smem, s>>>(G, n2, m, k_pi, key, i, sig2); count_launches(1);
+  power_iteration_kernel<<<1, 512, smem, s>>>(G, n2, m, k_pi, key, jsub, i, sig2); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }

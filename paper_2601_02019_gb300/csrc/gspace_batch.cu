@@ -35,10 +35,10 @@ __global__ void mirror_strip_kernel(const double* G, float* Gf, int n2, int vali
 }
 
 // ---- FP64 single-row path (any buffer size) ---------------------------------
-__global__ void fill_pi_start(double* x, int n2, int m, Key key, uint64_t i) {
+__global__ void fill_pi_start(double* x, int n2, int m, Key key, uint64_t i, uint64_t jsub) {
   for (int blk = blockIdx.x * blockDim.x + threadIdx.x; blk * 4 < n2; blk += gridDim.x * blockDim.x) {
     double z[4];
-    gauss4(key, kPurposePiStart, i, 0, blk, z);
+    gauss4(key, kPurposePiStart, i, jsub, blk, z);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const int p = blk * 4 + l;
@@ -323,6 +323,17 @@ __global__ void residual_kernel(float* C, int ldc, int d, int r, const float* __
   C[(size_t)p * ldc + c] = v;
 }
 
+// R[p][q] = G[p][q] - sum_{a < xi} GWU[p][a] GWU[q][a] for p, q < m (the Gram
+// of the residual C' - C' Z Z^T, Z the first xi columns), into R (ld n2).
+__global__ void residual_gram_kernel(const double* G, int n2, int m, const double* GWU, int k, int xi, double* R) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (q >= m || p >= m) return;
+  double acc = G[(size_t)p * n2 + q];
+  for (int a = 0; a < xi; ++a) acc -= GWU[(size_t)p * k + a] * GWU[(size_t)q * k + a];
+  R[(size_t)p * n2 + q] = acc;
+}
+
 // G[p][q] -= sum_a GWU[p][a] GWU[q][a]
 __global__ void gram_downdate_kernel(double* G, int n2, int r, const double* GWU, int k, int xi) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -360,9 +371,9 @@ static as_status gmul64(cudaStream_t s, const double* G, int n2, int m, int k, c
 }
 
 as_status launch_power_iteration_f64(cudaStream_t s, const double* G, int n2, int m, int k_pi, Key key, uint64_t i,
-                                     double* x, double* y, int* zero, double* sig2) {
+                                     double* x, double* y, int* zero, double* sig2, uint64_t jsub) {
   AS_CUDA_TRY(cudaMemsetAsync(zero, 0, sizeof(int), s));
-  fill_pi_start<<<(n2 / 4 + 255) / 256 + 1, 256, 0, s>>>(x, n2, m, key, i); count_launches(1);
+  fill_pi_start<<<(n2 / 4 + 255) / 256 + 1, 256, 0, s>>>(x, n2, m, key, i, jsub); count_launches(1);
   normalize_kernel<<<1, 512, 0, s>>>(x, x, m, zero); count_launches(1);
   for (int it = 0; it < k_pi; ++it) {
     as_status st = gmul64(s, G, n2, m, 1, x, y);
@@ -404,6 +415,14 @@ as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m
   as_status st = gmul64(s, G, n2, m, k, b.Y, b.GY);
   if (st != AS_OK) return st;
   rr2_kernel<<<1, 1024, 0, s>>>(n2, m, b.Y, b.GY, b.ritz, b.WU, b.GWU, status); count_launches(1);
+  AS_CUDA_TRY(cudaGetLastError());
+  return AS_OK;
+}
+
+as_status launch_residual_gram(cudaStream_t s, const double* G, int n2, int m, const double* GWU, int k, int xi,
+                               double* R) {
+  if (m <= 0) return AS_OK;
+  residual_gram_kernel<<<dim3((m + 255) / 256, m), 256, 0, s>>>(G, n2, m, GWU, k, xi, R); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
 }

@@ -50,7 +50,7 @@ as_status launch_gram_rows(cudaStream_t s, const float* C, int ldc, int d, int r
 // Algorithm 1 on C' via G = C' C'^T restricted to the first m rows; writes
 // sigma_hat_1^2 to *sig2.
 as_status launch_power_iteration(cudaStream_t s, const double* G, int n2, int m, int k_pi, Key key,
-                                 uint64_t i, double* sig2);
+                                 uint64_t i, double* sig2, uint64_t jsub = 0);
 
 struct SiBuffers {
   double* Y;      // n2 x kmax
@@ -154,7 +154,11 @@ as_status launch_batch_persist(cudaStream_t s, const float* Gf, int n2, int r0, 
 // FP64 single-row power iteration and simultaneous iteration built from
 // multi-block products (any buffer size).  x, y: n2 doubles; zero: 1 int.
 as_status launch_power_iteration_f64(cudaStream_t s, const double* G, int n2, int m, int k_pi, Key key,
-                                     uint64_t i, double* x, double* y, int* zero, double* sig2);
+                                     uint64_t i, double* x, double* y, int* zero, double* sig2, uint64_t jsub = 0);
+// R = G - (GWU)_xi (GWU)_xi^T on the leading m x m block (ld n2): the Gram of
+// the residual C' - C' Z Z^T (probability amplification, Algorithm 7).
+as_status launch_residual_gram(cudaStream_t s, const double* G, int n2, int m, const double* GWU, int k, int xi,
+                               double* R);
 as_status launch_simul_iter_f64(cudaStream_t s, const double* G, int n2, int m, int k, int q, Key key, uint64_t i,
                                 int j, const SiBuffers& b, int* status);
 
