@@ -286,6 +286,94 @@ as_status as_sw_level(as_sw* w, int32_t j, as_sketch** out);
 /* Destroy w and its levels.  NULL is a no-op. */
 as_status as_sw_destroy(as_sw* w);
 
+/* ---- Footprint, grouped updates and the serving runtime ------------------
+ *
+ * Many independent sketches (sessions, levels, sites) progress at once: each
+ * has its own stream, and host worker threads drive them so that their
+ * kernels overlap on the GPU.  A sketch's kernels and launch shapes depend only
+ * on its own configuration and rows, so its results are bitwise the same
+ * alone and in any mix. */
+
+/* Device bytes a sketch of configuration cfg holds once sketch_reserve(h,
+ * snapshot_rank) has run: the state sketch_create allocates, the buffers that
+ * otherwise grow on demand at their maxima, and a snapshot store for snapshots
+ * of total rank snapshot_rank (2 d floats per unit of rank: Z and Y).  With
+ * ATTP (Algorithm 8) the total snapshot rank after T rows is at most
+ * (2/eps) ln(2 ||A_T||_F^2 / (eps ||A_1||_F^2)) (the space analysis of Algorithm 8).
+ * Host arithmetic only: no allocation, no device call (AS_ENOTSUP for the tensor
+ * forms without a device).  AS_EINVAL for a bad configuration. */
+as_status sketch_footprint(const as_config* cfg, int64_t snapshot_rank, int64_t* bytes);
+
+/* Allocate now what sketch_footprint counts: the on-demand buffers at their
+ * maxima and room for snapshot_rank more units of snapshot rank.  After it, the
+ * sketch's device_bytes equals the footprint.  A larger rank later still
+ * grows the store. */
+as_status sketch_reserve(as_sketch* h, int64_t snapshot_rank);
+
+/* Update `count` sketches, sketch k with rows[k] (n[k] rows, stride ld[k], host
+ * or device), on the library's worker threads (at most 16), each sketch on
+ * its own stream.  Entries naming the same sketch run in list order.  Blocks
+ * until all are done; returns AS_OK or the status of the first failing entry
+ * in list order (the other entries still run).  The caller keeps the rows
+ * valid until the call returns. */
+as_status sketch_update_many(as_sketch* const* hs, const float* const* rows, const int64_t* n, const int64_t* ld,
+                             int32_t count);
+
+/* The serving runtime: sessions (one persistent-mode sketch each, on a stream
+ * of its own) admitted against an HBM budget by their footprint; requests
+ * (a batch of rows for one session) queued and run by worker threads with
+ * continuous batching: a free worker takes the session whose oldest pending
+ * request is the oldest, so requests of different sessions run concurrently and
+ * each session's requests run in submission order. */
+typedef struct as_server as_server;
+
+typedef struct {
+  int64_t hbm_budget;   /* bytes the sessions may hold; 0 = 90% of the device's free memory at create */
+  int32_t workers;      /* worker threads, 1..64 (0 = 16) */
+  int32_t reserved;
+} as_server_config;
+
+typedef struct {
+  int64_t sessions_open;
+  int64_t sessions_refused;   /* opens refused for the budget (AS_EBUSY) */
+  int64_t footprint_bytes;    /* the open sessions' footprints */
+  int64_t requests_done;      /* completed requests (since the last reset) */
+  int64_t requests_failed;
+  int64_t rows_done;
+  double p50_ms, p99_ms, max_ms, mean_ms;   /* latency: completion - submission, completed requests */
+  double span_s;              /* first submission to last completion since the last reset */
+} as_server_counters;
+
+as_status as_server_create(const as_server_config* cfg, as_server** out);
+/* Open a persistent-mode session (cfg->mode must be AS_PERSISTENT).  Its
+ * footprint is sketch_footprint(cfg, rank) with rank = the snapshot bound
+ * above for mass_ratio = ||A_T||_F^2 / ||A_1||_F^2 >= 1 (the caller's bound on
+ * the session's growth).  AS_EBUSY if the open sessions' footprints plus this
+ * one exceed the budget (nothing allocated); *session receives an id > 0. */
+as_status as_server_open(as_server* sv, const as_config* cfg, double mass_ratio, int64_t* session);
+/* Queue n rows (host or device, stride ld) for a session; *ticket (may be
+ * NULL) receives the request's id.  The caller keeps the rows valid until the
+ * request completes (as_server_wait or as_server_drain). */
+as_status as_server_submit(as_server* sv, int64_t session, const float* rows, int64_t n, int64_t ld,
+                           int64_t* ticket);
+/* Wait for one request; returns its status, *latency_ms (may be NULL) its
+ * completion - submission time.  A ticket can be waited on once. */
+as_status as_server_wait(as_server* sv, int64_t ticket, double* latency_ms);
+/* Wait until no request is pending or running; returns the first failure
+ * status among the requests completed since the last drain, else AS_OK. */
+as_status as_server_drain(as_server* sv);
+/* Borrowed handle of a session's sketch (owned by the server) for queries and
+ * stats; use it only while the session has no pending request. */
+as_status as_server_session(as_server* sv, int64_t session, as_sketch** out);
+/* Close a session with no pending request (AS_EBUSY otherwise), freeing its
+ * footprint. */
+as_status as_server_close(as_server* sv, int64_t session);
+as_status as_server_stats(as_server* sv, as_server_counters* out);
+/* Clear the latency record, the request counters and the span. */
+as_status as_server_reset_stats(as_server* sv);
+/* Stop the workers (after the running requests), close every session. */
+as_status as_server_destroy(as_server* sv);
+
 /* Counters and the sticky device status.  Synchronises. */
 as_status sketch_stats(as_sketch* h, as_stats* out);
 

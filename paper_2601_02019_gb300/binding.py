@@ -22,7 +22,9 @@ EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram
             "sketch_set_theta", "sketch_send_snapshots", "as_p5_create", "as_p5_round", "as_p5_query",
             "as_p5_query_gram", "as_p5_stats", "as_p5_site", "as_p5_coordinator", "as_p5_destroy",
             "as_sw_create", "as_sw_update", "as_sw_query", "as_sw_query_gram", "as_sw_stats", "as_sw_level",
-            "as_sw_destroy")
+            "as_sw_destroy", "sketch_footprint", "sketch_reserve", "sketch_update_many", "as_server_create",
+            "as_server_open", "as_server_submit", "as_server_wait", "as_server_drain", "as_server_session",
+            "as_server_close", "as_server_stats", "as_server_reset_stats", "as_server_destroy")
 
 
 class AsConfig(ct.Structure):
@@ -30,6 +32,17 @@ class AsConfig(ct.Structure):
                 ("prec", ct.c_int32), ("theta", ct.c_double), ("eps_si", ct.c_double), ("k_pi", ct.c_int32),
                 ("q_si", ct.c_int32), ("seed", ct.c_uint64), ("stream_id", ct.c_uint64), ("flags", ct.c_uint32),
                 ("reserved", ct.c_uint32), ("delta", ct.c_double)]
+
+
+class AsServerConfig(ct.Structure):
+    _fields_ = [("hbm_budget", ct.c_int64), ("workers", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class AsServerCounters(ct.Structure):
+    _fields_ = [("sessions_open", ct.c_int64), ("sessions_refused", ct.c_int64), ("footprint_bytes", ct.c_int64),
+                ("requests_done", ct.c_int64), ("requests_failed", ct.c_int64), ("rows_done", ct.c_int64),
+                ("p50_ms", ct.c_double), ("p99_ms", ct.c_double), ("max_ms", ct.c_double), ("mean_ms", ct.c_double),
+                ("span_s", ct.c_double)]
 
 
 class AsStats(ct.Structure):
@@ -120,6 +133,19 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.as_sw_stats.argtypes = [P, ct.POINTER(AsSwCounters)]
     L.as_sw_level.argtypes = [P, I32, ct.POINTER(P)]
     L.as_sw_destroy.argtypes = [P]
+    L.sketch_footprint.argtypes = [ct.POINTER(AsConfig), I64, ct.POINTER(I64)]
+    L.sketch_reserve.argtypes = [P, I64]
+    L.sketch_update_many.argtypes = [ct.POINTER(P), ct.POINTER(P), ct.POINTER(I64), ct.POINTER(I64), I32]
+    L.as_server_create.argtypes = [ct.POINTER(AsServerConfig), ct.POINTER(P)]
+    L.as_server_open.argtypes = [P, ct.POINTER(AsConfig), ct.c_double, ct.POINTER(I64)]
+    L.as_server_submit.argtypes = [P, I64, P, I64, I64, ct.POINTER(I64)]
+    L.as_server_wait.argtypes = [P, I64, ct.POINTER(ct.c_double)]
+    L.as_server_drain.argtypes = [P]
+    L.as_server_session.argtypes = [P, I64, ct.POINTER(P)]
+    L.as_server_close.argtypes = [P, I64]
+    L.as_server_stats.argtypes = [P, ct.POINTER(AsServerCounters)]
+    L.as_server_reset_stats.argtypes = [P]
+    L.as_server_destroy.argtypes = [P]
     L.as_status_str.argtypes = [ct.c_int]
     L.as_status_str.restype = ct.c_char_p
     L.as_last_error.argtypes = []
@@ -175,6 +201,11 @@ class Sketch:
             self.close()
         except Exception:
             pass
+
+    def reserve(self, snapshot_rank: int) -> None:
+        """Allocate the on-demand buffers at their maxima and room for
+        `snapshot_rank` more units of snapshot rank (sketch_reserve)."""
+        _check(lib().sketch_reserve(self._h, int(snapshot_rank)), "sketch_reserve")
 
     def update(self, rows, ld: int | None = None) -> None:
         """rows: (n, d) float32 numpy array (host) or torch tensor (host or device)."""
@@ -356,6 +387,110 @@ def replay_from_trace(events: list[dict]) -> dict:
             c >>= 4
             j += 1
     return rec
+
+
+def _row_args(rows) -> tuple[int, int, int]:
+    """(pointer, n, ld) of a float32 row block: numpy (host) or torch (host or device)."""
+    n = int(rows.shape[0])
+    if isinstance(rows, np.ndarray):
+        assert rows.dtype == np.float32 and rows.strides[1] == 4
+        ld = int(rows.strides[0] // 4) if n > 0 else int(rows.shape[1])
+    else:
+        ld = int(rows.stride(0))
+    return _ptr(rows), n, ld
+
+
+def footprint(d: int, ell: int = 0, eps: float = 0.0, *, prec: int = AS_FP32_PLAIN, snapshot_rank: int = 0,
+              delta: float = 0.0) -> int:
+    """Device bytes of a sketch after sketch_reserve(snapshot_rank) (sketch_footprint; host arithmetic)."""
+    cfg = AsConfig(d=d, ell=ell, eps=eps, mode=AS_PERSISTENT, prec=prec, delta=delta)
+    b = ct.c_int64()
+    _check(lib().sketch_footprint(ct.byref(cfg), int(snapshot_rank), ct.byref(b)), "sketch_footprint")
+    return b.value
+
+
+def update_many(sketches: list, blocks: list) -> None:
+    """sketch_update_many: sketch k gets blocks[k]; the sketches run concurrently
+    on the library's worker threads, each on its own stream."""
+    assert len(sketches) == len(blocks)
+    k = len(sketches)
+    hs = (ct.c_void_p * max(1, k))(*[s._h.value for s in sketches])
+    args = [_row_args(b) for b in blocks]
+    rp = (ct.c_void_p * max(1, k))(*[a[0] for a in args])
+    ns = (ct.c_int64 * max(1, k))(*[a[1] for a in args])
+    lds = (ct.c_int64 * max(1, k))(*[a[2] for a in args])
+    _check(lib().sketch_update_many(hs, rp, ns, lds, k), "sketch_update_many")
+
+
+class Server:
+    """The serving runtime (C ABI as_server): sessions admitted against an HBM
+    budget by their footprint, requests run with continuous batching."""
+
+    def __init__(self, hbm_budget: int = 0, workers: int = 0):
+        cfg = AsServerConfig(hbm_budget=int(hbm_budget), workers=int(workers))
+        h = ct.c_void_p()
+        _check(lib().as_server_create(ct.byref(cfg), ct.byref(h)), "as_server_create")
+        self._h = h
+        self._keep: dict[int, object] = {}   # rows of pending requests, kept alive until completion
+        self._dims: dict[int, int] = {}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().as_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def open(self, d: int, ell: int = 0, eps: float = 0.0, *, mass_ratio: float = 1e6, prec: int = AS_FP32_PLAIN,
+             seed: int = 0, stream_id: int = 0, trace: bool = False) -> int:
+        """A persistent-mode session; raises AeroSketchError(AS_EBUSY) when the budget refuses it."""
+        cfg = AsConfig(d=d, ell=ell, eps=eps, mode=AS_PERSISTENT, prec=prec, seed=seed, stream_id=stream_id,
+                       flags=AS_TRACE_DECISIONS if trace else 0)
+        sid = ct.c_int64()
+        _check(lib().as_server_open(self._h, ct.byref(cfg), float(mass_ratio), ct.byref(sid)), "as_server_open")
+        self._dims[sid.value] = d
+        return sid.value
+
+    def submit(self, session: int, rows) -> int:
+        p, n, ld = _row_args(rows)
+        t = ct.c_int64()
+        _check(lib().as_server_submit(self._h, int(session), ct.c_void_p(p), n, ld, ct.byref(t)), "as_server_submit")
+        self._keep[t.value] = rows
+        return t.value
+
+    def wait(self, ticket: int) -> float:
+        lat = ct.c_double()
+        code = lib().as_server_wait(self._h, int(ticket), ct.byref(lat))
+        self._keep.pop(ticket, None)
+        _check(code, "as_server_wait")
+        return lat.value
+
+    def drain(self) -> None:
+        code = lib().as_server_drain(self._h)
+        self._keep.clear()
+        _check(code, "as_server_drain")
+
+    def sketch(self, session: int) -> "Sketch":
+        h = ct.c_void_p()
+        _check(lib().as_server_session(self._h, int(session), ct.byref(h)), "as_server_session")
+        return _Borrowed(h, self._dims[session], self)
+
+    def close_session(self, session: int) -> None:
+        _check(lib().as_server_close(self._h, int(session)), "as_server_close")
+        self._dims.pop(session, None)
+
+    def stats(self) -> dict:
+        c = AsServerCounters()
+        _check(lib().as_server_stats(self._h, ct.byref(c)), "as_server_stats")
+        return {f: getattr(c, f) for f, _ in AsServerCounters._fields_}
+
+    def reset_stats(self) -> None:
+        _check(lib().as_server_reset_stats(self._h), "as_server_reset_stats")
 
 
 def default_k_pi(d: int) -> int:

@@ -9,6 +9,10 @@
 
 // Records a failed CUDA call (error name, file, line) for as_last_error().
 void as_note_cuda_error(cudaError_t e, const char* file, int line);
+// Raise a kernel's dynamic shared memory limit on the current device to at
+// least `bytes`; it is never lowered, so a launch on another host thread that
+// needs less still fits (setting the attribute per launch would race).
+cudaError_t as_raise_smem_limit(const void* fn, size_t bytes);
 
 #define AS_CUDA_TRY(expr)                                   \
   do {                                                      \

@@ -583,7 +583,7 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
     AS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = std::max(1, std::min(sms, nparts_max));
     const size_t smem = 3 * (size_t)n * sizeof(df64);
-    AS_CUDA_TRY(cudaFuncSetAttribute(tri_persist_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AS_CUDA_TRY(as_raise_smem_limit((const void*)tri_persist_df, smem));
     int per = 0;
     AS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tri_persist_df, kTriThreads, smem));
     if ((long long)per * sms < grid) return AS_ENOTSUP;
@@ -610,7 +610,7 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
   if (prof) prof->end(PK_EIG_SOLVE, s, 0.0, 0.0);
   if (prof) prof->begin(PK_EIG_BACK, s);
   const size_t smem3 = (size_t)n * kSlab * sizeof(df64);
-  AS_CUDA_TRY(cudaFuncSetAttribute(back_transform_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+  AS_CUDA_TRY(as_raise_smem_limit((const void*)back_transform_df, smem3));
   back_transform_df<<<(nev + kSlab - 1) / kSlab, 256, smem3, s>>>(Ad, lda, n, nev, X, ldx); count_launches(1);
   if (prof) prof->end(PK_EIG_BACK, s, 2.0 * (double)n * n * nev, 8.0 * (double)n * n);
   AS_CUDA_TRY(cudaGetLastError());

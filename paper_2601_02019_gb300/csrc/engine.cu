@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -115,6 +116,7 @@ struct as_sketch {
   as_config cfg{};
   int d = 0, ell = 0, n2 = 0, ldc = 0, k_pi = 0, q = 0, jmax = 0, mode = 0;
   int amp_r = 0, amp_s = 0, q_amp = 0;   // probability amplification (Algorithm 7); amp_r = 0: off
+  int dev = 0;                           // the CUDA device the state lives on
   double eps = 0, eps_si = 0, theta = 0;
   cudaStream_t s = nullptr;
   Key key{};
@@ -199,10 +201,13 @@ as_status fetch(as_sketch* h, const double* src, int n) {
   return AS_OK;
 }
 
-as_status arena_reserve(as_sketch* h, size_t extra) {
+// Room for `extra` more floats in the snapshot store: the capacity doubles
+// (from 8 d l floats), or with exact = true grows to exactly what is needed.
+as_status arena_reserve(as_sketch* h, size_t extra, bool exact = false) {
   if (h->arena_used + extra <= h->arena_cap) return AS_OK;
   size_t cap = h->arena_cap ? h->arena_cap : (size_t)8 * h->d * h->ell;
   while (cap < h->arena_used + extra) cap *= 2;
+  if (exact) cap = h->arena_used + extra;
   float* na = nullptr;
   as_status st = dalloc(&na, cap);
   if (st != AS_OK) return st;
@@ -234,9 +239,13 @@ as_status ensure_prb(as_sketch* h, size_t need) {
   if (need <= h->prb_cap) return AS_OK;
   if (h->Prb) cudaFree(h->Prb);
   h->Prb = nullptr;
+  h->dev_bytes -= h->prb_cap * sizeof(float);
   h->prb_cap = 0;
   as_status st = dalloc(&h->Prb, need);
-  if (st == AS_OK) h->prb_cap = need;
+  if (st == AS_OK) {
+    h->dev_bytes += (need - h->prb_cap) * sizeof(float);
+    h->prb_cap = need;
+  }
   return st;
 }
 
@@ -323,6 +332,28 @@ as_status fd_shrink(as_sketch* h) {
   return AS_OK;
 }
 
+as_status ensure_dwork(as_sketch* h, size_t need) {
+  if (need <= h->dwork_cap) return AS_OK;
+  if (h->dwork) cudaFree(h->dwork);
+  h->dwork = nullptr;
+  h->dev_bytes -= h->dwork_cap * sizeof(double);
+  h->dwork_cap = 0;
+  as_status st = dalloc(&h->dwork, need);
+  if (st != AS_OK) return st;
+  h->dev_bytes += need * sizeof(double);
+  h->dwork_cap = need;
+  return AS_OK;
+}
+
+// Largest sizes of the buffers that grow on demand: the dump work (xi <= l)
+// and, for the tensor-core forms, the split-K planes of the Gram rows (at most
+// ldc/64 planes of bmax x 2l) and of the FD rebuild (n2p/64 planes of (l-1) x d).
+size_t dwork_max(const as_sketch* h) { return dump_work_doubles(h->d, h->n2, h->ell); }
+size_t prb_max(const as_sketch* h) {
+  if (!h->tc) return 0;
+  return std::max((size_t)(h->ldc / 64) * h->bmax * h->n2, (size_t)(h->n2p / 64) * (h->ell - 1) * h->d);
+}
+
 // Algorithm 4 lines 14-16 for the first xi columns of the last SI (k columns).
 as_status dump(as_sketch* h, int xi, int k, int64_t i) {
   const int d = h->d, r = h->r, ldc = h->ldc, n2 = h->n2;
@@ -330,15 +361,8 @@ as_status dump(as_sketch* h, int xi, int k, int64_t i) {
   if (st != AS_OK) return st;
   float* Z = h->arena + h->arena_used;
   float* Y = Z + (size_t)d * xi;
-  const size_t need = dump_work_doubles(d, n2, xi);
-  if (need > h->dwork_cap) {
-    if (h->dwork) cudaFree(h->dwork);
-    h->dwork = nullptr;
-    h->dwork_cap = 0;
-    st = dalloc(&h->dwork, need);
-    if (st != AS_OK) return st;
-    h->dwork_cap = need;
-  }
+  st = ensure_dwork(h, dump_work_doubles(d, n2, xi));
+  if (st != AS_OK) return st;
   st = launch_dump(h->s, h->C, ldc, d, r, h->G, n2, h->si.WU, h->si.GWU, k, xi, Z, Y, h->dwork);
   if (st != AS_OK) return st;
   h->gf_valid = 0;
@@ -726,6 +750,8 @@ bool is_device_ptr(const void* p) {
 namespace as {
 
 cudaStream_t sk_stream(const as_sketch* h) { return h->s; }
+int sk_device(const as_sketch* h) { return h->dev; }
+int64_t sk_device_bytes(const as_sketch* h) { return (int64_t)h->dev_bytes; }
 int64_t sk_rows(const as_sketch* h) { return h->T; }
 int sk_snap_count(const as_sketch* h) { return (int)h->snaps.size(); }
 int64_t sk_snap_t(const as_sketch* h, int k) { return h->snaps[(size_t)k].t; }
@@ -776,37 +802,38 @@ as_status sk_eig_shrink(as_sketch* h, double* B, float* out, int64_t ldo) { retu
 
 
 namespace {
+// The calling thread's last failed CUDA call, and the last one of any thread
+// (runtimes such as the server run sketches on worker threads).
 thread_local char g_last_error[192] = "";
+char g_last_error_any[192] = "";
+std::mutex g_last_error_mu;
+std::mutex g_smem_mu;
+std::map<std::pair<const void*, int>, size_t> g_smem_limit;   // (kernel, device) -> limit set
 }
 
 void as_note_cuda_error(cudaError_t e, const char* file, int line) {
   const char* base = std::strrchr(file, '/');
   std::snprintf(g_last_error, sizeof(g_last_error), "%s (%s:%d)", cudaGetErrorName(e), base ? base + 1 : file, line);
+  std::lock_guard<std::mutex> lk(g_last_error_mu);
+  std::memcpy(g_last_error_any, g_last_error, sizeof(g_last_error));
+}
+
+cudaError_t as_raise_smem_limit(const void* fn, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  size_t& cur = g_smem_limit[{fn, dev}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 
-extern "C" {
-
-const char* as_last_error(void) { return g_last_error; }
-
-const char* as_status_str(as_status s) {
-  switch (s) {
-    case AS_OK: return "AS_OK";
-    case AS_EINVAL: return "AS_EINVAL";
-    case AS_ENOMEM: return "AS_ENOMEM";
-    case AS_EDEVICE: return "AS_EDEVICE";
-    case AS_ENUMERIC: return "AS_ENUMERIC";
-    case AS_ETIMEOUT: return "AS_ETIMEOUT";
-    case AS_EBUSY: return "AS_EBUSY";
-    case AS_ENOTSUP: return "AS_ENOTSUP";
-  }
-  return "AS_UNKNOWN";
-}
-
-as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out) {
-  if (!cfg || !out) return AS_EINVAL;
-  *out = nullptr;
-  as_config c = *cfg;
+// Validate a configuration and fill its defaults; the amplification counts of
+// Algorithm 7 come back in amp_r, amp_s (0 when off).
+static as_status normalize_config(as_config& c, int& amp_r, int& amp_s) {
   if (c.d < 2) return AS_EINVAL;
   if (!(c.eps >= 0.0) || std::isinf(c.eps)) return AS_EINVAL;
   if (c.ell == 0) {
@@ -829,7 +856,7 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   // Algorithm 7: r = ceil(log_100(2/delta)) SIs, s = ceil(2 log_3(2/delta))
   // estimates each; r <= 15 and s <= 63 keep the trace's 4-bit choices and the
   // Philox sub-indices 64 h + g of the estimates distinct
-  int amp_r = 0, amp_s = 0;
+  amp_r = amp_s = 0;
   if (c.delta != 0.0) {
     if (!(c.delta > 0.0 && c.delta < 1.0)) return AS_EINVAL;
     const double lg = std::log(2.0 / c.delta);
@@ -837,9 +864,11 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
     amp_s = std::max(1, (int)std::ceil(2.0 * lg / std::log(3.0)));
     if (amp_r > 15 || amp_s > 63) return AS_EINVAL;
   }
+  return AS_OK;
+}
 
-  as_sketch* h = new (std::nothrow) as_sketch();
-  if (!h) return AS_ENOMEM;
+// The sketch's shape and control fields from a normalised configuration.
+static void init_fields(as_sketch* h, const as_config& c, int amp_r, int amp_s, void* cuda_stream) {
   h->cfg = c;
   h->d = c.d;
   h->ell = c.ell;
@@ -862,14 +891,18 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   h->big = h->n2 > 128;
   h->bmax = 64;
   h->bnext = 64;
+}
 
+// Allocate the device state of a sketch whose fields are set (init_fields);
+// with dry = true nothing is allocated and only the byte count is returned.
+static as_status alloc_state(as_sketch* h, bool dry, size_t* out_bytes) {
   const int n2 = h->n2, ell = h->ell, kmax = ell, bmax = h->bmax;
   size_t bytes = 0;
   as_status st = AS_OK;
 #define ALLOC(ptr, n)                                          \
   do {                                                         \
     if (st == AS_OK) {                                         \
-      st = dalloc(&(ptr), (n));                                \
+      if (!dry) st = dalloc(&(ptr), (n));                      \
       bytes += (size_t)(n) * sizeof(*(ptr));                   \
     }                                                          \
   } while (0)
@@ -913,9 +946,9 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   ALLOC(h->si.WU, (size_t)n2 * kmax);
   ALLOC(h->si.GWU, (size_t)n2 * kmax);
   ALLOC(h->si.tmp, (size_t)n2 * kmax + 3 * (size_t)kmax * kmax + kmax);
-  if (st == AS_OK && c.prec != AS_FP32_PLAIN) {
+  if (st == AS_OK && h->cfg.prec != AS_FP32_PLAIN) {
     h->tc = true;
-    h->dpass = (c.prec == AS_BF16X6) ? 6 : (c.prec == AS_BF16X3) ? 3 : 1;
+    h->dpass = (h->cfg.prec == AS_BF16X6) ? 6 : (h->cfg.prec == AS_BF16X3) ? 3 : 1;
     h->n2p = (n2 + 63) / 64 * 64;
     const int rp = std::max(256, std::max(n2, std::max(3 * bmax, ell)));
     h->rows_pad = rp;
@@ -924,6 +957,10 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
     ALLOC(h->Chi, cN); ALLOC(h->Clo, cN); ALLOC(h->Cthi, ctN); ALLOC(h->Ctlo, ctN);
     ALLOC(h->Wh, wN); ALLOC(h->Wl, wN);
     if (h->dpass == 6) { ALLOC(h->Cl2, cN); ALLOC(h->Ctl2, ctN); ALLOC(h->Wl2, wN); }
+    if (dry) {
+      *out_bytes = bytes;
+      return st;
+    }
     __nv_bfloat16* bz[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Wh, h->Wl, h->Cl2, h->Ctl2, h->Wl2};
     const size_t bn[] = {cN, cN, ctN, ctN, wN, wN, cN, ctN, wN};
     for (int t = 0; t < 9 && st == AS_OK; ++t)
@@ -944,6 +981,52 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
     mk(h->mCtB, h->Cthi, h->Ctlo, h->Ctl2, (int)(ctN / h->n2p), h->n2p, h->n2p, 64);
   }
 #undef ALLOC
+  *out_bytes = bytes;
+  return st;
+}
+
+extern "C" {
+
+const char* as_last_error(void) {
+  if (!g_last_error[0]) {
+    std::lock_guard<std::mutex> lk(g_last_error_mu);
+    std::memcpy(g_last_error, g_last_error_any, sizeof(g_last_error));
+  }
+  return g_last_error;
+}
+
+const char* as_status_str(as_status s) {
+  switch (s) {
+    case AS_OK: return "AS_OK";
+    case AS_EINVAL: return "AS_EINVAL";
+    case AS_ENOMEM: return "AS_ENOMEM";
+    case AS_EDEVICE: return "AS_EDEVICE";
+    case AS_ENUMERIC: return "AS_ENUMERIC";
+    case AS_ETIMEOUT: return "AS_ETIMEOUT";
+    case AS_EBUSY: return "AS_EBUSY";
+    case AS_ENOTSUP: return "AS_ENOTSUP";
+  }
+  return "AS_UNKNOWN";
+}
+
+as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out) {
+  if (!cfg || !out) return AS_EINVAL;
+  *out = nullptr;
+  as_config c = *cfg;
+  int amp_r = 0, amp_s = 0;
+  as_status st0 = normalize_config(c, amp_r, amp_s);
+  if (st0 != AS_OK) return st0;
+  as_sketch* h = new (std::nothrow) as_sketch();
+  if (!h) return AS_ENOMEM;
+  init_fields(h, c, amp_r, amp_s, cuda_stream);
+  if (cudaGetDevice(&h->dev) != cudaSuccess) {
+    as_note_cuda_error(cudaGetLastError(), __FILE__, __LINE__);
+    delete h;
+    return AS_EDEVICE;
+  }
+  const int n2 = h->n2, bmax = h->bmax;
+  size_t bytes = 0;
+  as_status st = alloc_state(h, false, &bytes);
   if (st == AS_OK && cudaMallocHost((void**)&h->h_buf, (size_t)(4 * std::max(n2, bmax) + 64) * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     h->h_buf = nullptr;
@@ -969,6 +1052,33 @@ as_status sketch_create(const as_config* cfg, void* cuda_stream, as_sketch** out
   h->st.ell = h->ell;
   *out = h;
   return AS_OK;
+}
+
+as_status sketch_footprint(const as_config* cfg, int64_t snapshot_rank, int64_t* bytes) {
+  if (!cfg || !bytes || snapshot_rank < 0) return AS_EINVAL;
+  as_config c = *cfg;
+  int amp_r = 0, amp_s = 0;
+  as_status st = normalize_config(c, amp_r, amp_s);
+  if (st != AS_OK) return st;
+  as_sketch t;
+  init_fields(&t, c, amp_r, amp_s, nullptr);
+  size_t b = 0;
+  st = alloc_state(&t, true, &b);
+  if (st != AS_OK) return st;
+  b += dwork_max(&t) * sizeof(double) + prb_max(&t) * sizeof(float);
+  b += (size_t)2 * t.d * (size_t)snapshot_rank * sizeof(float);
+  *bytes = (int64_t)b;
+  return AS_OK;
+}
+
+as_status sketch_reserve(as_sketch* h, int64_t snapshot_rank) {
+  if (!h || snapshot_rank < 0) return AS_EINVAL;
+  std::unique_lock<std::mutex> lk(h->mu, std::try_to_lock);
+  if (!lk.owns_lock()) return AS_EBUSY;
+  as_status st = ensure_dwork(h, dwork_max(h));
+  if (st == AS_OK && h->tc) st = ensure_prb(h, prb_max(h));
+  if (st == AS_OK && snapshot_rank > 0) st = arena_reserve(h, (size_t)2 * h->d * (size_t)snapshot_rank, true);
+  return st;
 }
 
 as_status sketch_update(as_sketch* h, const float* rows, int64_t n, int64_t ld) {

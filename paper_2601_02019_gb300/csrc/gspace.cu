@@ -342,7 +342,7 @@ as_status launch_gram_rows(cudaStream_t s, const float* C, int ldc, int d, int r
 as_status launch_power_iteration(cudaStream_t s, const double* G, int n2, int m, int k_pi, Key key, uint64_t i,
                                  double* sig2, uint64_t jsub) {
   const size_t smem = 2 * (size_t)n2 * sizeof(double);
-  AS_CUDA_TRY(cudaFuncSetAttribute(power_iteration_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  AS_CUDA_TRY(as_raise_smem_limit((const void*)power_iteration_kernel, smem));
   power_iteration_kernel<<<1, 512, smem, s>>>(G, n2, m, k_pi, key, jsub, i, sig2); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;

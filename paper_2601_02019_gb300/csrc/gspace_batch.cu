@@ -242,9 +242,13 @@ __global__ void promote_pair_kernel(const float* X, int n2, int col0, int m, int
 }
 
 // ---- dump (Algorithm 4 lines 14-16) -----------------------------------------
-// Partial sums over row chunks s: Zp[s][c][a] = sum_p C[p][c] WU[p][a] and
-// Yp[s][a][c] = sum_p GWU[p][a] C[p][c] for a in [a0, a0+na), one thread per column c.
+// Partial sums over row chunks s: Zp[s][c][a - ab] = sum_p C[p][c] WU[p][a] and
+// Yp[s][a - ab][c] = sum_p GWU[p][a] C[p][c] for a in [a0, a0+na) inside the
+// column block [ab, ab + w), one thread per column c.  Blocks of at most
+// kDumpBlock snapshot columns bound the partial planes to 2 kDumpChunks d
+// kDumpBlock doubles whatever xi is.
 constexpr int kDumpChunks = 8;
+constexpr int kDumpBlock = 64;
 
 // FP32 copies of the first xi columns of WU and GWU (rows < r, row-major
 // r x xi), and the low part GWUlo = fl32(GWU - GWUf) for the residual.
@@ -263,7 +267,8 @@ __global__ void dump_coef_f32(const double* WU, const double* GWU, int r, int k,
 }
 
 __global__ void dump_partial_kernel(const float* __restrict__ C, int ldc, int d, int r, const float* __restrict__ WUf,
-                                    const float* __restrict__ GWUf, int xi, int a0, int na, double* Zp, double* Yp) {
+                                    const float* __restrict__ GWUf, int xi, int a0, int na, int ab, int w, double* Zp,
+                                    double* Yp) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blockIdx.y;
   if (c >= d) return;
@@ -291,18 +296,22 @@ __global__ void dump_partial_kernel(const float* __restrict__ C, int ldc, int d,
 #pragma unroll
   for (int a = 0; a < 8; ++a)
     if (a < na) {
-      Zp[((size_t)s * d + c) * xi + a0 + a] = z[a] + zf[a];
-      Yp[((size_t)s * xi + a0 + a) * d + c] = y[a] + yf[a];
+      Zp[((size_t)s * d + c) * w + (a0 - ab) + a] = z[a] + zf[a];
+      Yp[((size_t)s * w + (a0 - ab) + a) * d + c] = y[a] + yf[a];
     }
 }
 
-__global__ void dump_reduce_kernel(const double* Zp, const double* Yp, int d, int xi, float* Z, float* Y) {
-  const int tot = d * xi;
+// Columns [ab, ab + w) of Z (d x xi row-major) and rows [ab, ab + w) of Y
+// (xi x d row-major) from the block's partial planes.
+__global__ void dump_reduce_kernel(const double* Zp, const double* Yp, int d, int xi, int ab, int w, float* Z,
+                                   float* Y) {
+  const int tot = d * w;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
     double z = 0.0, y = 0.0;
     for (int s = 0; s < kDumpChunks; ++s) { z += Zp[(size_t)s * tot + e]; y += Yp[(size_t)s * tot + e]; }
-    Z[e] = (float)z;   // Z: d x xi row-major (e = c*xi + a)
-    Y[e] = (float)y;   // Y: xi x d row-major (e = a*d + c)
+    const int c = e / w, a = e - c * w;
+    Z[(size_t)c * xi + ab + a] = (float)z;   // Zp element e = c*w + a
+    Y[(size_t)ab * d + e] = (float)y;        // Yp element e = a*d + c
   }
 }
 
@@ -428,25 +437,31 @@ as_status launch_residual_gram(cudaStream_t s, const double* G, int n2, int m, c
 }
 
 size_t dump_work_doubles(int d, int n2, int xi) {
-  return (size_t)2 * kDumpChunks * d * xi + ((size_t)3 * n2 * xi + 1) / 2;   // + the FP32 coefficients
+  // partial planes of one column block + the FP32 coefficients
+  return (size_t)2 * kDumpChunks * d * std::min(xi, kDumpBlock) + ((size_t)3 * n2 * xi + 1) / 2;
 }
 
 as_status launch_dump(cudaStream_t s, float* C, int ldc, int d, int r, double* G, int n2, const double* WU,
                       const double* GWU, int k, int xi, float* Z, float* Y, double* work) {
+  const int wmax = std::min(xi, kDumpBlock);
   double* Zp = work;
-  double* Yp = work + (size_t)kDumpChunks * d * xi;
-  float* WUf = reinterpret_cast<float*>(Yp + (size_t)kDumpChunks * d * xi);
+  double* Yp = work + (size_t)kDumpChunks * d * wmax;
+  float* WUf = reinterpret_cast<float*>(Yp + (size_t)kDumpChunks * d * wmax);
   float* GWUf = WUf + (size_t)n2 * xi;
   float* GWUlo = GWUf + (size_t)n2 * xi;
   if (r > 0) {
     dump_coef_f32<<<(r * xi + 255) / 256, 256, 0, s>>>(WU, GWU, r, k, xi, WUf, GWUf, GWUlo); count_launches(1);
   }
-  for (int a0 = 0; a0 < xi; a0 += 8) {
-    const int na = std::min(8, xi - a0);
-    dim3 grid((d + 127) / 128, kDumpChunks);
-    dump_partial_kernel<<<grid, 128, 0, s>>>(C, ldc, d, r, WUf, GWUf, xi, a0, na, Zp, Yp); count_launches(1);
+  for (int ab = 0; ab < xi; ab += kDumpBlock) {
+    const int w = std::min(kDumpBlock, xi - ab);
+    for (int a0 = ab; a0 < ab + w; a0 += 8) {
+      const int na = std::min(8, ab + w - a0);
+      dim3 grid((d + 127) / 128, kDumpChunks);
+      dump_partial_kernel<<<grid, 128, 0, s>>>(C, ldc, d, r, WUf, GWUf, xi, a0, na, ab, w, Zp, Yp);
+      count_launches(1);
+    }
+    dump_reduce_kernel<<<(d * w + 255) / 256, 256, 0, s>>>(Zp, Yp, d, xi, ab, w, Z, Y); count_launches(1);
   }
-  dump_reduce_kernel<<<(d * xi + 255) / 256, 256, 0, s>>>(Zp, Yp, d, xi, Z, Y); count_launches(1);
   if (r > 0) {
     residual_kernel<<<dim3((d + 255) / 256, r), 256, 0, s>>>(C, ldc, d, r, GWUf, GWUlo, xi, Z); count_launches(1);
     gram_downdate_kernel<<<dim3((r + 255) / 256, r), 256, 0, s>>>(G, n2, r, GWU, k, xi); count_launches(1);

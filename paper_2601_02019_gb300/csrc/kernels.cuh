@@ -187,6 +187,8 @@ as_status launch_split_bf16(cudaStream_t s, const float* src, long long lds, int
 // row indices), the windowed query Gram, raw-row Grams, dropping the oldest
 // snapshots, and the eigen-shrink of a device B (Algorithm 5 lines 5-7).
 cudaStream_t sk_stream(const as_sketch* h);
+int sk_device(const as_sketch* h);
+int64_t sk_device_bytes(const as_sketch* h);
 int64_t sk_rows(const as_sketch* h);
 int sk_snap_count(const as_sketch* h);
 int64_t sk_snap_t(const as_sketch* h, int k);

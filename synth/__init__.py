@@ -68,3 +68,16 @@ def workload_rows(name: str, n: int | None = None, start: int = 0, seed: int = 0
     w = WORKLOADS[name]
     n = w["n"] if n is None else n
     return low_rank_noisy(n, w["d"], w["r"], spectrum(w["spectrum"], w["r"]), seed=seed, start=start)
+
+
+def serving_mix(sessions: int, requests: int, seed: int = 0) -> dict:
+    """A serving workload of `sessions` independent streams:
+    d = round8(exp U[ln 256, ln 8192]), l uniform on {32, 64, 128, 256, 512}
+    clamped to d/2; `requests` batches, each for a uniformly chosen session,
+    of b = round(exp U[0, ln 4096]) rows (at least 1)."""
+    g = _rng(seed, 2_000_000)
+    d = (np.rint(np.exp(g.uniform(np.log(256.0), np.log(8192.0), sessions)) / 8.0) * 8).astype(np.int64)
+    ell = np.minimum(g.choice(np.array([32, 64, 128, 256, 512]), sessions), d // 2)
+    who = g.integers(0, sessions, requests)
+    b = np.maximum(1, np.rint(np.exp(g.uniform(0.0, np.log(4096.0), requests)))).astype(np.int64)
+    return {"d": d, "ell": ell, "session": who, "rows": b}

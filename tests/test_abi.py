@@ -55,8 +55,10 @@ def test_struct_layouts_match_c():
 #include <stdio.h>
 #include "aerosketch.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(as_config), sizeof(as_stats), sizeof(as_event),
-         offsetof(as_config, seed), offsetof(as_stats, device_status), offsetof(as_event, ritz_1));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(as_config), sizeof(as_stats), sizeof(as_event),
+         offsetof(as_config, seed), offsetof(as_stats, device_status), offsetof(as_event, ritz_1),
+         offsetof(as_config, delta), offsetof(as_event, amp_choice), sizeof(as_server_config),
+         sizeof(as_server_counters), offsetof(as_server_counters, span_s));
   return 0;
 }
 '''
@@ -69,4 +71,22 @@ int main(void) {
             pytest.skip("gcc unavailable: " + r.stderr[:200])
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     assert vals == [ct.sizeof(b.AsConfig), ct.sizeof(b.AsStats), ct.sizeof(b.AsEvent),
-                    b.AsConfig.seed.offset, b.AsStats.device_status.offset, b.AsEvent.ritz_1.offset]
+                    b.AsConfig.seed.offset, b.AsStats.device_status.offset, b.AsEvent.ritz_1.offset,
+                    b.AsConfig.delta.offset, b.AsEvent.amp_choice.offset, ct.sizeof(b.AsServerConfig),
+                    ct.sizeof(b.AsServerCounters), b.AsServerCounters.span_s.offset]
+
+
+def test_footprint_is_host_arithmetic():
+    """sketch_footprint needs no device (FP32 form): the snapshot store adds
+    exactly 2 d floats per unit of snapshot rank, the state grows with d and l,
+    and a bad configuration is refused."""
+    b = _lib()
+    f0 = b.footprint(512, 64)
+    assert b.footprint(512, 64, snapshot_rank=100) - f0 == 8 * 512 * 100
+    assert b.footprint(1024, 64) > f0 and b.footprint(512, 128) > f0
+    # at least C and its rebuild target (2l x d FP32 each) and G (2l x 2l FP64)
+    assert f0 >= 2 * (128 * 512 * 4) + 128 * 128 * 8
+    with pytest.raises(b.AeroSketchError):
+        b.footprint(64, 40)
+    with pytest.raises(b.AeroSketchError):
+        b.footprint(64, 8, snapshot_rank=-1)
