@@ -112,6 +112,22 @@ struct EventProf final : Prof {
 
 }  // namespace
 
+// Buffer sizes (2l) from which the FP64 single-row iterations spread over
+// many blocks, and from which the FD shrink uses the GPU-wide df64
+// eigensolver; below them one block does the work in FP64.  FP64 runs at a
+// small fraction of the FP32 rate on this part, so one block is the slower
+// choice at every size measured (2l = 32 .. 256: 1.2x to 3x per sketch), and
+// both thresholds default to 0; the one-block forms stay for the build-time
+// choice and for as_symeig.
+#ifndef AS_MULTI_ROW_MIN
+#define AS_MULTI_ROW_MIN 0
+#endif
+#ifndef AS_EIG_LARGE_MIN
+#define AS_EIG_LARGE_MIN 0
+#endif
+constexpr int kMultiRowMin = AS_MULTI_ROW_MIN;
+constexpr int kEigLargeMin = AS_EIG_LARGE_MIN;
+
 struct as_sketch {
   as_config cfg{};
   int d = 0, ell = 0, n2 = 0, ldc = 0, k_pi = 0, q = 0, jmax = 0, mode = 0;
@@ -130,7 +146,8 @@ struct as_sketch {
   SiBuffers si{};
   BatchBuffers bb{};
   int bmax = 64, bnext = 64;
-  bool big = false;  // 2l > 128: multi-block FP64 path and the spread eigensolver
+  bool big = false;      // multi-block FP64 single-row iterations (2l >= kMultiRowMin)
+  bool big_eig = false;  // the GPU-wide df64 eigensolver for the FD shrink (2l >= kEigLargeMin)
   double* h_buf = nullptr;  // pinned host scratch for branch scalars
   int stage_rows = 0;
   // host mirror of the control state
@@ -277,7 +294,7 @@ as_status fd_shrink(as_sketch* h) {
   const int n2 = h->n2, ell = h->ell, d = h->d;
   AS_CUDA_TRY(cudaMemcpyAsync(h->Gtmp, h->G, (size_t)n2 * n2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
   if (h->prof) h->prof->begin(PK_EIG, h->s);
-  as_status st = h->big ? launch_eig_large(h->s, n2, h->Gtmp, n2, ell, h->lam, h->U, ell, h->eigw, h->prof, h->dstatus)
+  as_status st = h->big_eig ? launch_eig_large(h->s, n2, h->Gtmp, n2, ell, h->lam, h->U, ell, h->eigw, h->prof, h->dstatus)
                          : launch_eig(h->s, n2, h->Gtmp, n2, ell, h->lam, h->U, ell, h->eigw);
   if (st != AS_OK) return st;
   // tridiagonalisation 4/3 n^3 + back-transformation 2 n^2 nev; G read once
@@ -888,7 +905,8 @@ static void init_fields(as_sketch* h, const as_config& c, int amp_r, int amp_s, 
   h->s = (cudaStream_t)cuda_stream;
   h->key = Key{c.seed, c.stream_id};
   h->stage_rows = 256;
-  h->big = h->n2 > 128;
+  h->big = h->n2 >= kMultiRowMin;
+  h->big_eig = h->n2 >= kEigLargeMin;
   h->bmax = 64;
   h->bnext = 64;
 }
@@ -914,7 +932,7 @@ static as_status alloc_state(as_sketch* h, bool dry, size_t* out_bytes) {
   ALLOC(h->Gtmp, (size_t)n2 * n2);
   ALLOC(h->lam, (size_t)n2);
   ALLOC(h->U, (size_t)n2 * ell);
-  ALLOC(h->eigw, h->big ? eig_large_work_doubles(n2, ell) : eig_work_doubles(n2, ell));
+  ALLOC(h->eigw, h->big_eig ? eig_large_work_doubles(n2, ell) : eig_work_doubles(n2, ell));
   ALLOC(h->scal, 1024);
   ALLOC(h->bad, 1);
   ALLOC(h->dstatus, 1);

@@ -363,6 +363,7 @@ as_status launch_gf_mirror(cudaStream_t s, const double* G, float* Gf, int n2, i
 }
 
 static as_status gmul_thin(cudaStream_t s, const double* G, int n2, int m, int k, const double* X, double* Y) {
+  if (m <= 0) return AS_OK;   // an empty buffer: no rows of Y to form
   const int grid = (m + 7) / 8;
   if (k <= 2) {
     gmul_thin_kernel<2><<<grid, 256, 0, s>>>(G, n2, m, k, X, Y); count_launches(1);
@@ -375,12 +376,17 @@ static as_status gmul_thin(cudaStream_t s, const double* G, int n2, int m, int k
 
 // products by G for the FP64 single-row path: thin kernel for k <= 8, else the tiled GEMM
 static as_status gmul64(cudaStream_t s, const double* G, int n2, int m, int k, const double* X, double* Y) {
+  if (m <= 0) return AS_OK;
   if (k <= 8) return gmul_thin(s, G, n2, m, k, X, Y);
   return gemm_strided<double, double, double>(s, m, k, m, G, n2, 1, X, k, 1, Y, k, 1, 1.0, 0.0);
 }
 
 as_status launch_power_iteration_f64(cudaStream_t s, const double* G, int n2, int m, int k_pi, Key key, uint64_t i,
                                      double* x, double* y, int* zero, double* sig2, uint64_t jsub) {
+  if (m <= 0) {   // an empty buffer (after the shrink of l = 1): sigma_hat^2 = 0
+    AS_CUDA_TRY(cudaMemsetAsync(sig2, 0, sizeof(double), s));
+    return AS_OK;
+  }
   AS_CUDA_TRY(cudaMemsetAsync(zero, 0, sizeof(int), s));
   fill_pi_start<<<(n2 / 4 + 255) / 256 + 1, 256, 0, s>>>(x, n2, m, key, i, jsub); count_launches(1);
   normalize_kernel<<<1, 512, 0, s>>>(x, x, m, zero); count_launches(1);
@@ -430,6 +436,7 @@ as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m
 
 as_status launch_residual_gram(cudaStream_t s, const double* G, int n2, int m, const double* GWU, int k, int xi,
                                double* R) {
+  if (m <= 0) return AS_OK;
   if (m <= 0) return AS_OK;
   residual_gram_kernel<<<dim3((m + 255) / 256, m), 256, 0, s>>>(G, n2, m, GWU, k, xi, R); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
