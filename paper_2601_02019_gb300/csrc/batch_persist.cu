@@ -503,6 +503,12 @@ size_t batch_persist_part_floats(int bmax) {
   return 2 * (size_t)kSlots * ((bmax + 1) / 2 + bmax) * kMaxGrid;
 }
 
+void launch_persist_fill(cudaStream_t s, const PersistBuffers& pb, int mmax, int nb, int npi, int r0, Key key,
+                         uint64_t i0) {
+  persist_fill_kernel<<<dim3(nb, 2), 128, 0, s>>>(pb.Y + pb.ybuf, pb.ldy, mmax, nb, npi, r0, key, i0);
+  count_launches(1);
+}
+
 as_status launch_batch_persist(cudaStream_t s, const float* Gf, int n2, int r0, int nb, int k_pi, int q, Key key,
                                uint64_t i0, const PersistBuffers& pb, int* status, Prof* prof) {
   if (nb <= 0) return AS_OK;

@@ -1,0 +1,612 @@
+// Tensor-core form of the block-speculative G-space iterations (the tensor
+// precision forms): the same power iteration (Algorithm 1) and first doubling
+// step (k = 2) of the simultaneous iteration (Algorithm 2) for every row of a
+// block as the FP32 persistent kernel, in one cooperative launch, with the
+// products by G on tcgen05.
+//
+// Row t of the block sees the leading m_t = r0 + t + 1 rows of the buffer, so
+// every column of the batch matrix is zero below m_t and each iteration is
+//   Z = G Y_it,   Y_{it+1} = Z C_it   (rows >= m_t of each column zeroed),
+// where C_it is the per-pair 2 x 2 normalisation of Y_it (1/||y|| for the
+// power-iteration columns, the inverse Cholesky factor of the pair's Gram for
+// a simultaneous-iteration pair).  G (C_it applied after the product) equals
+// G (Y_it C_it) in exact arithmetic; applying it afterwards lets both operands
+// of the product come from memory through TMA, in split-BF16 levels:
+//   x = x0 + x1 (+ x2),  x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1),
+// accumulating every level product whose order is above 2^-16 (three passes)
+// or 2^-24 (six passes).
+//
+// Work split.  CTA (rb, ks) multiplies the 128 rows rb of G by the rows
+// [ks kc, (ks+1) kc) of Y_it (UMMA M = 128, N = the padded column count,
+// K = kc): a TMA producer lane streams G and Y tiles (64 K-elements, 128-byte
+// swizzle) through a 4-stage ring, one lane issues tcgen05.mma into two TMEM
+// accumulators (the leading level product and the corrections), and the
+// partial 128 x N block goes to global memory.  After a grid barrier CTA c
+// sums the K-split partials of its rpc rows in a fixed order, applies C_it,
+// masks, writes Y_{it+1} (FP32 and its BF16 levels) and its per-pair partial
+// sums; a second grid barrier closes the iteration.  The coefficients C_it
+// are computed from those partial sums by the other warps while the product
+// runs.  Every mbarrier and grid-barrier wait is bounded; on a timeout the
+// status word gets AS_ETIMEOUT and every CTA frees its TMEM and returns.
+#include <algorithm>
+#include <mutex>
+
+#include "grid.cuh"
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace as {
+
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kTcStages = 4;
+constexpr int kTcSlots = 6;     // partial sums per pair
+constexpr int kTcMaxRpc = 32;   // rows per CTA in the reduction phase
+constexpr int kTcMaxCols = 192; // batch columns (2 P)
+
+struct TcArgs {
+  float* Y;            // FP32 columns, two buffers of ybuf floats, ld ldy
+  long long ybuf;
+  int ldy;
+  __nv_bfloat16* Yb;   // BF16 levels: [level][buffer][ycols][ldyb]
+  long long yblevel;   // elements per level (2 buffers)
+  long long ybbuf;     // elements per buffer
+  int ldyb;
+  int ycols;
+  float* X;            // final basis of every pair (ld ldx)
+  int ldx;
+  float* part;         // K-split partial products, two buffers of [nks][kpad][nc]
+  long long pplane;
+  float* sums;         // per-pair partial sums, two buffers of sbuf floats: [pair * kTcSlots + slot][cta]
+  long long sbuf;
+  unsigned* cnt;
+  unsigned* flags;     // per CTA: 1 + the last iteration whose reduction it published
+  int* status;
+  int nb, npi, r0, k_pi, q, mmax;
+  int kpad, nrb, nks, kc, nc, rpc;
+  double* sig2;
+  double* ritz;
+};
+
+__device__ __forceinline__ int tc_col_rows(const TcArgs& a, int c) {
+  const int pcol = 2 * a.npi;
+  if (c < pcol) return (c < a.nb) ? a.r0 + c + 1 : 0;
+  return a.r0 + ((c - pcol) >> 1) + 1;
+}
+
+__device__ __forceinline__ void split_levels(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  a = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r1);
+  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+
+__device__ __forceinline__ void eig2_sym_tc(double s00, double s01, double s11, double& l0, double& l1, double& v00,
+                                            double& v01, double& v10, double& v11) {
+  const double tr = 0.5 * (s00 + s11), df = 0.5 * (s00 - s11);
+  const double rad = sqrt(df * df + s01 * s01);
+  l0 = tr + rad;
+  l1 = tr - rad;
+  if (rad == 0.0) { v00 = 1; v10 = 0; v01 = 0; v11 = 1; return; }
+  const double th = 0.5 * atan2(2.0 * s01, s00 - s11);
+  v00 = cos(th); v10 = sin(th); v01 = -v10; v11 = v00;
+}
+
+// Final values of the pairs whose last product was iteration `fin_it`, from
+// the partial sums that every CTA wrote in that iteration's reduction
+// (FP64 over the CTAs, spread over the CTAs); warp w0 the power-iteration
+// estimates, warp w1 the Rayleigh-Ritz values of the k = 2 step.
+__device__ __forceinline__ void tc_finals(const TcArgs& a, const float* s, int fin_it, int warp, int lane, int w0,
+                                          int w1) {
+  const int G = gridDim.x, blk = blockIdx.x;
+  if (fin_it == a.k_pi && warp == w0) {
+    for (int t = blk; t < a.nb; t += G) {
+      const float* q0 = s + (size_t)((t >> 1) * kTcSlots + (t & 1)) * G;
+      double v = 0.0;
+      for (int g = lane; g < G; g += 32) v += (double)__ldcg(q0 + g);
+      v = warp_sum(v);
+      if (lane == 0) a.sig2[t] = v;
+    }
+  }
+  if (fin_it == a.q && warp == w1) {
+    for (int t = blk; t < a.nb; t += G) {
+      const float* q0 = s + (size_t)((a.npi + t) * kTcSlots) * G;
+      double v[kTcSlots];
+#pragma unroll
+      for (int e = 0; e < kTcSlots; ++e) {
+        double x = 0.0;
+        for (int g = lane; g < G; g += 32) x += (double)__ldcg(q0 + (size_t)e * G + g);
+        v[e] = warp_sum(x);
+      }
+      if (lane == 0) {
+        // S = X^T G X, H = (G X)^T (G X); G-orthonormal W = X V diag(a),
+        // Ritz values = eig(diag(a) V^T H V diag(a))
+        double l0, l1, v00, v01, v10, v11;
+        eig2_sym_tc(v[0], v[1], v[2], l0, l1, v00, v01, v10, v11);
+        const double tol = 1e-6 * fmax(l0, 0.0);
+        const double a0 = (l0 > tol && l0 > 0) ? 1.0 / sqrt(l0) : 0.0;
+        const double a1 = (l1 > tol && l1 > 0) ? 1.0 / sqrt(l1) : 0.0;
+        const double h00 = v[3], h01 = v[4], h11 = v[5];
+        const double hv00 = h00 * v00 + h01 * v10, hv10 = h01 * v00 + h11 * v10;
+        const double hv01 = h00 * v01 + h01 * v11, hv11 = h01 * v01 + h11 * v11;
+        const double m00 = a0 * a0 * (v00 * hv00 + v10 * hv10);
+        const double m01 = a0 * a1 * (v00 * hv01 + v10 * hv11);
+        const double m11 = a1 * a1 * (v01 * hv01 + v11 * hv11);
+        const double tr = 0.5 * (m00 + m11), df = 0.5 * (m00 - m11);
+        const double rad = sqrt(df * df + m01 * m01);
+        a.ritz[2 * t] = (a0 > 0) ? tr + rad : 0.0;
+        a.ritz[2 * t + 1] = (a0 > 0 && a1 > 0) ? tr - rad : 0.0;
+      }
+    }
+  }
+}
+
+// Synchronisation.  One grid barrier per iteration separates the K-split
+// partial products from their reduction.  The reduction of CTA c publishes
+// rows [c rpc, (c+1) rpc) of Y_{it+1} and its partial sums with a release
+// store of flags[c] = it + 1; the product of the next iteration waits
+// (acquire) only for the flags of the CTAs whose rows form its K range, and
+// the coefficient warps, which need every CTA's partial sums, wait for all
+// flags while the product runs.  The partial products are double buffered by
+// iteration parity, so a product never overwrites a plane that a slower
+// CTA's reduction still reads.
+template <int NPASS>
+__global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
+                                                                 const __grid_constant__ UmmaOperand mG,
+                                                                 const __grid_constant__ UmmaOperand mY) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t A_BYTES = UM * UK * 2;
+  const uint32_t B_BYTES = (uint32_t)a.nc * UK * 2;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + kTcStages * A_BYTES;
+  float* zs = reinterpret_cast<float*>(smem);   // reduction phase: reuses the ring
+  __shared__ __align__(8) uint64_t full_bar[kTcStages];
+  __shared__ __align__(8) uint64_t empty_bar[kTcStages];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int fail_s;
+  __shared__ float4 coef[kTcMaxCols / 2];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x, blk = blockIdx.x;
+  const int rb = blk / a.nks, ks = blk - rb * a.nks;
+  const int P = a.npi + a.nb;
+  const int k0 = ks * a.kc, k1 = min(a.kpad, k0 + a.kc);
+  const int ktiles = (k1 > k0) ? (k1 - k0) / UK : 0;
+  const int niter = ktiles * NPASS;
+
+  if (tid == 0) {
+    for (int s = 0; s < kTcStages; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    mbar_init(&done_bar, 1);
+    fail_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {   // two accumulators of nc columns (<= 384): all 512 TMEM columns of the SM
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_s;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a.nc >> 3) << 17) |
+                         ((uint32_t)(UM >> 4) << 24);
+
+  const int iters = max(a.k_pi, a.q);
+  unsigned bar_target = 0;
+  bool alive = true;
+  for (int it = 0; it <= iters; ++it) {
+    const bool pi_on = it <= a.k_pi, si_on = it <= a.q;
+    const int pa0 = pi_on ? 0 : a.npi, pa1 = si_on ? P : a.npi;
+    const int nact = pa1 - pa0;
+    const int bold = (it + 1) & 1, bnew = it & 1;
+    const float* Yold = a.Y + (size_t)bold * a.ybuf;
+    float* Ynew = a.Y + (size_t)bnew * a.ybuf;
+    const float* sold = a.sums + (size_t)bold * a.sbuf;
+    float* snew = a.sums + (size_t)bnew * a.sbuf;
+    float* part = a.part + (size_t)bnew * a.nks * a.pplane;
+
+    // ---- product phase: Z(rows rb, all columns) over K range ks ----
+    if (warp == 0 && lane == 0 && niter > 0) {
+      bool ok = true;
+      if (it > 0) {   // rows [k0, k1) of Y_it: the reductions of the previous iteration that hold them
+        const int c_lo = k0 / a.rpc, c_hi = min(G - 1, (k1 - 1) / a.rpc);
+        for (int c = c_lo; c <= c_hi && ok; ++c) ok = wait_flag_ge(a.flags + c, (unsigned)it, a.status);
+      }
+      asm volatile("fence.proxy.async.global;" ::: "memory");   // Y_it was written through the generic proxy
+      for (int li = 0; li < niter && ok; ++li) {
+        const int g = it * niter + li;
+        const int s = g % kTcStages;
+        const uint32_t ph = (uint32_t)(g / kTcStages) & 1u;
+        if (!mbar_wait(&empty_bar[s], ph ^ 1u)) { ok = false; break; }
+        const int kt = li / NPASS, pass = li - kt * NPASS;
+        const int kx = k0 + kt * UK;
+        const int la = (NPASS == 1) ? 0 : kPassA[pass], lb = (NPASS == 1) ? 0 : kPassB[pass];
+        mbar_expect_tx(&full_bar[s], A_BYTES + B_BYTES);
+        tma_load_2d(sA + s * A_BYTES, &mG.m[la], &full_bar[s], kx, rb * UM);
+        tma_load_2d(sB + s * B_BYTES, &mY.m[lb], &full_bar[s], kx, bold * a.ycols);
+      }
+      if (!ok) atomicExch(&fail_s, 1);
+    } else if (warp == 1 && lane == 0 && niter > 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int li = 0; li < niter; ++li) {
+        const int g = it * niter + li;
+        const int s = g % kTcStages;
+        const uint32_t ph = (uint32_t)(g / kTcStages) & 1u;
+        if (!mbar_wait(&full_bar[s], ph)) { atomicExch(&fail_s, 1); break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+        const int pass = li % NPASS;
+#pragma unroll
+        for (int kk = 0; kk < UK / 16; ++kk) {
+          const int aidx = (pass == 0) ? 0 : 1;
+          const bool first = (pass == 0) ? (li == 0 && kk == 0) : (li == 1 && kk == 0);
+          const uint32_t dst = tmem + (uint32_t)(aidx * a.nc);
+          const uint64_t da = smem_desc(a0 + kk * 32), db = smem_desc(b0 + kk * 32);
+          const uint32_t acc = first ? 0u : 1u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
+              "l"(da), "l"(db), "r"(idesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&empty_bar[s]))
+                     : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&done_bar))
+                   : "memory");
+    } else if (warp >= 2) {
+      // coefficients C_it of the active pairs from every CTA's partial sums of Y_it
+      constexpr int kCT = kTcThreads - 64;
+      const int ct = tid - 64;
+      if (it == 0) {
+        for (int p = ct; p < P; p += kCT) coef[p] = make_float4(1.f, 0.f, 0.f, 1.f);
+      } else {
+        bool ok = true;
+        for (int c = ct; c < G && ok; c += kCT) ok = wait_flag_ge(a.flags + c, (unsigned)it, a.status);
+        if (!ok) atomicExch(&fail_s, 1);
+        asm volatile("bar.sync 1, %0;" ::"r"(kCT) : "memory");
+        // pairs whose last product was the previous iteration: their final values
+        tc_finals(a, sold, it - 1, warp, lane, 2, 3);
+        for (int pbase = pa0 + 4 * (warp - 2); pbase < pa1; pbase += 4 * (kCT / 32)) {
+          float sv[4][3];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) sv[j][0] = sv[j][1] = sv[j][2] = 0.f;
+          for (int g0 = 0; g0 < G; g0 += 128) {
+            float buf[4][4][3];
+#pragma unroll
+            for (int gg = 0; gg < 4; ++gg) {
+              const int g = g0 + 32 * gg + lane;
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int p = pbase + j;
+                const bool on = p < pa1 && g < G;
+                const float* q0 = sold + (size_t)(p * kTcSlots) * G + g;
+                buf[gg][j][0] = on ? __ldcg(q0) : 0.f;
+                buf[gg][j][1] = on ? __ldcg(q0 + G) : 0.f;
+                buf[gg][j][2] = (on && p >= a.npi) ? __ldcg(q0 + 2 * G) : 0.f;
+              }
+            }
+#pragma unroll
+            for (int gg = 0; gg < 4; ++gg)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                sv[j][0] += buf[gg][j][0];
+                sv[j][1] += buf[gg][j][1];
+                sv[j][2] += buf[gg][j][2];
+              }
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            sv[j][0] = warp_sum(sv[j][0]);
+            sv[j][1] = warp_sum(sv[j][1]);
+            sv[j][2] = warp_sum(sv[j][2]);
+          }
+          const int p = pbase + lane;
+          if (lane < 4 && p < pa1) {
+            float s0 = sv[0][0], s1 = sv[0][1], s2 = sv[0][2];
+#pragma unroll
+            for (int j = 1; j < 4; ++j)
+              if (lane == j) { s0 = sv[j][0]; s1 = sv[j][1]; s2 = sv[j][2]; }
+            float c00 = 0.f, c10 = 0.f, c01 = 0.f, c11 = 0.f;
+            if (p < a.npi) {
+              c00 = (s0 > 0.f) ? rsqrtf(s0) : 0.f;
+              c11 = (s1 > 0.f) ? rsqrtf(s1) : 0.f;
+            } else if (s0 > 0.f) {
+              // [y0 y1] = [x0 x1] R, R = [[sqrt(a), b/sqrt(a)], [0, sqrt(c - b^2/a)]]
+              const float r00 = sqrtf(s0), l = s1 / s0;
+              const float sc = fmaxf(s2 - s1 * l, 1e-12f * s2);
+              c00 = 1.f / r00;
+              if (s2 > 0.f) {
+                c11 = rsqrtf(sc);
+                c01 = -l * c11;
+              }
+            }
+            coef[p] = make_float4(c00, c10, c01, c11);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    // epilogue: warps 0-3 move the 128 x nc block (both accumulators summed) to part[ks]
+    if (warp < 4 && niter > 0) {
+      // wait for the MMAs even after a failure, so none is in flight when the TMEM is freed
+      bool have = mbar_wait(&done_bar, (uint32_t)it & 1u);
+      if (!have) atomicExch(&fail_s, 1);
+      if (fail_s) have = false;
+      have = __all_sync(0xffffffffu, have);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = rb * UM + warp * 32 + lane;
+      float* o = part + (size_t)ks * a.pplane + (size_t)row * a.nc;
+      for (int c0 = 0; c0 < a.nc; c0 += 16) {
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        if (have) {
+#pragma unroll
+          for (int acc = 0; acc < 2; ++acc) {
+            if (acc == 1 && NPASS == 1) break;
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + acc * a.nc);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(r[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          __stcg(reinterpret_cast<float4*>(o + c0 + j), make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]));
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && fail_s) set_status(a.status, AS_ETIMEOUT);
+    bar_target += (unsigned)G;
+    if (!grid_barrier(a.cnt, bar_target, a.status)) { alive = false; break; }
+
+    // ---- reduction phase: rows [rw0, rw1) of Y_{it+1} = Z C_it ----
+    const int rw0 = blk * a.rpc, rw1 = min(a.kpad, rw0 + a.rpc);
+    const int R = max(0, rw1 - rw0);
+    const int c0a = 2 * pa0, nca = 2 * nact;
+    for (int e = tid; e < R * nca; e += kTcThreads) {
+      const int r = e / nca, cl = e - r * nca;
+      const float* pp = part + (size_t)(rw0 + r) * a.nc + c0a + cl;
+      float z = 0.f;
+      for (int k = 0; k < a.nks; ++k) z += __ldcg(pp + (size_t)k * a.pplane);
+      zs[r * nca + cl] = z;
+    }
+    __syncthreads();
+    if (tid < nact) {
+      const int p = pa0 + tid;
+      const bool si = p >= a.npi;
+      const bool fin = si ? (it == a.q) : (it == a.k_pi);
+      const float4 cf = coef[p];
+      const int ca = 2 * p, cb = 2 * p + 1;
+      const int ma = tc_col_rows(a, ca), mb = tc_col_rows(a, cb);
+      float ps[kTcSlots] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int r = 0; r < R; ++r) {
+        const int row = rw0 + r;
+        const float za = zs[r * nca + 2 * tid], zb = zs[r * nca + 2 * tid + 1];
+        const float y0 = (row < ma) ? fmaf(cf.x, za, cf.y * zb) : 0.f;
+        const float y1 = (row < mb) ? fmaf(cf.z, za, cf.w * zb) : 0.f;
+        const bool in_y = row < a.ldy;   // rows past the FP32 columns are zero (>= m_t)
+        if (in_y) {
+          Ynew[(size_t)ca * a.ldy + row] = y0;
+          Ynew[(size_t)cb * a.ldy + row] = y1;
+        }
+        __nv_bfloat16 l0, l1, l2;
+        split_levels(y0, l0, l1, l2);
+        __nv_bfloat16* ya = a.Yb + (size_t)bnew * a.ybbuf + (size_t)ca * a.ldyb + row;
+        ya[0] = l0;
+        ya[a.yblevel] = l1;
+        ya[2 * a.yblevel] = l2;
+        split_levels(y1, l0, l1, l2);
+        __nv_bfloat16* yb = ya + a.ldyb;
+        yb[0] = l0;
+        yb[a.yblevel] = l1;
+        yb[2 * a.yblevel] = l2;
+        if (!fin) {
+          ps[0] = fmaf(y0, y0, ps[0]);
+          if (si) {
+            ps[1] = fmaf(y0, y1, ps[1]);
+            ps[2] = fmaf(y1, y1, ps[2]);
+          } else {
+            ps[1] = fmaf(y1, y1, ps[1]);
+          }
+        } else {
+          // x = Y_it C_it (the normalised iterate), y = G x
+          const float ya0 = in_y ? __ldcg(Yold + (size_t)ca * a.ldy + row) : 0.f;
+          const float yb0 = in_y ? __ldcg(Yold + (size_t)cb * a.ldy + row) : 0.f;
+          const float x0 = fmaf(cf.x, ya0, cf.y * yb0), x1 = fmaf(cf.z, ya0, cf.w * yb0);
+          if (!si) {
+            ps[0] = fmaf(x0, y0, ps[0]);
+            ps[1] = fmaf(x1, y1, ps[1]);
+          } else {
+            ps[0] = fmaf(x0, y0, ps[0]);
+            ps[1] = fmaf(0.5f, fmaf(x0, y1, x1 * y0), ps[1]);
+            ps[2] = fmaf(x1, y1, ps[2]);
+            ps[3] = fmaf(y0, y0, ps[3]);
+            ps[4] = fmaf(y0, y1, ps[4]);
+            ps[5] = fmaf(y1, y1, ps[5]);
+            if (row < a.ldx) {
+              a.X[(size_t)ca * a.ldx + row] = x0;
+              a.X[(size_t)cb * a.ldx + row] = x1;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < kTcSlots; ++e) snew[(size_t)(p * kTcSlots + e) * G + blk] = ps[e];
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");   // the BF16 levels feed other CTAs' TMA loads
+    __syncthreads();   // also: the ring (zs) is free for the next product
+    if (tid == 0) st_release_u32(a.flags + blk, (unsigned)(it + 1));
+  }
+  // the pairs whose last product was the final iteration
+  if (alive) {
+    __shared__ int ok_s;
+    if (tid == 0) ok_s = 1;
+    __syncthreads();
+    for (int c = tid; c < G; c += kTcThreads)
+      if (!wait_flag_ge(a.flags + c, (unsigned)(iters + 1), a.status)) ok_s = 0;
+    __syncthreads();
+    if (ok_s) tc_finals(a, a.sums + (size_t)(iters & 1) * a.sbuf, iters, warp, lane, 0, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 2) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// x^(0) and Pi of every row (FP32, buffer 1) as the FP32 form writes them,
+// then their BF16 levels for rows [0, kpad) of columns [0, ncols).
+__global__ void tc_split_start_kernel(const float* Y, int ldy, int mmax, int ncols, int kpad, __nv_bfloat16* Yb,
+                                      long long yblevel, int ldyb) {
+  const int c = blockIdx.x;
+  if (c >= ncols) return;
+  for (int r = threadIdx.x; r < kpad; r += blockDim.x) {
+    const float v = (r < mmax) ? Y[(size_t)c * ldy + r] : 0.f;
+    __nv_bfloat16 l0, l1, l2;
+    split_levels(v, l0, l1, l2);
+    __nv_bfloat16* o = Yb + (size_t)c * ldyb + r;
+    o[0] = l0;
+    o[yblevel] = l1;
+    o[2 * yblevel] = l2;
+  }
+}
+
+// BF16 levels of rows and columns [valid, m) of the leading m x m block of G.
+__global__ void tc_mirror_kernel(const double* G, int n2, int valid, int m, __nv_bfloat16* Gb, long long level,
+                                 int ldg) {
+  const int p = blockIdx.x;
+  if (p >= m) return;
+  const int q0 = (p < valid) ? valid : 0;
+  for (int q = q0 + threadIdx.x; q < m; q += blockDim.x) {
+    const double x = G[(size_t)p * n2 + q];
+    const __nv_bfloat16 l0 = __double2bfloat16(x);
+    const double r1 = x - (double)__bfloat162float(l0);
+    const __nv_bfloat16 l1 = __double2bfloat16(r1);
+    const __nv_bfloat16 l2 = __double2bfloat16(r1 - (double)__bfloat162float(l1));
+    __nv_bfloat16* o = Gb + (size_t)p * ldg + q;
+    o[0] = l0;
+    o[level] = l1;
+    o[2 * level] = l2;
+  }
+}
+
+struct TcDevice {
+  int sms = 0;
+  size_t attr[2] = {0, 0};
+};
+TcDevice g_tcdev[64];
+std::mutex g_tcdev_mu;
+
+}  // namespace
+
+as_status launch_tc_mirror(cudaStream_t s, const double* G, int n2, int valid, int m, const TcBatchBuffers& tb) {
+  if (m <= 0 || valid >= m) return AS_OK;
+  tc_mirror_kernel<<<m, 256, 0, s>>>(G, n2, std::max(valid, 0), m, tb.Gb, tb.glevel, tb.ldg);
+  count_launches(1);
+  AS_CUDA_TRY(cudaGetLastError());
+  return AS_OK;
+}
+
+size_t batch_tc_part_floats(int n2, int ycols) {
+  const size_t kpad = (size_t)(n2 + 127) / 128 * 128;
+  // two buffers of nks <= 16 planes (checked at launch), then the CTA flags
+  return (size_t)2 * 16 * kpad * (size_t)std::min(ycols, kTcMaxCols) + 256;
+}
+
+as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int q, Key key, uint64_t i0,
+                          const PersistBuffers& pb, const TcBatchBuffers& tb, int npass, int* status, Prof* prof,
+                          bool* used) {
+  *used = false;
+  if (nb <= 0) return AS_OK;
+  const int mmax = r0 + nb;
+  const int npi = (nb + 1) / 2, P = npi + nb;
+  const int kpad = (mmax + 127) / 128 * 128;
+  const int ncols = 2 * P;
+  const int nc = (ncols + 15) / 16 * 16;
+  if (kpad < 256 || nc > kTcMaxCols || nc > (int)pb.ycols || (npass != 3 && npass != 6)) return AS_OK;
+  int dev = 0;
+  AS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return AS_OK;
+  std::unique_lock<std::mutex> lk(g_tcdev_mu);
+  TcDevice& td = g_tcdev[dev];
+  if (td.sms == 0) AS_CUDA_TRY(cudaDeviceGetAttribute(&td.sms, cudaDevAttrMultiProcessorCount, dev));
+  // K range per CTA: as short as the co-resident grid (one CTA per SM) allows
+  const int nrb = kpad / 128;
+  const long long need = ((long long)kpad * kpad + 128LL * td.sms - 1) / (128LL * td.sms);
+  int kc = (int)std::max<long long>(64, (need + 63) / 64 * 64);
+  const int nks = (kpad + kc - 1) / kc;
+  kc = (kpad + nks - 1) / nks;
+  kc = (kc + 63) / 64 * 64;
+  const int ncta = nrb * nks;
+  const int rpc = (kpad + ncta - 1) / ncta;
+  if (nks > 16 || ncta > td.sms || rpc > kTcMaxRpc) return AS_OK;
+  const size_t smem = 1024 + (size_t)kTcStages * (UM * UK * 2 + (size_t)nc * UK * 2);
+  const int v = (npass == 6) ? 1 : 0;
+  const void* fn = v ? (const void*)batch_tc_kernel<6> : (const void*)batch_tc_kernel<3>;
+  if (smem > td.attr[v]) {
+    AS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    td.attr[v] = smem;
+  }
+  int per = 0;
+  AS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kTcThreads, smem));
+  if (per < 1 || (long long)per * td.sms < ncta) return AS_OK;
+  lk.unlock();
+  // the BF16 levels of the batch vectors: two buffers of ycols columns per level
+  UmmaOperand mY{};
+  for (int l = 0; l < 3; ++l) {
+    as_status st = umma_make_map(&mY.m[l], tb.Yb + (size_t)l * tb.yblevel, 2 * (int)pb.ycols, tb.ldyb, tb.ldyb, nc);
+    if (st != AS_OK) return st;
+  }
+  if (prof) prof->begin(PK_BATCH_ORTH, s);
+  launch_persist_fill(s, pb, mmax, nb, npi, r0, key, i0);
+  tc_split_start_kernel<<<ncols, 256, 0, s>>>(pb.Y + pb.ybuf, pb.ldy, mmax, ncols, kpad,
+                                              tb.Yb + (size_t)pb.ycols * tb.ldyb, tb.yblevel, tb.ldyb);
+  count_launches(1);
+  AS_CUDA_TRY(cudaGetLastError());
+  if (prof) prof->end(PK_BATCH_ORTH, s, 0.0, 12.0 * mmax * (double)nb);
+  AS_CUDA_TRY(cudaMemsetAsync(pb.cnt, 0, sizeof(unsigned), s));
+  unsigned* flags = reinterpret_cast<unsigned*>(tb.part + batch_tc_part_floats(n2, (int)pb.ycols) - 256);
+  AS_CUDA_TRY(cudaMemsetAsync(flags, 0, 256 * sizeof(unsigned), s));
+  TcArgs a{};
+  a.Y = pb.Y; a.ybuf = pb.ybuf; a.ldy = pb.ldy;
+  a.Yb = tb.Yb; a.yblevel = tb.yblevel; a.ybbuf = (long long)pb.ycols * tb.ldyb; a.ldyb = tb.ldyb;
+  a.ycols = (int)pb.ycols;
+  a.X = pb.X; a.ldx = n2;
+  a.part = tb.part; a.pplane = (long long)kpad * nc;
+  a.sums = pb.part; a.sbuf = (long long)kTcSlots * P * ncta;
+  a.cnt = pb.cnt; a.flags = flags; a.status = status;
+  a.nb = nb; a.npi = npi; a.r0 = r0; a.k_pi = k_pi; a.q = q; a.mmax = mmax;
+  a.kpad = kpad; a.nrb = nrb; a.nks = nks; a.kc = kc; a.nc = nc; a.rpc = rpc;
+  a.sig2 = pb.sig2; a.ritz = pb.ritz;
+  void* args[] = {&a, (void*)&tb.mG, &mY};
+  if (prof) prof->begin(PK_BATCH_GEMM, s);
+  AS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(ncta), dim3(kTcThreads), args, smem, s));
+  count_launches(1);
+  if (prof) {
+    double m2 = 0.0, m1 = 0.0;
+    for (int t = 0; t < nb; ++t) {
+      const double m = (double)(r0 + t + 1);
+      m2 += m * m;
+      m1 += m;
+    }
+    const double prods = (double)(k_pi + 1) + 2.0 * (double)(q + 1);
+    prof->end(PK_BATCH_GEMM, s, 2.0 * m2 * prods, 2.0 * npass / 3.0 * (double)kpad * kpad + 8.0 * m1 * prods);
+  }
+  *used = true;
+  return AS_OK;
+}
+
+}  // namespace as

@@ -179,6 +179,8 @@ struct as_sketch {
   UmmaOperand mCA{}, mCB64{}, mCB256{}, mWA{}, mCtB{};
   // persistent batched iterations
   PersistBuffers pb{};
+  bool tcb = false;         // tcgen05 form of the batched iterations (tensor forms, 2l >= 256)
+  TcBatchBuffers tb{};
   int gf_valid = 0;         // leading rows/columns of Gf that equal G (FP32-rounded)
 };
 
@@ -197,8 +199,9 @@ void free_all(as_sketch* h) {
   if (h->pb.cnt) cudaFree(h->pb.cnt);
   double* xp[] = {h->Bx, h->sx_yz, h->sx_t};
   for (double* p : xp) if (p) cudaFree(p);
-  __nv_bfloat16* bp[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Wh, h->Wl, h->Cl2, h->Ctl2, h->Wl2};
+  __nv_bfloat16* bp[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Wh, h->Wl, h->Cl2, h->Ctl2, h->Wl2, h->tb.Gb, h->tb.Yb};
   for (__nv_bfloat16* p : bp) if (p) cudaFree(p);
+  if (h->tb.part) cudaFree(h->tb.part);
   if (h->h_buf) cudaFreeHost(h->h_buf);
   delete h->prof;
   h->prof = nullptr;
@@ -537,15 +540,30 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
   if (nbb > 0) {
     if (h->prof) h->prof->begin(PK_BATCH_ORTH, h->s);
     st = launch_gf_mirror(h->s, h->G, h->Gf, n2, h->gf_valid, r0 + nbb);
+    if (st == AS_OK && h->tcb) st = launch_tc_mirror(h->s, h->G, n2, h->gf_valid, r0 + nbb, h->tb);
     if (st != AS_OK) return st;
     if (h->prof) {
       const double nm = (double)(r0 + nbb) * (r0 + nbb) - (double)h->gf_valid * h->gf_valid;
       h->prof->end(PK_BATCH_ORTH, h->s, 0.0, 12.0 * nm);
     }
     h->gf_valid = r0 + nbb;
-    st = launch_batch_persist(h->s, h->Gf, n2, r0, nbb, h->k_pi, h->q, h->key, (uint64_t)(h->T + 1), h->pb,
-                              h->dstatus, h->prof);
-    if (st != AS_OK) return st;
+    // tensor forms: the tcgen05 form of the batched iterations where the block's
+    // shape allows it, else the FP32 persistent kernel.  Three split-BF16
+    // passes (about 1e-5 relative) suffice in every form: the batch only
+    // decides (gate and k = 2 stop tests, each re-decided in FP64 within a
+    // 1e-4 relative tie band) and hands the event row a starting basis whose
+    // Rayleigh-Ritz step is redone in FP64.
+    bool on_tc = false;
+    if (h->tcb) {
+      st = launch_batch_tc(h->s, n2, r0, nbb, h->k_pi, h->q, h->key, (uint64_t)(h->T + 1), h->pb, h->tb,
+                           3, h->dstatus, h->prof, &on_tc);
+      if (st != AS_OK) return st;
+    }
+    if (!on_tc) {
+      st = launch_batch_persist(h->s, h->Gf, n2, r0, nbb, h->k_pi, h->q, h->key, (uint64_t)(h->T + 1), h->pb,
+                                h->dstatus, h->prof);
+      if (st != AS_OK) return st;
+    }
   }
   // one synchronisation per block: row norms, power-iteration values, Ritz
   // values and the sticky device status
@@ -975,13 +993,23 @@ static as_status alloc_state(as_sketch* h, bool dry, size_t* out_bytes) {
     ALLOC(h->Chi, cN); ALLOC(h->Clo, cN); ALLOC(h->Cthi, ctN); ALLOC(h->Ctlo, ctN);
     ALLOC(h->Wh, wN); ALLOC(h->Wl, wN);
     if (h->dpass == 6) { ALLOC(h->Cl2, cN); ALLOC(h->Ctl2, ctN); ALLOC(h->Wl2, wN); }
+    if (n2 >= 256) {   // the tcgen05 batched iterations: BF16 levels of G and of the batch vectors
+      h->tcb = true;
+      h->tb.ldg = h->n2p;
+      h->tb.glevel = (long long)h->n2p * h->n2p;
+      h->tb.ldyb = (n2 + 127) / 128 * 128;
+      h->tb.yblevel = 2LL * (long long)h->pb.ycols * h->tb.ldyb;
+      ALLOC(h->tb.Gb, 3 * (size_t)h->tb.glevel);
+      ALLOC(h->tb.Yb, 3 * (size_t)h->tb.yblevel);
+      ALLOC(h->tb.part, batch_tc_part_floats(n2, (int)h->pb.ycols));
+    }
     if (dry) {
       *out_bytes = bytes;
       return st;
     }
-    __nv_bfloat16* bz[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Wh, h->Wl, h->Cl2, h->Ctl2, h->Wl2};
-    const size_t bn[] = {cN, cN, ctN, ctN, wN, wN, cN, ctN, wN};
-    for (int t = 0; t < 9 && st == AS_OK; ++t)
+    __nv_bfloat16* bz[] = {h->Chi, h->Clo, h->Cthi, h->Ctlo, h->Wh, h->Wl, h->Cl2, h->Ctl2, h->Wl2, h->tb.Gb, h->tb.Yb};
+    const size_t bn[] = {cN, cN, ctN, ctN, wN, wN, cN, ctN, wN, 3 * (size_t)h->tb.glevel, 3 * (size_t)h->tb.yblevel};
+    for (int t = 0; t < 11 && st == AS_OK; ++t)
       if (bz[t] && cudaMemsetAsync(bz[t], 0, bn[t] * sizeof(__nv_bfloat16), h->s) != cudaSuccess) st = AS_EDEVICE;
     const int cr = (int)(cN / h->ldc);
     // level maps; a missing third level repeats the second (never read then)
@@ -997,6 +1025,8 @@ static as_status alloc_state(as_sketch* h, bool dry, size_t* out_bytes) {
     mk(h->mCB256, h->Chi, h->Clo, h->Cl2, cr, h->ldc, h->ldc, 256);
     mk(h->mWA, h->Wh, h->Wl, h->Wl2, (int)(wN / h->n2p), h->n2p, h->n2p, 128);
     mk(h->mCtB, h->Cthi, h->Ctlo, h->Ctl2, (int)(ctN / h->n2p), h->n2p, h->n2p, 64);
+    if (h->tcb)
+      mk(h->tb.mG, h->tb.Gb, h->tb.Gb + h->tb.glevel, h->tb.Gb + 2 * h->tb.glevel, h->n2p, h->n2p, h->n2p, 128);
   }
 #undef ALLOC
   *out_bytes = bytes;

@@ -19,6 +19,22 @@ __device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// One thread waits (bounded) until *flag >= target; false on a timeout
+// (status set to AS_ETIMEOUT) or when the sticky status is already set.
+__device__ __forceinline__ bool wait_flag_ge(const unsigned* flag, unsigned target, int* status) {
+  long long n = 0;
+  while (ld_acquire_u32(flag) < target) {
+    if (*(volatile int*)status != 0) return false;
+    if (++n > kGridBarrierSpins) { set_status(status, AS_ETIMEOUT); return false; }
+    __nanosleep(32);
+  }
+  return true;
+}
+
 // Returns false when this CTA gave up waiting (status set to AS_ETIMEOUT) or
 // found the sticky status already set; the caller then returns, and every
 // other CTA gives up at its next barrier.

@@ -151,6 +151,32 @@ int batch_si_col(int nb, int t);
 as_status launch_batch_persist(cudaStream_t s, const float* Gf, int n2, int r0, int nb, int k_pi, int q, Key key,
                                uint64_t i0, const PersistBuffers& pb, int* status, Prof* prof = nullptr);
 
+// x^(0) and Pi of every row of a block into buffer 1 of pb.Y (FP32), as the
+// persistent kernels read them at iteration 0.
+void launch_persist_fill(cudaStream_t s, const PersistBuffers& pb, int mmax, int nb, int npi, int r0, Key key,
+                         uint64_t i0);
+
+// Tensor-core form of the batched iterations (tensor precision forms):
+// BF16 levels of G (mirrored like the FP32 copy), of the batch vectors, and
+// the K-split partial products.
+struct TcBatchBuffers {
+  __nv_bfloat16* Gb;    // 3 levels of n2p x n2p (row-major, ld ldg), glevel elements apart
+  long long glevel;
+  int ldg;
+  UmmaOperand mG;       // tensor maps of the G levels (box 64 x 128)
+  __nv_bfloat16* Yb;    // 3 levels x 2 buffers x ycols columns of ldyb
+  long long yblevel;
+  int ldyb;
+  float* part;
+};
+size_t batch_tc_part_floats(int n2, int ycols);
+as_status launch_tc_mirror(cudaStream_t s, const double* G, int n2, int valid, int m, const TcBatchBuffers& tb);
+// Runs the block on tcgen05 when its shape allows (kpad >= 256, at most 192
+// columns, a co-resident grid); *used = false leaves it to launch_batch_persist.
+as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int q, Key key, uint64_t i0,
+                          const PersistBuffers& pb, const TcBatchBuffers& tb, int npass, int* status, Prof* prof,
+                          bool* used);
+
 // FP64 single-row power iteration and simultaneous iteration built from
 // multi-block products (any buffer size).  x, y: n2 doubles; zero: 1 int.
 as_status launch_power_iteration_f64(cudaStream_t s, const double* G, int n2, int m, int k_pi, Key key,

@@ -28,79 +28,13 @@
 #include <atomic>
 
 #include "kernels.cuh"
+#include "tc.cuh"
 
 namespace as {
 
 namespace {
 
-constexpr int UM = 128;     // tile rows (UMMA M)
-constexpr int UK = 64;      // K elements per stage (128 bytes of BF16)
 constexpr int STAGES = 4;
-constexpr uint32_t kSpinLimit = 1u << 22;   // bounded polling: a stuck pipeline reports an error
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// Bounded wait for the phase with the given parity; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t addr = smem_u32(bar);
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor (tcgen05): K-major operand, 128-byte
-// swizzle, 8-row groups 1024 bytes apart (SBO), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
-  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
-  d |= (uint64_t)1 << 46;                          // version
-  d |= (uint64_t)2 << 61;                          // layout: 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = bn.
-__host__ __device__ constexpr uint32_t idesc_bf16(int bn) {
-  return (1u << 4)                     // D format F32
-         | (1u << 7)                   // A format BF16
-         | (1u << 10)                  // B format BF16
-         | ((uint32_t)(bn >> 3) << 17) // N >> 3
-         | ((uint32_t)(UM >> 4) << 24);// M >> 4
-}
-
-// Operand levels multiplied in each pass: split-BF16 with two levels (npass 3:
-// hi*hi, hi*lo, lo*hi) or three levels (npass 6: every product of levels
-// i + j <= 2, i.e. all terms above 2^-24 relative).
-__device__ __constant__ int kPassA[6] = {0, 0, 1, 0, 1, 2};
-__device__ __constant__ int kPassB[6] = {0, 1, 0, 2, 1, 0};
-
 // PRECISE (state-writing products, BN <= 64): each of the four K = 16 MMAs of
 // a stage has its own hi*hi accumulator, so with 64-element K splits every
 // accumulator takes a single step and the rest of the sum happens in FP32
