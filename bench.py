@@ -38,6 +38,11 @@ WORKLOADS = {
 FP32_SIMT_LANES_PER_SM = 128   # FP32 FMA lanes per SM
 N_SM = 152
 FP64_NOMINAL_TFLOPS = 1.25
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as
+# it stands (a full-size launch of `python bench.py --steps 1 --warmup 3
+# --forms bf16x6 --no-cpu-baseline --no-err --no-e2e`, grid 128, 2l = 2048);
+# the summary is committed under profiles/.  Set to None when the kernel changes.
+TRAFFIC_BYTES = {"batch_tc": 17.29e6 + 0.65e6}
 
 
 def _peaks():
@@ -239,7 +244,8 @@ def our_arm(args) -> None:
     tot_prof = sum(x["total_ms"] for x in prof if x["name"] != "eig_fp64") or 1.0
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = N_SM * FP32_SIMT_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    kinds = {"batch_persist": "fp32", "eig_tridiag": "fp64", "eig_backtransform": "fp64", "ingest": "hbm"}
+    kinds = {"batch_persist": "fp32", "batch_tc": "tensor", "eig_tridiag": "fp64", "eig_backtransform": "fp64",
+             "ingest": "hbm"}
     single = [x for x in prof if x["name"] in kinds and (x["flops"] > 0 or x["bytes"] > 0)]
     top = max(single, key=lambda x: x["total_ms"])
     kind = kinds[top["name"]]
@@ -247,6 +253,12 @@ def our_arm(args) -> None:
         ach = top["bytes"] / (top["total_ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
         src = f"{peak_src} copy bandwidth"
+    elif kind == "tensor":
+        # the useful flops (2 m_t^2 per column product); the kernel issues three
+        # split-BF16 passes of each, so the tensor pipe does 3x this work
+        ach = top["flops"] / (top["total_ms"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s"}
+        src = f"{peak_src} cuBLAS bf16 GEMM, sustained (the kernel runs inside a long step)"
     elif kind == "fp32":
         ach = top["flops"] / (top["total_ms"] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s"}
@@ -256,7 +268,8 @@ def our_arm(args) -> None:
         ach = top["flops"] / (top["total_ms"] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s"}
         src = "FP64 nominal 1.25 TFLOP/s (no FP64 measurement on this pool)"
-    roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": None, "kernel": top["name"],
+    roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": TRAFFIC_BYTES.get(top["name"]),
+                 "kernel": top["name"],
                  "launches": top["launches"], "avg_launch_us": 1000 * top["total_ms"] / max(1, top["launches"]),
                  "peak_source": src})
 

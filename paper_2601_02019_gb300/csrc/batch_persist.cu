@@ -441,14 +441,16 @@ __global__ void __launch_bounds__(kPThreads, 1) batch_persist_kernel(const Persi
 // Starting vectors (buffer 1 = the buffer iteration 0 reads): x^(0) of row t
 // (Philox purpose 3, counter (3, i0 + t, 0, e >> 2)) in column t, and the
 // test matrix Pi (n2 x 2 row-major, purpose 4, sub-index j = 1) of row t in
-// its pair's columns; zero below m_t.  Grid (nb, 2).
+// its pair's columns; zero below m_t.  Grid (nb, 2, z): the z blocks of a
+// column split its four-value Philox blocks (the FP64 Box-Muller transform is
+// slow on this part, so a column is spread over several SMs).
 __global__ void persist_fill_kernel(float* Y, int ldy, int mmax, int nb, int npi, int r0, Key key, uint64_t i0) {
   const int t = blockIdx.x, kind = blockIdx.y;
   const int m = r0 + t + 1;
   const uint64_t i = i0 + (uint64_t)t;
   if (kind == 0) {
     float* x = Y + (size_t)t * ldy;
-    for (int blk = threadIdx.x; blk * 4 < mmax; blk += blockDim.x) {
+    for (int blk = blockIdx.z * blockDim.x + threadIdx.x; blk * 4 < mmax; blk += blockDim.x * gridDim.z) {
       double z[4];
       gauss4(key, kPurposePiStart, i, 0, blk, z);
 #pragma unroll
@@ -459,11 +461,11 @@ __global__ void persist_fill_kernel(float* Y, int ldy, int mmax, int nb, int npi
     }
     if (t == nb - 1 && (nb & 1)) {   // padding column of the last power-iteration pair
       float* z = Y + (size_t)nb * ldy;
-      for (int p = threadIdx.x; p < mmax; p += blockDim.x) z[p] = 0.f;
+      for (int p = blockIdx.z * blockDim.x + threadIdx.x; p < mmax; p += blockDim.x * gridDim.z) z[p] = 0.f;
     }
   } else {
     float* x0 = Y + (size_t)(2 * npi + 2 * t) * ldy;
-    for (int blk = threadIdx.x; blk * 4 < 2 * mmax; blk += blockDim.x) {
+    for (int blk = blockIdx.z * blockDim.x + threadIdx.x; blk * 4 < 2 * mmax; blk += blockDim.x * gridDim.z) {
       double z[4];
       gauss4(key, kPurposeSiTest, i, 1, blk, z);
 #pragma unroll
@@ -505,7 +507,8 @@ size_t batch_persist_part_floats(int bmax) {
 
 void launch_persist_fill(cudaStream_t s, const PersistBuffers& pb, int mmax, int nb, int npi, int r0, Key key,
                          uint64_t i0) {
-  persist_fill_kernel<<<dim3(nb, 2), 128, 0, s>>>(pb.Y + pb.ybuf, pb.ldy, mmax, nb, npi, r0, key, i0);
+  const int zc = std::max(1, (2 * mmax / 4 + 127) / 128);
+  persist_fill_kernel<<<dim3(nb, 2, zc), 128, 0, s>>>(pb.Y + pb.ybuf, pb.ldy, mmax, nb, npi, r0, key, i0);
   count_launches(1);
 }
 
@@ -565,8 +568,7 @@ as_status launch_batch_persist(cudaStream_t s, const float* Gf, int n2, int r0, 
   plk.unlock();
 
   if (prof) prof->begin(PK_BATCH_ORTH, s);
-  persist_fill_kernel<<<dim3(nb, 2), 128, 0, s>>>(pb.Y + pb.ybuf, pb.ldy, mmax, nb, npi, r0, key, i0);
-  count_launches(1);
+  launch_persist_fill(s, pb, mmax, nb, npi, r0, key, i0);
   AS_CUDA_TRY(cudaGetLastError());
   if (prof) prof->end(PK_BATCH_ORTH, s, 0.0, 12.0 * mmax * (double)nb);
   AS_CUDA_TRY(cudaMemsetAsync(pb.cnt, 0, sizeof(unsigned), s));

@@ -40,7 +40,7 @@ namespace as {
 namespace {
 
 constexpr int kTcThreads = 256;
-constexpr int kTcStages = 4;
+constexpr int kTcStages = 2;   // ring stages; a stage holds one K tile of every level used
 constexpr int kTcSlots = 6;     // partial sums per pair
 constexpr int kTcMaxRpc = 32;   // rows per CTA in the reduction phase
 constexpr int kTcMaxCols = 192; // batch columns (2 P)
@@ -157,10 +157,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
                                                                  const __grid_constant__ UmmaOperand mY) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // stage s: [G level 0][G level 1][Y level 0][Y level 1] of one 64-wide K tile
   const uint32_t A_BYTES = UM * UK * 2;
   const uint32_t B_BYTES = (uint32_t)a.nc * UK * 2;
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + kTcStages * A_BYTES;
+  const uint32_t S_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   float* zs = reinterpret_cast<float*>(smem);   // reduction phase: reuses the ring
   __shared__ __align__(8) uint64_t full_bar[kTcStages];
   __shared__ __align__(8) uint64_t empty_bar[kTcStages];
@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
   const int P = a.npi + a.nb;
   const int k0 = ks * a.kc, k1 = min(a.kpad, k0 + a.kc);
   const int ktiles = (k1 > k0) ? (k1 - k0) / UK : 0;
-  const int niter = ktiles * NPASS;
+  const int niter = ktiles;   // one ring step per K tile; the NPASS level products share it
+  static_assert(NPASS == 3, "the ring holds two levels of each operand");
 
   if (tid == 0) {
     for (int s = 0; s < kTcStages; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
@@ -222,12 +223,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
         const int s = g % kTcStages;
         const uint32_t ph = (uint32_t)(g / kTcStages) & 1u;
         if (!mbar_wait(&empty_bar[s], ph ^ 1u)) { ok = false; break; }
-        const int kt = li / NPASS, pass = li - kt * NPASS;
-        const int kx = k0 + kt * UK;
-        const int la = (NPASS == 1) ? 0 : kPassA[pass], lb = (NPASS == 1) ? 0 : kPassB[pass];
-        mbar_expect_tx(&full_bar[s], A_BYTES + B_BYTES);
-        tma_load_2d(sA + s * A_BYTES, &mG.m[la], &full_bar[s], kx, rb * UM);
-        tma_load_2d(sB + s * B_BYTES, &mY.m[lb], &full_bar[s], kx, bold * a.ycols);
+        const int kx = k0 + li * UK;
+        uint8_t* st = smem + (size_t)s * S_BYTES;
+        mbar_expect_tx(&full_bar[s], S_BYTES);
+        tma_load_2d(st, &mG.m[0], &full_bar[s], kx, rb * UM);
+        tma_load_2d(st + A_BYTES, &mG.m[1], &full_bar[s], kx, rb * UM);
+        tma_load_2d(st + 2 * A_BYTES, &mY.m[0], &full_bar[s], kx, bold * a.ycols);
+        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mY.m[1], &full_bar[s], kx, bold * a.ycols);
       }
       if (!ok) atomicExch(&fail_s, 1);
     } else if (warp == 1 && lane == 0 && niter > 0) {
@@ -238,19 +240,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
         const uint32_t ph = (uint32_t)(g / kTcStages) & 1u;
         if (!mbar_wait(&full_bar[s], ph)) { atomicExch(&fail_s, 1); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
-        const int pass = li % NPASS;
+        const uint32_t st = smem_u32(smem + (size_t)s * S_BYTES);
+        // level products G0 Y0 (leading accumulator), G0 Y1 and G1 Y0 (corrections)
 #pragma unroll
-        for (int kk = 0; kk < UK / 16; ++kk) {
-          const int aidx = (pass == 0) ? 0 : 1;
-          const bool first = (pass == 0) ? (li == 0 && kk == 0) : (li == 1 && kk == 0);
-          const uint32_t dst = tmem + (uint32_t)(aidx * a.nc);
-          const uint64_t da = smem_desc(a0 + kk * 32), db = smem_desc(b0 + kk * 32);
-          const uint32_t acc = first ? 0u : 1u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
-              "l"(da), "l"(db), "r"(idesc), "r"(acc));
+        for (int pass = 0; pass < 3; ++pass) {
+          const uint32_t a0 = st + (pass == 2 ? A_BYTES : 0u);
+          const uint32_t b0 = st + 2 * A_BYTES + (pass == 1 ? B_BYTES : 0u);
+#pragma unroll
+          for (int kk = 0; kk < UK / 16; ++kk) {
+            const int aidx = (pass == 0) ? 0 : 1;
+            const bool first = (li == 0) && (kk == 0) && (pass <= 1);
+            const uint32_t dst = tmem + (uint32_t)(aidx * a.nc);
+            const uint64_t da = smem_desc(a0 + kk * 32), db = smem_desc(b0 + kk * 32);
+            const uint32_t acc = first ? 0u : 1u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
+                "l"(da), "l"(db), "r"(idesc), "r"(acc));
+          }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&empty_bar[s]))
@@ -349,7 +356,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
         if (have) {
 #pragma unroll
           for (int acc = 0; acc < 2; ++acc) {
-            if (acc == 1 && NPASS == 1) break;
             uint32_t r[16];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + acc * a.nc);
             asm volatile(
@@ -536,7 +542,7 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
   const int kpad = (mmax + 127) / 128 * 128;
   const int ncols = 2 * P;
   const int nc = (ncols + 15) / 16 * 16;
-  if (kpad < 256 || nc > kTcMaxCols || nc > (int)pb.ycols || (npass != 3 && npass != 6)) return AS_OK;
+  if (kpad < 256 || nc > kTcMaxCols || nc > (int)pb.ycols || npass != 3) return AS_OK;
   int dev = 0;
   AS_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return AS_OK;
@@ -553,9 +559,9 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
   const int ncta = nrb * nks;
   const int rpc = (kpad + ncta - 1) / ncta;
   if (nks > 16 || ncta > td.sms || rpc > kTcMaxRpc) return AS_OK;
-  const size_t smem = 1024 + (size_t)kTcStages * (UM * UK * 2 + (size_t)nc * UK * 2);
-  const int v = (npass == 6) ? 1 : 0;
-  const void* fn = v ? (const void*)batch_tc_kernel<6> : (const void*)batch_tc_kernel<3>;
+  const size_t smem = 1024 + (size_t)kTcStages * 2 * (UM * UK * 2 + (size_t)nc * UK * 2);
+  const int v = 0;
+  const void* fn = (const void*)batch_tc_kernel<3>;
   if (smem > td.attr[v]) {
     AS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     td.attr[v] = smem;
@@ -592,7 +598,7 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
   a.kpad = kpad; a.nrb = nrb; a.nks = nks; a.kc = kc; a.nc = nc; a.rpc = rpc;
   a.sig2 = pb.sig2; a.ritz = pb.ritz;
   void* args[] = {&a, (void*)&tb.mG, &mY};
-  if (prof) prof->begin(PK_BATCH_GEMM, s);
+  if (prof) prof->begin(PK_BATCH_TC, s);
   AS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(ncta), dim3(kTcThreads), args, smem, s));
   count_launches(1);
   if (prof) {
@@ -603,7 +609,7 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
       m1 += m;
     }
     const double prods = (double)(k_pi + 1) + 2.0 * (double)(q + 1);
-    prof->end(PK_BATCH_GEMM, s, 2.0 * m2 * prods, 2.0 * npass / 3.0 * (double)kpad * kpad + 8.0 * m1 * prods);
+    prof->end(PK_BATCH_TC, s, 2.0 * m2 * prods, 2.0 * npass / 3.0 * (double)kpad * kpad + 8.0 * m1 * prods);
   }
   *used = true;
   return AS_OK;

@@ -59,7 +59,7 @@ namespace {
 const char* const kProfNames[PK_COUNT] = {"batch_persist",     "batch_prep",        "eig_fp64",
                                           "fd_rebuild_gemm",   "gram_rows_gemm",    "ingest",
                                           "event_row_fp64",    "eig_tridiag",       "eig_bisect_invit",
-                                          "eig_backtransform"};
+                                          "eig_backtransform", "batch_tc"};
 
 // CUDA-event timer per kernel class; pairs are resolved lazily.
 struct EventProf final : Prof {
@@ -383,11 +383,23 @@ as_status dump(as_sketch* h, int xi, int k, int64_t i) {
   float* Y = Z + (size_t)d * xi;
   st = ensure_dwork(h, dump_work_doubles(d, n2, xi));
   if (st != AS_OK) return st;
-  st = launch_dump(h->s, h->C, ldc, d, r, h->G, n2, h->si.WU, h->si.GWU, k, xi, Z, Y, h->dwork);
+  // the residual and the Gram downdate also refresh the BF16 levels of C and
+  // the mirrors of G (FP32, and BF16 for the tcgen05 batch) in their passes
+  DumpMirrors mir;
+  if (h->tc) {
+    mir.c0 = h->Chi;
+    mir.c1 = h->Clo;
+    mir.c2 = h->Cl2;
+  }
+  mir.gf = h->Gf;
+  if (h->tcb) {
+    mir.gb = h->tb.Gb;
+    mir.glevel = h->tb.glevel;
+    mir.ldg = h->tb.ldg;
+  }
+  st = launch_dump(h->s, h->C, ldc, d, r, h->G, n2, h->si.WU, h->si.GWU, k, xi, Z, Y, h->dwork, mir);
   if (st != AS_OK) return st;
-  h->gf_valid = 0;
-  st = tc_split_rows(h, 0, r);
-  if (st != AS_OK) return st;
+  h->gf_valid = r;   // rows and columns [0, r) of both mirrors were rewritten with G
   const int64_t s_prev = h->snaps.empty() ? 1 : h->snaps.back().t + 1;
   h->snaps.push_back(Snap{h->arena_used, xi, s_prev, i});
   h->arena_used += (size_t)2 * d * xi;

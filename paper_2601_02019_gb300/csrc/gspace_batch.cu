@@ -279,18 +279,28 @@ __global__ void dump_partial_kernel(const float* __restrict__ C, int ldc, int d,
 #pragma unroll
   for (int a = 0; a < 8; ++a) { z[a] = 0.0; y[a] = 0.0; zf[a] = 0.f; yf[a] = 0.f; }
   int cnt = 0;
-  for (int p = pb; p < pe; ++p) {
-    const float cv = C[(size_t)p * ldc + c];
+  // eight rows at a time: their loads of C go out together (one load per row
+  // and thread would leave the kernel waiting on memory latency)
+  for (int p8 = pb; p8 < pe; p8 += 8) {
+    float cv[8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
-      if (a < na) {
-        zf[a] = fmaf(cv, WUf[(size_t)p * xi + a0 + a], zf[a]);
-        yf[a] = fmaf(cv, GWUf[(size_t)p * xi + a0 + a], yf[a]);
+    for (int u = 0; u < 8; ++u) cv[u] = (p8 + u < pe) ? C[(size_t)(p8 + u) * ldc + c] : 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int p = p8 + u;
+      if (p < pe) {
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+          if (a < na) {
+            zf[a] = fmaf(cv[u], WUf[(size_t)p * xi + a0 + a], zf[a]);
+            yf[a] = fmaf(cv[u], GWUf[(size_t)p * xi + a0 + a], yf[a]);
+          }
+        if (++cnt == 64) {   // FP32 partial sums of 64 rows, combined in FP64
+          cnt = 0;
+#pragma unroll
+          for (int a = 0; a < 8; ++a) { z[a] += zf[a]; y[a] += yf[a]; zf[a] = 0.f; yf[a] = 0.f; }
+        }
       }
-    if (++cnt == 64) {   // FP32 partial sums of 64 rows, combined in FP64
-      cnt = 0;
-#pragma unroll
-      for (int a = 0; a < 8; ++a) { z[a] += zf[a]; y[a] += yf[a]; zf[a] = 0.f; yf[a] = 0.f; }
     }
   }
 #pragma unroll
@@ -318,8 +328,12 @@ __global__ void dump_reduce_kernel(const double* Zp, const double* Yp, int d, in
 // C[p][c] -= sum_a GWU[p][a] Z[c][a]   (the residual C' - C' Z Z^T), as an
 // FMA chain in FP32 with GWU split into hi + lo: each term enters with one
 // rounding, so a strongly cancelling entry keeps its relative accuracy.
+// With the tensor forms, the BF16 levels of the new entries (x0 = bf16(x),
+// x1 = bf16(x - x0), x2 = bf16(x - x0 - x1); l2 may be null) are written in
+// the same pass.
 __global__ void residual_kernel(float* C, int ldc, int d, int r, const float* __restrict__ GWUf,
-                                const float* __restrict__ GWUlo, int xi, const float* Z) {
+                                const float* __restrict__ GWUlo, int xi, const float* Z, __nv_bfloat16* l0,
+                                __nv_bfloat16* l1, __nv_bfloat16* l2) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   if (c >= d || p >= r) return;
@@ -329,7 +343,16 @@ __global__ void residual_kernel(float* C, int ldc, int d, int r, const float* __
     v = fmaf(-GWUf[(size_t)p * xi + a], z, v);
     v = fmaf(-GWUlo[(size_t)p * xi + a], z, v);
   }
-  C[(size_t)p * ldc + c] = v;
+  const size_t o = (size_t)p * ldc + c;
+  C[o] = v;
+  if (l0) {
+    const __nv_bfloat16 a0 = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(a0);
+    const __nv_bfloat16 a1 = __float2bfloat16_rn(r1);
+    l0[o] = a0;
+    l1[o] = a1;
+    if (l2) l2[o] = __float2bfloat16_rn(r1 - __bfloat162float(a1));
+  }
 }
 
 // R[p][q] = G[p][q] - sum_{a < xi} GWU[p][a] GWU[q][a] for p, q < m (the Gram
@@ -343,14 +366,27 @@ __global__ void residual_gram_kernel(const double* G, int n2, int m, const doubl
   R[(size_t)p * n2 + q] = acc;
 }
 
-// G[p][q] -= sum_a GWU[p][a] GWU[q][a]
-__global__ void gram_downdate_kernel(double* G, int n2, int r, const double* GWU, int k, int xi) {
+// G[p][q] -= sum_a GWU[p][a] GWU[q][a], and the same entries of the FP32
+// mirror (Gf, ld n2) and of the BF16 levels (Gb, ld ldg, glevel apart) when given.
+__global__ void gram_downdate_kernel(double* G, int n2, int r, const double* GWU, int k, int xi, float* Gf,
+                                     __nv_bfloat16* Gb, long long glevel, int ldg) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   if (q >= r || p >= r) return;
   double acc = 0.0;
   for (int a = 0; a < xi; ++a) acc += GWU[(size_t)p * k + a] * GWU[(size_t)q * k + a];
-  G[(size_t)p * n2 + q] -= acc;
+  const double x = G[(size_t)p * n2 + q] - acc;
+  G[(size_t)p * n2 + q] = x;
+  if (Gf) Gf[(size_t)p * n2 + q] = (float)x;
+  if (Gb) {
+    const __nv_bfloat16 b0 = __double2bfloat16(x);
+    const double r1 = x - (double)__bfloat162float(b0);
+    const __nv_bfloat16 b1 = __double2bfloat16(r1);
+    __nv_bfloat16* o = Gb + (size_t)p * ldg + q;
+    o[0] = b0;
+    o[glevel] = b1;
+    o[2 * glevel] = __double2bfloat16(r1 - (double)__bfloat162float(b1));
+  }
 }
 
 }  // namespace
@@ -437,7 +473,6 @@ as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m
 as_status launch_residual_gram(cudaStream_t s, const double* G, int n2, int m, const double* GWU, int k, int xi,
                                double* R) {
   if (m <= 0) return AS_OK;
-  if (m <= 0) return AS_OK;
   residual_gram_kernel<<<dim3((m + 255) / 256, m), 256, 0, s>>>(G, n2, m, GWU, k, xi, R); count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;
@@ -449,7 +484,7 @@ size_t dump_work_doubles(int d, int n2, int xi) {
 }
 
 as_status launch_dump(cudaStream_t s, float* C, int ldc, int d, int r, double* G, int n2, const double* WU,
-                      const double* GWU, int k, int xi, float* Z, float* Y, double* work) {
+                      const double* GWU, int k, int xi, float* Z, float* Y, double* work, const DumpMirrors& mir) {
   const int wmax = std::min(xi, kDumpBlock);
   double* Zp = work;
   double* Yp = work + (size_t)kDumpChunks * d * wmax;
@@ -470,8 +505,12 @@ as_status launch_dump(cudaStream_t s, float* C, int ldc, int d, int r, double* G
     dump_reduce_kernel<<<(d * w + 255) / 256, 256, 0, s>>>(Zp, Yp, d, xi, ab, w, Z, Y); count_launches(1);
   }
   if (r > 0) {
-    residual_kernel<<<dim3((d + 255) / 256, r), 256, 0, s>>>(C, ldc, d, r, GWUf, GWUlo, xi, Z); count_launches(1);
-    gram_downdate_kernel<<<dim3((r + 255) / 256, r), 256, 0, s>>>(G, n2, r, GWU, k, xi); count_launches(1);
+    residual_kernel<<<dim3((d + 255) / 256, r), 256, 0, s>>>(C, ldc, d, r, GWUf, GWUlo, xi, Z, mir.c0, mir.c1,
+                                                             mir.c2);
+    count_launches(1);
+    gram_downdate_kernel<<<dim3((r + 255) / 256, r), 256, 0, s>>>(G, n2, r, GWU, k, xi, mir.gf, mir.gb, mir.glevel,
+                                                                  mir.ldg);
+    count_launches(1);
   }
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;

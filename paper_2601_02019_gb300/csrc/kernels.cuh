@@ -22,6 +22,7 @@ enum ProfClass {
   PK_EIG_TRI,         // eigensolver phase: tridiagonalisation
   PK_EIG_SOLVE,       // eigensolver phase: bisection, inverse iteration, cluster MGS
   PK_EIG_BACK,        // eigensolver phase: back-transformation
+  PK_BATCH_TC,        // batched G-space iterations on tcgen05 (tensor forms)
   PK_COUNT
 };
 struct Prof {
@@ -105,8 +106,18 @@ as_status launch_gram_rows_skinny(cudaStream_t s, const float* C, int ldc, int d
 // (row-major n2 x k): Z = C'^T (WU)_xi, Y = (GWU)_xi^T C', C -= (GWU)_xi Z^T,
 // G -= (GWU)_xi (GWU)_xi^T.  work: dump_work_doubles(d, n2, xi).
 size_t dump_work_doubles(int d, int n2, int xi);
+// Copies of C and G the dump keeps in step in the same passes (null: none):
+// the BF16 levels of C (ld ldc), the FP32 mirror of G (ld n2) and its BF16
+// levels (ld ldg, glevel elements apart).
+struct DumpMirrors {
+  __nv_bfloat16 *c0 = nullptr, *c1 = nullptr, *c2 = nullptr;
+  float* gf = nullptr;
+  __nv_bfloat16* gb = nullptr;
+  long long glevel = 0;
+  int ldg = 0;
+};
 as_status launch_dump(cudaStream_t s, float* C, int ldc, int d, int r, double* G, int n2, const double* WU,
-                      const double* GWU, int k, int xi, float* Z, float* Y, double* work);
+                      const double* GWU, int k, int xi, float* Z, float* Y, double* work, const DumpMirrors& mir);
 
 // FP32 mirror of the leading m x m block of G for the rows/columns at or past
 // `valid` (the leading valid x valid block is already mirrored).
