@@ -358,6 +358,10 @@ EXTRA = {
     # chosen sessions; a saturation phase measures capacity, then Poisson
     # arrivals at three fractions of it give the latency percentiles
     "serve_c4_s2000": dict(sessions=2000, requests=2000, loads=(0.5, 0.8, 0.95), pool_rows=4096, dmax=8192),
+    # many sketches in one launch: the C3 rows of 16 sites fed through
+    # sketch_update_grouped (lockstep blocks, grouped batched iterations),
+    # beside sketch_update_many (each sketch independent on a worker thread)
+    "group_d512_l64_m16": dict(d=512, ell=64, m=16, rows_per_site=256),
 }
 
 
@@ -466,6 +470,57 @@ def serve_arm(args) -> None:
     }))
 
 
+def group_arm(args) -> None:
+    """sketch_update_grouped over 16 sketches (lockstep blocks, grouped
+    launches) and, on fresh sketches, the same rows through sketch_update_many
+    (each sketch progressing independently on a worker thread).
+    Both calls return after their work is done, so each step is timed on the
+    host clock with the device synchronised on both sides."""
+    import torch
+
+    import paper_2601_02019_gb300 as p
+    w = EXTRA[args.workload]
+    K, W = args.steps, args.warmup
+    torch.cuda.set_device(0)
+    rows = [torch.from_numpy(x).cuda() for x in _p5_rows(w, W + K, seed=0)]
+    b, m, d, ell = w["rows_per_site"], w["m"], w["d"], w["ell"]
+
+    def make():
+        return [p.Sketch(d, ell, stream_id=j, stream=torch.cuda.Stream()) for j in range(m)]
+
+    def grouped(sks, k):
+        p.update_grouped(sks, [x[k * b:(k + 1) * b] for x in rows])
+
+    def threaded(sks, k):
+        p.update_many(sks, [x[k * b:(k + 1) * b] for x in rows])
+
+    out = {}
+    with ClockSampler(0) as clk:
+        for name, fn in (("grouped", grouped), ("independent", threaded)):
+            sks = make()
+            for k in range(W):
+                fn(sks, k)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(W, W + K):
+                fn(sks, k)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            out[name] = {"rows_per_s": K * b * m / dt, "ms_per_step": 1e3 * dt / K,
+                         "grouped_batches": int(sum(x.stats()["grouped_batches"] for x in sks))}
+    print(json.dumps({
+        "metric": "rows/s of sketch_update_grouped (16 sketches, grouped launches)",
+        "value": out["grouped"]["rows_per_s"],
+        "unit": "rows/s", "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": out["grouped"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 products, f64 core",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "d": d, "ell": ell, "sketches": m, "rows_per_sketch_per_step": b,
+                   "timing": "host clock around synchronous calls, device synchronised on both sides",
+                   "l2": "per-sketch state far below L2; rows resident in HBM"},
+        "modes": out, "clocks": clk.summary(),
+    }))
+
+
 def extra_arm(args) -> None:
     import torch
 
@@ -543,6 +598,8 @@ def main() -> None:
             print(json.dumps({"impl": "reference", "unavailable": "the oracle arm is timed on the headline workload"}))
         elif args.workload.startswith("serve"):
             serve_arm(args)
+        elif args.workload.startswith("group"):
+            group_arm(args)
         else:
             extra_arm(args)
     elif args.impl == "reference":

@@ -11,4 +11,4 @@ fails if the library has not been built.
 from .binding import (AS_BF16, AS_BF16X3, AS_BF16X6, AS_COORDINATOR, AS_FIXED_THETA, AS_FP32_PLAIN,  # noqa: F401
                       AS_PERSISTENT, AS_PROFILE, AS_SITE, AS_TRACE_DECISIONS, AsConfig, AsEvent, AsStats,
                       AeroSketchError, P5, Server, Sketch, SlidingWindow, footprint, lib, load_library,
-                      update_many)
+                      update_grouped, update_many)

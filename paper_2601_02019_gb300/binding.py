@@ -22,7 +22,8 @@ EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram
             "sketch_set_theta", "sketch_send_snapshots", "as_p5_create", "as_p5_round", "as_p5_query",
             "as_p5_query_gram", "as_p5_stats", "as_p5_site", "as_p5_coordinator", "as_p5_destroy",
             "as_sw_create", "as_sw_update", "as_sw_query", "as_sw_query_gram", "as_sw_stats", "as_sw_level",
-            "as_sw_destroy", "sketch_footprint", "sketch_reserve", "sketch_update_many", "as_server_create",
+            "as_sw_destroy", "sketch_footprint", "sketch_reserve", "sketch_update_many", "sketch_update_grouped",
+            "as_server_create",
             "as_server_open", "as_server_submit", "as_server_wait", "as_server_drain", "as_server_session",
             "as_server_close", "as_server_stats", "as_server_reset_stats", "as_server_destroy")
 
@@ -51,7 +52,8 @@ class AsStats(ct.Structure):
                 ("shrinks", ct.c_int64), ("gates", ct.c_int64), ("dumps", ct.c_int64),
                 ("snapshot_rank", ct.c_int64), ("si_runs", ct.c_int64), ("device_bytes", ct.c_int64),
                 ("device_status", ct.c_int32), ("reserved1", ct.c_int32), ("kernel_launches", ct.c_int64),
-                ("snapshots_sent", ct.c_int64), ("snapshots_received", ct.c_int64)]
+                ("snapshots_sent", ct.c_int64), ("snapshots_received", ct.c_int64),
+                ("grouped_batches", ct.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
@@ -136,6 +138,7 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.sketch_footprint.argtypes = [ct.POINTER(AsConfig), I64, ct.POINTER(I64)]
     L.sketch_reserve.argtypes = [P, I64]
     L.sketch_update_many.argtypes = [ct.POINTER(P), ct.POINTER(P), ct.POINTER(I64), ct.POINTER(I64), I32]
+    L.sketch_update_grouped.argtypes = [ct.POINTER(P), ct.POINTER(P), ct.POINTER(I64), ct.POINTER(I64), I32]
     L.as_server_create.argtypes = [ct.POINTER(AsServerConfig), ct.POINTER(P)]
     L.as_server_open.argtypes = [P, ct.POINTER(AsConfig), ct.c_double, ct.POINTER(I64)]
     L.as_server_submit.argtypes = [P, I64, P, I64, I64, ct.POINTER(I64)]
@@ -409,9 +412,7 @@ def footprint(d: int, ell: int = 0, eps: float = 0.0, *, prec: int = AS_FP32_PLA
     return b.value
 
 
-def update_many(sketches: list, blocks: list) -> None:
-    """sketch_update_many: sketch k gets blocks[k]; the sketches run concurrently
-    on the library's worker threads, each on its own stream."""
+def _many(fn: str, sketches: list, blocks: list) -> None:
     assert len(sketches) == len(blocks)
     k = len(sketches)
     hs = (ct.c_void_p * max(1, k))(*[s._h.value for s in sketches])
@@ -419,7 +420,19 @@ def update_many(sketches: list, blocks: list) -> None:
     rp = (ct.c_void_p * max(1, k))(*[a[0] for a in args])
     ns = (ct.c_int64 * max(1, k))(*[a[1] for a in args])
     lds = (ct.c_int64 * max(1, k))(*[a[2] for a in args])
-    _check(lib().sketch_update_many(hs, rp, ns, lds, k), "sketch_update_many")
+    _check(getattr(lib(), fn)(hs, rp, ns, lds, k), fn)
+
+
+def update_many(sketches: list, blocks: list) -> None:
+    """sketch_update_many: sketch k gets blocks[k]; the sketches progress
+    independently on the library's worker threads, each on its own stream."""
+    _many("sketch_update_many", sketches, blocks)
+
+
+def update_grouped(sketches: list, blocks: list) -> None:
+    """sketch_update_grouped: the same update in lockstep blocks whose batched
+    iterations share cooperative launches (bitwise the same results)."""
+    _many("sketch_update_grouped", sketches, blocks)
 
 
 class Server:

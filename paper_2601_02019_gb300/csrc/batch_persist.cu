@@ -50,6 +50,7 @@ constexpr int kPairsPerUnit = 4;     // a warp unit: 4 column pairs (8 columns) 
 constexpr int kMaxUnits = 64;
 constexpr int kSlots = 6;            // partial sums per pair
 constexpr int kMaxGrid = 1024;
+constexpr int kMaxGroup = 32;        // problems in one grouped launch
 
 struct PersistArgs {
   const float* G;      // FP32 copy of the leading mmax x mmax block of G (row-major, ld ldg)
@@ -124,11 +125,15 @@ __device__ __forceinline__ void eig2_sym(double s00, double s01, double s11, dou
 
 // Shared memory (floats): [Gs: kTile x mpad, GSMEM only] [coef: 4 per pair]
 // [red: kMaxUnits x 128] [Ys: 2 * pairs x kTile].
+// The body of one problem: G CTAs (this one is blk of them) iterate to
+// `iters` (at least the problem's own max(k_pi, q); a grouped launch runs to
+// the largest of its problems and a problem idles past its own), meeting the
+// other CTAs of the launch (gtotal in all) at each grid barrier.
 template <bool GSMEM>
-__global__ void __launch_bounds__(kPThreads, 1) batch_persist_kernel(const PersistArgs a) {
+__device__ __forceinline__ void persist_body(const PersistArgs& a, const int G, const int blk, const int iters,
+                                             const unsigned gtotal) {
   extern __shared__ __align__(16) float sm[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int G = gridDim.x, blk = blockIdx.x;
   const int P = a.npi + a.nb;
   const int mpad = (a.mmax + 3) & ~3;
   float* Gs = sm;
@@ -144,7 +149,6 @@ __global__ void __launch_bounds__(kPThreads, 1) batch_persist_kernel(const Persi
       Gs[e] = (r < R && k < a.mmax) ? a.G[(size_t)(row0 + r) * a.ldg + k] : 0.f;
     }
   }
-  const int iters = max(a.k_pi, a.q);
   for (int it = 0; it <= iters; ++it) {
     const bool pi_on = it <= a.k_pi, si_on = it <= a.q;
     const int pa0 = pi_on ? 0 : a.npi, pa1 = si_on ? P : a.npi;
@@ -392,7 +396,7 @@ __global__ void __launch_bounds__(kPThreads, 1) batch_persist_kernel(const Persi
 #pragma unroll
       for (int e = 0; e < kSlots; ++e) pnew[(size_t)(p * kSlots + e) * G + blk] = ps[e];
     }
-    if (!grid_barrier(a.cnt, (unsigned)(it + 1) * (unsigned)G, a.status)) return;
+    if (!grid_barrier(a.cnt, (unsigned)(it + 1) * gtotal, a.status)) return;
 
     // final values (FP64 over the CTAs), spread over the CTAs
     if (pi_on && it == a.k_pi && warp == 0) {
@@ -436,6 +440,29 @@ __global__ void __launch_bounds__(kPThreads, 1) batch_persist_kernel(const Persi
       }
     }
   }
+}
+
+template <bool GSMEM>
+__global__ void __launch_bounds__(kPThreads, 1) batch_persist_kernel(const PersistArgs a) {
+  persist_body<GSMEM>(a, gridDim.x, blockIdx.x, max(a.k_pi, a.q), gridDim.x);
+}
+
+// Many sketches' blocks in one cooperative launch: problem j owns CTAs
+// [cta0[j], cta0[j+1]), one 16-row tile each with its rows of G in shared
+// memory (the same CTAs and arithmetic as its own launch, so its results are
+// bitwise those of running it alone); every CTA meets all others at the
+// shared grid barrier.
+struct GroupArgs {
+  PersistArgs p[kMaxGroup];
+  int cta0[kMaxGroup + 1];
+  int n;
+  int iters;
+};
+
+__global__ void __launch_bounds__(kPThreads, 1) batch_group_kernel(const __grid_constant__ GroupArgs g) {
+  int j = 0;
+  while (j + 1 < g.n && (int)blockIdx.x >= g.cta0[j + 1]) ++j;
+  persist_body<true>(g.p[j], g.cta0[j + 1] - g.cta0[j], (int)blockIdx.x - g.cta0[j], g.iters, gridDim.x);
 }
 
 // Starting vectors (buffer 1 = the buffer iteration 0 reads): x^(0) of row t
@@ -485,6 +512,8 @@ struct PersistDevice {
   int optin = 0;                   // opt-in shared memory per block
   int stat[2] = {-1, -1};          // static shared memory of each variant
   size_t attr[2] = {0, 0};         // dynamic shared memory limit set so far
+  int gstat = 0;                   // the grouped kernel's static shared memory
+  size_t gattr = 0;                // and its dynamic limit set so far
 };
 PersistDevice g_pdev[64];
 std::mutex g_pdev_mu;   // guards g_pdev (sketches may run from several host threads)
@@ -510,6 +539,90 @@ void launch_persist_fill(cudaStream_t s, const PersistBuffers& pb, int mmax, int
   const int zc = std::max(1, (2 * mmax / 4 + 127) / 128);
   persist_fill_kernel<<<dim3(nb, 2, zc), 128, 0, s>>>(pb.Y + pb.ybuf, pb.ldy, mmax, nb, npi, r0, key, i0);
   count_launches(1);
+}
+
+int batch_group_capacity() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return 0; }
+  std::lock_guard<std::mutex> lk(g_pdev_mu);
+  PersistDevice& pd = g_pdev[dev];
+  if (pd.sms == 0 && cudaDeviceGetAttribute(&pd.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return pd.sms;   // one CTA per SM (255 registers x 256 threads)
+}
+
+int batch_group_tiles(const BatchJob& j) {
+  const int mmax = j.r0 + j.nb;
+  if (j.nb <= 0 || mmax > j.n2 || (size_t)2 * ((j.nb + 1) / 2 + j.nb) > j.pb.ycols || j.nb > j.pb.bmax) return 0;
+  return (mmax + kTile - 1) / kTile;
+}
+
+as_status launch_batch_group(cudaStream_t s, const BatchJob* jobs, int n, unsigned* cnt) {
+  if (n <= 0) return AS_OK;
+  if (n > kMaxGroup) return AS_EINVAL;
+  int dev = 0;
+  AS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return AS_EINVAL;
+  GroupArgs g{};
+  size_t smax = 0;
+  int total = 0, iters = 0;
+  for (int j = 0; j < n; ++j) {
+    const BatchJob& b = jobs[j];
+    const int tiles = batch_group_tiles(b);
+    if (tiles <= 0) return AS_EINVAL;
+    const int mmax = b.r0 + b.nb, npi = (b.nb + 1) / 2, P = npi + b.nb;
+    smax = std::max(smax, persist_smem_bytes(true, mmax, P));
+    PersistArgs& a = g.p[j];
+    a.G = b.Gf; a.ldg = b.n2; a.mmax = mmax;
+    a.Y = b.pb.Y; a.ybuf = b.pb.ybuf; a.ldy = b.pb.ldy;
+    a.X = b.pb.X; a.ldx = b.n2;
+    a.part = b.pb.part; a.pbuf = (long long)kSlots * P * tiles;
+    a.cnt = cnt; a.status = b.status;
+    a.nb = b.nb; a.npi = npi; a.r0 = b.r0; a.k_pi = b.k_pi; a.q = b.q;
+    a.ntiles = tiles;
+    a.sig2 = b.pb.sig2; a.ritz = b.pb.ritz;
+    g.cta0[j] = total;
+    total += tiles;
+    iters = std::max(iters, std::max(b.k_pi, b.q));
+  }
+  g.cta0[n] = total;
+  g.n = n;
+  g.iters = iters;
+  {
+    std::unique_lock<std::mutex> plk(g_pdev_mu);
+    PersistDevice& pd = g_pdev[dev];
+    if (pd.sms == 0) {
+      AS_CUDA_TRY(cudaDeviceGetAttribute(&pd.sms, cudaDevAttrMultiProcessorCount, dev));
+      AS_CUDA_TRY(cudaDeviceGetAttribute(&pd.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    }
+    if (pd.optin == 0) AS_CUDA_TRY(cudaDeviceGetAttribute(&pd.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (pd.gattr == 0) {
+      cudaFuncAttributes fa{};
+      AS_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)batch_group_kernel));
+      pd.gstat = (int)fa.sharedSizeBytes;
+    }
+    if (smax + (size_t)pd.gstat > (size_t)pd.optin) return AS_ENOTSUP;
+    if (smax > pd.gattr) {
+      AS_CUDA_TRY(cudaFuncSetAttribute((const void*)batch_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smax));
+      pd.gattr = smax;
+    }
+    int per = 0;
+    AS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_group_kernel, kPThreads, smax));
+    if ((long long)per * pd.sms < total) return AS_ENOTSUP;
+  }
+  for (int j = 0; j < n; ++j) {
+    const BatchJob& b = jobs[j];
+    launch_persist_fill(s, b.pb, b.r0 + b.nb, b.nb, (b.nb + 1) / 2, b.r0, b.key, b.i0);
+  }
+  AS_CUDA_TRY(cudaGetLastError());
+  AS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned), s));
+  void* args[] = {&g};
+  AS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)batch_group_kernel, dim3(total), dim3(kPThreads), args, smax, s));
+  count_launches(1);
+  return AS_OK;
 }
 
 as_status launch_batch_persist(cudaStream_t s, const float* Gf, int n2, int r0, int nb, int k_pi, int q, Key key,

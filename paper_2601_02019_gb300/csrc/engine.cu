@@ -16,6 +16,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "eig.cuh"
@@ -528,10 +529,23 @@ as_status finish_row(as_sketch* h, int64_t i, double theta, int known_gate, doub
 // that row, and it is finished in FP64.  Returns the rows consumed in *used.
 constexpr double kTieBand = 1e-4;
 
-as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t* used, bool* bad_row) {
+// A block between its launch phase and its decision phase.
+struct BlockCtx {
+  int b = 0, nbb = 0, r0 = 0;
+  bool deferred = false;   // the FP32 batched iterations are left to the caller (a grouped launch)
+};
+
+// Launch phase of one block (Algorithm 8 lines 1-3 and Algorithm 4 lines 1, 7
+// and the first doubling step of 9-11 for every row, speculatively): ingest,
+// Gram rows, mirrors of G and the batched iterations.  With defer, a block
+// that would run the FP32 persistent kernel is left for a grouped launch
+// (block_job describes it).
+as_status block_prepare(as_sketch* h, const float* src, int64_t navail, BlockCtx& c, bool defer) {
   const int d = h->d, n2 = h->n2, r0 = h->r;
-  *bad_row = false;
   const int b = (int)std::min<int64_t>({navail, (int64_t)(n2 - r0), (int64_t)h->bnext});
+  c.b = b;
+  c.r0 = r0;
+  c.deferred = false;
   if (h->prof) h->prof->begin(PK_INGEST, h->s);
   as_status st = launch_ingest(h->s, src, d, b, d, h->C, h->ldc, r0, h->norm2, h->bad);
   if (st != AS_OK) return st;
@@ -549,6 +563,7 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
     h->prof->end(PK_GRAM, h->s, 2.0 * (r0 + b) * (double)b * d, 4.0 * (r0 + b) * (double)d + 8.0 * (r0 + b) * b);
   const bool fills_all = (r0 + b == n2);
   const int nbb = fills_all ? b - 1 : b;   // batched rows (the filling row needs the shrink first)
+  c.nbb = nbb;
   if (nbb > 0) {
     if (h->prof) h->prof->begin(PK_BATCH_ORTH, h->s);
     st = launch_gf_mirror(h->s, h->G, h->Gf, n2, h->gf_valid, r0 + nbb);
@@ -572,13 +587,41 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
       if (st != AS_OK) return st;
     }
     if (!on_tc) {
-      st = launch_batch_persist(h->s, h->Gf, n2, r0, nbb, h->k_pi, h->q, h->key, (uint64_t)(h->T + 1), h->pb,
-                                h->dstatus, h->prof);
-      if (st != AS_OK) return st;
+      if (defer) {
+        c.deferred = true;
+      } else {
+        st = launch_batch_persist(h->s, h->Gf, n2, r0, nbb, h->k_pi, h->q, h->key, (uint64_t)(h->T + 1), h->pb,
+                                  h->dstatus, h->prof);
+        if (st != AS_OK) return st;
+      }
     }
   }
-  // one synchronisation per block: row norms, power-iteration values, Ritz
-  // values and the sticky device status
+  return AS_OK;
+}
+
+BatchJob block_job(const as_sketch* h, const BlockCtx& c) {
+  BatchJob j{};
+  j.Gf = h->Gf;
+  j.n2 = h->n2;
+  j.r0 = c.r0;
+  j.nb = c.nbb;
+  j.k_pi = h->k_pi;
+  j.q = h->q;
+  j.key = h->key;
+  j.i0 = (uint64_t)(h->T + 1);
+  j.pb = h->pb;
+  j.status = h->dstatus;
+  return j;
+}
+
+// Decision phase of one block: one synchronisation for the row norms, the
+// power-iteration values, the Ritz values and the sticky device status; then
+// the first state-changing row is found, the rows before it are committed, the
+// state is cut back to it and it is finished in FP64.
+as_status block_finish(as_sketch* h, const BlockCtx& c, int64_t* used, bool* bad_row) {
+  const int d = h->d, n2 = h->n2, r0 = c.r0, b = c.b, nbb = c.nbb;
+  as_status st = AS_OK;
+  *bad_row = false;
   AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf, h->norm2, b * sizeof(double), cudaMemcpyDeviceToHost, h->s));
   if (nbb > 0) {
     AS_CUDA_TRY(cudaMemcpyAsync(h->h_buf + b, h->pb.sig2, nbb * sizeof(double), cudaMemcpyDeviceToHost, h->s));
@@ -683,6 +726,13 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
   st = finish_row(h, h->T, h->theta, gate_known, sig2_star, bcol, 3 * nbb);
   if (h->prof) h->prof->end(PK_EVENT, h->s, 0.0, 0.0);
   return st;
+}
+
+as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t* used, bool* bad_row) {
+  BlockCtx c;
+  as_status st = block_prepare(h, src, navail, c, false);
+  if (st != AS_OK) return st;
+  return block_finish(h, c, used, bad_row);
 }
 
 __global__ void add_f64_kernel(double* dst, const double* src, size_t n) {
@@ -795,6 +845,221 @@ bool is_device_ptr(const void* p) {
 
 // ---- library-internal access for the runtimes built on sketches (sliding.cu)
 namespace as {
+
+as_status sk_group_update(as_sketch* const* hs, const float* const* rows, const int64_t* n, const int64_t* ld,
+                          int32_t count, as_status* status) {
+  if (count <= 0) return AS_OK;
+  struct Cur {
+    as_sketch* h = nullptr;
+    std::vector<int> ent;                 // entries of this sketch, in list order
+    size_t e = 0;                         // current entry
+    int64_t t0 = 0, nb = 0, done = 0;     // staged chunk [t0, t0 + nb) of the entry, rows consumed
+    const float* base = nullptr;
+    bool active = false;
+    BlockCtx ctx;
+    as_status fst = AS_OK;
+    int64_t used = 0;
+    bool bad = false;
+    std::unique_lock<std::mutex> lk;
+    cudaEvent_t ev = nullptr;
+  };
+  std::vector<Cur> cur;
+  std::unordered_map<const as_sketch*, size_t> at;
+  int dev = -1;
+  for (int32_t k = 0; k < count; ++k) {
+    status[k] = AS_OK;
+    as_sketch* h = hs[k];
+    if (!h || h->mode == AS_COORDINATOR || n[k] < 0 || (n[k] > 0 && (!rows[k] || ld[k] < h->d))) {
+      status[k] = AS_EINVAL;
+      continue;
+    }
+    if (dev < 0) dev = h->dev;
+    if (h->dev != dev) {   // one device per call
+      status[k] = AS_EINVAL;
+      continue;
+    }
+    if (n[k] == 0) continue;
+    auto it = at.find(h);
+    if (it == at.end()) {
+      at.emplace(h, cur.size());
+      cur.emplace_back();
+      cur.back().h = h;
+      cur.back().ent.push_back(k);
+    } else {
+      cur[it->second].ent.push_back(k);
+    }
+  }
+  if (cur.empty()) return AS_OK;
+  AS_CUDA_TRY(cudaSetDevice(dev));
+  for (Cur& c : cur) {
+    c.lk = std::unique_lock<std::mutex>(c.h->mu, std::try_to_lock);
+    if (!c.lk.owns_lock())
+      for (int k : c.ent) status[k] = AS_EBUSY;
+  }
+  cudaStream_t gs = nullptr;
+  cudaEvent_t gev = nullptr;
+  as_status gst = AS_OK;
+  if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&gev, cudaEventDisableTiming) != cudaSuccess) {
+    as_note_cuda_error(cudaGetLastError(), __FILE__, __LINE__);
+    gst = AS_EDEVICE;
+  }
+  for (Cur& c : cur)
+    if (gst == AS_OK && cudaEventCreateWithFlags(&c.ev, cudaEventDisableTiming) != cudaSuccess) {
+      as_note_cuda_error(cudaGetLastError(), __FILE__, __LINE__);
+      gst = AS_EDEVICE;
+    }
+  // stage the next chunk of the cursor's current entry (as sketch_update does)
+  auto stage = [&](Cur& c) -> as_status {
+    for (;;) {
+      if (c.e >= c.ent.size()) {
+        c.active = false;
+        return AS_OK;
+      }
+      const int k = c.ent[c.e];
+      if (status[k] != AS_OK || c.t0 >= n[k]) {
+        ++c.e;
+        c.t0 = 0;
+        continue;
+      }
+      as_sketch* h = c.h;
+      const int64_t nb = std::min<int64_t>(h->stage_rows, n[k] - c.t0);
+      const float* src = rows[k] + c.t0 * ld[k];
+      const float* base = src;
+      if (!is_device_ptr(rows[k])) {
+        AS_CUDA_TRY(cudaMemcpy2DAsync(h->stage, (size_t)h->d * sizeof(float), src, (size_t)ld[k] * sizeof(float),
+                                      (size_t)h->d * sizeof(float), (size_t)nb, cudaMemcpyHostToDevice, h->s));
+        base = h->stage;
+      } else if (ld[k] != h->d) {
+        AS_CUDA_TRY(cudaMemcpy2DAsync(h->stage, (size_t)h->d * sizeof(float), src, (size_t)ld[k] * sizeof(float),
+                                      (size_t)h->d * sizeof(float), (size_t)nb, cudaMemcpyDeviceToDevice, h->s));
+        base = h->stage;
+      }
+      c.base = base;
+      c.nb = nb;
+      c.done = 0;
+      c.active = true;
+      return AS_OK;
+    }
+  };
+  auto fail = [&](Cur& c, as_status st) {   // a device-level failure ends the sketch's remaining entries
+    for (size_t e = c.e; e < c.ent.size(); ++e)
+      if (status[c.ent[e]] == AS_OK) status[c.ent[e]] = st;
+    c.active = false;
+  };
+  for (Cur& c : cur)
+    if (gst == AS_OK && c.lk.owns_lock()) {
+      as_status st = stage(c);
+      if (st != AS_OK) fail(c, st);
+    }
+  const int cap = batch_group_capacity();
+  std::vector<size_t> act;
+  while (gst == AS_OK) {
+    act.clear();
+    for (size_t i = 0; i < cur.size(); ++i)
+      if (cur[i].active) act.push_back(i);
+    if (act.empty()) break;
+    // launch phase of every sketch's next block
+    run_parallel((int)act.size(), [&](int t) {
+      Cur& c = cur[act[(size_t)t]];
+      c.ctx = BlockCtx();
+      c.fst = block_prepare(c.h, c.base + c.done * c.h->d, c.nb - c.done, c.ctx, true);
+    });
+    // the deferred FP32 batched iterations, grouped
+    std::vector<size_t> grp;
+    std::vector<BatchJob> jobs;
+    int tiles = 0;
+    auto flush = [&]() -> as_status {
+      if (jobs.empty()) return AS_OK;
+      as_status st = AS_ENOTSUP;
+      if (jobs.size() > 1) {
+        for (size_t g : grp) {
+          AS_CUDA_TRY(cudaEventRecord(cur[g].ev, cur[g].h->s));
+          AS_CUDA_TRY(cudaStreamWaitEvent(gs, cur[g].ev, 0));
+        }
+        st = launch_batch_group(gs, jobs.data(), (int)jobs.size(), cur[grp[0]].h->pb.cnt);
+        if (st == AS_OK) {
+          for (size_t g : grp) cur[g].h->st.grouped_batches++;
+          AS_CUDA_TRY(cudaEventRecord(gev, gs));
+          for (size_t g : grp) AS_CUDA_TRY(cudaStreamWaitEvent(cur[g].h->s, gev, 0));
+        } else if (st != AS_ENOTSUP) {
+          return st;
+        }
+      }
+      if (st == AS_ENOTSUP)   // one job, or the group did not fit: each on its own stream
+        for (size_t q = 0; q < grp.size(); ++q) {
+          as_sketch* h = cur[grp[q]].h;
+          const BatchJob& j = jobs[q];
+          st = launch_batch_persist(h->s, j.Gf, j.n2, j.r0, j.nb, j.k_pi, j.q, j.key, j.i0, j.pb, j.status, h->prof);
+          if (st != AS_OK) return st;
+        }
+      grp.clear();
+      jobs.clear();
+      tiles = 0;
+      return AS_OK;
+    };
+    for (size_t i : act) {
+      Cur& c = cur[i];
+      if (c.fst != AS_OK || !c.ctx.deferred) continue;
+      const BatchJob j = block_job(c.h, c.ctx);
+      const int t = batch_group_tiles(j);
+      if (t <= 0 || t > cap) {
+        c.fst = launch_batch_persist(c.h->s, j.Gf, j.n2, j.r0, j.nb, j.k_pi, j.q, j.key, j.i0, j.pb, j.status,
+                                     c.h->prof);
+        continue;
+      }
+      if (tiles + t > cap || jobs.size() == 32) {
+        gst = flush();
+        if (gst != AS_OK) break;
+      }
+      grp.push_back(i);
+      jobs.push_back(j);
+      tiles += t;
+    }
+    if (gst == AS_OK) gst = flush();
+    if (gst != AS_OK) break;
+    // decision phase of every block
+    run_parallel((int)act.size(), [&](int t) {
+      Cur& c = cur[act[(size_t)t]];
+      if (c.fst != AS_OK) return;
+      c.used = 0;
+      c.bad = false;
+      c.fst = block_finish(c.h, c.ctx, &c.used, &c.bad);
+    });
+    for (size_t i : act) {
+      Cur& c = cur[i];
+      if (c.fst != AS_OK) {
+        fail(c, c.fst);
+        continue;
+      }
+      c.done += c.used;
+      as_status st = AS_OK;
+      if (c.bad) {   // a non-finite row ends its entry (rows before it are in)
+        status[c.ent[c.e]] = AS_EINVAL;
+        ++c.e;
+        c.t0 = 0;
+        st = stage(c);
+      } else if (c.done >= c.nb) {
+        c.t0 += c.nb;
+        st = stage(c);
+      }
+      if (st != AS_OK) fail(c, st);
+    }
+  }
+  for (Cur& c : cur) {
+    if (gst != AS_OK) fail(c, gst);
+    if (c.lk.owns_lock()) {
+      as_status ds = sync_status(c.h);
+      if (ds != AS_OK)
+        for (int k : c.ent)
+          if (status[k] == AS_OK) status[k] = ds;
+    }
+    if (c.ev) cudaEventDestroy(c.ev);
+  }
+  if (gev) cudaEventDestroy(gev);
+  if (gs) cudaStreamDestroy(gs);
+  return gst;
+}
 
 cudaStream_t sk_stream(const as_sketch* h) { return h->s; }
 int sk_device(const as_sketch* h) { return h->dev; }

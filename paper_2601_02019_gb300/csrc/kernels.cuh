@@ -1,6 +1,8 @@
 // Launchers of the AeroSketch kernels (internal C++ interface of the library).
 #pragma once
 
+#include <functional>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -162,6 +164,24 @@ int batch_si_col(int nb, int t);
 as_status launch_batch_persist(cudaStream_t s, const float* Gf, int n2, int r0, int nb, int k_pi, int q, Key key,
                                uint64_t i0, const PersistBuffers& pb, int* status, Prof* prof = nullptr);
 
+// One block of one sketch for a grouped launch of the FP32 persistent kernel.
+struct BatchJob {
+  const float* Gf;
+  int n2, r0, nb, k_pi, q;
+  Key key;
+  uint64_t i0;
+  PersistBuffers pb;
+  int* status;
+};
+// CTAs a grouped launch may hold (one per SM), and a job's tiles (0: it
+// cannot join a group).
+int batch_group_capacity();
+int batch_group_tiles(const BatchJob& j);
+// The jobs' blocks in one cooperative launch on stream s (at most 32 jobs,
+// their tiles within the capacity); cnt is the launch's barrier counter.
+// Each job's results equal those of its own launch_batch_persist.
+as_status launch_batch_group(cudaStream_t s, const BatchJob* jobs, int n, unsigned* cnt);
+
 // x^(0) and Pi of every row of a block into buffer 1 of pb.Y (FP32), as the
 // persistent kernels read them at iteration 0.
 void launch_persist_fill(cudaStream_t s, const PersistBuffers& pb, int mmax, int nb, int npi, int r0, Key key,
@@ -223,6 +243,15 @@ as_status launch_split_bf16(cudaStream_t s, const float* src, long long lds, int
 // (engine.cu): stream, rows fed, the snapshot queue's times (the sketch's own
 // row indices), the windowed query Gram, raw-row Grams, dropping the oldest
 // snapshots, and the eigen-shrink of a device B (Algorithm 5 lines 5-7).
+// Runs f(0) .. f(n-1) on the library's worker threads and waits for all.
+void run_parallel(int n, const std::function<void(int)>& f);
+// Several sketches updated in lockstep: each step prepares one block of every
+// sketch, runs their FP32 batched iterations in grouped cooperative launches
+// (as many sketches per launch as fit on the GPU at once), then finishes every
+// block in parallel.  Entries naming the same sketch run in list order;
+// status[k] receives entry k's status, as sketch_update would return it.
+as_status sk_group_update(as_sketch* const* hs, const float* const* rows, const int64_t* n, const int64_t* ld,
+                          int32_t count, as_status* status);
 cudaStream_t sk_stream(const as_sketch* h);
 int sk_device(const as_sketch* h);
 int64_t sk_device_bytes(const as_sketch* h);

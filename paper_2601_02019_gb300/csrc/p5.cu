@@ -18,8 +18,8 @@
 //
 // The scalar protocol runs on the host; the rows, the snapshot terms and the
 // coordinator's query run in the library's kernels (sketch calls only).  Each
-// site has its own stream, and a round updates the sites from several host
-// threads so that their kernels overlap on the GPU.
+// site has its own stream, and a round updates the sites from the library's
+// worker threads so that their kernels overlap on the GPU.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -99,23 +99,19 @@ as_status as_p5_round(as_p5* p, const float* const* rows, const int64_t* n, cons
   if (!p || !rows || !n || !ld) return AS_EINVAL;
   for (int j = 0; j < p->m; ++j)
     if (n[j] < 0 || (n[j] > 0 && (!rows[j] || ld[j] < p->d))) return AS_EINVAL;
-  // the sites' rows, concurrently (one host thread and one stream per site,
-  // at most 16 threads): row norms for the protocol and the site updates
+  // the sites' rows, each site on its own stream and a worker thread: row
+  // norms for the protocol and the site update.  The sites progress
+  // independently: lockstep blocks sharing grouped launches of the batched
+  // iterations (sketch_update_many) measured slower here, since every step
+  // then waits for the slowest site's FP64 event rows.
   const int m = p->m;
   std::vector<std::vector<double>> nrm((size_t)m);
   std::vector<as_status> sts((size_t)m, AS_OK);
-  auto work = [&](int j) {
+  as::run_parallel(m, [&](int j) {
     nrm[(size_t)j].assign((size_t)n[j], 0.0);
     sts[(size_t)j] = as::row_norms_f64(rows[j], n[j], ld[j], p->d, p->ss[(size_t)j], nrm[(size_t)j].data());
     if (sts[(size_t)j] == AS_OK && n[j] > 0) sts[(size_t)j] = sketch_update(p->sites[(size_t)j], rows[j], n[j], ld[j]);
-  };
-  const int nt = std::min(m, 16);
-  std::vector<std::thread> pool;
-  for (int w = 0; w < nt; ++w)
-    pool.emplace_back([&, w]() {
-      for (int j = w; j < m; j += nt) work(j);
-    });
-  for (std::thread& t : pool) t.join();
+  });
   for (as_status st : sts)
     if (st != AS_OK) return st;
   // messages and snapshots in site order (the coordinator's sums keep a fixed order)

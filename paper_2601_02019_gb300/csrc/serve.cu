@@ -104,6 +104,28 @@ double percentile(std::vector<double> v, double p) {   // nearest rank
 
 }  // namespace
 
+namespace as {
+
+void run_parallel(int n, const std::function<void(int)>& f) {
+  if (n <= 0) return;
+  if (n == 1) {
+    f(0);
+    return;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  Latch latch((size_t)n);
+  for (int i = 0; i < n; ++i)
+    pool().run([&, i]() {
+      cudaSetDevice(dev);
+      f(i);
+      latch.done();
+    });
+  latch.wait();
+}
+
+}  // namespace as
+
 struct as_server {
   struct Session {
     as_sketch* h = nullptr;
@@ -189,7 +211,7 @@ as_status sketch_update_many(as_sketch* const* hs, const float* const* rows, con
   for (int32_t k = 0; k < count; ++k)
     if (!hs[k]) return AS_EINVAL;
   if (count == 1) return sketch_update(hs[0], rows[0], n[0], ld[0]);
-  // entries grouped by sketch, each group in list order
+  // entries grouped by sketch, each group in list order, one worker per sketch
   std::vector<std::vector<int32_t>> groups;
   std::unordered_map<const as_sketch*, size_t> gi;
   for (int32_t k = 0; k < count; ++k) {
@@ -202,17 +224,25 @@ as_status sketch_update_many(as_sketch* const* hs, const float* const* rows, con
     }
   }
   std::vector<as_status> st((size_t)count, AS_OK);
-  Latch latch(groups.size());
-  for (const std::vector<int32_t>& g : groups) {
-    pool().run([&, g]() {
-      cudaSetDevice(as::sk_device(hs[g[0]]));
-      for (int32_t k : g) st[(size_t)k] = sketch_update(hs[k], rows[k], n[k], ld[k]);
-      latch.done();
-    });
-  }
-  latch.wait();
-  for (as_status s : st)
-    if (s != AS_OK) return s;
+  as::run_parallel((int)groups.size(), [&](int g) {
+    for (int32_t k : groups[(size_t)g]) st[(size_t)k] = sketch_update(hs[k], rows[k], n[k], ld[k]);
+  });
+  for (as_status e : st)
+    if (e != AS_OK) return e;
+  return AS_OK;
+}
+
+as_status sketch_update_grouped(as_sketch* const* hs, const float* const* rows, const int64_t* n, const int64_t* ld,
+                                int32_t count) {
+  if (count < 0) return AS_EINVAL;
+  if (count == 0) return AS_OK;
+  if (!hs || !rows || !n || !ld) return AS_EINVAL;
+  // lockstep blocks: one grouped launch of the batched iterations per step
+  std::vector<as_status> st((size_t)count, AS_OK);
+  const as_status g = as::sk_group_update(hs, rows, n, ld, count, st.data());
+  if (g != AS_OK) return g;
+  for (as_status e : st)
+    if (e != AS_OK) return e;
   return AS_OK;
 }
 

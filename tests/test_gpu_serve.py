@@ -52,8 +52,10 @@ def test_footprint_is_the_reserved_device_bytes(d, ell):
         assert s.stats()["device_bytes"] == p.footprint(d, ell, snapshot_rank=rank)
 
 
-def test_update_many_is_bitwise_the_sketches_alone():
+@pytest.mark.parametrize("mode", ["update_many", "update_grouped"])
+def test_update_many_is_bitwise_the_sketches_alone(mode):
     p = _gpu()
+    upd = getattr(p, mode)
     rng = np.random.default_rng(3)
     sk, blocks, plan = [], [], []
     for t, (d, ell) in enumerate(SHAPES):
@@ -62,13 +64,16 @@ def test_update_many_is_bitwise_the_sketches_alone():
         plan.append((d, ell, A))
     # two rounds; in the second the first sketch appears twice (in list order)
     cut = [len(A) // 2 for _, _, A in plan]
-    p.update_many(sk, [A[:c] for (_, _, A), c in zip(plan, cut)])
-    p.update_many([sk[0]] + sk, [plan[0][2][cut[0]:cut[0] + 40]] +
+    upd(sk, [A[:c] for (_, _, A), c in zip(plan, cut)])
+    upd([sk[0]] + sk, [plan[0][2][cut[0]:cut[0] + 40]] +
                   [A[c + 40:] if t == 0 else A[c:] for t, ((_, _, A), c) in enumerate(zip(plan, cut))])
     for t, (d, ell, A) in enumerate(plan):
         c = cut[t]
         blocks = [A[:c], A[c:c + 40], A[c + 40:]] if t == 0 else [A[:c], A[c:]]
         _same(sk[t], _alone(p, d, ell, blocks, seed=t))
+    # grouped: the sketches' batched iterations did share cooperative launches
+    grouped = sum(s.stats()["grouped_batches"] for s in sk)
+    assert (grouped > 0) if mode == "update_grouped" else (grouped == 0)
 
 
 def test_server_sessions_are_bitwise_the_sketches_alone():
