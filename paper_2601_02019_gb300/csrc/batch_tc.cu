@@ -18,16 +18,18 @@
 //
 // Work split.  CTA (rb, ks) multiplies the 128 rows rb of G by the rows
 // [ks kc, (ks+1) kc) of Y_it (UMMA M = 128, N = the padded column count,
-// K = kc): a TMA producer lane streams G and Y tiles (64 K-elements, 128-byte
-// swizzle) through a 4-stage ring, one lane issues tcgen05.mma into two TMEM
-// accumulators (the leading level product and the corrections), and the
-// partial 128 x N block goes to global memory.  After a grid barrier CTA c
-// sums the K-split partials of its rpc rows in a fixed order, applies C_it,
-// masks, writes Y_{it+1} (FP32 and its BF16 levels) and its per-pair partial
-// sums; a second grid barrier closes the iteration.  The coefficients C_it
-// are computed from those partial sums by the other warps while the product
-// runs.  Every mbarrier and grid-barrier wait is bounded; on a timeout the
-// status word gets AS_ETIMEOUT and every CTA frees its TMEM and returns.
+// K = kc): a TMA producer lane streams, per 64-wide K tile, both BF16 levels
+// of G and of Y (128-byte swizzle) through a 2-stage ring, one lane issues
+// the three level products as tcgen05.mma into two TMEM accumulators (the
+// leading level product and the corrections), and the partial 128 x N block
+// goes to global memory.  After a grid barrier CTA c sums the K-split
+// partials of its rpc rows in a fixed order, applies C_it, masks, writes
+// Y_{it+1} (FP32 and its BF16 levels) and its per-pair partial sums, and
+// publishes them with a release flag (synchronisation below).  The
+// coefficients C_it are computed from those partial sums by the other warps
+// while the product runs.  Every mbarrier, flag and grid-barrier wait is
+// bounded; on a timeout the status word gets AS_ETIMEOUT and every CTA frees
+// its TMEM and returns.
 #include <algorithm>
 #include <mutex>
 

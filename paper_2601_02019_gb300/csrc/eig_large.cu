@@ -350,6 +350,7 @@ struct TriPersist {
 constexpr int kTriThreads = 512;
 constexpr int kTriWarps = kTriThreads / 32;
 constexpr int kTriUnroll = 16;  // row entries in flight per lane
+constexpr int kTriPre = 4;      // entries of p and of row r per thread loaded at the top of a pass
 
 __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersist t) {
   extern __shared__ df64 smp[];
@@ -363,6 +364,18 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
   const int W = G * kTriWarps, gw = blockIdx.x * kTriWarps + warp;
   for (int r = 0; r <= n - 2; ++r) {
     const bool upd = r >= 1;
+    const df64* arow = t.A + (size_t)r * t.lda;
+    // the entries j = r + tid + kTriThreads u of p_{r-1} and of row r are loaded
+    // together with the partial sums below: one L2 round trip instead of three
+    // (p and row r do not depend on the coefficient those sums give)
+    df64 pjr[kTriPre], ajr[kTriPre];
+#pragma unroll
+    for (int u = 0; u < kTriPre; ++u) {
+      const int j = r + tid + kTriThreads * u;
+      const df64* pin = ((r - 1) & 1) ? t.p[1] : t.p[0];
+      pjr[u] = (upd && j < n) ? pin[j] : df64{0.f, 0.f};
+      ajr[u] = (j < n) ? arow[j] : df64{0.f, 0.f};
+    }
     if (upd) {
       const df64* qin = ((r - 1) & 1) ? t.q[1] : t.q[0];
       if (tid < 32) {   // loads of 8 partials per lane in flight before the adds
@@ -383,14 +396,17 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
       __syncthreads();
       const df64 c2{2.f * c_s.hi, 2.f * c_s.lo};
       const df64* pin = ((r - 1) & 1) ? t.p[1] : t.p[0];
-#pragma unroll 4
-      for (int j = r + tid; j < n; j += blockDim.x) {
+#pragma unroll
+      for (int u = 0; u < kTriPre; ++u) {
+        const int j = r + tid + kTriThreads * u;
+        if (j < n) wk[j] = df_sub(df64{2.f * pjr[u].hi, 2.f * pjr[u].lo}, df_mul(c2, vcur[j]));
+      }
+      for (int j = r + tid + kTriThreads * kTriPre; j < n; j += blockDim.x) {
         const df64 pj = pin[j];
         wk[j] = df_sub(df64{2.f * pj.hi, 2.f * pj.lo}, df_mul(c2, vcur[j]));
       }
       __syncthreads();
     }
-    const df64* arow = t.A + (size_t)r * t.lda;
     const df64 vr = upd ? vcur[r] : df64{0.f, 0.f};
     const df64 wr = upd ? wk[r] : df64{0.f, 0.f};
     if (blockIdx.x == 0) {
@@ -399,8 +415,16 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
       if (tid == 0) t.d[r] = df_to_double(upd ? df_rank2(arow[r], vr, wr, wr, vr) : arow[r]);
     }
     df64 acc{0.f, 0.f};
-#pragma unroll 4
-    for (int j = r + 1 + tid; j < n; j += blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < kTriPre; ++u) {
+      const int j = r + tid + kTriThreads * u;
+      if (j >= r + 1 && j < n) {
+        const df64 x = upd ? df_rank2(ajr[u], vr, wk[j], wr, vcur[j]) : ajr[u];
+        vnew[j] = x;
+        acc = df_fma(x, x, acc);
+      }
+    }
+    for (int j = r + tid + kTriThreads * kTriPre; j < n; j += blockDim.x) {
       const df64 x = upd ? df_rank2(arow[j], vr, wk[j], wr, vcur[j]) : arow[j];
       vnew[j] = x;
       acc = df_fma(x, x, acc);
