@@ -389,6 +389,14 @@ as_status as_server_reset_stats(as_server* sv);
 /* Stop the workers (after the running requests), close every session. */
 as_status as_server_destroy(as_server* sv);
 
+/* Self-test of the library's bounded device waits: runs one of them on
+ * something that nothing completes (kind 0: a release flag, 1: a grid
+ * barrier, 2: an mbarrier phase) with a limit of limit_ms (1..2000) in one
+ * small kernel on cuda_stream.  Returns AS_ETIMEOUT when the wait gave up as
+ * designed (the device context stays usable), AS_OK if it did not, AS_EINVAL
+ * for bad arguments.  Synchronises.  Production waits use a 2 s limit. */
+as_status as_wait_selftest(int32_t kind, int32_t limit_ms, void* cuda_stream);
+
 /* Counters and the sticky device status.  Synchronises. */
 as_status sketch_stats(as_sketch* h, as_stats* out);
 

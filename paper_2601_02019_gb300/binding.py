@@ -25,7 +25,7 @@ EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram
             "as_sw_destroy", "sketch_footprint", "sketch_reserve", "sketch_update_many", "sketch_update_grouped",
             "as_server_create",
             "as_server_open", "as_server_submit", "as_server_wait", "as_server_drain", "as_server_session",
-            "as_server_close", "as_server_stats", "as_server_reset_stats", "as_server_destroy")
+            "as_server_close", "as_server_stats", "as_server_reset_stats", "as_server_destroy", "as_wait_selftest")
 
 
 class AsConfig(ct.Structure):
@@ -149,6 +149,7 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.as_server_stats.argtypes = [P, ct.POINTER(AsServerCounters)]
     L.as_server_reset_stats.argtypes = [P]
     L.as_server_destroy.argtypes = [P]
+    L.as_wait_selftest.argtypes = [I32, I32, P]
     L.as_status_str.argtypes = [ct.c_int]
     L.as_status_str.restype = ct.c_char_p
     L.as_last_error.argtypes = []

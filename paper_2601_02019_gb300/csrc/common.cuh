@@ -141,4 +141,16 @@ __device__ __forceinline__ void set_status(int* st, int code) {
   if (st) atomicCAS(st, 0, code);
 }
 
+// Device waits (grid barriers, release flags, mbarriers) give up after this
+// much wall time, or after an iteration count should the timer not advance,
+// set AS_ETIMEOUT and return, so that a stuck wait cannot hold the GPU.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+constexpr long long kWaitMaxIters = 1LL << 26;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 }  // namespace as

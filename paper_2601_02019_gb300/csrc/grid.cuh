@@ -7,7 +7,6 @@
 
 namespace as {
 
-constexpr long long kGridBarrierSpins = 1LL << 24;
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
@@ -25,11 +24,13 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 
 // One thread waits (bounded) until *flag >= target; false on a timeout
 // (status set to AS_ETIMEOUT) or when the sticky status is already set.
-__device__ __forceinline__ bool wait_flag_ge(const unsigned* flag, unsigned target, int* status) {
+__device__ __forceinline__ bool wait_flag_ge(const unsigned* flag, unsigned target, int* status,
+                                             unsigned long long limit_ns = kWaitLimitNs) {
+  const unsigned long long t0 = global_ns();
   long long n = 0;
   while (ld_acquire_u32(flag) < target) {
     if (*(volatile int*)status != 0) return false;
-    if (++n > kGridBarrierSpins) { set_status(status, AS_ETIMEOUT); return false; }
+    if (++n > kWaitMaxIters || global_ns() - t0 > limit_ns) { set_status(status, AS_ETIMEOUT); return false; }
     __nanosleep(32);
   }
   return true;
@@ -38,7 +39,8 @@ __device__ __forceinline__ bool wait_flag_ge(const unsigned* flag, unsigned targ
 // Returns false when this CTA gave up waiting (status set to AS_ETIMEOUT) or
 // found the sticky status already set; the caller then returns, and every
 // other CTA gives up at its next barrier.
-__device__ __forceinline__ bool grid_barrier(unsigned* cnt, unsigned target, int* status) {
+__device__ __forceinline__ bool grid_barrier(unsigned* cnt, unsigned target, int* status,
+                                             unsigned long long limit_ns = kWaitLimitNs) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -46,10 +48,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned* cnt, unsigned target, int
     // visible with the arrival; acquire on the loads that observe the target
     red_release_add_u32(cnt, 1u);
     int ok = 1;
+    const unsigned long long t0 = global_ns();
     long long n = 0;
     while (ld_acquire_u32(cnt) < target) {
       if (*(volatile int*)status != 0) { ok = 0; break; }
-      if (++n > kGridBarrierSpins) { set_status(status, AS_ETIMEOUT); ok = 0; break; }
+      if (++n > kWaitMaxIters || global_ns() - t0 > limit_ns) { set_status(status, AS_ETIMEOUT); ok = 0; break; }
       __nanosleep(32);
     }
     s_ok = ok;
