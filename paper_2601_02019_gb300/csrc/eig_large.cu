@@ -139,8 +139,7 @@ __device__ int sturm_count_df(int n, const df64* dd, const df64* e2, df64 x, flo
 // eigenvalue), then inverse iteration in FP64 by the group's first lane.  The
 // bracket is kept in FP64; evaluation points are rounded to df64.  Stops at a
 // width of 2^-44 of ||T|| (df64 resolution).
-__global__ void bisect_invit_df(int n, int nev, TriWork w, const double* norms, const df64* dd, const df64* e2,
-                                double* evals, double* X, int ldx, double* lu) {
+__global__ void bisect_df(int n, int nev, const double* norms, const df64* dd, const df64* e2, double* evals) {
   const int lane = threadIdx.x & 31;
   const int g = lane & (kBisLanes - 1), grp = lane / kBisLanes;
   const int j = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / kBisLanes) + grp;
@@ -174,10 +173,24 @@ __global__ void bisect_invit_df(int n, int nev, TriWork w, const double* norms, 
     }
   }
   if (g != 0 || !active) return;
-  const double* d = w.d;
-  const double* e = w.e;
   const double lam = (tnorm == 0.0) ? 0.0 : 0.5 * (lo + hi) * tnorm;   // of the scaled matrix
   evals[j] = lam * norms[3];                                            // exact power-of-two unscaling
+}
+
+// Inverse iteration for the eigenvalues found by bisect_df, one thread per
+// eigenvector in full warps spread over many SMs: the LU factorisation and
+// the solves are FP64 recurrences, and FP64 issue is scarce on this part, so
+// no lane of a warp should idle.  lam = evals[j] / norms[3] undoes the exact
+// power-of-two unscaling.
+__global__ void __launch_bounds__(32) invit_df(int n, int nev, TriWork w, const double* norms, const double* evals,
+                                               double* X, int ldx, double* lu) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nev) return;
+  const double tnorm = norms[0];
+  const double eps = 2.220446049250313e-16;
+  const double lam = (tnorm == 0.0) ? 0.0 : evals[j] / norms[3];
+  const double* d = w.d;
+  const double* e = w.e;
   // inverse iteration (same factorisation as eig.cuh)
   const double tiny = fmax(eps * tnorm, 1e-300);
   double* u0 = lu + (size_t)(0 * n) * nev + j;
@@ -627,7 +640,9 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
   tri_scale_df<<<(n + 255) / 256, 256, 0, s>>>(n, w, norms, dd, e2); count_launches(1);
   {
     const int per_block = (128 / 32) * (32 / kBisLanes);   // eigenvalues per block of 128 threads
-    bisect_invit_df<<<(nev + per_block - 1) / per_block, 128, 0, s>>>(n, nev, w, norms, dd, e2, evals, X, ldx, lu);
+    bisect_df<<<(nev + per_block - 1) / per_block, 128, 0, s>>>(n, nev, norms, dd, e2, evals);
+    count_launches(1);
+    invit_df<<<(nev + 31) / 32, 32, 0, s>>>(n, nev, w, norms, evals, X, ldx, lu);
     count_launches(1);
   }
   cluster_mgs<<<1, 512, 0, s>>>(n, nev, norms, evals, X, ldx); count_launches(1);
