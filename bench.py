@@ -328,6 +328,7 @@ def our_arm(args) -> None:
                       "bf16x6": "3-level split-bf16 tensor products (f32 acc), f64 core"}[head],
             "data": "synthetic",
             "config": {"workload": args.workload, "d": d, "ell": ell, "rows_per_step": B, "precision": head,
+                       "timed_rows": f"{W * B}..{(W + K) * B - 1} of the stream (after {W * B} warm-up rows)",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": forms_out[head]["gpu_launches"],
