@@ -67,6 +67,28 @@ def _compare(p, A, d, ell, seed=0, err_tol=1e-6, err_rel=0.0, tie=TIE, b_tol=1e-
 
 
 @pytest.mark.parametrize("d,ell,n,seed", [(32, 4, 300, 0), (64, 8, 700, 1), (40, 5, 333, 2)])
+def test_parity_free_running(d, ell, n, seed):
+    """Free-running parity: the oracle without the GPU's decision record.
+    Where the replayed run adopted no GPU choice (no decision fell in the tie
+    band), the two runs take the same decisions and must agree at the FP32
+    bar; otherwise the runs may part at a tie, and both must still meet the
+    paper's deterministic bound."""
+    p = _gpu()
+    A = low_rank_noisy(n, d, 6, spectrum("geometric", 6), noise=0.05, seed=seed)
+    s = _run_gpu(p, A, d, ell, seed=seed)
+    rep = p.binding.replay_from_trace(s.trace())
+    replayed = AeroSketch(d, ell, seed=seed, replay=rep, tie_rel=TIE).run(A.astype(np.float64))
+    free = AeroSketch(d, ell, seed=seed).run(A.astype(np.float64))
+    AtA = A.astype(np.float64).T @ A.astype(np.float64)
+    eg, ef = cov_err(A, s.query(), AtA), cov_err(A, free.query(), AtA)
+    assert eg <= 2.0 / ell and ef <= 2.0 / ell
+    if replayed.replayed == 0:
+        assert abs(eg - ef) <= 1e-6, (eg, ef)
+        assert s.stats()["dumps"] == len(free.S)
+        assert s.stats()["shrinks"] == len(free.shrink_rows)
+
+
+@pytest.mark.parametrize("d,ell,n,seed", [(32, 4, 300, 0), (64, 8, 700, 1), (40, 5, 333, 2)])
 def test_parity_small(d, ell, n, seed):
     p = _gpu()
     A = low_rank_noisy(n, d, 6, spectrum("geometric", 6), noise=0.05, seed=seed)
