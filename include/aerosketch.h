@@ -67,7 +67,9 @@ typedef enum {
  *   AS_FP32_PLAIN  SIMT FP32 products, FP32 partial sums combined in FP64.
  *   AS_BF16        d-side products (Gram rows, FD rebuild) on the tcgen05
  *                  tensor cores with BF16 operands and FP32 accumulation;
- *                  batched G-space products in split-BF16 on tcgen05.
+ *                  batched G-space products (the decision iterations) in
+ *                  two-level split-BF16 on tcgen05 for blocks of 256 or more
+ *                  padded rows, in FP32 SIMT below that.
  *   AS_BF16X3      as AS_BF16 with the d-side products in two-level split-BF16
  *                  (x = hi + lo; hi*hi + hi*lo + lo*hi: ~16-bit operands).
  *   AS_BF16X6      as AS_BF16 with the d-side products in three-level
@@ -96,7 +98,7 @@ typedef struct {
   int32_t q_si;       /* simultaneous-iteration products; 0 => ceil(ln d / eps_si) */
   uint64_t seed;      /* Philox key word 0 for the method's random draws */
   uint64_t stream_id; /* Philox key word 1 */
-  uint32_t flags;     /* AS_TRACE_DECISIONS */
+  uint32_t flags;     /* AS_TRACE_DECISIONS | AS_PROFILE */
   uint32_t reserved;
   double delta;       /* probability amplification (Algorithm 7): 0 = off, else the
                          failure probability delta in (0, 1): at every doubling step
@@ -105,7 +107,8 @@ typedef struct {
                          maximum of s = ceil(2 log_3(2/delta)) power-iteration estimates
                          is kept; SI h draws its test matrix at Philox sub-index
                          j + 64 (h-1), estimate g of SI h its start vector at 64 h + g.
-                         Every row whose gate passes takes the FP64 single-row path. */
+                         Every row whose gate passes takes the FP64 single-row path.
+                         AS_EINVAL unless r <= 15 and s <= 63 (delta >~ 2e-15). */
 } as_config;
 
 typedef struct {
@@ -214,8 +217,9 @@ as_status sketch_set_theta(as_sketch* h, double theta);
 as_status sketch_send_snapshots(as_sketch* src, as_sketch* dst, int32_t* sent);
 
 /* ---- P5: distributed sites and coordinator (Algorithm 10) --------------
- * m AS_SITE sketches and one AS_COORDINATOR sketch on one stream, driven in
- * synchronous rounds.  Per row of site j: F_j += ||a||^2; when F_j >=
+ * m AS_SITE sketches (each on a stream of its own, updated from the library's
+ * worker threads so that their kernels overlap) and one AS_COORDINATOR
+ * sketch on cuda_stream, driven in synchronous rounds.  Per row of site j: F_j += ||a||^2; when F_j >=
  * (eps/m) F_hat (the last broadcast value) the site messages F_j and resets
  * it; the row updates site j; site j's snapshots are then sent to the
  * coordinator.  At the end of a round the coordinator adds the messages in
@@ -290,8 +294,9 @@ as_status as_sw_destroy(as_sw* w);
 /* ---- Footprint, grouped updates and the serving runtime ------------------
  *
  * Many independent sketches (sessions, levels, sites) progress at once: each
- * has its own stream, and host worker threads drive them so that their
- * kernels overlap on the GPU.  A sketch's kernels and launch shapes depend only
+ * on a stream of its own, driven by host worker threads, so that their
+ * kernels overlap on the GPU; or in lockstep with shared launches
+ * (sketch_update_grouped).  A sketch's kernels and launch shapes depend only
  * on its own configuration and rows, so its results are bitwise the same
  * alone and in any mix. */
 
@@ -313,8 +318,8 @@ as_status sketch_reserve(as_sketch* h, int64_t snapshot_rank);
 
 /* Update `count` sketches, sketch k with rows[k] (n[k] rows, stride ld[k], host
  * or device), each progressing independently on the library's worker
- * threads (at most 16), each sketch on its own stream, so that their kernels
- * overlap on the GPU.  Entries naming the same sketch run in list order.
+ * threads (at most 16), each on the stream it was created with (sketches
+ * created on streams of their own overlap their kernels on the GPU).  Entries naming the same sketch run in list order.
  * Blocks until all are done; returns AS_OK or the status of the first failing
  * entry in list order (the other entries still run).  The caller keeps the
  * rows valid until the call returns. */
