@@ -2,11 +2,11 @@
  * aerosketch.h - C ABI of the GB300 AeroSketch update path.
  *
  * AeroSketch (arXiv 2601.02019) keeps a 2l x d residual buffer C, applies the
- * exact Frequent Directions shrink when the buffer is full (Algorithm 4 lines
- * 2-4), gates each update with a power iteration (Algorithm 1, Algorithm 4
- * line 7-8), and moves components whose squared singular value reaches the
+ * exact Frequent Directions shrink when the buffer is full (Algorithm 4,
+ * Section 2.3), gates each update with a power iteration (Algorithm 1 inside
+ * Algorithm 4), and moves components whose squared singular value reaches the
  * threshold theta into snapshots (Z, Z^T C'^T C') found by a doubling
- * simultaneous iteration (Algorithm 2, Algorithm 4 lines 9-17).  A query
+ * simultaneous iteration (Algorithm 2 inside Algorithm 4).  A query
  * assembles B = C^T C + the snapshot terms and shrinks it by its l-th
  * eigenvalue (Algorithm 5).  The persistent (ATTP) setting sets
  * theta = eps ||A_t||_F^2 before every update (Algorithm 8).
@@ -57,7 +57,7 @@ typedef enum {
                           snapshots are moved to a coordinator by sketch_send_snapshots */
   AS_COORDINATOR = 4   /* Algorithm 10, the coordinator: no rows (sketch_update returns
                           AS_EINVAL); accumulates received snapshot terms; its query is
-                          Algorithm 5 lines 5-7 on that sum */
+                          the eigen-shrink of Algorithm 5 on that sum */
 } as_mode;
 
 /* Arithmetic of the products.  In every form the orthonormalisations, the
@@ -89,11 +89,11 @@ typedef enum {
 typedef struct {
   int32_t d;          /* row dimension, >= 2 */
   int32_t ell;        /* sketch size l, 1 <= l <= d/2 (Section 2.3); 0 => ceil(2/eps) */
-  double eps;         /* error parameter; 0 => 2/l (Algorithm 3 line 1) */
+  double eps;         /* error parameter; 0 => 2/l (Algorithm 3) */
   int32_t mode;       /* as_mode */
   int32_t prec;       /* as_precision */
   double theta;       /* dump threshold for AS_FIXED_THETA (may be +inf) */
-  double eps_si;      /* simultaneous-iteration accuracy; 0 => 0.4 (Algorithm 4 line 11) */
+  double eps_si;      /* simultaneous-iteration accuracy; 0 => 0.4 (Algorithm 4) */
   int32_t k_pi;       /* power iterations; 0 => ceil(log2 d) + 1 (Corollary 1) */
   int32_t q_si;       /* simultaneous-iteration products; 0 => ceil(ln d / eps_si) */
   uint64_t seed;      /* Philox key word 0 for the method's random draws */
@@ -118,7 +118,7 @@ typedef struct {
   int32_t reserved0;
   double fro2;             /* ||A_T||_F^2 (FP64) */
   double theta;            /* threshold in force after the last update */
-  int64_t shrinks;         /* FD shrinks (Algorithm 4 lines 2-4) */
+  int64_t shrinks;         /* FD shrinks (Algorithm 4) */
   int64_t gates;           /* rows whose power-iteration gate passed */
   int64_t dumps;           /* snapshots taken */
   int64_t snapshot_rank;   /* sum of xi over the snapshot queue */
@@ -148,7 +148,7 @@ typedef struct {
   double sig2_pi;   /* power-iteration estimate sigma_hat_1^2 (Algorithm 1) */
   double theta;     /* threshold in force */
   int32_t j_stop;   /* doubling step that broke the loop, 0 if none */
-  int32_t xi;       /* components dumped (Algorithm 4 line 13) */
+  int32_t xi;       /* components dumped, xi (Algorithm 4) */
   double ritz_k;    /* sigma_hat_k^2 at the stopping step (or the last one) */
   double ritz_1;    /* sigma_hat_1^2 at that step */
   uint64_t amp_choice; /* with probability amplification: the simultaneous
@@ -180,7 +180,7 @@ as_status sketch_update(as_sketch* h, const float* rows, int64_t n, int64_t ld);
  * B_t of the ATTP error analysis).  Other t: AS_EINVAL.  Synchronises. */
 as_status sketch_query(as_sketch* h, int64_t t, float* out, int64_t ldo, int32_t* rows_out);
 
-/* The matrix B of Algorithm 5 lines 1-4 for the time t of sketch_query
+/* The matrix B of Algorithm 5 (before its eigendecomposition) for the time t of sketch_query
  * (before its eigendecomposition): d x d FP64, row-major, to host memory
  * `out`.  Synchronises. */
 as_status sketch_query_gram(as_sketch* h, int64_t t, double* out);
@@ -242,7 +242,7 @@ as_status as_p5_create(const as_config* site_cfg, int32_t m, void* cuda_stream, 
 /* One synchronous round: rows[j] (host or device, n[j] rows of d FP32 values,
  * row stride ld[j] >= d) are site j's rows; n[j] = 0 is allowed. */
 as_status as_p5_round(as_p5* p, const float* const* rows, const int64_t* n, const int64_t* ld);
-/* The coordinator's Query (Algorithm 5 lines 5-7 on B): l x d, as sketch_query. */
+/* The coordinator's Query (the eigen-shrink of Algorithm 5 on B): l x d, as sketch_query. */
 as_status as_p5_query(as_p5* p, float* out, int64_t ldo, int32_t* rows_out);
 /* The coordinator's B (d x d FP64, host memory). */
 as_status as_p5_query_gram(as_p5* p, double* out);
@@ -263,8 +263,8 @@ as_status as_p5_destroy(as_p5* p);
  * snapshot rule of Algorithm 4, read for raw rows too).  The query answers
  * from the lowest level whose queue is empty or starts at s <= max(1,
  * T - N + 1) (the top level if none), with B = its residual C^T C + its
- * queued snapshot terms and raw rows a^T a in (T-N, T], then Algorithm 5
- * lines 5-7.  A level's sketch numbers its own rows for its random draws. */
+ * queued snapshot terms and raw rows a^T a in (T-N, T], then the eigen-shrink
+ * of Algorithm 5.  A level's sketch numbers its own rows for its random draws. */
 typedef struct as_sw as_sw;
 
 typedef struct {
@@ -418,8 +418,8 @@ as_status sketch_profile(as_sketch* h, as_kernel_stat* out, int32_t cap, int32_t
 as_status sketch_profile_reset(as_sketch* h);
 
 /* FP64 symmetric eigendecomposition on the current device: the core
- * factorisation that the FD shrink (Algorithm 4 line 3, through the Gram
- * matrix of the buffer) and the query (Algorithm 5 line 5) use.  A is n x n,
+ * factorisation that the FD shrink (Algorithm 4, through the Gram matrix of
+ * the buffer) and the query (Algorithm 5) use.  A is n x n,
  * row-major, host memory (only its values are read; it is not modified).
  * Writes the nev largest eigenvalues in descending order to evals (host) and
  * the matching unit eigenvectors as the columns of vecs (host, n x nev,

@@ -42,7 +42,7 @@ the design notes of the repository):
  R10 The sign of each singular pair (u_j, v_j) is fixed so that the entry of
      largest magnitude of u_j (the left singular vector, a 2l-vector) is
      positive, the lowest index winning exact ties.
- R11 The current-time query (lb = 0, ub = T) includes C_T (Algorithm 5 line 1).
+ R11 The current-time query (lb = 0, ub = T) includes C_T (Algorithm 5).
  R17 Probability amplification (Algorithm 7, optional: delta): r and s are
      rounded up; SI h of the r draws its test matrix at sub-index
      j + 64 (h - 1) (h = 1 is the plain draw), estimate g of SI h its start
@@ -69,7 +69,7 @@ def default_k_pi(d: int) -> int:
 
 
 def default_q(d: int, eps_si: float) -> int:
-    """Algorithm 2 line 1, q = Theta(log d / eps_SI), read as ceil(ln d / eps_SI)."""
+    """Algorithm 2, q = Theta(log d / eps_SI), read as ceil(ln d / eps_SI)."""
     return int(math.ceil(math.log(d) / eps_si))
 
 
@@ -224,14 +224,14 @@ class AeroSketch:
             self.theta = self.eps * self.F
         theta = self.theta
         ell = self.ell
-        self.C[self.r] = a                      # line 1
+        self.C[self.r] = a                      # insert into the first empty row
         self.r += 1
-        if self.r == 2 * ell:                   # lines 2-4
+        if self.r == 2 * ell:                   # full buffer: FD shrink
             self._shrink(i)
         Cp = self.C                             # C'_i
         x0 = philox.gaussians(self.seed, self.stream_id, philox.PURPOSE_PI_START, i, 0, 2 * ell)
-        sig2, _ = power_iteration(Cp.T, self.k_pi, x0)          # line 7
-        own_gate = sig2 >= theta / 2.0 and sig2 > 0.0            # line 8, R6
+        sig2, _ = power_iteration(Cp.T, self.k_pi, x0)          # Algorithm 1 on C'^T
+        own_gate = sig2 >= theta / 2.0 and sig2 > 0.0            # the gate (R6)
         gate = self._decide(own_gate, sig2, theta / 2.0, "gate", i, self._replay_gate(i))
         if not gate:
             return
@@ -239,21 +239,21 @@ class AeroSketch:
         self.events.append(ev)
         other = self._replay_si(i)
         jmax = int(math.ceil(math.log2(min(ell, self.d)))) if min(ell, self.d) > 1 else 0
-        for j in range(1, jmax + 1):                              # line 9
-            k = min(2 ** j, ell, self.d)                          # line 10
+        for j in range(1, jmax + 1):                              # doubling loop
+            k = min(2 ** j, ell, self.d)
             if self.delta is None:
                 Pi = philox.gaussians(self.seed, self.stream_id, philox.PURPOSE_SI_TEST,
                                       i, j, 2 * ell * k).reshape(2 * ell, k)
-                Zp, s2 = simul_iter(Cp.T, self.q, Pi)             # line 11
+                Zp, s2 = simul_iter(Cp.T, self.q, Pi)             # Algorithm 2 on C'^T
             else:
-                Zp, s2 = self._amplified_si(Cp, k, i, j, theta)   # Algorithm 7 in place of line 11
+                Zp, s2 = self._amplified_si(Cp, k, i, j, theta)   # Algorithm 7 in place of Algorithm 2
             ev.ritz.append(s2.copy())
-            own_stop = s2[k - 1] < theta                          # line 12
+            own_stop = s2[k - 1] < theta                          # stop test
             stop = self._decide(own_stop, s2[k - 1], theta, "stop", i,
                                 None if other is None else (other[0] == j))
             if not stop:
                 continue
-            own_xi = int(np.sum((s2 >= theta) & (s2 > 0.0)))     # line 13
+            own_xi = int(np.sum((s2 >= theta) & (s2 > 0.0)))     # xi
             xi = own_xi
             if other is not None and other[0] == j:
                 near = np.any(np.abs(s2 - theta) <= self.tie_rel * theta)
@@ -265,19 +265,19 @@ class AeroSketch:
                     self.mismatches.append(("xi", i, own_xi, other[1]))
             ev.j_stop, ev.xi = j, xi
             if xi >= 1:                                           # R7
-                Z = Zp[:, :xi]                                    # line 14
+                Z = Zp[:, :xi]
                 CZ = Cp @ Z
                 Y = CZ.T @ Cp                                     # Z^T C'^T C'
                 s_prev = self.S[-1].t + 1 if self.S else 1
-                self.S.append(Snapshot(Z=Z, Y=Y, s=s_prev, t=i))  # line 15
-                Cnew = Cp - CZ @ Z.T                              # line 16
+                self.S.append(Snapshot(Z=Z, Y=Y, s=s_prev, t=i))  # snapshot
+                Cnew = Cp - CZ @ Z.T                              # residual C' - C' Z Z^T
                 if self.check_restore:
                     lhs = Cnew.T @ Cnew + snapshot_term(Z, Y)
                     rhs = Cp.T @ Cp
                     den = max(np.linalg.norm(rhs), 1e-300)
                     self.restore_err = max(self.restore_err, float(np.linalg.norm(lhs - rhs) / den))
                 self.C = Cnew
-            return                                                # line 17
+            return                                                # break
         # loop ended without break: C_i <- C'_i (R8)
 
     def _amplified_si(self, Cp: np.ndarray, k: int, i: int, j: int, theta: float):
@@ -339,7 +339,7 @@ class AeroSketch:
 
     # -- Algorithm 5 ------------------------------------------------------------
     def pre_query(self, lb: int = 0, ub: int | None = None) -> np.ndarray:
-        """B of Algorithm 5 lines 1-4 (before the eigendecomposition).
+        """B of Algorithm 5 (before the eigendecomposition).
 
         At the current time (ub = T) B = C_T^T C_T plus the snapshot terms
         with lb < t <= T.  For a historical time ub < T (the ATTP Query(t) of
@@ -356,7 +356,7 @@ class AeroSketch:
         return 0.5 * (B + B.T)
 
     def query(self, lb: int = 0, ub: int | None = None) -> np.ndarray:
-        """Algorithm 5 lines 5-7: the l x d sketch B_hat."""
+        """The eigen-shrink of Algorithm 5: the l x d sketch B_hat."""
         B = self.pre_query(lb, ub)
         lam, V = np.linalg.eigh(B)
         lam, V = lam[::-1], V[:, ::-1]

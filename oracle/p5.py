@@ -3,7 +3,7 @@ plain FP64 (oracle; test infrastructure only).
 
 m sites each run AeroSketch (Algorithms 3-5) with a threshold theta that
 the coordinator controls; the coordinator sums the sites' snapshot terms into
-B and answers queries from B (Algorithm 5 lines 5-7 on B).
+B and answers queries from B (the eigen-shrink of Algorithm 5 on B).
 
 Site j, for each row a (Algorithm 10, site Update):
   F_j += ||a||^2; if F_j >= (eps/m) F_hat: send F_j, F_j = 0;

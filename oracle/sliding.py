@@ -12,7 +12,7 @@ level's snapshots (Z, Z^T C'^T C') and raw heavy rows.  For each row a_i
 Query at time T: the lowest level j whose queue is empty or starts at
 S_j[0].s <= T - N + 1; B = C_j^T C_j + the snapshot terms and the raw rows
 a^T a of S_j with t in (T-N, T]; eigendecomposition, shrink by lambda_l, top
-l rows (Algorithm 5 lines 5-7).
+l rows (the eigen-shrink of Algorithm 5).
 
 Readings (also in the design notes):
   R15 s = S[-1].t + 1 for every item (Algorithm 4 prints +1, Algorithm 6's raw

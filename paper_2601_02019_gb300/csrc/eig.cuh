@@ -1,10 +1,9 @@
 // FP64 symmetric eigensolver run by one thread block.
 //
 // Used for the small core factorisations of AeroSketch: the FD shrink's
-// eigendecomposition of the 2l x 2l Gram G = C~ C~^T (the SVD of Algorithm 4
-// line 3 computed through its Gram), the k x k matrices of the Rayleigh-Ritz
-// step of Algorithm 2 (lines 4-5), and the query's eigendecomposition
-// (Algorithm 5 line 5).
+// eigendecomposition of the 2l x 2l Gram G = C~ C~^T (the SVD of Algorithm 4's
+// FD shrink computed through its Gram), the k x k matrices of the Rayleigh-Ritz
+// step of Algorithm 2, and the query's eigendecomposition (Algorithm 5).
 //
 // Method (textbook dense symmetric eigensolver):
 //   1. Householder reduction to tridiagonal form, A = Q T Q^T with

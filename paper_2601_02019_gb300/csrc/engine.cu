@@ -293,7 +293,7 @@ as_status tc_gram_rows(as_sketch* h, int r, int b, const UmmaOperand& Bmap, int 
   return launch_gram_reduce(h->s, P, M, (long long)b * M, S, M, r, b, h->G, h->n2);
 }
 
-// Algorithm 4 lines 3-4: FD shrink of the full buffer through its Gram.
+// The FD shrink of Algorithm 4 (Section 2.3) on the full buffer, through its Gram.
 as_status fd_shrink(as_sketch* h) {
   const int n2 = h->n2, ell = h->ell, d = h->d;
   AS_CUDA_TRY(cudaMemcpyAsync(h->Gtmp, h->G, (size_t)n2 * n2 * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
@@ -375,7 +375,8 @@ size_t prb_max(const as_sketch* h) {
   return std::max((size_t)(h->ldc / 64) * h->bmax * h->n2, (size_t)(h->n2p / 64) * (h->ell - 1) * h->d);
 }
 
-// Algorithm 4 lines 14-16 for the first xi columns of the last SI (k columns).
+// The snapshot and residual step of Algorithm 4 for the first xi columns of
+// the last SI (k columns).
 as_status dump(as_sketch* h, int xi, int k, int64_t i) {
   const int d = h->d, r = h->r, ldc = h->ldc, n2 = h->n2;
   as_status st = arena_reserve(h, (size_t)2 * d * xi);
@@ -431,7 +432,8 @@ as_status si_f64(as_sketch* h, int64_t i, int jsub, int k, int q) {
   return fetch(h, h->si.ritz, k);
 }
 
-// Algorithm 7 in place of Algorithm 4 line 11 (doubling step j, k columns):
+// Algorithm 7 in place of Algorithm 4's simultaneous iteration (doubling step
+// j, k columns):
 // amp_r simultaneous iterations with eps_SI = 0.2, SI h drawing its test matrix
 // at sub-index j + 64 (h-1); each is scored by the largest of amp_s power-
 // iteration estimates (start vectors at sub-index 64 h + g) of the top
@@ -471,51 +473,58 @@ as_status amplified_si(as_sketch* h, int64_t i, int j, int k, double theta, int*
   return si_f64(h, i, j + 64 * (hbest - 1), k, h->q_amp);
 }
 
-// Algorithm 4 lines 7-17 for row i on the current state, in FP64.  When the
-// gate outcome is already known (from the batched pass, outside its tie band)
-// it is passed in and the power iteration is not repeated.
+// The decision part of Algorithm 4 for row i on the current state (the
+// power-iteration gate, the doubling simultaneous iteration, the selection of
+// xi components and the dump), in FP64; Algorithm 7 replaces each
+// simultaneous iteration when amplification is on.  The batched pass has
+// usually decided the gate already: outside its tie band the outcome comes in
+// as known_gate (with its estimate sig2) and no FP64 power iteration runs.
+// For the first doubling step (k = 2) of a large buffer the batch also hands
+// over its iterated basis (column batch_col of the batch's X), and only the
+// FP64 Rayleigh-Ritz step is redone.  A dump ends the doubling loop as soon
+// as the k-th Ritz value falls below theta; xi = 0 leaves the state as it is.
 as_status finish_row(as_sketch* h, int64_t i, double theta, int known_gate, double sig2, int batch_col = -1,
                      int batch_ld = 0) {
   as_status st = AS_OK;
   if (known_gate < 0) {
-    st = pi_f64(h, i, &sig2);                        // line 7
+    st = pi_f64(h, i, &sig2);
     if (st != AS_OK) return st;
   }
-  const bool gate = (known_gate >= 0) ? (known_gate == 1) : (sig2 >= theta / 2.0 && sig2 > 0.0);  // line 8
+  const bool gate = (known_gate >= 0) ? (known_gate == 1) : (sig2 >= theta / 2.0 && sig2 > 0.0);
   if (!gate) return AS_OK;
   h->st.gates++;
   as_event ev{};
   ev.i = i;
   ev.sig2_pi = sig2;
   ev.theta = theta;
-  for (int j = 1; j <= h->jmax; ++j) {              // line 9
-    const int k = std::min(std::min(1 << std::min(j, 30), h->ell), h->d);  // line 10
-    if (h->amp_r > 0) {                             // Algorithm 7 in place of line 11
+  for (int j = 1; j <= h->jmax; ++j) {
+    const int k = std::min(std::min(1 << std::min(j, 30), h->ell), h->d);   // k = 2, 4, ... capped at min(l, d)
+    if (h->amp_r > 0) {
       int hk = 0;
       st = amplified_si(h, i, j, k, theta, &hk);
       if (st == AS_OK && j <= 16) ev.amp_choice |= (uint64_t)hk << (4 * (j - 1));
-    } else if (j == 1 && k == 2 && batch_col >= 0) {  // iterated basis from the batched pass
+    } else if (j == 1 && k == 2 && batch_col >= 0) {
       st = launch_si_rr_from_batch(h->s, h->G, h->n2, h->r, h->pb.X, batch_col, h->si, h->dstatus);
       if (st == AS_OK) st = fetch(h, h->si.ritz, k);
       h->st.si_runs++;
     } else {
-      st = si_f64(h, i, j, k, h->q);                // line 11
+      st = si_f64(h, i, j, k, h->q);
     }
     if (st != AS_OK) return st;
-    const double* ritz = h->h_buf;
+    const double* ritz = h->h_buf;   // Ritz values, descending
     ev.ritz_1 = ritz[0];
     ev.ritz_k = ritz[k - 1];
-    if (ritz[k - 1] < theta) {                      // line 12
-      int xi = 0;                                   // line 13
+    if (ritz[k - 1] < theta) {   // the subspace holds every component at or above theta
+      int xi = 0;
       for (int c = 0; c < k; ++c)
         if (ritz[c] >= theta && ritz[c] > 0.0) ++xi;
       ev.j_stop = j;
       ev.xi = xi;
-      if (xi >= 1) {                                // lines 14-16
+      if (xi >= 1) {
         st = dump(h, xi, k, i);
         if (st != AS_OK) return st;
       }
-      break;                                        // line 17
+      break;
     }
   }
   if (h->cfg.flags & AS_TRACE_DECISIONS) h->trace.push_back(ev);
@@ -535,8 +544,8 @@ struct BlockCtx {
   bool deferred = false;   // the FP32 batched iterations are left to the caller (a grouped launch)
 };
 
-// Launch phase of one block (Algorithm 8 lines 1-3 and Algorithm 4 lines 1, 7
-// and the first doubling step of 9-11 for every row, speculatively): ingest,
+// Launch phase of one block (Algorithm 8's threshold update and Algorithm 4's
+// insert, gate and first doubling step for every row, speculatively): ingest,
 // Gram rows, mirrors of G and the batched iterations.  With defer, a block
 // that would run the FP32 persistent kernel is left for a grouped launch
 // (block_job describes it).
@@ -552,7 +561,7 @@ as_status block_prepare(as_sketch* h, const float* src, int64_t navail, BlockCtx
   if (h->prof) h->prof->end(PK_INGEST, h->s, 2.0 * b * (double)d, 8.0 * b * (double)d);
   st = tc_split_rows(h, r0, r0 + b);
   if (st != AS_OK) return st;
-  // line 1 for the whole block: G gains the new rows and columns (a rejected
+  // the insert for the whole block: G gains the new rows and columns (a rejected
   // row was ingested as zeros, so nothing non-finite reaches the products)
   if (h->prof) h->prof->begin(PK_GRAM, h->s);
   st = h->tc ? tc_gram_rows(h, r0, b, h->mCB64, 64)
@@ -647,7 +656,7 @@ as_status block_finish(as_sketch* h, const BlockCtx& c, int64_t* used, bool* bad
     if (st != AS_OK) return st;
     if (bb == 0) { *used = 0; return AS_OK; }
   }
-  // thresholds before each row (Algorithm 8 lines 2-3)
+  // thresholds before each row (Algorithm 8)
   std::vector<double> Ft(bb), th(bb);
   double F = h->F;
   for (int t = 0; t < bb; ++t) {
@@ -715,7 +724,7 @@ as_status block_finish(as_sketch* h, const BlockCtx& c, int64_t* used, bool* bad
   h->theta = th[tstar];
   *used = tstar + 1;
   h->bnext = std::max(8, std::min(h->bmax, 2 * (tstar + 1)));
-  if (h->r == n2) {                                  // lines 2-4
+  if (h->r == n2) {   // the buffer is full: FD shrink, then the row's decisions
     st = fd_shrink(h);
     if (st != AS_OK) return st;
     return finish_row(h, h->T, h->theta, -1, 0.0);
@@ -750,7 +759,7 @@ as_status ensure_bx(as_sketch* h) {
 }
 
 // B += Z Y + (Z Y)^T - Z (Y Z) Z^T for every snapshot of `src` taken at a
-// row <= tmax (Algorithm 5 line 4), in time order, on stream st; the scratch
+// row <= tmax (Algorithm 5), in time order, on stream st; the scratch
 // of `scr` (xi x xi and d x xi) is grown as needed.
 as_status add_snapshot_terms(const as_sketch* src, int64_t tmax, double* B, as_sketch* scr, cudaStream_t st,
                              int64_t tmin_excl = INT64_MIN) {
@@ -785,7 +794,7 @@ as_status add_snapshot_terms(const as_sketch* src, int64_t tmax, double* B, as_s
   return st2;
 }
 
-// Algorithm 5 lines 1-4 with lb = 0, ub = t: the residual C_t only at the
+// The matrix B of Algorithm 5 (before its eigendecomposition) with lb = 0, ub = t: the residual C_t only at the
 // current time (t = T; older residuals are not stored) plus the snapshot
 // terms with t_j <= t, plus (current time only) the absorbed terms Bx.
 as_status build_query_gram(as_sketch* h, int64_t t, double* B) {
@@ -806,7 +815,7 @@ as_status build_query_gram(as_sketch* h, int64_t t, double* B) {
 }
 
 // Eigendecomposition of the device matrix B (d x d FP64, destroyed) and the
-// shrink of Algorithm 5 lines 5-7: the l x d sketch to out (host or device,
+// eigen-shrink of Algorithm 5: the l x d sketch to out (host or device,
 // row stride ldo).  Synchronises.
 as_status eig_shrink_to(as_sketch* h, double* B, float* out, int64_t ldo) {
   const int d = h->d, ell = h->ell;
@@ -1150,7 +1159,7 @@ static as_status normalize_config(as_config& c, int& amp_r, int& amp_s) {
   if (!(c.eps >= 0.0) || std::isinf(c.eps)) return AS_EINVAL;
   if (c.ell == 0) {
     if (c.eps <= 0.0) return AS_EINVAL;
-    c.ell = (int32_t)std::ceil(2.0 / c.eps);  // Algorithm 3 line 1
+    c.ell = (int32_t)std::ceil(2.0 / c.eps);  // Algorithm 3
   }
   if (c.ell < 1 || 2 * (int64_t)c.ell > c.d) return AS_EINVAL;
   if (c.eps == 0.0) c.eps = 2.0 / c.ell;
@@ -1484,10 +1493,10 @@ as_status sketch_query(as_sketch* h, int64_t t, float* out, int64_t ldo, int32_t
   if (st == AS_OK) st = dalloc(&w, big_q ? eig_large_work_doubles(d, ell) : eig_work_doubles(d, ell));
   if (st == AS_OK) st = dalloc(&o, (size_t)ell * d);
   if (st == AS_OK) st = build_query_gram(h, t, B);
-  if (st == AS_OK)                                                          // Algorithm 5 line 5
+  if (st == AS_OK)   // Algorithm 5: eigendecomposition of B, then the shrink by lambda_l
     st = big_q ? launch_eig_large(h->s, d, B, d, ell, lam, V, ell, w, nullptr, h->dstatus)
                : launch_eig(h->s, d, B, d, ell, lam, V, ell, w);
-  if (st == AS_OK) st = launch_shrink_rows(h->s, d, ell, lam, V, ell, o, d);  // line 6
+  if (st == AS_OK) st = launch_shrink_rows(h->s, d, ell, lam, V, ell, o, d);
   if (st == AS_OK) {
     cudaError_t e = cudaMemcpy2DAsync(out, (size_t)ldo * sizeof(float), o, (size_t)d * sizeof(float),
                                       (size_t)d * sizeof(float), (size_t)ell, cudaMemcpyDefault, h->s);

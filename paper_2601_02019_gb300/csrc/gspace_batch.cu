@@ -1,7 +1,7 @@
 // The FP64 single-row path of the G-space iterations for large buffers
 // (power iteration, simultaneous iteration, Rayleigh-Ritz from the batched
 // basis), the incremental FP32 mirror of G read by the batched iterations
-// (batch_persist.cu), and the dump kernels (Algorithm 4 lines 14-16).
+// (batch_persist.cu), and the dump kernels (the snapshot and residual step of Algorithm 4).
 #include <algorithm>
 
 #include "eig.cuh"
@@ -241,7 +241,7 @@ __global__ void promote_pair_kernel(const float* X, int n2, int col0, int m, int
   }
 }
 
-// ---- dump (Algorithm 4 lines 14-16) -----------------------------------------
+// ---- dump (snapshot and residual, Algorithm 4) -------------------------------
 // Partial sums over row chunks s: Zp[s][c][a - ab] = sum_p C[p][c] WU[p][a] and
 // Yp[s][a - ab][c] = sum_p GWU[p][a] C[p][c] for a in [a0, a0+na) inside the
 // column block [ab, ab + w), one thread per column c.  Blocks of at most

@@ -104,7 +104,7 @@ as_status launch_gram_reduce(cudaStream_t s, const float* P, long long ldp, long
 as_status launch_gram_rows_skinny(cudaStream_t s, const float* C, int ldc, int d, int r, int b, double* G, int n2,
                                   float* P, size_t p_cap);
 
-// Dump (Algorithm 4 lines 14-16) for the first xi columns of W U / G W U
+// Dump (the snapshot and residual step of Algorithm 4) for the first xi columns of W U / G W U
 // (row-major n2 x k): Z = C'^T (WU)_xi, Y = (GWU)_xi^T C', C -= (GWU)_xi Z^T,
 // G -= (GWU)_xi (GWU)_xi^T.  work: dump_work_doubles(d, n2, xi).
 size_t dump_work_doubles(int d, int n2, int xi);
@@ -242,7 +242,7 @@ as_status launch_split_bf16(cudaStream_t s, const float* src, long long lds, int
 // Library-internal access to a sketch for the runtimes built on sketches
 // (engine.cu): stream, rows fed, the snapshot queue's times (the sketch's own
 // row indices), the windowed query Gram, raw-row Grams, dropping the oldest
-// snapshots, and the eigen-shrink of a device B (Algorithm 5 lines 5-7).
+// snapshots, and the eigen-shrink of a device B (the eigen-shrink of Algorithm 5).
 // Runs f(0) .. f(n-1) on the library's worker threads and waits for all.
 void run_parallel(int n, const std::function<void(int)>& f);
 // Several sketches updated in lockstep: each step prepares one block of every

@@ -9,7 +9,7 @@
 //   each message: F_hat += F_j, msgs += 1; at msgs >= m: msgs = 0 and
 //   broadcast F_hat (every site then uses theta = (eps/m) F_hat);
 //   each snapshot (Z, Y = Z^T C'^T C'): B += Z Y + Y^T Z^T - Z (Y Z) Z^T;
-//   Query: Algorithm 5 lines 5-7 on B.
+//   Query: the eigen-shrink of Algorithm 5 on B.
 // Readings: a site starts with theta = +inf (Algorithm 10 leaves the initial
 // threshold open; with 0 the stop test of Algorithm 2 would depend on the
 // rounding sign of numerically zero Ritz values), its threshold after a

@@ -12,7 +12,7 @@
 // Query at time T: the lowest level whose queue is empty or starts at
 // s <= max(1, T - N + 1) (the top level if none); B = the level's residual
 // C^T C + its queued snapshot terms and raw rows a^T a with t in (T-N, T];
-// then Algorithm 5 lines 5-7.
+// then the eigen-shrink of Algorithm 5.
 //
 // A level's sketch computation does not depend on its queue, so a block of
 // rows runs each level's sketch over its runs of light rows first, then

@@ -56,7 +56,7 @@ def _compare(p, A, d, ell, seed=0, err_tol=1e-6, err_rel=0.0, tie=TIE, b_tol=1e-
     AtA = A.astype(np.float64).T @ A.astype(np.float64)
     eg, eo = cov_err(A, Bg, AtA), cov_err(A, o.query(), AtA)
     assert abs(eg - eo) <= max(err_tol, err_rel * eo), (eg, eo)
-    # the pre-query matrix B_T (Algorithm 5 lines 1-4) agrees too
+    # the pre-query matrix B_T of Algorithm 5 agrees too
     Bt = s.query_gram()
     assert np.abs(Bt - o.pre_query()).max() <= b_tol * np.trace(AtA)
     # and the paper's deterministic bound holds on the GPU result
@@ -221,7 +221,7 @@ def test_full_size_window_d4096_l1024():
     Aw = A[start:].astype(np.float64)
     scale = np.trace(C0.astype(np.float64).T @ C0.astype(np.float64)) + np.sum(Aw * Aw)
     assert np.abs(C1.T @ C1 - o.C.T @ o.C).max() <= 1e-5 * scale
-    # what the window added to B (Algorithm 5 lines 1-4) agrees
+    # what the window added to B (Algorithm 5, before the eigendecomposition) agrees
     dB_gpu = s.query_gram() - B0
     dB_orc = o.pre_query() - C0.astype(np.float64).T @ C0.astype(np.float64)
     assert np.abs(dB_gpu - dB_orc).max() <= 1e-5 * scale

@@ -67,7 +67,7 @@ def test_historical_query_shrinks_and_validates():
     Bh = s.query(ub=t)
     B = s.pre_query(ub=t)
     lam = np.sort(np.linalg.eigvalsh(B))[::-1]
-    # Algorithm 5 lines 5-7: B_hat^T B_hat = sum_j max(lam_j - lam_l, 0) v_j v_j^T
+    # the eigen-shrink of Algorithm 5: B_hat^T B_hat = sum_j max(lam_j - lam_l, 0) v_j v_j^T
     got = np.sort(np.linalg.eigvalsh(Bh.T @ Bh))[::-1][:3]
     want = np.maximum(lam[:3] - lam[2], 0.0)
     assert np.allclose(got, want, rtol=1e-9, atol=1e-9 * lam[0])
