@@ -38,6 +38,10 @@ WORKLOADS = {
 FP32_SIMT_LANES_PER_SM = 128   # FP32 FMA lanes per SM
 N_SM = 152
 FP64_NOMINAL_TFLOPS = 1.25
+# FP32 instructions of one df64 multiply-add (df_fma: TwoProduct 2, TwoSum 6,
+# three corrections 3, FastTwoSum renormalisation 3, one add 1): the df64
+# eigensolver's peak is the FP32 issue rate x 2 flop / this count
+DF64_FP32_OPS_PER_FMA = 15
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as
 # it stands (a full-size launch of `python bench.py --steps 1 --warmup 3
 # --forms bf16x6 --no-cpu-baseline --no-err --no-e2e`, grid 128, 2l = 2048);
@@ -244,7 +248,7 @@ def our_arm(args) -> None:
     tot_prof = sum(x["total_ms"] for x in prof if x["name"] != "eig_fp64") or 1.0
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = N_SM * FP32_SIMT_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    kinds = {"batch_persist": "fp32", "batch_tc": "tensor", "eig_tridiag": "fp64", "eig_backtransform": "fp64",
+    kinds = {"batch_persist": "fp32", "batch_tc": "tensor", "eig_tridiag": "df64", "eig_backtransform": "df64",
              "ingest": "hbm"}
     single = [x for x in prof if x["name"] in kinds and (x["flops"] > 0 or x["bytes"] > 0)]
     top = max(single, key=lambda x: x["total_ms"])
@@ -254,8 +258,11 @@ def our_arm(args) -> None:
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
         src = f"{peak_src} copy bandwidth"
     elif kind == "tensor":
-        # the useful flops (2 m_t^2 per column product); the kernel issues three
-        # split-BF16 passes of each, so the tensor pipe does 3x this work
+        # algorithmic flops: the power iterations of the rows whose gate the batch
+        # decided and the k = 2 simultaneous iterations of the gated rows that used
+        # it (2 m_t^2 per column product).  The kernel issues more: every row of the
+        # block (rows after the first state-changing row are fed again), and three
+        # split-BF16 passes of each product; issued_flops counts the rows, once.
         ach = top["flops"] / (top["total_ms"] / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s"}
         src = f"{peak_src} cuBLAS bf16 GEMM, sustained (the kernel runs inside a long step)"
@@ -266,12 +273,17 @@ def our_arm(args) -> None:
                "(max SM clock of the measured peaks file)")
     else:
         ach = top["flops"] / (top["total_ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s"}
-        src = "FP64 nominal 1.25 TFLOP/s (no FP64 measurement on this pool)"
+        roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak / DF64_FP32_OPS_PER_FMA, "unit": "TFLOP/s"}
+        src = (f"df64 on the FP32 pipes: the FP32 SIMT peak ({fp32_peak:.1f} TFLOP/s) / "
+               f"{DF64_FP32_OPS_PER_FMA} FP32 operations per df64 multiply-add")
     roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": TRAFFIC_BYTES.get(top["name"]),
                  "kernel": top["name"],
                  "launches": top["launches"], "avg_launch_us": 1000 * top["total_ms"] / max(1, top["launches"]),
                  "peak_source": src})
+    if top.get("issued_flops", 0.0) > top["flops"] > 0.0:
+        roof["issued_flops_per_launch"] = top["issued_flops"] / max(1, top["launches"])
+        roof["algorithmic_flops_per_launch"] = top["flops"] / max(1, top["launches"])
+        roof["issued_frac"] = top["issued_flops"] / (top["total_ms"] / 1e3) / 1e12 / roof["peak"]
 
     # end to end through the C ABI from pinned host memory (host->device copy
     # inside the timed region, device->host read of the counters each step)
@@ -323,9 +335,10 @@ def our_arm(args) -> None:
         out = {
             "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": ws, "steps": K, "warmup": W,
             "ms_per_step": hr["t_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32 products, f64 core", "bf16": "bf16 tensor products (f32 acc), f64 core",
-                      "bf16x3": "2-level split-bf16 tensor products (f32 acc), f64 core",
-                      "bf16x6": "3-level split-bf16 tensor products (f32 acc), f64 core"}[head],
+            "dtype": {"fp32": "f32 products", "bf16": "bf16 tensor products (f32 acc)",
+                      "bf16x3": "2-level split-bf16 tensor products (f32 acc)",
+                      "bf16x6": "3-level split-bf16 tensor products (f32 acc)"}[head]
+                     + "; f64 orthonormalisation and Rayleigh-Ritz; df64 (~48-bit) eigensolver",
             "data": "synthetic",
             "config": {"workload": args.workload, "d": d, "ell": ell, "rows_per_step": B, "precision": head,
                        "timed_rows": f"{W * B}..{(W + K) * B - 1} of the stream (after {W * B} warm-up rows)",
@@ -462,7 +475,7 @@ def serve_arm(args) -> None:
         "metric": "rows/s of the serving loop at saturation (host-fed requests)", "value": sat["rows_per_s"],
         "unit": "rows/s", "n_gpus": 1, "steps": phases, "warmup": args.warmup,
         "ms_per_step": 1e3 * sat["span_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 products, f64 core", "data": "synthetic",
+        "dtype": "f32 products; f64 orthonormalisation and Rayleigh-Ritz; df64 (~48-bit) eigensolver", "data": "synthetic",
         "config": {"workload": args.workload, "sessions": S, "admitted": len(sid), "refused": refused,
                    "requests_per_phase": len(reqs), "rows_per_phase": int(sum(b for _, b, _ in reqs)),
                    "footprint_GB": fp / 1e9, "open_s": open_s, "workers": 16,
@@ -513,7 +526,7 @@ def group_arm(args) -> None:
         "metric": "rows/s of sketch_update_grouped (16 sketches, grouped launches)",
         "value": out["grouped"]["rows_per_s"],
         "unit": "rows/s", "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": out["grouped"]["ms_per_step"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 products, f64 core",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 products; f64 orthonormalisation and Rayleigh-Ritz; df64 (~48-bit) eigensolver",
         "data": "synthetic",
         "config": {"workload": args.workload, "d": d, "ell": ell, "sketches": m, "rows_per_sketch_per_step": b,
                    "timing": "host clock around synchronous calls, device synchronised on both sides",
@@ -572,7 +585,7 @@ def extra_arm(args) -> None:
         "metric": "rows/s of the " + ("P5 round (all sites)" if args.workload.startswith("p5")
                                       else "sliding-window update"),
         "value": value, "unit": "rows/s", "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": ms / K,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 products, f64 core",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 products; f64 orthonormalisation and Rayleigh-Ritz; df64 (~48-bit) eigensolver",
         "data": "synthetic", "config": cfg, "clocks": clk.summary(),
     }))
 

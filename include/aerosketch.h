@@ -60,10 +60,13 @@ typedef enum {
                           the eigen-shrink of Algorithm 5 on that sum */
 } as_mode;
 
-/* Arithmetic of the products.  In every form the orthonormalisations, the
- * Rayleigh-Ritz steps and the eigendecompositions run in FP64, and every
- * branch of Algorithm 4 is decided on FP64 values (values inside a 1e-4
- * relative band of a threshold are recomputed in FP64).
+/* Arithmetic of the products.  In every form the orthonormalisations and the
+ * Rayleigh-Ritz steps run in FP64; the eigensolver of the FD shrink (and of
+ * queries with d > 256) runs in double-float arithmetic (df64: pairs of FP32
+ * values, about 48 significant bits; its O(n) scalars and inverse iteration
+ * in FP64), the smaller eigendecompositions in FP64.  Every branch of
+ * Algorithm 4 is decided on FP64 values (values inside a 1e-4 relative band
+ * of a threshold are recomputed in FP64).
  *   AS_FP32_PLAIN  SIMT FP32 products, FP32 partial sums combined in FP64.
  *   AS_BF16        d-side products (Gram rows, FD rebuild) on the tcgen05
  *                  tensor cores with BF16 operands and FP32 accumulation;
@@ -138,8 +141,14 @@ typedef struct {
   char name[32];
   int64_t launches;
   double total_ms;
-  double flops;     /* algorithmic floating-point operations, summed over launches */
+  double flops;     /* algorithmic floating-point operations, summed over launches.  For the
+                       batched iterations ("batch_tc", "batch_persist"): the power iterations
+                       of the rows whose gate they decided and the k = 2 simultaneous
+                       iterations of the gated rows that used them, 2 m_t^2 per product */
   double bytes;     /* algorithmic DRAM bytes, summed over launches */
+  double issued_flops;  /* floating-point operations the launches issued (for the batched
+                           iterations: every row of every block, including the rows after a
+                           block's first state-changing row, which are fed again) */
 } as_kernel_stat;
 
 /* One decision record (AS_TRACE_DECISIONS): a row whose gate passed. */
@@ -417,10 +426,12 @@ as_status sketch_profile(as_sketch* h, as_kernel_stat* out, int32_t cap, int32_t
 /* Clear the kernel-class timings. */
 as_status sketch_profile_reset(as_sketch* h);
 
-/* FP64 symmetric eigendecomposition on the current device: the core
- * factorisation that the FD shrink (Algorithm 4, through the Gram matrix of
- * the buffer) and the query (Algorithm 5) use.  A is n x n,
- * row-major, host memory (only its values are read; it is not modified).
+/* Symmetric eigendecomposition on the current device, FP64 in and out: the
+ * core factorisation that the FD shrink (Algorithm 4, through the Gram matrix
+ * of the buffer) and the query (Algorithm 5) use.  n <= 256: one thread block
+ * in FP64; n > 256: the GPU-wide solver in df64 (about 48 significant bits).
+ * A is n x n, row-major, host memory (only its values are read; it is not
+ * modified).
  * Writes the nev largest eigenvalues in descending order to evals (host) and
  * the matching unit eigenvectors as the columns of vecs (host, n x nev,
  * row-major).  1 <= nev <= n.  Synchronous. */
@@ -438,17 +449,20 @@ as_status as_tc_gemm(int32_t M, int32_t N, int32_t K, const float* A, const floa
                      double* out);
 
 /* as_symeig without any allocation, for callers that cannot allocate device
- * memory (inside a CUDA stream capture, in allocator callbacks, on serving
- * paths that forbid allocation after start-up).  The paper has no
- * counterpart: this is a library service.  A (n x n, row-major, device
- * memory, not modified), evals (nev, device) and vecs (n x nev row-major,
- * device) are the caller's; the scratch space is a fixed device array of
- * 788,992 bytes inside the library, reserved on every GPU that loads it.
- * n must be <= 128 (AS_EINVAL otherwise).  Work is ordered on cuda_stream
- * (NULL = legacy default stream) and the call returns without synchronising.
- * All calls share the scratch array: calls that overlap on the GPU race.  The
- * first call on a device looks up the array's address; make it before any
- * stream capture. */
+ * memory: allocator callbacks, and real-time serving paths that forbid
+ * allocation after start-up.  The paper has no counterpart: this is a library
+ * service.  A (n x n, row-major, device memory, not modified), evals (nev,
+ * device) and vecs (n x nev row-major, device) are the caller's; the scratch
+ * space is a fixed device array of 788,992 bytes inside the library, reserved
+ * on every GPU that loads it until the process exits.  n must be <= 128
+ * (AS_EINVAL otherwise).  Work is ordered on cuda_stream (NULL = legacy default
+ * stream) and the call returns without synchronising.  All calls share the
+ * scratch array and it keeps the last call's contents (every value the solver
+ * reads is written earlier in the same call): calls that overlap on the GPU
+ * race.  The first call on a device, and the first after that device's
+ * context was destroyed and made again (cudaDeviceReset), looks up the array's
+ * address; make that first call before any stream capture.  AS_ENOTSUP if the
+ * driver entry point for the current context cannot be found. */
 as_status as_symeig_noalloc(int32_t n, const double* A, int32_t nev, double* evals, double* vecs, void* cuda_stream);
 
 /* Free every resource of the sketch.  NULL is a no-op. */

@@ -78,7 +78,7 @@ class AsEvent(ct.Structure):
 
 class AsKernelStat(ct.Structure):
     _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int64), ("total_ms", ct.c_double),
-                ("flops", ct.c_double), ("bytes", ct.c_double)]
+                ("flops", ct.c_double), ("bytes", ct.c_double), ("issued_flops", ct.c_double)]
 
 
 class AeroSketchError(RuntimeError):
@@ -264,7 +264,8 @@ class Sketch:
         n = ct.c_int32()
         _check(lib().sketch_profile(self._h, arr, 32, ct.byref(n)), "sketch_profile")
         return [{"name": arr[t].name.decode(), "launches": arr[t].launches, "total_ms": arr[t].total_ms,
-                 "flops": arr[t].flops, "bytes": arr[t].bytes} for t in range(min(n.value, 32))]
+                 "flops": arr[t].flops, "bytes": arr[t].bytes, "issued_flops": arr[t].issued_flops}
+                for t in range(min(n.value, 32))]
 
     def profile_reset(self) -> None:
         _check(lib().sketch_profile_reset(self._h), "sketch_profile_reset")

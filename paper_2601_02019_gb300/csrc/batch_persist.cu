@@ -712,7 +712,8 @@ as_status launch_batch_persist(cudaStream_t s, const float* Gf, int n2, int r0, 
       m1 += m;
     }
     const double prods = (double)(k_pi + 1) + 2.0 * (double)(q + 1);
-    prof->end(PK_BATCH_GEMM, s, 2.0 * m2 * prods, 4.0 * (double)mmax * mmax + 8.0 * m1 * prods);
+    // algorithmic work recorded at the block's decisions (add_work); issued here
+    prof->end(PK_BATCH_GEMM, s, 0.0, 4.0 * (double)mmax * mmax + 8.0 * m1 * prods, 2.0 * m2 * prods);
   }
   return AS_OK;
 }

@@ -611,7 +611,9 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
       m1 += m;
     }
     const double prods = (double)(k_pi + 1) + 2.0 * (double)(q + 1);
-    prof->end(PK_BATCH_TC, s, 2.0 * m2 * prods, 2.0 * npass / 3.0 * (double)kpad * kpad + 8.0 * m1 * prods);
+    // the algorithmic work of the block is recorded when its decisions are
+    // taken (add_work); here the work issued for every row of the block
+    prof->end(PK_BATCH_TC, s, 0.0, 2.0 * npass / 3.0 * (double)kpad * kpad + 8.0 * m1 * prods, 2.0 * m2 * prods);
   }
   *used = true;
   return AS_OK;

@@ -64,11 +64,11 @@ const char* const kProfNames[PK_COUNT] = {"batch_persist",     "batch_prep",    
 
 // CUDA-event timer per kernel class; pairs are resolved lazily.
 struct EventProf final : Prof {
-  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
+  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes, issued; };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   int64_t launches[PK_COUNT] = {};
-  double ms[PK_COUNT] = {}, flops[PK_COUNT] = {}, bytes[PK_COUNT] = {};
+  double ms[PK_COUNT] = {}, flops[PK_COUNT] = {}, bytes[PK_COUNT] = {}, issued[PK_COUNT] = {};
   cudaEvent_t open_ev[PK_COUNT] = {};
 
   cudaEvent_t get() {
@@ -81,12 +81,13 @@ struct EventProf final : Prof {
     open_ev[cls] = get();
     cudaEventRecord(open_ev[cls], s);
   }
-  void end(int cls, cudaStream_t s, double f, double b) override {
+  void end(int cls, cudaStream_t s, double f, double b, double iss = -1.0) override {
     cudaEvent_t e = get();
     cudaEventRecord(e, s);
-    pending.push_back(Pending{cls, open_ev[cls], e, f, b});
+    pending.push_back(Pending{cls, open_ev[cls], e, f, b, iss < 0.0 ? f : iss});
     if (pending.size() > 8192) resolve();
   }
+  void add_work(int cls, double f) override { flops[cls] += f; }
   void resolve() {
     for (Pending& p : pending) {
       cudaEventSynchronize(p.b);
@@ -96,6 +97,7 @@ struct EventProf final : Prof {
       launches[p.cls] += 1;
       flops[p.cls] += p.flops;
       bytes[p.cls] += p.bytes;
+      issued[p.cls] += p.issued;
       pool.push_back(p.a);
       pool.push_back(p.b);
     }
@@ -103,7 +105,7 @@ struct EventProf final : Prof {
   }
   void reset() {
     resolve();
-    for (int c = 0; c < PK_COUNT; ++c) { launches[c] = 0; ms[c] = flops[c] = bytes[c] = 0; }
+    for (int c = 0; c < PK_COUNT; ++c) { launches[c] = 0; ms[c] = flops[c] = bytes[c] = issued[c] = 0; }
   }
   ~EventProf() override {
     for (Pending& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
@@ -542,6 +544,7 @@ constexpr double kTieBand = 1e-4;
 struct BlockCtx {
   int b = 0, nbb = 0, r0 = 0;
   bool deferred = false;   // the FP32 batched iterations are left to the caller (a grouped launch)
+  int batch_cls = -1;      // profiler class of the block's own batched launch (-1: none or grouped)
 };
 
 // Launch phase of one block (Algorithm 8's threshold update and Algorithm 4's
@@ -595,6 +598,7 @@ as_status block_prepare(as_sketch* h, const float* src, int64_t navail, BlockCtx
                            3, h->dstatus, h->prof, &on_tc);
       if (st != AS_OK) return st;
     }
+    if (on_tc) c.batch_cls = PK_BATCH_TC;
     if (!on_tc) {
       if (defer) {
         c.deferred = true;
@@ -602,6 +606,7 @@ as_status block_prepare(as_sketch* h, const float* src, int64_t navail, BlockCtx
         st = launch_batch_persist(h->s, h->Gf, n2, r0, nbb, h->k_pi, h->q, h->key, (uint64_t)(h->T + 1), h->pb,
                                   h->dstatus, h->prof);
         if (st != AS_OK) return st;
+        c.batch_cls = PK_BATCH_GEMM;
       }
     }
   }
@@ -669,6 +674,7 @@ as_status block_finish(as_sketch* h, const BlockCtx& c, int64_t* used, bool* bad
   // scan for the first state-changing row
   int tstar = -1, gate_known = -1;
   double sig2_star = 0.0;
+  std::vector<char> gated((size_t)std::max(nb, 1), 0);
   for (int t = 0; t < nb; ++t) {
     const double theta = th[t];
     double s2 = sig2[t];
@@ -683,6 +689,7 @@ as_status block_finish(as_sketch* h, const BlockCtx& c, int64_t* used, bool* bad
     }
     const bool gate = s2 >= theta / 2.0 && s2 > 0.0;
     if (!gate) continue;
+    gated[(size_t)t] = 1;
     const double r1 = ritz[2 * (size_t)t];
     if (r1 >= theta * (1.0 - kTieBand) || h->amp_r > 0) {  // a dump is possible (amplified: always)
       tstar = t;
@@ -699,6 +706,27 @@ as_status block_finish(as_sketch* h, const BlockCtx& c, int64_t* used, bool* bad
       ev.ritz_1 = r1; ev.ritz_k = ritz[2 * (size_t)t + 1];
       h->trace.push_back(ev);
     }
+  }
+  // algorithmic work of the batch: the power iterations (k_PI products and the
+  // Rayleigh quotient, 2 m_t^2 flop each) of the rows whose decision it gave,
+  // and the k = 2 simultaneous iteration (q + 1 products of two columns) of the
+  // gated rows that used it; rows after the first state-changing one were
+  // speculation and are not counted
+  const int bcol = (h->big && h->amp_r == 0 && tstar >= 0) ? batch_si_col(nbb, tstar) : -1;
+  if (h->prof && c.batch_cls >= 0) {
+    const int t_end = (tstar >= 0) ? tstar + 1 : nb;
+    double w = 0.0;
+    for (int t = 0; t < t_end; ++t) {
+      const double m = (double)(r0 + t + 1);
+      w += 2.0 * m * m * (double)(h->k_pi + 1);
+    }
+    for (int t = 0; t < t_end; ++t) {
+      const bool gated_kept = (t < tstar || tstar < 0) ? gated[t] : (bcol >= 0);
+      if (!gated_kept) continue;
+      const double m = (double)(r0 + t + 1);
+      w += 2.0 * m * m * 2.0 * (double)(h->q + 1);
+    }
+    h->prof->add_work(c.batch_cls, w);
   }
   if (tstar < 0 && fills) { tstar = bb - 1; gate_known = -1; }
   if (tstar < 0) {
@@ -729,8 +757,7 @@ as_status block_finish(as_sketch* h, const BlockCtx& c, int64_t* used, bool* bad
     if (st != AS_OK) return st;
     return finish_row(h, h->T, h->theta, -1, 0.0);
   }
-  // large buffers reuse the batch's FP32-iterated basis for the k = 2 step
-  const int bcol = (h->big && h->amp_r == 0) ? batch_si_col(nbb, tstar) : -1;
+  // large buffers reuse the batch's FP32-iterated basis for the k = 2 step (bcol)
   if (h->prof) h->prof->begin(PK_EVENT, h->s);
   st = finish_row(h, h->T, h->theta, gate_known, sig2_star, bcol, 3 * nbb);
   if (h->prof) h->prof->end(PK_EVENT, h->s, 0.0, 0.0);
@@ -1623,6 +1650,7 @@ as_status sketch_profile(as_sketch* h, as_kernel_stat* out, int32_t cap, int32_t
       k.total_ms = h->prof->ms[c];
       k.flops = h->prof->flops[c];
       k.bytes = h->prof->bytes[c];
+      k.issued_flops = h->prof->issued[c];
     }
     ++n;
   }

@@ -27,9 +27,15 @@ enum ProfClass {
   PK_BATCH_TC,        // batched G-space iterations on tcgen05 (tensor forms)
   PK_COUNT
 };
+// end() records the algorithmic work of the bracketed launches; `issued` is
+// the floating-point work they issued when that differs (< 0: the same).  The
+// batched iterations compute every row of a block speculatively, so their
+// algorithmic work is known only when the block's decisions are taken, and
+// add_work() records it then.
 struct Prof {
   virtual void begin(int cls, cudaStream_t s) = 0;
-  virtual void end(int cls, cudaStream_t s, double flops, double bytes) = 0;
+  virtual void end(int cls, cudaStream_t s, double flops, double bytes, double issued = -1.0) = 0;
+  virtual void add_work(int cls, double flops) = 0;
   virtual ~Prof() {}
 };
 

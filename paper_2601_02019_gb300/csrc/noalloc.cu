@@ -11,9 +11,11 @@
 // process exits.  All calls share it and it keeps the last call's contents
 // (nothing in it has to start at zero: every value the solver reads is
 // written earlier in the same call).  Calls whose work overlaps on the GPU
-// race with each other.  The first call on a device looks up the array's
-// device address; make that first call before any stream capture.
-#include <atomic>
+// race with each other.  The first call on a device (and the first call after
+// that device's context was destroyed and made again, for example after
+// cudaDeviceReset, which loads the module and its array anew) looks up the
+// array's device address; make that first call before any stream capture.
+#include <mutex>
 
 #include "eig.cuh"
 #include "kernels.cuh"
@@ -29,7 +31,31 @@ constexpr size_t kNoAllocDoubles = (size_t)kNoAllocMaxN * kNoAllocMaxN + 2 * (si
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 constexpr int kMaxDevices = 64;
-std::atomic<double*> g_scratch_ptr[kMaxDevices] = {};   // device address of the array, per device
+// Per device: the context in which the array's address was looked up, and
+// that address.  A new context (after a device reset) holds a new copy of the
+// module, so the address is looked up again when the current context differs.
+struct ScratchAddr {
+  CUcontext ctx = nullptr;
+  double* ptr = nullptr;
+};
+ScratchAddr g_scratch[kMaxDevices];
+std::mutex g_scratch_mu;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+
+// cuCtxGetCurrent through the runtime's driver entry point (the library links
+// the CUDA runtime only).
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(p);
+  }();
+  return fn;
+}
 
 }  // namespace
 
@@ -39,14 +65,28 @@ extern "C" as_status as_symeig_noalloc(int32_t n, const double* A, int32_t nev, 
   int dev = 0;
   AS_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return AS_EINVAL;
-  if (!g_scratch_ptr[dev].load()) {
-    // once per device, with that device current: the host-side name of the
-    // array is only a stand-in, the kernels need its device address
-    void* p = nullptr;
-    AS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_scratch_ptr[dev].store((double*)p);
+  CtxGetCurrentFn get_ctx = ctx_get_current();
+  if (!get_ctx) return AS_ENOTSUP;
+  CUcontext ctx = nullptr;
+  if (get_ctx(&ctx) != CUDA_SUCCESS) return AS_EDEVICE;
+  if (!ctx) {   // no context current on this thread yet: cudaSetDevice makes the primary one current
+    AS_CUDA_TRY(cudaSetDevice(dev));
+    if (get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return AS_EDEVICE;
   }
-  double* Acopy = g_scratch_ptr[dev].load();
+  double* Acopy = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    ScratchAddr& sa = g_scratch[dev];
+    if (sa.ctx != ctx || !sa.ptr) {
+      // once per device and context, with that device current: the host-side
+      // name of the array is only a stand-in, the kernels need its device address
+      void* p = nullptr;
+      AS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      sa.ctx = ctx;
+      sa.ptr = (double*)p;
+    }
+    Acopy = sa.ptr;
+  }
   double* work = Acopy + (size_t)kNoAllocMaxN * kNoAllocMaxN;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   AS_CUDA_TRY(cudaMemcpyAsync(Acopy, A, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s));

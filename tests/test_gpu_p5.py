@@ -31,11 +31,15 @@ def _sites(m, n, d, seed, r=6):
             for j in range(m)]
 
 
-@pytest.mark.parametrize("m,n,d,ell,b,seed", [(4, 120, 32, 4, 10, 1), (3, 200, 64, 8, 25, 2), (5, 90, 48, 6, 9, 3)])
-def test_p5_parity(m, n, d, ell, b, seed):
+@pytest.mark.parametrize("m,n,d,ell,b,seed,prec", [(4, 120, 32, 4, 10, 1, 0), (3, 200, 64, 8, 25, 2, 0),
+                                                  (5, 90, 48, 6, 9, 3, 0), (2, 320, 256, 128, 64, 4, 3)])
+def test_p5_parity(m, n, d, ell, b, seed, prec):
+    """prec 3 (split-BF16 x6) with 2l = 256: the sites' batched iterations run on
+    tcgen05 once a block's buffer passes 128 rows, and their Gram rows and FD
+    rebuilds on the tcgen05 GEMM."""
     p = _gpu()
     rows = _sites(m, n, d, seed)
-    g = p.P5(d, ell, m, seed=seed, trace=True)
+    g = p.P5(d, ell, m, seed=seed, trace=True, prec=prec)
     for t0 in range(0, n, b):
         g.round([x[t0:t0 + b] for x in rows])
     rep = [p.binding.replay_from_trace(g.site(j).trace()) for j in range(m)]

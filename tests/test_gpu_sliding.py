@@ -44,15 +44,19 @@ def test_all_raw_window_is_exact():
         assert np.abs(B - W.T @ W).max() <= 1e-6 * np.sum(W * W)
 
 
-@pytest.mark.parametrize("d,ell,N,blk,seed", [(32, 8, 120, 37, 1), (48, 6, 200, 50, 2)])
-def test_sliding_parity(d, ell, N, blk, seed):
+@pytest.mark.parametrize("d,ell,N,blk,seed,prec", [(32, 8, 120, 37, 1, 0), (48, 6, 200, 50, 2, 0),
+                                                  (256, 128, 400, 97, 3, 3)])
+def test_sliding_parity(d, ell, N, blk, seed, prec):
+    """prec 3 (split-BF16 x6) with 2l = 256: each level's batched iterations run
+    on tcgen05 once its buffer passes 128 rows, and its Gram rows and FD
+    rebuilds on the tcgen05 GEMM."""
     p = _gpu()
     A1 = low_rank_noisy(300, d, 6, spectrum("geometric", 6), noise=0.05, seed=seed, stream=1)
     A2 = low_rank_noisy(300, d, 6, spectrum("geometric", 6), noise=0.05, seed=seed + 10, stream=2)
     A = np.vstack([A1, 2.0 * A2]).astype(np.float32)
     A64 = A.astype(np.float64)
     R = float(np.max(np.sum(A64 * A64, axis=1)))
-    w = p.SlidingWindow(d, ell, N, R, seed=seed, trace=True)
+    w = p.SlidingWindow(d, ell, N, R, seed=seed, trace=True, prec=prec)
     got = {}
     for t0 in range(0, len(A), blk):
         w.update(A[t0:t0 + blk])

@@ -1,8 +1,7 @@
 """as_symeig_noalloc: the eigensolver entry point that allocates nothing.
 
-It serves callers that cannot allocate device memory (code running under a
-CUDA stream capture, allocator callbacks, serving loops that forbid
-allocation after start-up).  Its output must equal that of as_symeig, which
+It serves callers that cannot allocate device memory (allocator callbacks,
+real-time serving loops that forbid allocation after start-up).  Its output must equal that of as_symeig, which
 allocates its own buffers, on consecutive calls that share the library's
 fixed scratch array.  This file is collected last on purpose.
 """
@@ -37,7 +36,9 @@ def _noalloc(p, torch, A, nev):
 def test_matches_allocating_entry_point_on_consecutive_calls():
     p, torch = _setup()
     rng = np.random.default_rng(3)
-    for n, nev in [(100, 40), (64, 64)]:        # two calls in a row share the scratch array
+    # calls in a row share the scratch array; (128, 128) is the largest order,
+    # where the copy of A and the solver's work fill the array exactly
+    for n, nev in [(100, 40), (64, 64), (128, 128)]:
         B = rng.standard_normal((n, n + 5))
         A = B @ B.T
         lam0, V0 = p.binding.symeig(A, nev)
