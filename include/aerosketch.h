@@ -18,7 +18,8 @@
  * return data to the host synchronise that stream.
  *
  * Error behaviour: invalid arguments return AS_EINVAL without side effects;
- * allocation failures return AS_ENOMEM and leave the sketch unchanged;
+ * allocation failures return AS_ENOMEM (sketch_update keeps the rows before
+ * the one whose step failed; every other call leaves the sketch unchanged);
  * conditions detected on the device (non-finite input, numerical breakdown,
  * a bounded device wait that ran out) are recorded in a sticky status that the
  * next synchronising call returns.
@@ -88,6 +89,7 @@ typedef enum {
 /* Flags. */
 #define AS_TRACE_DECISIONS 0x1u /* record every gate / doubling decision (sketch_trace) */
 #define AS_PROFILE 0x2u         /* time each kernel class with CUDA events (sketch_profile) */
+#define AS_QUERY_DENSE 0x4u     /* sketch_query always takes the dense d x d route (see sketch_query) */
 
 typedef struct {
   int32_t d;          /* row dimension, >= 2 */
@@ -186,7 +188,13 @@ as_status sketch_update(as_sketch* h, const float* rows, int64_t n, int64_t ld);
  * t = -1 or t = T (rows fed so far) is the current time: B = C_T^T C_T plus
  * every snapshot term.  0 <= t < T is a historical time: the residual C_t is
  * not stored, and B is the sum of the snapshot terms taken at rows <= t (the
- * B_t of the ATTP error analysis).  Other t: AS_EINVAL.  Synchronises. */
+ * B_t of the ATTP error analysis).  Other t: AS_EINVAL.  Synchronises.
+ * Route: B = F^T H F with F the r_F stacked factor rows [C; Z_j^T; Y_j] and a
+ * small block-diagonal H.  When r_F <= 3d/4 (and the sketch holds no merged
+ * terms) the eigenpairs come from two r_F x r_F eigenproblems (the Gram of F
+ * and the core matrix on its row space); otherwise, or with AS_QUERY_DENSE,
+ * from the d x d matrix B.  Both routes give the same B_hat up to rounding and
+ * the signs of its rows. */
 as_status sketch_query(as_sketch* h, int64_t t, float* out, int64_t ldo, int32_t* rows_out);
 
 /* The matrix B of Algorithm 5 (before its eigendecomposition) for the time t of sketch_query
@@ -467,6 +475,16 @@ as_status as_symeig_noalloc(int32_t n, const double* A, int32_t nev, double* eva
 
 /* Free every resource of the sketch.  NULL is a no-op. */
 as_status sketch_destroy(as_sketch* h);
+
+/* Test hook for the allocation-failure paths (a library service; the paper
+ * has no counterpart): after `after` >= 0 more successful device allocations
+ * made by sketches of this library (any thread), the next one fails as if the
+ * device were out of memory, and the hook turns itself off; after = -1 turns
+ * it off at once.  AS_EINVAL for after < -1.  A failing sketch_create frees
+ * what it allocated; a failing query, merge or sketch_reserve leaves the
+ * sketch as it was; a failing sketch_update keeps the rows before the one
+ * whose step needed the allocation. */
+as_status as_inject_alloc_failure(int32_t after);
 
 /* Static string naming a status. */
 const char* as_status_str(as_status s);

@@ -15,10 +15,12 @@ AS_PERSISTENT, AS_FIXED_THETA, AS_SLIDING, AS_SITE, AS_COORDINATOR = range(5)
 AS_FP32_PLAIN, AS_BF16, AS_BF16X3, AS_BF16X6 = 0, 1, 2, 3
 AS_TRACE_DECISIONS = 0x1
 AS_PROFILE = 0x2
+AS_QUERY_DENSE = 0x4
 
 EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram", "sketch_get_buffer", "sketch_get_gram",
             "sketch_merge", "sketch_stats", "sketch_trace", "sketch_profile", "sketch_profile_reset",
             "sketch_destroy", "as_symeig", "as_symeig_noalloc", "as_tc_gemm", "as_status_str", "as_last_error",
+            "as_inject_alloc_failure",
             "sketch_set_theta", "sketch_send_snapshots", "as_p5_create", "as_p5_round", "as_p5_query",
             "as_p5_query_gram", "as_p5_stats", "as_p5_site", "as_p5_coordinator", "as_p5_destroy",
             "as_sw_create", "as_sw_update", "as_sw_query", "as_sw_query_gram", "as_sw_stats", "as_sw_level",
@@ -117,6 +119,7 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.sketch_destroy.argtypes = [P]
     L.as_symeig.argtypes = [I32, P, I32, P, P]
     L.as_symeig_noalloc.argtypes = [I32, P, I32, P, P, P]
+    L.as_inject_alloc_failure.argtypes = [I32]
     L.as_tc_gemm.argtypes = [I32, I32, I32, P, P, I32, I32, P]
     L.sketch_set_theta.argtypes = [P, ct.c_double]
     L.sketch_send_snapshots.argtypes = [P, P, ct.POINTER(I32)]
@@ -183,9 +186,10 @@ class Sketch:
     def __init__(self, d: int, ell: int = 0, eps: float = 0.0, *, mode: int = AS_PERSISTENT,
                  prec: int = AS_FP32_PLAIN, theta: float = 0.0, eps_si: float = 0.0, k_pi: int = 0,
                  q_si: int = 0, seed: int = 0, stream_id: int = 0, trace: bool = False, profile: bool = False,
-                 delta: float = 0.0, stream=None):
+                 delta: float = 0.0, stream=None, dense_query: bool = False):
         L = lib()
-        flags = (AS_TRACE_DECISIONS if trace else 0) | (AS_PROFILE if profile else 0)
+        flags = ((AS_TRACE_DECISIONS if trace else 0) | (AS_PROFILE if profile else 0)
+                 | (AS_QUERY_DENSE if dense_query else 0))
         cfg = AsConfig(d=d, ell=ell, eps=eps, mode=mode, prec=prec, theta=theta, eps_si=eps_si, k_pi=k_pi,
                        q_si=q_si, seed=seed, stream_id=stream_id, flags=flags, delta=delta)
         h = ct.c_void_p()

@@ -32,10 +32,14 @@ struct Snap {
   int64_t s, t;
 };
 
+// as_inject_alloc_failure: allocations left before the one that fails (-1: off).
+std::atomic<int64_t> g_fail_after{-1};
+
 template <typename T>
 as_status dalloc(T** p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 1;
+  if (g_fail_after.load(std::memory_order_relaxed) >= 0 && g_fail_after.fetch_sub(1) == 0) return AS_ENOMEM;
   cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
   if (e != cudaSuccess) { cudaGetLastError(); *p = nullptr; return AS_ENOMEM; }
   return AS_OK;
@@ -788,20 +792,28 @@ as_status ensure_bx(as_sketch* h) {
 // B += Z Y + (Z Y)^T - Z (Y Z) Z^T for every snapshot of `src` taken at a
 // row <= tmax (Algorithm 5), in time order, on stream st; the scratch
 // of `scr` (xi x xi and d x xi) is grown as needed.
+// The scratch of the snapshot-term products of scr, for snapshots of src.
+as_status ensure_sx(const as_sketch* src, as_sketch* scr) {
+  int ximax = 1;
+  for (const Snap& sn : src->snaps) ximax = std::max(ximax, sn.xi);
+  if (ximax <= scr->sx_cap) return AS_OK;
+  if (scr->sx_yz) cudaFree(scr->sx_yz);
+  if (scr->sx_t) cudaFree(scr->sx_t);
+  scr->sx_yz = scr->sx_t = nullptr;
+  scr->sx_cap = 0;
+  as_status st2 = dalloc(&scr->sx_yz, (size_t)ximax * ximax);
+  if (st2 == AS_OK) st2 = dalloc(&scr->sx_t, (size_t)scr->d * ximax);
+  if (st2 != AS_OK) return st2;
+  scr->sx_cap = ximax;
+  return AS_OK;
+}
+
 as_status add_snapshot_terms(const as_sketch* src, int64_t tmax, double* B, as_sketch* scr, cudaStream_t st,
                              int64_t tmin_excl = INT64_MIN) {
   const int d = src->d;
-  int ximax = 1;
-  for (const Snap& sn : src->snaps) ximax = std::max(ximax, sn.xi);
-  if (ximax > scr->sx_cap) {
-    if (scr->sx_yz) cudaFree(scr->sx_yz);
-    if (scr->sx_t) cudaFree(scr->sx_t);
-    scr->sx_yz = scr->sx_t = nullptr;
-    scr->sx_cap = 0;
-    as_status st2 = dalloc(&scr->sx_yz, (size_t)ximax * ximax);
-    if (st2 == AS_OK) st2 = dalloc(&scr->sx_t, (size_t)scr->d * ximax);
+  {
+    as_status st2 = ensure_sx(src, scr);
     if (st2 != AS_OK) return st2;
-    scr->sx_cap = ximax;
   }
   double* YZ = scr->sx_yz;
   double* T = scr->sx_t;
@@ -868,6 +880,134 @@ as_status eig_shrink_to(as_sketch* h, double* B, float* out, int64_t ldo) {
     if (ds != AS_OK) st = ds;
   }
   cudaFree(lam); cudaFree(V); cudaFree(w); cudaFree(o);
+  return st;
+}
+
+// The low-rank route of Algorithm 5 (lowrank.cu explains the algebra): B_hat
+// of time t to the device buffer o (l x d, row-major).  *used = false (and
+// nothing written) when the route does not apply: merged terms present, the
+// stacked factor rows r_F above 3d/4, or AS_QUERY_DENSE.
+as_status query_lowrank(as_sketch* h, int64_t t, float* o, bool* used) {
+  *used = false;
+  const int d = h->d, ell = h->ell;
+  if (h->cfg.flags & AS_QUERY_DENSE) return AS_OK;
+  if (t == h->T && h->Bx) return AS_OK;
+  const int rc = (t == h->T) ? h->r : 0;
+  int64_t rf64 = rc;
+  for (const Snap& sn : h->snaps) {
+    if (sn.t > t) break;
+    rf64 += 2 * (int64_t)sn.xi;
+  }
+  if (rf64 < 1 || 4 * rf64 > 3 * (int64_t)d) return AS_OK;
+  const int rF = (int)rf64;
+  float* F = nullptr;
+  double *W = nullptr, *Ws = nullptr, *Hs = nullptr, *lw = nullptr, *U = nullptr, *ew = nullptr, *T = nullptr;
+  double *K = nullptr, *mu = nullptr, *Uk = nullptr, *P = nullptr, *V = nullptr, *lam = nullptr;
+  int4* kind = nullptr;
+  const bool big = rF > 256;
+  as_status st = dalloc(&F, (size_t)rF * d);
+  if (st == AS_OK) st = dalloc(&W, (size_t)rF * rF);
+  if (st == AS_OK) st = dalloc(&Ws, (size_t)rF * rF);
+  if (st == AS_OK) st = dalloc(&Hs, (size_t)rF * rF);
+  if (st == AS_OK) st = dalloc(&lw, (size_t)rF);
+  if (st == AS_OK) st = dalloc(&U, (size_t)rF * rF);
+  if (st == AS_OK) st = dalloc(&ew, big ? eig_large_work_doubles(rF, rF) : eig_work_doubles(rF, rF));
+  if (st == AS_OK) st = dalloc(&T, (size_t)rF * rF);
+  if (st == AS_OK) st = dalloc(&kind, (size_t)rF);
+  std::vector<int4> hk((size_t)rF);
+  // F = [C; Z_1^T; Y_1; ...] (FP32, ld d) and the row kinds
+  int row = 0;
+  if (st == AS_OK && rc > 0) {
+    cudaError_t e = cudaMemcpy2DAsync(F, (size_t)d * sizeof(float), h->C, (size_t)h->ldc * sizeof(float),
+                                      (size_t)d * sizeof(float), (size_t)rc, cudaMemcpyDeviceToDevice, h->s);
+    if (e != cudaSuccess) st = as_from_cuda(e);
+    for (; row < rc; ++row) hk[(size_t)row] = make_int4(0, 0, 0, 0);
+  }
+  for (const Snap& sn : h->snaps) {
+    if (st != AS_OK || sn.t > t) break;
+    const float* Z = h->arena + sn.off;
+    const float* Y = Z + (size_t)d * sn.xi;
+    st = launch_transpose_f32(h->s, Z, d, sn.xi, F + (size_t)row * d, d);
+    if (st != AS_OK) break;
+    cudaError_t e = cudaMemcpyAsync(F + (size_t)(row + sn.xi) * d, Y, (size_t)sn.xi * d * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, h->s);
+    if (e != cudaSuccess) { st = as_from_cuda(e); break; }
+    for (int a = 0; a < sn.xi; ++a) {
+      hk[(size_t)(row + a)] = make_int4(1, row, sn.xi, 0);
+      hk[(size_t)(row + sn.xi + a)] = make_int4(2, row, sn.xi, 0);
+    }
+    row += 2 * sn.xi;
+  }
+  if (st == AS_OK) {
+    cudaError_t e = cudaMemcpyAsync(kind, hk.data(), (size_t)rF * sizeof(int4), cudaMemcpyHostToDevice, h->s);
+    if (e != cudaSuccess) st = as_from_cuda(e);
+  }
+  // W = F F^T, scaled; H' from it
+  if (st == AS_OK) st = gemm_strided<float, float, double>(h->s, rF, rF, d, F, d, 1, F, 1, d, W, rF, 1, 1.0, 0.0);
+  if (st == AS_OK) st = launch_lr_scale(h->s, W, rF, kind, Ws, Hs);
+  // W' = U L U^T (all rF pairs), then the numerical rank r'
+  if (st == AS_OK)
+    st = big ? launch_eig_large(h->s, rF, Ws, rF, rF, lw, U, rF, ew, nullptr, h->dstatus)
+             : launch_eig(h->s, rF, Ws, rF, rF, lw, U, rF, ew);
+  std::vector<double> hl((size_t)rF);
+  if (st == AS_OK) {
+    cudaError_t e = cudaMemcpyAsync(hl.data(), lw, (size_t)rF * sizeof(double), cudaMemcpyDeviceToHost, h->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+    if (e != cudaSuccess) st = as_from_cuda(e);
+  }
+  if (st == AS_OK) st = sync_status(h);
+  int rr = 0;
+  if (st == AS_OK && hl[0] > 0.0) {
+    const double cut = 1e-11 * hl[0];
+    while (rr < rF && hl[(size_t)rr] > cut) ++rr;
+  }
+  const int lp = std::min(ell, rr);
+  if (st == AS_OK) st = dalloc(&V, (size_t)d * ell);
+  if (st == AS_OK) st = dalloc(&lam, (size_t)ell);
+  if (st == AS_OK) {
+    cudaError_t e = cudaMemsetAsync(V, 0, (size_t)d * ell * sizeof(double), h->s);
+    if (e != cudaSuccess) st = as_from_cuda(e);
+  }
+  if (st == AS_OK && rr > 0) {
+    const bool bigk = rr > 256;
+    double* ek = nullptr;
+    st = dalloc(&K, (size_t)rr * rr);
+    if (st == AS_OK) st = dalloc(&mu, (size_t)lp);
+    if (st == AS_OK) st = dalloc(&Uk, (size_t)rr * lp);
+    if (st == AS_OK) st = dalloc(&P, (size_t)rF * lp);
+    if (st == AS_OK) st = dalloc(&ek, bigk ? eig_large_work_doubles(rr, lp) : eig_work_doubles(rr, lp));
+    // T = H' U_r (rF x r'), K0 = U_r^T T, K = L^1/2 sym(K0) L^1/2
+    if (st == AS_OK)
+      st = gemm_strided<double, double, double>(h->s, rF, rr, rF, Hs, rF, 1, U, rF, 1, T, rr, 1, 1.0, 0.0);
+    if (st == AS_OK)
+      st = gemm_strided<double, double, double>(h->s, rr, rr, rF, U, 1, rF, T, rr, 1, Ws, rr, 1, 1.0, 0.0);
+    if (st == AS_OK) st = launch_lr_core(h->s, Ws, rr, lw, rr, K);
+    if (st == AS_OK)
+      st = bigk ? launch_eig_large(h->s, rr, K, rr, lp, mu, Uk, lp, ek, nullptr, h->dstatus)
+                : launch_eig(h->s, rr, K, rr, lp, mu, Uk, lp, ek);
+    // E = D U_r L_r^-1/2 U_k, V = F^T E
+    if (st == AS_OK) st = launch_lr_colscale(h->s, U, rF, rF, lw, rr);
+    if (st == AS_OK)
+      st = gemm_strided<double, double, double>(h->s, rF, lp, rr, U, rF, 1, Uk, lp, 1, P, lp, 1, 1.0, 0.0);
+    if (st == AS_OK) st = launch_lr_rowscale(h->s, W, rF, P, lp);
+    if (st == AS_OK)
+      st = gemm_strided<float, double, double>(h->s, d, lp, rF, F, 1, d, P, lp, 1, V, ell, 1, 1.0, 0.0);
+    if (st == AS_OK) st = launch_lr_lambda(h->s, mu, lp, ell, lam);
+    if (ek) cudaFree(ek);
+  } else if (st == AS_OK) {
+    cudaError_t e = cudaMemsetAsync(lam, 0, (size_t)ell * sizeof(double), h->s);
+    if (e != cudaSuccess) st = as_from_cuda(e);
+  }
+  if (st == AS_OK) st = launch_shrink_rows(h->s, d, ell, lam, V, ell, o, d);
+  if (st == AS_OK) {
+    cudaError_t e = cudaStreamSynchronize(h->s);
+    if (e != cudaSuccess) st = as_from_cuda(e);
+  }
+  if (st == AS_OK) st = sync_status(h);
+  void* ptrs[] = {F, W, Ws, Hs, lw, U, ew, T, K, mu, Uk, P, V, lam, kind};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (st == AS_OK) *used = true;
   return st;
 }
 
@@ -1356,6 +1496,12 @@ const char* as_last_error(void) {
   return g_last_error;
 }
 
+as_status as_inject_alloc_failure(int32_t after) {
+  if (after < -1) return AS_EINVAL;
+  g_fail_after.store(after);
+  return AS_OK;
+}
+
 const char* as_status_str(as_status s) {
   switch (s) {
     case AS_OK: return "AS_OK";
@@ -1513,17 +1659,21 @@ as_status sketch_query(as_sketch* h, int64_t t, float* out, int64_t ldo, int32_t
   const int d = h->d, ell = h->ell;
   double *B = nullptr, *lam = nullptr, *V = nullptr, *w = nullptr;
   float* o = nullptr;
-  as_status st = dalloc(&B, (size_t)d * d);
-  if (st == AS_OK) st = dalloc(&lam, (size_t)d);
-  if (st == AS_OK) st = dalloc(&V, (size_t)d * ell);
-  const bool big_q = d > 256;
-  if (st == AS_OK) st = dalloc(&w, big_q ? eig_large_work_doubles(d, ell) : eig_work_doubles(d, ell));
-  if (st == AS_OK) st = dalloc(&o, (size_t)ell * d);
-  if (st == AS_OK) st = build_query_gram(h, t, B);
-  if (st == AS_OK)   // Algorithm 5: eigendecomposition of B, then the shrink by lambda_l
-    st = big_q ? launch_eig_large(h->s, d, B, d, ell, lam, V, ell, w, nullptr, h->dstatus)
-               : launch_eig(h->s, d, B, d, ell, lam, V, ell, w);
-  if (st == AS_OK) st = launch_shrink_rows(h->s, d, ell, lam, V, ell, o, d);
+  as_status st = dalloc(&o, (size_t)ell * d);
+  bool low = false;
+  if (st == AS_OK) st = query_lowrank(h, t, o, &low);
+  if (st == AS_OK && !low) {   // the dense route: B (d x d), its eigendecomposition, the shrink by lambda_l
+    const bool big_q = d > 256;
+    st = dalloc(&B, (size_t)d * d);
+    if (st == AS_OK) st = dalloc(&lam, (size_t)d);
+    if (st == AS_OK) st = dalloc(&V, (size_t)d * ell);
+    if (st == AS_OK) st = dalloc(&w, big_q ? eig_large_work_doubles(d, ell) : eig_work_doubles(d, ell));
+    if (st == AS_OK) st = build_query_gram(h, t, B);
+    if (st == AS_OK)
+      st = big_q ? launch_eig_large(h->s, d, B, d, ell, lam, V, ell, w, nullptr, h->dstatus)
+                 : launch_eig(h->s, d, B, d, ell, lam, V, ell, w);
+    if (st == AS_OK) st = launch_shrink_rows(h->s, d, ell, lam, V, ell, o, d);
+  }
   if (st == AS_OK) {
     cudaError_t e = cudaMemcpy2DAsync(out, (size_t)ldo * sizeof(float), o, (size_t)d * sizeof(float),
                                       (size_t)d * sizeof(float), (size_t)ell, cudaMemcpyDefault, h->s);
@@ -1564,7 +1714,9 @@ as_status sketch_merge(as_sketch* dst, const as_sketch* src_c) {
   std::unique_lock<std::mutex> l2(src->mu, std::try_to_lock);
   if (!l2.owns_lock()) return AS_EBUSY;
   AS_CUDA_TRY(cudaStreamSynchronize(src->s));
+  // everything the merge allocates comes first, so a failure leaves dst as it was
   as_status st = ensure_bx(dst);
+  if (st == AS_OK) st = ensure_sx(src, dst);
   if (st != AS_OK) return st;
   const int d = dst->d;
   // dst.Bx += src.C^T C + src's snapshot terms + src.Bx: src's whole query Gram

@@ -245,6 +245,18 @@ as_status launch_umma_gemm(cudaStream_t s, const UmmaOperand& A, const UmmaOpera
 as_status launch_split_bf16(cudaStream_t s, const float* src, long long lds, int rows, int cols, __nv_bfloat16* hi,
                             __nv_bfloat16* lo, long long ldd, bool transpose, __nv_bfloat16* lo2 = nullptr);
 
+// Low-rank route of the query (lowrank.cu): out = Z^T (Z: d x xi row-major);
+// W' = D W D and H' = D^-1 H D^-1 from W = F F^T (kind[i] = {0: a row of C,
+// 1: a row of Z_j^T, 2: a row of Y_j; first row of Z_j^T; xi_j}); the core
+// K = L^1/2 sym(T) L^1/2 from T = U_r^T H' U_r; column scaling by lam^-1/2,
+// row scaling by D; the l largest eigenvalues of B from those of K.
+as_status launch_transpose_f32(cudaStream_t s, const float* Z, int d, int xi, float* out, long long ldo);
+as_status launch_lr_scale(cudaStream_t s, const double* W, int n, const int4* kind, double* Ws, double* Hs);
+as_status launch_lr_core(cudaStream_t s, const double* T, int ldt, const double* lam, int r, double* K);
+as_status launch_lr_colscale(cudaStream_t s, double* U, int n, int ldu, const double* lam, int r);
+as_status launch_lr_rowscale(cudaStream_t s, const double* W, int n, double* P, int m);
+as_status launch_lr_lambda(cudaStream_t s, const double* mu, int lp, int ell, double* lam_out);
+
 // Library-internal access to a sketch for the runtimes built on sketches
 // (engine.cu): stream, rows fed, the snapshot queue's times (the sketch's own
 // row indices), the windowed query Gram, raw-row Grams, dropping the oldest

@@ -1,8 +1,7 @@
 // as_symeig_noalloc: the FP64 symmetric eigensolver with no allocation.
 //
-// Some callers cannot allocate device memory: code running inside a CUDA
-// stream capture (cudaMalloc is not capturable), allocators' own callbacks,
-// and real-time serving paths that forbid allocation after start-up.  This
+// Some callers cannot allocate device memory: allocators' own callbacks, and
+// real-time serving paths that forbid allocation after start-up.  This
 // entry point takes device pointers for its input and outputs and keeps its
 // scratch space (a copy of A, since the solver overwrites its input, and the
 // solver's work vectors) in one file-scope device array.
