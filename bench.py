@@ -168,6 +168,45 @@ def reference_arm(args) -> None:
 
 PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3}
 
+_ORACLE_CHILD = r"""
+import sys, time, numpy as np
+sys.path.insert(0, sys.argv[1])
+from oracle.aerosketch import AeroSketch
+z = np.load(sys.argv[2])
+o = AeroSketch(int(z["d"]), int(z["ell"]), stream_id=int(z["sid"]))
+o.load_state(z["C0"].astype(np.float64), int(z["r0"]), float(z["fro2"]), int(z["rows"]))
+blk = z["blk"].astype(np.float64)
+t0 = time.perf_counter()
+o.run(blk)
+print(len(blk) / (time.perf_counter() - t0))
+"""
+
+
+def _oracle_rate(C0, r0, fro2, rows, blk, d, ell, sid, threads=None) -> float:
+    """rows/s of the oracle (plain FP64 NumPy) on `blk` from the GPU's exact
+    state; threads = 1 runs it in a child process with BLAS on one thread."""
+    import numpy as np
+    if threads is None:
+        from oracle.aerosketch import AeroSketch
+        o = AeroSketch(d, ell, stream_id=sid)
+        o.load_state(C0.astype(np.float64), r0, fro2, rows)
+        b64 = blk.astype(np.float64)
+        t0 = time.perf_counter()
+        o.run(b64)
+        return len(b64) / (time.perf_counter() - t0)
+    import tempfile
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "state.npz")
+        np.savez(path, C0=C0, r0=r0, fro2=fro2, rows=rows, blk=blk, d=d, ell=ell, sid=sid)
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[k] = str(threads)
+        out = subprocess.run([sys.executable, "-c", _ORACLE_CHILD, ROOT, path], env=env, capture_output=True,
+                             text=True, timeout=600)
+        if out.returncode != 0:
+            raise RuntimeError(out.stderr[-2000:])
+        return float(out.stdout.strip().splitlines()[-1])
+
 
 def _run_form(p, torch, args, A_dev, d, ell, B, K, W, rank, local, ws, prec, want_state=False):
     """Warm up W steps, time K steps (L2 flushed between steps); returns timings,
@@ -305,17 +344,18 @@ def our_arm(args) -> None:
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            from oracle.aerosketch import AeroSketch
             C0, r0, st0 = hr["state"]
-            o = AeroSketch(d, ell, stream_id=rank)
-            o.load_state(C0.astype(np.float64), r0, st0["fro2"], st0["rows"])
             S = args.cpu_rows
-            blk = A[W * B: W * B + S].astype(np.float64)
-            t0 = time.perf_counter()
-            o.run(blk)
-            dt = time.perf_counter() - t0
-            cpu = {"value": S / dt, "unit": "rows/s", "cores": os.cpu_count(), "kind": "oracle",
+            blk = A[W * B: W * B + S]
+            rate = _oracle_rate(C0, r0, st0["fro2"], st0["rows"], blk, d, ell, rank, threads=None)
+            cpu = {"value": rate, "unit": "rows/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"first {S} rows of the timed region, from the GPU's exact state at its start"}
+            if args.cpu_rows_1core > 0:
+                S1 = min(S, args.cpu_rows_1core)
+                rate1 = _oracle_rate(C0, r0, st0["fro2"], st0["rows"], blk[:S1], d, ell, rank, threads=1)
+                cpu["single_core"] = {"value": rate1, "unit": "rows/s", "cores": 1,
+                                      "sample": f"first {S1} rows of the same sample, BLAS on one thread "
+                                                "(the paper's single-core setting)"}
         forms_out = {}
         errs = {}
         if not args.no_err:
@@ -599,6 +639,8 @@ def main() -> None:
     ap.add_argument("--workload", default="tight_d4096_l1024", choices=sorted(WORKLOADS) + sorted(EXTRA))
     ap.add_argument("--rows-per-step", type=int, default=1024)
     ap.add_argument("--cpu-rows", type=int, default=48)
+    ap.add_argument("--cpu-rows-1core", type=int, default=8,
+                    help="rows of the CPU-baseline sample also timed with BLAS on one thread (0: skip)")
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-err", action="store_true")

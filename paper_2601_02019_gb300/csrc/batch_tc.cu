@@ -46,6 +46,8 @@ constexpr int kTcStages = 2;   // ring stages; a stage holds one K tile of every
 constexpr int kTcSlots = 6;     // partial sums per pair
 constexpr int kTcMaxRpc = 32;   // rows per CTA in the reduction phase
 constexpr int kTcMaxCols = 192; // batch columns (2 P)
+constexpr int kTcMaxSplits = 16; // K ranges per row block (nks, checked at launch)
+constexpr int kRedElems = 4;     // elements per thread whose loads are in flight together in the reduction
 
 struct TcArgs {
   float* Y;            // FP32 columns, two buffers of ybuf floats, ld ldy
@@ -70,6 +72,16 @@ struct TcArgs {
   double* sig2;
   double* ritz;
 };
+
+// 16 consecutive FP32 columns of one TMEM accumulator, this warp's 32 lanes
+// (rows); the caller waits with tcgen05.wait::ld before reading r.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
 
 __device__ __forceinline__ int tc_col_rows(const TcArgs& a, int c) {
   const int pcol = 2 * a.npi;
@@ -351,29 +363,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int row = rb * UM + warp * 32 + lane;
       float* o = part + (size_t)ks * a.pplane + (size_t)row * a.nc;
-      for (int c0 = 0; c0 < a.nc; c0 += 16) {
-        float v[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = 0.f;
+      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+      // 32 columns of both accumulators per wait (nc is a multiple of 16)
+      for (int c0 = 0; c0 < a.nc; c0 += 32) {
+        const bool two = c0 + 16 < a.nc;   // warp-uniform
+        uint32_t r[4][16];
         if (have) {
-#pragma unroll
-          for (int acc = 0; acc < 2; ++acc) {
-            uint32_t r[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + acc * a.nc);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] += __uint_as_float(r[j]);
+          tmem_ld16(trow + (uint32_t)c0, r[0]);
+          tmem_ld16(trow + (uint32_t)(c0 + a.nc), r[1]);
+          if (two) {
+            tmem_ld16(trow + (uint32_t)(c0 + 16), r[2]);
+            tmem_ld16(trow + (uint32_t)(c0 + 16 + a.nc), r[3]);
           }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         }
 #pragma unroll
-        for (int j = 0; j < 16; j += 4)
-          __stcg(reinterpret_cast<float4*>(o + c0 + j), make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]));
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !two) break;
+          float v[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            v[j] = have ? __uint_as_float(r[2 * h][j]) + __uint_as_float(r[2 * h + 1][j]) : 0.f;
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            __stcg(reinterpret_cast<float4*>(o + c0 + 16 * h + j), make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]));
+        }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -386,12 +400,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
     const int rw0 = blk * a.rpc, rw1 = min(a.kpad, rw0 + a.rpc);
     const int R = max(0, rw1 - rw0);
     const int c0a = 2 * pa0, nca = 2 * nact;
-    for (int e = tid; e < R * nca; e += kTcThreads) {
-      const int r = e / nca, cl = e - r * nca;
-      const float* pp = part + (size_t)(rw0 + r) * a.nc + c0a + cl;
-      float z = 0.f;
-      for (int k = 0; k < a.nks; ++k) z += __ldcg(pp + (size_t)k * a.pplane);
-      zs[r * nca + cl] = z;
+    {
+      // every load of kRedElems elements (all their K-split planes) is issued
+      // before the sums that use them: one L2 round trip per batch instead of
+      // one per element; the planes are still summed in the order k = 0, 1, ...
+      // (the zeros past nks leave each sum unchanged)
+      const int total = R * nca;
+      for (int e0 = tid; e0 < total; e0 += kTcThreads * kRedElems) {
+        float buf[kRedElems][kTcMaxSplits];
+#pragma unroll
+        for (int q = 0; q < kRedElems; ++q) {
+          const int e = e0 + q * kTcThreads;
+          const bool on = e < total;
+          const int r = on ? e / nca : 0, cl = on ? e - r * nca : 0;
+          const float* pp = part + (size_t)(rw0 + r) * a.nc + c0a + cl;
+#pragma unroll
+          for (int k = 0; k < kTcMaxSplits; ++k)
+            buf[q][k] = (on && k < a.nks) ? __ldcg(pp + (size_t)k * a.pplane) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < kRedElems; ++q) {
+          const int e = e0 + q * kTcThreads;
+          if (e < total) {
+            float z = 0.f;
+#pragma unroll
+            for (int k = 0; k < kTcMaxSplits; ++k) z += buf[q][k];
+            zs[e] = z;   // e = r * nca + cl
+          }
+        }
+      }
     }
     __syncthreads();
     if (tid < nact) {
@@ -560,7 +597,7 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
   kc = (kc + 63) / 64 * 64;
   const int ncta = nrb * nks;
   const int rpc = (kpad + ncta - 1) / ncta;
-  if (nks > 16 || ncta > td.sms || rpc > kTcMaxRpc) return AS_OK;
+  if (nks > kTcMaxSplits || ncta > td.sms || rpc > kTcMaxRpc) return AS_OK;
   const size_t smem = 1024 + (size_t)kTcStages * 2 * (UM * UK * 2 + (size_t)nc * UK * 2);
   const int v = 0;
   const void* fn = (const void*)batch_tc_kernel<3>;

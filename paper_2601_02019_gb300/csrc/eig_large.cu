@@ -178,10 +178,22 @@ __global__ void bisect_df(int n, int nev, const double* norms, const df64* dd, c
 }
 
 // Inverse iteration for the eigenvalues found by bisect_df, one thread per
-// eigenvector in full warps spread over many SMs: the LU factorisation and
-// the solves are FP64 recurrences, and FP64 issue is scarce on this part, so
-// no lane of a warp should idle.  lam = evals[j] / norms[3] undoes the exact
-// power-of-two unscaling.
+// eigenvector in full warps: the LU factorisation and the solves are FP64
+// recurrences, and FP64 issue is scarce on this part, so no lane of a warp
+// should idle.  lam = evals[j] / norms[3] undoes the exact power-of-two
+// unscaling.
+//
+// The sweeps over the factors are bound by memory latency, not arithmetic:
+// each step's loads do not depend on the recurrence, so they are issued in
+// batches of kInvitBatch steps ahead of the arithmetic that uses them (every
+// value a batch reads was written in an earlier sweep, or earlier in the
+// forward sweep at a lower index).  The LU stores the reciprocal of each
+// pivot (off the recurrence's dependent chain); the normalisation of an
+// iterate is folded into the next forward sweep (the sweep is linear), so an
+// iteration is two sweeps; the first iteration starts from ii_start without
+// reading X, and one final pass scales the last iterate.
+constexpr int kInvitBatch = 8;
+
 __global__ void __launch_bounds__(32) invit_df(int n, int nev, TriWork w, const double* norms, const double* evals,
                                                double* X, int ldx, double* lu) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -191,74 +203,115 @@ __global__ void __launch_bounds__(32) invit_df(int n, int nev, TriWork w, const 
   const double lam = (tnorm == 0.0) ? 0.0 : evals[j] / norms[3];
   const double* d = w.d;
   const double* e = w.e;
-  // inverse iteration (same factorisation as eig.cuh)
-  const double tiny = fmax(eps * tnorm, 1e-300);
-  double* u0 = lu + (size_t)(0 * n) * nev + j;
-  double* u1 = lu + (size_t)(1 * n) * nev + j;
-  double* u2 = lu + (size_t)(2 * n) * nev + j;
-  double* ll = lu + (size_t)(3 * n) * nev + j;
-  double* pv = lu + (size_t)(4 * n) * nev + j;
-  double cd = d[0] - lam, cs = e[0];
-  for (int i = 0; i + 1 < n; ++i) {
-    const double b = e[i];
-    const double nd = d[i + 1] - lam, ns = (i + 2 < n) ? e[i + 1] : 0.0;
-    if (fabs(cd) >= fabs(b)) {
-      if (cd == 0.0) cd = tiny;
-      const double li = b / cd;
-      u0[(size_t)i * nev] = cd; u1[(size_t)i * nev] = cs; u2[(size_t)i * nev] = 0.0;
-      ll[(size_t)i * nev] = li; pv[(size_t)i * nev] = 0.0;
-      cd = nd - li * cs; cs = ns;
-    } else {
-      const double li = cd / b;
-      u0[(size_t)i * nev] = b; u1[(size_t)i * nev] = nd; u2[(size_t)i * nev] = ns;
-      ll[(size_t)i * nev] = li; pv[(size_t)i * nev] = 1.0;
-      cd = cs - li * nd; cs = -li * ns;
-    }
-  }
-  if (fabs(cd) < tiny) cd = (cd < 0 ? -tiny : tiny);
-  u0[(size_t)(n - 1) * nev] = cd;
-  // u0 <- 1 / u0 (pivots kept away from zero): the divisions are independent
-  // of each other here, and the solves below then multiply
-#pragma unroll 4
-  for (int i = 0; i < n; ++i) {
-    double p = u0[(size_t)i * nev];
-    if (fabs(p) < tiny) p = (p < 0 ? -tiny : tiny);
-    u0[(size_t)i * nev] = 1.0 / p;
-  }
   if (tnorm == 0.0) {   // zero matrix: any orthonormal basis is an eigenbasis
     for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] = (i == j) ? 1.0 : 0.0;
     return;
   }
-  for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] = ii_start(i, j);
-  // The recurrences carry their running values in registers: every load
-  // below reads a value written in an earlier sweep, off the dependent chain.
+  const double tiny = fmax(eps * tnorm, 1e-300);
+  double* u0 = lu + (size_t)(0 * n) * nev + j;   // 1 / pivot (kept away from zero)
+  double* u1 = lu + (size_t)(1 * n) * nev + j;
+  double* u2 = lu + (size_t)(2 * n) * nev + j;
+  double* ll = lu + (size_t)(3 * n) * nev + j;
+  double* pv = lu + (size_t)(4 * n) * nev + j;
+  // LU of T - lam I with partial pivoting (as eig.cuh)
+  double cd = d[0] - lam, cs = e[0];
+  for (int i = 0; i + 1 < n; ++i) {
+    const double b = e[i];
+    const double nd = d[i + 1] - lam, ns = (i + 2 < n) ? e[i + 1] : 0.0;
+    double piv;
+    if (fabs(cd) >= fabs(b)) {
+      if (cd == 0.0) cd = tiny;
+      const double li = b / cd;
+      piv = cd;
+      u1[(size_t)i * nev] = cs; u2[(size_t)i * nev] = 0.0;
+      ll[(size_t)i * nev] = li; pv[(size_t)i * nev] = 0.0;
+      cd = nd - li * cs; cs = ns;
+    } else {
+      const double li = cd / b;
+      piv = b;
+      u1[(size_t)i * nev] = nd; u2[(size_t)i * nev] = ns;
+      ll[(size_t)i * nev] = li; pv[(size_t)i * nev] = 1.0;
+      cd = cs - li * nd; cs = -li * ns;
+    }
+    if (fabs(piv) < tiny) piv = (piv < 0 ? -tiny : tiny);
+    u0[(size_t)i * nev] = 1.0 / piv;
+  }
+  if (fabs(cd) < tiny) cd = (cd < 0 ? -tiny : tiny);
+  u0[(size_t)(n - 1) * nev] = 1.0 / cd;
+  double* x = X + j;
+  const size_t sx = (size_t)ldx;
+  double rhs = 1.0;   // scale of the stored iterate (its pending normalisation)
   for (int it = 0; it < 3; ++it) {
-    double cur = X[j];   // forward elimination with the row interchanges
-#pragma unroll 4
-    for (int i = 0; i + 1 < n; ++i) {
-      double yi = cur, yn = X[(size_t)(i + 1) * ldx + j];
-      if (pv[(size_t)i * nev] != 0.0) { const double t = yi; yi = yn; yn = t; }
-      yn -= ll[(size_t)i * nev] * yi;
-      X[(size_t)i * ldx + j] = yi;
-      cur = yn;
+    // forward elimination with the row interchanges: y = L^-1 P (rhs x)
+    double cur = (it == 0) ? ii_start(0, j) : x[0] * rhs;
+    for (int ib = 0; ib + 1 < n; ib += kInvitBatch) {
+      const int nb = min(kInvitBatch, n - 1 - ib);
+      double xr[kInvitBatch], lr[kInvitBatch], pr[kInvitBatch];
+#pragma unroll
+      for (int u = 0; u < kInvitBatch; ++u) {
+        if (u < nb) {
+          const int i = ib + u;
+          xr[u] = (it == 0) ? ii_start(i + 1, j) : x[(size_t)(i + 1) * sx] * rhs;
+          lr[u] = ll[(size_t)i * nev];
+          pr[u] = pv[(size_t)i * nev];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kInvitBatch; ++u) {
+        if (u < nb) {
+          double yi = cur, yn = xr[u];
+          if (pr[u] != 0.0) { const double t = yi; yi = yn; yn = t; }
+          yn -= lr[u] * yi;
+          x[(size_t)(ib + u) * sx] = yi;
+          cur = yn;
+        }
+      }
     }
-    X[(size_t)(n - 1) * ldx + j] = cur;
-    double xn1 = 0.0, xn2 = 0.0, mx = 0.0;   // back substitution (u0 holds 1 / pivot)
-#pragma unroll 4
-    for (int i = n - 1; i >= 0; --i) {
-      const double xi = (X[(size_t)i * ldx + j] - u1[(size_t)i * nev] * xn1 - u2[(size_t)i * nev] * xn2) *
-                        u0[(size_t)i * nev];
-      X[(size_t)i * ldx + j] = xi;
-      xn2 = xn1; xn1 = xi;
-      mx = fmax(mx, fabs(xi));
+    x[(size_t)(n - 1) * sx] = cur;
+    // back substitution (u0 holds 1 / pivot), with the max and the sum of squares
+    double xn1 = 0.0, xn2 = 0.0, mx = 0.0, ss = 0.0;
+    for (int ib = n - 1; ib >= 0; ib -= kInvitBatch) {
+      const int nb = min(kInvitBatch, ib + 1);
+      double xr[kInvitBatch], a0[kInvitBatch], a1[kInvitBatch], a2[kInvitBatch];
+#pragma unroll
+      for (int u = 0; u < kInvitBatch; ++u) {
+        if (u < nb) {
+          const size_t i = (size_t)(ib - u);
+          xr[u] = x[i * sx];
+          a0[u] = u0[i * nev];
+          a1[u] = u1[i * nev];
+          a2[u] = u2[i * nev];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kInvitBatch; ++u) {
+        if (u < nb) {
+          const double xi = (xr[u] - a1[u] * xn1 - a2[u] * xn2) * a0[u];
+          x[(size_t)(ib - u) * sx] = xi;
+          xn2 = xn1; xn1 = xi;
+          mx = fmax(mx, fabs(xi));
+          ss = fma(xi, xi, ss);
+        }
+      }
     }
-    const double rmx = 1.0 / mx;
-    double nrm = 0.0;
-#pragma unroll 4
-    for (int i = 0; i < n; ++i) { const double v = X[(size_t)i * ldx + j] * rmx; nrm += v * v; }
-    const double sc = rmx / sqrt(nrm);
-#pragma unroll 4
-    for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] *= sc;
+    if (ss > 0.0 && ss < 1e300) {
+      rhs = 1.0 / sqrt(ss);
+    } else {   // squares out of range: normalise in two scaled passes
+      const double rmx = (mx > 0.0) ? 1.0 / mx : 0.0;
+      double nrm = 0.0;
+      for (int i = 0; i < n; ++i) { const double v = x[(size_t)i * sx] * rmx; nrm += v * v; }
+      rhs = (nrm > 0.0) ? rmx / sqrt(nrm) : 0.0;
+    }
+  }
+  for (int ib = 0; ib < n; ib += kInvitBatch) {
+    const int nb = min(kInvitBatch, n - ib);
+    double xr[kInvitBatch];
+#pragma unroll
+    for (int u = 0; u < kInvitBatch; ++u)
+      if (u < nb) xr[u] = x[(size_t)(ib + u) * sx];
+#pragma unroll
+    for (int u = 0; u < kInvitBatch; ++u)
+      if (u < nb) x[(size_t)(ib + u) * sx] = xr[u] * rhs;
   }
 }
 
