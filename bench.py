@@ -404,9 +404,17 @@ EXTRA = {
     # C3 reduced to 16 sites so a run takes minutes: d = 512, l = 64, shared
     # rank 50 (sigma_i = 10 * 0.85^i) plus a rank-5 site part (5 * 0.85^i)
     "p5_d512_l64_m16": dict(d=512, ell=64, m=16, rows_per_site=256),
+    # C3 at its stated 512 sites (d = 512, l = 64; the same rows), 64 rows per
+    # site per synchronous round, a bounded number of rounds of the 2*10^4
+    "p5_d512_l64_m512": dict(d=512, ell=64, m=512, rows_per_site=64),
     # C2 with the window reduced to 16384 rows (the timed steps then run with
     # a full window): d = 1024, l = 128, rows as the d = 256 workload
     "sliding_d1024_l128_N16384": dict(d=1024, ell=128, N=16384, rows_per_step=4096),
+    # C2 at its stated window N = 10^5 (d = 1024, l = 128, rows as the d = 256
+    # workload), the basis rotated by a Givens sweep every 250,000 rows: a
+    # segment of the 2*10^6-row stream that fills the window with rows of the
+    # old basis and times the steps right after the rotation at row 250,000
+    "sliding_d1024_l128_N100000_drift": dict(d=1024, ell=128, N=100_000, rows_per_step=4096, drift=250_000),
     # C4: 2000 sessions (d = round8(exp U[ln 256, ln 8192]), l in {32..512}
     # clamped to d/2), batches of round(exp U[0, ln 4096]) rows for uniformly
     # chosen sessions; a saturation phase measures capacity, then Poisson
@@ -426,10 +434,11 @@ def _p5_rows(w, rounds, seed):
     sig = 10.0 * 0.85 ** np.arange(50)
     sig5 = 5.0 * 0.85 ** np.arange(5)
     out = []
+    ch = 4096 if m <= 16 else max(1, rounds * b)   # many sites: draw only the rows used
     for j in range(m):
-        shared = low_rank_noisy(rounds * b, d, 50, sig, noise=0.01, seed=seed, stream=2 * j + 1, V=V)
+        shared = low_rank_noisy(rounds * b, d, 50, sig, noise=0.01, seed=seed, stream=2 * j + 1, V=V, chunk=ch)
         own = low_rank_noisy(rounds * b, d, 5, sig5, noise=0.0, seed=seed, stream=2 * j + 2,
-                             V=basis(d, 5, seed=seed, stream=j + 1))
+                             V=basis(d, 5, seed=seed, stream=j + 1), chunk=ch)
         out.append((shared + own).astype(np.float32))
     return out
 
@@ -596,18 +605,33 @@ def extra_arm(args) -> None:
                "l2": "per-site state far below L2; inputs staged from host each round"}
     else:
         d, ell, N, B = w["d"], w["ell"], w["N"], w["rows_per_step"]
-        A = low_rank_noisy((W + K) * B, d, 20, spectrum("geometric", 20), seed=0)
+        drift = w.get("drift")
+        if drift:
+            # rows [s0, s0 + N) fill the window before the warm-up steps; the timed
+            # steps start at the rotation (row `drift`)
+            from synth import drifting_rows
+            s0 = drift - N - W * B
+            pre = N
+            A = drifting_rows(pre + (W + K) * B, d, 20, spectrum("geometric", 20), period=drift, seed=0, start=s0)
+        else:
+            pre = 0
+            A = low_rank_noisy((W + K) * B, d, 20, spectrum("geometric", 20), seed=0)
         A *= 1.0 / np.sqrt(np.min(np.sum(A.astype(np.float64) ** 2, axis=1)))   # ||a||^2 >= 1 (the model)
         A = A.astype(np.float32)
         R = 2.0 ** np.ceil(np.log2(np.max(np.sum(A.astype(np.float64) ** 2, axis=1))))
         A_dev = torch.from_numpy(A).cuda()
         g = p.SlidingWindow(d, ell, N, R, stream=stream)
         step_rows = B
+        for t0 in range(0, pre, B):
+            g.update(A_dev[t0:min(pre, t0 + B)])
 
         def step(k):
-            g.update(A_dev[k * B:(k + 1) * B])
+            g.update(A_dev[pre + k * B:pre + (k + 1) * B])
         cfg = {"workload": args.workload, "d": d, "ell": ell, "window": N, "rows_per_step": B, "R": R,
                "levels": g.stats()["levels"], "l2": "rows resident in HBM; per-level state re-read each step"}
+        if drift:
+            cfg.update({"drift_every_rows": drift, "stream_rows": f"{s0}..{s0 + pre + (W + K) * B - 1}",
+                        "timed_rows": f"{drift}..{drift + K * B - 1} (the first {K * B} rows after the rotation)"})
     for k in range(W):
         step(k)
     torch.cuda.synchronize()

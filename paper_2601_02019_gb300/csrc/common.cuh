@@ -14,11 +14,15 @@ void as_note_cuda_error(cudaError_t e, const char* file, int line);
 // needs less still fits (setting the attribute per launch would race).
 cudaError_t as_raise_smem_limit(const void* fn, size_t bytes);
 
+// On failure the error is recorded and the thread's last-error state is
+// cleared (cudaGetLastError), so that a later launch check does not report it
+// again.
 #define AS_CUDA_TRY(expr)                                   \
   do {                                                      \
     cudaError_t _e = (expr);                                \
     if (_e != cudaSuccess) {                                \
       as_note_cuda_error(_e, __FILE__, __LINE__);           \
+      (void)cudaGetLastError();                             \
       return as_from_cuda(_e);                              \
     }                                                       \
   } while (0)

@@ -85,8 +85,6 @@ __global__ void cluster_mgs(int n, int nev, const double* norms, const double* e
   }
 }
 
-// Back-transformation: each block owns columns [c0, c0 + kSlab) of X.
-constexpr int kSlab = 4;
 
 
 // ---- double-float (df64) kernels -------------------------------------------
@@ -576,55 +574,120 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
   }
 }
 
-// Back-transformation in df64: each block owns columns [c0, c0 + kSlab) of X
-// (df64 in shared memory) and applies every reflector H_k = I - 2 v_k v_k^T,
-// k = n-3 .. 0, read from row k of the df64 matrix Vd (ld ldv).  X is read and
-// written in FP64.
-__global__ void __launch_bounds__(256) back_transform_df(const df64* Vd, int ldv, int n, int nev, double* X,
-                                                          int ldx) {
-  extern __shared__ df64 xd[];  // n x kSlab
-  __shared__ df64 red[kSlab][8];
-  const int c0 = blockIdx.x * kSlab;
-  const int nc = min(kSlab, nev - c0);
-  for (int e = threadIdx.x; e < n * kSlab; e += blockDim.x) {
-    const int i = e / kSlab, c = e - i * kSlab;
-    xd[e] = (c < nc) ? df_from_double(X[(size_t)i * ldx + c0 + c]) : df64{0.f, 0.f};
+// Back-transformation in df64, blocked (compact WY).  The reflectors
+// H_k = I - 2 v_k v_k^T (k = 0 .. n-3, v_k unit, in row k of the df64 matrix Vd
+// at columns k+1 .. n-1) are taken kBtNb at a time: H_k0 ... H_k1-1 =
+// I - V T V^T with T upper triangular (T_ii = 2 and
+// T[0:i, i] = -2 T[0:i, 0:i] (V[:, 0:i]^T v_i), the forward column recurrence of
+// the compact WY form; bt_tfactor_df builds it per group).  Each block of
+// bt_apply_df owns SW columns of X (df64 in shared memory) and applies the
+// groups from the last to the first: W = V^T X, W <- T W, X <- X - V W: three
+// block-wide steps per group instead of two per reflector.
+constexpr int kBtNb = 16;
+
+__global__ void __launch_bounds__(256) bt_tfactor_df(const df64* Vd, int ldv, int n, int nk, df64* Tout) {
+  const int g = blockIdx.x;
+  const int k0 = g * kBtNb, k1 = min(k0 + kBtNb, nk), nbg = k1 - k0;
+  __shared__ df64 S[kBtNb][kBtNb];
+  __shared__ df64 T[kBtNb][kBtNb];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // S[p][i] = v_{k0+p} . v_{k0+i} (p < i), over rows k0+i+1 .. n-1 where v_{k0+i} lives
+  for (int pi = warp; pi < kBtNb * kBtNb; pi += 8) {
+    const int p = pi / kBtNb, i = pi - p * kBtNb;
+    if (p >= i || i >= nbg) continue;
+    const df64* vp = Vd + (size_t)(k0 + p) * ldv;
+    const df64* vi = Vd + (size_t)(k0 + i) * ldv;
+    df64 a0{0.f, 0.f}, a1{0.f, 0.f};
+    int c = k0 + i + 1 + lane;
+    for (; c + 32 < n; c += 64) {
+      a0 = df_fma(vp[c], vi[c], a0);
+      a1 = df_fma(vp[c + 32], vi[c + 32], a1);
+    }
+    if (c < n) a0 = df_fma(vp[c], vi[c], a0);
+    const df64 acc = df_warp_sum(df_add(a0, a1));
+    if (lane == 0) S[p][i] = acc;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int k = n - 3; k >= 0; --k) {
-    const int m = n - k - 1;
-    const df64* v = Vd + (size_t)k * ldv + (k + 1);
-    df64 s[kSlab];
-#pragma unroll
-    for (int c = 0; c < kSlab; ++c) s[c] = df64{0.f, 0.f};
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const df64 vi = v[i];
-#pragma unroll
-      for (int c = 0; c < kSlab; ++c) s[c] = df_fma(vi, xd[(k + 1 + i) * kSlab + c], s[c]);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kBtNb; ++i)
+      for (int p = 0; p < kBtNb; ++p) T[p][i] = df64{0.f, 0.f};
+    for (int i = 0; i < nbg; ++i) {
+      T[i][i] = df64{2.f, 0.f};
+      for (int p = 0; p < i; ++p) {
+        df64 sacc{0.f, 0.f};
+        for (int q = p; q < i; ++q) sacc = df_fma(T[p][q], S[q][i], sacc);
+        T[p][i] = df64{-2.f * sacc.hi, -2.f * sacc.lo};   // exact scaling by -2
+      }
     }
-#pragma unroll
-    for (int c = 0; c < kSlab; ++c) {
-      const df64 t = df_warp_sum(s[c]);
-      if (lane == 0) red[c][wid] = t;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < kSlab; ++c) {
-      df64 t = red[c][0];
-      for (int q = 1; q < 8; ++q) t = df_add(t, red[c][q]);
-      s[c] = df64{-2.f * t.hi, -2.f * t.lo};   // exact scaling by -2
-    }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const df64 vi = v[i];
-#pragma unroll
-      for (int c = 0; c < kSlab; ++c) xd[(k + 1 + i) * kSlab + c] = df_fma(s[c], vi, xd[(k + 1 + i) * kSlab + c]);
-    }
-    __syncthreads();
   }
-  for (int e = threadIdx.x; e < n * kSlab; e += blockDim.x) {
-    const int i = e / kSlab, c = e - i * kSlab;
-    if (c < nc) X[(size_t)i * ldx + c0 + c] = df_to_double(xd[e]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < kBtNb * kBtNb; e += blockDim.x)
+    Tout[(size_t)g * kBtNb * kBtNb + e] = T[e / kBtNb][e % kBtNb];
+}
+
+template <int SW>
+__global__ void __launch_bounds__(256) bt_apply_df(const df64* Vd, int ldv, int n, int nk, const df64* Tf, int nev,
+                                                    double* X, int ldx) {
+  extern __shared__ df64 xd[];  // n x SW
+  constexpr int kOut = kBtNb * SW;               // outputs of W
+  constexpr int kSplit = 256 / kOut;             // row splits of the W sums
+  __shared__ df64 Ts[kBtNb][kBtNb];
+  __shared__ df64 Wp[kSplit][kBtNb][SW];
+  __shared__ df64 W2[kBtNb][SW];
+  const int c0 = blockIdx.x * SW;
+  const int nc = min(SW, nev - c0);
+  for (int e = threadIdx.x; e < n * SW; e += blockDim.x) {
+    const int i = e / SW, c = e - i * SW;
+    xd[e] = (c < nc) ? df_from_double(X[(size_t)i * ldx + c0 + c]) : df64{0.f, 0.f};
+  }
+  const int ngroups = (nk + kBtNb - 1) / kBtNb;
+  const int o = threadIdx.x % kOut, sp = threadIdx.x / kOut;
+  const int p = o / SW, c = o - p * SW;
+  for (int g = ngroups - 1; g >= 0; --g) {
+    const int k0 = g * kBtNb, nbg = min(kBtNb, nk - k0);
+    for (int e = threadIdx.x; e < kBtNb * kBtNb; e += blockDim.x)
+      Ts[e / kBtNb][e % kBtNb] = Tf[(size_t)g * kBtNb * kBtNb + e];
+    __syncthreads();   // xd (previous group) and Ts ready
+    // W[p][c] = sum over rows i >= k0+p+1 of v_{k0+p}[i] X[i][c], rows split kSplit ways
+    {
+      df64 a0{0.f, 0.f}, a1{0.f, 0.f};
+      if (sp < kSplit && p < nbg) {
+        const df64* vp = Vd + (size_t)(k0 + p) * ldv;
+        int i = k0 + p + 1 + sp;
+        for (; i + kSplit < n; i += 2 * kSplit) {
+          a0 = df_fma(vp[i], xd[i * SW + c], a0);
+          a1 = df_fma(vp[i + kSplit], xd[(i + kSplit) * SW + c], a1);
+        }
+        if (i < n) a0 = df_fma(vp[i], xd[i * SW + c], a0);
+      }
+      if (sp < kSplit) Wp[sp][p][c] = df_add(a0, a1);
+    }
+    __syncthreads();
+    // W2 = T W (T upper triangular), the split partials summed in a fixed order
+    if (threadIdx.x < kOut) {
+      df64 sacc{0.f, 0.f};
+      for (int q = p; q < nbg; ++q) {
+        df64 w = Wp[0][q][c];
+        for (int t = 1; t < kSplit; ++t) w = df_add(w, Wp[t][q][c]);
+        sacc = df_fma(Ts[p][q], w, sacc);
+      }
+      W2[p][c] = sacc;
+    }
+    __syncthreads();
+    // X[i][c] -= sum_p v_{k0+p}[i] W2[p][c] for rows i >= k0+1 (v_{k0+p}[i] = 0 for i <= k0+p)
+    const int rows = n - k0 - 1;
+    for (int e = threadIdx.x; e < rows * SW; e += blockDim.x) {
+      const int i = k0 + 1 + e / SW, cc = e % SW;
+      const int pmax = min(nbg, i - k0);
+      df64 sacc{0.f, 0.f};
+      for (int q = 0; q < pmax; ++q) sacc = df_fma(Vd[(size_t)(k0 + q) * ldv + i], W2[q][cc], sacc);
+      xd[i * SW + cc] = df_sub(xd[i * SW + cc], sacc);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * SW; e += blockDim.x) {
+    const int i = e / SW, cc = e - i * SW;
+    if (cc < nc) X[(size_t)i * ldx + c0 + cc] = df_to_double(xd[e]);
   }
 }
 
@@ -634,7 +697,9 @@ size_t eig_large_work_doubles(int n, int nev) {
   const int nparts = (n + kTriRowsPerBlock - 1) / kTriRowsPerBlock;
   // ... + the df64 copy of T (2n values, one double each)
   // ... + the barrier counter and a status word (one double)
-  return 6 * (size_t)n + 2 * (size_t)nparts + 4 + 5 * (size_t)n * nev + 2 * (size_t)n + 1 + 64;
+  // ... + the compact-WY T factors of the back-transformation (kBtNb^2 df64 per group)
+  const size_t tf = (size_t)((n + kBtNb - 1) / kBtNb) * kBtNb * kBtNb;
+  return 6 * (size_t)n + 2 * (size_t)nparts + 4 + 5 * (size_t)n * nev + 2 * (size_t)n + 1 + 64 + tf;
 }
 
 as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, double* evals, double* X, int ldx,
@@ -701,9 +766,24 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
   cluster_mgs<<<1, 512, 0, s>>>(n, nev, norms, evals, X, ldx); count_launches(1);
   if (prof) prof->end(PK_EIG_SOLVE, s, 0.0, 0.0);
   if (prof) prof->begin(PK_EIG_BACK, s);
-  const size_t smem3 = (size_t)n * kSlab * sizeof(df64);
-  AS_CUDA_TRY(as_raise_smem_limit((const void*)back_transform_df, smem3));
-  back_transform_df<<<(nev + kSlab - 1) / kSlab, 256, smem3, s>>>(Ad, lda, n, nev, X, ldx); count_launches(1);
+  {
+    const int nk = n - 2;   // reflectors k = 0 .. n-3
+    const int ngroups = (nk + kBtNb - 1) / kBtNb;
+    df64* tf = reinterpret_cast<df64*>(reinterpret_cast<double*>(cnt) + 64);
+    bt_tfactor_df<<<ngroups, 256, 0, s>>>(Ad, lda, n, nk, tf); count_launches(1);
+    // the widest slab of columns whose df64 copy fits the shared memory
+    int sw = 4;
+    while (sw > 1 && (size_t)n * sw * sizeof(df64) > 160 * 1024) sw >>= 1;
+    const size_t smem3 = (size_t)n * sw * sizeof(df64);
+    const void* fn = sw == 4 ? (const void*)bt_apply_df<4> : sw == 2 ? (const void*)bt_apply_df<2>
+                                                                     : (const void*)bt_apply_df<1>;
+    AS_CUDA_TRY(as_raise_smem_limit(fn, smem3));
+    const int nb = (nev + sw - 1) / sw;
+    if (sw == 4) bt_apply_df<4><<<nb, 256, smem3, s>>>(Ad, lda, n, nk, tf, nev, X, ldx);
+    else if (sw == 2) bt_apply_df<2><<<nb, 256, smem3, s>>>(Ad, lda, n, nk, tf, nev, X, ldx);
+    else bt_apply_df<1><<<nb, 256, smem3, s>>>(Ad, lda, n, nk, tf, nev, X, ldx);
+    count_launches(1);
+  }
   if (prof) prof->end(PK_EIG_BACK, s, 2.0 * (double)n * n * nev, 8.0 * (double)n * n);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;

@@ -942,8 +942,19 @@ as_status query_lowrank(as_sketch* h, int64_t t, float* o, bool* used) {
     cudaError_t e = cudaMemcpyAsync(kind, hk.data(), (size_t)rF * sizeof(int4), cudaMemcpyHostToDevice, h->s);
     if (e != cudaSuccess) st = as_from_cuda(e);
   }
-  // W = F F^T, scaled; H' from it
-  if (st == AS_OK) st = gemm_strided<float, float, double>(h->s, rF, rF, d, F, d, 1, F, 1, d, W, rF, 1, 1.0, 0.0);
+  // W = F F^T in FP64 (F's FP32 values are exact; FP32 partial sums would leave
+  // noise of about 1e-7 in W', above the rank cutoff), scaled; H' from it
+  if (st == AS_OK) {
+    double* F64 = nullptr;
+    st = dalloc(&F64, (size_t)rF * d);
+    if (st == AS_OK) st = launch_f32_to_f64(h->s, F, (size_t)rF * d, F64);
+    if (st == AS_OK)
+      st = gemm_strided<double, double, double>(h->s, rF, rF, d, F64, d, 1, F64, 1, d, W, rF, 1, 1.0, 0.0);
+    if (F64) {
+      cudaStreamSynchronize(h->s);
+      cudaFree(F64);
+    }
+  }
   if (st == AS_OK) st = launch_lr_scale(h->s, W, rF, kind, Ws, Hs);
   // W' = U L U^T (all rF pairs), then the numerical rank r'
   if (st == AS_OK)
@@ -958,7 +969,7 @@ as_status query_lowrank(as_sketch* h, int64_t t, float* o, bool* used) {
   if (st == AS_OK) st = sync_status(h);
   int rr = 0;
   if (st == AS_OK && hl[0] > 0.0) {
-    const double cut = 1e-11 * hl[0];
+    const double cut = 1e-10 * hl[0];
     while (rr < rF && hl[(size_t)rr] > cut) ++rr;
   }
   const int lp = std::min(ell, rr);

@@ -251,6 +251,7 @@ as_status launch_split_bf16(cudaStream_t s, const float* src, long long lds, int
 // K = L^1/2 sym(T) L^1/2 from T = U_r^T H' U_r; column scaling by lam^-1/2,
 // row scaling by D; the l largest eigenvalues of B from those of K.
 as_status launch_transpose_f32(cudaStream_t s, const float* Z, int d, int xi, float* out, long long ldo);
+as_status launch_f32_to_f64(cudaStream_t s, const float* in, size_t n, double* out);
 as_status launch_lr_scale(cudaStream_t s, const double* W, int n, const int4* kind, double* Ws, double* Hs);
 as_status launch_lr_core(cudaStream_t s, const double* T, int ldt, const double* lam, int r, double* K);
 as_status launch_lr_colscale(cudaStream_t s, double* U, int n, int ldu, const double* lam, int r);

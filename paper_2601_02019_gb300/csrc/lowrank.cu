@@ -114,7 +114,20 @@ __global__ void lr_lambda_kernel(const double* mu, int lp, int ell, double* lam_
   }
 }
 
+__global__ void f32_to_f64_kernel(const float* in, size_t n, double* out) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = (double)in[e];
+}
+
 }  // namespace
+
+as_status launch_f32_to_f64(cudaStream_t s, const float* in, size_t n, double* out) {
+  if (n == 0) return AS_OK;
+  f32_to_f64_kernel<<<1024, 256, 0, s>>>(in, n, out);
+  count_launches(1);
+  AS_CUDA_TRY(cudaGetLastError());
+  return AS_OK;
+}
 
 as_status launch_transpose_f32(cudaStream_t s, const float* Z, int d, int xi, float* out, long long ldo) {
   if (d <= 0 || xi <= 0) return AS_OK;

@@ -37,15 +37,15 @@ def spectrum(kind: str, r: int) -> np.ndarray:
 
 def low_rank_noisy(n: int, d: int, r: int, sigma: np.ndarray, noise: float = 0.01,
                    seed: int = 0, stream: int = 0, start: int = 0,
-                   V: np.ndarray | None = None) -> np.ndarray:
+                   V: np.ndarray | None = None, chunk: int = 4096) -> np.ndarray:
     """Rows start..start+n-1 of the stream, FP32, C-contiguous (n x d).
 
-    Rows are drawn in chunks of 4096 keyed by chunk index, so any window of the
-    stream is reproducible without drawing the rows before it."""
+    Rows are drawn in chunks of `chunk` rows keyed by chunk index, so any
+    window of the stream is reproducible without drawing the rows before it
+    (streams with another chunk size are other streams)."""
     if V is None:
         V = basis(d, r, seed, stream)
     out = np.empty((n, d), dtype=np.float32)
-    chunk = 4096
     c0, c1 = start // chunk, (start + n + chunk - 1) // chunk
     for c in range(c0, c1):
         rng = _rng(seed, (stream << 32) + c)
@@ -54,6 +54,42 @@ def low_rank_noisy(n: int, d: int, r: int, sigma: np.ndarray, noise: float = 0.0
         blk = (g * sigma[None, :]) @ V.T + eta
         lo, hi = max(start, c * chunk), min(start + n, (c + 1) * chunk)
         out[lo - start:hi - start] = blk[lo - c * chunk:hi - c * chunk]
+    return out
+
+
+def givens_sweep(V: np.ndarray, seed: int, k: int) -> np.ndarray:
+    """G_k V for the k-th sweep of Givens rotations on the coordinate pairs
+    (j, j+1), j = 0 .. d-2 in order, angles uniform on [0, 2 pi) from a stream
+    of their own (keyed by seed and k)."""
+    V = np.array(V, dtype=np.float64, copy=True)
+    th = _rng(seed, 3_000_000 + k).uniform(0.0, 2.0 * np.pi, V.shape[0] - 1)
+    c, s = np.cos(th), np.sin(th)
+    for j in range(V.shape[0] - 1):
+        a, b = V[j].copy(), V[j + 1].copy()
+        V[j] = c[j] * a - s[j] * b
+        V[j + 1] = s[j] * a + c[j] * b
+    return V
+
+
+def drifting_rows(n: int, d: int, r: int, sigma: np.ndarray, period: int, noise: float = 0.01,
+                  seed: int = 0, start: int = 0) -> np.ndarray:
+    """Rows start..start+n-1 of a stream whose basis rotates by one Givens
+    sweep every `period` rows: row t uses V_k, k = t // period, V_0 = basis(d, r)
+    and V_k = G_k V_{k-1}; within a period the rows are those of
+    low_rank_noisy with that basis."""
+    out = np.empty((n, d), dtype=np.float32)
+    V = basis(d, r, seed)
+    k_have = 0
+    t = start
+    while t < start + n:
+        k = t // period
+        while k_have < k:
+            k_have += 1
+            V = givens_sweep(V, seed, k_have)
+        t1 = min(start + n, (k + 1) * period)
+        out[t - start:t1 - start] = low_rank_noisy(t1 - t, d, r, sigma, noise=noise, seed=seed, stream=k,
+                                                   start=t - k * period, V=V)
+        t = t1
     return out
 
 

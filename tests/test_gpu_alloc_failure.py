@@ -43,7 +43,7 @@ def test_query_failure_leaves_the_sketch(p, dense):
     s = p.Sketch(d, ell, dense_query=dense)
     s.update(A)
     B0, Bh0 = s.query_gram(), s.query()
-    for after in (0, 2, 5):
+    for after in (0, 2, 4):     # every route makes at least five allocations
         p.lib().as_inject_alloc_failure(after)
         _enomem(p, lambda: s.query())
         assert np.array_equal(s.query_gram(), B0)
