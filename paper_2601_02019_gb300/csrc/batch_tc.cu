@@ -225,14 +225,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
     float* part = a.part + (size_t)bnew * a.nks * a.pplane;
 
     // ---- product phase: Z(rows rb, all columns) over K range ks ----
-    if (warp == 0 && lane == 0 && niter > 0) {
+    if (warp == 0 && niter > 0) {
       bool ok = true;
-      if (it > 0) {   // rows [k0, k1) of Y_it: the reductions of the previous iteration that hold them
+      if (it > 0) {
+        // rows [k0, k1) of Y_it: the reductions of the previous iteration that
+        // hold them; the warp's lanes poll those CTAs' flags at the same time
+        // (one L2 round trip when they are set, not one per flag)
         const int c_lo = k0 / a.rpc, c_hi = min(G - 1, (k1 - 1) / a.rpc);
-        for (int c = c_lo; c <= c_hi && ok; ++c) ok = wait_flag_ge(a.flags + c, (unsigned)it, a.status);
+        for (int c = c_lo + lane; c <= c_hi; c += 32)
+          if (ok) ok = wait_flag_ge(a.flags + c, (unsigned)it, a.status);
       }
-      asm volatile("fence.proxy.async.global;" ::: "memory");   // Y_it was written through the generic proxy
-      for (int li = 0; li < niter && ok; ++li) {
+      ok = __all_sync(0xffffffffu, ok);
+      if (lane == 0 && ok) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");          // the other lanes' acquires, for lane 0
+        asm volatile("fence.proxy.async.global;" ::: "memory");   // Y_it was written through the generic proxy
+      }
+      for (int li = 0; li < niter && ok && lane == 0; ++li) {
         const int g = it * niter + li;
         const int s = g % kTcStages;
         const uint32_t ph = (uint32_t)(g / kTcStages) & 1u;
@@ -245,7 +253,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
         tma_load_2d(st + 2 * A_BYTES, &mY.m[0], &full_bar[s], kx, bold * a.ycols);
         tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mY.m[1], &full_bar[s], kx, bold * a.ycols);
       }
-      if (!ok) atomicExch(&fail_s, 1);
+      if (lane == 0 && !ok) atomicExch(&fail_s, 1);
     } else if (warp == 1 && lane == 0 && niter > 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       for (int li = 0; li < niter; ++li) {

@@ -422,16 +422,20 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
   df64* vcur = smp;           // v_{r-1}[j], j in [r, n)
   df64* vnew = smp + n;       // row r, then v_r[j], j in [r+1, n)
   df64* wk = smp + 2 * n;     // w_{r-1}[j], j in [r, n)
-  __shared__ df64 red[32];
-  __shared__ df64 c_s;
+  __shared__ df64 red[kTriWarps];
+  __shared__ df64 x0_s;
   __shared__ df64 wpart[kTriWarps];
   const int W = G * kTriWarps, gw = blockIdx.x * kTriWarps + warp;
+  // Every thread owns the entries j = r + tid + kTriThreads u of the pass's
+  // vectors (row r, w, v_r) and is the only one to write them before the
+  // barrier that publishes v_r to the sweep; the pass has four CTA barriers
+  // (after w, after the norm partials of row r, after v_r, and the grid
+  // barrier's own) besides the grid barrier.
   for (int r = 0; r <= n - 2; ++r) {
     const bool upd = r >= 1;
     const df64* arow = t.A + (size_t)r * t.lda;
-    // the entries j = r + tid + kTriThreads u of p_{r-1} and of row r are loaded
-    // together with the partial sums below: one L2 round trip instead of three
-    // (p and row r do not depend on the coefficient those sums give)
+    // the entries of p_{r-1} and of row r are loaded together with the partial
+    // sums below: one L2 round trip (they do not depend on the coefficient)
     df64 pjr[kTriPre], ajr[kTriPre];
 #pragma unroll
     for (int u = 0; u < kTriPre; ++u) {
@@ -441,24 +445,22 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
       ajr[u] = (j < n) ? arow[j] : df64{0.f, 0.f};
     }
     if (upd) {
+      // c = v^T p from the per-CTA partials: every warp sums them itself, in the
+      // same order, so all threads hold the same value without a barrier
       const df64* qin = ((r - 1) & 1) ? t.q[1] : t.q[0];
-      if (tid < 32) {   // loads of 8 partials per lane in flight before the adds
-        df64 c{0.f, 0.f};
-        for (int g0 = 0; g0 < G; g0 += 256) {
-          df64 qb[8];
+      df64 c{0.f, 0.f};
+      for (int g0 = 0; g0 < G; g0 += 256) {
+        df64 qb[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int g = g0 + 32 * u + tid;
-            qb[u] = (g < G) ? qin[g] : df64{0.f, 0.f};
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) c = df_add(c, qb[u]);
+        for (int u = 0; u < 8; ++u) {
+          const int g = g0 + 32 * u + lane;
+          qb[u] = (g < G) ? qin[g] : df64{0.f, 0.f};
         }
-        c = df_warp_sum(c);
-        if (tid == 0) c_s = c;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) c = df_add(c, qb[u]);
       }
-      __syncthreads();
-      const df64 c2{2.f * c_s.hi, 2.f * c_s.lo};
+      c = df_warp_sum(c);
+      const df64 c2{2.f * c.hi, 2.f * c.lo};
       const df64* pin = ((r - 1) & 1) ? t.p[1] : t.p[0];
 #pragma unroll
       for (int u = 0; u < kTriPre; ++u) {
@@ -485,6 +487,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
       if (j >= r + 1 && j < n) {
         const df64 x = upd ? df_rank2(ajr[u], vr, wk[j], wr, vcur[j]) : ajr[u];
         vnew[j] = x;
+        if (j == r + 1) x0_s = x;
         acc = df_fma(x, x, acc);
       }
     }
@@ -493,7 +496,14 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
       vnew[j] = x;
       acc = df_fma(x, x, acc);
     }
-    const df64 s = df_block_sum(acc, red);
+    // ||x||^2 over the block: warp sums, one barrier, then every thread adds
+    // the warps' sums in the same order
+    acc = df_warp_sum(acc);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    df64 s = red[0];
+#pragma unroll
+    for (int q = 1; q < kTriWarps; ++q) s = df_add(s, red[q]);
     if (r == n - 2) {   // 2 x 2 tail: no further reflector
       if (blockIdx.x == 0 && tid == 0) {
         const int j = n - 1;
@@ -507,7 +517,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
     // Householder scalars in df64 (FP64 instructions are slow on this part and
     // these sit on every pass's critical path): alpha = -sign(x0) ||x||, and
     // ||x - alpha e_1||^2 = s - x0^2 + (|x0| + ||x||)^2 = 2 (s + |x0| ||x||)
-    const df64 x0 = vnew[r + 1];
+    const df64 x0 = x0_s;
     const bool szero = !(s.hi > 0.f);
     df64 alpha{0.f, 0.f}, rvn{1.f, 0.f};
     if (!szero) {
@@ -517,8 +527,14 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
       const df64 h = df_add(s, df_mul(ax0, sq));
       rvn = df_div(df64{1.f, 0.f}, df_sqrt(df64{2.f * h.hi, 2.f * h.lo}));
     }
-    __syncthreads();
-    for (int j = r + 1 + tid; j < n; j += blockDim.x) vnew[j] = house_v_df(vnew[j], j == r + 1, szero, alpha, rvn);
+    // v_r from this thread's own entries of x (x0 came through x0_s)
+#pragma unroll
+    for (int u = 0; u < kTriPre; ++u) {
+      const int j = r + tid + kTriThreads * u;
+      if (j >= r + 1 && j < n) vnew[j] = house_v_df(vnew[j], j == r + 1, szero, alpha, rvn);
+    }
+    for (int j = r + tid + kTriThreads * kTriPre; j < n; j += blockDim.x)
+      vnew[j] = house_v_df(vnew[j], j == r + 1, szero, alpha, rvn);
     if (blockIdx.x == 0 && tid == 0) t.e[r] = df_to_double(alpha);
     __syncthreads();
     // rows i >= r+1 of this warp: update with (v_{r-1}, w_{r-1}), dot with v_r
@@ -561,13 +577,15 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
       }
     }
     if (lane == 0) wpart[warp] = contrib;
-    __syncthreads();
-    if (tid == 0) {
+    // the grid barrier's first CTA barrier also orders wpart; thread 0 then
+    // publishes this CTA's partial of v_r^T p_r before it arrives
+    df64* qout = (r & 1) ? t.q[1] : t.q[0];
+    const bool ok = grid_barrier_then(t.cnt, (unsigned)(r + 1) * (unsigned)G, t.status, [&] {
       df64 q = wpart[0];
       for (int u = 1; u < kTriWarps; ++u) q = df_add(q, wpart[u]);
-      ((r & 1) ? t.q[1] : t.q[0])[blockIdx.x] = q;
-    }
-    if (!grid_barrier(t.cnt, (unsigned)(r + 1) * (unsigned)G, t.status)) return;
+      qout[blockIdx.x] = q;
+    });
+    if (!ok) return;
     df64* tmp = vcur;   // v_r becomes the vector of the next pass's update
     vcur = vnew;
     vnew = tmp;

@@ -256,11 +256,14 @@ as_status tc_split_rows(as_sketch* h, int r0, int r1) {
                            h->Cl2 ? h->Cl2 + (size_t)r0 * h->ldc : nullptr);
 }
 
-// Longest K range that one TMEM accumulator sums for the products that write
-// state (Gram rows, FD rebuild): longer ranges are split and the partial
-// planes summed in FP64, which keeps the accumulation error of the tensor
-// forms near that of the FP32 form (FP32 partial sums of 64, combined in FP64).
-constexpr int kTcStateChunk = 64;
+// Longest K range of one split of the products that write state (Gram rows,
+// FD rebuild): longer ranges are split and the partial planes summed in FP64.
+// In the precise mode of the tcgen05 GEMM each of the four K = 16 MMAs of a
+// 64-wide tile has its own accumulator, so a 256-element split costs each
+// accumulator three truncating accumulate steps; this keeps the accumulation
+// error near that of the FP32 form (FP32 partial sums of 64, combined in FP64)
+// while writing a quarter of the planes of 64-element splits.
+constexpr int kTcStateChunk = 256;
 
 as_status ensure_prb(as_sketch* h, size_t need) {
   if (need <= h->prb_cap) return AS_OK;

@@ -28,10 +28,14 @@ __device__ __forceinline__ bool wait_flag_ge(const unsigned* flag, unsigned targ
                                              unsigned long long limit_ns = kWaitLimitNs) {
   const unsigned long long t0 = global_ns();
   long long n = 0;
+  // the sticky status and the clock are checked every 8th poll, so a poll is
+  // one L2 round trip
   while (ld_acquire_u32(flag) < target) {
-    if (*(volatile int*)status != 0) return false;
-    if (++n > kWaitMaxIters || global_ns() - t0 > limit_ns) { set_status(status, AS_ETIMEOUT); return false; }
-    __nanosleep(32);
+    if ((++n & 7) == 0) {
+      if (*(volatile int*)status != 0) return false;
+      if (n > kWaitMaxIters || global_ns() - t0 > limit_ns) { set_status(status, AS_ETIMEOUT); return false; }
+    }
+    __nanosleep(20);
   }
   return true;
 }
@@ -51,14 +55,43 @@ __device__ __forceinline__ bool grid_barrier(unsigned* cnt, unsigned target, int
     const unsigned long long t0 = global_ns();
     long long n = 0;
     while (ld_acquire_u32(cnt) < target) {
-      if (*(volatile int*)status != 0) { ok = 0; break; }
-      if (++n > kWaitMaxIters || global_ns() - t0 > limit_ns) { set_status(status, AS_ETIMEOUT); ok = 0; break; }
-      __nanosleep(32);
+      if ((++n & 7) == 0) {
+        if (*(volatile int*)status != 0) { ok = 0; break; }
+        if (n > kWaitMaxIters || global_ns() - t0 > limit_ns) { set_status(status, AS_ETIMEOUT); ok = 0; break; }
+      }
+      __nanosleep(20);
     }
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// grid_barrier with `before_arrive` run by thread 0 after the CTA barrier and
+// before its arrival (e.g. publishing a per-CTA partial that the block's
+// shared memory holds); the arrival releases what it wrote.
+template <typename F>
+__device__ __forceinline__ bool grid_barrier_then(unsigned* cnt, unsigned target, int* status, F&& before_arrive,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
+  __shared__ int s_ok2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    before_arrive();
+    red_release_add_u32(cnt, 1u);
+    int ok = 1;
+    const unsigned long long t0 = global_ns();
+    long long n = 0;
+    while (ld_acquire_u32(cnt) < target) {
+      if ((++n & 7) == 0) {
+        if (*(volatile int*)status != 0) { ok = 0; break; }
+        if (n > kWaitMaxIters || global_ns() - t0 > limit_ns) { set_status(status, AS_ETIMEOUT); ok = 0; break; }
+      }
+      __nanosleep(20);
+    }
+    s_ok2 = ok;
+  }
+  __syncthreads();
+  return s_ok2 != 0;
 }
 
 }  // namespace as

@@ -36,9 +36,10 @@ namespace {
 
 constexpr int STAGES = 4;
 // PRECISE (state-writing products, BN <= 64): each of the four K = 16 MMAs of
-// a stage has its own hi*hi accumulator, so with 64-element K splits every
-// accumulator takes a single step and the rest of the sum happens in FP32
-// registers (round to nearest) and in the FP64 plane reduction.
+// a stage has its own hi*hi accumulator, so a K split of t tiles costs every
+// accumulator t - 1 accumulate steps (the engine uses splits of at most four
+// tiles) and the rest of the sum happens in FP32 registers (round to nearest)
+// and in the FP64 plane reduction.
 template <int BN, int NPASS, bool PRECISE>
 __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant__ UmmaOperand opA,
                                                            const __grid_constant__ UmmaOperand opB, int M, int N,
