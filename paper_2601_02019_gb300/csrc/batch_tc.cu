@@ -22,14 +22,14 @@
 // of G and of Y (128-byte swizzle) through a 2-stage ring, one lane issues
 // the three level products as tcgen05.mma into two TMEM accumulators (the
 // leading level product and the corrections), and the partial 128 x N block
-// goes to global memory.  After a grid barrier CTA c sums the K-split
-// partials of its rpc rows in a fixed order, applies C_it, masks, writes
-// Y_{it+1} (FP32 and its BF16 levels) and its per-pair partial sums, and
-// publishes them with a release flag (synchronisation below).  The
-// coefficients C_it are computed from those partial sums by the other warps
-// while the product runs.  Every mbarrier, flag and grid-barrier wait is
-// bounded; on a timeout the status word gets AS_ETIMEOUT and every CTA frees
-// its TMEM and returns.
+// goes to global memory.  Once the nks products of its row block are in, CTA
+// (rb, ks) sums the K-split partials of its rpb rows of that row block in a
+// fixed order, applies C_it, masks, writes Y_{it+1} (FP32 and its BF16
+// levels) and its per-pair partial sums, and publishes them with a release
+// flag (synchronisation below).  The coefficients C_it are computed from
+// those partial sums by the other warps while the product runs.  Every
+// mbarrier, counter and flag wait is bounded; on a timeout the status word
+// gets AS_ETIMEOUT and every CTA frees its TMEM and returns.
 #include <algorithm>
 #include <mutex>
 
@@ -64,11 +64,11 @@ struct TcArgs {
   long long pplane;
   float* sums;         // per-pair partial sums, two buffers of sbuf floats: [pair * kTcSlots + slot][cta]
   long long sbuf;
-  unsigned* cnt;
   unsigned* flags;     // per CTA: 1 + the last iteration whose reduction it published
+  unsigned* rbcnt;     // per row block: arrivals of its K-split products (nks per iteration)
   int* status;
   int nb, npi, r0, k_pi, q, mmax;
-  int kpad, nrb, nks, kc, nc, rpc;
+  int kpad, nrb, nks, kc, nc, rpb;   // rpb: rows of its row block that a CTA reduces
   double* sig2;
   double* ritz;
 };
@@ -156,15 +156,20 @@ __device__ __forceinline__ void tc_finals(const TcArgs& a, const float* s, int f
   }
 }
 
-// Synchronisation.  One grid barrier per iteration separates the K-split
-// partial products from their reduction.  The reduction of CTA c publishes
-// rows [c rpc, (c+1) rpc) of Y_{it+1} and its partial sums with a release
-// store of flags[c] = it + 1; the product of the next iteration waits
-// (acquire) only for the flags of the CTAs whose rows form its K range, and
-// the coefficient warps, which need every CTA's partial sums, wait for all
-// flags while the product runs.  The partial products are double buffered by
-// iteration parity, so a product never overwrites a plane that a slower
-// CTA's reduction still reads.
+// Synchronisation.  No grid-wide barrier: a row block's K-split products and
+// their reduction are separated by a counter of that row block alone (each of
+// its nks CTAs adds one per iteration, release, and waits for nks (it + 1),
+// acquire).  The reduction of CTA (rb, ks) publishes rows
+// rb 128 + [ks rpb, (ks+1) rpb) of Y_{it+1} and its partial sums with a
+// release store of flags[cta] = it + 1; the product of the next iteration
+// waits (acquire) only for the flags of the CTAs whose rows form its K range,
+// and the coefficient warps, which need every CTA's partial sums, wait for all
+// flags while the product runs, so no CTA starts the reduction of iteration
+// it + 1 before every CTA has finished that of iteration it.  With the
+// products, Y and the partial sums double buffered by iteration parity, no
+// buffer is then written while a slower CTA still reads it: a CTA writes only
+// its own row block's rows of the product planes, and a CTA at iteration it + 2
+// has waited for everyone's reduction of it + 1.
 template <int NPASS>
 __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
                                                                  const __grid_constant__ UmmaOperand mG,
@@ -211,7 +216,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
                          ((uint32_t)(UM >> 4) << 24);
 
   const int iters = max(a.k_pi, a.q);
-  unsigned bar_target = 0;
   bool alive = true;
   for (int it = 0; it <= iters; ++it) {
     const bool pi_on = it <= a.k_pi, si_on = it <= a.q;
@@ -231,9 +235,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
         // rows [k0, k1) of Y_it: the reductions of the previous iteration that
         // hold them; the warp's lanes poll those CTAs' flags at the same time
         // (one L2 round trip when they are set, not one per flag)
-        const int c_lo = k0 / a.rpc, c_hi = min(G - 1, (k1 - 1) / a.rpc);
-        for (int c = c_lo + lane; c <= c_hi; c += 32)
-          if (ok) ok = wait_flag_ge(a.flags + c, (unsigned)it, a.status);
+        // CTA (rb', ks') reduced rows rb' 128 + [ks' rpb, (ks'+1) rpb)
+        const int rb_lo = k0 / UM, rb_hi = (k1 - 1) / UM;
+        const int ncand = (rb_hi - rb_lo + 1) * a.nks;
+        for (int e = lane; e < ncand; e += 32) {
+          const int rbx = rb_lo + e / a.nks, ksx = e - (e / a.nks) * a.nks;
+          const int lo = rbx * UM + ksx * a.rpb, hi = min(rbx * UM + UM, lo + a.rpb);
+          if (lo < k1 && hi > k0 && ok) ok = wait_flag_ge(a.flags + rbx * a.nks + ksx, (unsigned)it, a.status);
+        }
       }
       ok = __all_sync(0xffffffffu, ok);
       if (lane == 0 && ok) {
@@ -400,12 +409,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (tid == 0 && fail_s) set_status(a.status, AS_ETIMEOUT);
-    bar_target += (unsigned)G;
-    if (!grid_barrier(a.cnt, bar_target, a.status)) { alive = false; break; }
+    // the row block's K-split products of this iteration are all written: each
+    // CTA of the row block arrives once (release) and waits for the others
+    // (acquire, bounded); no other row block takes part
+    {
+      __shared__ int rb_ok;
+      if (tid == 0) {
+        if (fail_s) set_status(a.status, AS_ETIMEOUT);
+        red_release_add_u32(a.rbcnt + rb, 1u);
+        rb_ok = wait_flag_ge(a.rbcnt + rb, (unsigned)(it + 1) * (unsigned)a.nks, a.status) ? 1 : 0;
+      }
+      __syncthreads();
+      if (!rb_ok) { alive = false; break; }
+    }
 
-    // ---- reduction phase: rows [rw0, rw1) of Y_{it+1} = Z C_it ----
-    const int rw0 = blk * a.rpc, rw1 = min(a.kpad, rw0 + a.rpc);
+    // ---- reduction phase: rows [rw0, rw1) of row block rb of Y_{it+1} = Z C_it ----
+    const int rw0 = rb * UM + ks * a.rpb, rw1 = min(rb * UM + UM, rw0 + a.rpb);
     const int R = max(0, rw1 - rw0);
     const int c0a = 2 * pa0, nca = 2 * nact;
     {
@@ -575,8 +594,9 @@ as_status launch_tc_mirror(cudaStream_t s, const double* G, int n2, int valid, i
 
 size_t batch_tc_part_floats(int n2, int ycols) {
   const size_t kpad = (size_t)(n2 + 127) / 128 * 128;
-  // two buffers of nks <= 16 planes (checked at launch), then the CTA flags
-  return (size_t)2 * 16 * kpad * (size_t)std::min(ycols, kTcMaxCols) + 256;
+  // two buffers of nks <= 16 planes (checked at launch), then 256 CTA flags
+  // and 256 row-block counters
+  return (size_t)2 * 16 * kpad * (size_t)std::min(ycols, kTcMaxCols) + 512;
 }
 
 as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int q, Key key, uint64_t i0,
@@ -604,8 +624,8 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
   kc = (kpad + nks - 1) / nks;
   kc = (kc + 63) / 64 * 64;
   const int ncta = nrb * nks;
-  const int rpc = (kpad + ncta - 1) / ncta;
-  if (nks > kTcMaxSplits || ncta > td.sms || rpc > kTcMaxRpc) return AS_OK;
+  const int rpb = (UM + nks - 1) / nks;   // rows of its own row block that each CTA reduces
+  if (nks > kTcMaxSplits || ncta > td.sms || rpb > kTcMaxRpc) return AS_OK;
   const size_t smem = 1024 + (size_t)kTcStages * 2 * (UM * UK * 2 + (size_t)nc * UK * 2);
   const int v = 0;
   const void* fn = (const void*)batch_tc_kernel<3>;
@@ -630,9 +650,8 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
   count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   if (prof) prof->end(PK_BATCH_ORTH, s, 0.0, 12.0 * mmax * (double)nb);
-  AS_CUDA_TRY(cudaMemsetAsync(pb.cnt, 0, sizeof(unsigned), s));
-  unsigned* flags = reinterpret_cast<unsigned*>(tb.part + batch_tc_part_floats(n2, (int)pb.ycols) - 256);
-  AS_CUDA_TRY(cudaMemsetAsync(flags, 0, 256 * sizeof(unsigned), s));
+  unsigned* flags = reinterpret_cast<unsigned*>(tb.part + batch_tc_part_floats(n2, (int)pb.ycols) - 512);
+  AS_CUDA_TRY(cudaMemsetAsync(flags, 0, 512 * sizeof(unsigned), s));   // CTA flags and row-block counters
   TcArgs a{};
   a.Y = pb.Y; a.ybuf = pb.ybuf; a.ldy = pb.ldy;
   a.Yb = tb.Yb; a.yblevel = tb.yblevel; a.ybbuf = (long long)pb.ycols * tb.ldyb; a.ldyb = tb.ldyb;
@@ -640,9 +659,9 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
   a.X = pb.X; a.ldx = n2;
   a.part = tb.part; a.pplane = (long long)kpad * nc;
   a.sums = pb.part; a.sbuf = (long long)kTcSlots * P * ncta;
-  a.cnt = pb.cnt; a.flags = flags; a.status = status;
+  a.flags = flags; a.rbcnt = flags + 256; a.status = status;
   a.nb = nb; a.npi = npi; a.r0 = r0; a.k_pi = k_pi; a.q = q; a.mmax = mmax;
-  a.kpad = kpad; a.nrb = nrb; a.nks = nks; a.kc = kc; a.nc = nc; a.rpc = rpc;
+  a.kpad = kpad; a.nrb = nrb; a.nks = nks; a.kc = kc; a.nc = nc; a.rpb = rpb;
   a.sig2 = pb.sig2; a.ritz = pb.ritz;
   void* args[] = {&a, (void*)&tb.mG, &mY};
   if (prof) prof->begin(PK_BATCH_TC, s);

@@ -697,9 +697,14 @@ __global__ void __launch_bounds__(256) bt_apply_df(const df64* Vd, int ldv, int 
     for (int e = threadIdx.x; e < rows * SW; e += blockDim.x) {
       const int i = k0 + 1 + e / SW, cc = e % SW;
       const int pmax = min(nbg, i - k0);
-      df64 sacc{0.f, 0.f};
-      for (int q = 0; q < pmax; ++q) sacc = df_fma(Vd[(size_t)(k0 + q) * ldv + i], W2[q][cc], sacc);
-      xd[i * SW + cc] = df_sub(xd[i * SW + cc], sacc);
+      df64 s0{0.f, 0.f}, s1{0.f, 0.f};   // two chains: even and odd reflectors
+      int q = 0;
+      for (; q + 1 < pmax; q += 2) {
+        s0 = df_fma(Vd[(size_t)(k0 + q) * ldv + i], W2[q][cc], s0);
+        s1 = df_fma(Vd[(size_t)(k0 + q + 1) * ldv + i], W2[q + 1][cc], s1);
+      }
+      if (q < pmax) s0 = df_fma(Vd[(size_t)(k0 + q) * ldv + i], W2[q][cc], s0);
+      xd[i * SW + cc] = df_sub(xd[i * SW + cc], df_add(s0, s1));
     }
   }
   __syncthreads();
@@ -789,9 +794,13 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
     const int ngroups = (nk + kBtNb - 1) / kBtNb;
     df64* tf = reinterpret_cast<df64*>(reinterpret_cast<double*>(cnt) + 64);
     bt_tfactor_df<<<ngroups, 256, 0, s>>>(Ad, lda, n, nk, tf); count_launches(1);
-    // the widest slab of columns whose df64 copy fits the shared memory
+    // the widest slab of columns whose df64 copy fits the shared memory and
+    // leaves at least three blocks per SM to hide the df64 chains' latency
+    int dev = 0, sms = 0;
+    AS_CUDA_TRY(cudaGetDevice(&dev));
+    AS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int sw = 4;
-    while (sw > 1 && (size_t)n * sw * sizeof(df64) > 160 * 1024) sw >>= 1;
+    while (sw > 1 && ((size_t)n * sw * sizeof(df64) > 160 * 1024 || (nev + sw - 1) / sw < 3 * sms)) sw >>= 1;
     const size_t smem3 = (size_t)n * sw * sizeof(df64);
     const void* fn = sw == 4 ? (const void*)bt_apply_df<4> : sw == 2 ? (const void*)bt_apply_df<2>
                                                                      : (const void*)bt_apply_df<1>;
