@@ -167,6 +167,10 @@ def reference_arm(args) -> None:
 
 
 PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "bf16x6": 3}
+DTYPES = {f: {"fp32": "f32 products", "bf16": "bf16 tensor products (f32 acc)",
+              "bf16x3": "2-level split-bf16 tensor products (f32 acc)",
+              "bf16x6": "3-level split-bf16 tensor products (f32 acc)"}[f]
+          + "; f64 orthonormalisation and Rayleigh-Ritz; df64 (~48-bit) eigensolver" for f in PRECISIONS}
 
 _ORACLE_CHILD = r"""
 import sys, time, numpy as np
@@ -472,7 +476,7 @@ def serve_arm(args) -> None:
     sid, refused = {}, 0
     for s in range(S):
         try:
-            sid[s] = sv.open(int(mix["d"][s]), int(mix["ell"][s]), stream_id=s,
+            sid[s] = sv.open(int(mix["d"][s]), int(mix["ell"][s]), stream_id=s, prec=PRECISIONS[args.prec],
                              mass_ratio=max(1.0, 10.0 * (phases * planned[s] + args.warmup * 64)))
         except p.AeroSketchError as e:
             if "AS_EBUSY" not in str(e):
@@ -524,8 +528,12 @@ def serve_arm(args) -> None:
         "metric": "rows/s of the serving loop at saturation (host-fed requests)", "value": sat["rows_per_s"],
         "unit": "rows/s", "n_gpus": 1, "steps": phases, "warmup": args.warmup,
         "ms_per_step": 1e3 * sat["span_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 products; f64 orthonormalisation and Rayleigh-Ritz; df64 (~48-bit) eigensolver", "data": "synthetic",
-        "config": {"workload": args.workload, "sessions": S, "admitted": len(sid), "refused": refused,
+        "dtype": {"fp32": "f32 products", "bf16": "bf16 tensor products (f32 acc)",
+                  "bf16x3": "2-level split-bf16 tensor products (f32 acc)",
+                  "bf16x6": "3-level split-bf16 tensor products (f32 acc)"}[args.prec]
+                 + "; f64 orthonormalisation and Rayleigh-Ritz; df64 (~48-bit) eigensolver", "data": "synthetic",
+        "config": {"workload": args.workload, "precision": args.prec, "sessions": S, "admitted": len(sid),
+                   "refused": refused,
                    "requests_per_phase": len(reqs), "rows_per_phase": int(sum(b for _, b, _ in reqs)),
                    "footprint_GB": fp / 1e9, "open_s": open_s, "workers": 16,
                    "l2": "per-session state re-read from HBM; rows copied from pinned host memory per request"},
@@ -596,7 +604,7 @@ def extra_arm(args) -> None:
     if args.workload.startswith("p5"):
         rows = _p5_rows(w, W + K, seed=0)
         b, m = w["rows_per_site"], w["m"]
-        g = p.P5(w["d"], w["ell"], m, stream=stream)
+        g = p.P5(w["d"], w["ell"], m, stream=stream, prec=PRECISIONS[args.prec])
         step_rows = b * m
 
         def step(k):
@@ -620,7 +628,7 @@ def extra_arm(args) -> None:
         A = A.astype(np.float32)
         R = 2.0 ** np.ceil(np.log2(np.max(np.sum(A.astype(np.float64) ** 2, axis=1))))
         A_dev = torch.from_numpy(A).cuda()
-        g = p.SlidingWindow(d, ell, N, R, stream=stream)
+        g = p.SlidingWindow(d, ell, N, R, stream=stream, prec=PRECISIONS[args.prec])
         step_rows = B
         for t0 in range(0, pre, B):
             g.update(A_dev[t0:min(pre, t0 + B)])
@@ -649,8 +657,8 @@ def extra_arm(args) -> None:
         "metric": "rows/s of the " + ("P5 round (all sites)" if args.workload.startswith("p5")
                                       else "sliding-window update"),
         "value": value, "unit": "rows/s", "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": ms / K,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 products; f64 orthonormalisation and Rayleigh-Ritz; df64 (~48-bit) eigensolver",
-        "data": "synthetic", "config": cfg, "clocks": clk.summary(),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.prec],
+        "data": "synthetic", "config": dict(cfg, precision=args.prec), "clocks": clk.summary(),
     }))
 
 
