@@ -21,13 +21,15 @@
 // K = kc): a TMA producer lane streams, per 64-wide K tile, both BF16 levels
 // of G and of Y (128-byte swizzle) through a 2-stage ring, one lane issues
 // the three level products as tcgen05.mma into two TMEM accumulators (the
-// leading level product and the corrections), and the partial 128 x N block
-// goes to global memory.  Once the nks products of its row block are in, CTA
+// leading level product and the corrections), and warps 4-7 (one TMEM lane
+// quarter each) move the partial 128 x N block to global memory, after which
+// warp 1 announces it to the row block.  Once the nks products of its row block are in, CTA
 // (rb, ks) sums the K-split partials of its rpb rows of that row block in a
 // fixed order, applies C_it, masks, writes Y_{it+1} (FP32 and its BF16
 // levels) and its per-pair partial sums, and publishes them with a release
 // flag (synchronisation below).  The coefficients C_it are computed from
-// those partial sums by the other warps while the product runs.  Every
+// those partial sums by warps 2-7 (warps 4-7 after their epilogue, so the
+// product's announcement never waits for the coefficients).  Every
 // mbarrier, counter and flag wait is bounded; on a timeout the status word
 // gets AS_ETIMEOUT and every CTA frees its TMEM and returns.
 #include <algorithm>
@@ -47,7 +49,6 @@ constexpr int kTcSlots = 6;     // partial sums per pair
 constexpr int kTcMaxRpc = 32;   // rows per CTA in the reduction phase
 constexpr int kTcMaxCols = 192; // batch columns (2 P)
 constexpr int kTcMaxSplits = 16; // K ranges per row block (nks, checked at launch)
-constexpr int kRedElems = 4;     // elements per thread whose loads are in flight together in the reduction
 
 struct TcArgs {
   float* Y;            // FP32 columns, two buffers of ybuf floats, ld ldy
@@ -180,13 +181,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
   const uint32_t A_BYTES = UM * UK * 2;
   const uint32_t B_BYTES = (uint32_t)a.nc * UK * 2;
   const uint32_t S_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  float* zs = reinterpret_cast<float*>(smem);   // reduction phase: reuses the ring
   __shared__ __align__(8) uint64_t full_bar[kTcStages];
   __shared__ __align__(8) uint64_t empty_bar[kTcStages];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int fail_s;
   __shared__ float4 coef[kTcMaxCols / 2];
+  __shared__ int rb_ok_s;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x, blk = blockIdx.x;
@@ -263,41 +264,95 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
         tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mY.m[1], &full_bar[s], kx, bold * a.ycols);
       }
       if (lane == 0 && !ok) atomicExch(&fail_s, 1);
-    } else if (warp == 1 && lane == 0 && niter > 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int li = 0; li < niter; ++li) {
-        const int g = it * niter + li;
-        const int s = g % kTcStages;
-        const uint32_t ph = (uint32_t)(g / kTcStages) & 1u;
-        if (!mbar_wait(&full_bar[s], ph)) { atomicExch(&fail_s, 1); break; }
+    } else if (warp == 1) {
+      if (lane == 0 && niter > 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t st = smem_u32(smem + (size_t)s * S_BYTES);
-        // level products G0 Y0 (leading accumulator), G0 Y1 and G1 Y0 (corrections)
-#pragma unroll
-        for (int pass = 0; pass < 3; ++pass) {
-          const uint32_t a0 = st + (pass == 2 ? A_BYTES : 0u);
-          const uint32_t b0 = st + 2 * A_BYTES + (pass == 1 ? B_BYTES : 0u);
-#pragma unroll
-          for (int kk = 0; kk < UK / 16; ++kk) {
-            const int aidx = (pass == 0) ? 0 : 1;
-            const bool first = (li == 0) && (kk == 0) && (pass <= 1);
-            const uint32_t dst = tmem + (uint32_t)(aidx * a.nc);
-            const uint64_t da = smem_desc(a0 + kk * 32), db = smem_desc(b0 + kk * 32);
-            const uint32_t acc = first ? 0u : 1u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
-                "l"(da), "l"(db), "r"(idesc), "r"(acc));
+        for (int li = 0; li < niter; ++li) {
+          const int g = it * niter + li;
+          const int s = g % kTcStages;
+          const uint32_t ph = (uint32_t)(g / kTcStages) & 1u;
+          if (!mbar_wait(&full_bar[s], ph)) { atomicExch(&fail_s, 1); break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = smem_u32(smem + (size_t)s * S_BYTES);
+          // level products G0 Y0 (leading accumulator), G0 Y1 and G1 Y0 (corrections)
+  #pragma unroll
+          for (int pass = 0; pass < 3; ++pass) {
+            const uint32_t a0 = st + (pass == 2 ? A_BYTES : 0u);
+            const uint32_t b0 = st + 2 * A_BYTES + (pass == 1 ? B_BYTES : 0u);
+  #pragma unroll
+            for (int kk = 0; kk < UK / 16; ++kk) {
+              const int aidx = (pass == 0) ? 0 : 1;
+              const bool first = (li == 0) && (kk == 0) && (pass <= 1);
+              const uint32_t dst = tmem + (uint32_t)(aidx * a.nc);
+              const uint64_t da = smem_desc(a0 + kk * 32), db = smem_desc(b0 + kk * 32);
+              const uint32_t acc = first ? 0u : 1u;
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
+                  "l"(da), "l"(db), "r"(idesc), "r"(acc));
+            }
           }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&empty_bar[s]))
+                       : "memory");
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&empty_bar[s]))
+                         smem_u32(&done_bar))
                      : "memory");
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&done_bar))
-                   : "memory");
+      __syncwarp();
+      // the row block's K-split products of this iteration are all written once
+      // the epilogue warps (4-7) pass barrier 2: this CTA arrives (release) and
+      // waits (acquire, bounded) for the row block's other CTAs; no other row
+      // block takes part
+      asm volatile("bar.sync 2, 160;" ::: "memory");
+      if (lane == 0) {
+        if (fail_s) set_status(a.status, AS_ETIMEOUT);
+        red_release_add_u32(a.rbcnt + rb, 1u);
+        rb_ok_s = wait_flag_ge(a.rbcnt + rb, (unsigned)(it + 1) * (unsigned)a.nks, a.status) ? 1 : 0;
+      }
     } else if (warp >= 2) {
+      if (warp >= 4) {
+        // epilogue: warps 4-7 (TMEM lane quarters 0-3) move the 128 x nc block,
+        // both accumulators summed, to part[ks]; the MMAs are waited for even
+        // after a failure, so none is in flight when the TMEM is freed
+        const int wq = warp - 4;
+        bool have = niter > 0 && mbar_wait(&done_bar, (uint32_t)it & 1u);
+        if (niter > 0 && !have) atomicExch(&fail_s, 1);
+        if (fail_s) have = false;
+        have = __all_sync(0xffffffffu, have);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int row = rb * UM + wq * 32 + lane;
+        float* o = part + (size_t)ks * a.pplane + (size_t)row * a.nc;
+        const uint32_t trow = tmem + ((uint32_t)(wq * 32) << 16);
+        // 32 columns of both accumulators per wait (nc is a multiple of 16)
+        for (int c0 = 0; c0 < a.nc && niter > 0; c0 += 32) {
+          const bool two = c0 + 16 < a.nc;   // warp-uniform
+          uint32_t r[4][16];
+          if (have) {
+            tmem_ld16(trow + (uint32_t)c0, r[0]);
+            tmem_ld16(trow + (uint32_t)(c0 + a.nc), r[1]);
+            if (two) {
+              tmem_ld16(trow + (uint32_t)(c0 + 16), r[2]);
+              tmem_ld16(trow + (uint32_t)(c0 + 16 + a.nc), r[3]);
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          }
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !two) break;
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              v[j] = have ? __uint_as_float(r[2 * h][j]) + __uint_as_float(r[2 * h + 1][j]) : 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+              __stcg(reinterpret_cast<float4*>(o + c0 + 16 * h + j), make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]));
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("bar.sync 2, 160;" ::: "memory");   // with warp 1: the product is written
+      }
       // coefficients C_it of the active pairs from every CTA's partial sums of Y_it
       constexpr int kCT = kTcThreads - 64;
       const int ct = tid - 64;
@@ -369,159 +424,114 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
         }
       }
     }
-    __syncwarp();
-    // epilogue: warps 0-3 move the 128 x nc block (both accumulators summed) to part[ks]
-    if (warp < 4 && niter > 0) {
-      // wait for the MMAs even after a failure, so none is in flight when the TMEM is freed
-      bool have = mbar_wait(&done_bar, (uint32_t)it & 1u);
-      if (!have) atomicExch(&fail_s, 1);
-      if (fail_s) have = false;
-      have = __all_sync(0xffffffffu, have);
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int row = rb * UM + warp * 32 + lane;
-      float* o = part + (size_t)ks * a.pplane + (size_t)row * a.nc;
-      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-      // 32 columns of both accumulators per wait (nc is a multiple of 16)
-      for (int c0 = 0; c0 < a.nc; c0 += 32) {
-        const bool two = c0 + 16 < a.nc;   // warp-uniform
-        uint32_t r[4][16];
-        if (have) {
-          tmem_ld16(trow + (uint32_t)c0, r[0]);
-          tmem_ld16(trow + (uint32_t)(c0 + a.nc), r[1]);
-          if (two) {
-            tmem_ld16(trow + (uint32_t)(c0 + 16), r[2]);
-            tmem_ld16(trow + (uint32_t)(c0 + 16 + a.nc), r[3]);
-          }
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h == 1 && !two) break;
-          float v[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            v[j] = have ? __uint_as_float(r[2 * h][j]) + __uint_as_float(r[2 * h + 1][j]) : 0.f;
-#pragma unroll
-          for (int j = 0; j < 16; j += 4)
-            __stcg(reinterpret_cast<float4*>(o + c0 + 16 * h + j), make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]));
-        }
-      }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    // the row block's K-split products of this iteration are all written: each
-    // CTA of the row block arrives once (release) and waits for the others
-    // (acquire, bounded); no other row block takes part
-    {
-      __shared__ int rb_ok;
-      if (tid == 0) {
-        if (fail_s) set_status(a.status, AS_ETIMEOUT);
-        red_release_add_u32(a.rbcnt + rb, 1u);
-        rb_ok = wait_flag_ge(a.rbcnt + rb, (unsigned)(it + 1) * (unsigned)a.nks, a.status) ? 1 : 0;
-      }
-      __syncthreads();
-      if (!rb_ok) { alive = false; break; }
-    }
+    __syncthreads();   // coefficients, the row block's products and rb_ok_s
+    if (!rb_ok_s) { alive = false; break; }
 
     // ---- reduction phase: rows [rw0, rw1) of row block rb of Y_{it+1} = Z C_it ----
+    // A group of lpp lanes (a half warp for up to 16 rows, else a warp) takes
+    // one column pair, one row per lane: the K-split planes of its row are
+    // summed in the order k = 0, 1, ..., the row of Y_{it+1} is written in FP32
+    // and BF16 levels (consecutive lanes, consecutive rows: coalesced), and the
+    // pair's partial sums are reduced across the group.  The loads of two
+    // steps are issued before either step's arithmetic.
     const int rw0 = rb * UM + ks * a.rpb, rw1 = min(rb * UM + UM, rw0 + a.rpb);
     const int R = max(0, rw1 - rw0);
-    const int c0a = 2 * pa0, nca = 2 * nact;
-    {
-      // every load of kRedElems elements (all their K-split planes) is issued
-      // before the sums that use them: one L2 round trip per batch instead of
-      // one per element; the planes are still summed in the order k = 0, 1, ...
-      // (the zeros past nks leave each sum unchanged)
-      const int total = R * nca;
-      for (int e0 = tid; e0 < total; e0 += kTcThreads * kRedElems) {
-        float buf[kRedElems][kTcMaxSplits];
+    const int lpp = (R <= 16) ? 16 : 32;
+    const int sub = (lpp == 16) ? (lane >> 4) : 0, rl = lane & (lpp - 1);
+    const int pstep = kTcThreads / lpp;   // pairs per step (all warps)
+    const int row = rw0 + rl;
+    const bool row_on = rl < R;
+    const bool in_y = row < a.ldy;        // rows past the FP32 columns are zero (>= m_t)
+    for (int pb0 = 0; pb0 < nact; pb0 += 2 * pstep) {
+      float2 zz[2][kTcMaxSplits];
 #pragma unroll
-        for (int q = 0; q < kRedElems; ++q) {
-          const int e = e0 + q * kTcThreads;
-          const bool on = e < total;
-          const int r = on ? e / nca : 0, cl = on ? e - r * nca : 0;
-          const float* pp = part + (size_t)(rw0 + r) * a.nc + c0a + cl;
+      for (int h = 0; h < 2; ++h) {
+        const int pl = pb0 + h * pstep + warp * (32 / lpp) + sub;
+        const bool on = pl < nact && row_on;
+        const float* pp = part + (size_t)row * a.nc + 2 * (pa0 + pl);
 #pragma unroll
-          for (int k = 0; k < kTcMaxSplits; ++k)
-            buf[q][k] = (on && k < a.nks) ? __ldcg(pp + (size_t)k * a.pplane) : 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < kRedElems; ++q) {
-          const int e = e0 + q * kTcThreads;
-          if (e < total) {
-            float z = 0.f;
-#pragma unroll
-            for (int k = 0; k < kTcMaxSplits; ++k) z += buf[q][k];
-            zs[e] = z;   // e = r * nca + cl
-          }
-        }
+        for (int k = 0; k < kTcMaxSplits; ++k)
+          zz[h][k] = (on && k < a.nks) ? __ldcg(reinterpret_cast<const float2*>(pp + (size_t)k * a.pplane))
+                                       : make_float2(0.f, 0.f);
       }
-    }
-    __syncthreads();
-    if (tid < nact) {
-      const int p = pa0 + tid;
-      const bool si = p >= a.npi;
-      const bool fin = si ? (it == a.q) : (it == a.k_pi);
-      const float4 cf = coef[p];
-      const int ca = 2 * p, cb = 2 * p + 1;
-      const int ma = tc_col_rows(a, ca), mb = tc_col_rows(a, cb);
-      float ps[kTcSlots] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (int r = 0; r < R; ++r) {
-        const int row = rw0 + r;
-        const float za = zs[r * nca + 2 * tid], zb = zs[r * nca + 2 * tid + 1];
-        const float y0 = (row < ma) ? fmaf(cf.x, za, cf.y * zb) : 0.f;
-        const float y1 = (row < mb) ? fmaf(cf.z, za, cf.w * zb) : 0.f;
-        const bool in_y = row < a.ldy;   // rows past the FP32 columns are zero (>= m_t)
-        if (in_y) {
-          Ynew[(size_t)ca * a.ldy + row] = y0;
-          Ynew[(size_t)cb * a.ldy + row] = y1;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int pl = pb0 + h * pstep + warp * (32 / lpp) + sub;
+        const bool pon = pl < nact;
+        const bool on = pon && row_on;
+        const int p = pa0 + (pon ? pl : 0);
+        float za = 0.f, zb = 0.f;
+#pragma unroll
+        for (int k = 0; k < kTcMaxSplits; ++k) {
+          za += zz[h][k].x;
+          zb += zz[h][k].y;
         }
-        __nv_bfloat16 l0, l1, l2;
-        split_levels(y0, l0, l1, l2);
-        __nv_bfloat16* ya = a.Yb + (size_t)bnew * a.ybbuf + (size_t)ca * a.ldyb + row;
-        ya[0] = l0;
-        ya[a.yblevel] = l1;
-        ya[2 * a.yblevel] = l2;
-        split_levels(y1, l0, l1, l2);
-        __nv_bfloat16* yb = ya + a.ldyb;
-        yb[0] = l0;
-        yb[a.yblevel] = l1;
-        yb[2 * a.yblevel] = l2;
-        if (!fin) {
-          ps[0] = fmaf(y0, y0, ps[0]);
-          if (si) {
-            ps[1] = fmaf(y0, y1, ps[1]);
-            ps[2] = fmaf(y1, y1, ps[2]);
-          } else {
-            ps[1] = fmaf(y1, y1, ps[1]);
+        const bool si = p >= a.npi;
+        const bool fin = si ? (it == a.q) : (it == a.k_pi);
+        const float4 cf = coef[p];
+        const int ca = 2 * p, cb = 2 * p + 1;
+        const int ma = tc_col_rows(a, ca), mb = tc_col_rows(a, cb);
+        const float y0 = (on && row < ma) ? fmaf(cf.x, za, cf.y * zb) : 0.f;
+        const float y1 = (on && row < mb) ? fmaf(cf.z, za, cf.w * zb) : 0.f;
+        float ps[kTcSlots] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (on) {
+          if (in_y) {
+            Ynew[(size_t)ca * a.ldy + row] = y0;
+            Ynew[(size_t)cb * a.ldy + row] = y1;
           }
-        } else {
-          // x = Y_it C_it (the normalised iterate), y = G x
-          const float ya0 = in_y ? __ldcg(Yold + (size_t)ca * a.ldy + row) : 0.f;
-          const float yb0 = in_y ? __ldcg(Yold + (size_t)cb * a.ldy + row) : 0.f;
-          const float x0 = fmaf(cf.x, ya0, cf.y * yb0), x1 = fmaf(cf.z, ya0, cf.w * yb0);
-          if (!si) {
-            ps[0] = fmaf(x0, y0, ps[0]);
-            ps[1] = fmaf(x1, y1, ps[1]);
+          __nv_bfloat16 l0, l1, l2;
+          split_levels(y0, l0, l1, l2);
+          __nv_bfloat16* ya = a.Yb + (size_t)bnew * a.ybbuf + (size_t)ca * a.ldyb + row;
+          ya[0] = l0;
+          ya[a.yblevel] = l1;
+          ya[2 * a.yblevel] = l2;
+          split_levels(y1, l0, l1, l2);
+          __nv_bfloat16* yb = ya + a.ldyb;
+          yb[0] = l0;
+          yb[a.yblevel] = l1;
+          yb[2 * a.yblevel] = l2;
+          if (!fin) {
+            ps[0] = y0 * y0;
+            if (si) {
+              ps[1] = y0 * y1;
+              ps[2] = y1 * y1;
+            } else {
+              ps[1] = y1 * y1;
+            }
           } else {
-            ps[0] = fmaf(x0, y0, ps[0]);
-            ps[1] = fmaf(0.5f, fmaf(x0, y1, x1 * y0), ps[1]);
-            ps[2] = fmaf(x1, y1, ps[2]);
-            ps[3] = fmaf(y0, y0, ps[3]);
-            ps[4] = fmaf(y0, y1, ps[4]);
-            ps[5] = fmaf(y1, y1, ps[5]);
-            if (row < a.ldx) {
-              a.X[(size_t)ca * a.ldx + row] = x0;
-              a.X[(size_t)cb * a.ldx + row] = x1;
+            // x = Y_it C_it (the normalised iterate), y = G x
+            const float ya0 = in_y ? __ldcg(Yold + (size_t)ca * a.ldy + row) : 0.f;
+            const float yb0 = in_y ? __ldcg(Yold + (size_t)cb * a.ldy + row) : 0.f;
+            const float x0 = fmaf(cf.x, ya0, cf.y * yb0), x1 = fmaf(cf.z, ya0, cf.w * yb0);
+            if (!si) {
+              ps[0] = x0 * y0;
+              ps[1] = x1 * y1;
+            } else {
+              ps[0] = x0 * y0;
+              ps[1] = 0.5f * fmaf(x0, y1, x1 * y0);
+              ps[2] = x1 * y1;
+              ps[3] = y0 * y0;
+              ps[4] = y0 * y1;
+              ps[5] = y1 * y1;
+              if (row < a.ldx) {
+                a.X[(size_t)ca * a.ldx + row] = x0;
+                a.X[(size_t)cb * a.ldx + row] = x1;
+              }
             }
           }
         }
-      }
+        // the pair's partial sums over its rows (every lane takes part)
 #pragma unroll
-      for (int e = 0; e < kTcSlots; ++e) snew[(size_t)(p * kTcSlots + e) * G + blk] = ps[e];
+        for (int e = 0; e < kTcSlots; ++e)
+          for (int o = lpp >> 1; o > 0; o >>= 1) ps[e] += __shfl_xor_sync(0xffffffffu, ps[e], o);
+        if (pon && rl == 0) {
+#pragma unroll
+          for (int e = 0; e < kTcSlots; ++e) snew[(size_t)(p * kTcSlots + e) * G + blk] = ps[e];
+        }
+      }
     }
     asm volatile("fence.proxy.async.global;" ::: "memory");   // the BF16 levels feed other CTAs' TMA loads
-    __syncthreads();   // also: the ring (zs) is free for the next product
+    __syncthreads();
     if (tid == 0) st_release_u32(a.flags + blk, (unsigned)(it + 1));
   }
   // the pairs whose last product was the final iteration
@@ -616,16 +626,13 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
   std::unique_lock<std::mutex> lk(g_tcdev_mu);
   TcDevice& td = g_tcdev[dev];
   if (td.sms == 0) AS_CUDA_TRY(cudaDeviceGetAttribute(&td.sms, cudaDevAttrMultiProcessorCount, dev));
-  // K range per CTA: as short as the co-resident grid (one CTA per SM) allows
+  // K range per CTA: by default as short as the co-resident grid (one CTA per
+  // SM) allows; the autotuner may take two or four times fewer K splits
+  // (fewer partial planes to reduce, more MMA work per CTA)
   const int nrb = kpad / 128;
   const long long need = ((long long)kpad * kpad + 128LL * td.sms - 1) / (128LL * td.sms);
-  int kc = (int)std::max<long long>(64, (need + 63) / 64 * 64);
-  const int nks = (kpad + kc - 1) / kc;
-  kc = (kpad + nks - 1) / nks;
-  kc = (kc + 63) / 64 * 64;
-  const int ncta = nrb * nks;
-  const int rpb = (UM + nks - 1) / nks;   // rows of its own row block that each CTA reduces
-  if (nks > kTcMaxSplits || ncta > td.sms || rpb > kTcMaxRpc) return AS_OK;
+  const int kc0 = (int)std::max<long long>(64, (need + 63) / 64 * 64);
+  const int nks0 = (kpad + kc0 - 1) / kc0;
   const size_t smem = 1024 + (size_t)kTcStages * 2 * (UM * UK * 2 + (size_t)nc * UK * 2);
   const int v = 0;
   const void* fn = (const void*)batch_tc_kernel<3>;
@@ -635,49 +642,87 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
   }
   int per = 0;
   AS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kTcThreads, smem));
-  if (per < 1 || (long long)per * td.sms < ncta) return AS_OK;
+  const int sms = td.sms;
   lk.unlock();
+  // the split shape of a candidate K-split count: (kc, nks) with kc a multiple
+  // of 64, or nks = 0 when the shape does not fit
+  auto shape = [&](int want, int* kc_out) -> int {
+    if (want < 1) return 0;
+    int kc = (kpad + want - 1) / want;
+    kc = (kc + 63) / 64 * 64;
+    const int nks = (kpad + kc - 1) / kc;
+    const int rpb = (UM + nks - 1) / nks;
+    if (nks > kTcMaxSplits || rpb > kTcMaxRpc || nrb * nks > sms || per < 1 || (long long)per * sms < nrb * nks)
+      return 0;
+    *kc_out = kc;
+    return nks;
+  };
+  int choices[3], nch = 0;
+  for (int f = 1; f <= 4; f *= 2) {
+    int kc = 0;
+    const int nks = shape((nks0 + f - 1) / f, &kc);
+    bool dup = false;
+    for (int c = 0; c < nch; ++c) dup = dup || choices[c] == nks;
+    if (nks > 0 && !dup) choices[nch++] = nks;
+  }
+  if (nch == 0) return AS_OK;
   // the BF16 levels of the batch vectors: two buffers of ycols columns per level
   UmmaOperand mY{};
   for (int l = 0; l < 3; ++l) {
     as_status st = umma_make_map(&mY.m[l], tb.Yb + (size_t)l * tb.yblevel, 2 * (int)pb.ycols, tb.ldyb, tb.ldyb, nc);
     if (st != AS_OK) return st;
   }
-  if (prof) prof->begin(PK_BATCH_ORTH, s);
-  launch_persist_fill(s, pb, mmax, nb, npi, r0, key, i0);
-  tc_split_start_kernel<<<ncols, 256, 0, s>>>(pb.Y + pb.ybuf, pb.ldy, mmax, ncols, kpad,
-                                              tb.Yb + (size_t)pb.ycols * tb.ldyb, tb.yblevel, tb.ldyb);
-  count_launches(1);
-  AS_CUDA_TRY(cudaGetLastError());
-  if (prof) prof->end(PK_BATCH_ORTH, s, 0.0, 12.0 * mmax * (double)nb);
   unsigned* flags = reinterpret_cast<unsigned*>(tb.part + batch_tc_part_floats(n2, (int)pb.ycols) - 512);
-  AS_CUDA_TRY(cudaMemsetAsync(flags, 0, 512 * sizeof(unsigned), s));   // CTA flags and row-block counters
-  TcArgs a{};
-  a.Y = pb.Y; a.ybuf = pb.ybuf; a.ldy = pb.ldy;
-  a.Yb = tb.Yb; a.yblevel = tb.yblevel; a.ybbuf = (long long)pb.ycols * tb.ldyb; a.ldyb = tb.ldyb;
-  a.ycols = (int)pb.ycols;
-  a.X = pb.X; a.ldx = n2;
-  a.part = tb.part; a.pplane = (long long)kpad * nc;
-  a.sums = pb.part; a.sbuf = (long long)kTcSlots * P * ncta;
-  a.flags = flags; a.rbcnt = flags + 256; a.status = status;
-  a.nb = nb; a.npi = npi; a.r0 = r0; a.k_pi = k_pi; a.q = q; a.mmax = mmax;
-  a.kpad = kpad; a.nrb = nrb; a.nks = nks; a.kc = kc; a.nc = nc; a.rpb = rpb;
-  a.sig2 = pb.sig2; a.ritz = pb.ritz;
-  void* args[] = {&a, (void*)&tb.mG, &mY};
-  if (prof) prof->begin(PK_BATCH_TC, s);
-  AS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(ncta), dim3(kTcThreads), args, smem, s));
-  count_launches(1);
-  if (prof) {
-    double m2 = 0.0, m1 = 0.0;
-    for (int t = 0; t < nb; ++t) {
-      const double m = (double)(r0 + t + 1);
-      m2 += m * m;
-      m1 += m;
+  // one launch of the block with nks K splits: starting vectors, then the kernel
+  auto run = [&](int want) -> as_status {
+    int kc = 0;
+    const int nks = shape(want, &kc);
+    if (nks == 0) return AS_ENOTSUP;
+    const int ncta = nrb * nks, rpb = (UM + nks - 1) / nks;
+    if (prof) prof->begin(PK_BATCH_ORTH, s);
+    launch_persist_fill(s, pb, mmax, nb, npi, r0, key, i0);
+    tc_split_start_kernel<<<ncols, 256, 0, s>>>(pb.Y + pb.ybuf, pb.ldy, mmax, ncols, kpad,
+                                                tb.Yb + (size_t)pb.ycols * tb.ldyb, tb.yblevel, tb.ldyb);
+    count_launches(1);
+    AS_CUDA_TRY(cudaGetLastError());
+    if (prof) prof->end(PK_BATCH_ORTH, s, 0.0, 12.0 * mmax * (double)nb);
+    AS_CUDA_TRY(cudaMemsetAsync(flags, 0, 512 * sizeof(unsigned), s));   // CTA flags and row-block counters
+    TcArgs a{};
+    a.Y = pb.Y; a.ybuf = pb.ybuf; a.ldy = pb.ldy;
+    a.Yb = tb.Yb; a.yblevel = tb.yblevel; a.ybbuf = (long long)pb.ycols * tb.ldyb; a.ldyb = tb.ldyb;
+    a.ycols = (int)pb.ycols;
+    a.X = pb.X; a.ldx = n2;
+    a.part = tb.part; a.pplane = (long long)kpad * nc;
+    a.sums = pb.part; a.sbuf = (long long)kTcSlots * P * ncta;
+    a.flags = flags; a.rbcnt = flags + 256; a.status = status;
+    a.nb = nb; a.npi = npi; a.r0 = r0; a.k_pi = k_pi; a.q = q; a.mmax = mmax;
+    a.kpad = kpad; a.nrb = nrb; a.nks = nks; a.kc = kc; a.nc = nc; a.rpb = rpb;
+    a.sig2 = pb.sig2; a.ritz = pb.ritz;
+    void* args[] = {&a, (void*)&tb.mG, &mY};
+    if (prof) prof->begin(PK_BATCH_TC, s);
+    AS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(ncta), dim3(kTcThreads), args, smem, s));
+    count_launches(1);
+    if (prof) {
+      double m2 = 0.0, m1 = 0.0;
+      for (int t = 0; t < nb; ++t) {
+        const double m = (double)(r0 + t + 1);
+        m2 += m * m;
+        m1 += m;
+      }
+      const double prods = (double)(k_pi + 1) + 2.0 * (double)(q + 1);
+      // the algorithmic work of the block is recorded when its decisions are
+      // taken (add_work); here the work issued for every row of the block
+      prof->end(PK_BATCH_TC, s, 0.0, 2.0 * npass / 3.0 * (double)kpad * kpad + 8.0 * m1 * prods, 2.0 * m2 * prods);
     }
-    const double prods = (double)(k_pi + 1) + 2.0 * (double)(q + 1);
-    // the algorithmic work of the block is recorded when its decisions are
-    // taken (add_work); here the work issued for every row of the block
-    prof->end(PK_BATCH_TC, s, 0.0, 2.0 * npass / 3.0 * (double)kpad * kpad + 8.0 * m1 * prods, 2.0 * m2 * prods);
+    return AS_OK;
+  };
+  as_status st = AS_OK;
+  bool ran = false;
+  const int nks = tune_pick(s, "batch_tc_nks", kpad, choices, nch, run, &st, &ran);
+  if (st != AS_OK) return st;
+  if (!ran) {
+    st = run(nks);
+    if (st != AS_OK) return st;
   }
   *used = true;
   return AS_OK;

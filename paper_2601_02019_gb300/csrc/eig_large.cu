@@ -53,11 +53,10 @@ __global__ void tri_norm(int n, TriWork w, double* out2) {
   if (threadIdx.x == 0) { out2[0] = tn; out2[1] = 2.2250738585072014e-308 * fmax(1.0, em); }
 }
 
-// Lanes per eigenvalue of the multisection: kBisLanes - 1 interior points per
-// round narrow the bracket kBisLanes-fold.  Measured on the FD shrink's
-// 2048 x 2048 Gram: 8 lanes beat both 4 (more rounds) and 32 (more Sturm
-// counts per bit).
-constexpr int kBisLanes = 8;
+// Lanes per eigenvalue of the multisection: LANES - 1 interior points per
+// round narrow the bracket LANES-fold.  More lanes mean fewer dependent
+// rounds but more Sturm counts per bit; the launcher lets the autotuner pick
+// 4, 8, 16 or 32 per matrix order (8 when tuning is off).
 
 // Modified Gram-Schmidt inside clusters of close eigenvalues (one block).
 __global__ void cluster_mgs(int n, int nev, const double* norms, const double* evals, double* X, int ldx) {
@@ -137,6 +136,7 @@ __device__ int sturm_count_df(int n, const df64* dd, const df64* e2, df64 x, flo
 // eigenvalue), then inverse iteration in FP64 by the group's first lane.  The
 // bracket is kept in FP64; evaluation points are rounded to df64.  Stops at a
 // width of 2^-44 of ||T|| (df64 resolution).
+template <int kBisLanes>
 __global__ void bisect_df(int n, int nev, const double* norms, const df64* dd, const df64* e2, double* evals) {
   const int lane = threadIdx.x & 31;
   const int g = lane & (kBisLanes - 1), grp = lane / kBisLanes;
@@ -780,9 +780,28 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
   tri_norm<<<1, 256, 0, s>>>(n, w, norms); count_launches(1);
   tri_scale_df<<<(n + 255) / 256, 256, 0, s>>>(n, w, norms, dd, e2); count_launches(1);
   {
-    const int per_block = (128 / 32) * (32 / kBisLanes);   // eigenvalues per block of 128 threads
-    bisect_df<<<(nev + per_block - 1) / per_block, 128, 0, s>>>(n, nev, norms, dd, e2, evals);
-    count_launches(1);
+    // multisection lanes per eigenvalue, tuned per matrix order
+    auto bisect = [&](int lanes) -> as_status {
+      const int per_block = (128 / 32) * (32 / lanes);   // eigenvalues per block of 128 threads
+      const int nblk = (nev + per_block - 1) / per_block;
+      if (lanes == 4) bisect_df<4><<<nblk, 128, 0, s>>>(n, nev, norms, dd, e2, evals);
+      else if (lanes == 16) bisect_df<16><<<nblk, 128, 0, s>>>(n, nev, norms, dd, e2, evals);
+      else if (lanes == 32) bisect_df<32><<<nblk, 128, 0, s>>>(n, nev, norms, dd, e2, evals);
+      else bisect_df<8><<<nblk, 128, 0, s>>>(n, nev, norms, dd, e2, evals);
+      count_launches(1);
+      AS_CUDA_TRY(cudaGetLastError());
+      return AS_OK;
+    };
+    static const int kLaneChoices[4] = {8, 4, 16, 32};
+    as_status tst = AS_OK;
+    bool ran = false;
+    const int lanes = tune_pick(s, "bisect_df", ((long long)n << 20) | (long long)nev, kLaneChoices, 4, bisect,
+                                &tst, &ran);
+    if (tst != AS_OK) return tst;
+    if (!ran) {
+      tst = bisect(lanes);
+      if (tst != AS_OK) return tst;
+    }
     invit_df<<<(nev + 31) / 32, 32, 0, s>>>(n, nev, w, norms, evals, X, ldx, lu);
     count_launches(1);
   }

@@ -258,6 +258,13 @@ as_status launch_lr_colscale(cudaStream_t s, double* U, int n, int ldu, const do
 as_status launch_lr_rowscale(cudaStream_t s, const double* W, int n, double* P, int m);
 as_status launch_lr_lambda(cudaStream_t s, const double* mu, int lp, int ell, double* lam_out);
 
+// Launch-shape autotuner (tune.cu): the fastest of `choices` for (device,
+// kernel, key), timed on the first call's inputs by running run(choice); the
+// choice is cached per key.  *ran = true when run(result) already produced
+// this call's outputs.  AS_TUNE=0 in the environment returns choices[0].
+int tune_pick(cudaStream_t s, const char* kernel, long long key, const int* choices, int n,
+              const std::function<as_status(int)>& run, as_status* st, bool* ran);
+
 // Library-internal access to a sketch for the runtimes built on sketches
 // (engine.cu): stream, rows fed, the snapshot queue's times (the sketch's own
 // row indices), the windowed query Gram, raw-row Grams, dropping the oldest
