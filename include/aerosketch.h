@@ -343,16 +343,17 @@ as_status sketch_reserve(as_sketch* h, int64_t snapshot_rank);
 as_status sketch_update_many(as_sketch* const* hs, const float* const* rows, const int64_t* n, const int64_t* ld,
                              int32_t count);
 
-/* The same update in lockstep blocks with the sketches' batched iterations in
- * shared launches: each step launches one block of every sketch (on its own
- * stream), runs their FP32 batched iterations (the power iteration and first
- * simultaneous-iteration step of every row) in one cooperative launch per set
- * of sketches whose tiles fit the GPU at once (as_stats.grouped_batches counts
- * them), then takes every block's decisions on the worker threads.  Each
- * sketch's results are bitwise those of sketch_update on its rows.  Arguments,
- * ordering and errors as sketch_update_many.  Every step waits for the slowest
- * block, so with frequent event rows sketch_update_many can be faster (16
- * sketches, d = 512, l = 64: 42k against 65k rows/s). */
+/* The same update with the sketches' batched iterations in shared launches:
+ * every sketch progresses on a worker thread of its own, as in
+ * sketch_update_many, but a block whose FP32 batched iterations (the power
+ * iteration and first simultaneous-iteration step of every row) are ready is
+ * handed to the device's launch combiner, which runs the pending blocks of all
+ * sketches in one cooperative launch (as_stats.grouped_batches counts them) as
+ * soon as every sketch of the call has a block pending, or 40 us after the
+ * first one arrived.  No sketch waits for another's decisions.  Each sketch's
+ * results are bitwise those of sketch_update on its rows.  Arguments, ordering
+ * and errors as sketch_update_many; all sketches must live on one device
+ * (AS_EINVAL otherwise). */
 as_status sketch_update_grouped(as_sketch* const* hs, const float* const* rows, const int64_t* n, const int64_t* ld,
                                 int32_t count);
 

@@ -362,6 +362,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
         bool ok = true;
         for (int c = ct; c < G && ok; c += kCT) ok = wait_flag_ge(a.flags + c, (unsigned)it, a.status);
         if (!ok) atomicExch(&fail_s, 1);
+        __syncwarp();
         asm volatile("bar.sync 1, %0;" ::"r"(kCT) : "memory");
         // pairs whose last product was the previous iteration: their final values
         tc_finals(a, sold, it - 1, warp, lane, 2, 3);
@@ -424,6 +425,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
         }
       }
     }
+    // a block barrier is executed by converged warps only: warps 0 and 1 may
+    // still be split (lane 0 alone ran the producer or the row-block wait)
+    __syncwarp();
     __syncthreads();   // coefficients, the row block's products and rb_ok_s
     if (!rb_ok_s) { alive = false; break; }
 
@@ -531,6 +535,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
       }
     }
     asm volatile("fence.proxy.async.global;" ::: "memory");   // the BF16 levels feed other CTAs' TMA loads
+    __syncwarp();
     __syncthreads();
     if (tid == 0) st_release_u32(a.flags + blk, (unsigned)(it + 1));
   }
@@ -538,13 +543,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
   if (alive) {
     __shared__ int ok_s;
     if (tid == 0) ok_s = 1;
+    __syncwarp();
     __syncthreads();
     for (int c = tid; c < G; c += kTcThreads)
       if (!wait_flag_ge(a.flags + c, (unsigned)(iters + 1), a.status)) ok_s = 0;
+    __syncwarp();
     __syncthreads();
     if (ok_s) tc_finals(a, a.sums + (size_t)(iters & 1) * a.sbuf, iters, warp, lane, 0, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncwarp();
   __syncthreads();
   if (warp == 2) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }

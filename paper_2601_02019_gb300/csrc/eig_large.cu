@@ -471,6 +471,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
         const df64 pj = pin[j];
         wk[j] = df_sub(df64{2.f * pj.hi, 2.f * pj.lo}, df_mul(c2, vcur[j]));
       }
+      __syncwarp();
       __syncthreads();
     }
     const df64 vr = upd ? vcur[r] : df64{0.f, 0.f};
@@ -500,6 +501,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
     // the warps' sums in the same order
     acc = df_warp_sum(acc);
     if (lane == 0) red[warp] = acc;
+    __syncwarp();
     __syncthreads();
     df64 s = red[0];
 #pragma unroll
@@ -536,6 +538,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
     for (int j = r + tid + kTriThreads * kTriPre; j < n; j += blockDim.x)
       vnew[j] = house_v_df(vnew[j], j == r + 1, szero, alpha, rvn);
     if (blockIdx.x == 0 && tid == 0) t.e[r] = df_to_double(alpha);
+    __syncwarp();
     __syncthreads();
     // rows i >= r+1 of this warp: update with (v_{r-1}, w_{r-1}), dot with v_r
     df64* pout = (r & 1) ? t.p[1] : t.p[0];

@@ -13,8 +13,11 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <new>
 #include <unordered_map>
 #include <vector>
@@ -189,6 +192,7 @@ struct as_sketch {
   bool tcb = false;         // tcgen05 form of the batched iterations (tensor forms, 2l >= 256)
   TcBatchBuffers tb{};
   int gf_valid = 0;         // leading rows/columns of Gf that equal G (FP32-rounded)
+  cudaEvent_t comb_ev = nullptr;   // a deferred block's launch phase is done (launch combiner)
 };
 
 namespace {
@@ -210,6 +214,7 @@ void free_all(as_sketch* h) {
   for (__nv_bfloat16* p : bp) if (p) cudaFree(p);
   if (h->tb.part) cudaFree(h->tb.part);
   if (h->h_buf) cudaFreeHost(h->h_buf);
+  if (h->comb_ev) cudaEventDestroy(h->comb_ev);
   delete h->prof;
   h->prof = nullptr;
 }
@@ -771,10 +776,171 @@ as_status block_finish(as_sketch* h, const BlockCtx& c, int64_t* used, bool* bad
   return st;
 }
 
-as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t* used, bool* bad_row) {
+// ---- launch combiner: the FP32 batched iterations of many sketches --------
+// Sketches updated together progress independently, each on its own host
+// thread and stream; a block whose batched iterations would run the FP32
+// persistent kernel hands its job to the device's combiner instead.  The
+// combiner's thread launches whichever jobs are pending as one grouped
+// cooperative launch (launch_batch_group): as soon as every sketch of the
+// update has a job pending, or kCombineWindow after the first job arrived,
+// whichever is earlier.  No sketch waits for another's decision phase (the
+// lockstep of earlier builds made every step wait for the slowest sketch's
+// event rows).  Each job's result equals that of its own launch, so a
+// sketch's results do not depend on the groups it landed in.
+constexpr auto kCombineWindow = std::chrono::microseconds(40);
+
+struct CombineReq {
+  BatchJob job;
+  as_sketch* h = nullptr;
+  bool done = false;
+  as_status st = AS_OK;
+};
+
+class Combiner {
+ public:
+  explicit Combiner(int dev) : dev_(dev) {}
+  as_status start() {
+    AS_CUDA_TRY(cudaSetDevice(dev_));
+    AS_CUDA_TRY(cudaStreamCreateWithFlags(&gs_, cudaStreamNonBlocking));
+    AS_CUDA_TRY(cudaEventCreateWithFlags(&gev_, cudaEventDisableTiming));
+    as_status st = dalloc(&cnt_, 1);
+    if (st != AS_OK) return st;
+    cap_ = batch_group_capacity();
+    th_ = std::thread([this] { loop(); });
+    th_.detach();   // lives for the whole process, like the worker pool
+    return AS_OK;
+  }
+  void enter() {
+    std::lock_guard<std::mutex> lk(mu_);
+    ++active_;
+  }
+  void leave() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      --active_;
+    }
+    cv_.notify_all();
+  }
+  as_status submit(CombineReq* r) {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      if (pending_.empty()) first_ = std::chrono::steady_clock::now();
+      pending_.push_back(r);
+    }
+    cv_.notify_all();
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return r->done; });
+    return r->st;
+  }
+
+ private:
+  void loop() {
+    cudaSetDevice(dev_);
+    std::vector<CombineReq*> batch;
+    std::vector<BatchJob> jobs;
+    for (;;) {
+      batch.clear();
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return !pending_.empty(); });
+        cv_.wait_until(lk, first_ + kCombineWindow, [&] { return (int)pending_.size() >= active_; });
+        int tiles = 0;
+        size_t k = 0;
+        for (; k < pending_.size() && batch.size() < 32; ++k) {
+          const int t = batch_group_tiles(pending_[k]->job);
+          if (!batch.empty() && (t <= 0 || tiles + t > cap_)) break;
+          batch.push_back(pending_[k]);
+          tiles += std::max(t, 0);
+          if (t <= 0 || t > cap_) { ++k; break; }   // a job that cannot share a launch goes alone
+        }
+        pending_.erase(pending_.begin(), pending_.begin() + (long)k);
+        if (!pending_.empty()) first_ = std::chrono::steady_clock::now();
+      }
+      launch(batch);
+      {
+        std::lock_guard<std::mutex> lk(mu_);
+        for (CombineReq* r : batch) r->done = true;
+      }
+      done_cv_.notify_all();
+    }
+  }
+  void launch(std::vector<CombineReq*>& batch) {
+    as_status st = AS_ENOTSUP;
+    if (batch.size() > 1) {
+      jobs_.clear();
+      for (CombineReq* r : batch) jobs_.push_back(r->job);
+      cudaError_t e = cudaSuccess;
+      for (CombineReq* r : batch)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(gs_, r->h->comb_ev, 0);
+      st = (e == cudaSuccess) ? launch_batch_group(gs_, jobs_.data(), (int)jobs_.size(), cnt_) : as_from_cuda(e);
+      if (st == AS_OK) {
+        e = cudaEventRecord(gev_, gs_);
+        for (CombineReq* r : batch) {
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(r->h->s, gev_, 0);
+          r->h->st.grouped_batches++;
+        }
+        if (e != cudaSuccess) st = as_from_cuda(e);
+        for (CombineReq* r : batch) r->st = st;
+        return;
+      }
+    }
+    // one job, or a group that did not fit: each job on its own sketch's stream
+    for (CombineReq* r : batch) {
+      const BatchJob& j = r->job;
+      r->st = launch_batch_persist(r->h->s, j.Gf, j.n2, j.r0, j.nb, j.k_pi, j.q, j.key, j.i0, j.pb, j.status,
+                                   r->h->prof);
+    }
+  }
+
+  int dev_;
+  cudaStream_t gs_ = nullptr;
+  cudaEvent_t gev_ = nullptr;
+  unsigned* cnt_ = nullptr;
+  int cap_ = 0;
+  std::thread th_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_cv_;
+  std::vector<CombineReq*> pending_;
+  std::vector<BatchJob> jobs_;
+  std::chrono::steady_clock::time_point first_;
+  int active_ = 0;
+};
+
+std::mutex g_comb_mu;
+std::map<int, Combiner*> g_comb;
+
+// The device's combiner (made on first use; it lives for the whole process).
+as_status combiner_for(int dev, Combiner** out) {
+  std::lock_guard<std::mutex> lk(g_comb_mu);
+  auto it = g_comb.find(dev);
+  if (it != g_comb.end()) {
+    *out = it->second;
+    return AS_OK;
+  }
+  Combiner* c = new (std::nothrow) Combiner(dev);
+  if (!c) return AS_ENOMEM;
+  as_status st = c->start();
+  if (st != AS_OK) return st;   // not kept (its thread did not start)
+  g_comb[dev] = c;
+  *out = c;
+  return AS_OK;
+}
+
+// One block; with a combiner, FP32 batched iterations go through it.
+as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t* used, bool* bad_row,
+                        Combiner* comb = nullptr) {
   BlockCtx c;
-  as_status st = block_prepare(h, src, navail, c, false);
+  as_status st = block_prepare(h, src, navail, c, comb != nullptr);
   if (st != AS_OK) return st;
+  if (c.deferred) {
+    if (!h->comb_ev) AS_CUDA_TRY(cudaEventCreateWithFlags(&h->comb_ev, cudaEventDisableTiming));
+    AS_CUDA_TRY(cudaEventRecord(h->comb_ev, h->s));
+    CombineReq r;
+    r.job = block_job(h, c);
+    r.h = h;
+    st = comb->submit(&r);
+    if (st != AS_OK) return st;
+  }
   return block_finish(h, c, used, bad_row);
 }
 
@@ -1035,221 +1201,6 @@ bool is_device_ptr(const void* p) {
 
 // ---- library-internal access for the runtimes built on sketches (sliding.cu)
 namespace as {
-
-as_status sk_group_update(as_sketch* const* hs, const float* const* rows, const int64_t* n, const int64_t* ld,
-                          int32_t count, as_status* status) {
-  if (count <= 0) return AS_OK;
-  struct Cur {
-    as_sketch* h = nullptr;
-    std::vector<int> ent;                 // entries of this sketch, in list order
-    size_t e = 0;                         // current entry
-    int64_t t0 = 0, nb = 0, done = 0;     // staged chunk [t0, t0 + nb) of the entry, rows consumed
-    const float* base = nullptr;
-    bool active = false;
-    BlockCtx ctx;
-    as_status fst = AS_OK;
-    int64_t used = 0;
-    bool bad = false;
-    std::unique_lock<std::mutex> lk;
-    cudaEvent_t ev = nullptr;
-  };
-  std::vector<Cur> cur;
-  std::unordered_map<const as_sketch*, size_t> at;
-  int dev = -1;
-  for (int32_t k = 0; k < count; ++k) {
-    status[k] = AS_OK;
-    as_sketch* h = hs[k];
-    if (!h || h->mode == AS_COORDINATOR || n[k] < 0 || (n[k] > 0 && (!rows[k] || ld[k] < h->d))) {
-      status[k] = AS_EINVAL;
-      continue;
-    }
-    if (dev < 0) dev = h->dev;
-    if (h->dev != dev) {   // one device per call
-      status[k] = AS_EINVAL;
-      continue;
-    }
-    if (n[k] == 0) continue;
-    auto it = at.find(h);
-    if (it == at.end()) {
-      at.emplace(h, cur.size());
-      cur.emplace_back();
-      cur.back().h = h;
-      cur.back().ent.push_back(k);
-    } else {
-      cur[it->second].ent.push_back(k);
-    }
-  }
-  if (cur.empty()) return AS_OK;
-  AS_CUDA_TRY(cudaSetDevice(dev));
-  for (Cur& c : cur) {
-    c.lk = std::unique_lock<std::mutex>(c.h->mu, std::try_to_lock);
-    if (!c.lk.owns_lock())
-      for (int k : c.ent) status[k] = AS_EBUSY;
-  }
-  cudaStream_t gs = nullptr;
-  cudaEvent_t gev = nullptr;
-  as_status gst = AS_OK;
-  if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&gev, cudaEventDisableTiming) != cudaSuccess) {
-    as_note_cuda_error(cudaGetLastError(), __FILE__, __LINE__);
-    gst = AS_EDEVICE;
-  }
-  for (Cur& c : cur)
-    if (gst == AS_OK && cudaEventCreateWithFlags(&c.ev, cudaEventDisableTiming) != cudaSuccess) {
-      as_note_cuda_error(cudaGetLastError(), __FILE__, __LINE__);
-      gst = AS_EDEVICE;
-    }
-  // stage the next chunk of the cursor's current entry (as sketch_update does)
-  auto stage = [&](Cur& c) -> as_status {
-    for (;;) {
-      if (c.e >= c.ent.size()) {
-        c.active = false;
-        return AS_OK;
-      }
-      const int k = c.ent[c.e];
-      if (status[k] != AS_OK || c.t0 >= n[k]) {
-        ++c.e;
-        c.t0 = 0;
-        continue;
-      }
-      as_sketch* h = c.h;
-      const int64_t nb = std::min<int64_t>(h->stage_rows, n[k] - c.t0);
-      const float* src = rows[k] + c.t0 * ld[k];
-      const float* base = src;
-      if (!is_device_ptr(rows[k])) {
-        AS_CUDA_TRY(cudaMemcpy2DAsync(h->stage, (size_t)h->d * sizeof(float), src, (size_t)ld[k] * sizeof(float),
-                                      (size_t)h->d * sizeof(float), (size_t)nb, cudaMemcpyHostToDevice, h->s));
-        base = h->stage;
-      } else if (ld[k] != h->d) {
-        AS_CUDA_TRY(cudaMemcpy2DAsync(h->stage, (size_t)h->d * sizeof(float), src, (size_t)ld[k] * sizeof(float),
-                                      (size_t)h->d * sizeof(float), (size_t)nb, cudaMemcpyDeviceToDevice, h->s));
-        base = h->stage;
-      }
-      c.base = base;
-      c.nb = nb;
-      c.done = 0;
-      c.active = true;
-      return AS_OK;
-    }
-  };
-  auto fail = [&](Cur& c, as_status st) {   // a device-level failure ends the sketch's remaining entries
-    for (size_t e = c.e; e < c.ent.size(); ++e)
-      if (status[c.ent[e]] == AS_OK) status[c.ent[e]] = st;
-    c.active = false;
-  };
-  for (Cur& c : cur)
-    if (gst == AS_OK && c.lk.owns_lock()) {
-      as_status st = stage(c);
-      if (st != AS_OK) fail(c, st);
-    }
-  const int cap = batch_group_capacity();
-  std::vector<size_t> act;
-  while (gst == AS_OK) {
-    act.clear();
-    for (size_t i = 0; i < cur.size(); ++i)
-      if (cur[i].active) act.push_back(i);
-    if (act.empty()) break;
-    // launch phase of every sketch's next block
-    run_parallel((int)act.size(), [&](int t) {
-      Cur& c = cur[act[(size_t)t]];
-      c.ctx = BlockCtx();
-      c.fst = block_prepare(c.h, c.base + c.done * c.h->d, c.nb - c.done, c.ctx, true);
-    });
-    // the deferred FP32 batched iterations, grouped
-    std::vector<size_t> grp;
-    std::vector<BatchJob> jobs;
-    int tiles = 0;
-    auto flush = [&]() -> as_status {
-      if (jobs.empty()) return AS_OK;
-      as_status st = AS_ENOTSUP;
-      if (jobs.size() > 1) {
-        for (size_t g : grp) {
-          AS_CUDA_TRY(cudaEventRecord(cur[g].ev, cur[g].h->s));
-          AS_CUDA_TRY(cudaStreamWaitEvent(gs, cur[g].ev, 0));
-        }
-        st = launch_batch_group(gs, jobs.data(), (int)jobs.size(), cur[grp[0]].h->pb.cnt);
-        if (st == AS_OK) {
-          for (size_t g : grp) cur[g].h->st.grouped_batches++;
-          AS_CUDA_TRY(cudaEventRecord(gev, gs));
-          for (size_t g : grp) AS_CUDA_TRY(cudaStreamWaitEvent(cur[g].h->s, gev, 0));
-        } else if (st != AS_ENOTSUP) {
-          return st;
-        }
-      }
-      if (st == AS_ENOTSUP)   // one job, or the group did not fit: each on its own stream
-        for (size_t q = 0; q < grp.size(); ++q) {
-          as_sketch* h = cur[grp[q]].h;
-          const BatchJob& j = jobs[q];
-          st = launch_batch_persist(h->s, j.Gf, j.n2, j.r0, j.nb, j.k_pi, j.q, j.key, j.i0, j.pb, j.status, h->prof);
-          if (st != AS_OK) return st;
-        }
-      grp.clear();
-      jobs.clear();
-      tiles = 0;
-      return AS_OK;
-    };
-    for (size_t i : act) {
-      Cur& c = cur[i];
-      if (c.fst != AS_OK || !c.ctx.deferred) continue;
-      const BatchJob j = block_job(c.h, c.ctx);
-      const int t = batch_group_tiles(j);
-      if (t <= 0 || t > cap) {
-        c.fst = launch_batch_persist(c.h->s, j.Gf, j.n2, j.r0, j.nb, j.k_pi, j.q, j.key, j.i0, j.pb, j.status,
-                                     c.h->prof);
-        continue;
-      }
-      if (tiles + t > cap || jobs.size() == 32) {
-        gst = flush();
-        if (gst != AS_OK) break;
-      }
-      grp.push_back(i);
-      jobs.push_back(j);
-      tiles += t;
-    }
-    if (gst == AS_OK) gst = flush();
-    if (gst != AS_OK) break;
-    // decision phase of every block
-    run_parallel((int)act.size(), [&](int t) {
-      Cur& c = cur[act[(size_t)t]];
-      if (c.fst != AS_OK) return;
-      c.used = 0;
-      c.bad = false;
-      c.fst = block_finish(c.h, c.ctx, &c.used, &c.bad);
-    });
-    for (size_t i : act) {
-      Cur& c = cur[i];
-      if (c.fst != AS_OK) {
-        fail(c, c.fst);
-        continue;
-      }
-      c.done += c.used;
-      as_status st = AS_OK;
-      if (c.bad) {   // a non-finite row ends its entry (rows before it are in)
-        status[c.ent[c.e]] = AS_EINVAL;
-        ++c.e;
-        c.t0 = 0;
-        st = stage(c);
-      } else if (c.done >= c.nb) {
-        c.t0 += c.nb;
-        st = stage(c);
-      }
-      if (st != AS_OK) fail(c, st);
-    }
-  }
-  for (Cur& c : cur) {
-    if (gst != AS_OK) fail(c, gst);
-    if (c.lk.owns_lock()) {
-      as_status ds = sync_status(c.h);
-      if (ds != AS_OK)
-        for (int k : c.ent)
-          if (status[k] == AS_OK) status[k] = ds;
-    }
-    if (c.ev) cudaEventDestroy(c.ev);
-  }
-  if (gev) cudaEventDestroy(gev);
-  if (gs) cudaStreamDestroy(gs);
-  return gst;
-}
 
 cudaStream_t sk_stream(const as_sketch* h) { return h->s; }
 int sk_device(const as_sketch* h) { return h->dev; }
@@ -1602,7 +1553,9 @@ as_status sketch_reserve(as_sketch* h, int64_t snapshot_rank) {
   return st;
 }
 
-as_status sketch_update(as_sketch* h, const float* rows, int64_t n, int64_t ld) {
+// sketch_update, with the FP32 batched iterations going through the device's
+// launch combiner when comb is given.
+static as_status update_rows(as_sketch* h, const float* rows, int64_t n, int64_t ld, Combiner* comb) {
   if (!h) return AS_EINVAL;
   if (h->mode == AS_COORDINATOR) return AS_EINVAL;   // a coordinator only receives
   if (n == 0) return AS_OK;
@@ -1634,7 +1587,7 @@ as_status sketch_update(as_sketch* h, const float* rows, int64_t n, int64_t ld) 
     while (done < nb && st == AS_OK) {
       int64_t used = 0;
       bool bad = false;
-      st = process_block(h, base + done * h->d, nb - done, &used, &bad);
+      st = process_block(h, base + done * h->d, nb - done, &used, &bad, comb);
       done += used;
       if (st == AS_OK && bad) st = AS_EINVAL;
     }
@@ -1645,6 +1598,12 @@ as_status sketch_update(as_sketch* h, const float* rows, int64_t n, int64_t ld) 
   }
   return st;
 }
+
+as_status sketch_update(as_sketch* h, const float* rows, int64_t n, int64_t ld) {
+  return update_rows(h, rows, n, ld, nullptr);
+}
+
+
 
 as_status sketch_query_gram(as_sketch* h, int64_t t, double* out) {
   if (!h || !out) return AS_EINVAL;
@@ -1931,3 +1890,21 @@ as_status sketch_destroy(as_sketch* h) {
 }
 
 }  // extern "C"
+
+namespace as {
+// sketch_update of one of several sketches updated together (the caller runs
+// them on separate host threads, between combined_begin and combined_end on
+// the same device): FP32 batched iterations share grouped launches.
+as_status combined_begin(int dev, void** token) {
+  Combiner* c = nullptr;
+  as_status st = combiner_for(dev, &c);
+  if (st != AS_OK) return st;
+  *token = c;
+  return AS_OK;
+}
+void combined_enter(void* token) { static_cast<Combiner*>(token)->enter(); }
+void combined_leave(void* token) { static_cast<Combiner*>(token)->leave(); }
+as_status sk_update_combined(as_sketch* h, const float* rows, int64_t n, int64_t ld, void* token) {
+  return update_rows(h, rows, n, ld, static_cast<Combiner*>(token));
+}
+}  // namespace as

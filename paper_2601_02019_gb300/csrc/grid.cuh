@@ -46,6 +46,7 @@ __device__ __forceinline__ bool wait_flag_ge(const unsigned* flag, unsigned targ
 __device__ __forceinline__ bool grid_barrier(unsigned* cnt, unsigned target, int* status,
                                              unsigned long long limit_ns = kWaitLimitNs) {
   __shared__ int s_ok;
+  __syncwarp();   // a block barrier needs converged warps (thread 0 ran alone)
   __syncthreads();
   if (threadIdx.x == 0) {
     // release: this CTA's writes (ordered before by __syncthreads) become
@@ -63,6 +64,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* cnt, unsigned target, int
     }
     s_ok = ok;
   }
+  __syncwarp();   // a block barrier needs converged warps (thread 0 ran alone)
   __syncthreads();
   return s_ok != 0;
 }
@@ -74,6 +76,7 @@ template <typename F>
 __device__ __forceinline__ bool grid_barrier_then(unsigned* cnt, unsigned target, int* status, F&& before_arrive,
                                                   unsigned long long limit_ns = kWaitLimitNs) {
   __shared__ int s_ok2;
+  __syncwarp();   // a block barrier needs converged warps (thread 0 ran alone)
   __syncthreads();
   if (threadIdx.x == 0) {
     before_arrive();
@@ -90,6 +93,7 @@ __device__ __forceinline__ bool grid_barrier_then(unsigned* cnt, unsigned target
     }
     s_ok2 = ok;
   }
+  __syncwarp();   // a block barrier needs converged warps (thread 0 ran alone)
   __syncthreads();
   return s_ok2 != 0;
 }

@@ -271,13 +271,15 @@ int tune_pick(cudaStream_t s, const char* kernel, long long key, const int* choi
 // snapshots, and the eigen-shrink of a device B (the eigen-shrink of Algorithm 5).
 // Runs f(0) .. f(n-1) on the library's worker threads and waits for all.
 void run_parallel(int n, const std::function<void(int)>& f);
-// Several sketches updated in lockstep: each step prepares one block of every
-// sketch, runs their FP32 batched iterations in grouped cooperative launches
-// (as many sketches per launch as fit on the GPU at once), then finishes every
-// block in parallel.  Entries naming the same sketch run in list order;
-// status[k] receives entry k's status, as sketch_update would return it.
-as_status sk_group_update(as_sketch* const* hs, const float* const* rows, const int64_t* n, const int64_t* ld,
-                          int32_t count, as_status* status);
+// Several sketches updated together through the device's launch combiner
+// (engine.cu): combined_begin returns the device's combiner as a token; each
+// sketch's host thread brackets its updates with combined_enter/leave and
+// calls sk_update_combined (sketch_update whose FP32 batched iterations share
+// grouped launches with the other sketches' ready blocks).
+as_status combined_begin(int dev, void** token);
+void combined_enter(void* token);
+void combined_leave(void* token);
+as_status sk_update_combined(as_sketch* h, const float* rows, int64_t n, int64_t ld, void* token);
 cudaStream_t sk_stream(const as_sketch* h);
 int sk_device(const as_sketch* h);
 int64_t sk_device_bytes(const as_sketch* h);

@@ -237,10 +237,40 @@ as_status sketch_update_grouped(as_sketch* const* hs, const float* const* rows, 
   if (count < 0) return AS_EINVAL;
   if (count == 0) return AS_OK;
   if (!hs || !rows || !n || !ld) return AS_EINVAL;
-  // lockstep blocks: one grouped launch of the batched iterations per step
+  for (int32_t k = 0; k < count; ++k)
+    if (!hs[k]) return AS_EINVAL;
+  // every sketch on a host thread of its own, its FP32 batched iterations
+  // grouped with whichever other sketches have a block ready (the device's
+  // launch combiner)
+  const int dev = as::sk_device(hs[0]);
+  for (int32_t k = 1; k < count; ++k)
+    if (as::sk_device(hs[k]) != dev) return AS_EINVAL;
+  void* comb = nullptr;
+  {
+    int cur = 0;
+    AS_CUDA_TRY(cudaGetDevice(&cur));
+    AS_CUDA_TRY(cudaSetDevice(dev));
+    const as_status cs = as::combined_begin(dev, &comb);
+    AS_CUDA_TRY(cudaSetDevice(cur));
+    if (cs != AS_OK) return cs;
+  }
+  std::vector<std::vector<int32_t>> groups;
+  std::unordered_map<const as_sketch*, size_t> gi;
+  for (int32_t k = 0; k < count; ++k) {
+    auto it = gi.find(hs[k]);
+    if (it == gi.end()) {
+      gi.emplace(hs[k], groups.size());
+      groups.push_back({k});
+    } else {
+      groups[it->second].push_back(k);
+    }
+  }
   std::vector<as_status> st((size_t)count, AS_OK);
-  const as_status g = as::sk_group_update(hs, rows, n, ld, count, st.data());
-  if (g != AS_OK) return g;
+  as::run_parallel((int)groups.size(), [&](int g) {
+    as::combined_enter(comb);
+    for (int32_t k : groups[(size_t)g]) st[(size_t)k] = as::sk_update_combined(hs[k], rows[k], n[k], ld[k], comb);
+    as::combined_leave(comb);
+  });
   for (as_status e : st)
     if (e != AS_OK) return e;
   return AS_OK;
