@@ -176,122 +176,162 @@ __global__ void bisect_df(int n, int nev, const double* norms, const df64* dd, c
 }
 
 // Inverse iteration for the eigenvalues found by bisect_df, one thread per
-// eigenvector in full warps: the LU factorisation and the solves are FP64
-// recurrences, and FP64 issue is scarce on this part, so no lane of a warp
-// should idle.  lam = evals[j] / norms[3] undoes the exact power-of-two
+// eigenvector, 32 eigenvectors per block: the LU factorisation and the solves
+// are FP64 recurrences, and FP64 issue is scarce on this part, so no lane of a
+// warp should idle.  lam = evals[j] / norms[3] undoes the exact power-of-two
 // unscaling.
 //
 // The sweeps over the factors are bound by memory latency, not arithmetic:
-// each step's loads do not depend on the recurrence, so they are issued in
-// batches of kInvitBatch steps ahead of the arithmetic that uses them (every
-// value a batch reads was written in an earlier sweep, or earlier in the
-// forward sweep at a lower index).  The LU stores the reciprocal of each
-// pivot (off the recurrence's dependent chain); the normalisation of an
-// iterate is folded into the next forward sweep (the sweep is linear), so an
-// iteration is two sweeps; the first iteration starts from ii_start without
-// reading X, and one final pass scales the last iterate.
-constexpr int kInvitBatch = 8;
+// their loads do not depend on the recurrence.  The factors and the iterate
+// are interleaved by eigenvector (entry i of vector j at i * nev + j), so the
+// block's 32 vectors' entries of one step are 256 contiguous bytes; each
+// thread copies its own entries of the next kInvitTile steps to shared memory
+// with cp.async while it runs the recurrence over the current tile (double
+// buffered).  A thread reads back only what it copied itself, so no block
+// barrier is needed.  The LU stores the reciprocal of each pivot (off the
+// recurrence's dependent chain); the normalisation of an iterate is folded
+// into the next forward sweep (the sweep is linear), so an iteration is two
+// sweeps; the first iteration starts from ii_start, and one final pass scales
+// the last iterate.
+constexpr int kInvitTile = 24;   // 2 x 4 x 24 x 32 doubles = 48 KB of static shared memory
+constexpr int kInvitArrays = 4;   // staged arrays per step (at most)
+
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __global__ void __launch_bounds__(32) invit_df(int n, int nev, TriWork w, const double* norms, const double* evals,
                                                double* X, int ldx, double* lu) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nev) return;
+  // [buffer][array][step][lane]
+  __shared__ double stg[2][kInvitArrays][kInvitTile][32];
+  const int lane = threadIdx.x;
+  const int j = blockIdx.x * blockDim.x + lane;
+  const bool valid = j < nev;
+  const int jj = valid ? j : nev - 1;   // an in-range column for the copies of lanes past nev
   const double tnorm = norms[0];
   const double eps = 2.220446049250313e-16;
-  const double lam = (tnorm == 0.0) ? 0.0 : evals[j] / norms[3];
+  const double lam = (tnorm == 0.0) ? 0.0 : evals[jj] / norms[3];
   const double* d = w.d;
   const double* e = w.e;
   if (tnorm == 0.0) {   // zero matrix: any orthonormal basis is an eigenbasis
-    for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] = (i == j) ? 1.0 : 0.0;
+    if (valid)
+      for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] = (i == j) ? 1.0 : 0.0;
     return;
   }
   const double tiny = fmax(eps * tnorm, 1e-300);
-  double* u0 = lu + (size_t)(0 * n) * nev + j;   // 1 / pivot (kept away from zero)
-  double* u1 = lu + (size_t)(1 * n) * nev + j;
-  double* u2 = lu + (size_t)(2 * n) * nev + j;
-  double* ll = lu + (size_t)(3 * n) * nev + j;
-  double* pv = lu + (size_t)(4 * n) * nev + j;
-  // LU of T - lam I with partial pivoting (as eig.cuh)
+  double* u0 = lu + (size_t)(0 * n) * nev + jj;   // 1 / pivot (kept away from zero)
+  double* u1 = lu + (size_t)(1 * n) * nev + jj;
+  double* u2 = lu + (size_t)(2 * n) * nev + jj;
+  double* ll = lu + (size_t)(3 * n) * nev + jj;
+  double* pv = lu + (size_t)(4 * n) * nev + jj;
+  // LU of T - lam I with partial pivoting (as eig.cuh); lanes past nev
+  // repeat the last vector's factorisation and store nothing
   double cd = d[0] - lam, cs = e[0];
   for (int i = 0; i + 1 < n; ++i) {
     const double b = e[i];
     const double nd = d[i + 1] - lam, ns = (i + 2 < n) ? e[i + 1] : 0.0;
-    double piv;
+    double piv, U1, U2, L, P;
     if (fabs(cd) >= fabs(b)) {
       if (cd == 0.0) cd = tiny;
       const double li = b / cd;
-      piv = cd;
-      u1[(size_t)i * nev] = cs; u2[(size_t)i * nev] = 0.0;
-      ll[(size_t)i * nev] = li; pv[(size_t)i * nev] = 0.0;
+      piv = cd; U1 = cs; U2 = 0.0; L = li; P = 0.0;
       cd = nd - li * cs; cs = ns;
     } else {
       const double li = cd / b;
-      piv = b;
-      u1[(size_t)i * nev] = nd; u2[(size_t)i * nev] = ns;
-      ll[(size_t)i * nev] = li; pv[(size_t)i * nev] = 1.0;
+      piv = b; U1 = nd; U2 = ns; L = li; P = 1.0;
       cd = cs - li * nd; cs = -li * ns;
     }
     if (fabs(piv) < tiny) piv = (piv < 0 ? -tiny : tiny);
-    u0[(size_t)i * nev] = 1.0 / piv;
+    if (valid) {
+      u0[(size_t)i * nev] = 1.0 / piv;
+      u1[(size_t)i * nev] = U1; u2[(size_t)i * nev] = U2;
+      ll[(size_t)i * nev] = L; pv[(size_t)i * nev] = P;
+    }
   }
   if (fabs(cd) < tiny) cd = (cd < 0 ? -tiny : tiny);
-  u0[(size_t)(n - 1) * nev] = 1.0 / cd;
-  double* x = X + j;
+  if (valid) u0[(size_t)(n - 1) * nev] = 1.0 / cd;
+  __threadfence_block();   // the factors (and later the iterate) are read back through cp.async
+  __syncwarp();
+  double* x = X + jj;
   const size_t sx = (size_t)ldx;
   double rhs = 1.0;   // scale of the stored iterate (its pending normalisation)
   for (int it = 0; it < 3; ++it) {
-    // forward elimination with the row interchanges: y = L^-1 P (rhs x)
-    double cur = (it == 0) ? ii_start(0, j) : x[0] * rhs;
-    for (int ib = 0; ib + 1 < n; ib += kInvitBatch) {
-      const int nb = min(kInvitBatch, n - 1 - ib);
-      double xr[kInvitBatch], lr[kInvitBatch], pr[kInvitBatch];
-#pragma unroll
-      for (int u = 0; u < kInvitBatch; ++u) {
-        if (u < nb) {
-          const int i = ib + u;
-          xr[u] = (it == 0) ? ii_start(i + 1, j) : x[(size_t)(i + 1) * sx] * rhs;
-          lr[u] = ll[(size_t)i * nev];
-          pr[u] = pv[(size_t)i * nev];
-        }
+    // forward elimination with the row interchanges: y = L^-1 P (rhs x), steps
+    // i = 0 .. n-2 in tiles; a tile stages ll[i], pv[i] and x[i+1]
+    const int nsteps = n - 1;
+    const int ntiles = (nsteps + kInvitTile - 1) / kInvitTile;
+    auto stage_fwd = [&](int t, int buf) {
+      const int i0 = t * kInvitTile, cnt = min(kInvitTile, nsteps - i0);
+      for (int u = 0; u < cnt; ++u) {
+        const size_t i = (size_t)(i0 + u);
+        cp_async8(&stg[buf][0][u][lane], ll + i * nev);
+        cp_async8(&stg[buf][1][u][lane], pv + i * nev);
+        if (it > 0) cp_async8(&stg[buf][2][u][lane], x + (i + 1) * sx);
       }
-#pragma unroll
-      for (int u = 0; u < kInvitBatch; ++u) {
-        if (u < nb) {
-          double yi = cur, yn = xr[u];
-          if (pr[u] != 0.0) { const double t = yi; yi = yn; yn = t; }
-          yn -= lr[u] * yi;
-          x[(size_t)(ib + u) * sx] = yi;
-          cur = yn;
-        }
+      cp_async_commit();
+    };
+    double cur = (it == 0) ? ii_start(0, jj) : x[0] * rhs;
+    if (ntiles > 0) stage_fwd(0, 0);
+    for (int t = 0; t < ntiles; ++t) {
+      if (t + 1 < ntiles) {
+        stage_fwd(t + 1, (t + 1) & 1);
+        cp_async_wait1();
+      } else {
+        cp_async_wait0();
+      }
+      const int buf = t & 1, i0 = t * kInvitTile, cnt = min(kInvitTile, nsteps - i0);
+      for (int u = 0; u < cnt; ++u) {
+        const int i = i0 + u;
+        double yi = cur;
+        double yn = (it == 0) ? ii_start(i + 1, jj) : stg[buf][2][u][lane] * rhs;
+        if (stg[buf][1][u][lane] != 0.0) { const double tt = yi; yi = yn; yn = tt; }
+        yn -= stg[buf][0][u][lane] * yi;
+        if (valid) x[(size_t)i * sx] = yi;
+        cur = yn;
       }
     }
-    x[(size_t)(n - 1) * sx] = cur;
-    // back substitution (u0 holds 1 / pivot), with the max and the sum of squares
+    if (valid) x[(size_t)(n - 1) * sx] = cur;
+    __threadfence_block();
+    __syncwarp();
+    // back substitution (u0 holds 1 / pivot), with the max and the sum of
+    // squares; steps i = n-1 .. 0 in tiles, staging x[i], u0[i], u1[i], u2[i]
+    const int btiles = (n + kInvitTile - 1) / kInvitTile;
+    auto stage_back = [&](int t, int buf) {
+      const int ihi = n - 1 - t * kInvitTile, cnt = min(kInvitTile, ihi + 1);
+      for (int u = 0; u < cnt; ++u) {
+        const size_t i = (size_t)(ihi - u);
+        cp_async8(&stg[buf][0][u][lane], x + i * sx);
+        cp_async8(&stg[buf][1][u][lane], u0 + i * nev);
+        cp_async8(&stg[buf][2][u][lane], u1 + i * nev);
+        cp_async8(&stg[buf][3][u][lane], u2 + i * nev);
+      }
+      cp_async_commit();
+    };
     double xn1 = 0.0, xn2 = 0.0, mx = 0.0, ss = 0.0;
-    for (int ib = n - 1; ib >= 0; ib -= kInvitBatch) {
-      const int nb = min(kInvitBatch, ib + 1);
-      double xr[kInvitBatch], a0[kInvitBatch], a1[kInvitBatch], a2[kInvitBatch];
-#pragma unroll
-      for (int u = 0; u < kInvitBatch; ++u) {
-        if (u < nb) {
-          const size_t i = (size_t)(ib - u);
-          xr[u] = x[i * sx];
-          a0[u] = u0[i * nev];
-          a1[u] = u1[i * nev];
-          a2[u] = u2[i * nev];
-        }
+    stage_back(0, 0);
+    for (int t = 0; t < btiles; ++t) {
+      if (t + 1 < btiles) {
+        stage_back(t + 1, (t + 1) & 1);
+        cp_async_wait1();
+      } else {
+        cp_async_wait0();
       }
-#pragma unroll
-      for (int u = 0; u < kInvitBatch; ++u) {
-        if (u < nb) {
-          const double xi = (xr[u] - a1[u] * xn1 - a2[u] * xn2) * a0[u];
-          x[(size_t)(ib - u) * sx] = xi;
-          xn2 = xn1; xn1 = xi;
-          mx = fmax(mx, fabs(xi));
-          ss = fma(xi, xi, ss);
-        }
+      const int buf = t & 1, ihi = n - 1 - t * kInvitTile, cnt = min(kInvitTile, ihi + 1);
+      for (int u = 0; u < cnt; ++u) {
+        const double xi = (stg[buf][0][u][lane] - stg[buf][2][u][lane] * xn1 - stg[buf][3][u][lane] * xn2) *
+                          stg[buf][1][u][lane];
+        if (valid) x[(size_t)(ihi - u) * sx] = xi;
+        xn2 = xn1; xn1 = xi;
+        mx = fmax(mx, fabs(xi));
+        ss = fma(xi, xi, ss);
       }
     }
+    __threadfence_block();
+    __syncwarp();
     if (ss > 0.0 && ss < 1e300) {
       rhs = 1.0 / sqrt(ss);
     } else {   // squares out of range: normalise in two scaled passes
@@ -301,16 +341,8 @@ __global__ void __launch_bounds__(32) invit_df(int n, int nev, TriWork w, const 
       rhs = (nrm > 0.0) ? rmx / sqrt(nrm) : 0.0;
     }
   }
-  for (int ib = 0; ib < n; ib += kInvitBatch) {
-    const int nb = min(kInvitBatch, n - ib);
-    double xr[kInvitBatch];
-#pragma unroll
-    for (int u = 0; u < kInvitBatch; ++u)
-      if (u < nb) xr[u] = x[(size_t)(ib + u) * sx];
-#pragma unroll
-    for (int u = 0; u < kInvitBatch; ++u)
-      if (u < nb) x[(size_t)(ib + u) * sx] = xr[u] * rhs;
-  }
+  if (valid)
+    for (int i = 0; i < n; ++i) x[(size_t)i * sx] *= rhs;
 }
 
 __device__ __forceinline__ df64 df_warp_sum(df64 v) {

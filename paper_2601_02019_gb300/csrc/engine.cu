@@ -781,9 +781,10 @@ as_status block_finish(as_sketch* h, const BlockCtx& c, int64_t* used, bool* bad
 // thread and stream; a block whose batched iterations would run the FP32
 // persistent kernel hands its job to the device's combiner instead.  The
 // combiner's thread launches whichever jobs are pending as one grouped
-// cooperative launch (launch_batch_group): as soon as every sketch of the
-// update has a job pending, or kCombineWindow after the first job arrived,
-// whichever is earlier.  No sketch waits for another's decision phase (the
+// cooperative launch (launch_batch_group) as soon as no other sketch of the
+// update is in its launch phase (the only phase that can still add a job
+// soon), or kCombineWindow after the first job arrived, whichever is earlier.
+// No sketch waits for another's decision phase (the
 // lockstep of earlier builds made every step wait for the slowest sketch's
 // event rows).  Each job's result equals that of its own launch, so a
 // sketch's results do not depend on the groups it landed in.
@@ -799,13 +800,20 @@ struct CombineReq {
 class Combiner {
  public:
   explicit Combiner(int dev) : dev_(dev) {}
-  as_status start() {
+  as_status start() {   // the calling thread's current device is left as it was
+    int prev = 0;
+    AS_CUDA_TRY(cudaGetDevice(&prev));
     AS_CUDA_TRY(cudaSetDevice(dev_));
-    AS_CUDA_TRY(cudaStreamCreateWithFlags(&gs_, cudaStreamNonBlocking));
-    AS_CUDA_TRY(cudaEventCreateWithFlags(&gev_, cudaEventDisableTiming));
-    as_status st = dalloc(&cnt_, 1);
+    as_status st = AS_OK;
+    if (cudaStreamCreateWithFlags(&gs_, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&gev_, cudaEventDisableTiming) != cudaSuccess) {
+      as_note_cuda_error(cudaGetLastError(), __FILE__, __LINE__);
+      st = AS_EDEVICE;
+    }
+    if (st == AS_OK) st = dalloc(&cnt_, 1);
+    if (st == AS_OK) cap_ = batch_group_capacity();
+    cudaSetDevice(prev);
     if (st != AS_OK) return st;
-    cap_ = batch_group_capacity();
     th_ = std::thread([this] { loop(); });
     th_.detach();   // lives for the whole process, like the worker pool
     return AS_OK;
@@ -813,6 +821,18 @@ class Combiner {
   void enter() {
     std::lock_guard<std::mutex> lk(mu_);
     ++active_;
+  }
+  // a sketch's launch phase (which may end with a job for the combiner)
+  void prep_begin() {
+    std::lock_guard<std::mutex> lk(mu_);
+    ++preparing_;
+  }
+  void prep_end() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      --preparing_;
+    }
+    cv_.notify_all();
   }
   void leave() {
     {
@@ -826,6 +846,7 @@ class Combiner {
       std::lock_guard<std::mutex> lk(mu_);
       if (pending_.empty()) first_ = std::chrono::steady_clock::now();
       pending_.push_back(r);
+      --preparing_;
     }
     cv_.notify_all();
     std::unique_lock<std::mutex> lk(mu_);
@@ -843,7 +864,8 @@ class Combiner {
       {
         std::unique_lock<std::mutex> lk(mu_);
         cv_.wait(lk, [&] { return !pending_.empty(); });
-        cv_.wait_until(lk, first_ + kCombineWindow, [&] { return (int)pending_.size() >= active_; });
+        cv_.wait_until(lk, first_ + kCombineWindow,
+                       [&] { return preparing_ == 0 || (int)pending_.size() >= active_; });
         int tiles = 0;
         size_t k = 0;
         for (; k < pending_.size() && batch.size() < 32; ++k) {
@@ -904,6 +926,7 @@ class Combiner {
   std::vector<BatchJob> jobs_;
   std::chrono::steady_clock::time_point first_;
   int active_ = 0;
+  int preparing_ = 0;   // sketches in a launch phase that has not handed over its job yet
 };
 
 std::mutex g_comb_mu;
@@ -930,7 +953,9 @@ as_status combiner_for(int dev, Combiner** out) {
 as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t* used, bool* bad_row,
                         Combiner* comb = nullptr) {
   BlockCtx c;
+  if (comb) comb->prep_begin();
   as_status st = block_prepare(h, src, navail, c, comb != nullptr);
+  if (comb && (st != AS_OK || !c.deferred)) comb->prep_end();
   if (st != AS_OK) return st;
   if (c.deferred) {
     if (!h->comb_ev) AS_CUDA_TRY(cudaEventCreateWithFlags(&h->comb_ev, cudaEventDisableTiming));
@@ -938,7 +963,7 @@ as_status process_block(as_sketch* h, const float* src, int64_t navail, int64_t*
     CombineReq r;
     r.job = block_job(h, c);
     r.h = h;
-    st = comb->submit(&r);
+    st = comb->submit(&r);   // ends the launch phase (prep_end) once the job is pending
     if (st != AS_OK) return st;
   }
   return block_finish(h, c, used, bad_row);
@@ -1893,8 +1918,8 @@ as_status sketch_destroy(as_sketch* h) {
 
 namespace as {
 // sketch_update of one of several sketches updated together (the caller runs
-// them on separate host threads, between combined_begin and combined_end on
-// the same device): FP32 batched iterations share grouped launches.
+// them on separate host threads, each between combined_enter and
+// combined_leave, all on the device of combined_begin): FP32 batched iterations share grouped launches.
 as_status combined_begin(int dev, void** token) {
   Combiner* c = nullptr;
   as_status st = combiner_for(dev, &c);

@@ -247,11 +247,7 @@ as_status sketch_update_grouped(as_sketch* const* hs, const float* const* rows, 
     if (as::sk_device(hs[k]) != dev) return AS_EINVAL;
   void* comb = nullptr;
   {
-    int cur = 0;
-    AS_CUDA_TRY(cudaGetDevice(&cur));
-    AS_CUDA_TRY(cudaSetDevice(dev));
     const as_status cs = as::combined_begin(dev, &comb);
-    AS_CUDA_TRY(cudaSetDevice(cur));
     if (cs != AS_OK) return cs;
   }
   std::vector<std::vector<int32_t>> groups;
