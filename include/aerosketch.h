@@ -470,7 +470,7 @@ as_status as_tc_gemm(int32_t M, int32_t N, int32_t K, const float* A, const floa
  * reads is written earlier in the same call): calls that overlap on the GPU
  * race.  The first call on a device, and the first after that device's
  * context was destroyed and made again (cudaDeviceReset), looks up the array's
- * address; make that first call before any stream capture.  AS_ENOTSUP if the
+ * address with a host-side driver query (no allocation).  AS_ENOTSUP if the
  * driver entry point for the current context cannot be found. */
 as_status as_symeig_noalloc(int32_t n, const double* A, int32_t nev, double* evals, double* vecs, void* cuda_stream);
 

@@ -12,11 +12,14 @@
 //     (every block recomputes it from row r) and p = A22 v_r, one warp per
 //     row, with per-block partial sums of v^T p summed in a fixed order by the
 //     next pass.  No atomics: results are bitwise reproducible.
-//   * bisection: eight lanes per eigenvalue (multisection) on df64 Sturm
+//   * bisection: several lanes per eigenvalue (multisection, the lane count
+//     picked per matrix order by the launch-shape autotuner) on df64 Sturm
 //     counts of T / ||T||; inverse iteration in FP64, one thread per
-//     eigenvalue.
-//   * back-transformation (df64): each block owns a slab of eigenvector
-//     columns in shared memory and applies every reflector to it.
+//     eigenvalue, its tridiagonal factors staged through shared memory with
+//     cp.async.
+//   * back-transformation (df64, blocked): reflectors are grouped into
+//     compact-WY factors I - V T V^T; each block owns a slab of eigenvector
+//     columns in shared memory and applies the groups to it.
 #include "df64.cuh"
 #include "eig.cuh"
 #include "grid.cuh"

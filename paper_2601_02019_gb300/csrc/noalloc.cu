@@ -13,7 +13,7 @@
 // race with each other.  The first call on a device (and the first call after
 // that device's context was destroyed and made again, for example after
 // cudaDeviceReset, which loads the module and its array anew) looks up the
-// array's device address; make that first call before any stream capture.
+// array's device address with a host-side driver query, which allocates nothing.
 #include <mutex>
 
 #include "eig.cuh"
