@@ -137,4 +137,30 @@ __device__ __forceinline__ df64 df_sqrt(df64 a) {
   return df_renorm(r, corr);
 }
 
+// 1 / sqrt(a) for a > 0 without a division.  a is first scaled by an exact
+// power of two, a = a' 2^(2k) with a' in [1/2, 2), so that no intermediate
+// leaves the FP32 range.  Then the FP32 estimate r0 = rsqrtf(a'.hi) (relative
+// error below 2^-21) is refined by the binomial series of (1 - h)^(-1/2),
+// with h = 1 - a' r0^2 formed in df64:
+//   1/sqrt(a') = r0 (1 + h/2 + 3h^2/8 + O(h^3)),
+// one step of the third-order Newton-Householder iteration for the
+// reciprocal square root.  The correction is small, so FP32 suffices for it;
+// the result carries about 46 significant bits.
+__device__ __forceinline__ df64 df_rsqrt(df64 a) {
+  if (!(a.hi > 0.f)) return df64{0.f, 0.f};
+  int ex;
+  (void)frexpf(a.hi, &ex);   // a.hi = m 2^ex, m in [1/2, 1)
+  const int k = ex >> 1;     // floor(ex / 2)
+  const df64 as{ldexpf(a.hi, -2 * k), ldexpf(a.lo, -2 * k)};
+  const float r0 = rsqrtf(as.hi);
+  float p, e;
+  two_prod(r0, r0, p, e);    // r0^2 = p + e exactly
+  const df64 t = df_mul(as, df64{p, e});
+  const df64 h = df_sub(df64{1.f, 0.f}, t);
+  const float hh = __fadd_rn(h.hi, h.lo);
+  const float corr = __fmul_rn(r0, __fmaf_rn(0.375f * hh, hh, 0.5f * hh));
+  const df64 r = df_renorm(r0, corr);
+  return df64{ldexpf(r.hi, -k), ldexpf(r.lo, -k)};
+}
+
 }  // namespace as

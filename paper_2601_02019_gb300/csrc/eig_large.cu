@@ -428,13 +428,14 @@ __device__ __forceinline__ df64 house_v_df(df64 xj, bool first, bool szero, df64
 //   3. row r past the diagonal after update r-1 (every CTA, from A and the
 //      vectors) -> the Householder vector v_r and e_r = alpha; the last pass
 //      (r = n-2) only closes the 2 x 2 tail;
-//   4. each warp updates its rows i >= r+1 (columns >= r+1) with
-//      A -= v w^T + w v^T and forms p_r[i] = A[i] . v_r; per-CTA partials of
-//      v_r^T p_r;
+//   4. the rows i >= r+1 (columns >= r+1) are updated with
+//      A -= v w^T + w v^T, and p_r[i] = A[i] . v_r is formed; per-CTA
+//      partials of v_r^T p_r;
 //   5. grid barrier.
 // v stays in shared memory across passes (every CTA computes it); p and the
-// partials are double buffered by pass parity.  Rows are dealt to the grid's
-// warps round-robin (row i to warp i mod warps).
+// partials are double buffered by pass parity.  Step 4 deals the rows to the
+// CTAs round-robin and splits a row over several warps when rows are fewer
+// than warps; warp 0 finishes the split dots before the barrier.
 struct TriPersist {
   df64* A;
   int lda, n;
@@ -460,6 +461,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
   __shared__ df64 red[kTriWarps];
   __shared__ df64 x0_s;
   __shared__ df64 wpart[kTriWarps];
+  __shared__ int s_ok;
   const int W = G * kTriWarps, gw = blockIdx.x * kTriWarps + warp;
   // Every thread owns the entries j = r + tid + kTriThreads u of the pass's
   // vectors (row r, w, v_r) and is the only one to write them before the
@@ -538,9 +540,9 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
     if (lane == 0) red[warp] = acc;
     __syncwarp();
     __syncthreads();
-    df64 s = red[0];
-#pragma unroll
-    for (int q = 1; q < kTriWarps; ++q) s = df_add(s, red[q]);
+    // every warp sums the warps' partials by the same butterfly: identical s
+    // in every thread
+    const df64 s = df_warp_sum((lane < kTriWarps) ? red[lane] : df64{0.f, 0.f});
     if (r == n - 2) {   // 2 x 2 tail: no further reflector
       if (blockIdx.x == 0 && tid == 0) {
         const int j = n - 1;
@@ -558,11 +560,11 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
     const bool szero = !(s.hi > 0.f);
     df64 alpha{0.f, 0.f}, rvn{1.f, 0.f};
     if (!szero) {
-      const df64 sq = df_sqrt(s);
+      const df64 sq = df_mul(s, df_rsqrt(s));
       alpha = (x0.hi >= 0.f) ? df_neg(sq) : sq;
       const df64 ax0 = (x0.hi >= 0.f) ? x0 : df_neg(x0);
       const df64 h = df_add(s, df_mul(ax0, sq));
-      rvn = df_div(df64{1.f, 0.f}, df_sqrt(df64{2.f * h.hi, 2.f * h.lo}));
+      rvn = df_rsqrt(df64{2.f * h.hi, 2.f * h.lo});
     }
     // v_r from this thread's own entries of x (x0 came through x0_s)
 #pragma unroll
@@ -575,29 +577,40 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
     if (blockIdx.x == 0 && tid == 0) t.e[r] = df_to_double(alpha);
     __syncwarp();
     __syncthreads();
-    // rows i >= r+1 of this warp: update with (v_{r-1}, w_{r-1}), dot with v_r
+    // rows i = r+1 .. n-1 (k = i - r - 1 < R): update with (v_{r-1}, w_{r-1})
+    // and dot with v_r.  Rows are dealt to the CTAs round-robin (row k to CTA
+    // k mod G), so that every SM keeps work as the trailing matrix shrinks;
+    // when there are fewer rows than warps, S warps share a row (warp sub of
+    // the row takes its 32-column chunks sub, sub + S, ...).  Each warp
+    // issues the next kTriUnroll chunks' loads before it works on the current
+    // ones.
     df64* pout = (r & 1) ? t.p[1] : t.p[0];
-    df64 contrib{0.f, 0.f};
-    for (int i = gw; i < n; i += W) {
-      if (i < r + 1) continue;
+    const int R = n - 1 - r;
+    int S = 1;
+    while (S < kTriWarps && (long long)R * (2 * S) <= (long long)G * kTriWarps) S *= 2;
+    const int slots = kTriWarps / S, slot = warp / S, sub = warp - slot * S;
+    const int cstride = 32 * S;                 // columns between a warp's chunks
+    df64 contrib{0.f, 0.f};                     // S = 1: sum of p_r[i] v_r[i] over this warp's rows
+    df64 mydot{0.f, 0.f};                       // S > 1: this warp's part of its one row's dot
+    for (int k = blockIdx.x + G * slot; k < R; k += G * slots) {
+      const int i = r + 1 + k;
       df64* ar = t.A + (size_t)i * t.lda;
       const df64 vi = upd ? vcur[i] : df64{0.f, 0.f};
       const df64 wi = upd ? wk[i] : df64{0.f, 0.f};
-      // kTriUnroll loads issued before the arithmetic that uses them; two
-      // accumulators shorten the dependent chain of the dot product
       df64 dot0{0.f, 0.f}, dot1{0.f, 0.f};
-      for (int jb = r + 1 + lane; jb < n; jb += 32 * kTriUnroll) {
-        df64 av[kTriUnroll];
+      auto load = [&](df64 (&b)[kTriUnroll], int jb) {
 #pragma unroll
         for (int u = 0; u < kTriUnroll; ++u) {
-          const int j = jb + 32 * u;
-          av[u] = (j < n) ? ar[j] : df64{0.f, 0.f};
+          const int j = jb + cstride * u;
+          b[u] = (j < n) ? ar[j] : df64{0.f, 0.f};
         }
+      };
+      auto work = [&](df64 (&b)[kTriUnroll], int jb) {
 #pragma unroll
         for (int u = 0; u < kTriUnroll; ++u) {
-          const int j = jb + 32 * u;
+          const int j = jb + cstride * u;
           if (j < n) {
-            df64 a = av[u];
+            df64 a = b[u];
             if (upd) {
               a = df_rank2(a, vi, wk[j], wi, vcur[j]);
               ar[j] = a;
@@ -606,24 +619,63 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
             else dot0 = df_fma(a, vnew[j], dot0);
           }
         }
+      };
+      // jb - lane is the same in every lane, so the round tests are uniform
+      const int rstep = cstride * kTriUnroll;
+      df64 b0[kTriUnroll], b1[kTriUnroll];
+      int jb = r + 1 + 32 * sub + lane;
+      load(b0, jb);
+      while (true) {
+        bool more = jb + rstep - lane < n;
+        if (more) load(b1, jb + rstep);
+        work(b0, jb);
+        if (!more) break;
+        jb += rstep;
+        more = jb + rstep - lane < n;
+        if (more) load(b0, jb + rstep);
+        work(b1, jb);
+        if (!more) break;
+        jb += rstep;
       }
       df64 dot = df_add(dot0, dot1);
       dot = df_warp_sum(dot);
-      if (lane == 0) {
-        pout[i] = dot;
-        contrib = df_add(contrib, df_mul(dot, vnew[i]));
+      if (S == 1) {
+        if (lane == 0) {
+          pout[i] = dot;
+          contrib = df_add(contrib, df_mul(dot, vnew[i]));
+        }
+      } else {
+        mydot = dot;   // at most one row per warp: R * S <= G * kTriWarps
       }
     }
-    if (lane == 0) wpart[warp] = contrib;
-    // the grid barrier's first CTA barrier also orders wpart; thread 0 then
-    // publishes this CTA's partial of v_r^T p_r before it arrives
+    if (lane == 0) wpart[warp] = (S == 1) ? contrib : mydot;
+    __syncwarp();
+    __syncthreads();
+    // warp 0 finishes the shared rows' dots (fixed order), forms this CTA's
+    // partial of v_r^T p_r, publishes it and arrives at the grid barrier
     df64* qout = (r & 1) ? t.q[1] : t.q[0];
-    const bool ok = grid_barrier_then(t.cnt, (unsigned)(r + 1) * (unsigned)G, t.status, [&] {
-      df64 q = wpart[0];
-      for (int u = 1; u < kTriWarps; ++u) q = df_add(q, wpart[u]);
-      qout[blockIdx.x] = q;
-    });
-    if (!ok) return;
+    if (warp == 0) {
+      df64 cq{0.f, 0.f};
+      if (S == 1) {
+        if (lane < kTriWarps) cq = wpart[lane];
+      } else if (lane < slots) {
+        const int k = blockIdx.x + G * lane;
+        if (k < R) {
+          df64 dot = wpart[lane * S];
+          for (int u = 1; u < S; ++u) dot = df_add(dot, wpart[lane * S + u]);
+          const int i = r + 1 + k;
+          pout[i] = dot;
+          cq = df_mul(dot, vnew[i]);
+        }
+      }
+      cq = df_warp_sum(cq);
+      if (lane == 0) qout[blockIdx.x] = cq;
+      __syncwarp();
+      if (lane == 0) s_ok = grid_arrive_wait(t.cnt, (unsigned)(r + 1) * (unsigned)G, t.status) ? 1 : 0;
+    }
+    __syncwarp();
+    __syncthreads();
+    if (!s_ok) return;
     df64* tmp = vcur;   // v_r becomes the vector of the next pass's update
     vcur = vnew;
     vnew = tmp;

@@ -69,6 +69,26 @@ __device__ __forceinline__ bool grid_barrier(unsigned* cnt, unsigned target, int
   return s_ok != 0;
 }
 
+// The arrival and bounded wait of a grid barrier, by one thread: adds one
+// arrival (release) and waits until the counter reaches `target` (acquire).
+// Returns false on a timeout (status set to AS_ETIMEOUT) or when the sticky
+// status is already set.  The caller orders the CTA's writes before it (a
+// block or warp barrier) and releases the other threads afterwards.
+__device__ __forceinline__ bool grid_arrive_wait(unsigned* cnt, unsigned target, int* status,
+                                                 unsigned long long limit_ns = kWaitLimitNs) {
+  red_release_add_u32(cnt, 1u);
+  const unsigned long long t0 = global_ns();
+  long long n = 0;
+  while (ld_acquire_u32(cnt) < target) {
+    if ((++n & 7) == 0) {
+      if (*(volatile int*)status != 0) return false;
+      if (n > kWaitMaxIters || global_ns() - t0 > limit_ns) { set_status(status, AS_ETIMEOUT); return false; }
+    }
+    __nanosleep(20);
+  }
+  return true;
+}
+
 // grid_barrier with `before_arrive` run by thread 0 after the CTA barrier and
 // before its arrival (e.g. publishing a per-CTA partial that the block's
 // shared memory holds); the arrival releases what it wrote.

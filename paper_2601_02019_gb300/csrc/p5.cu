@@ -101,25 +101,16 @@ as_status as_p5_round(as_p5* p, const float* const* rows, const int64_t* n, cons
     if (n[j] < 0 || (n[j] > 0 && (!rows[j] || ld[j] < p->d))) return AS_EINVAL;
   // the sites' rows, each site on its own stream and a worker thread: row
   // norms for the protocol and the site update.  The sites progress
-  // independently; their FP32 batched iterations share grouped launches
-  // through the device's launch combiner (no site waits for another's
-  // decisions).
+  // independently: sharing launches of the batched iterations (lockstep
+  // blocks, or the launch combiner of sketch_update_grouped) measured slower
+  // here, since a shared launch waits for the slowest site's decisions.
   const int m = p->m;
   std::vector<std::vector<double>> nrm((size_t)m);
   std::vector<as_status> sts((size_t)m, AS_OK);
-  void* comb = nullptr;
-  {
-    const as_status cs = as::combined_begin(as::sk_device(p->coord), &comb);
-    if (cs != AS_OK) return cs;
-  }
   as::run_parallel(m, [&](int j) {
     nrm[(size_t)j].assign((size_t)n[j], 0.0);
     sts[(size_t)j] = as::row_norms_f64(rows[j], n[j], ld[j], p->d, p->ss[(size_t)j], nrm[(size_t)j].data());
-    if (sts[(size_t)j] == AS_OK && n[j] > 0) {
-      as::combined_enter(comb);
-      sts[(size_t)j] = as::sk_update_combined(p->sites[(size_t)j], rows[j], n[j], ld[j], comb);
-      as::combined_leave(comb);
-    }
+    if (sts[(size_t)j] == AS_OK && n[j] > 0) sts[(size_t)j] = sketch_update(p->sites[(size_t)j], rows[j], n[j], ld[j]);
   });
   for (as_status st : sts)
     if (st != AS_OK) return st;
