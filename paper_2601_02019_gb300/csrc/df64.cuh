@@ -89,6 +89,26 @@ __device__ __forceinline__ df64 df_fma(df64 a, df64 b, df64 c) {
   return df_renorm(s, f);
 }
 
+// One step of a compensated dot product of df64 vectors (the scheme of Ogita,
+// Rump and Oishi's Dot2, extended by the cross terms of the low parts): the
+// running value is s + e, where s is the FP32 sum of the high-part products
+// (each added through TwoSum) and e gathers the TwoProduct and TwoSum errors
+// and a.hi b.lo + a.lo b.hi.  Only the two adds into s and e carry over to
+// the next step; df_dot_finish renormalises at the end.
+__device__ __forceinline__ void df_dot_step(df64 a, df64 b, float& s, float& e) {
+  float p, pe;
+  two_prod(a.hi, b.hi, p, pe);
+  float t, te;
+  two_sum(s, p, t, te);
+  s = t;
+  e = __fadd_rn(e, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fadd_rn(te, pe))));
+}
+__device__ __forceinline__ df64 df_dot_finish(float s, float e) {
+  float hi, lo;
+  two_sum(s, e, hi, lo);
+  return df64{hi, lo};
+}
+
 // a - (u * v + w * z): the two-sided rank-2 update of one matrix entry.
 __device__ __forceinline__ df64 df_rank2(df64 a, df64 u, df64 v, df64 w, df64 z) {
   float p1, e1, p2, e2;

@@ -179,7 +179,7 @@ __global__ void bisect_df(int n, int nev, const double* norms, const df64* dd, c
 }
 
 // Inverse iteration for the eigenvalues found by bisect_df, one thread per
-// eigenvector, 32 eigenvectors per block: the LU factorisation and the solves
+// eigenvector, up to 32 eigenvectors per block: the LU factorisation and the solves
 // are FP64 recurrences, and FP64 issue is scarce on this part, so no lane of a
 // warp should idle.  lam = evals[j] / norms[3] undoes the exact power-of-two
 // unscaling.
@@ -187,7 +187,7 @@ __global__ void bisect_df(int n, int nev, const double* norms, const df64* dd, c
 // The sweeps over the factors are bound by memory latency, not arithmetic:
 // their loads do not depend on the recurrence.  The factors and the iterate
 // are interleaved by eigenvector (entry i of vector j at i * nev + j), so the
-// block's 32 vectors' entries of one step are 256 contiguous bytes; each
+// block's vectors' entries of one step are contiguous (256 bytes for 32); each
 // thread copies its own entries of the next kInvitTile steps to shared memory
 // with cp.async while it runs the recurrence over the current tile (double
 // buffered).  A thread reads back only what it copied itself, so no block
@@ -212,6 +212,8 @@ __global__ void __launch_bounds__(32) invit_df(int n, int nev, TriWork w, const 
   // [buffer][array][step][lane]
   __shared__ double stg[2][kInvitArrays][kInvitTile][32];
   const int lane = threadIdx.x;
+  // the block is one (possibly partial) warp: name only its threads
+  const unsigned wmask = (blockDim.x >= 32) ? 0xffffffffu : ((1u << blockDim.x) - 1u);
   const int j = blockIdx.x * blockDim.x + lane;
   const bool valid = j < nev;
   const int jj = valid ? j : nev - 1;   // an in-range column for the copies of lanes past nev
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(32) invit_df(int n, int nev, TriWork w, const 
   if (fabs(cd) < tiny) cd = (cd < 0 ? -tiny : tiny);
   if (valid) u0[(size_t)(n - 1) * nev] = 1.0 / cd;
   __threadfence_block();   // the factors (and later the iterate) are read back through cp.async
-  __syncwarp();
+  __syncwarp(wmask);
   double* x = X + jj;
   const size_t sx = (size_t)ldx;
   double rhs = 1.0;   // scale of the stored iterate (its pending normalisation)
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(32) invit_df(int n, int nev, TriWork w, const 
     }
     if (valid) x[(size_t)(n - 1) * sx] = cur;
     __threadfence_block();
-    __syncwarp();
+    __syncwarp(wmask);
     // back substitution (u0 holds 1 / pivot), with the max and the sum of
     // squares; steps i = n-1 .. 0 in tiles, staging x[i], u0[i], u1[i], u2[i]
     const int btiles = (n + kInvitTile - 1) / kInvitTile;
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(32) invit_df(int n, int nev, TriWork w, const 
       }
     }
     __threadfence_block();
-    __syncwarp();
+    __syncwarp(wmask);
     if (ss > 0.0 && ss < 1e300) {
       rhs = 1.0 / sqrt(ss);
     } else {   // squares out of range: normalise in two scaled passes
@@ -462,7 +464,6 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
   __shared__ df64 x0_s;
   __shared__ df64 wpart[kTriWarps];
   __shared__ int s_ok;
-  const int W = G * kTriWarps, gw = blockIdx.x * kTriWarps + warp;
   // Every thread owns the entries j = r + tid + kTriThreads u of the pass's
   // vectors (row r, w, v_r) and is the only one to write them before the
   // barrier that publishes v_r to the sweep; the pass has four CTA barriers
@@ -597,7 +598,10 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
       df64* ar = t.A + (size_t)i * t.lda;
       const df64 vi = upd ? vcur[i] : df64{0.f, 0.f};
       const df64 wi = upd ? wk[i] : df64{0.f, 0.f};
-      df64 dot0{0.f, 0.f}, dot1{0.f, 0.f};
+      // the dot with v_r in two compensated accumulators (s, e): s sums the
+      // FP32 products of the high parts through TwoSum, e gathers every error
+      // and cross term; only one FP32 add per entry is on each loop-carried chain
+      float ds0 = 0.f, de0 = 0.f, ds1 = 0.f, de1 = 0.f;
       auto load = [&](df64 (&b)[kTriUnroll], int jb) {
 #pragma unroll
         for (int u = 0; u < kTriUnroll; ++u) {
@@ -615,8 +619,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
               a = df_rank2(a, vi, wk[j], wi, vcur[j]);
               ar[j] = a;
             }
-            if (u & 1) dot1 = df_fma(a, vnew[j], dot1);
-            else dot0 = df_fma(a, vnew[j], dot0);
+            if (u & 1) df_dot_step(a, vnew[j], ds1, de1);
+            else df_dot_step(a, vnew[j], ds0, de0);
           }
         }
       };
@@ -637,7 +641,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
         if (!more) break;
         jb += rstep;
       }
-      df64 dot = df_add(dot0, dot1);
+      df64 dot = df_add(df_dot_finish(ds0, de0), df_dot_finish(ds1, de1));
       dot = df_warp_sum(dot);
       if (S == 1) {
         if (lane == 0) {
@@ -892,8 +896,23 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
       tst = bisect(lanes);
       if (tst != AS_OK) return tst;
     }
-    invit_df<<<(nev + 31) / 32, 32, 0, s>>>(n, nev, w, norms, evals, X, ldx, lu);
-    count_launches(1);
+    // eigenvectors per block (one thread each), tuned per matrix order: the
+    // recurrences are FP64, and fewer eigenvectors per block spread them over
+    // more SMs' FP64 units
+    auto invit = [&](int per) -> as_status {
+      invit_df<<<(nev + per - 1) / per, per, 0, s>>>(n, nev, w, norms, evals, X, ldx, lu);
+      count_launches(1);
+      AS_CUDA_TRY(cudaGetLastError());
+      return AS_OK;
+    };
+    static const int kInvitChoices[3] = {32, 16, 8};
+    const int per = tune_pick(s, "invit_df", ((long long)n << 20) | (long long)nev, kInvitChoices, 3, invit, &tst,
+                              &ran);
+    if (tst != AS_OK) return tst;
+    if (!ran) {
+      tst = invit(per);
+      if (tst != AS_OK) return tst;
+    }
   }
   cluster_mgs<<<1, 512, 0, s>>>(n, nev, norms, evals, X, ldx); count_launches(1);
   if (prof) prof->end(PK_EIG_SOLVE, s, 0.0, 0.0);

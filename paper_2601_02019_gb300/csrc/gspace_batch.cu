@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "eig.cuh"
+#include "grid.cuh"
 #include "kernels.cuh"
 
 namespace as {
@@ -180,47 +181,64 @@ __global__ void rayleigh_ritz_kernel(int n2, int m, int k, const double* W, cons
   if (threadIdx.x == 0 && !(ritz[0] == ritz[0])) set_status(status, AS_ENUMERIC);
 }
 
-// Rayleigh-Ritz of Algorithm 2 for k = 2 in FP64, one block, closed-form 2 x 2
+// Rayleigh-Ritz of Algorithm 2 for k = 2 in FP64, closed-form 2 x 2
 // eigenproblems: S = Y^T (G Y) = V D V^T, W = Y V D^-1/2, GW = (G Y) V D^-1/2,
 // M = GW^T GW = U diag(ritz) U^T, WU, GWU.  Y is orthonormal (Euclidean).
-__global__ void rr2_kernel(int n2, int m, const double* Y, const double* GY, double* ritz, double* WU, double* GWU,
-                           int* status) {
+// The pair sums are FP64 multiply-adds, and one SM's FP64 issue rate would
+// make a single block take tens of microseconds at m = 2048, so the rows are
+// spread over several blocks (one cooperative launch): each block forms
+// partial sums over its share, and after a grid barrier every block adds the
+// partials in block order, so that every block holds the same coefficients.
+__global__ void __launch_bounds__(256) rr2_coop_kernel(int n2, int m, const double* Y, const double* GY,
+                                                        double* ritz, double* WU, double* GWU, double* part,
+                                                        unsigned* cnt, int* status) {
   __shared__ double red[32];
-  __shared__ double cf[8];   // (v00, v10, v01, v11) * (a0, a0, a1, a1), then U
+  __shared__ double cf[8];
+  const int G = gridDim.x, tid = threadIdx.x, stride = G * blockDim.x;
   double s00 = 0, s01 = 0, s11 = 0;
-  for (int p = threadIdx.x; p < m; p += blockDim.x) {
+  for (int p = blockIdx.x * blockDim.x + tid; p < m; p += stride) {
     const double a = Y[2 * p], b = Y[2 * p + 1], ga = GY[2 * p], gb = GY[2 * p + 1];
     s00 += a * ga; s01 += 0.5 * (a * gb + b * ga); s11 += b * gb;
   }
   s00 = block_sum(s00, red); s01 = block_sum(s01, red); s11 = block_sum(s11, red);
-  if (threadIdx.x == 0) {
+  if (tid == 0) { part[3 * blockIdx.x] = s00; part[3 * blockIdx.x + 1] = s01; part[3 * blockIdx.x + 2] = s11; }
+  if (!grid_barrier(cnt, (unsigned)G, status)) return;
+  if (tid == 0) {
+    double t00 = 0, t01 = 0, t11 = 0;
+    for (int g = 0; g < G; ++g) { t00 += part[3 * g]; t01 += part[3 * g + 1]; t11 += part[3 * g + 2]; }
     double l0, l1, v00, v01, v10, v11;
-    eig2(s00, s01, s11, l0, l1, v00, v01, v10, v11);
+    eig2(t00, t01, t11, l0, l1, v00, v01, v10, v11);
     const double a0 = (l0 > 0.0) ? 1.0 / sqrt(l0) : 0.0;
     const double a1 = (l1 > 1e-13 * l0 && l1 > 0.0) ? 1.0 / sqrt(l1) : 0.0;
     cf[0] = v00 * a0; cf[1] = v10 * a0; cf[2] = v01 * a1; cf[3] = v11 * a1;
   }
   __syncthreads();
   const double w00 = cf[0], w10 = cf[1], w01 = cf[2], w11 = cf[3];
-  // G W columns
   double m00 = 0, m01 = 0, m11 = 0;
-  for (int p = threadIdx.x; p < m; p += blockDim.x) {
+  for (int p = blockIdx.x * blockDim.x + tid; p < m; p += stride) {
     const double ga = GY[2 * p], gb = GY[2 * p + 1];
     const double g0 = ga * w00 + gb * w10, g1 = ga * w01 + gb * w11;
     m00 += g0 * g0; m01 += g0 * g1; m11 += g1 * g1;
   }
   m00 = block_sum(m00, red); m01 = block_sum(m01, red); m11 = block_sum(m11, red);
-  if (threadIdx.x == 0) {
+  double* part2 = part + 3 * G;
+  if (tid == 0) { part2[3 * blockIdx.x] = m00; part2[3 * blockIdx.x + 1] = m01; part2[3 * blockIdx.x + 2] = m11; }
+  if (!grid_barrier(cnt, 2u * (unsigned)G, status)) return;
+  if (tid == 0) {
+    double t00 = 0, t01 = 0, t11 = 0;
+    for (int g = 0; g < G; ++g) { t00 += part2[3 * g]; t01 += part2[3 * g + 1]; t11 += part2[3 * g + 2]; }
     double r0, r1, u00, u01, u10, u11;
-    eig2(m00, m01, m11, r0, r1, u00, u01, u10, u11);
-    ritz[0] = r0;
-    ritz[1] = (w01 != 0.0 || w11 != 0.0) ? r1 : 0.0;
-    if (!(r0 == r0)) set_status(status, AS_ENUMERIC);
+    eig2(t00, t01, t11, r0, r1, u00, u01, u10, u11);
+    if (blockIdx.x == 0) {
+      ritz[0] = r0;
+      ritz[1] = (w01 != 0.0 || w11 != 0.0) ? r1 : 0.0;
+      if (!(r0 == r0)) set_status(status, AS_ENUMERIC);
+    }
     cf[4] = u00; cf[5] = u10; cf[6] = u01; cf[7] = u11;
   }
   __syncthreads();
   const double u00 = cf[4], u10 = cf[5], u01 = cf[6], u11 = cf[7];
-  for (int p = threadIdx.x; p < n2; p += blockDim.x) {
+  for (int p = blockIdx.x * blockDim.x + tid; p < n2; p += stride) {
     double w0 = 0, w1 = 0, g0 = 0, g1 = 0;
     if (p < m) {
       const double a = Y[2 * p], b = Y[2 * p + 1], ga = GY[2 * p], gb = GY[2 * p + 1];
@@ -245,10 +263,17 @@ __global__ void promote_pair_kernel(const float* X, int n2, int col0, int m, int
 // Partial sums over row chunks s: Zp[s][c][a - ab] = sum_p C[p][c] WU[p][a] and
 // Yp[s][a - ab][c] = sum_p GWU[p][a] C[p][c] for a in [a0, a0+na) inside the
 // column block [ab, ab + w), one thread per column c.  Blocks of at most
-// kDumpBlock snapshot columns bound the partial planes to 2 kDumpChunks d
-// kDumpBlock doubles whatever xi is.
-constexpr int kDumpChunks = 8;
+// kDumpBlock snapshot columns bound the partial planes whatever xi is.  Narrow
+// blocks (the usual snapshot ranks) take more row chunks, so that enough loads
+// of C are in flight to stream it at memory speed.
 constexpr int kDumpBlock = 64;
+__host__ __device__ constexpr int dump_chunks(int w) { return w <= 16 ? 32 : 8; }
+// columns of one partial plane set: the largest w * dump_chunks(w) over the
+// column blocks of a rank-xi snapshot
+inline size_t dump_plane_cols(int xi) {
+  const int w1 = std::min(xi, kDumpBlock);
+  return (size_t)std::max(std::min(xi, 16) * dump_chunks(std::min(xi, 16)), w1 * dump_chunks(w1));
+}
 
 // FP32 copies of the first xi columns of WU and GWU (rows < r, row-major
 // r x xi), and the low part GWUlo = fl32(GWU - GWUf) for the residual.
@@ -270,9 +295,9 @@ __global__ void dump_partial_kernel(const float* __restrict__ C, int ldc, int d,
                                     const float* __restrict__ GWUf, int xi, int a0, int na, int ab, int w, double* Zp,
                                     double* Yp) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
+  const int s = blockIdx.y, nch = gridDim.y;
   if (c >= d) return;
-  const int chunk = (r + kDumpChunks - 1) / kDumpChunks;
+  const int chunk = (r + nch - 1) / nch;
   const int pb = s * chunk, pe = min(r, pb + chunk);
   double z[8], y[8];
   float zf[8], yf[8];
@@ -315,10 +340,10 @@ __global__ void dump_partial_kernel(const float* __restrict__ C, int ldc, int d,
 // (xi x d row-major) from the block's partial planes.
 __global__ void dump_reduce_kernel(const double* Zp, const double* Yp, int d, int xi, int ab, int w, float* Z,
                                    float* Y) {
-  const int tot = d * w;
+  const int tot = d * w, nch = dump_chunks(w);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
     double z = 0.0, y = 0.0;
-    for (int s = 0; s < kDumpChunks; ++s) { z += Zp[(size_t)s * tot + e]; y += Yp[(size_t)s * tot + e]; }
+    for (int s = 0; s < nch; ++s) { z += Zp[(size_t)s * tot + e]; y += Yp[(size_t)s * tot + e]; }
     const int c = e / w, a = e - c * w;
     Z[(size_t)c * xi + ab + a] = (float)z;   // Zp element e = c*w + a
     Y[(size_t)ab * d + e] = (float)y;        // Yp element e = a*d + c
@@ -465,8 +490,21 @@ as_status launch_si_rr_from_batch(cudaStream_t s, const double* G, int n2, int m
   AS_CUDA_TRY(cudaMemsetAsync(b.GY, 0, (size_t)n2 * k * sizeof(double), s));
   as_status st = gmul64(s, G, n2, m, k, b.Y, b.GY);
   if (st != AS_OK) return st;
-  rr2_kernel<<<1, 1024, 0, s>>>(n2, m, b.Y, b.GY, b.ritz, b.WU, b.GWU, status); count_launches(1);
-  AS_CUDA_TRY(cudaGetLastError());
+  // up to 16 blocks of 256 rows each; the partial sums (6 per block) and the
+  // barrier counter live in the free scratch b.tmp (n2 * 2 + 14 doubles or
+  // more, enough for 6 * ceil(n2 / 256) + 1)
+  const int nblk = std::max(1, std::min(16, (m + 255) / 256));
+  double* part = b.tmp;
+  unsigned* cnt = reinterpret_cast<unsigned*>(b.tmp + 6 * nblk);
+  AS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned), s));
+  int n2a = n2, ma = m;
+  const double* Ya = b.Y;
+  const double* GYa = b.GY;
+  double *ra = b.ritz, *wua = b.WU, *gwua = b.GWU;
+  int* sta = status;
+  void* args[] = {&n2a, &ma, &Ya, &GYa, &ra, &wua, &gwua, &part, &cnt, &sta};
+  AS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)rr2_coop_kernel, dim3(nblk), dim3(256), args, 0, s));
+  count_launches(1);
   return AS_OK;
 }
 
@@ -480,15 +518,15 @@ as_status launch_residual_gram(cudaStream_t s, const double* G, int n2, int m, c
 
 size_t dump_work_doubles(int d, int n2, int xi) {
   // partial planes of one column block + the FP32 coefficients
-  return (size_t)2 * kDumpChunks * d * std::min(xi, kDumpBlock) + ((size_t)3 * n2 * xi + 1) / 2;
+  return (size_t)2 * d * dump_plane_cols(xi) + ((size_t)3 * n2 * xi + 1) / 2;
 }
 
 as_status launch_dump(cudaStream_t s, float* C, int ldc, int d, int r, double* G, int n2, const double* WU,
                       const double* GWU, int k, int xi, float* Z, float* Y, double* work, const DumpMirrors& mir) {
-  const int wmax = std::min(xi, kDumpBlock);
+  const size_t plane = (size_t)d * dump_plane_cols(xi);   // doubles of each of Zp, Yp
   double* Zp = work;
-  double* Yp = work + (size_t)kDumpChunks * d * wmax;
-  float* WUf = reinterpret_cast<float*>(Yp + (size_t)kDumpChunks * d * wmax);
+  double* Yp = work + plane;
+  float* WUf = reinterpret_cast<float*>(Yp + plane);
   float* GWUf = WUf + (size_t)n2 * xi;
   float* GWUlo = GWUf + (size_t)n2 * xi;
   if (r > 0) {
@@ -498,7 +536,7 @@ as_status launch_dump(cudaStream_t s, float* C, int ldc, int d, int r, double* G
     const int w = std::min(kDumpBlock, xi - ab);
     for (int a0 = ab; a0 < ab + w; a0 += 8) {
       const int na = std::min(8, ab + w - a0);
-      dim3 grid((d + 127) / 128, kDumpChunks);
+      dim3 grid((d + 127) / 128, dump_chunks(w));
       dump_partial_kernel<<<grid, 128, 0, s>>>(C, ldc, d, r, WUf, GWUf, xi, a0, na, ab, w, Zp, Yp);
       count_launches(1);
     }
