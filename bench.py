@@ -42,11 +42,15 @@ FP64_NOMINAL_TFLOPS = 1.25
 # three corrections 3, FastTwoSum renormalisation 3, one add 1): the df64
 # eigensolver's peak is the FP32 issue rate x 2 flop / this count
 DF64_FP32_OPS_PER_FMA = 15
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel as
-# it stands (a full-size launch of `python bench.py --steps 1 --warmup 3
-# --forms bf16x6 --no-cpu-baseline --no-err --no-e2e`, grid 128, 2l = 2048);
-# the summary is committed under profiles/.  Set to None when the kernel changes.
-TRAFFIC_BYTES = {"batch_tc": 17.29e6 + 0.65e6}
+# DRAM traffic per launch from one ncu capture of the kernel as it stands
+# (launch 781 of batch_tc in `python bench.py --steps 1 --warmup 3 --forms
+# bf16x6 --no-cpu-baseline --no-err --no-e2e`, kpad = 1792; summary under
+# profiles/), as the ratio of the measured dram__bytes_read.sum +
+# dram__bytes_write.sum to that launch's algorithmic bytes (G's two BF16
+# levels read once, 4 kpad^2).  A launch's traffic grows with kpad^2 like its
+# algorithmic bytes, so the line's traffic is this ratio times the mean
+# algorithmic bytes of the timed launches.  Set to None when the kernel changes.
+TRAFFIC_RATIO = {"batch_tc": (13.152512e6 + 0.22656e6) / (4.0 * 1792 ** 2)}
 
 
 def _peaks():
@@ -319,7 +323,9 @@ def our_arm(args) -> None:
         roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak / DF64_FP32_OPS_PER_FMA, "unit": "TFLOP/s"}
         src = (f"df64 on the FP32 pipes: the FP32 SIMT peak ({fp32_peak:.1f} TFLOP/s) / "
                f"{DF64_FP32_OPS_PER_FMA} FP32 operations per df64 multiply-add")
-    roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": TRAFFIC_BYTES.get(top["name"]),
+    ratio = TRAFFIC_RATIO.get(top["name"])
+    traffic = ratio * top["bytes"] / max(1, top["launches"]) if ratio is not None and top["bytes"] > 0 else None
+    roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": traffic,
                  "kernel": top["name"],
                  "launches": top["launches"], "avg_launch_us": 1000 * top["total_ms"] / max(1, top["launches"]),
                  "peak_source": src})

@@ -470,7 +470,8 @@ as_status as_tc_gemm(int32_t M, int32_t N, int32_t K, const float* A, const floa
  * reads is written earlier in the same call): calls that overlap on the GPU
  * race.  The first call on a device, and the first after that device's
  * context was destroyed and made again (cudaDeviceReset), looks up the array's
- * address with a host-side driver query (no allocation).  AS_ENOTSUP if the
+ * address (cudaGetSymbolAddress, no allocation); make that first call on each
+ * device before any stream capture begins.  AS_ENOTSUP if the
  * driver entry point for the current context cannot be found. */
 as_status as_symeig_noalloc(int32_t n, const double* A, int32_t nev, double* evals, double* vecs, void* cuda_stream);
 

@@ -711,16 +711,17 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
     AS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(ncta), dim3(kTcThreads), args, smem, s));
     count_launches(1);
     if (prof) {
-      double m2 = 0.0, m1 = 0.0;
+      double m2 = 0.0;
       for (int t = 0; t < nb; ++t) {
         const double m = (double)(r0 + t + 1);
         m2 += m * m;
-        m1 += m;
       }
       const double prods = (double)(k_pi + 1) + 2.0 * (double)(q + 1);
       // the algorithmic work of the block is recorded when its decisions are
-      // taken (add_work); here the work issued for every row of the block
-      prof->end(PK_BATCH_TC, s, 0.0, 2.0 * npass / 3.0 * (double)kpad * kpad + 8.0 * m1 * prods, 2.0 * m2 * prods);
+      // taken (add_work); here the work issued for every row of the block, and
+      // the algorithmic DRAM bytes: the two BF16 levels of G read once (Y and
+      // the partial planes stay in L2)
+      prof->end(PK_BATCH_TC, s, 0.0, 4.0 * (double)kpad * kpad, 2.0 * m2 * prods);
     }
     return AS_OK;
   };

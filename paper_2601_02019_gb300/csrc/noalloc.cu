@@ -12,8 +12,10 @@
 // written earlier in the same call).  Calls whose work overlaps on the GPU
 // race with each other.  The first call on a device (and the first call after
 // that device's context was destroyed and made again, for example after
-// cudaDeviceReset, which loads the module and its array anew) looks up the
-// array's device address with a host-side driver query, which allocates nothing.
+// cudaDeviceReset, which loads the module and its array anew) does a one-time
+// set-up: it looks up the array's device address with cudaGetSymbolAddress,
+// which allocates nothing.  Make that first call on each device before any
+// stream capture begins.
 #include <mutex>
 
 #include "eig.cuh"
