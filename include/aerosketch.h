@@ -435,6 +435,14 @@ as_status sketch_profile(as_sketch* h, as_kernel_stat* out, int32_t cap, int32_t
 /* Clear the kernel-class timings. */
 as_status sketch_profile_reset(as_sketch* h);
 
+/* Restrict the AS_PROFILE timing to the kernel classes whose bits are set in
+ * class_mask: bit c stands for entry c of sketch_profile's list (a fixed
+ * order).  The other classes are no longer bracketed with CUDA events, which
+ * takes their event records (host calls on every block) off the update path;
+ * their counters stop growing.  All classes are timed by default.  A library
+ * service with no counterpart in the paper.  AS_EINVAL without AS_PROFILE. */
+as_status sketch_profile_select(as_sketch* h, uint32_t class_mask);
+
 /* Symmetric eigendecomposition on the current device, FP64 in and out: the
  * core factorisation that the FD shrink (Algorithm 4, through the Gram matrix
  * of the buffer) and the query (Algorithm 5) use.  n <= 256: one thread block

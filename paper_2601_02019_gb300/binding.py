@@ -19,6 +19,7 @@ AS_QUERY_DENSE = 0x4
 
 EXPORTED = ("sketch_create", "sketch_update", "sketch_query", "sketch_query_gram", "sketch_get_buffer", "sketch_get_gram",
             "sketch_merge", "sketch_stats", "sketch_trace", "sketch_profile", "sketch_profile_reset",
+            "sketch_profile_select",
             "sketch_destroy", "as_symeig", "as_symeig_noalloc", "as_tc_gemm", "as_status_str", "as_last_error",
             "as_inject_alloc_failure",
             "sketch_set_theta", "sketch_send_snapshots", "as_p5_create", "as_p5_round", "as_p5_query",
@@ -116,6 +117,7 @@ def load_library(path: str = LIB_PATH) -> ct.CDLL:
     L.sketch_trace.argtypes = [P, ct.POINTER(AsEvent), I64, ct.POINTER(I64)]
     L.sketch_profile.argtypes = [P, ct.POINTER(AsKernelStat), I32, ct.POINTER(I32)]
     L.sketch_profile_reset.argtypes = [P]
+    L.sketch_profile_select.argtypes = [P, ct.c_uint32]
     L.sketch_destroy.argtypes = [P]
     L.as_symeig.argtypes = [I32, P, I32, P, P]
     L.as_symeig_noalloc.argtypes = [I32, P, I32, P, P, P]
@@ -273,6 +275,20 @@ class Sketch:
 
     def profile_reset(self) -> None:
         _check(lib().sketch_profile_reset(self._h), "sketch_profile_reset")
+
+    def profile_select(self, names: list[str] | None) -> None:
+        """Time only the named kernel classes (None: all of them)."""
+        order = [k["name"] for k in self.profile()]
+        if names is None:
+            mask = 0xFFFFFFFF
+        else:
+            unknown = [n for n in names if n not in order]
+            if unknown:
+                raise ValueError(f"unknown kernel classes {unknown}; known: {order}")
+            mask = 0
+            for n in names:
+                mask |= 1 << order.index(n)
+        _check(lib().sketch_profile_select(self._h, mask), "sketch_profile_select")
 
     def merge(self, other: "Sketch") -> None:
         """Absorb other's whole query Gram (decomposability); other is unchanged."""

@@ -14,9 +14,10 @@
 //     next pass.  No atomics: results are bitwise reproducible.
 //   * bisection: several lanes per eigenvalue (multisection, the lane count
 //     picked per matrix order by the launch-shape autotuner) on df64 Sturm
-//     counts of T / ||T||; inverse iteration in FP64, one thread per
-//     eigenvalue, its tridiagonal factors staged through shared memory with
-//     cp.async.
+//     counts of T / ||T||; inverse iteration in df64 on T / ||T||, one
+//     thread per eigenvalue, its tridiagonal factors staged through shared
+//     memory with cp.async (FP64 for the rare eigenvector whose df64 iterate
+//     leaves the FP32 range).
 //   * back-transformation (df64, blocked): reflectors are grouped into
 //     compact-WY factors I - V T V^T; each block owns a slab of eigenvector
 //     columns in shared memory and applies the groups to it.
@@ -90,14 +91,16 @@ __global__ void cluster_mgs(int n, int nev, const double* norms, const double* e
 
 
 // ---- double-float (df64) kernels -------------------------------------------
-// T scaled by 1/||T|| in df64: dd[i] = d_i / tn, e2[i] = (e_i / tn)^2.  With
-// |entries| <= 1 the Sturm recurrence stays far from FP32 overflow.
-__global__ void tri_scale_df(int n, TriWork w, const double* norms, df64* dd, df64* e2) {
+// T scaled by 1/||T|| in df64: dd[i] = d_i / tn, ee[i] = e_i / tn and
+// e2[i] = (e_i / tn)^2.  With |entries| <= 1 the Sturm recurrence and the
+// inverse iteration stay far from FP32 overflow.
+__global__ void tri_scale_df(int n, TriWork w, const double* norms, df64* dd, df64* e2, df64* ee) {
   const double tn = norms[0];
   const double inv = (tn > 0.0) ? 1.0 / tn : 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     dd[i] = df_from_double(w.d[i] * inv);
     const double es = (i + 1 < n) ? w.e[i] * inv : 0.0;
+    ee[i] = df_from_double(es);
     e2[i] = df_from_double(es * es);
   }
 }
@@ -146,7 +149,6 @@ __global__ void bisect_df(int n, int nev, const double* norms, const df64* dd, c
   const int j = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / kBisLanes) + grp;
   const bool active = j < nev;
   const double tnorm = norms[0];
-  const double eps = 2.220446049250313e-16;
   const int idx = n - 1 - j;
   const float pivmin = 0x1p-100f;
   const double tol = 0x1p-44;
@@ -178,8 +180,9 @@ __global__ void bisect_df(int n, int nev, const double* norms, const df64* dd, c
   evals[j] = lam * norms[3];                                            // exact power-of-two unscaling
 }
 
-// Inverse iteration for the eigenvalues found by bisect_df, one thread per
-// eigenvector, up to 32 eigenvectors per block: the LU factorisation and the solves
+// Inverse iteration in FP64 for the eigenvalues found by bisect_df (the
+// fallback of invit_dd below, for the eigenvectors `only` flags), one thread
+// per eigenvector, up to 32 eigenvectors per block: the LU factorisation and the solves
 // are FP64 recurrences, and FP64 issue is scarce on this part, so no lane of a
 // warp should idle.  lam = evals[j] / norms[3] undoes the exact power-of-two
 // unscaling.
@@ -208,15 +211,18 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __global__ void __launch_bounds__(32) invit_df(int n, int nev, TriWork w, const double* norms, const double* evals,
-                                               double* X, int ldx, double* lu) {
+                                               double* X, int ldx, double* lu, const int* only) {
   // [buffer][array][step][lane]
   __shared__ double stg[2][kInvitArrays][kInvitTile][32];
   const int lane = threadIdx.x;
   // the block is one (possibly partial) warp: name only its threads
   const unsigned wmask = (blockDim.x >= 32) ? 0xffffffffu : ((1u << blockDim.x) - 1u);
   const int j = blockIdx.x * blockDim.x + lane;
-  const bool valid = j < nev;
-  const int jj = valid ? j : nev - 1;   // an in-range column for the copies of lanes past nev
+  // with `only`, just the eigenvectors it flags (the others' lanes compute
+  // and store nothing)
+  const bool valid = j < nev && (!only || only[j] != 0);
+  if (only && __all_sync(wmask, !valid)) return;
+  const int jj = (j < nev) ? j : nev - 1;   // an in-range column for the copies of lanes past nev
   const double tnorm = norms[0];
   const double eps = 2.220446049250313e-16;
   const double lam = (tnorm == 0.0) ? 0.0 : evals[jj] / norms[3];
@@ -350,6 +356,173 @@ __global__ void __launch_bounds__(32) invit_df(int n, int nev, TriWork w, const 
     for (int i = 0; i < n; ++i) x[(size_t)i * sx] *= rhs;
 }
 
+// The same inverse iteration in df64 on the FP32 pipes, on T / ||T|| (dd, ee):
+// the FP64 recurrences of invit_df are long dependent chains of slow FP64
+// instructions on this part.  Same factorisation (partial pivoting, pivots
+// kept at least eps in magnitude), same three iterations from ii_start, same
+// storage (a df64 value in each 8-byte slot of lu and X), same staging.  The
+// sum of squares is accumulated in df64 (compensated) and the reciprocal norm
+// taken with df_rsqrt.  An iterate that leaves the FP32 range (several nearly
+// zero pivots on one eigenvector) is flagged in bad[j] and left for invit_df,
+// which the launcher runs on the flagged eigenvectors afterwards.
+__global__ void __launch_bounds__(32) invit_dd(int n, int nev, const df64* dd, const df64* ee, const double* norms,
+                                               const double* evals, double* X, int ldx, double* lu, int* bad) {
+  __shared__ df64 stg[2][kInvitArrays][kInvitTile][32];
+  const int lane = threadIdx.x;
+  const unsigned wmask = (blockDim.x >= 32) ? 0xffffffffu : ((1u << blockDim.x) - 1u);
+  const int j = blockIdx.x * blockDim.x + lane;
+  const bool valid = j < nev;
+  const int jj = valid ? j : nev - 1;
+  const double tnorm = norms[0];
+  if (tnorm == 0.0) {   // zero matrix: any orthonormal basis is an eigenbasis
+    if (valid) {
+      for (int i = 0; i < n; ++i) X[(size_t)i * ldx + j] = (i == j) ? 1.0 : 0.0;
+      bad[j] = 0;
+    }
+    return;
+  }
+  const df64 lam = df_from_double(evals[jj] / norms[3] / tnorm);
+  const float tiny = 2.220446049250313e-16f;   // eps * ||T / ||T|| ||
+  df64* u0 = reinterpret_cast<df64*>(lu) + (size_t)(0 * n) * nev + jj;   // 1 / pivot
+  df64* u1 = reinterpret_cast<df64*>(lu) + (size_t)(1 * n) * nev + jj;
+  df64* u2 = reinterpret_cast<df64*>(lu) + (size_t)(2 * n) * nev + jj;
+  df64* ll = reinterpret_cast<df64*>(lu) + (size_t)(3 * n) * nev + jj;
+  df64* pv = reinterpret_cast<df64*>(lu) + (size_t)(4 * n) * nev + jj;
+  const df64 zero{0.f, 0.f}, one{1.f, 0.f};
+  df64 cd = df_sub(dd[0], lam), cs = ee[0];
+  for (int i = 0; i + 1 < n; ++i) {
+    const df64 b = ee[i];
+    const df64 nd = df_sub(dd[i + 1], lam), ns = (i + 2 < n) ? ee[i + 1] : zero;
+    df64 piv, U1, U2, L, P;
+    if (fabsf(cd.hi) >= fabsf(b.hi)) {
+      if (cd.hi == 0.f) cd = df64{tiny, 0.f};
+      const df64 li = df_div_fast(b, cd);
+      piv = cd; U1 = cs; U2 = zero; L = li; P = zero;
+      cd = df_sub(nd, df_mul(li, cs));
+      cs = ns;
+    } else {
+      const df64 li = df_div_fast(cd, b);
+      piv = b; U1 = nd; U2 = ns; L = li; P = one;
+      cd = df_sub(cs, df_mul(li, nd));
+      cs = df_neg(df_mul(li, ns));
+    }
+    if (fabsf(piv.hi) < tiny) piv = df64{piv.hi < 0.f ? -tiny : tiny, 0.f};
+    if (valid) {
+      u0[(size_t)i * nev] = df_div_fast(one, piv);
+      u1[(size_t)i * nev] = U1; u2[(size_t)i * nev] = U2;
+      ll[(size_t)i * nev] = L; pv[(size_t)i * nev] = P;
+    }
+  }
+  if (fabsf(cd.hi) < tiny) cd = df64{cd.hi < 0.f ? -tiny : tiny, 0.f};
+  if (valid) u0[(size_t)(n - 1) * nev] = df_div_fast(one, cd);
+  __threadfence_block();
+  __syncwarp(wmask);
+  df64* x = reinterpret_cast<df64*>(X) + jj;
+  const size_t sx = (size_t)ldx;
+  df64 rhs = one;
+  bool finite = true;
+  for (int it = 0; it < 3; ++it) {
+    const int nsteps = n - 1;
+    const int ntiles = (nsteps + kInvitTile - 1) / kInvitTile;
+    auto stage_fwd = [&](int t, int buf) {
+      const int i0 = t * kInvitTile, cnt = min(kInvitTile, nsteps - i0);
+      for (int u = 0; u < cnt; ++u) {
+        const size_t i = (size_t)(i0 + u);
+        cp_async8(reinterpret_cast<double*>(&stg[buf][0][u][lane]), reinterpret_cast<const double*>(ll + i * nev));
+        cp_async8(reinterpret_cast<double*>(&stg[buf][1][u][lane]), reinterpret_cast<const double*>(pv + i * nev));
+        if (it > 0)
+          cp_async8(reinterpret_cast<double*>(&stg[buf][2][u][lane]), reinterpret_cast<const double*>(x + (i + 1) * sx));
+      }
+      cp_async_commit();
+    };
+    df64 cur = (it == 0) ? df_from_double(ii_start(0, jj)) : df_mul(x[0], rhs);
+    if (ntiles > 0) stage_fwd(0, 0);
+    for (int t = 0; t < ntiles; ++t) {
+      if (t + 1 < ntiles) {
+        stage_fwd(t + 1, (t + 1) & 1);
+        cp_async_wait1();
+      } else {
+        cp_async_wait0();
+      }
+      const int buf = t & 1, i0 = t * kInvitTile, cnt = min(kInvitTile, nsteps - i0);
+      for (int u = 0; u < cnt; ++u) {
+        const int i = i0 + u;
+        df64 yi = cur;
+        df64 yn = (it == 0) ? df_from_double(ii_start(i + 1, jj)) : df_mul(stg[buf][2][u][lane], rhs);
+        if (stg[buf][1][u][lane].hi != 0.f) { const df64 tt = yi; yi = yn; yn = tt; }
+        yn = df_sub(yn, df_mul(stg[buf][0][u][lane], yi));
+        if (valid) x[(size_t)i * sx] = yi;
+        cur = yn;
+      }
+    }
+    if (valid) x[(size_t)(n - 1) * sx] = cur;
+    __threadfence_block();
+    __syncwarp(wmask);
+    const int btiles = (n + kInvitTile - 1) / kInvitTile;
+    auto stage_back = [&](int t, int buf) {
+      const int ihi = n - 1 - t * kInvitTile, cnt = min(kInvitTile, ihi + 1);
+      for (int u = 0; u < cnt; ++u) {
+        const size_t i = (size_t)(ihi - u);
+        cp_async8(reinterpret_cast<double*>(&stg[buf][0][u][lane]), reinterpret_cast<const double*>(x + i * sx));
+        cp_async8(reinterpret_cast<double*>(&stg[buf][1][u][lane]), reinterpret_cast<const double*>(u0 + i * nev));
+        cp_async8(reinterpret_cast<double*>(&stg[buf][2][u][lane]), reinterpret_cast<const double*>(u1 + i * nev));
+        cp_async8(reinterpret_cast<double*>(&stg[buf][3][u][lane]), reinterpret_cast<const double*>(u2 + i * nev));
+      }
+      cp_async_commit();
+    };
+    df64 xn1 = zero, xn2 = zero;
+    float mx = 0.f, ss = 0.f, se = 0.f;
+    bool nan = false;
+    stage_back(0, 0);
+    for (int t = 0; t < btiles; ++t) {
+      if (t + 1 < btiles) {
+        stage_back(t + 1, (t + 1) & 1);
+        cp_async_wait1();
+      } else {
+        cp_async_wait0();
+      }
+      const int buf = t & 1, ihi = n - 1 - t * kInvitTile, cnt = min(kInvitTile, ihi + 1);
+      for (int u = 0; u < cnt; ++u) {
+        const df64 xi = df_mul(df_rank2(stg[buf][0][u][lane], stg[buf][2][u][lane], xn1, stg[buf][3][u][lane], xn2),
+                               stg[buf][1][u][lane]);
+        if (valid) x[(size_t)(ihi - u) * sx] = xi;
+        xn2 = xn1; xn1 = xi;
+        mx = fmaxf(mx, fabsf(xi.hi));
+        nan = nan || (xi.hi != xi.hi);
+        df_dot_step(xi, xi, ss, se);
+      }
+    }
+    __threadfence_block();
+    __syncwarp(wmask);
+    if (nan || !(mx <= 3.0e38f)) {   // the iterate left the FP32 range (or is not a number)
+      finite = false;
+      break;
+    }
+    const df64 sq = df_dot_finish(ss, se);
+    if (sq.hi > 0.f && sq.hi <= 3.0e38f) {   // false also when the squares overflowed (NaN)
+      rhs = df_rsqrt(sq);
+    } else {   // squares out of range: normalise in two scaled passes
+      const float rmx = (mx > 0.f) ? 1.f / mx : 0.f;
+      float ns = 0.f, ne = 0.f;
+      for (int i = 0; i < n; ++i) {
+        const df64 v = df_mul(x[(size_t)i * sx], df64{rmx, 0.f});
+        df_dot_step(v, v, ns, ne);
+      }
+      const df64 nrm = df_dot_finish(ns, ne);
+      rhs = (nrm.hi > 0.f) ? df_mul(df64{rmx, 0.f}, df_rsqrt(nrm)) : zero;
+    }
+  }
+  if (valid) {
+    bad[j] = finite ? 0 : 1;
+    double* xd = X + j;
+    if (finite)
+      for (int i = 0; i < n; ++i) {
+        const df64 v = df_mul(x[(size_t)i * sx], rhs);
+        xd[(size_t)i * sx] = (double)v.hi + (double)v.lo;
+      }
+  }
+}
+
 __device__ __forceinline__ df64 df_warp_sum(df64 v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -394,24 +567,6 @@ __global__ void to_df_inplace(double* A, int lda, int n, const double* scale) {
     const df64 v = df_from_double(*p * sc);
     *reinterpret_cast<df64*>(p) = v;
   }
-}
-
-// Sum over the block of a df64 value; every thread gets the result.
-__device__ __forceinline__ df64 df_block_sum(df64 v, df64* red) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nw = (blockDim.x + 31) >> 5;
-  v = df_warp_sum(v);
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    df64 t = red[0];
-    for (int q = 1; q < nw; ++q) t = df_add(t, red[q]);
-    red[0] = t;
-  }
-  __syncthreads();
-  const df64 t = red[0];
-  __syncthreads();
-  return t;
 }
 
 // v_j = (x_j - alpha [j == 0]) / vn in df64 (zero vector when szero).
@@ -872,7 +1027,8 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
   if (prof) prof->end(PK_EIG_TRI, s, 4.0 / 3.0 * (double)n * n * n, 8.0 * (double)n * n);
   if (prof) prof->begin(PK_EIG_SOLVE, s);
   tri_norm<<<1, 256, 0, s>>>(n, w, norms); count_launches(1);
-  tri_scale_df<<<(n + 255) / 256, 256, 0, s>>>(n, w, norms, dd, e2); count_launches(1);
+  tri_scale_df<<<(n + 255) / 256, 256, 0, s>>>(n, w, norms, dd, e2, reinterpret_cast<df64*>(w.v));
+  count_launches(1);
   {
     // multisection lanes per eigenvalue, tuned per matrix order
     auto bisect = [&](int lanes) -> as_status {
@@ -896,23 +1052,28 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
       tst = bisect(lanes);
       if (tst != AS_OK) return tst;
     }
-    // eigenvectors per block (one thread each), tuned per matrix order: the
-    // recurrences are FP64, and fewer eigenvectors per block spread them over
-    // more SMs' FP64 units
+    // inverse iteration in df64, eigenvectors per block (one thread each)
+    // tuned per matrix order; then the FP64 kernel redoes the eigenvectors
+    // whose df64 iterate left the FP32 range (a warp with none returns at once)
+    df64* ee = reinterpret_cast<df64*>(w.v);      // free after the reduction
+    int* bad = reinterpret_cast<int*>(w.p2);      // n doubles >= nev ints
     auto invit = [&](int per) -> as_status {
-      invit_df<<<(nev + per - 1) / per, per, 0, s>>>(n, nev, w, norms, evals, X, ldx, lu);
+      invit_dd<<<(nev + per - 1) / per, per, 0, s>>>(n, nev, dd, ee, norms, evals, X, ldx, lu, bad);
       count_launches(1);
       AS_CUDA_TRY(cudaGetLastError());
       return AS_OK;
     };
     static const int kInvitChoices[3] = {32, 16, 8};
-    const int per = tune_pick(s, "invit_df", ((long long)n << 20) | (long long)nev, kInvitChoices, 3, invit, &tst,
+    const int per = tune_pick(s, "invit_dd", ((long long)n << 20) | (long long)nev, kInvitChoices, 3, invit, &tst,
                               &ran);
     if (tst != AS_OK) return tst;
     if (!ran) {
       tst = invit(per);
       if (tst != AS_OK) return tst;
     }
+    invit_df<<<(nev + 31) / 32, 32, 0, s>>>(n, nev, w, norms, evals, X, ldx, lu, bad);
+    count_launches(1);
+    AS_CUDA_TRY(cudaGetLastError());
   }
   cluster_mgs<<<1, 512, 0, s>>>(n, nev, norms, evals, X, ldx); count_launches(1);
   if (prof) prof->end(PK_EIG_SOLVE, s, 0.0, 0.0);

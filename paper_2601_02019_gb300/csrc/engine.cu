@@ -77,6 +77,7 @@ struct EventProf final : Prof {
   int64_t launches[PK_COUNT] = {};
   double ms[PK_COUNT] = {}, flops[PK_COUNT] = {}, bytes[PK_COUNT] = {}, issued[PK_COUNT] = {};
   cudaEvent_t open_ev[PK_COUNT] = {};
+  uint32_t mask = ~0u;   // classes bracketed with events (sketch_profile_select)
 
   cudaEvent_t get() {
     if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
@@ -85,10 +86,12 @@ struct EventProf final : Prof {
     return e;
   }
   void begin(int cls, cudaStream_t s) override {
+    if (!((mask >> cls) & 1u)) return;
     open_ev[cls] = get();
     cudaEventRecord(open_ev[cls], s);
   }
   void end(int cls, cudaStream_t s, double f, double b, double iss = -1.0) override {
+    if (!((mask >> cls) & 1u)) return;
     cudaEvent_t e = get();
     cudaEventRecord(e, s);
     pending.push_back(Pending{cls, open_ev[cls], e, f, b, iss < 0.0 ? f : iss});
@@ -1805,6 +1808,14 @@ as_status sketch_profile(as_sketch* h, as_kernel_stat* out, int32_t cap, int32_t
     ++n;
   }
   *count = n;
+  return AS_OK;
+}
+
+as_status sketch_profile_select(as_sketch* h, uint32_t class_mask) {
+  if (!h || !h->prof) return AS_EINVAL;
+  AS_CUDA_TRY(cudaStreamSynchronize(h->s));
+  h->prof->resolve();
+  h->prof->mask = class_mask;
   return AS_OK;
 }
 
