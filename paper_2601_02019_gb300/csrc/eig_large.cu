@@ -604,12 +604,15 @@ struct TriPersist {
   int* status;
 };
 
-constexpr int kTriThreads = 512;
-constexpr int kTriWarps = kTriThreads / 32;
-constexpr int kTriUnroll = 16;  // row entries in flight per lane
 constexpr int kTriPre = 4;      // entries of p and of row r per thread loaded at the top of a pass
 
+// kTriThreads threads per CTA (one CTA per SM), kTriUnroll row entries in
+// flight per lane: the launcher lets the launch-shape autotuner pick among a
+// few shapes per matrix order (more warps hide more latency; fewer leave
+// more registers to each thread's independent entries).
+template <int kTriThreads, int kTriUnroll>
 __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersist t) {
+  constexpr int kTriWarps = kTriThreads / 32;
   extern __shared__ df64 smp[];
   const int n = t.n, G = gridDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   df64* vcur = smp;           // v_{r-1}[j], j in [r, n)
@@ -621,22 +624,28 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
   __shared__ int s_ok;
   // Every thread owns the entries j = r + tid + kTriThreads u of the pass's
   // vectors (row r, w, v_r) and is the only one to write them before the
-  // barrier that publishes v_r to the sweep; the pass has four CTA barriers
-  // (after w, after the norm partials of row r, after v_r, and the grid
-  // barrier's own) besides the grid barrier.
+  // barrier that publishes v_r to the sweep; the pass has four CTA barriers:
+  // after the norm partials of row r, after v_r, and the two around the grid
+  // arrival.
   for (int r = 0; r <= n - 2; ++r) {
     const bool upd = r >= 1;
     const df64* arow = t.A + (size_t)r * t.lda;
     // the entries of p_{r-1} and of row r are loaded together with the partial
     // sums below: one L2 round trip (they do not depend on the coefficient)
     df64 pjr[kTriPre], ajr[kTriPre];
+    const df64* pin = ((r - 1) & 1) ? t.p[1] : t.p[0];
 #pragma unroll
     for (int u = 0; u < kTriPre; ++u) {
       const int j = r + tid + kTriThreads * u;
-      const df64* pin = ((r - 1) & 1) ? t.p[1] : t.p[0];
       pjr[u] = (upd && j < n) ? pin[j] : df64{0.f, 0.f};
       ajr[u] = (j < n) ? arow[j] : df64{0.f, 0.f};
     }
+    // p_{r-1}[r] in every thread: each thread forms w_{r-1}[r] itself (the
+    // same operations as the thread that stores wk[r]), so no block barrier
+    // is needed between w and the update of row r; every other entry of w a
+    // thread uses there is one it computed
+    const df64 pr = upd ? pin[r] : df64{0.f, 0.f};
+    df64 wr{0.f, 0.f};
     if (upd) {
       // c = v^T p from the per-CTA partials: every warp sums them itself, in the
       // same order, so all threads hold the same value without a barrier
@@ -654,7 +663,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
       }
       c = df_warp_sum(c);
       const df64 c2{2.f * c.hi, 2.f * c.lo};
-      const df64* pin = ((r - 1) & 1) ? t.p[1] : t.p[0];
+      wr = df_sub(df64{2.f * pr.hi, 2.f * pr.lo}, df_mul(c2, vcur[r]));
 #pragma unroll
       for (int u = 0; u < kTriPre; ++u) {
         const int j = r + tid + kTriThreads * u;
@@ -664,11 +673,8 @@ __global__ void __launch_bounds__(kTriThreads, 1) tri_persist_df(const TriPersis
         const df64 pj = pin[j];
         wk[j] = df_sub(df64{2.f * pj.hi, 2.f * pj.lo}, df_mul(c2, vcur[j]));
       }
-      __syncwarp();
-      __syncthreads();
     }
     const df64 vr = upd ? vcur[r] : df64{0.f, 0.f};
-    const df64 wr = upd ? wk[r] : df64{0.f, 0.f};
     if (blockIdx.x == 0) {
       if (upd)
         for (int j = r + tid; j < n; j += blockDim.x) t.A[(size_t)(r - 1) * t.lda + j] = vcur[j];
@@ -1010,19 +1016,49 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
     AS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = std::max(1, std::min(sms, nparts_max));
     const size_t smem = 3 * (size_t)n * sizeof(df64);
-    AS_CUDA_TRY(as_raise_smem_limit((const void*)tri_persist_df, smem));
-    int per = 0;
-    AS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tri_persist_df, kTriThreads, smem));
-    if ((long long)per * sms < grid) return AS_ENOTSUP;
-    AS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned), s));
     TriPersist tp{};
     tp.A = Ad; tp.lda = lda; tp.n = n;
     tp.p[0] = reinterpret_cast<df64*>(w.p); tp.p[1] = reinterpret_cast<df64*>(w.p2);
     tp.q[0] = reinterpret_cast<df64*>(w.part); tp.q[1] = reinterpret_cast<df64*>(w.part2);
     tp.d = w.d; tp.e = w.e; tp.cnt = cnt; tp.status = status;
-    void* args[] = {&tp};
-    AS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)tri_persist_df, dim3(grid), dim3(kTriThreads), args, smem, s));
-    count_launches(1);
+    // The reduction overwrites the matrix, so a tuning run starts from a copy
+    // of the df64 matrix kept in lu (free until the inverse iteration); when
+    // lu is too small for it (few eigenvectors) the default shape runs untuned.
+    const size_t abytes = (size_t)n * lda * sizeof(double);
+    const bool can_tune = (size_t)lda <= 5 * (size_t)nev;
+    bool tuning = false, saved = false;
+    auto tri = [&](int shape) -> as_status {
+      if (tuning) {
+        if (!saved) AS_CUDA_TRY(cudaMemcpyAsync(lu, A, abytes, cudaMemcpyDeviceToDevice, s));
+        else AS_CUDA_TRY(cudaMemcpyAsync(A, lu, abytes, cudaMemcpyDeviceToDevice, s));
+        saved = true;
+      }
+      const void* fn = shape == 1 ? (const void*)tri_persist_df<256, 16>
+                     : shape == 2 ? (const void*)tri_persist_df<512, 8>
+                                  : (const void*)tri_persist_df<512, 16>;
+      const int threads = shape == 1 ? 256 : 512;
+      AS_CUDA_TRY(as_raise_smem_limit(fn, smem));
+      int per = 0;
+      AS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem));
+      if ((long long)per * sms < grid) return AS_ENOTSUP;
+      AS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned), s));
+      void* args[] = {&tp};
+      AS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, smem, s));
+      count_launches(1);
+      return AS_OK;
+    };
+    // shapes (threads, entries in flight): (512, 16), (256, 16), (512, 8)
+    static const int kTriShapes[3] = {0, 1, 2};
+    as_status tst = AS_OK;
+    bool ran = false;
+    tuning = can_tune;   // copies are made only while candidates are timed
+    const int shape = can_tune ? tune_pick(s, "tri_persist_df", n, kTriShapes, 3, tri, &tst, &ran) : 0;
+    tuning = false;
+    if (tst != AS_OK) return tst;
+    if (!ran) {   // a cached or default choice, straight on A
+      tst = tri(shape);
+      if (tst != AS_OK) return tst;
+    }
   }
   if (prof) prof->end(PK_EIG_TRI, s, 4.0 / 3.0 * (double)n * n * n, 8.0 * (double)n * n);
   if (prof) prof->begin(PK_EIG_SOLVE, s);

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _rows(n=600, d=256):
-    return low_rank_noisy(n, d, 12, spectrum("harmonic", 12), stream=3)
+    return low_rank_noisy(n, d, 12, spectrum("powerlaw", 12), stream=3)
 
 
 @pytest.mark.parametrize("prec", [0, 3])
