@@ -184,7 +184,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
   __shared__ __align__(8) uint64_t full_bar[kTcStages];
   __shared__ __align__(8) uint64_t empty_bar[kTcStages];
   __shared__ __align__(8) uint64_t done_bar;
-  __shared__ __align__(8) uint64_t red_bar;   // the reduction's bulk copies of the K-split rows
   __shared__ uint32_t tmem_base_s;
   __shared__ int fail_s;
   __shared__ float4 coef[kTcMaxCols / 2];
@@ -202,7 +201,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
   if (tid == 0) {
     for (int s = 0; s < kTcStages; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
     mbar_init(&done_bar, 1);
-    mbar_init(&red_bar, 1);
     fail_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -434,42 +432,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
     if (!rb_ok_s) { alive = false; break; }
 
     // ---- reduction phase: rows [rw0, rw1) of row block rb of Y_{it+1} = Z C_it ----
-    // The K-split planes' rows of this CTA are first staged in shared memory
-    // (the ring is idle between the last MMA and the next product): warp 0's
-    // lanes issue one bulk copy per (plane, row) into rows padded by 4 floats,
-    // which keeps the lanes' float2 reads on distinct banks, all completing
-    // on red_bar.  A group of lpp lanes (a half warp for up to 16 rows, else
-    // a warp) takes one column pair, one row per lane: the K-split partials
-    // of its row are summed in the order k = 0, 1, ..., the row of Y_{it+1}
-    // is written in FP32 and BF16 levels (consecutive lanes, consecutive
-    // rows: coalesced), and the pair's partial sums are reduced across the
-    // group.
+    // A group of lpp lanes (a half warp for up to 16 rows, else a warp) takes
+    // one column pair, one row per lane: the K-split planes of its row are
+    // summed in the order k = 0, 1, ..., the row of Y_{it+1} is written in FP32
+    // and BF16 levels (consecutive lanes, consecutive rows: coalesced), and the
+    // pair's partial sums are reduced across the group.  The loads of two
+    // steps are issued before either step's arithmetic.
     const int rw0 = rb * UM + ks * a.rpb, rw1 = min(rb * UM + UM, rw0 + a.rpb);
     const int R = max(0, rw1 - rw0);
-    const int rstride = a.nc + 4;                       // floats per staged row
-    const float* stage = reinterpret_cast<const float*>(smem);
-    if (R > 0) {
-      if (warp == 0) {
-        const uint32_t rbytes = (uint32_t)a.nc * 4u;
-        if (lane == 0) mbar_expect_tx(&red_bar, rbytes * (uint32_t)(a.nks * R));
-        __syncwarp();
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");          // the row block's products, acquired by warp 1
-        asm volatile("fence.proxy.async.global;" ::: "memory");   // written through the generic proxy
-        for (int e = lane; e < a.nks * R; e += 32) {
-          const int k = e / R, rr = e - k * R;
-          bulk_load(smem + (size_t)e * rstride * 4, part + (size_t)k * a.pplane + (size_t)(rw0 + rr) * a.nc, rbytes,
-                    &red_bar);
-        }
-      }
-      const bool got = mbar_wait(&red_bar, (uint32_t)it & 1u);
-      if (__syncthreads_or(got ? 0 : 1)) {
-        if (tid == 0) set_status(a.status, AS_ETIMEOUT);
-        // the copies may still be in flight: wait for them (bounded) before leaving
-        if (!got) (void)mbar_wait(&red_bar, (uint32_t)it & 1u);
-        alive = false;
-        break;
-      }
-    }
     const int lpp = (R <= 16) ? 16 : 32;
     const int sub = (lpp == 16) ? (lane >> 4) : 0, rl = lane & (lpp - 1);
     const int pstep = kTcThreads / lpp;   // pairs per step (all warps)
@@ -482,10 +452,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
       for (int h = 0; h < 2; ++h) {
         const int pl = pb0 + h * pstep + warp * (32 / lpp) + sub;
         const bool on = pl < nact && row_on;
-        const float* pp = stage + (size_t)rl * rstride + 2 * (pa0 + pl);
+        const float* pp = part + (size_t)row * a.nc + 2 * (pa0 + pl);
 #pragma unroll
         for (int k = 0; k < kTcMaxSplits; ++k)
-          zz[h][k] = (on && k < a.nks) ? *reinterpret_cast<const float2*>(pp + (size_t)k * R * rstride)
+          zz[h][k] = (on && k < a.nks) ? __ldcg(reinterpret_cast<const float2*>(pp + (size_t)k * a.pplane))
                                        : make_float2(0.f, 0.f);
       }
 #pragma unroll
@@ -564,10 +534,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
         }
       }
     }
-    // the BF16 levels feed other CTAs' TMA loads, and the next TMA loads
-    // overwrite the staged rows just read: both order generic accesses before
-    // async-proxy ones
-    asm volatile("fence.proxy.async;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");   // the BF16 levels feed other CTAs' TMA loads
     __syncwarp();
     __syncthreads();
     if (tid == 0) st_release_u32(a.flags + blk, (unsigned)(it + 1));
@@ -615,10 +582,8 @@ __global__ void tc_mirror_kernel(const double* G, int n2, int valid, int m, __nv
   const int q0 = (p < valid) ? valid : 0;
   for (int q = q0 + threadIdx.x; q < m; q += blockDim.x) {
     const double x = G[(size_t)p * n2 + q];
-    const __nv_bfloat16 l0 = __double2bfloat16(x);
-    const double r1 = x - (double)__bfloat162float(l0);
-    const __nv_bfloat16 l1 = __double2bfloat16(r1);
-    const __nv_bfloat16 l2 = __double2bfloat16(r1 - (double)__bfloat162float(l1));
+    __nv_bfloat16 l0, l1, l2;
+    g_levels(x, l0, l1, l2);
     __nv_bfloat16* o = Gb + (size_t)p * ldg + q;
     o[0] = l0;
     o[level] = l1;

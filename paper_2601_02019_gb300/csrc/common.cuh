@@ -2,6 +2,7 @@
 // plumbing, block reductions and the Philox4x64-10 generator.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -88,6 +89,20 @@ __device__ __forceinline__ void gauss4(Key key, uint64_t purpose, uint64_t i, ui
 // ---------------------------------------------------------------------------
 // Reductions.
 // ---------------------------------------------------------------------------
+// BF16 levels of a G entry for the tensor-core products: x0 = bf16(x),
+// x1 = bf16(x - x0), x2 = bf16(x - x0 - x1), formed from x rounded to FP32.
+// Each difference is exact in FP32 (a level is its operand rounded to 8 bits,
+// within a factor of two of it), so no FP64 instruction is needed beyond the
+// one conversion; the levels carry about 24 bits of x, as many as the FP32
+// rounding keeps.
+__device__ __forceinline__ void g_levels(double x, __nv_bfloat16& l0, __nv_bfloat16& l1, __nv_bfloat16& l2) {
+  const float xf = __double2float_rn(x);
+  l0 = __float2bfloat16_rn(xf);
+  const float r1 = xf - __bfloat162float(l0);
+  l1 = __float2bfloat16_rn(r1);
+  l2 = __float2bfloat16_rn(r1 - __bfloat162float(l1));
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -104,18 +104,52 @@ __global__ void dot_kernel(const double* x, const double* y, int m, const int* z
   if (threadIdx.x == 0) *out = (*zero) ? 0.0 : s;
 }
 
-// S = sym(A^T B) over the first m rows (A, B row-major n2 x k).
+// S = sym(A^T B) over the first m rows (A, B row-major n2 x k).  For k <= 8
+// every thread accumulates all k (k + 1) / 2 entries over its rows in one pass
+// (a row's k values are contiguous), and the entries are then reduced
+// together, each in the order of block_sum: a warp butterfly, then warp 0 over
+// the warps' sums.
 __device__ void block_gram(int m, int k, const double* A, const double* B, double* S, double* red) {
   if (k <= 8) {
-    for (int a = 0; a < k; ++a)
-      for (int c = a; c < k; ++c) {
-        double acc = 0.0;
-        for (int p = threadIdx.x; p < m; p += blockDim.x)
-          acc += 0.5 * (A[(size_t)p * k + a] * B[(size_t)p * k + c] + A[(size_t)p * k + c] * B[(size_t)p * k + a]);
-        acc = block_sum(acc, red);
-        if (threadIdx.x == 0) { S[a * k + c] = acc; S[c * k + a] = acc; }
+    constexpr int kT = 36;   // entries (a, c), a <= c < 8
+    __shared__ double wsum[32][kT];
+    double acc[kT];
+#pragma unroll
+    for (int t = 0; t < kT; ++t) acc[t] = 0.0;
+    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+      double ar[8], br[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        ar[a] = (a < k) ? A[(size_t)p * k + a] : 0.0;
+        br[a] = (a < k) ? B[(size_t)p * k + a] : 0.0;
       }
+      int t = 0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = a; c < 8; ++c, ++t)
+          if (c < k) acc[t] += 0.5 * (ar[a] * br[c] + ar[c] * br[a]);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int t = 0; t < kT; ++t) {
+      const double v = warp_sum(acc[t]);
+      if (lane == 0) wsum[wid][t] = v;
+    }
     __syncthreads();
+    if (wid == 0) {
+      int t = 0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = a; c < 8; ++c, ++t) {
+          if (c >= k) continue;
+          const double v = warp_sum((lane < nw) ? wsum[lane][t] : 0.0);
+          if (lane == 0) { S[a * k + c] = v; S[c * k + a] = v; }
+        }
+    }
+    __syncthreads();
+    (void)red;
     return;
   }
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
@@ -134,7 +168,7 @@ __device__ void block_gram(int m, int k, const double* A, const double* B, doubl
 
 // One block: SVQB of X with S = X^T X (or X^T Xg for the G inner product);
 // X, Xg <- (.) V D^-1/2 on the kept columns.  Rows >= m are zero.
-__global__ void svqb_kernel(int n2, int m, int k, double* X, double* Xg, int g_inner, double* S, double* V,
+__global__ void __launch_bounds__(512) svqb_kernel(int n2, int m, int k, double* X, double* Xg, int g_inner, double* S, double* V,
                             double* D, double* eigw, double* tmp) {
   __shared__ double red[32];
   block_gram(m, k, X, g_inner ? Xg : X, S, red);
@@ -142,15 +176,21 @@ __global__ void svqb_kernel(int n2, int m, int k, double* X, double* Xg, int g_i
   cta_eig_sym(k, S, k, k, D, V, k, w, red);
   __syncthreads();
   const double dmax = D[0];
+  // 1 / sqrt(D_c) once per column (0 for a numerically null direction)
+  __shared__ double rs[64];
+  for (int c = threadIdx.x; c < k && c < 64; c += blockDim.x)
+    rs[c] = (dmax > 0.0 && D[c] > 1e-13 * dmax) ? 1.0 / sqrt(D[c]) : 0.0;
+  __syncthreads();
   const int passes = Xg ? 2 : 1;
   for (int pass = 0; pass < passes; ++pass) {
     double* M = (pass == 0) ? X : Xg;
     for (int p = threadIdx.x; p < n2; p += blockDim.x) {
       for (int c = 0; c < k; ++c) {
         double acc = 0.0;
-        if (p < m && dmax > 0.0 && D[c] > 1e-13 * dmax) {
+        const double sc = (c < 64) ? rs[c] : ((dmax > 0.0 && D[c] > 1e-13 * dmax) ? 1.0 / sqrt(D[c]) : 0.0);
+        if (p < m && sc != 0.0) {
           for (int a = 0; a < k; ++a) acc += M[(size_t)p * k + a] * V[a * k + c];
-          acc /= sqrt(D[c]);
+          acc *= sc;
         }
         tmp[(size_t)p * k + c] = acc;
       }
@@ -161,7 +201,7 @@ __global__ void svqb_kernel(int n2, int m, int k, double* X, double* Xg, int g_i
 }
 
 // One block: with W G-orthonormal and GW: M = GW^T GW, eig -> ritz (descending), WU, GWU.
-__global__ void rayleigh_ritz_kernel(int n2, int m, int k, const double* W, const double* GW, double* M, double* U,
+__global__ void __launch_bounds__(512) rayleigh_ritz_kernel(int n2, int m, int k, const double* W, const double* GW, double* M, double* U,
                                      double* ritz, double* eigw, double* WU, double* GWU, int* status) {
   __shared__ double red[32];
   block_gram(m, k, GW, GW, M, red);
@@ -404,13 +444,12 @@ __global__ void gram_downdate_kernel(double* G, int n2, int r, const double* GWU
   G[(size_t)p * n2 + q] = x;
   if (Gf) Gf[(size_t)p * n2 + q] = (float)x;
   if (Gb) {
-    const __nv_bfloat16 b0 = __double2bfloat16(x);
-    const double r1 = x - (double)__bfloat162float(b0);
-    const __nv_bfloat16 b1 = __double2bfloat16(r1);
+    __nv_bfloat16 b0, b1, b2;
+    g_levels(x, b0, b1, b2);
     __nv_bfloat16* o = Gb + (size_t)p * ldg + q;
     o[0] = b0;
     o[glevel] = b1;
-    o[2 * glevel] = __double2bfloat16(r1 - (double)__bfloat162float(b1));
+    o[2 * glevel] = b2;
   }
 }
 

@@ -20,8 +20,9 @@ def _rows(n=600, d=256):
 @pytest.mark.parametrize("prec", [0, 3])
 def test_profile_select_times_only_the_chosen_classes(prec):
     A = _rows()
-    plain = p.Sketch(256, 64, prec=prec)
-    plain.update(A)
+    plain = p.Sketch(256, 64, prec=prec)   # fed in the same two calls
+    plain.update(A[:300])
+    plain.update(A[300:])
     prof = p.Sketch(256, 64, prec=prec, profile=True)
     prof.update(A[:300])
     full = {k["name"]: k["launches"] for k in prof.profile()}
