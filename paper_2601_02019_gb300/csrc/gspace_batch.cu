@@ -104,52 +104,66 @@ __global__ void dot_kernel(const double* x, const double* y, int m, const int* z
   if (threadIdx.x == 0) *out = (*zero) ? 0.0 : s;
 }
 
-// S = sym(A^T B) over the first m rows (A, B row-major n2 x k).  For k <= 8
-// every thread accumulates all k (k + 1) / 2 entries over its rows in one pass
-// (a row's k values are contiguous), and the entries are then reduced
-// together, each in the order of block_sum: a warp butterfly, then warp 0 over
-// the warps' sums.
-__device__ void block_gram(int m, int k, const double* A, const double* B, double* S, double* red) {
-  if (k <= 8) {
-    constexpr int kT = 36;   // entries (a, c), a <= c < 8
-    __shared__ double wsum[32][kT];
-    double acc[kT];
+// S = sym(A^T B) over the first m rows (A, B row-major n2 x k), for k = K
+// known at compile time: every thread accumulates the K (K + 1) / 2 entries
+// over its rows in one pass (a row's K values are contiguous), and the
+// entries are then reduced together, each in the order of block_sum: a warp
+// butterfly, then warp 0 over the warps' sums.  FP64 issue is scarce on this
+// part, so no entry beyond k is computed.
+template <int K>
+__device__ void block_gram_k(int m, const double* A, const double* B, double* S) {
+  constexpr int kT = K * (K + 1) / 2;
+  __shared__ double wsum[32][kT];
+  double acc[kT];
 #pragma unroll
-    for (int t = 0; t < kT; ++t) acc[t] = 0.0;
-    for (int p = threadIdx.x; p < m; p += blockDim.x) {
-      double ar[8], br[8];
+  for (int t = 0; t < kT; ++t) acc[t] = 0.0;
+  for (int p = threadIdx.x; p < m; p += blockDim.x) {
+    double ar[K], br[K];
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        ar[a] = (a < k) ? A[(size_t)p * k + a] : 0.0;
-        br[a] = (a < k) ? B[(size_t)p * k + a] : 0.0;
+    for (int a = 0; a < K; ++a) {
+      ar[a] = A[(size_t)p * K + a];
+      br[a] = B[(size_t)p * K + a];
+    }
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+      for (int c = a; c < K; ++c, ++t) acc[t] += 0.5 * (ar[a] * br[c] + ar[c] * br[a]);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int t = 0; t < kT; ++t) {
+    const double v = warp_sum(acc[t]);
+    if (lane == 0) wsum[wid][t] = v;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+      for (int c = a; c < K; ++c, ++t) {
+        const double v = warp_sum((lane < nw) ? wsum[lane][t] : 0.0);
+        if (lane == 0) { S[a * K + c] = v; S[c * K + a] = v; }
       }
-      int t = 0;
-#pragma unroll
-      for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int c = a; c < 8; ++c, ++t)
-          if (c < k) acc[t] += 0.5 * (ar[a] * br[c] + ar[c] * br[a]);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int t = 0; t < kT; ++t) {
-      const double v = warp_sum(acc[t]);
-      if (lane == 0) wsum[wid][t] = v;
-    }
+  }
+  __syncthreads();
+}
+
+__device__ void block_gram(int m, int k, const double* A, const double* B, double* S, double* red) {
+  if (k == 2) { block_gram_k<2>(m, A, B, S); return; }
+  if (k == 4) { block_gram_k<4>(m, A, B, S); return; }
+  if (k == 8) { block_gram_k<8>(m, A, B, S); return; }
+  if (k < 8) {
+    for (int a = 0; a < k; ++a)
+      for (int c = a; c < k; ++c) {
+        double acc = 0.0;
+        for (int p = threadIdx.x; p < m; p += blockDim.x)
+          acc += 0.5 * (A[(size_t)p * k + a] * B[(size_t)p * k + c] + A[(size_t)p * k + c] * B[(size_t)p * k + a]);
+        acc = block_sum(acc, red);
+        if (threadIdx.x == 0) { S[a * k + c] = acc; S[c * k + a] = acc; }
+      }
     __syncthreads();
-    if (wid == 0) {
-      int t = 0;
-#pragma unroll
-      for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int c = a; c < 8; ++c, ++t) {
-          if (c >= k) continue;
-          const double v = warp_sum((lane < nw) ? wsum[lane][t] : 0.0);
-          if (lane == 0) { S[a * k + c] = v; S[c * k + a] = v; }
-        }
-    }
-    __syncthreads();
-    (void)red;
     return;
   }
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
