@@ -171,7 +171,9 @@ __device__ __forceinline__ void tc_finals(const TcArgs& a, const float* s, int f
 // buffer is then written while a slower CTA still reads it: a CTA writes only
 // its own row block's rows of the product planes, and a CTA at iteration it + 2
 // has waited for everyone's reduction of it + 1.
-template <int NPASS>
+// SPL bounds the K splits the reduction sums (nks <= SPL); with SPL = 8 a
+// round of the reduction issues the loads of four steps instead of two.
+template <int NPASS, int SPL>
 __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
                                                                  const __grid_constant__ UmmaOperand mG,
                                                                  const __grid_constant__ UmmaOperand mY) {
@@ -446,27 +448,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
     const int row = rw0 + rl;
     const bool row_on = rl < R;
     const bool in_y = row < a.ldy;        // rows past the FP32 columns are zero (>= m_t)
-    for (int pb0 = 0; pb0 < nact; pb0 += 2 * pstep) {
-      float2 zz[2][kTcMaxSplits];
+    constexpr int HS = 32 / SPL;          // steps whose loads go out together
+    for (int pb0 = 0; pb0 < nact; pb0 += HS * pstep) {
+      float2 zz[HS][SPL];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < HS; ++h) {
         const int pl = pb0 + h * pstep + warp * (32 / lpp) + sub;
         const bool on = pl < nact && row_on;
         const float* pp = part + (size_t)row * a.nc + 2 * (pa0 + pl);
 #pragma unroll
-        for (int k = 0; k < kTcMaxSplits; ++k)
+        for (int k = 0; k < SPL; ++k)
           zz[h][k] = (on && k < a.nks) ? __ldcg(reinterpret_cast<const float2*>(pp + (size_t)k * a.pplane))
                                        : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < HS; ++h) {
         const int pl = pb0 + h * pstep + warp * (32 / lpp) + sub;
         const bool pon = pl < nact;
         const bool on = pon && row_on;
         const int p = pa0 + (pon ? pl : 0);
         float za = 0.f, zb = 0.f;
 #pragma unroll
-        for (int k = 0; k < kTcMaxSplits; ++k) {
+        for (int k = 0; k < SPL; ++k) {
           za += zz[h][k].x;
           zb += zz[h][k].y;
         }
@@ -640,14 +643,17 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
   const int kc0 = (int)std::max<long long>(64, (need + 63) / 64 * 64);
   const int nks0 = (kpad + kc0 - 1) / kc0;
   const size_t smem = 1024 + (size_t)kTcStages * 2 * (UM * UK * 2 + (size_t)nc * UK * 2);
-  const int v = 0;
-  const void* fn = (const void*)batch_tc_kernel<3>;
-  if (smem > td.attr[v]) {
-    AS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    td.attr[v] = smem;
+  const void* fns[2] = {(const void*)batch_tc_kernel<3, 8>, (const void*)batch_tc_kernel<3, 16>};
+  int per = 1 << 30;
+  for (int v = 0; v < 2; ++v) {
+    if (smem > td.attr[v]) {
+      AS_CUDA_TRY(cudaFuncSetAttribute(fns[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      td.attr[v] = smem;
+    }
+    int pv = 0;
+    AS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pv, fns[v], kTcThreads, smem));
+    per = std::min(per, pv);
   }
-  int per = 0;
-  AS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kTcThreads, smem));
   const int sms = td.sms;
   lk.unlock();
   // the split shape of a candidate K-split count: (kc, nks) with kc a multiple
@@ -706,7 +712,7 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
     a.sig2 = pb.sig2; a.ritz = pb.ritz;
     void* args[] = {&a, (void*)&tb.mG, &mY};
     if (prof) prof->begin(PK_BATCH_TC, s);
-    AS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(ncta), dim3(kTcThreads), args, smem, s));
+    AS_CUDA_TRY(cudaLaunchCooperativeKernel(fns[nks <= 8 ? 0 : 1], dim3(ncta), dim3(kTcThreads), args, smem, s));
     count_launches(1);
     if (prof) {
       double m2 = 0.0;

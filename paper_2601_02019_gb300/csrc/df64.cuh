@@ -159,7 +159,8 @@ __device__ __forceinline__ df64 df_sqrt(df64 a) {
 
 // 1 / sqrt(a) for a > 0 without a division.  a is first scaled by an exact
 // power of two, a = a' 2^(2k) with a' in [1/2, 2), so that no intermediate
-// leaves the FP32 range.  Then the FP32 estimate r0 = rsqrtf(a'.hi) (relative
+// leaves the FP32 range (the scale comes from the exponent bits, with
+// frexpf/ldexpf only for a subnormal or huge a.hi).  Then the FP32 estimate r0 = rsqrtf(a'.hi) (relative
 // error below 2^-21) is refined by the binomial series of (1 - h)^(-1/2),
 // with h = 1 - a' r0^2 formed in df64:
 //   1/sqrt(a') = r0 (1 + h/2 + 3h^2/8 + O(h^3)),
@@ -168,10 +169,27 @@ __device__ __forceinline__ df64 df_sqrt(df64 a) {
 // the result carries about 46 significant bits.
 __device__ __forceinline__ df64 df_rsqrt(df64 a) {
   if (!(a.hi > 0.f)) return df64{0.f, 0.f};
-  int ex;
-  (void)frexpf(a.hi, &ex);   // a.hi = m 2^ex, m in [1/2, 1)
-  const int k = ex >> 1;     // floor(ex / 2)
-  const df64 as{ldexpf(a.hi, -2 * k), ldexpf(a.lo, -2 * k)};
+  // the exponent from the bits (a normal a.hi; otherwise frexpf/ldexpf)
+  const int eb = (__float_as_int(a.hi) >> 23) & 0xff;
+  const int k = (eb - 126) >> 1;   // floor(ex / 2) for a.hi = m 2^ex, m in [1/2, 1)
+  const bool fast = eb >= 1 && eb <= 254 && 127 - 2 * k >= 1 && 127 - 2 * k <= 254;
+  df64 as;
+  if (fast) {
+    const float sc = __int_as_float((127 - 2 * k) << 23);   // 2^-2k, exact
+    as = df64{a.hi * sc, a.lo * sc};
+  } else {
+    int ex;
+    (void)frexpf(a.hi, &ex);
+    const int kk = ex >> 1;
+    as = df64{ldexpf(a.hi, -2 * kk), ldexpf(a.lo, -2 * kk)};
+    const float r0s = rsqrtf(as.hi);
+    float p, e;
+    two_prod(r0s, r0s, p, e);
+    const df64 h = df_sub(df64{1.f, 0.f}, df_mul(as, df64{p, e}));
+    const float hh = __fadd_rn(h.hi, h.lo);
+    const df64 r = df_renorm(r0s, __fmul_rn(r0s, __fmaf_rn(0.375f * hh, hh, 0.5f * hh)));
+    return df64{ldexpf(r.hi, -kk), ldexpf(r.lo, -kk)};
+  }
   const float r0 = rsqrtf(as.hi);
   float p, e;
   two_prod(r0, r0, p, e);    // r0^2 = p + e exactly
@@ -180,7 +198,8 @@ __device__ __forceinline__ df64 df_rsqrt(df64 a) {
   const float hh = __fadd_rn(h.hi, h.lo);
   const float corr = __fmul_rn(r0, __fmaf_rn(0.375f * hh, hh, 0.5f * hh));
   const df64 r = df_renorm(r0, corr);
-  return df64{ldexpf(r.hi, -k), ldexpf(r.lo, -k)};
+  const float sk = __int_as_float((127 - k) << 23);   // 2^-k, exact (127 - k in [64, 190])
+  return df64{r.hi * sk, r.lo * sk};
 }
 
 }  // namespace as
