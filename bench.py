@@ -453,8 +453,9 @@ EXTRA = {
     # arrivals at three fractions of it give the latency percentiles
     "serve_c4_s2000": dict(sessions=2000, requests=2000, loads=(0.5, 0.8, 0.95), pool_rows=4096, dmax=8192),
     # many sketches in one launch: the C3 rows of 16 sites fed through
-    # sketch_update_grouped (lockstep blocks, grouped batched iterations),
-    # beside sketch_update_many (each sketch independent on a worker thread)
+    # sketch_update_grouped (each sketch on its own worker thread, the launch
+    # combiner grouping their batched iterations), beside sketch_update_many
+    # (each sketch independent on a worker thread)
     "group_d512_l64_m16": dict(d=512, ell=64, m=16, rows_per_site=256),
 }
 
@@ -570,8 +571,8 @@ def serve_arm(args) -> None:
 
 
 def group_arm(args) -> None:
-    """sketch_update_grouped over 16 sketches (lockstep blocks, grouped
-    launches) and, on fresh sketches, the same rows through sketch_update_many
+    """sketch_update_grouped over 16 sketches (each on its own worker thread,
+    their batched iterations grouped by the launch combiner) and, on fresh sketches, the same rows through sketch_update_many
     (each sketch progressing independently on a worker thread).
     Both calls return after their work is done, so each step is timed on the
     host clock with the device synchronised on both sides."""

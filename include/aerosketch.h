@@ -312,8 +312,8 @@ as_status as_sw_destroy(as_sw* w);
  *
  * Many independent sketches (sessions, levels, sites) progress at once: each
  * on a stream of its own, driven by host worker threads, so that their
- * kernels overlap on the GPU; or in lockstep with shared launches
- * (sketch_update_grouped).  A sketch's kernels and launch shapes depend only
+ * kernels overlap on the GPU; or with their batched iterations sharing
+ * cooperative launches through a launch combiner (sketch_update_grouped).  A sketch's kernels and launch shapes depend only
  * on its own configuration and rows, so its results are bitwise the same
  * alone and in any mix. */
 

@@ -452,8 +452,9 @@ def update_many(sketches: list, blocks: list) -> None:
 
 
 def update_grouped(sketches: list, blocks: list) -> None:
-    """sketch_update_grouped: the same update in lockstep blocks whose batched
-    iterations share cooperative launches (bitwise the same results)."""
+    """sketch_update_grouped: the same update, each sketch on its own worker
+    thread, with the blocks' batched iterations sharing cooperative launches
+    through the launch combiner (bitwise the same results)."""
     _many("sketch_update_grouped", sketches, blocks)
 
 
