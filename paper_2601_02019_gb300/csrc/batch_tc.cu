@@ -172,7 +172,8 @@ __device__ __forceinline__ void tc_finals(const TcArgs& a, const float* s, int f
 // its own row block's rows of the product planes, and a CTA at iteration it + 2
 // has waited for everyone's reduction of it + 1.
 // SPL bounds the K splits the reduction sums (nks <= SPL); with SPL = 8 a
-// round of the reduction issues the loads of four steps instead of two.
+// round of the reduction issues the loads of six steps instead of two (all
+// 96 pairs of a block in one round when a half warp takes a pair).
 template <int NPASS, int SPL>
 __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
                                                                  const __grid_constant__ UmmaOperand mG,
@@ -448,7 +449,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
     const int row = rw0 + rl;
     const bool row_on = rl < R;
     const bool in_y = row < a.ldy;        // rows past the FP32 columns are zero (>= m_t)
-    constexpr int HS = 32 / SPL;          // steps whose loads go out together
+    constexpr int HS = (SPL == 8) ? 6 : 2;   // steps whose loads go out together
     for (int pb0 = 0; pb0 < nact; pb0 += HS * pstep) {
       float2 zz[HS][SPL];
 #pragma unroll
