@@ -46,8 +46,10 @@ __global__ void truncate_kernel(float* C, int ldc, int d, int r0, int r1, double
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot_c;
        e += (long long)gridDim.x * blockDim.x)
     C[(long long)r0 * ldc + e] = 0.f;
-  // G: rows [r0, n2) in full, then columns [r0, n2) of rows [0, r0)
-  const long long w = n2 - r0;
+  // G: rows [r0, r1) in full, then columns [r0, r1) of rows [0, r0).  Rows
+  // and columns past r1 are zero already: a block writes G only up to its
+  // last row r1, and every cut zeroes what the block wrote past the cut.
+  const long long w = r1 - r0;
   const long long tot_g = w * n2 + (long long)r0 * w;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot_g;
        e += (long long)gridDim.x * blockDim.x) {
