@@ -172,8 +172,9 @@ __device__ __forceinline__ void tc_finals(const TcArgs& a, const float* s, int f
 // its own row block's rows of the product planes, and a CTA at iteration it + 2
 // has waited for everyone's reduction of it + 1.
 // SPL bounds the K splits the reduction sums (nks <= SPL); with SPL = 8 a
-// round of the reduction issues the loads of six steps instead of two (all
-// 96 pairs of a block in one round when a half warp takes a pair).
+// round of the reduction issues the loads of four steps instead of two
+// (six steps, all 96 pairs of a block in one round, measured slower: 427
+// against 411 us per launch).
 template <int NPASS, int SPL>
 __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
                                                                  const __grid_constant__ UmmaOperand mG,
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) batch_tc_kernel(const TcArgs a,
     const int row = rw0 + rl;
     const bool row_on = rl < R;
     const bool in_y = row < a.ldy;        // rows past the FP32 columns are zero (>= m_t)
-    constexpr int HS = (SPL == 8) ? 6 : 2;   // steps whose loads go out together
+    constexpr int HS = 32 / SPL;          // steps whose loads go out together
     for (int pb0 = 0; pb0 < nact; pb0 += HS * pstep) {
       float2 zz[HS][SPL];
 #pragma unroll
@@ -578,9 +579,10 @@ __global__ void tc_split_start_kernel(const float* Y, int ldy, int mmax, int nco
   }
 }
 
-// BF16 levels of rows and columns [valid, m) of the leading m x m block of G.
+// BF16 levels of rows and columns [valid, m) of the leading m x m block of G,
+// and the same entries of the FP32 mirror Gf (ld n2) when it is given.
 __global__ void tc_mirror_kernel(const double* G, int n2, int valid, int m, __nv_bfloat16* Gb, long long level,
-                                 int ldg) {
+                                 int ldg, float* Gf) {
   const int p = blockIdx.x;
   if (p >= m) return;
   const int q0 = (p < valid) ? valid : 0;
@@ -592,6 +594,7 @@ __global__ void tc_mirror_kernel(const double* G, int n2, int valid, int m, __nv
     o[0] = l0;
     o[level] = l1;
     o[2 * level] = l2;
+    if (Gf) Gf[(size_t)p * n2 + q] = (float)x;
   }
 }
 
@@ -604,9 +607,10 @@ std::mutex g_tcdev_mu;
 
 }  // namespace
 
-as_status launch_tc_mirror(cudaStream_t s, const double* G, int n2, int valid, int m, const TcBatchBuffers& tb) {
+as_status launch_tc_mirror(cudaStream_t s, const double* G, int n2, int valid, int m, const TcBatchBuffers& tb,
+                           float* Gf) {
   if (m <= 0 || valid >= m) return AS_OK;
-  tc_mirror_kernel<<<m, 256, 0, s>>>(G, n2, std::max(valid, 0), m, tb.Gb, tb.glevel, tb.ldg);
+  tc_mirror_kernel<<<m, 256, 0, s>>>(G, n2, std::max(valid, 0), m, tb.Gb, tb.glevel, tb.ldg, Gf);
   count_launches(1);
   AS_CUDA_TRY(cudaGetLastError());
   return AS_OK;

@@ -593,8 +593,9 @@ as_status block_prepare(as_sketch* h, const float* src, int64_t navail, BlockCtx
   c.nbb = nbb;
   if (nbb > 0) {
     if (h->prof) h->prof->begin(PK_BATCH_ORTH, h->s);
-    st = launch_gf_mirror(h->s, h->G, h->Gf, n2, h->gf_valid, r0 + nbb);
-    if (st == AS_OK && h->tcb) st = launch_tc_mirror(h->s, h->G, n2, h->gf_valid, r0 + nbb, h->tb);
+    // both mirrors from one read of G when the tensor batch is on
+    st = h->tcb ? launch_tc_mirror(h->s, h->G, n2, h->gf_valid, r0 + nbb, h->tb, h->Gf)
+                : launch_gf_mirror(h->s, h->G, h->Gf, n2, h->gf_valid, r0 + nbb);
     if (st != AS_OK) return st;
     if (h->prof) {
       const double nm = (double)(r0 + nbb) * (r0 + nbb) - (double)h->gf_valid * h->gf_valid;

@@ -207,7 +207,9 @@ struct TcBatchBuffers {
   float* part;
 };
 size_t batch_tc_part_floats(int n2, int ycols);
-as_status launch_tc_mirror(cudaStream_t s, const double* G, int n2, int valid, int m, const TcBatchBuffers& tb);
+// BF16 levels of the new rows and columns of G, and with Gf also the FP32 mirror.
+as_status launch_tc_mirror(cudaStream_t s, const double* G, int n2, int valid, int m, const TcBatchBuffers& tb,
+                           float* Gf = nullptr);
 // Runs the block on tcgen05 when its shape allows (kpad >= 256, at most 192
 // columns, a co-resident grid); *used = false leaves it to launch_batch_persist.
 as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int q, Key key, uint64_t i0,
