@@ -50,7 +50,7 @@ DF64_FP32_OPS_PER_FMA = 15
 # levels read once, 4 kpad^2).  A launch's traffic grows with kpad^2 like its
 # algorithmic bytes, so the line's traffic is this ratio times the mean
 # algorithmic bytes of the timed launches.  Set to None when the kernel changes.
-TRAFFIC_RATIO = {"batch_tc": (13.152512e6 + 0.22656e6) / (4.0 * 1792 ** 2)}
+TRAFFIC_RATIO = {"batch_tc": (13.152e6 + 0.199424e6) / (4.0 * 1792 ** 2)}
 
 
 def _peaks():
