@@ -359,12 +359,19 @@ __global__ void __launch_bounds__(32) invit_df(int n, int nev, TriWork w, const 
 // The same inverse iteration in df64 on the FP32 pipes, on T / ||T|| (dd, ee):
 // the FP64 recurrences of invit_df are long dependent chains of slow FP64
 // instructions on this part.  Same factorisation (partial pivoting, pivots
-// kept at least eps in magnitude), same three iterations from ii_start, same
-// storage (a df64 value in each 8-byte slot of lu and X), same staging.  The
-// sum of squares is accumulated in df64 (compensated) and the reciprocal norm
-// taken with df_rsqrt.  An iterate that leaves the FP32 range (several nearly
+// kept at least eps in magnitude), the same start ii_start, the same storage
+// (a df64 value in each 8-byte slot of lu and X), the same staging, and two
+// iterations (kInvitDdIters) instead of three.  The sum of squares is
+// accumulated in df64 (compensated) and the reciprocal norm taken with
+// df_rsqrt.  An iterate that leaves the FP32 range (several nearly
 // zero pivots on one eigenvector) is flagged in bad[j] and left for invit_df,
 // which the launcher runs on the flagged eigenvectors afterwards.
+// Two iterations: with eigenvalues bisected to 2^-44 of ||T||, the error of an
+// eigenvector after two solves is of order (2^-44 / gap)^2, below the 1e-8
+// orthogonality of the solver's tests down to the gap at which cluster_mgs
+// takes over (1e-9 relative); the FP64 fallback keeps three.
+constexpr int kInvitDdIters = 2;
+
 __global__ void __launch_bounds__(32) invit_dd(int n, int nev, const df64* dd, const df64* ee, const double* norms,
                                                const double* evals, double* X, int ldx, double* lu, int* bad) {
   __shared__ df64 stg[2][kInvitArrays][kInvitTile][32];
@@ -421,7 +428,7 @@ __global__ void __launch_bounds__(32) invit_dd(int n, int nev, const df64* dd, c
   const size_t sx = (size_t)ldx;
   df64 rhs = one;
   bool finite = true;
-  for (int it = 0; it < 3; ++it) {
+  for (int it = 0; it < kInvitDdIters; ++it) {
     const int nsteps = n - 1;
     const int ntiles = (nsteps + kInvitTile - 1) / kInvitTile;
     auto stage_fwd = [&](int t, int buf) {
