@@ -1042,8 +1042,10 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
       }
       const void* fn = shape == 1 ? (const void*)tri_persist_df<256, 16>
                      : shape == 2 ? (const void*)tri_persist_df<512, 8>
+                     : shape == 3 ? (const void*)tri_persist_df<512, 4>
+                     : shape == 4 ? (const void*)tri_persist_df<256, 8>
                                   : (const void*)tri_persist_df<512, 16>;
-      const int threads = shape == 1 ? 256 : 512;
+      const int threads = (shape == 1 || shape == 4) ? 256 : 512;
       AS_CUDA_TRY(as_raise_smem_limit(fn, smem));
       int per = 0;
       AS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem));
@@ -1054,12 +1056,13 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
       count_launches(1);
       return AS_OK;
     };
-    // shapes (threads, entries in flight): (512, 16), (256, 16), (512, 8)
-    static const int kTriShapes[3] = {0, 1, 2};
+    // shapes (threads, entries in flight): (512, 16), (256, 16), (512, 8),
+    // (512, 4), (256, 8)
+    static const int kTriShapes[5] = {0, 1, 2, 3, 4};
     as_status tst = AS_OK;
     bool ran = false;
     tuning = can_tune;   // copies are made only while candidates are timed
-    const int shape = can_tune ? tune_pick(s, "tri_persist_df", n, kTriShapes, 3, tri, &tst, &ran) : 0;
+    const int shape = can_tune ? tune_pick(s, "tri_persist_df", n, kTriShapes, 5, tri, &tst, &ran) : 0;
     tuning = false;
     if (tst != AS_OK) return tst;
     if (!ran) {   // a cached or default choice, straight on A
@@ -1131,17 +1134,48 @@ as_status launch_eig_large(cudaStream_t s, int n, double* A, int lda, int nev, d
     int dev = 0, sms = 0;
     AS_CUDA_TRY(cudaGetDevice(&dev));
     AS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int sw = 4;
-    while (sw > 1 && ((size_t)n * sw * sizeof(df64) > 160 * 1024 || (nev + sw - 1) / sw < 3 * sms)) sw >>= 1;
-    const size_t smem3 = (size_t)n * sw * sizeof(df64);
-    const void* fn = sw == 4 ? (const void*)bt_apply_df<4> : sw == 2 ? (const void*)bt_apply_df<2>
-                                                                     : (const void*)bt_apply_df<1>;
-    AS_CUDA_TRY(as_raise_smem_limit(fn, smem3));
-    const int nb = (nev + sw - 1) / sw;
-    if (sw == 4) bt_apply_df<4><<<nb, 256, smem3, s>>>(Ad, lda, n, nk, tf, nev, X, ldx);
-    else if (sw == 2) bt_apply_df<2><<<nb, 256, smem3, s>>>(Ad, lda, n, nk, tf, nev, X, ldx);
-    else bt_apply_df<1><<<nb, 256, smem3, s>>>(Ad, lda, n, nk, tf, nev, X, ldx);
-    count_launches(1);
+    int sw0 = 4;
+    while (sw0 > 1 && ((size_t)n * sw0 * sizeof(df64) > 160 * 1024 || (nev + sw0 - 1) / sw0 < 3 * sms)) sw0 >>= 1;
+    // the slab width is tuned per shape among those whose slab fits 160 KB,
+    // the heuristic's choice first; a tuning run starts from a copy of the
+    // eigenvectors of T kept in lu (free once the inverse iteration is done)
+    const size_t xbytes = (size_t)n * ldx * sizeof(double);
+    const bool can_tune_bt = (size_t)ldx <= 5 * (size_t)nev;
+    bool bt_tuning = false, bt_saved = false;
+    auto bt = [&](int sw) -> as_status {
+      if ((size_t)n * sw * sizeof(df64) > 160 * 1024) return AS_ENOTSUP;
+      if (bt_tuning) {
+        if (!bt_saved) AS_CUDA_TRY(cudaMemcpyAsync(lu, X, xbytes, cudaMemcpyDeviceToDevice, s));
+        else AS_CUDA_TRY(cudaMemcpyAsync(X, lu, xbytes, cudaMemcpyDeviceToDevice, s));
+        bt_saved = true;
+      }
+      const size_t smem3 = (size_t)n * sw * sizeof(df64);
+      const void* fn = sw == 4 ? (const void*)bt_apply_df<4> : sw == 2 ? (const void*)bt_apply_df<2>
+                                                                       : (const void*)bt_apply_df<1>;
+      AS_CUDA_TRY(as_raise_smem_limit(fn, smem3));
+      const int nb = (nev + sw - 1) / sw;
+      if (sw == 4) bt_apply_df<4><<<nb, 256, smem3, s>>>(Ad, lda, n, nk, tf, nev, X, ldx);
+      else if (sw == 2) bt_apply_df<2><<<nb, 256, smem3, s>>>(Ad, lda, n, nk, tf, nev, X, ldx);
+      else bt_apply_df<1><<<nb, 256, smem3, s>>>(Ad, lda, n, nk, tf, nev, X, ldx);
+      count_launches(1);
+      AS_CUDA_TRY(cudaGetLastError());
+      return AS_OK;
+    };
+    int swc[3] = {sw0, 0, 0}, nsw = 1;
+    for (int c = 4; c >= 1; c >>= 1)
+      if (c != sw0) swc[nsw++] = c;
+    as_status bst = AS_OK;
+    bool bran = false;
+    bt_tuning = can_tune_bt;
+    const int sw = can_tune_bt ? tune_pick(s, "bt_apply_df", ((long long)n << 20) | (long long)nev, swc, nsw, bt,
+                                           &bst, &bran)
+                               : sw0;
+    bt_tuning = false;
+    if (bst != AS_OK) return bst;
+    if (!bran) {
+      bst = bt(sw);
+      if (bst != AS_OK) return bst;
+    }
   }
   if (prof) prof->end(PK_EIG_BACK, s, 2.0 * (double)n * n * nev, 8.0 * (double)n * n);
   AS_CUDA_TRY(cudaGetLastError());

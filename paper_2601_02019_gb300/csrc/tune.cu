@@ -10,7 +10,8 @@
 // sketch's results do not depend on which other sketches run beside it; they
 // can differ between processes when two candidates time alike, and
 // AS_TUNE=0 in the environment turns tuning off (the first candidate, the
-// default shape, is used everywhere).
+// default shape, is used everywhere).  A candidate whose run returns
+// AS_ENOTSUP (a shape the device cannot hold) is skipped.
 #include <cstdlib>
 #include <map>
 #include <mutex>
@@ -58,10 +59,14 @@ int tune_pick(cudaStream_t s, const char* kernel, long long key, const int* choi
     if (e0) cudaEventDestroy(e0);
     return choices[0];
   }
-  int best = 0, last = -1;
+  int best = -1, last = -1;
   float best_ms = 0.f;
   for (int c = 0; c < n && *st == AS_OK; ++c) {
     *st = run(choices[c]);   // untimed: first-launch costs (module loading, attributes)
+    if (*st == AS_ENOTSUP) {   // a shape this device cannot run: skip it
+      *st = AS_OK;
+      continue;
+    }
     if (*st != AS_OK) break;
     cudaEventRecord(e0, s);
     *st = run(choices[c]);
@@ -75,13 +80,14 @@ int tune_pick(cudaStream_t s, const char* kernel, long long key, const int* choi
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (c == 0 || ms < best_ms) {
+    if (best < 0 || ms < best_ms) {
       best_ms = ms;
       best = c;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (*st == AS_OK && best < 0) *st = AS_ENOTSUP;   // no candidate could run
   if (*st != AS_OK) return choices[0];
   g_tuned[k] = choices[best];
   if (best == last) {
