@@ -623,9 +623,30 @@ size_t batch_tc_part_floats(int n2, int ycols) {
   return (size_t)2 * 16 * kpad * (size_t)std::min(ycols, kTcMaxCols) + 512;
 }
 
+as_status launch_batch_tc_prefill(cudaStream_t s, int n2, int r0, int nb, Key key, uint64_t i0,
+                                  const PersistBuffers& pb, const TcBatchBuffers& tb, bool* done) {
+  *done = false;
+  if (nb <= 0) return AS_OK;
+  const int mmax = r0 + nb;
+  const int npi = (nb + 1) / 2, P = npi + nb;
+  const int kpad = (mmax + 127) / 128 * 128;
+  const int ncols = 2 * P;
+  const int nc = (ncols + 15) / 16 * 16;
+  if (kpad < 256 || nc > kTcMaxCols || nc > (int)pb.ycols) return AS_OK;
+  launch_persist_fill(s, pb, mmax, nb, npi, r0, key, i0);
+  tc_split_start_kernel<<<ncols, 256, 0, s>>>(pb.Y + pb.ybuf, pb.ldy, mmax, ncols, kpad,
+                                              tb.Yb + (size_t)pb.ycols * tb.ldyb, tb.yblevel, tb.ldyb);
+  count_launches(1);
+  AS_CUDA_TRY(cudaGetLastError());
+  unsigned* flags = reinterpret_cast<unsigned*>(tb.part + batch_tc_part_floats(n2, (int)pb.ycols) - 512);
+  AS_CUDA_TRY(cudaMemsetAsync(flags, 0, 512 * sizeof(unsigned), s));
+  *done = true;
+  return AS_OK;
+}
+
 as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int q, Key key, uint64_t i0,
                           const PersistBuffers& pb, const TcBatchBuffers& tb, int npass, int* status, Prof* prof,
-                          bool* used) {
+                          bool* used, bool prefilled) {
   *used = false;
   if (nb <= 0) return AS_OK;
   const int mmax = r0 + nb;
@@ -690,20 +711,25 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
     if (st != AS_OK) return st;
   }
   unsigned* flags = reinterpret_cast<unsigned*>(tb.part + batch_tc_part_floats(n2, (int)pb.ycols) - 512);
-  // one launch of the block with nks K splits: starting vectors, then the kernel
+  // one launch of the block with nks K splits: starting vectors (unless the
+  // caller filled them already, launch_batch_tc_prefill), then the kernel;
+  // every tuning run refills them, since the kernel overwrites them
+  bool tuning = false;
   auto run = [&](int want) -> as_status {
     int kc = 0;
     const int nks = shape(want, &kc);
     if (nks == 0) return AS_ENOTSUP;
     const int ncta = nrb * nks, rpb = (UM + nks - 1) / nks;
-    if (prof) prof->begin(PK_BATCH_ORTH, s);
-    launch_persist_fill(s, pb, mmax, nb, npi, r0, key, i0);
-    tc_split_start_kernel<<<ncols, 256, 0, s>>>(pb.Y + pb.ybuf, pb.ldy, mmax, ncols, kpad,
-                                                tb.Yb + (size_t)pb.ycols * tb.ldyb, tb.yblevel, tb.ldyb);
-    count_launches(1);
-    AS_CUDA_TRY(cudaGetLastError());
-    if (prof) prof->end(PK_BATCH_ORTH, s, 0.0, 12.0 * mmax * (double)nb);
-    AS_CUDA_TRY(cudaMemsetAsync(flags, 0, 512 * sizeof(unsigned), s));   // CTA flags and row-block counters
+    if (tuning || !prefilled) {
+      if (prof) prof->begin(PK_BATCH_ORTH, s);
+      launch_persist_fill(s, pb, mmax, nb, npi, r0, key, i0);
+      tc_split_start_kernel<<<ncols, 256, 0, s>>>(pb.Y + pb.ybuf, pb.ldy, mmax, ncols, kpad,
+                                                  tb.Yb + (size_t)pb.ycols * tb.ldyb, tb.yblevel, tb.ldyb);
+      count_launches(1);
+      AS_CUDA_TRY(cudaGetLastError());
+      if (prof) prof->end(PK_BATCH_ORTH, s, 0.0, 12.0 * mmax * (double)nb);
+      AS_CUDA_TRY(cudaMemsetAsync(flags, 0, 512 * sizeof(unsigned), s));   // CTA flags and row-block counters
+    }
     TcArgs a{};
     a.Y = pb.Y; a.ybuf = pb.ybuf; a.ldy = pb.ldy;
     a.Yb = tb.Yb; a.yblevel = tb.yblevel; a.ybbuf = (long long)pb.ycols * tb.ldyb; a.ldyb = tb.ldyb;
@@ -736,7 +762,9 @@ as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int 
   };
   as_status st = AS_OK;
   bool ran = false;
+  tuning = true;
   const int nks = tune_pick(s, "batch_tc_nks", kpad, choices, nch, run, &st, &ran);
+  tuning = false;
   if (st != AS_OK) return st;
   if (!ran) {
     st = run(nks);

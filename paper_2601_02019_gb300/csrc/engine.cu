@@ -196,6 +196,10 @@ struct as_sketch {
   TcBatchBuffers tb{};
   int gf_valid = 0;         // leading rows/columns of Gf that equal G (FP32-rounded)
   cudaEvent_t comb_ev = nullptr;   // a deferred block's launch phase is done (launch combiner)
+  // side stream for the starting vectors of a block's tcgen05 batch, filled
+  // while the block's rows are ingested and its Gram rows formed
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_blk = nullptr, ev_fill = nullptr;
 };
 
 namespace {
@@ -218,6 +222,9 @@ void free_all(as_sketch* h) {
   if (h->tb.part) cudaFree(h->tb.part);
   if (h->h_buf) cudaFreeHost(h->h_buf);
   if (h->comb_ev) cudaEventDestroy(h->comb_ev);
+  if (h->ev_blk) cudaEventDestroy(h->ev_blk);
+  if (h->ev_fill) cudaEventDestroy(h->ev_fill);
+  if (h->s2) cudaStreamDestroy(h->s2);
   delete h->prof;
   h->prof = nullptr;
 }
@@ -573,6 +580,23 @@ as_status block_prepare(as_sketch* h, const float* src, int64_t navail, BlockCtx
   c.b = b;
   c.r0 = r0;
   c.deferred = false;
+  // tensor forms: the batch's starting vectors on the side stream, after all
+  // work already on the sketch's stream, overlapping ingest and Gram rows
+  const int nbb_early = (r0 + b == n2) ? b - 1 : b;
+  bool prefilled = false;
+  if (h->tcb && nbb_early > 0) {
+    if (!h->s2) {
+      AS_CUDA_TRY(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
+      AS_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_blk, cudaEventDisableTiming));
+      AS_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_fill, cudaEventDisableTiming));
+    }
+    AS_CUDA_TRY(cudaEventRecord(h->ev_blk, h->s));
+    AS_CUDA_TRY(cudaStreamWaitEvent(h->s2, h->ev_blk, 0));
+    as_status pst = launch_batch_tc_prefill(h->s2, n2, r0, nbb_early, h->key, (uint64_t)(h->T + 1), h->pb, h->tb,
+                                            &prefilled);
+    if (pst != AS_OK) return pst;
+    AS_CUDA_TRY(cudaEventRecord(h->ev_fill, h->s2));
+  }
   if (h->prof) h->prof->begin(PK_INGEST, h->s);
   as_status st = launch_ingest(h->s, src, d, b, d, h->C, h->ldc, r0, h->norm2, h->bad);
   if (st != AS_OK) return st;
@@ -609,9 +633,10 @@ as_status block_prepare(as_sketch* h, const float* src, int64_t navail, BlockCtx
     // 1e-4 relative tie band) and hands the event row a starting basis whose
     // Rayleigh-Ritz step is redone in FP64.
     bool on_tc = false;
+    if (h->tcb && h->s2) AS_CUDA_TRY(cudaStreamWaitEvent(h->s, h->ev_fill, 0));   // the side stream's writes
     if (h->tcb) {
       st = launch_batch_tc(h->s, n2, r0, nbb, h->k_pi, h->q, h->key, (uint64_t)(h->T + 1), h->pb, h->tb,
-                           3, h->dstatus, h->prof, &on_tc);
+                           3, h->dstatus, h->prof, &on_tc, prefilled);
       if (st != AS_OK) return st;
     }
     if (on_tc) c.batch_cls = PK_BATCH_TC;

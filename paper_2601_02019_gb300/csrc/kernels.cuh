@@ -212,9 +212,14 @@ as_status launch_tc_mirror(cudaStream_t s, const double* G, int n2, int valid, i
                            float* Gf = nullptr);
 // Runs the block on tcgen05 when its shape allows (kpad >= 256, at most 192
 // columns, a co-resident grid); *used = false leaves it to launch_batch_persist.
+// The starting vectors of a block's tcgen05 batch (and its flags cleared) on
+// stream s, ahead of launch_batch_tc(..., prefilled = true); *done = false
+// when the block's shape does not take the tcgen05 batch.
+as_status launch_batch_tc_prefill(cudaStream_t s, int n2, int r0, int nb, Key key, uint64_t i0,
+                                  const PersistBuffers& pb, const TcBatchBuffers& tb, bool* done);
 as_status launch_batch_tc(cudaStream_t s, int n2, int r0, int nb, int k_pi, int q, Key key, uint64_t i0,
                           const PersistBuffers& pb, const TcBatchBuffers& tb, int npass, int* status, Prof* prof,
-                          bool* used);
+                          bool* used, bool prefilled = false);
 
 // FP64 single-row power iteration and simultaneous iteration built from
 // multi-block products (any buffer size).  x, y: n2 doubles; zero: 1 int.
