@@ -276,50 +276,22 @@ def _run_form(p, torch, args, A_dev, d, ell, B, K, W, rank, local, ws, prec, wan
                 state=state)
 
 
-def our_arm(args) -> None:
-    import numpy as np
-    import torch
+ROOF_KINDS = {"batch_persist": "fp32", "batch_tc": "tensor", "eig_tridiag": "df64", "eig_backtransform": "df64",
+              "ingest": "hbm"}
 
-    import paper_2601_02019_gb300 as p
-    from synth import low_rank_noisy, spectrum
 
-    ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    w = WORKLOADS[args.workload]
-    d, ell, B = w["d"], w["ell"], args.rows_per_step
-    K, W = args.steps, args.warmup
-    ntot = (W + K + PROFILE_STEPS) * B
-    A = low_rank_noisy(ntot, d, w["r"], spectrum(w["spectrum"], w["r"]), stream=rank)
-    A_dev = torch.from_numpy(A).to(dev)
-    forms = [f for f in args.forms.split(",") if f]
-    head = args.prec
-    if head not in forms:
-        forms.append(head)
-    runs = {}
-    for f in forms:
-        runs[f] = _run_form(p, torch, args, A_dev, d, ell, B, K, W, rank, local, ws, PRECISIONS[f],
-                            want_state=(f == head))
-    hr = runs[head]
-    value = _job_rows_per_s(ws, K, B, hr["t_ms"] / 1000.0)
-
-    # roofline of the dominant single-kernel class of the headline form
-    # (fd_rebuild_gemm, gram_rows_gemm, event_row_fp64 and eig_fp64 span
-    # several kernels and are listed in "profile" only)
-    peaks, peak_src = _peaks()
-    prof = hr["prof"]
-    prof_full = hr["prof_full"]
-    tot_prof = sum(x["total_ms"] for x in prof_full if x["name"] != "eig_fp64") or 1.0
+def roofline(prof: list, peaks: dict, peak_src: str) -> dict:
+    """The roofline object of the dominant single-kernel class in a kernel-class
+    profile (fd_rebuild_gemm, gram_rows_gemm, event_row_fp64 and eig_fp64 span
+    several kernels and are listed in "profile" only).  `achieved` is the
+    class's algorithmic work over its event-measured time; `traffic` the
+    measured DRAM-to-algorithmic ratio times the mean algorithmic bytes per
+    launch."""
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = N_SM * FP32_SIMT_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    kinds = {"batch_persist": "fp32", "batch_tc": "tensor", "eig_tridiag": "df64", "eig_backtransform": "df64",
-             "ingest": "hbm"}
-    single = [x for x in prof if x["name"] in kinds and (x["flops"] > 0 or x["bytes"] > 0)]
+    single = [x for x in prof if x["name"] in ROOF_KINDS and (x["flops"] > 0 or x["bytes"] > 0)]
     top = max(single, key=lambda x: x["total_ms"])
-    kind = kinds[top["name"]]
+    kind = ROOF_KINDS[top["name"]]
     if kind == "hbm":
         ach = top["bytes"] / (top["total_ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
@@ -353,6 +325,44 @@ def our_arm(args) -> None:
         roof["issued_flops_per_launch"] = top["issued_flops"] / max(1, top["launches"])
         roof["algorithmic_flops_per_launch"] = top["flops"] / max(1, top["launches"])
         roof["issued_frac"] = top["issued_flops"] / (top["total_ms"] / 1e3) / 1e12 / roof["peak"]
+    return roof
+
+
+def our_arm(args) -> None:
+    import numpy as np
+    import torch
+
+    import paper_2601_02019_gb300 as p
+    from synth import low_rank_noisy, spectrum
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[args.workload]
+    d, ell, B = w["d"], w["ell"], args.rows_per_step
+    K, W = args.steps, args.warmup
+    ntot = (W + K + PROFILE_STEPS) * B
+    A = low_rank_noisy(ntot, d, w["r"], spectrum(w["spectrum"], w["r"]), stream=rank)
+    A_dev = torch.from_numpy(A).to(dev)
+    forms = [f for f in args.forms.split(",") if f]
+    head = args.prec
+    if head not in forms:
+        forms.append(head)
+    runs = {}
+    for f in forms:
+        runs[f] = _run_form(p, torch, args, A_dev, d, ell, B, K, W, rank, local, ws, PRECISIONS[f],
+                            want_state=(f == head))
+    hr = runs[head]
+    value = _job_rows_per_s(ws, K, B, hr["t_ms"] / 1000.0)
+
+    peaks, peak_src = _peaks()
+    prof = hr["prof"]
+    prof_full = hr["prof_full"]
+    tot_prof = sum(x["total_ms"] for x in prof_full if x["name"] != "eig_fp64") or 1.0
+    roof = roofline(prof, peaks, peak_src)
 
     # end to end through the C ABI from pinned host memory (host->device copy
     # inside the timed region, device->host read of the counters each step)
